@@ -1,0 +1,105 @@
+"""Chebyshev filter polynomials (Section 2.2 of arXiv 2409.15053). Test infrastructure only.
+
+Notation follows the paper: the spectrum of A lies in [lambda_min, lambda_max],
+A is mapped to [-1, 1] by eq. (transf), phi is the indicator of the mapped
+interval [alpha, beta], b_i are its Chebyshev coefficients and p_m is the
+degree-m truncation of the Chebyshev series of phi.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+# The tolerance of eq. (optimaldegree). The paper only says it is chosen
+# experimentally; 0.3123 is the reading under which the degree rule returns
+# all five automatic degrees of Table 2 (49, 49, 61, 98, 308) from the
+# Table 1 spectra and the Table 2 intervals.
+DEGREE_EPS = 0.3123
+
+
+def spectral_map(lmin: float, lmax: float):
+    """Eq. (transf): A := (A - cI)/e with c = (lmin+lmax)/2, e = (lmax-lmin)/2."""
+    c = 0.5 * (lmin + lmax)
+    e = 0.5 * (lmax - lmin)
+    return c, e
+
+
+def map_interval(alpha: float, beta: float, lmin: float, lmax: float):
+    """Apply eq. (transf) to the user's interval; returns (c, e, alpha', beta')."""
+    c, e = spectral_map(lmin, lmax)
+    return c, e, (alpha - c) / e, (beta - c) / e
+
+
+def filter_coefficients(alpha: float, beta: float, m: int) -> np.ndarray:
+    """b_0..b_m of the ideal filter phi on [alpha, beta] within [-1, 1] (Section 2.2).
+
+    b_0 = (arccos(alpha) - arccos(beta)) / pi and, for i > 0,
+    b_i = 2 (sin(i arccos(alpha)) - sin(i arccos(beta))) / (i pi).
+    """
+    ta = np.arccos(alpha)
+    tb = np.arccos(beta)
+    b = np.empty(m + 1)
+    b[0] = (ta - tb) / np.pi
+    for i in range(1, m + 1):
+        b[i] = 2.0 * (np.sin(i * ta) - np.sin(i * tb)) / (i * np.pi)
+    return b
+
+
+def ideal_filter_norm_sq(alpha: float, beta: float) -> float:
+    """||phi||^2 in the weighted Chebyshev 2-norm: the integral of 1/sqrt(1-z^2) over [alpha, beta]."""
+    return float(np.arccos(alpha) - np.arccos(beta))
+
+
+def truncation_error_sq(alpha: float, beta: float, m: int) -> float:
+    """||p_m - phi||^2 in the weighted norm, by Parseval on the orthogonality relation.
+
+    With ||T_0||^2 = pi and ||T_i||^2 = pi/2 (i > 0), the tail of the series is
+    ||phi||^2 - pi b_0^2 - (pi/2) sum_{i=1..m} b_i^2.
+    """
+    b = filter_coefficients(alpha, beta, m)
+    kept = np.pi * b[0] ** 2 + 0.5 * np.pi * float(np.sum(b[1:] ** 2))
+    return ideal_filter_norm_sq(alpha, beta) - kept
+
+
+def auto_degree(alpha: float, beta: float, eps: float = DEGREE_EPS, m_max: int = 100000) -> int:
+    """Eq. (optimaldegree): the least m > 0 with ||p_m - phi|| < eps ||phi||."""
+    norm_sq = ideal_filter_norm_sq(alpha, beta)
+    ta = np.arccos(alpha)
+    tb = np.arccos(beta)
+    b0 = (ta - tb) / np.pi
+    kept = np.pi * b0 ** 2
+    for m in range(1, m_max + 1):
+        bm = 2.0 * (np.sin(m * ta) - np.sin(m * tb)) / (m * np.pi)
+        kept += 0.5 * np.pi * bm ** 2
+        if norm_sq - kept < eps ** 2 * norm_sq:
+            return m
+    raise ValueError("degree rule did not terminate below m_max")
+
+
+def clenshaw_scalar(b: np.ndarray, z) -> np.ndarray:
+    """p_m(z) = sum_i b_i T_i(z) at points z by Clenshaw's algorithm."""
+    z = np.asarray(z, dtype=np.float64)
+    u1 = np.zeros_like(z)
+    u2 = np.zeros_like(z)
+    for k in range(len(b) - 1, 0, -1):
+        u1, u2 = b[k] + 2.0 * z * u1 - u2, u1
+    return b[0] + z * u1 - u2
+
+
+def apply_mapped(A, c: float, e: float, Y: np.ndarray) -> np.ndarray:
+    """(A - cI)/e times Y, eq. (transf) applied to a block."""
+    return (A @ Y - c * Y) / e
+
+
+def clenshaw_apply(A, c: float, e: float, b: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """p_m((A - cI)/e) V by the vectorized Clenshaw algorithm the paper uses (Section 2.2).
+
+    U_{m+1} = U_{m+2} = 0; U_k = b_k V + 2 Ahat U_{k+1} - U_{k+2} for k = m..1;
+    p_m(Ahat) V = b_0 V + Ahat U_1 - U_2.
+    """
+    V = np.asarray(V, dtype=np.float64)
+    u1 = np.zeros_like(V)
+    u2 = np.zeros_like(V)
+    for k in range(len(b) - 1, 0, -1):
+        u1, u2 = b[k] * V + 2.0 * apply_mapped(A, c, e, u1) - u2, u1
+    return b[0] * V + apply_mapped(A, c, e, u1) - u2
