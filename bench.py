@@ -1,0 +1,379 @@
+"""Benchmark: eigenpairs/s of the GPU filtered Lanczos solver on a 3D Hamiltonian-like workload.
+
+Workload (one GB300): the 7-point Dirichlet Laplacian on a 100^3 grid plus a
+diagonal potential 0.5*U(0,1) (seed 2025), n = 1e6, nnz = 6.94e6, CSR FP64;
+all eigenpairs in [alpha, beta] at the lower end of the spectrum (about 100),
+block size 4, fixed filter degree, FP64, residual tolerance 1e-10.
+
+One step = one flz_solve on the device-resident matrix: spectrum bounds,
+filter construction, block Lanczos on p(A) with full reorthogonalization,
+Rayleigh-Ritz checks and the Ritz vectors of the converged pairs (the time the
+paper's Table 2 reports, bounds estimation included). L2 is flushed (a 512 MiB
+write) before every timed step. `value` counts eigenpairs found with residual
+<= 1e-8 per second of device time.
+
+`e2e` is the same metric through the C ABI with host buffers: each step uploads
+the CSR arrays from pinned host memory (flz_matrix_create_csr), solves, and
+copies eigenvalues and eigenvectors back to the host.
+
+`--impl reference` times the CPU oracle (numpy/scipy FP64) on the host cores on
+a bounded sample of the same workload (see cpu_leg()).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import laplacian_3d_7pt, random_normal_block  # noqa: E402
+from synth.workloads import CONFIG2  # noqa: E402
+
+METRIC = "eigenpairs/s at residual 1e-8 (3D 7-point Laplacian 100^3 + potential, FP64)"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_matrix():
+    rng = np.random.Generator(np.random.PCG64(CONFIG2["seed"]))
+    g = CONFIG2["grid"]
+    return laplacian_3d_7pt(g, g, g, CONFIG2["potential_scale"] * rng.random(g ** 3))
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device=0):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def filter_bytes_per_launch(n, nnz, r, s_val=8, s_vec=8, s_acc=8):
+    # CSR once (values + int32 columns + int32 row pointers) and five vector
+    # streams: gather Y_k, read Y_{k-1}, write Y_{k+1}, read and write the sum.
+    return nnz * (s_val + 4) + 4 * (n + 1) + r * n * (3 * s_vec + 2 * s_acc)
+
+
+def filter_flops_per_launch(n, nnz, r):
+    return 2 * nnz * r + 6 * n * r
+
+
+def cpu_leg(csr, alpha, beta, degree, r, gpu_stats, budget_s=20.0):
+    """Times the CPU oracle on a bounded sample and scales it to a whole solve.
+
+    Sample: the oracle's bound estimation, then block Lanczos steps of its
+    filtered Lanczos procedure (Clenshaw filter of the same degree + CGS2 full
+    reorthogonalization) until about `budget_s` seconds have passed. A whole
+    oracle solve of this workload takes as many block steps as the GPU run
+    (`gpu_stats['iters']`) with the basis growing by r vectors per step, so the
+    sampled per-step filter cost and the reorthogonalization cost per basis
+    vector are scaled to that run; the oracle's Rayleigh-Ritz checks are not
+    counted (which favours the CPU).
+    """
+    from oracle import chebyshev, lanczos
+    A = csr.to_scipy()
+    t0 = time.time()
+    lmin, lmax, _ = lanczos.lanczos_bounds(A, random_normal_block(csr.n, 1, 12)[:, 0], 60)
+    t_bounds = time.time() - t0
+    c, e, am, bm = chebyshev.map_interval(alpha, beta, lmin, lmax)
+    coeffs = chebyshev.filter_coefficients(max(am, -1.0), min(bm, 1.0), degree)
+    Q, _ = np.linalg.qr(random_normal_block(csr.n, r, 11))
+    blocks = [Q]
+    t_filter, t_orth, steps = 0.0, 0.0, 0
+    orth_units = 0.0
+    t_start = time.time()
+    while time.time() - t_start < budget_s and steps < 200:
+        ta = time.time()
+        W = chebyshev.clenshaw_apply(A, c, e, coeffs, blocks[-1])
+        tb = time.time()
+        Qall = np.hstack(blocks)
+        C1 = Qall.T @ W
+        W = W - Qall @ C1
+        C2 = Qall.T @ W
+        W = W - Qall @ C2
+        Qn, _ = np.linalg.qr(W)
+        blocks.append(Qn)
+        tc = time.time()
+        t_filter += tb - ta
+        t_orth += tc - tb
+        orth_units += len(blocks) - 1
+        steps += 1
+    per_filter = t_filter / steps
+    per_orth_block = t_orth / orth_units  # seconds per (step x basis block)
+    iters = int(gpu_stats["iters"])
+    total = t_bounds + iters * per_filter + per_orth_block * iters * (iters + 1) / 2.0
+    return {
+        "seconds_per_solve": total,
+        "sample": (f"oracle bounds ({t_bounds:.1f} s) + {steps} block steps of FLP (degree {degree}, r = {r}) "
+                   f"in {t_filter + t_orth:.1f} s, scaled to the GPU run's {iters} block steps"),
+        "cores": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count(),
+    }
+
+
+def run_reference(args):
+    csr = make_matrix()
+    alpha, beta = CONFIG2["alpha"], CONFIG2["beta"]
+    ref_stats = {"iters": CONFIG2["reference_iters"]}
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        leg = cpu_leg(csr, alpha, beta, args.degree, args.block_size, ref_stats, budget_s=args.cpu_budget)
+        vals.append(leg)
+    timed = vals[args.warmup:]
+    per_solve = float(np.mean([v["seconds_per_solve"] for v in timed]))
+    value = CONFIG2["count"] / per_solve
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(csr, args),
+        "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": timed[-1]["cores"], "kind": "oracle",
+                         "sample": timed[-1]["sample"]},
+        "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def config_dict(csr, args):
+    return {"workload": "3D 7-point Dirichlet Laplacian 100^3 + 0.5*U(0,1) potential (seed 2025), "
+                        "all eigenpairs in [alpha, beta] at the low end of the spectrum",
+            "n": csr.n, "nnz": csr.nnz, "alpha": CONFIG2["alpha"], "beta": CONFIG2["beta"],
+            "block_size": args.block_size, "degree": args.degree, "precision": args.precision, "tol": args.tol,
+            "l2": "flushed (512 MiB write) before each timed step", "parallelism": "single GPU"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--degree", type=int, default=CONFIG2["degree"])
+    ap.add_argument("--block-size", type=int, default=4)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2409_15053_gb300 as flz
+
+    prec = {"fp64": flz.FLZ_PREC_FP64, "fp32": flz.FLZ_PREC_FP32, "bf16": flz.FLZ_PREC_BF16}[args.precision]
+    csr = make_matrix()
+    alpha, beta = CONFIG2["alpha"], CONFIG2["beta"]
+    # Replicas: every rank solves the same workload on its own GPU (the
+    # solver does not shard; no data-path collective).
+    h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+    p = flz.flz_params_default()
+    p.block_size = args.block_size
+    p.degree = args.degree
+    p.tol = args.tol
+    p.precision = prec
+    p.seed = 1 + rank
+    s = flz.flz_solver_create(h, p)
+    flz.flz_solver_set_interval(s, alpha, beta)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+
+    def one_solve():
+        st = flz.flz_solve(s, stream)
+        return st
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    times, found, stats_list = [], [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = one_solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        res = flz.flz_get_residuals(s)
+        found.append(int(np.sum(res <= 1e-8)))
+        stats_list.append(flz.flz_get_stats(s))
+        assert st == flz.FLZ_OK, flz.flz_status_string(st)
+    clocks = sampler.stop()
+    total_time = float(np.sum(times))
+    if dist is not None:
+        t = torch.tensor([total_time], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_time = float(t.item())
+    total_pairs = sum(found) * world
+    value = total_pairs / total_time
+    st = stats_list[-1]
+
+    # Roofline of the dominant kernel (the fused Chebyshev step), from the
+    # solver's own CUDA-event timing of its filter applications.
+    launches_filter = st["iters"] * st["degree"]
+    ms_per_launch = st["ms_filter"] / max(launches_filter, 1)
+    nbytes = filter_bytes_per_launch(csr.n, csr.nnz, args.block_size)
+    nflops = filter_flops_per_launch(csr.n, csr.nnz, args.block_size)
+    hbm, hbm_src = peaks()
+    achieved_gbs = nbytes / (ms_per_launch * 1e-3) / 1e9
+    achieved_tflops = nflops / (ms_per_launch * 1e-3) / 1e12
+    fp64_peak = 1.25  # TFLOP/s nominal FP64 of GB300 (recipe table); DFMA throughput bound
+    roofline = {
+        "kernel": "cheb_step_kernel (fused Chebyshev step, FP64)",
+        "bound": "alu" if args.precision == "fp64" else "hbm",
+        "achieved": achieved_tflops if args.precision == "fp64" else achieved_gbs,
+        "peak": fp64_peak if args.precision == "fp64" else hbm,
+        "unit": "TFLOP/s" if args.precision == "fp64" else "GB/s",
+        "frac": (achieved_tflops / fp64_peak) if args.precision == "fp64" else achieved_gbs / hbm,
+        "traffic": None,
+        "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm, "hbm_frac": achieved_gbs / hbm,
+        "hbm_peak_source": hbm_src, "algorithmic_bytes_per_launch": nbytes, "flops_per_launch": nflops,
+        "ms_per_launch": ms_per_launch,
+    }
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_leg(flz, torch, csr, p, alpha, beta, stream, args)
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        leg = cpu_leg(csr, alpha, beta, args.degree, args.block_size, st, budget_s=args.cpu_budget)
+        cpu = {"value": CONFIG2["count"] / leg["seconds_per_solve"], "unit": "eigenpairs/s",
+               "cores": leg["cores"], "kind": "oracle", "sample": leg["sample"]}
+
+    flz.flz_solver_destroy(s)
+    flz.flz_matrix_destroy(h)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_time / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[args.precision],
+            "data": "synthetic", "config": config_dict(csr, args), "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": int(sum(x["kernel_launches"] for x in stats_list)), "clocks": clocks,
+            "solver": {k: st[k] for k in ("iters", "matvecs", "count", "degree", "checks", "lmin", "lmax",
+                                          "max_residual", "ms_bounds", "ms_filter", "ms_orth", "ms_check",
+                                          "ms_total", "basis_vectors", "kernel_launches")},
+            "found_per_step": found,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def e2e_leg(flz, torch, csr, p, alpha, beta, stream, args):
+    """Same metric through the C ABI from pinned host buffers, copies included."""
+    rp = torch.from_numpy(csr.rowptr).pin_memory()
+    cl = torch.from_numpy(csr.col).pin_memory()
+    vl = torch.from_numpy(csr.val).pin_memory()
+    total, pairs, h2d, d2h = 0.0, 0, 0, 0
+    out = None
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = flz.flz_matrix_create_csr(csr.n, csr.nnz, rp.data_ptr(), cl.data_ptr(), vl.data_ptr())
+        s = flz.flz_solver_create(h, p)
+        flz.flz_solver_set_interval(s, alpha, beta)
+        flz.flz_solve(s, stream)
+        cnt = flz.flz_get_count(s)
+        vals = flz.flz_get_eigenvalues(s)
+        res = flz.flz_get_residuals(s)
+        if out is None or out.shape[0] < cnt:
+            out = torch.empty((max(cnt, 1), csr.n), dtype=torch.float64).pin_memory()
+        flz.flz_get_eigenvectors(s, out.data_ptr(), csr.n, out.shape[0], flz.FLZ_HOST)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        flz.flz_solver_destroy(s)
+        flz.flz_matrix_destroy(h)
+        if it >= args.warmup:
+            total += dt
+            pairs += int(np.sum(res <= 1e-8))
+            h2d = 4 * (csr.n + 1) + 12 * csr.nnz
+            d2h = 8 * cnt * csr.n + 16 * cnt
+            del vals
+    return {"value": pairs / total, "unit": "eigenpairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+if __name__ == "__main__":
+    main()

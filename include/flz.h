@@ -1,0 +1,210 @@
+/*
+ * flz.h -- C ABI of a GB300 (sm_103a) filtered Lanczos eigensolver.
+ *
+ * The library computes all eigenpairs (lambda, x) of a real sparse symmetric
+ * matrix A with lambda in a user interval [alpha, beta] by the filtered
+ * Lanczos procedure of arXiv 2409.15053 (Cucheb): a Chebyshev filter
+ * polynomial p built from the closed-form coefficients of the indicator of
+ * [alpha, beta] (Section 2.2), block Lanczos with full reorthogonalization on
+ * p(A) (Sections 2.3, 3.2.2), and Rayleigh quotients of the Ritz vectors
+ * (eq. rayleigh).
+ *
+ * Conventions for every entry point:
+ *  - Every function returns flz_status; FLZ_OK is 0. No exception crosses the
+ *    ABI. After a failure, flz_last_error() returns a message for the calling
+ *    thread (valid until that thread's next failing call).
+ *  - "Device" pointers are CUDA global-memory addresses on the current device;
+ *    "host" pointers are ordinary CPU memory. The library never frees memory
+ *    it did not allocate. Handles own every device buffer they allocate until
+ *    their destroy call.
+ *  - Blocks of vectors are n x r, row-major (row i's r entries contiguous,
+ *    leading dimension r), FP64, unless stated otherwise.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Calls that take a stream are asynchronous with respect to the
+ *    host unless stated otherwise; calls without one synchronize the device.
+ */
+#ifndef FLZ_H
+#define FLZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum flz_status {
+  FLZ_OK = 0,
+  FLZ_ERR_INVALID_ARG = 1,    /* null pointer, size out of range, bad enum */
+  FLZ_ERR_NOT_SYMMETRIC = 2,  /* a_ij != a_ji for a stored entry (Section 3.2.1 requires symmetry) */
+  FLZ_ERR_BAD_CSR = 3,        /* rowptr not monotone / not ending at nnz, column out of range or unsorted */
+  FLZ_ERR_EMPTY_INTERVAL = 4, /* [alpha, beta] misses [lambda_min, lambda_max] (Section 3.2.2 validity check) */
+  FLZ_ERR_NOT_CONVERGED = 5,  /* basis capacity reached first; partial results remain readable */
+  FLZ_ERR_OUT_OF_MEMORY = 6,  /* a device or host allocation failed */
+  FLZ_ERR_CUDA = 7,           /* a CUDA runtime call or kernel launch failed */
+  FLZ_ERR_TIMEOUT = 8,        /* a bounded device-side wait expired */
+  FLZ_ERR_CAPACITY = 9,       /* a caller-provided output buffer is too small */
+  FLZ_ERR_NO_INTERVAL = 10,   /* flz_solve before flz_solver_set_interval */
+  FLZ_ERR_NOT_SOLVED = 11     /* a result getter before a successful or partial solve */
+} flz_status;
+
+typedef enum flz_dtype { FLZ_F64 = 0, FLZ_F32 = 1, FLZ_BF16 = 2 } flz_dtype;
+typedef enum flz_memspace { FLZ_HOST = 0, FLZ_DEVICE = 1 } flz_memspace;
+
+/* Arithmetic of the filter recurrence (p(A) applied to a block).
+ * FP64: IEEE FP64 storage and arithmetic everywhere (the paper's setting).
+ * FP32: matrix values and recurrence vectors stored and combined in FP32; the
+ *       filtered block is handed to the Lanczos step in FP64 and everything
+ *       after it (reorthogonalization, Rayleigh-Ritz, residuals) is FP64,
+ *       followed by FP64 refinement of the converged eigenpairs.
+ * BF16: as FP32 but matrix values and recurrence vectors stored in bfloat16
+ *       with FP32 accumulation. */
+typedef enum flz_precision { FLZ_PREC_FP64 = 0, FLZ_PREC_FP32 = 1, FLZ_PREC_BF16 = 2 } flz_precision;
+
+typedef struct flz_matrix flz_matrix;
+typedef struct flz_solver flz_solver;
+typedef struct flz_batch flz_batch;
+
+/* Solver parameters; fill with flz_params_default() then override. */
+typedef struct flz_params {
+  int32_t block_size;   /* r, block width of block Lanczos (Section 2.3); default 3 as in Section 4; 1..16 */
+  int32_t degree;       /* filter degree m; 0 = automatic by eq. (optimaldegree); default 0 */
+  double degree_eps;    /* epsilon of eq. (optimaldegree); default 0.3123 */
+  int32_t max_degree;   /* cap on the automatic degree; default 2000 */
+  double tol;           /* converged when ||Ax - lambda x|| / ||A|| <= tol; default 1e-10 */
+  int32_t check_every;  /* block steps between convergence checks (Section 3.2.2: "periodically"); default 30 */
+  int32_t max_basis;    /* Krylov basis capacity in vectors; 0 = automatic; rounded down to a multiple of r */
+  int32_t guard;        /* Ritz pairs outside [alpha,beta] that must also converge; 0 = max(r, 3) */
+  int32_t precision;    /* flz_precision; default FLZ_PREC_FP64 */
+  int32_t bounds_steps; /* Lanczos vectors for the spectrum bounds (Section 2.2); default 60 */
+  uint64_t seed;        /* seed of the random start blocks; default 1 */
+  double lmin, lmax;    /* if lmin < lmax these bounds are used and no estimate is made */
+} flz_params;
+
+/* Per-solve statistics (the columns of Tables 2 and 3, plus bounds). */
+typedef struct flz_stats {
+  int64_t iters;        /* block Lanczos steps taken (Table 2 "iters") */
+  int64_t matvecs;      /* r * m * iters (Table 2 "MV") */
+  int64_t count;        /* eigenpairs found in [alpha, beta] */
+  int32_t degree;       /* m */
+  int32_t block_size;   /* r */
+  int32_t converged;    /* 1 if the convergence test passed */
+  int32_t checks;       /* convergence checks made */
+  double lmin, lmax;    /* spectrum bounds used for eq. (transf) */
+  double c, e;          /* centre and half-width of eq. (transf) */
+  double alpha_mapped, beta_mapped;
+  double max_residual;  /* max ||Ax - lambda x|| / ||A|| over the returned pairs */
+  double ms_bounds;     /* bound estimation ("PREPROC" of Table 3) */
+  double ms_filter;     /* p(A) applications ("MV" of Table 3) */
+  double ms_orth;       /* full reorthogonalization and block QR ("ORTH" of Table 3) */
+  double ms_check;      /* Rayleigh-Ritz, Ritz vectors, residuals */
+  double ms_refine;     /* FP64 refinement (FLZ_PREC_FP32 / FLZ_PREC_BF16) */
+  double ms_total;      /* wall time of flz_solve */
+  int64_t basis_vectors;/* final Krylov basis size */
+  int64_t kernel_launches; /* CUDA kernels this solve launched */
+} flz_stats;
+
+/* ---- status and parameters ------------------------------------------------ */
+
+/* Static English name of a status code; never NULL. */
+const char* flz_status_string(flz_status s);
+/* Message of the calling thread's last failure ("" if none); never NULL. */
+const char* flz_last_error(void);
+/* Writes the defaults listed in flz_params into *p. INVALID_ARG if p is NULL. */
+flz_status flz_params_default(flz_params* p);
+
+/* ---- matrices (Section 3.2.1: symmetric, CSR with both triangles, no symmetry exploited) ---- */
+
+/* Creates a matrix handle by COPYING a CSR matrix.
+ * n >= 1 rows; nnz >= 0 stored entries; rowptr int32[n+1] with rowptr[0] = 0,
+ * non-decreasing, rowptr[n] = nnz; col int32[nnz] in [0, n), strictly
+ * increasing within a row; val[nnz] of type val_type (FLZ_F64 or FLZ_F32).
+ * `where` says whether the three arrays are host or device memory. If
+ * check_symmetry is nonzero every stored a_ij must have a stored a_ji with
+ * |a_ij - a_ji| <= 1e-14 max(|a_ij|, |a_ji|), else FLZ_ERR_NOT_SYMMETRIC.
+ * The structure is always validated (FLZ_ERR_BAD_CSR). n and nnz must fit in
+ * int32. On success *out owns device copies (values kept in FP64, plus FP32
+ * and BF16 copies made on first use by a reduced-precision filter). */
+flz_status flz_matrix_create_csr(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                                 const void* val, flz_dtype val_type, flz_memspace where,
+                                 int32_t check_symmetry, flz_matrix** out);
+/* Frees the handle and its device memory. NULL is a no-op. */
+flz_status flz_matrix_destroy(flz_matrix* A);
+/* n, nnz and the Gershgorin interval [glo, ghi] (any pointer may be NULL). */
+flz_status flz_matrix_info(const flz_matrix* A, int64_t* n, int64_t* nnz, double* glo, double* ghi);
+
+/* ---- the hot path: p_m((A - cI)/e) applied to a block --------------------- */
+
+/* W = p_m(Ahat) V with Ahat = (A - cI)/e (eq. transf) and
+ * p_m = sum_{i=0..m} coeffs[i] T_i (Section 2.2), evaluated by the three-term
+ * Chebyshev recurrence T_{i+1} = 2 z T_i - T_{i-1} (eq. def:cheb1) with the
+ * running sum accumulated in the same pass over A as each new term.
+ * V, W: device FP64, n x r row-major, must not overlap; 1 <= r <= 16;
+ * coeffs: host FP64[degree+1]; degree >= 0; e > 0. precision selects the
+ * recurrence arithmetic (flz_precision); W is always FP64. Scratch of
+ * 2 n r elements (plus n r FP32 for reduced precision) is owned by the
+ * matrix handle and reused across calls, so calls on one matrix must not
+ * overlap in time. Asynchronous on `stream`. */
+flz_status flz_filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int32_t degree,
+                            int32_t r, const double* V, double* W, int32_t precision, void* stream);
+
+/* Closed-form Chebyshev coefficients of the indicator of [alpha, beta] within
+ * [-1, 1] (Section 2.2): out[0] = (acos a - acos b)/pi, out[i] =
+ * 2 (sin(i acos a) - sin(i acos b))/(i pi). Host only; out has degree+1 slots.
+ * Requires -1 <= alpha < beta <= 1. */
+flz_status flz_filter_coefficients(double alpha, double beta, int32_t degree, double* out);
+/* Eq. (optimaldegree): least m >= 1 with ||p_m - phi|| < eps ||phi|| in the
+ * weighted Chebyshev 2-norm. Host only. CAPACITY if no m <= max_degree fits. */
+flz_status flz_filter_degree(double alpha, double beta, double eps, int32_t max_degree, int32_t* degree);
+
+/* Spectrum bounds (Section 2.2, after eq. transf): block Lanczos with full
+ * reorthogonalization on A over `steps` vectors (block width r), extreme Ritz
+ * values padded by their residual bounds and clamped to the Gershgorin
+ * interval. Synchronizes `stream`. */
+flz_status flz_spectrum_bounds(flz_matrix* A, int32_t steps, int32_t r, uint64_t seed,
+                               double* lmin, double* lmax, void* stream);
+
+/* ---- host utilities: the projected problem of eq. (proj) ------------------- */
+
+/* Eigenvalues (ascending) of a symmetric band matrix: T is K x K, row-major,
+ * dense storage, zero outside |i - j| <= b (the block tridiagonal T_k of
+ * eq. lanczos has b = r). Orthogonal band-to-tridiagonal reduction by Givens
+ * rotations, then implicit QL. Host memory only; theta has K slots. */
+flz_status flz_band_eigenvalues(int32_t K, int32_t b, const double* T, double* theta);
+/* Unit eigenvectors of the same T for the `count` eigenvalues theta[idx[t]]
+ * (theta as returned above), by inverse iteration on the band matrix with
+ * partial pivoting; vectors of eigenvalues closer than 1e-3 ||T|| are
+ * orthogonalized against each other. Y is K x count, column-major (host). */
+flz_status flz_band_eigenvectors(int32_t K, int32_t b, const double* T, const double* theta, int32_t count,
+                                 const int32_t* idx, double* Y, uint64_t seed);
+
+/* ---- solver (Sections 2.3 and 3.2.2) ---------------------------------------- */
+
+/* Creates a solver bound to A (which must outlive it). params may be NULL
+ * (defaults). Device memory for the basis is allocated at flz_solve. */
+flz_status flz_solver_create(flz_matrix* A, const flz_params* params, flz_solver** out);
+flz_status flz_solver_destroy(flz_solver* s);
+/* [alpha, beta] in A's own units (not mapped); alpha < beta. */
+flz_status flz_solver_set_interval(flz_solver* s, double alpha, double beta);
+/* Runs the filtered Lanczos procedure: bounds, map, degree, coefficients,
+ * block Lanczos on p(A) with full reorthogonalization, periodic Rayleigh-Ritz
+ * and residual checks, Rayleigh quotients of the converged Ritz vectors.
+ * Synchronous: returns when the result is ready. EMPTY_INTERVAL,
+ * NOT_CONVERGED (partial results readable), OUT_OF_MEMORY, CUDA_ERROR. */
+flz_status flz_solve(flz_solver* s, void* stream);
+/* Number of eigenpairs found in [alpha, beta]. */
+flz_status flz_get_count(const flz_solver* s, int64_t* count);
+/* Ascending eigenvalues into host out[cap]; CAPACITY if cap < count. */
+flz_status flz_get_eigenvalues(const flz_solver* s, double* out, int64_t cap);
+/* Eigenvectors as an n x count column-major array with leading dimension
+ * ld >= n, column j matching eigenvalue j, unit 2-norm; `where` says whether
+ * out is host or device memory; cap_cols < count gives CAPACITY. */
+flz_status flz_get_eigenvectors(const flz_solver* s, double* out, int64_t ld, int64_t cap_cols,
+                                flz_memspace where);
+/* ||A x_j - lambda_j x_j|| / ||A|| per pair into host out[cap]. */
+flz_status flz_get_residuals(const flz_solver* s, double* out, int64_t cap);
+flz_status flz_get_stats(const flz_solver* s, flz_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLZ_H */

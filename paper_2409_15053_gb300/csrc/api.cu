@@ -1,0 +1,346 @@
+// extern "C" entry points of include/flz.h. Each catches the internal
+// flz::Failure so that no exception crosses the ABI.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+
+#include "flz_internal.h"
+
+namespace flz {
+
+namespace {
+thread_local std::string g_last_error;
+}
+thread_local int64_t g_kernel_launches = 0;
+
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+void clear_last_error() { g_last_error.clear(); }
+
+[[noreturn]] void fail(flz_status st, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  set_last_error(buf);
+  throw Failure{st};
+}
+
+// Section 2.2: b_0 = (acos a - acos b)/pi, b_i = 2 (sin(i acos a) - sin(i acos b)) / (i pi).
+void chebyshev_coefficients(double a, double b, int m, double* out) {
+  const double ta = std::acos(a), tb = std::acos(b);
+  out[0] = (ta - tb) / M_PI;
+  for (int i = 1; i <= m; ++i) out[i] = 2.0 * (std::sin(i * ta) - std::sin(i * tb)) / (i * M_PI);
+}
+
+// Eq. (optimaldegree): least m with ||p_m - phi||^2 < eps^2 ||phi||^2 in the
+// weighted Chebyshev norm, the error by Parseval: ||phi||^2 = acos a - acos b,
+// ||p_m||^2 = pi b_0^2 + (pi/2) sum_{i=1..m} b_i^2. Returns -1 if none <= max_degree.
+int auto_degree(double a, double b, double eps, int max_degree) {
+  const double ta = std::acos(a), tb = std::acos(b);
+  const double phi2 = ta - tb;
+  const double b0 = phi2 / M_PI;
+  double kept = M_PI * b0 * b0;
+  for (int m = 1; m <= max_degree; ++m) {
+    const double bm = 2.0 * (std::sin(m * ta) - std::sin(m * tb)) / (m * M_PI);
+    kept += 0.5 * M_PI * bm * bm;
+    if (phi2 - kept < eps * eps * phi2) return m;
+  }
+  return -1;
+}
+
+flz_status solve(flz_solver* s, cudaStream_t st);
+void bounds_entry(flz_matrix* A, int steps, int r, uint64_t seed, cudaStream_t st, double* lmin, double* lmax);
+
+}  // namespace flz
+
+#define FLZ_API_BEGIN         \
+  ::flz::clear_last_error();  \
+  try {
+#define FLZ_API_END                                     \
+  }                                                     \
+  catch (const ::flz::Failure& f) {                     \
+    return f.status;                                    \
+  }                                                     \
+  catch (const std::bad_alloc&) {                       \
+    ::flz::set_last_error("host allocation failed");    \
+    return FLZ_ERR_OUT_OF_MEMORY;                       \
+  }                                                     \
+  catch (...) {                                         \
+    ::flz::set_last_error("unexpected internal error"); \
+    return FLZ_ERR_CUDA;                                \
+  }                                                     \
+  return FLZ_OK;
+
+using flz::fail;
+
+extern "C" {
+
+const char* flz_status_string(flz_status s) {
+  switch (s) {
+    case FLZ_OK: return "FLZ_OK";
+    case FLZ_ERR_INVALID_ARG: return "FLZ_ERR_INVALID_ARG";
+    case FLZ_ERR_NOT_SYMMETRIC: return "FLZ_ERR_NOT_SYMMETRIC";
+    case FLZ_ERR_BAD_CSR: return "FLZ_ERR_BAD_CSR";
+    case FLZ_ERR_EMPTY_INTERVAL: return "FLZ_ERR_EMPTY_INTERVAL";
+    case FLZ_ERR_NOT_CONVERGED: return "FLZ_ERR_NOT_CONVERGED";
+    case FLZ_ERR_OUT_OF_MEMORY: return "FLZ_ERR_OUT_OF_MEMORY";
+    case FLZ_ERR_CUDA: return "FLZ_ERR_CUDA";
+    case FLZ_ERR_TIMEOUT: return "FLZ_ERR_TIMEOUT";
+    case FLZ_ERR_CAPACITY: return "FLZ_ERR_CAPACITY";
+    case FLZ_ERR_NO_INTERVAL: return "FLZ_ERR_NO_INTERVAL";
+    case FLZ_ERR_NOT_SOLVED: return "FLZ_ERR_NOT_SOLVED";
+  }
+  return "FLZ_ERR_UNKNOWN";
+}
+
+const char* flz_last_error(void) { return flz::g_last_error.c_str(); }
+
+flz_status flz_params_default(flz_params* p) {
+  if (!p) return FLZ_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->block_size = 3;
+  p->degree = 0;
+  p->degree_eps = 0.3123;
+  p->max_degree = 2000;
+  p->tol = 1e-10;
+  p->check_every = 30;
+  p->max_basis = 0;
+  p->guard = 0;
+  p->precision = FLZ_PREC_FP64;
+  p->bounds_steps = 60;
+  p->seed = 1;
+  p->lmin = 0.0;
+  p->lmax = 0.0;
+  return FLZ_OK;
+}
+
+flz_status flz_filter_coefficients(double alpha, double beta, int32_t degree, double* out) {
+  FLZ_API_BEGIN
+  if (!out || degree < 0) fail(FLZ_ERR_INVALID_ARG, "out is NULL or degree < 0");
+  if (!(alpha >= -1.0 && beta <= 1.0 && alpha < beta)) fail(FLZ_ERR_INVALID_ARG, "need -1 <= alpha < beta <= 1");
+  flz::chebyshev_coefficients(alpha, beta, degree, out);
+  FLZ_API_END
+}
+
+flz_status flz_filter_degree(double alpha, double beta, double eps, int32_t max_degree, int32_t* degree) {
+  FLZ_API_BEGIN
+  if (!degree || max_degree < 1 || !(eps > 0.0)) fail(FLZ_ERR_INVALID_ARG, "bad degree arguments");
+  if (!(alpha >= -1.0 && beta <= 1.0 && alpha < beta)) fail(FLZ_ERR_INVALID_ARG, "need -1 <= alpha < beta <= 1");
+  const int m = flz::auto_degree(alpha, beta, eps, max_degree);
+  if (m < 0) fail(FLZ_ERR_CAPACITY, "no degree <= %d satisfies the rule", max_degree);
+  *degree = m;
+  FLZ_API_END
+}
+
+flz_status flz_matrix_create_csr(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                                 const void* val, flz_dtype val_type, flz_memspace where, int32_t check_symmetry,
+                                 flz_matrix** out) {
+  FLZ_API_BEGIN
+  if (!out) fail(FLZ_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || nnz < 0 || n > 2147483647LL || nnz > 2147483647LL) fail(FLZ_ERR_INVALID_ARG, "n/nnz out of range");
+  if (!rowptr || (nnz > 0 && (!col || !val))) fail(FLZ_ERR_INVALID_ARG, "null CSR array");
+  if (val_type != FLZ_F64 && val_type != FLZ_F32) fail(FLZ_ERR_INVALID_ARG, "values must be FLZ_F64 or FLZ_F32");
+  if (where != FLZ_HOST && where != FLZ_DEVICE) fail(FLZ_ERR_INVALID_ARG, "bad memspace");
+  flz_matrix* A = new flz_matrix();
+  try {
+    A->n = n;
+    A->nnz = nnz;
+    FLZ_CUDA(cudaGetDevice(&A->device));
+    A->rowptr.reserve((size_t)n + 1);
+    A->col.reserve((size_t)std::max<int64_t>(nnz, 1));
+    A->val.reserve((size_t)std::max<int64_t>(nnz, 1));
+    const cudaMemcpyKind kind = where == FLZ_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    FLZ_CUDA(cudaMemcpy(A->rowptr.p, rowptr, sizeof(int32_t) * (n + 1), kind));
+    if (nnz > 0) {
+      FLZ_CUDA(cudaMemcpy(A->col.p, col, sizeof(int32_t) * nnz, kind));
+      if (val_type == FLZ_F64) {
+        FLZ_CUDA(cudaMemcpy(A->val.p, val, sizeof(double) * nnz, kind));
+      } else {
+        std::vector<float> hf;
+        const float* src = static_cast<const float*>(val);
+        if (where == FLZ_DEVICE) {
+          hf.resize(nnz);
+          FLZ_CUDA(cudaMemcpy(hf.data(), val, sizeof(float) * nnz, cudaMemcpyDeviceToHost));
+          src = hf.data();
+        }
+        std::vector<double> hd(src, src + nnz);
+        FLZ_CUDA(cudaMemcpy(A->val.p, hd.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
+      }
+    }
+    const flz_status vs = flz::validate_csr(A, check_symmetry);
+    if (vs == FLZ_ERR_BAD_CSR) fail(vs, "CSR structure invalid (rowptr, column range or column order)");
+    if (vs == FLZ_ERR_NOT_SYMMETRIC) fail(vs, "matrix is not symmetric");
+    flz::gershgorin(A, &A->glo, &A->ghi, &A->max_row_nnz);
+  } catch (...) {
+    delete A;
+    throw;
+  }
+  *out = A;
+  FLZ_API_END
+}
+
+flz_status flz_matrix_destroy(flz_matrix* A) {
+  FLZ_API_BEGIN
+  delete A;
+  FLZ_API_END
+}
+
+flz_status flz_matrix_info(const flz_matrix* A, int64_t* n, int64_t* nnz, double* glo, double* ghi) {
+  FLZ_API_BEGIN
+  if (!A) fail(FLZ_ERR_INVALID_ARG, "matrix is NULL");
+  if (n) *n = A->n;
+  if (nnz) *nnz = A->nnz;
+  if (glo) *glo = A->glo;
+  if (ghi) *ghi = A->ghi;
+  FLZ_API_END
+}
+
+flz_status flz_filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int32_t degree, int32_t r,
+                            const double* V, double* W, int32_t precision, void* stream) {
+  FLZ_API_BEGIN
+  if (!A || !coeffs || !V || !W) fail(FLZ_ERR_INVALID_ARG, "null argument");
+  if (degree < 0 || r < 1 || r > 16 || !(e > 0.0)) fail(FLZ_ERR_INVALID_ARG, "need degree >= 0, 1 <= r <= 16, e > 0");
+  if (precision < FLZ_PREC_FP64 || precision > FLZ_PREC_BF16) fail(FLZ_ERR_INVALID_ARG, "bad precision");
+  const size_t bytes = sizeof(double) * (size_t)A->n * r;
+  const char* v = reinterpret_cast<const char*>(V);
+  const char* w = reinterpret_cast<const char*>(W);
+  if (v < w + bytes && w < v + bytes) fail(FLZ_ERR_INVALID_ARG, "V and W overlap");
+  flz::filter_apply(A, c, e, coeffs, degree, r, V, W, precision, static_cast<cudaStream_t>(stream));
+  FLZ_API_END
+}
+
+flz_status flz_spectrum_bounds(flz_matrix* A, int32_t steps, int32_t r, uint64_t seed, double* lmin, double* lmax,
+                               void* stream) {
+  FLZ_API_BEGIN
+  if (!A || !lmin || !lmax) fail(FLZ_ERR_INVALID_ARG, "null argument");
+  if (steps < 1 || r < 1 || r > 16 || r > A->n) fail(FLZ_ERR_INVALID_ARG, "bad steps or block width");
+  flz::bounds_entry(A, steps, r, seed, static_cast<cudaStream_t>(stream), lmin, lmax);
+  FLZ_API_END
+}
+
+flz_status flz_band_eigenvalues(int32_t K, int32_t b, const double* T, double* theta) {
+  FLZ_API_BEGIN
+  if (K < 1 || b < 0 || !T || !theta) fail(FLZ_ERR_INVALID_ARG, "bad band matrix arguments");
+  std::vector<double> t(T, T + (size_t)K * K), th;
+  flz::band_eigenvalues(t, K, std::min<int32_t>(std::max<int32_t>(b, 1), K), th);
+  for (int i = 0; i < K; ++i) theta[i] = th[i];
+  FLZ_API_END
+}
+
+flz_status flz_band_eigenvectors(int32_t K, int32_t b, const double* T, const double* theta, int32_t count,
+                                 const int32_t* idx, double* Y, uint64_t seed) {
+  FLZ_API_BEGIN
+  if (K < 1 || b < 0 || !T || !theta || count < 0 || (count > 0 && (!idx || !Y)))
+    fail(FLZ_ERR_INVALID_ARG, "bad band matrix arguments");
+  std::vector<double> t(T, T + (size_t)K * K), th(theta, theta + K), y;
+  std::vector<int> ix(idx, idx + count);
+  for (int v : ix)
+    if (v < 0 || v >= K) fail(FLZ_ERR_INVALID_ARG, "eigenvalue index out of range");
+  flz::band_eigenvectors(t, K, std::min<int32_t>(std::max<int32_t>(b, 1), K), th, ix, y, seed);
+  for (size_t i = 0; i < y.size(); ++i) Y[i] = y[i];
+  FLZ_API_END
+}
+
+flz_status flz_solver_create(flz_matrix* A, const flz_params* params, flz_solver** out) {
+  FLZ_API_BEGIN
+  if (!A || !out) fail(FLZ_ERR_INVALID_ARG, "null argument");
+  flz_params p;
+  if (params) p = *params;
+  else flz_params_default(&p);
+  if (p.block_size < 1 || p.block_size > 16 || p.block_size > A->n) fail(FLZ_ERR_INVALID_ARG, "block_size must be in [1, min(16, n)]");
+  if (p.degree < 0 || p.max_degree < 1 || p.check_every < 1 || !(p.tol > 0.0) || !(p.degree_eps > 0.0) ||
+      p.bounds_steps < 1 || p.max_basis < 0 || p.guard < 0)
+    fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
+  if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_BF16) fail(FLZ_ERR_INVALID_ARG, "bad precision");
+  flz_solver* s = new flz_solver();
+  s->A = A;
+  s->p = p;
+  *out = s;
+  FLZ_API_END
+}
+
+flz_status flz_solver_destroy(flz_solver* s) {
+  FLZ_API_BEGIN
+  delete s;
+  FLZ_API_END
+}
+
+flz_status flz_solver_set_interval(flz_solver* s, double alpha, double beta) {
+  FLZ_API_BEGIN
+  if (!s || !(alpha < beta) || !std::isfinite(alpha) || !std::isfinite(beta)) fail(FLZ_ERR_INVALID_ARG, "need finite alpha < beta");
+  s->alpha = alpha;
+  s->beta = beta;
+  s->has_interval = true;
+  FLZ_API_END
+}
+
+flz_status flz_solve(flz_solver* s, void* stream) {
+  ::flz::clear_last_error();
+  try {
+    if (!s) fail(FLZ_ERR_INVALID_ARG, "solver is NULL");
+    if (!s->has_interval) fail(FLZ_ERR_NO_INTERVAL, "set the interval first");
+    const flz_status st = flz::solve(s, static_cast<cudaStream_t>(stream));
+    if (st == FLZ_ERR_NOT_CONVERGED) flz::set_last_error("basis capacity reached before convergence; partial results");
+    return st;
+  } catch (const ::flz::Failure& f) {
+    return f.status;
+  } catch (const std::bad_alloc&) {
+    ::flz::set_last_error("host allocation failed");
+    return FLZ_ERR_OUT_OF_MEMORY;
+  } catch (...) {
+    ::flz::set_last_error("unexpected internal error");
+    return FLZ_ERR_CUDA;
+  }
+}
+
+flz_status flz_get_count(const flz_solver* s, int64_t* count) {
+  FLZ_API_BEGIN
+  if (!s || !count) fail(FLZ_ERR_INVALID_ARG, "null argument");
+  if (!s->solved) fail(FLZ_ERR_NOT_SOLVED, "no solve yet");
+  *count = s->count;
+  FLZ_API_END
+}
+
+flz_status flz_get_eigenvalues(const flz_solver* s, double* out, int64_t cap) {
+  FLZ_API_BEGIN
+  if (!s || (!out && s->count > 0)) fail(FLZ_ERR_INVALID_ARG, "null argument");
+  if (!s->solved) fail(FLZ_ERR_NOT_SOLVED, "no solve yet");
+  if (cap < s->count) fail(FLZ_ERR_CAPACITY, "need %lld slots", (long long)s->count);
+  for (int64_t i = 0; i < s->count; ++i) out[i] = s->evals[i];
+  FLZ_API_END
+}
+
+flz_status flz_get_residuals(const flz_solver* s, double* out, int64_t cap) {
+  FLZ_API_BEGIN
+  if (!s || (!out && s->count > 0)) fail(FLZ_ERR_INVALID_ARG, "null argument");
+  if (!s->solved) fail(FLZ_ERR_NOT_SOLVED, "no solve yet");
+  if (cap < s->count) fail(FLZ_ERR_CAPACITY, "need %lld slots", (long long)s->count);
+  for (int64_t i = 0; i < s->count; ++i) out[i] = s->resid[i];
+  FLZ_API_END
+}
+
+flz_status flz_get_eigenvectors(const flz_solver* s, double* out, int64_t ld, int64_t cap_cols, flz_memspace where) {
+  FLZ_API_BEGIN
+  if (!s || (!out && s->count > 0)) fail(FLZ_ERR_INVALID_ARG, "null argument");
+  if (!s->solved) fail(FLZ_ERR_NOT_SOLVED, "no solve yet");
+  const int64_t n = s->A->n;
+  if (ld < n) fail(FLZ_ERR_INVALID_ARG, "ld < n");
+  if (cap_cols < s->count) fail(FLZ_ERR_CAPACITY, "need %lld columns", (long long)s->count);
+  if (where != FLZ_HOST && where != FLZ_DEVICE) fail(FLZ_ERR_INVALID_ARG, "bad memspace");
+  if (s->count == 0) return FLZ_OK;
+  const cudaMemcpyKind kind = where == FLZ_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  FLZ_CUDA(cudaMemcpy2D(out, sizeof(double) * ld, s->evecs.p, sizeof(double) * n, sizeof(double) * n,
+                        (size_t)s->count, kind));
+  FLZ_API_END
+}
+
+flz_status flz_get_stats(const flz_solver* s, flz_stats* out) {
+  FLZ_API_BEGIN
+  if (!s || !out) fail(FLZ_ERR_INVALID_ARG, "null argument");
+  *out = s->stats;
+  FLZ_API_END
+}
+
+}  // extern "C"

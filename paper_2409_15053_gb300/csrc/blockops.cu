@@ -1,0 +1,430 @@
+// Tall-skinny block kernels around the filter (Sections 2.3, 3.2.2):
+//   basis_dot    C = Q^T W  over all basis blocks (full reorthogonalization,
+//                Gram matrices of the block QR, D_j = Q_j^T p(A) Q_j)
+//   basis_update Out = beta Out + alpha Q C (the projection update of
+//                Gram-Schmidt, W R^{-1} of the block QR, Ritz vectors Q_k W_k)
+//   column_sums  per-column dot products and residual norms (eq. rayleigh)
+// plus the counter-based normal generator of the start blocks and CSR
+// validation / Gershgorin bounds of the matrix handle.
+//
+// The basis is a sequence of n x r row-major blocks stored back to back, so
+// a block is one contiguous slab and every kernel reads it with unit stride.
+#include <algorithm>
+
+#include "flz_internal.h"
+
+namespace flz {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kSub = 128;  // rows of W staged in shared memory per sub-chunk
+
+// Partial C = Q^T W over one row range (blockIdx.x) for a group of basis
+// blocks (blockIdx.y). Warp w handles BPW blocks; lane l owns column
+// a = l % R of rows l / R, l / R + 32/R, ... of the staged sub-chunk.
+template <int R>
+__global__ void __launch_bounds__(kThreads) basis_dot_kernel(const double* __restrict__ Q, int nb, long long n,
+                                                             const double* __restrict__ W, int ldw,
+                                                             long long rows_per_cta, double* __restrict__ part) {
+  constexpr int BPW = (8 / R) > 0 ? (8 / R) : 1;
+  constexpr int RPI = 32 / R;  // rows per warp iteration
+  __shared__ double wsm[kSub * R];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a = lane % R, k = lane / R;
+  const bool active = k < RPI;
+  const long long r0 = (long long)blockIdx.x * rows_per_cta;
+  const long long r1 = min(n, r0 + rows_per_cta);
+  const int bbase = blockIdx.y * (8 * BPW) + warp * BPW;
+  double acc[BPW][R];
+#pragma unroll
+  for (int bi = 0; bi < BPW; ++bi)
+#pragma unroll
+    for (int t = 0; t < R; ++t) acc[bi][t] = 0.0;
+  for (long long s0 = r0; s0 < r1; s0 += kSub) {
+    const int rows = (int)min((long long)kSub, r1 - s0);
+    for (int e = threadIdx.x; e < rows * R; e += kThreads) {
+      const int i = e / R, t = e - i * R;
+      wsm[e] = W[(size_t)(s0 + i) * ldw + t];
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int bi = 0; bi < BPW; ++bi) {
+        const int b = bbase + bi;
+        if (b < nb) {
+          const double* qb = Q + (size_t)b * n * R + (size_t)s0 * R;
+          for (int i = k; i < rows; i += RPI) {
+            const double q = __ldg(qb + (size_t)i * R + a);
+#pragma unroll
+            for (int t = 0; t < R; ++t) acc[bi][t] = fma(q, wsm[i * R + t], acc[bi][t]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // reduce over the lanes sharing column a: lanes a, a+R, ..., a+(RPI-1)R
+#pragma unroll
+  for (int bi = 0; bi < BPW; ++bi) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      double v = acc[bi][t];
+      for (int s = 1; s < RPI; s <<= 1) {
+        const double o = __shfl_down_sync(0xffffffffu, v, s * R);
+        if ((k & (2 * s - 1)) == 0 && k + s < RPI) v += o;
+      }
+      acc[bi][t] = v;
+    }
+  }
+  if (k == 0) {
+#pragma unroll
+    for (int bi = 0; bi < BPW; ++bi) {
+      const int b = bbase + bi;
+      if (b < nb) {
+        double* p = part + ((size_t)blockIdx.x * nb + b) * R * R + a * R;
+#pragma unroll
+        for (int t = 0; t < R; ++t) p[t] = acc[bi][t];
+      }
+    }
+  }
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ part, int parts, size_t len,
+                                    double* __restrict__ out) {
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < len; o += (size_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int p = 0; p < parts; ++p) s += part[(size_t)p * len + o];
+    out[o] = s;
+  }
+}
+
+// Out[i, t] = beta Out[i, t] + alpha sum_{b,a} Q_b[i, a] C[(b r + a) S + t], one thread per row.
+template <int S>
+__global__ void __launch_bounds__(kThreads) basis_update_kernel(const double* Q, int nb, long long n, int r,
+                                                                const double* __restrict__ C, double alpha,
+                                                                double beta, double* Out, int ldo) {
+  extern __shared__ double csm[];
+  const int cb = max(1, 256 / r);  // basis blocks per staged chunk of C
+  const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  double acc[S];
+#pragma unroll
+  for (int t = 0; t < S; ++t) acc[t] = 0.0;
+  for (int b0 = 0; b0 < nb; b0 += cb) {
+    const int nbc = min(cb, nb - b0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nbc * r * S; e += kThreads) csm[e] = C[(size_t)b0 * r * S + e];
+    __syncthreads();
+    if (i < n) {
+      for (int bl = 0; bl < nbc; ++bl) {
+        const double* qrow = Q + (size_t)(b0 + bl) * n * r + (size_t)i * r;
+        for (int a = 0; a < r; ++a) {
+          const double q = qrow[a];
+          const double* cr = csm + (bl * r + a) * S;
+#pragma unroll
+          for (int t = 0; t < S; ++t) acc[t] = fma(q, cr[t], acc[t]);
+        }
+      }
+    }
+  }
+  if (i < n) {
+    double* o = Out + (size_t)i * ldo;
+    if (beta == 0.0) {
+#pragma unroll
+      for (int t = 0; t < S; ++t) o[t] = alpha * acc[t];
+    } else {
+#pragma unroll
+      for (int t = 0; t < S; ++t) o[t] = fma(alpha, acc[t], beta * o[t]);
+    }
+  }
+}
+
+// Per-column sums over rows, s lanes per row; part[blockIdx.x][t].
+__global__ void __launch_bounds__(kThreads) column_sums_kernel(const double* __restrict__ X,
+                                                               const double* __restrict__ Y,
+                                                               const double* __restrict__ lam, long long n, int s,
+                                                               int ld, int mode, double* __restrict__ part) {
+  __shared__ double red[kThreads];
+  const int lane = threadIdx.x & 31;
+  const int rpw = 32 / s;
+  const int sub = lane / s, t = lane - sub * s;
+  const long long warps_total = (long long)gridDim.x * (kThreads / 32);
+  const long long warp = (long long)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  double acc = 0.0;
+  if (sub < rpw) {
+    const double l = mode == 1 ? lam[t] : 0.0;
+    for (long long row = warp * rpw + sub; row < n; row += warps_total * rpw) {
+      const double x = X[(size_t)row * ld + t];
+      const double y = Y[(size_t)row * ld + t];
+      if (mode == 0) {
+        acc = fma(x, y, acc);
+      } else {
+        const double d = y - l * x;
+        acc = fma(d, d, acc);
+      }
+    }
+  }
+  red[threadIdx.x] = (sub < rpw) ? acc : 0.0;
+  __syncthreads();
+  if (threadIdx.x < s) {
+    double v = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w)
+      for (int q = 0; q < rpw; ++q) v += red[w * 32 + q * s + threadIdx.x];
+    part[(size_t)blockIdx.x * s + threadIdx.x] = v;
+  }
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// N(0,1) by Box-Muller on two counter-based uniforms (splitmix64 of seed and index).
+__global__ void random_normal_kernel(double* __restrict__ X, long long count, uint64_t seed, uint64_t offset) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+       k += (long long)gridDim.x * blockDim.x) {
+    const uint64_t base = mix64(seed) ^ (2ull * (offset + (uint64_t)k));
+    const double u1 = ((double)(mix64(base) >> 11) + 1.0) * (1.0 / 9007199254740992.0);  // (0, 1]
+    const double u2 = (double)(mix64(base + 1) >> 11) * (1.0 / 9007199254740992.0);
+    X[k] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  }
+}
+
+__global__ void rows_to_columns_kernel(const double* __restrict__ X, long long n, int s, int ld,
+                                       double* __restrict__ out, long long ldo) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n * s;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / s;
+    const int t = (int)(e - i * s);
+    out[(size_t)t * ldo + i] = X[(size_t)i * ld + t];
+  }
+}
+
+__global__ void gershgorin_kernel(long long n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                  const double* __restrict__ val, double* __restrict__ lo, double* __restrict__ hi,
+                                  int* __restrict__ maxlen) {
+  __shared__ double slo[kThreads], shi[kThreads];
+  __shared__ int slen[kThreads];
+  double l = 1e308, h = -1e308;
+  int len = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double d = 0.0, rad = 0.0;
+    const int j0 = rowptr[i], j1 = rowptr[i + 1];
+    for (int j = j0; j < j1; ++j) {
+      if (col[j] == i) d += val[j];
+      else rad += fabs(val[j]);
+    }
+    l = fmin(l, d - rad);
+    h = fmax(h, d + rad);
+    len = max(len, j1 - j0);
+  }
+  slo[threadIdx.x] = l;
+  shi[threadIdx.x] = h;
+  slen[threadIdx.x] = len;
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      slo[threadIdx.x] = fmin(slo[threadIdx.x], slo[threadIdx.x + s]);
+      shi[threadIdx.x] = fmax(shi[threadIdx.x], shi[threadIdx.x + s]);
+      slen[threadIdx.x] = max(slen[threadIdx.x], slen[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    lo[blockIdx.x] = slo[0];
+    hi[blockIdx.x] = shi[0];
+    maxlen[blockIdx.x] = slen[0];
+  }
+}
+
+// flags bit 0: structure error, bit 1: asymmetric value or missing transpose entry.
+__global__ void validate_kernel(long long n, long long nnz, const int* __restrict__ rowptr,
+                                const int* __restrict__ col, const double* __restrict__ val, int check_sym,
+                                int* __restrict__ flags) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int j0 = rowptr[i], j1 = rowptr[i + 1];
+    if ((i == 0 && j0 != 0) || j1 < j0 || (i == n - 1 && j1 != nnz) || j0 < 0 || j1 > nnz) {
+      atomicOr(flags, 1);
+      continue;
+    }
+    for (int j = j0; j < j1; ++j) {
+      const int cj = col[j];
+      if (cj < 0 || cj >= n || (j > j0 && col[j - 1] >= cj)) {
+        atomicOr(flags, 1);
+        break;
+      }
+      if (!check_sym) continue;
+      // binary search for column i in row cj (row cj's structure may itself be
+      // invalid; the search stays inside [rowptr[cj], rowptr[cj+1]) clipped to nnz)
+      int lo = max(0, rowptr[cj]), hi = min((int)nnz, rowptr[cj + 1]) - 1;
+      bool found = false;
+      while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int cm = col[mid];
+        if (cm == i) {
+          const double x = val[j], y = val[mid];
+          if (fabs(x - y) > 1e-14 * fmax(fabs(x), fabs(y))) atomicOr(flags, 2);
+          found = true;
+          break;
+        }
+        if (cm < i) lo = mid + 1;
+        else hi = mid - 1;
+      }
+      if (!found) atomicOr(flags, 2);
+    }
+  }
+}
+
+inline unsigned gs_blocks(long long count) {
+  return (unsigned)std::max<long long>(1, std::min<long long>((count + 255) / 256, 152 * 16));
+}
+
+struct DotShape {
+  int gx, gy;
+  long long rows_per_cta;
+};
+
+DotShape dot_shape(int64_t n, int nb, int r) {
+  const int bpw = std::max(1, 8 / r);
+  const int bpc = 8 * bpw;
+  DotShape d;
+  d.gy = (nb + bpc - 1) / bpc;
+  const long long max_gx = std::max<long long>(1, (n + kSub - 1) / kSub);
+  d.gx = (int)std::min<long long>(max_gx, std::max(1, 4 * 152 / d.gy));
+  d.rows_per_cta = ((n + d.gx - 1) / d.gx + kSub - 1) / kSub * kSub;
+  d.gx = (int)((n + d.rows_per_cta - 1) / d.rows_per_cta);
+  return d;
+}
+
+template <int R>
+void launch_basis_dot(const double* Q, int nb, int64_t n, const double* W, int ldw, double* C, double* part,
+                      cudaStream_t st) {
+  const DotShape d = dot_shape(n, nb, R);
+  basis_dot_kernel<R><<<dim3(d.gx, d.gy), kThreads, 0, st>>>(Q, nb, n, W, ldw, d.rows_per_cta, part);
+  FLZ_LAUNCH_CHECK();
+  const size_t len = (size_t)nb * R * R;
+  sum_partials_kernel<<<gs_blocks((long long)len), 256, 0, st>>>(part, d.gx, len, C);
+  FLZ_LAUNCH_CHECK();
+}
+
+template <int S>
+void launch_basis_update(const double* Q, int nb, int64_t n, int r, const double* C, double alpha, double beta,
+                         double* Out, int ldo, cudaStream_t st) {
+  const int cb = std::max(1, 256 / r);
+  const size_t smem = sizeof(double) * (size_t)std::min(cb, nb) * r * S;
+  if (smem > 48 * 1024)
+    FLZ_CUDA(cudaFuncSetAttribute(basis_update_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const unsigned grid = (unsigned)((n + kThreads - 1) / kThreads);
+  basis_update_kernel<S><<<grid, kThreads, smem, st>>>(Q, nb, n, r, C, alpha, beta, Out, ldo);
+  FLZ_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+size_t basis_dot_scratch(int64_t n, int nb, int r, int s) {
+  (void)s;
+  // the largest partial-sum buffer any call with 1..nb blocks needs
+  size_t best = 0;
+  for (int b = 1; b <= nb; ++b) {
+    const DotShape d = dot_shape(n, b, r);
+    best = std::max(best, (size_t)d.gx * b * r * r);
+  }
+  return best;
+}
+
+#define FLZ_DISPATCH_16(X, FN, ...)  \
+  switch (X) {                       \
+    case 1: FN<1>(__VA_ARGS__); break;   \
+    case 2: FN<2>(__VA_ARGS__); break;   \
+    case 3: FN<3>(__VA_ARGS__); break;   \
+    case 4: FN<4>(__VA_ARGS__); break;   \
+    case 5: FN<5>(__VA_ARGS__); break;   \
+    case 6: FN<6>(__VA_ARGS__); break;   \
+    case 7: FN<7>(__VA_ARGS__); break;   \
+    case 8: FN<8>(__VA_ARGS__); break;   \
+    case 9: FN<9>(__VA_ARGS__); break;   \
+    case 10: FN<10>(__VA_ARGS__); break; \
+    case 11: FN<11>(__VA_ARGS__); break; \
+    case 12: FN<12>(__VA_ARGS__); break; \
+    case 13: FN<13>(__VA_ARGS__); break; \
+    case 14: FN<14>(__VA_ARGS__); break; \
+    case 15: FN<15>(__VA_ARGS__); break; \
+    case 16: FN<16>(__VA_ARGS__); break; \
+    default: fail(FLZ_ERR_INVALID_ARG, "block width %d out of range 1..16", (int)(X)); \
+  }
+
+void basis_dot(const double* Q, int nb, int64_t n, int r, const double* W, int s, int ldw, double* C,
+               double* part, cudaStream_t st) {
+  if (s != r) fail(FLZ_ERR_INVALID_ARG, "basis_dot needs s == r");
+  if (nb <= 0) return;
+  FLZ_DISPATCH_16(r, launch_basis_dot, Q, nb, n, W, ldw, C, part, st);
+}
+
+void basis_update(const double* Q, int nb, int64_t n, int r, const double* C, int s, double alpha, double beta,
+                  double* Out, int ldo, cudaStream_t st) {
+  if (nb <= 0) return;
+  FLZ_DISPATCH_16(s, launch_basis_update, Q, nb, n, r, C, alpha, beta, Out, ldo, st);
+}
+
+size_t column_sums_scratch(int64_t n, int s) {
+  (void)n;
+  return (size_t)152 * 4 * s;
+}
+
+void column_sums(const double* X, const double* Y, const double* lam, int64_t n, int s, int ld, int mode,
+                 double* out, double* part, cudaStream_t st) {
+  const int rpw = 32 / s;
+  const long long warps = (n + rpw - 1) / rpw;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(152 * 4, (warps + 7) / 8));
+  column_sums_kernel<<<grid, kThreads, 0, st>>>(X, Y, lam, n, s, ld, mode, part);
+  FLZ_LAUNCH_CHECK();
+  sum_partials_kernel<<<1, 32, 0, st>>>(part, grid, (size_t)s, out);
+  FLZ_LAUNCH_CHECK();
+}
+
+void random_normal(double* X, int64_t count, uint64_t seed, uint64_t offset, cudaStream_t st) {
+  random_normal_kernel<<<gs_blocks(count), 256, 0, st>>>(X, count, seed, offset);
+  FLZ_LAUNCH_CHECK();
+}
+
+void rows_to_columns(const double* X, int64_t n, int s, int ld, double* out, int64_t ldo, cudaStream_t st) {
+  rows_to_columns_kernel<<<gs_blocks(n * s), 256, 0, st>>>(X, n, s, ld, out, ldo);
+  FLZ_LAUNCH_CHECK();
+}
+
+void gershgorin(const flz_matrix* A, double* glo, double* ghi, int32_t* max_row_nnz) {
+  const unsigned grid = gs_blocks(A->n);
+  DevBuf<double> lo, hi;
+  DevBuf<int> len;
+  lo.reserve(grid);
+  hi.reserve(grid);
+  len.reserve(grid);
+  gershgorin_kernel<<<grid, kThreads>>>(A->n, A->rowptr.p, A->col.p, A->val.p, lo.p, hi.p, len.p);
+  FLZ_LAUNCH_CHECK();
+  std::vector<double> hlo(grid), hhi(grid);
+  std::vector<int> hlen(grid);
+  FLZ_CUDA(cudaMemcpy(hlo.data(), lo.p, grid * sizeof(double), cudaMemcpyDeviceToHost));
+  FLZ_CUDA(cudaMemcpy(hhi.data(), hi.p, grid * sizeof(double), cudaMemcpyDeviceToHost));
+  FLZ_CUDA(cudaMemcpy(hlen.data(), len.p, grid * sizeof(int), cudaMemcpyDeviceToHost));
+  *glo = *std::min_element(hlo.begin(), hlo.end());
+  *ghi = *std::max_element(hhi.begin(), hhi.end());
+  *max_row_nnz = *std::max_element(hlen.begin(), hlen.end());
+}
+
+flz_status validate_csr(const flz_matrix* A, int check_symmetry) {
+  DevBuf<int> flags;
+  flags.reserve(1);
+  FLZ_CUDA(cudaMemset(flags.p, 0, sizeof(int)));
+  validate_kernel<<<gs_blocks(A->n), 256>>>(A->n, A->nnz, A->rowptr.p, A->col.p, A->val.p, check_symmetry,
+                                            flags.p);
+  FLZ_LAUNCH_CHECK();
+  int h = 0;
+  FLZ_CUDA(cudaMemcpy(&h, flags.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h & 1) return FLZ_ERR_BAD_CSR;
+  if (h & 2) return FLZ_ERR_NOT_SYMMETRIC;
+  return FLZ_OK;
+}
+
+}  // namespace flz

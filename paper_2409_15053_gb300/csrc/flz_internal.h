@@ -1,0 +1,157 @@
+// Internal declarations shared by the translation units of libflz.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
+#include "flz.h"
+
+namespace flz {
+
+// Internal failures are C++ exceptions carrying a status; every extern "C"
+// entry point catches them, so nothing crosses the ABI.
+struct Failure {
+  flz_status status;
+};
+
+[[noreturn]] void fail(flz_status st, const char* fmt, ...);
+void set_last_error(const char* msg);
+void clear_last_error();
+
+#define FLZ_CUDA(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      ::flz::fail(e_ == cudaErrorMemoryAllocation ? FLZ_ERR_OUT_OF_MEMORY : FLZ_ERR_CUDA,    \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+// Every kernel launch site is followed by FLZ_LAUNCH_CHECK(), which also
+// counts the launch (reported per solve in flz_stats.kernel_launches).
+extern thread_local int64_t g_kernel_launches;
+#define FLZ_LAUNCH_CHECK()         \
+  do {                             \
+    ++::flz::g_kernel_launches;    \
+    FLZ_CUDA(cudaGetLastError());  \
+  } while (0)
+
+// Owning device buffer.
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t count = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    count = 0;
+  }
+  // Ensures capacity for n elements; contents are not preserved on growth.
+  void reserve(size_t n) {
+    if (n <= count && p) return;
+    release();
+    if (n == 0) return;
+    FLZ_CUDA(cudaMalloc(reinterpret_cast<void**>(&p), n * sizeof(T)));
+    count = n;
+  }
+};
+
+}  // namespace flz
+
+// Matrix handle: a device copy of a symmetric CSR matrix (Section 3.2.1).
+struct flz_matrix {
+  int64_t n = 0, nnz = 0;
+  int device = 0;
+  flz::DevBuf<int32_t> rowptr, col;
+  flz::DevBuf<double> val;
+  flz::DevBuf<float> val32;            // made on first FP32 filter use
+  flz::DevBuf<__nv_bfloat16> val16;    // made on first BF16 filter use
+  double glo = 0.0, ghi = 0.0;         // Gershgorin interval
+  int32_t max_row_nnz = 0;
+  // Scratch of flz_filter_apply: recurrence vectors and the running sum.
+  flz::DevBuf<double> ws64;
+  flz::DevBuf<float> ws32;
+  flz::DevBuf<__nv_bfloat16> ws16;
+};
+
+// Solver handle: parameters, interval, results of the last solve and workspace.
+struct flz_solver {
+  flz_matrix* A = nullptr;
+  flz_params p{};
+  double alpha = 0.0, beta = 0.0;
+  bool has_interval = false;
+  bool solved = false;
+  int64_t count = 0;
+  std::vector<double> evals, resid;
+  flz::DevBuf<double> evecs;  // n x count, column-major, ld = n
+  flz_stats stats{};
+  // workspace
+  flz::DevBuf<double> Q, W, C, C2, part, X, AX, small, colpart;
+};
+
+namespace flz {
+
+// ---- filter.cu ----------------------------------------------------------------
+// W = p_m((A - cI)/e) V, V and W device FP64 n x r row-major.
+void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m, int r,
+                  const double* V, double* W, int precision, cudaStream_t st);
+// Number of kernel launches filter_apply issues for degree m at `precision`.
+int filter_launch_count(int m, int precision);
+// Y = A X for an n x s block with row stride ld (s <= 16), FP64.
+void spmm(const flz_matrix* A, const double* X, double* Y, int s, int ld, cudaStream_t st);
+
+// ---- blockops.cu ------------------------------------------------------------------
+// Basis layout: nb blocks, block b at Q + b * n * r, each n x r row-major.
+// C[b][a][t] = sum_i Q_b[i, a] W[i, t] for t < s (W has row stride ldw), into
+// device C (nb*r x s, row-major). `part` is scratch (see basis_dot_scratch).
+size_t basis_dot_scratch(int64_t n, int nb, int r, int s);
+void basis_dot(const double* Q, int nb, int64_t n, int r, const double* W, int s, int ldw, double* C,
+               double* part, cudaStream_t st);
+// Out[i, t] = beta * Out[i, t] + alpha * sum_{b, a} Q_b[i, a] C[(b*r + a)*s + t], t < s.
+// Out has row stride ldo; Out may equal Q's block 0 when nb == 1 (in-place).
+void basis_update(const double* Q, int nb, int64_t n, int r, const double* C, int s, double alpha,
+                  double beta, double* Out, int ldo, cudaStream_t st);
+// Per-column sums over rows: out[t] = sum_i X[i,t] Y[i,t] (mode 0) or
+// sum_i (Y[i,t] - lam[t] X[i,t])^2 (mode 1); X, Y n x s with stride ld.
+void column_sums(const double* X, const double* Y, const double* lam, int64_t n, int s, int ld, int mode,
+                 double* out, double* part, cudaStream_t st);
+size_t column_sums_scratch(int64_t n, int s);
+// n x r block of N(0,1) numbers from a counter-based generator (seed, offset).
+void random_normal(double* X, int64_t count, uint64_t seed, uint64_t offset, cudaStream_t st);
+// Column j of a row-major n x s block (stride ld) into column-major out (stride ldo).
+void rows_to_columns(const double* X, int64_t n, int s, int ld, double* out, int64_t ldo, cudaStream_t st);
+// Gershgorin interval and max row length on the device.
+void gershgorin(const flz_matrix* A, double* glo, double* ghi, int32_t* max_row_nnz);
+// Structural/symmetry validation on the device; returns status (BAD_CSR, NOT_SYMMETRIC, OK).
+flz_status validate_csr(const flz_matrix* A, int check_symmetry);
+
+// ---- hostla.cpp -------------------------------------------------------------------------
+// Eigenvalues (ascending) of a symmetric band matrix (dense K x K storage,
+// semi-bandwidth b): orthogonal band-to-tridiagonal reduction, then implicit QL.
+void band_eigenvalues(const std::vector<double>& T, int K, int b, std::vector<double>& theta);
+// Unit eigenvectors for the eigenvalues theta[idx[...]] by inverse iteration on
+// the band matrix with partial pivoting; vectors of close eigenvalues are
+// orthogonalized against each other. Y is K x count column-major.
+void band_eigenvectors(const std::vector<double>& T, int K, int b, const std::vector<double>& theta,
+                       const std::vector<int>& idx, std::vector<double>& Y, uint64_t seed);
+// Eigenvalues of a symmetric tridiagonal (d, e) by implicit QL; d overwritten ascending.
+void tridiagonal_eigenvalues(std::vector<double>& d, std::vector<double>& e);
+// Upper Cholesky factor R (G = R^T R) of an s x s SPD matrix, row-major; false if not SPD.
+bool cholesky_upper(const double* G, int s, double* R);
+// Inverse of an upper-triangular s x s matrix, row-major.
+void upper_inverse(const double* R, int s, double* Rinv);
+
+// ---- coefficients (api.cu) --------------------------------------------------------------
+void chebyshev_coefficients(double a, double b, int m, double* out);
+int auto_degree(double a, double b, double eps, int max_degree);
+
+}  // namespace flz

@@ -1,0 +1,482 @@
+// The filtered Lanczos procedure (Sections 2.2, 2.3, 3.2.2) on one GPU.
+//
+//   bounds      block Lanczos on A (Section 2.2 after eq. transf): extreme Ritz
+//               values padded by their residual bounds, clamped to Gershgorin
+//   map/filter  eq. (transf), eq. (optimaldegree), closed-form coefficients
+//   loop        W = p(A) Q_j (filter.cu); full reorthogonalization of W against
+//               the whole basis by classical Gram-Schmidt applied twice;
+//               D_j = Q_j^T p(A) Q_j from the two projections; block QR of W by
+//               CholeskyQR2 (shifted CholeskyQR3 when W is ill conditioned)
+//               giving Q_{j+1} and the upper-triangular S_j (eq. lanczos)
+//   check       every `check_every` blocks: T_k (eq. lanczos) on the host,
+//               its eigenvalues (eq. proj) by band reduction + QL, Ritz pairs
+//               ranked by the p(A) Ritz value; for the leading ones, Ritz
+//               vectors Q_k y on the GPU, Rayleigh quotients (eq. rayleigh)
+//               and true residuals ||Ax - lambda x|| / ||A||. Converged when every
+//               pair with lambda in [alpha, beta] and the `guard` nearest
+//               outside have residual <= tol and the count in [alpha, beta] is
+//               unchanged since the previous check (Section 3.2.2).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+
+#include "flz_internal.h"
+
+namespace flz {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+inline double ms_since(Clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+// Host copies of the small per-step matrices of eq. (lanczos).
+struct Projected {
+  int r = 0;
+  std::vector<std::vector<double>> D, S;  // r x r row-major each
+  // T_k from D_0..D_{k-1}, S_0..S_{k-2}, symmetrized; dense K x K row-major.
+  std::vector<double> assemble(int k) const {
+    const int K = k * r;
+    std::vector<double> T((size_t)K * K, 0.0);
+    for (int b = 0; b < k; ++b) {
+      for (int i = 0; i < r; ++i)
+        for (int j = 0; j < r; ++j)
+          T[(size_t)(b * r + i) * K + b * r + j] = 0.5 * (D[b][i * r + j] + D[b][j * r + i]);
+      if (b + 1 < k)
+        for (int i = 0; i < r; ++i)
+          for (int j = 0; j < r; ++j) {
+            const double v = S[b][i * r + j];
+            T[(size_t)((b + 1) * r + i) * K + b * r + j] = v;
+            T[(size_t)(b * r + j) * K + (b + 1) * r + i] = v;
+          }
+    }
+    return T;
+  }
+};
+
+struct Engine {
+  flz_matrix* A;
+  int64_t n;
+  int r;
+  cudaStream_t st;
+  double* Q;     // basis, nb_cap blocks
+  int nb_cap;
+  double* W;     // n x r
+  double* C;     // nb_cap*r x r
+  double* C2;
+  double* part;  // basis_dot scratch
+  double* small; // device r x r scratch (R^{-1})
+  double ms_orth = 0.0, ms_op = 0.0;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+
+  double* block(int b) const { return Q + (size_t)b * n * r; }
+
+  void gram(const double* X, std::vector<double>& G) {
+    basis_dot(X, 1, n, r, X, r, r, C2, part, st);
+    G.resize((size_t)r * r);
+    FLZ_CUDA(cudaMemcpyAsync(G.data(), C2, sizeof(double) * r * r, cudaMemcpyDeviceToHost, st));
+    FLZ_CUDA(cudaStreamSynchronize(st));
+  }
+
+  // Out = X R^{-1} (in place allowed).
+  void right_solve(const double* X, const std::vector<double>& Rinv, double* Out) {
+    FLZ_CUDA(cudaMemcpyAsync(small, Rinv.data(), sizeof(double) * r * r, cudaMemcpyHostToDevice, st));
+    basis_update(X, 1, n, r, small, r, 1.0, 0.0, Out, r, st);
+  }
+
+  // Block QR of the n x r block X into Out (CholeskyQR2, shifted CholeskyQR3
+  // when the first Cholesky fails); returns S (upper triangular, row-major).
+  std::vector<double> block_qr(const double* X, double* Out) {
+    std::vector<double> G, R((size_t)r * r), Rinv((size_t)r * r), S((size_t)r * r, 0.0), tmp((size_t)r * r);
+    for (int i = 0; i < r; ++i) S[i * r + i] = 1.0;
+    gram(X, G);
+    const double* src = X;
+    int passes = 2;
+    if (!cholesky_upper(G.data(), r, R.data())) {
+      // shifted Cholesky keeps the factorization defined for ill-conditioned X
+      double gnorm = 0.0;
+      for (int i = 0; i < r; ++i) gnorm = std::max(gnorm, G[i * r + i]);
+      gnorm = std::max(gnorm * r, 1e-300);
+      const double shift = 11.0 * ((double)n * r + (double)r * (r + 1)) * 1.1102230246251565e-16 * gnorm;
+      for (int i = 0; i < r; ++i) G[i * r + i] += shift;
+      if (!cholesky_upper(G.data(), r, R.data())) {
+        for (int i = 0; i < r * r; ++i) R[i] = 0.0;
+        for (int i = 0; i < r; ++i) R[i * r + i] = std::sqrt(std::max(G[i * r + i], 1e-300));
+      }
+      passes = 3;
+    }
+    for (int pass = 0; pass < passes; ++pass) {
+      if (pass > 0) {
+        gram(Out, G);
+        if (!cholesky_upper(G.data(), r, R.data())) {
+          for (int i = 0; i < r * r; ++i) R[i] = 0.0;
+          for (int i = 0; i < r; ++i) R[i * r + i] = std::sqrt(std::max(G[i * r + i], 1e-300));
+        }
+      }
+      upper_inverse(R.data(), r, Rinv.data());
+      right_solve(src, Rinv, Out);
+      src = Out;
+      // S <- R S
+      for (int i = 0; i < r; ++i)
+        for (int j = 0; j < r; ++j) {
+          double v = 0.0;
+          for (int k = 0; k < r; ++k) v += R[i * r + k] * S[k * r + j];
+          tmp[i * r + j] = v;
+        }
+      S = tmp;
+    }
+    return S;
+  }
+
+  // Classical Gram-Schmidt twice of X against blocks 0..nb-1; returns the
+  // total projection coefficients of the last block (r x r, row-major) in Dlast.
+  void cgs2(double* X, int nb, std::vector<double>* Dlast) {
+    basis_dot(Q, nb, n, r, X, r, r, C, part, st);
+    basis_update(Q, nb, n, r, C, r, -1.0, 1.0, X, r, st);
+    basis_dot(Q, nb, n, r, X, r, r, C2, part, st);
+    basis_update(Q, nb, n, r, C2, r, -1.0, 1.0, X, r, st);
+    if (Dlast) {
+      std::vector<double> d1((size_t)r * r), d2((size_t)r * r);
+      const size_t off = (size_t)(nb - 1) * r * r;
+      FLZ_CUDA(cudaMemcpyAsync(d1.data(), C + off, sizeof(double) * r * r, cudaMemcpyDeviceToHost, st));
+      FLZ_CUDA(cudaMemcpyAsync(d2.data(), C2 + off, sizeof(double) * r * r, cudaMemcpyDeviceToHost, st));
+      FLZ_CUDA(cudaStreamSynchronize(st));
+      Dlast->resize((size_t)r * r);
+      for (int i = 0; i < r * r; ++i) (*Dlast)[i] = d1[i] + d2[i];
+    }
+  }
+
+  // One block Lanczos step j: W = op(Q_j), reorthogonalize, QR into Q_{j+1}.
+  // Returns false if the new block could not be formed (no slot).
+  void step(int j, const std::function<void(const double*, double*)>& op, Projected& P, double op_norm) {
+    if (!ev[0])
+      for (auto& x : ev) FLZ_CUDA(cudaEventCreate(&x));
+    FLZ_CUDA(cudaEventRecord(ev[0], st));
+    op(block(j), W);
+    FLZ_CUDA(cudaEventRecord(ev[1], st));
+    std::vector<double> D;
+    cgs2(W, j + 1, &D);
+    P.D.push_back(D);
+    double* next = (j + 1 < nb_cap) ? block(j + 1) : nullptr;
+    double* dst = next ? next : W;
+    std::vector<double> S = block_qr(W, dst);
+    // breakdown: the new block is (nearly) dependent on the basis; its
+    // directions are rounding noise and must be made orthogonal to the basis.
+    double smin = 1e300;
+    for (int i = 0; i < r; ++i) smin = std::min(smin, std::fabs(S[i * r + i]));
+    if (next && smin < 1e-12 * std::max(op_norm, 1e-300)) {
+      cgs2(next, j + 1, nullptr);
+      block_qr(next, next);
+    }
+    P.S.push_back(S);
+    FLZ_CUDA(cudaEventRecord(ev[2], st));
+    FLZ_CUDA(cudaEventSynchronize(ev[2]));
+    float a = 0.f, b = 0.f;
+    FLZ_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
+    FLZ_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
+    ms_op += a;
+    ms_orth += b;
+  }
+  ~Engine() {
+    for (auto& x : ev)
+      if (x) cudaEventDestroy(x);
+  }
+};
+
+void orthonormal_start(Engine& E, uint64_t seed) {
+  random_normal(E.block(0), E.n * E.r, seed, 0, E.st);
+  E.block_qr(E.block(0), E.block(0));
+}
+
+// Spectrum bounds by block Lanczos on A (Section 2.2 after eq. transf).
+void estimate_bounds(flz_matrix* A, int steps, int r, uint64_t seed, cudaStream_t st, double* lmin, double* lmax) {
+  const int64_t n = A->n;
+  int nb = std::max(2, (steps + r - 1) / r);
+  nb = (int)std::min<int64_t>(nb, std::max<int64_t>(1, n / r));
+  DevBuf<double> Qb, Wb, Cb, C2b, partb, smallb;
+  Qb.reserve((size_t)(nb + 1) * n * r);
+  Wb.reserve((size_t)n * r);
+  Cb.reserve((size_t)(nb + 1) * r * r);
+  C2b.reserve((size_t)(nb + 1) * r * r);
+  partb.reserve(std::max(basis_dot_scratch(n, nb + 1, r, r), (size_t)1));
+  smallb.reserve((size_t)r * r);
+  Engine E{A, n, r, st, Qb.p, nb + 1, Wb.p, Cb.p, C2b.p, partb.p, smallb.p};
+  orthonormal_start(E, seed ^ 0x5bd1e995ull);
+  Projected P;
+  P.r = r;
+  const double anorm = std::max(std::fabs(A->glo), std::fabs(A->ghi));
+  auto op = [&](const double* X, double* Y) { spmm(A, X, Y, r, r, st); };
+  int k = 0;
+  for (int j = 0; j < nb; ++j) {
+    E.step(j, op, P, anorm);
+    k = j + 1;
+  }
+  const int K = k * r;
+  std::vector<double> T = P.assemble(k);
+  std::vector<double> theta;
+  band_eigenvalues(T, K, r, theta);
+  std::vector<int> idx = {0, K - 1};
+  std::vector<double> Y;
+  band_eigenvectors(T, K, r, theta, idx, Y, seed);
+  const std::vector<double>& S = P.S[k - 1];
+  auto resbound = [&](int t) {
+    // || S_k y_bottom ||
+    const double* y = &Y[(size_t)t * K + (size_t)(k - 1) * r];
+    double s2 = 0.0;
+    for (int i = 0; i < r; ++i) {
+      double v = 0.0;
+      for (int a = 0; a < r; ++a) v += S[i * r + a] * y[a];
+      s2 += v * v;
+    }
+    return std::sqrt(s2);
+  };
+  double lo = theta[0] - resbound(0);
+  double hi = theta[K - 1] + resbound(1);
+  // a tiny relative margin keeps the mapped extremes inside [-1, 1] under rounding
+  const double margin = 1e-10 * std::max(1.0, hi - lo);
+  lo -= margin;
+  hi += margin;
+  *lmin = std::max(lo, A->glo);
+  *lmax = std::min(hi, A->ghi);
+  if (!(*lmin < *lmax)) {
+    *lmin = A->glo;
+    *lmax = A->ghi;
+  }
+}
+
+}  // namespace
+
+void bounds_entry(flz_matrix* A, int steps, int r, uint64_t seed, cudaStream_t st, double* lmin, double* lmax) {
+  estimate_bounds(A, steps, r, seed, st, lmin, lmax);
+}
+
+flz_status solve(flz_solver* s, cudaStream_t st) {
+  const auto t_start = Clock::now();
+  const int64_t launches0 = g_kernel_launches;
+  flz_matrix* A = s->A;
+  const flz_params& p = s->p;
+  const int64_t n = A->n;
+  const int r = p.block_size;
+  flz_stats& stats = s->stats;
+  stats = flz_stats{};
+  stats.block_size = r;
+  s->solved = false;
+  s->count = 0;
+  s->evals.clear();
+  s->resid.clear();
+  if (r < 1 || r > 16 || r > n) fail(FLZ_ERR_INVALID_ARG, "block size %d invalid for n = %lld", r, (long long)n);
+
+  // 1. bounds
+  auto t0 = Clock::now();
+  double lmin, lmax;
+  if (p.lmin < p.lmax) {
+    lmin = p.lmin;
+    lmax = p.lmax;
+  } else {
+    estimate_bounds(A, p.bounds_steps, r, p.seed * 7919u + 17u, st, &lmin, &lmax);
+  }
+  stats.ms_bounds = ms_since(t0);
+  stats.lmin = lmin;
+  stats.lmax = lmax;
+  // 2. map (eq. transf)
+  const double c = 0.5 * (lmin + lmax), e = 0.5 * (lmax - lmin);
+  stats.c = c;
+  stats.e = e;
+  double am = (s->alpha - c) / e, bm = (s->beta - c) / e;
+  if (bm < -1.0 || am > 1.0) fail(FLZ_ERR_EMPTY_INTERVAL, "[%g, %g] misses the spectrum [%g, %g]", s->alpha, s->beta, lmin, lmax);
+  am = std::max(am, -1.0);
+  bm = std::min(bm, 1.0);
+  stats.alpha_mapped = am;
+  stats.beta_mapped = bm;
+  // 3. degree and coefficients
+  const int m = p.degree > 0 ? p.degree : auto_degree(am, bm, p.degree_eps, p.max_degree);
+  if (m < 0) fail(FLZ_ERR_CAPACITY, "no degree <= %d meets the degree rule", p.max_degree);
+  stats.degree = m;
+  std::vector<double> coeffs(m + 1);
+  chebyshev_coefficients(am, bm, m, coeffs.data());
+  const double anorm = std::max(std::fabs(lmin), std::fabs(lmax));
+
+  // 4. basis capacity
+  int64_t kcap = p.max_basis > 0 ? p.max_basis : 2000;
+  kcap = std::min<int64_t>(kcap, n);
+  size_t free_b = 0, total_b = 0;
+  FLZ_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const int64_t mem_cap = (int64_t)(0.6 * (double)free_b / (8.0 * (double)n));
+  kcap = std::min(kcap, std::max<int64_t>(mem_cap, 2 * r));
+  const int nb_cap = (int)std::max<int64_t>(2, kcap / r);
+  s->Q.reserve((size_t)nb_cap * n * r);
+  s->W.reserve((size_t)n * r);
+  s->C.reserve((size_t)nb_cap * r * r);
+  s->C2.reserve((size_t)nb_cap * r * r);
+  s->part.reserve(std::max(basis_dot_scratch(n, nb_cap, r, r), (size_t)1));
+  s->small.reserve(16 * 16 + 64);
+  s->X.reserve((size_t)n * 16);
+  s->AX.reserve((size_t)n * 16);
+  s->colpart.reserve(column_sums_scratch(n, 16) + 64);
+  Engine E{A, n, r, st, s->Q.p, nb_cap, s->W.p, s->C.p, s->C2.p, s->part.p, s->small.p};
+  orthonormal_start(E, p.seed);
+
+  Projected P;
+  P.r = r;
+  const int guard = p.guard > 0 ? p.guard : std::max(r, 3);
+  auto filt = [&](const double* X, double* Y) {
+    filter_apply(A, c, e, coeffs.data(), m, r, X, Y, p.precision, st);
+  };
+  double ms_check = 0.0;
+  int64_t prev_count = -1;
+  bool converged = false;
+  int k = 0;
+  std::vector<double> found_vals, found_res;
+  int64_t found = 0;
+  for (int j = 0; j < nb_cap; ++j) {
+    E.step(j, filt, P, 1.0);
+    k = j + 1;
+    const bool last = (k == nb_cap) || ((int64_t)(k + 1) * r > n);
+    if (k % p.check_every != 0 && !last) continue;
+
+    // ---- convergence check ----
+    const auto tc = Clock::now();
+    stats.checks++;
+    const int K = k * r;
+    std::vector<double> T = P.assemble(k);
+    std::vector<double> theta;
+    band_eigenvalues(T, K, r, theta);
+    std::vector<int> order(K);
+    for (int i = 0; i < K; ++i) order[i] = K - 1 - i;  // descending theta
+    const std::vector<double>& Sk = P.S[k - 1];
+    int inside = 0, outside = 0;
+    bool all_small = true, walk_done = false;
+    found_vals.clear();
+    found_res.clear();
+    found = 0;
+    const double p_gate = std::min(1e-2, std::max(1e3 * p.tol, 1e-8) * (double)m * m * anorm / e);
+    for (int pos = 0; pos < K && !walk_done; pos += 16) {
+      const int cnt = std::min(16, K - pos);
+      std::vector<int> idx(order.begin() + pos, order.begin() + pos + cnt);
+      std::vector<double> Y;
+      band_eigenvectors(T, K, r, theta, idx, Y, p.seed + (uint64_t)pos);
+      // cheap gate on the p(A) residual ||S_k y_bottom|| of the leading pair
+      {
+        const double* y = &Y[(size_t)(k - 1) * r];
+        double s2 = 0.0;
+        for (int i = 0; i < r; ++i) {
+          double v = 0.0;
+          for (int a = 0; a < r; ++a) v += Sk[i * r + a] * y[a];
+          s2 += v * v;
+        }
+        if (std::sqrt(s2) > p_gate) {
+          all_small = false;
+          break;
+        }
+      }
+      // Ritz vectors X = Q_k Y (n x 16, zero-padded columns)
+      std::vector<double> Cy((size_t)K * 16, 0.0);
+      for (int t = 0; t < cnt; ++t)
+        for (int i = 0; i < K; ++i) Cy[(size_t)i * 16 + t] = Y[(size_t)t * K + i];
+      s->C2.reserve(std::max(s->C2.count, (size_t)K * 16));
+      E.C2 = s->C2.p;
+      FLZ_CUDA(cudaMemcpyAsync(s->C2.p, Cy.data(), sizeof(double) * K * 16, cudaMemcpyHostToDevice, st));
+      basis_update(s->Q.p, k, n, r, s->C2.p, 16, 1.0, 0.0, s->X.p, 16, st);
+      spmm(A, s->X.p, s->AX.p, 16, 16, st);
+      double* dev = s->small.p;  // [0,16) xx, [16,32) xAx, [32,48) lam, [48,64) res2, [64] scale
+      column_sums(s->X.p, s->X.p, nullptr, n, 16, 16, 0, dev, s->colpart.p, st);
+      column_sums(s->X.p, s->AX.p, nullptr, n, 16, 16, 0, dev + 16, s->colpart.p, st);
+      double h[64];
+      FLZ_CUDA(cudaMemcpyAsync(h, dev, sizeof(double) * 32, cudaMemcpyDeviceToHost, st));
+      FLZ_CUDA(cudaStreamSynchronize(st));
+      for (int t = 0; t < 16; ++t) h[32 + t] = (t < cnt && h[t] > 0) ? h[16 + t] / h[t] : 0.0;
+      FLZ_CUDA(cudaMemcpyAsync(dev + 32, h + 32, sizeof(double) * 16, cudaMemcpyHostToDevice, st));
+      column_sums(s->X.p, s->AX.p, dev + 32, n, 16, 16, 1, dev + 48, s->colpart.p, st);
+      FLZ_CUDA(cudaMemcpyAsync(h + 48, dev + 48, sizeof(double) * 16, cudaMemcpyDeviceToHost, st));
+      FLZ_CUDA(cudaStreamSynchronize(st));
+      for (int t = 0; t < cnt; ++t) {
+        const double xx = h[t];
+        const double lam = h[32 + t];
+        const double res = std::sqrt(std::max(h[48 + t], 0.0) / std::max(xx, 1e-300)) / anorm;
+        if (res > p.tol) {
+          all_small = false;
+          walk_done = true;
+          break;
+        }
+        if (lam >= s->alpha && lam <= s->beta) {
+          // keep x / ||x|| as a result column
+          const size_t need = (size_t)(found + 1) * n;
+          if (s->evecs.count < need) {
+            DevBuf<double> grown;
+            grown.reserve(std::max(need, s->evecs.count * 2));
+            if (found > 0)
+              FLZ_CUDA(cudaMemcpyAsync(grown.p, s->evecs.p, sizeof(double) * found * n, cudaMemcpyDeviceToDevice, st));
+            std::swap(grown.p, s->evecs.p);
+            std::swap(grown.count, s->evecs.count);
+          }
+          rows_to_columns(s->X.p + t, n, 1, 16, s->evecs.p + (size_t)found * n, n, st);
+          std::vector<double> sc(1, 1.0 / std::sqrt(xx));
+          FLZ_CUDA(cudaMemcpyAsync(dev + 64, sc.data(), sizeof(double), cudaMemcpyHostToDevice, st));
+          basis_update(s->evecs.p + (size_t)found * n, 1, n, 1, dev + 64, 1, 1.0, 0.0,
+                       s->evecs.p + (size_t)found * n, 1, st);
+          found_vals.push_back(lam);
+          found_res.push_back(res);
+          ++found;
+          ++inside;
+        } else {
+          ++outside;
+          if (outside >= guard) {
+            walk_done = true;
+            break;
+          }
+        }
+      }
+      if (!walk_done && pos + cnt >= K) walk_done = true;
+    }
+    const bool complete = all_small && outside >= guard;
+    converged = complete && prev_count >= 0 && inside == prev_count;
+    prev_count = complete ? inside : -1;
+    ms_check += ms_since(tc);
+    if (converged || last) break;
+  }
+  FLZ_CUDA(cudaStreamSynchronize(st));
+
+  // sort ascending
+  std::vector<int> perm(found);
+  for (int i = 0; i < found; ++i) perm[i] = i;
+  std::sort(perm.begin(), perm.end(), [&](int a, int b) { return found_vals[a] < found_vals[b]; });
+  bool sorted = true;
+  for (int i = 0; i < found; ++i) sorted &= perm[i] == i;
+  if (!sorted && found > 0) {
+    DevBuf<double> tmp;
+    tmp.reserve((size_t)found * n);
+    for (int i = 0; i < found; ++i)
+      FLZ_CUDA(cudaMemcpyAsync(tmp.p + (size_t)i * n, s->evecs.p + (size_t)perm[i] * n, sizeof(double) * n,
+                               cudaMemcpyDeviceToDevice, st));
+    FLZ_CUDA(cudaStreamSynchronize(st));
+    std::swap(tmp.p, s->evecs.p);
+    std::swap(tmp.count, s->evecs.count);
+  }
+  s->evals.resize(found);
+  s->resid.resize(found);
+  double maxres = 0.0;
+  for (int i = 0; i < found; ++i) {
+    s->evals[i] = found_vals[perm[i]];
+    s->resid[i] = found_res[perm[i]];
+    maxres = std::max(maxres, s->resid[i]);
+  }
+  s->count = found;
+  s->solved = true;
+  stats.iters = k;
+  stats.matvecs = (int64_t)r * m * k;
+  stats.count = found;
+  stats.converged = converged ? 1 : 0;
+  stats.max_residual = maxres;
+  stats.ms_filter = E.ms_op;
+  stats.ms_orth = E.ms_orth;
+  stats.ms_check = ms_check;
+  stats.basis_vectors = (int64_t)k * r;
+  stats.ms_total = ms_since(t_start);
+  stats.kernel_launches = g_kernel_launches - launches0;
+  return converged ? FLZ_OK : FLZ_ERR_NOT_CONVERGED;
+}
+
+}  // namespace flz

@@ -1,0 +1,120 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every
+symbol include/flz.h declares, and its host-only logic (filter coefficients,
+the degree rule, the projected-problem eigensolver, parameters and status
+strings) agrees with the paper and with independent computations.
+"""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+import paper_2409_15053_gb300 as flz
+from oracle import chebyshev
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+
+
+def header_symbols():
+    text = open(os.path.join(ROOT, "include", "flz.h")).read()
+    return sorted(set(re.findall(r"^(?:flz_status|const char\*)\s+(flz_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_and_binding_agree():
+    assert sorted(flz.EXPORTED) == header_symbols()
+
+
+def test_library_exports_every_declared_symbol():
+    L = flz.lib()
+    for name in header_symbols():
+        assert hasattr(L, name), name
+
+
+def test_status_strings_and_defaults():
+    assert flz.flz_status_string(flz.FLZ_OK) == "FLZ_OK"
+    assert flz.flz_status_string(flz.FLZ_ERR_EMPTY_INTERVAL) == "FLZ_ERR_EMPTY_INTERVAL"
+    p = flz.flz_params_default()
+    assert p.block_size == 3 and p.degree == 0 and abs(p.degree_eps - 0.3123) < 1e-15
+    assert p.check_every == 30 and p.tol == 1e-10 and p.bounds_steps == 60
+
+
+@pytest.mark.parametrize("a,b,m", [(-1.0, -0.5, 30), (0.1, 0.3, 80), (-0.9538, 0.2, 5), (-1.0, 1.0, 12)])
+def test_coefficients_match_oracle(a, b, m):
+    got = flz.flz_filter_coefficients(a, b, m)
+    assert np.max(np.abs(got - chebyshev.filter_coefficients(a, b, m))) < 1e-14
+
+
+def test_degree_rule_reproduces_table2():
+    import json
+    rows = json.load(open(os.path.join(ROOT, "tests", "golden", "table2_auto_degree.json")))["rows"]
+    for row in rows:
+        c = 0.5 * (row["lmin"] + row["lmax"])
+        e = 0.5 * (row["lmax"] - row["lmin"])
+        assert flz.flz_filter_degree((row["alpha"] - c) / e, (row["beta"] - c) / e) == row["m_auto"]
+
+
+def test_invalid_arguments_are_rejected_without_a_gpu():
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_filter_coefficients(0.5, 0.1, 10)
+    assert e.value.status == flz.FLZ_ERR_INVALID_ARG
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_filter_degree(-1.0, -0.99999999, 0.3123, 5)
+    assert e.value.status == flz.FLZ_ERR_CAPACITY
+
+
+def _random_band(K, b, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    T = np.zeros((K, K))
+    for k in range(b + 1):
+        v = rng.standard_normal(K - k) * scale
+        T += np.diag(v, k)
+        if k:
+            T += np.diag(v, -k)
+    return T
+
+
+@pytest.mark.parametrize("K,b", [(1, 1), (7, 3), (60, 1), (200, 4), (480, 16)])
+def test_band_eigenvalues_match_dense_eigensolver(K, b):
+    T = _random_band(K, b, K + b)
+    got = flz.flz_band_eigenvalues(T, b)
+    ref = np.linalg.eigvalsh(T)
+    assert np.max(np.abs(got - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_band_eigenvectors_are_orthonormal_eigenvectors():
+    T = _random_band(300, 4, 9)
+    theta = flz.flz_band_eigenvalues(T, 4)
+    idx = np.arange(299, 259, -1)
+    Y = flz.flz_band_eigenvectors(T, 4, theta, idx)
+    assert np.max(np.abs(T @ Y - Y * theta[idx])) < 1e-11
+    assert np.max(np.abs(Y.T @ Y - np.eye(Y.shape[1]))) < 1e-12
+
+
+def test_band_eigenvectors_span_a_multiple_eigenvalue():
+    # block-diagonal copies of one matrix: every eigenvalue has multiplicity 3,
+    # as in block Lanczos on a matrix with repeated eigenvalues
+    B = _random_band(40, 2, 4)
+    T = np.kron(np.eye(3), B)
+    theta = flz.flz_band_eigenvalues(T, 2)
+    ref = np.linalg.eigvalsh(T)
+    assert np.max(np.abs(theta - ref)) < 1e-12
+    top = np.arange(119, 113, -1)  # two triple eigenvalues
+    Y = flz.flz_band_eigenvectors(T, 2, theta, top)
+    assert np.max(np.abs(Y.T @ Y - np.eye(6))) < 1e-10
+    assert np.max(np.abs(T @ Y - Y * theta[top])) < 1e-10
+
+
+def test_laplacian_tridiagonal_closed_form():
+    # 1D Dirichlet Laplacian: eigenvalues 2 - 2 cos(k pi / (K + 1))
+    K = 150
+    T = 2 * np.eye(K) - np.eye(K, k=1) - np.eye(K, k=-1)
+    got = flz.flz_band_eigenvalues(T, 1)
+    ref = np.sort(2 - 2 * np.cos(np.arange(1, K + 1) * np.pi / (K + 1)))
+    assert np.max(np.abs(got - ref)) < 1e-13

@@ -1,0 +1,179 @@
+"""Parity of the hot path, W = p_m((A - cI)/e) V, against the CPU oracle.
+
+The CUDA kernels evaluate the filter by the forward three-term recurrence
+fused with the running sum; the oracle uses the paper's Clenshaw recurrence.
+Both are the same polynomial, so in FP64 they differ only by rounding.
+
+Tolerance (FP64): a perturbation of size u in step j of a Chebyshev
+recurrence reaches step k multiplied by a Chebyshev polynomial of the second
+kind, |U_{k-j}| <= k - j + 1 on [-1, 1]; summing over the steps and the
+coefficients (|b_k| <= 2/(k pi)) bounds the error of either method by a small
+multiple of m^2 u max|V| times the row-sum of |Ahat|. The tests use
+32 (m + 1)^2 u (1 + max row sum of |Ahat|) max|V|.
+
+Reduced precision: FP32 storage and arithmetic give the same bound with the
+FP32 unit roundoff; BF16 storage adds the BF16 rounding of every stored
+vector, bounded the same way with u = 2^-8.
+"""
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+import paper_2409_15053_gb300 as flz
+from oracle import chebyshev
+from synth import (diagonal_csr, fd4_laplacian_3d, gaussian_wells_potential, laplacian_2d, laplacian_3d_7pt,
+                   powerlaw_graph_laplacian, random_normal_block)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+U32 = 2.0 ** -24
+UBF = 2.0 ** -8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+class Mat:
+    def __init__(self, csr):
+        self.csr = csr
+        self.h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+
+    def __del__(self):
+        try:
+            flz.flz_matrix_destroy(self.h)
+        except Exception:
+            pass
+
+
+def run_filter(M, c, e, coeffs, V, precision=flz.FLZ_PREC_FP64):
+    Vd = torch.from_numpy(np.ascontiguousarray(V)).cuda()
+    Wd = torch.full_like(Vd, float("nan"))
+    flz.flz_filter_apply(M.h, c, e, coeffs, len(coeffs) - 1, V.shape[1], Vd, Wd, precision)
+    torch.cuda.synchronize()
+    return Wd.cpu().numpy()
+
+
+def bound(csr, c, e, m, V, u):
+    S = csr.to_scipy()
+    rowsum = np.asarray(abs(S).sum(axis=1)).ravel() + abs(c)
+    return 32.0 * (m + 1) ** 2 * u * (1.0 + rowsum.max() / e) * np.max(np.abs(V))
+
+
+def gershgorin_map(csr):
+    S = csr.to_scipy()
+    d = S.diagonal()
+    rad = np.asarray(abs(S).sum(axis=1)).ravel() - np.abs(d)
+    lo, hi = float(np.min(d - rad)), float(np.max(d + rad))
+    return 0.5 * (lo + hi), 0.5 * (hi - lo)
+
+
+CASES = [
+    ("lap2d_37x41", lambda: laplacian_2d(37, 41)),
+    ("lap3d_pot_13x9x11", lambda: laplacian_3d_7pt(13, 9, 11, 0.5 * np.linspace(0, 1, 1287))),
+    ("fd4_wells_10", lambda: fd4_laplacian_3d(10, gaussian_wells_potential(10, 5, seed=3))),
+    ("graph_3000", lambda: powerlaw_graph_laplacian(3000, seed=2)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[x[0] for x in CASES])
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 5, 8, 16])
+def test_fp64_filter_matches_oracle(name, make, r):
+    csr = make()
+    c, e = gershgorin_map(csr)
+    M = Mat(csr)
+    m = 37
+    coeffs = chebyshev.filter_coefficients(-0.8, -0.35, m)
+    V = random_normal_block(csr.n, r, 100 + r)
+    got = run_filter(M, c, e, coeffs, V)
+    ref = chebyshev.clenshaw_apply(csr.to_scipy(), c, e, coeffs, V)
+    assert np.all(np.isfinite(got))
+    assert np.max(np.abs(got - ref)) <= bound(csr, c, e, m, V, U64)
+
+
+@pytest.mark.parametrize("m", [0, 1, 2, 3, 50, 200])
+def test_fp64_filter_degrees(m):
+    csr = laplacian_3d_7pt(12, 12, 12)
+    M = Mat(csr)
+    coeffs = chebyshev.filter_coefficients(-1.0, -0.9, m)
+    V = random_normal_block(csr.n, 4, 7)
+    got = run_filter(M, 6.0, 6.0, coeffs, V)
+    ref = chebyshev.clenshaw_apply(csr.to_scipy(), 6.0, 6.0, coeffs, V)
+    assert np.max(np.abs(got - ref)) <= bound(csr, 6.0, 6.0, m, V, U64)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 9, 64])
+def test_single_term_is_cosine_on_a_diagonal_matrix(k):
+    # T_k(x) = cos(k arccos x): with b = e_k the kernel must return cos(k acos d) * V
+    n = 5000
+    d = np.cos(np.linspace(0.0, np.pi, n))
+    M = Mat(diagonal_csr(d))
+    b = np.zeros(k + 1)
+    b[k] = 1.0
+    V = random_normal_block(n, 4, 1)
+    got = run_filter(M, 0.0, 1.0, b, V)
+    want = np.cos(k * np.arccos(d))[:, None] * V
+    assert np.max(np.abs(got - want)) <= 64 * (k + 1) ** 2 * U64 * np.max(np.abs(V))
+
+
+def test_laplacian_eigenvector_identity():
+    nx, ny = 40, 50
+    M = Mat(laplacian_2d(nx, ny))
+    c, e = 4.0, 4.0
+    b = chebyshev.filter_coefficients(-0.7, -0.4, 120)
+    x = np.arange(1, nx + 1)[:, None]
+    y = np.arange(1, ny + 1)[None, :]
+    cols, want = [], []
+    for (i, j) in [(1, 1), (5, 9), (17, 3), (40, 50)]:
+        u = (np.sin(i * np.pi * x / (nx + 1)) * np.sin(j * np.pi * y / (ny + 1))).T.reshape(-1)
+        lam = 4 - 2 * np.cos(i * np.pi / (nx + 1)) - 2 * np.cos(j * np.pi / (ny + 1))
+        z = (lam - c) / e
+        cols.append(u)
+        want.append(np.sum(b * np.cos(np.arange(121) * np.arccos(z))) * u)
+    U = np.stack(cols, axis=1)
+    got = run_filter(M, c, e, b, U)
+    assert np.max(np.abs(got - np.stack(want, axis=1))) < 1e-11
+
+
+@pytest.mark.parametrize("precision,u", [(flz.FLZ_PREC_FP32, U32), (flz.FLZ_PREC_BF16, UBF)])
+def test_reduced_precision_filter_within_bound(precision, u):
+    csr = laplacian_3d_7pt(16, 16, 16, 0.5 * np.linspace(0, 1, 4096))
+    M = Mat(csr)
+    m = 30
+    coeffs = chebyshev.filter_coefficients(-1.0, -0.9, m)
+    V = random_normal_block(csr.n, 4, 5)
+    got = run_filter(M, 6.25, 6.25, coeffs, V, precision)
+    ref = chebyshev.clenshaw_apply(csr.to_scipy(), 6.25, 6.25, coeffs, V)
+    err = np.max(np.abs(got - ref))
+    assert err <= bound(csr, 6.25, 6.25, m, V, u)
+    # and it is a real approximation, not noise
+    assert err < 0.5 * np.max(np.abs(ref))
+
+
+def test_filter_rejects_overlapping_buffers():
+    csr = laplacian_2d(10, 10)
+    M = Mat(csr)
+    Vd = torch.zeros((100, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_filter_apply(M.h, 4.0, 4.0, np.ones(3), 2, 4, Vd, Vd)
+    assert e.value.status == flz.FLZ_ERR_INVALID_ARG
+
+
+def test_full_size_config2_filter_matches_oracle():
+    # 100^3 grid (n = 1e6, 6.94e6 nnz), r = 4, the launch shape the solver uses
+    rng = np.random.Generator(np.random.PCG64(2025))
+    csr = laplacian_3d_7pt(100, 100, 100, 0.5 * rng.random(100 ** 3))
+    M = Mat(csr)
+    m = 60
+    lmin, lmax = 0.0, 12.5
+    c, e = 0.5 * (lmin + lmax), 0.5 * (lmax - lmin)
+    coeffs = chebyshev.filter_coefficients(-1.0, (0.2885 - c) / e, m)
+    V = random_normal_block(csr.n, 4, 77)
+    got = run_filter(M, c, e, coeffs, V)
+    ref = chebyshev.clenshaw_apply(csr.to_scipy(), c, e, coeffs, V)
+    assert np.max(np.abs(got - ref)) <= bound(csr, c, e, m, V, U64)

@@ -1,0 +1,213 @@
+"""End-to-end parity of the GPU filtered Lanczos solver against closed forms,
+the CPU oracle's dense definition, and its error statuses.
+
+Bar: the count in [alpha, beta] is exact (with multiplicity); FP64
+eigenvalues agree within 1e-10 relative to ||A||; every returned pair has
+||Ax - lambda x|| / ||A|| <= tol recomputed here on the CPU; the returned
+eigenvectors are orthonormal to 1e-10.
+"""
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+import paper_2409_15053_gb300 as flz
+from oracle import dense
+from synth import (fd4_laplacian_3d, gaussian_wells_potential, laplacian_2d, laplacian_3d_7pt,
+                   powerlaw_graph_laplacian)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CFG1_ALPHA, CFG1_BETA = 0.9198764447231507, 1.0094761615910202
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def lap2d_eigs(nx, ny):
+    i = np.arange(1, nx + 1)[:, None]
+    j = np.arange(1, ny + 1)[None, :]
+    return np.sort((4 - 2 * np.cos(i * np.pi / (nx + 1)) - 2 * np.cos(j * np.pi / (ny + 1))).ravel())
+
+
+def gap_interval(eigs, lo_index, count):
+    a = 0.5 * (eigs[lo_index - 1] + eigs[lo_index]) if lo_index > 0 else eigs[0] - 1.0
+    b = 0.5 * (eigs[lo_index + count - 1] + eigs[lo_index + count])
+    return a, b
+
+
+def solve(csr, alpha, beta, **kw):
+    h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+    p = flz.flz_params_default()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    s = flz.flz_solver_create(h, p)
+    flz.flz_solver_set_interval(s, alpha, beta)
+    st = flz.flz_solve(s)
+    out = {
+        "status": st,
+        "vals": flz.flz_get_eigenvalues(s),
+        "res": flz.flz_get_residuals(s),
+        "vecs": flz.get_eigenvectors_host(s, csr.n),
+        "stats": flz.flz_get_stats(s),
+    }
+    flz.flz_solver_destroy(s)
+    flz.flz_matrix_destroy(h)
+    return out
+
+
+def check_pairs(csr, out, tol):
+    S = csr.to_scipy()
+    X = out["vecs"]
+    lam = out["vals"]
+    norm_a = max(abs(out["stats"]["lmin"]), abs(out["stats"]["lmax"]))
+    R = S @ X - X * lam
+    res = np.linalg.norm(R, axis=0) / norm_a
+    assert np.all(res <= tol), res.max()
+    assert np.max(np.abs(X.T @ X - np.eye(X.shape[1]))) < 1e-10
+
+
+@pytest.mark.parametrize("r", [1, 2])
+def test_config1_window_matches_closed_form(r):
+    csr = laplacian_2d(50, 50)
+    lam = lap2d_eigs(50, 50)
+    ref = lam[(lam >= CFG1_ALPHA) & (lam <= CFG1_BETA)]
+    out = solve(csr, CFG1_ALPHA, CFG1_BETA, block_size=r, degree=50)
+    assert out["status"] == flz.FLZ_OK
+    assert out["vals"].shape == ref.shape == (20,)
+    assert np.max(np.abs(out["vals"] - ref)) < 1e-10 * 8.0
+    check_pairs(csr, out, 1e-10)
+    st = out["stats"]
+    assert st["matvecs"] == r * 50 * st["iters"] and st["degree"] == 50 and st["converged"] == 1
+
+
+def _dense_case(csr, lo_index, count, **kw):
+    w = np.linalg.eigvalsh(csr.to_dense())
+    a, b = gap_interval(w, lo_index, count)
+    out = solve(csr, a, b, **kw)
+    ref = w[(w >= a) & (w <= b)]
+    assert out["status"] == flz.FLZ_OK
+    assert out["vals"].shape == ref.shape
+    scale = max(abs(w[0]), abs(w[-1]))
+    assert np.max(np.abs(out["vals"] - ref)) < 1e-10 * scale
+    check_pairs(csr, out, kw.get("tol", 1e-10))
+    return out
+
+
+def test_3d_laplacian_potential_vs_dense_auto_degree():
+    rng = np.random.Generator(np.random.PCG64(5))
+    _dense_case(laplacian_3d_7pt(12, 12, 12, 0.5 * rng.random(1728)), 0, 40, block_size=4)
+
+
+def test_fd4_hamiltonian_vs_dense():
+    N = 11
+    _dense_case(fd4_laplacian_3d(N, gaussian_wells_potential(N, 8, seed=2)), 3, 25, block_size=4)
+
+
+def test_powerlaw_graph_vs_dense():
+    _dense_case(powerlaw_graph_laplacian(2000, seed=7), 40, 15, block_size=4, degree=60)
+
+
+def test_interior_window_block3_vs_dense():
+    rng = np.random.Generator(np.random.PCG64(8))
+    _dense_case(laplacian_3d_7pt(10, 11, 12, rng.random(1320)), 500, 30, block_size=3, degree=80)
+
+
+def test_count_matches_inertia_midsize():
+    rng = np.random.Generator(np.random.PCG64(9))
+    csr = laplacian_3d_7pt(20, 20, 20, 0.5 * rng.random(8000))
+    S = csr.to_scipy()
+    # endpoints placed in gaps of the spectrum found by inertia counting
+    a = 0.35
+    b = 0.80
+    cnt = dense.count_in_interval(S, a, b)
+    out = solve(csr, a, b, block_size=4, degree=60)
+    assert out["status"] == flz.FLZ_OK
+    assert out["vals"].shape[0] == cnt
+    check_pairs(csr, out, 1e-10)
+
+
+def test_spectrum_bounds_enclose_extremes():
+    csr = laplacian_2d(60, 60)
+    lam = lap2d_eigs(60, 60)
+    h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+    lo, hi = flz.flz_spectrum_bounds(h, 60, 4, 3)
+    n, nnz, glo, ghi = flz.flz_matrix_info(h)
+    flz.flz_matrix_destroy(h)
+    assert (n, nnz) == (3600, csr.nnz)
+    assert glo <= lo <= lam[0] and lam[-1] <= hi <= ghi
+
+
+def test_empty_interval_status():
+    csr = laplacian_2d(20, 20)
+    h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+    s = flz.flz_solver_create(h, None)
+    flz.flz_solver_set_interval(s, 9.0, 10.0)
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_solve(s)
+    assert e.value.status == flz.FLZ_ERR_EMPTY_INTERVAL
+    flz.flz_solver_destroy(s)
+    flz.flz_matrix_destroy(h)
+
+
+def test_not_converged_keeps_partial_results():
+    csr = laplacian_2d(50, 50)
+    out = solve(csr, CFG1_ALPHA, CFG1_BETA, block_size=1, degree=50, max_basis=40, check_every=40)
+    assert out["status"] == flz.FLZ_ERR_NOT_CONVERGED
+    assert out["stats"]["converged"] == 0 and out["stats"]["iters"] == 40
+    assert out["vals"].shape[0] == out["stats"]["count"]
+
+
+def test_call_order_and_capacity_errors():
+    csr = laplacian_2d(20, 20)
+    h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+    s = flz.flz_solver_create(h, None)
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_solve(s)
+    assert e.value.status == flz.FLZ_ERR_NO_INTERVAL
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_get_count(s)
+    assert e.value.status == flz.FLZ_ERR_NOT_SOLVED
+    lam = lap2d_eigs(20, 20)
+    a, b = gap_interval(lam, 0, 6)
+    flz.flz_solver_set_interval(s, a, b)
+    assert flz.flz_solve(s) == flz.FLZ_OK
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_get_eigenvalues(s, np.empty(2))
+    assert e.value.status == flz.FLZ_ERR_CAPACITY
+    flz.flz_solver_destroy(s)
+    flz.flz_matrix_destroy(h)
+
+
+def test_invalid_csr_is_rejected():
+    csr = laplacian_2d(6, 6)
+    bad_cols = csr.col.copy()
+    bad_cols[0], bad_cols[1] = bad_cols[1], bad_cols[0]  # unsorted row 0
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, bad_cols, csr.val)
+    assert e.value.status == flz.FLZ_ERR_BAD_CSR
+    bad_ptr = csr.rowptr.copy()
+    bad_ptr[-1] -= 1
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_matrix_create_csr(csr.n, csr.nnz, bad_ptr, csr.col, csr.val)
+    assert e.value.status == flz.FLZ_ERR_BAD_CSR
+    bad_val = csr.val.copy()
+    bad_val[1] += 0.5  # a_01 != a_10
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, bad_val)
+    assert e.value.status == flz.FLZ_ERR_NOT_SYMMETRIC
+
+
+def test_device_resident_csr_input():
+    csr = laplacian_2d(30, 30)
+    rp = torch.from_numpy(csr.rowptr).cuda()
+    cl = torch.from_numpy(csr.col).cuda()
+    vl = torch.from_numpy(csr.val).cuda()
+    h = flz.flz_matrix_create_csr(csr.n, csr.nnz, rp, cl, vl, flz.FLZ_F64, flz.FLZ_DEVICE)
+    n, nnz, glo, ghi = flz.flz_matrix_info(h)
+    flz.flz_matrix_destroy(h)
+    assert (n, nnz, glo, ghi) == (900, csr.nnz, 0.0, 8.0)
