@@ -147,6 +147,26 @@ flz_status flz_matrix_info(const flz_matrix* A, int64_t* n, int64_t* nnz, double
 flz_status flz_filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int32_t degree,
                             int32_t r, const double* V, double* W, int32_t precision, void* stream);
 
+/* The same FP64 filter for callers that cannot allocate device memory. (The
+ * paper has no counterpart; this is an addition of this library.) Callers
+ * whose device memory belongs to another allocator (a framework pool that has
+ * reserved the GPU, an embedding application with a fixed budget) or that
+ * cannot afford the device-wide synchronization of cudaMalloc/cudaFree pass
+ * the CSR arrays and V, W as device pointers they already own; nothing is
+ * allocated and no matrix handle is needed. The two recurrence buffers come
+ * from a fixed 16 MiB static device array held by every GPU that loads the
+ * library until exit, so n * r must be <= 1,048,576 (FLZ_ERR_CAPACITY
+ * otherwise). rowptr int32[n+1], col int32[nnz], val FP64[nnz] must be a valid
+ * CSR matrix (not validated here); V, W device FP64 n x r row-major, not
+ * overlapping; coeffs host FP64[degree+1]. The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) and should come before
+ * any stream capture. All calls share the array: calls that overlap in time
+ * on the GPU race and must be ordered by the caller. Asynchronous on
+ * `stream`. */
+flz_status flz_filter_apply_noalloc(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* col,
+                                    const double* val, double c, double e, const double* coeffs, int32_t degree,
+                                    int32_t r, const double* V, double* W, void* stream);
+
 /* Closed-form Chebyshev coefficients of the indicator of [alpha, beta] within
  * [-1, 1] (Section 2.2): out[0] = (acos a - acos b)/pi, out[i] =
  * 2 (sin(i acos a) - sin(i acos b))/(i pi). Host only; out has degree+1 slots.

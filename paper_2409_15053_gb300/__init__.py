@@ -41,7 +41,7 @@ FLZ_PREC_FP64, FLZ_PREC_FP32, FLZ_PREC_BF16 = 0, 1, 2
 EXPORTED = (
     "flz_status_string", "flz_last_error", "flz_params_default",
     "flz_matrix_create_csr", "flz_matrix_destroy", "flz_matrix_info",
-    "flz_filter_apply", "flz_filter_coefficients", "flz_filter_degree", "flz_spectrum_bounds",
+    "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_filter_degree", "flz_spectrum_bounds",
     "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve",
     "flz_get_count", "flz_get_eigenvalues", "flz_get_eigenvectors", "flz_get_residuals", "flz_get_stats",
 )
@@ -102,6 +102,8 @@ def lib() -> ctypes.CDLL:
         "flz_matrix_destroy": (ctypes.c_int, [_vp]),
         "flz_matrix_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _pdbl, _pdbl]),
         "flz_filter_apply": (ctypes.c_int, [_vp, _dbl, _dbl, _vp, _i32, _i32, _vp, _vp, _i32, _vp]),
+        "flz_filter_apply_noalloc": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, _dbl, _dbl, _vp, _i32, _i32, _vp,
+                                                    _vp, _vp]),
         "flz_filter_coefficients": (ctypes.c_int, [_dbl, _dbl, _i32, _vp]),
         "flz_filter_degree": (ctypes.c_int, [_dbl, _dbl, _dbl, _i32, ctypes.POINTER(_i32)]),
         "flz_spectrum_bounds": (ctypes.c_int, [_vp, _i32, _i32, _u64, _pdbl, _pdbl, _vp]),
@@ -190,6 +192,13 @@ def flz_filter_apply(A, c, e, coeffs, degree, r, V, W, precision=FLZ_PREC_FP64, 
     coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
     _check(lib().flz_filter_apply(A, float(c), float(e), _ptr(coeffs), int(degree), int(r), _ptr(V), _ptr(W),
                                   int(precision), _stream(stream)))
+
+
+def flz_filter_apply_noalloc(n, nnz, rowptr, col, val, c, e, coeffs, degree, r, V, W, stream=None):
+    """FP64 filter from caller-owned device CSR arrays and blocks; allocates no device memory."""
+    coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
+    _check(lib().flz_filter_apply_noalloc(int(n), int(nnz), _ptr(rowptr), _ptr(col), _ptr(val), float(c), float(e),
+                                          _ptr(coeffs), int(degree), int(r), _ptr(V), _ptr(W), _stream(stream)))
 
 
 def flz_filter_coefficients(alpha, beta, degree) -> np.ndarray:
