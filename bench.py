@@ -199,6 +199,7 @@ def config_dict(csr, args):
                         "all eigenpairs in [alpha, beta] at the low end of the spectrum",
             "n": csr.n, "nnz": csr.nnz, "alpha": CONFIG2["alpha"], "beta": CONFIG2["beta"],
             "block_size": args.block_size, "degree": args.degree, "precision": args.precision, "tol": args.tol,
+            "check_every": args.check_every,
             "l2": "flushed (512 MiB write) before each timed step", "parallelism": "single GPU"}
 
 
@@ -212,9 +213,13 @@ def main():
     ap.add_argument("--block-size", type=int, default=4)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--check-every", type=int, default=CONFIG2["check_every"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="solve", choices=["solve", "filter"],
+                    help="solve: whole flz_solve per step (default); filter: only flz_filter_apply at the "
+                         "solver's shape, for the kernel roofline and profiling")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -238,6 +243,8 @@ def main():
 
     prec = {"fp64": flz.FLZ_PREC_FP64, "fp32": flz.FLZ_PREC_FP32, "bf16": flz.FLZ_PREC_BF16}[args.precision]
     csr = make_matrix()
+    if args.mode == "filter":
+        return filter_mode(flz, torch, csr, prec, args)
     alpha, beta = CONFIG2["alpha"], CONFIG2["beta"]
     # Replicas: every rank solves the same workload on its own GPU (the
     # solver does not shard; no data-path collective).
@@ -246,6 +253,7 @@ def main():
     p.block_size = args.block_size
     p.degree = args.degree
     p.tol = args.tol
+    p.check_every = args.check_every
     p.precision = prec
     p.seed = 1 + rank
     s = flz.flz_solver_create(h, p)
@@ -340,6 +348,47 @@ def main():
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def filter_mode(flz, torch, csr, prec, args):
+    """Times flz_filter_apply alone (p_m(Ahat) on an n x r block) with CUDA events per call."""
+    r, m = args.block_size, args.degree
+    h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+    lmin, lmax = 0.0, 12.5
+    c, e = 0.5 * (lmin + lmax), 0.5 * (lmax - lmin)
+    coeffs = flz.flz_filter_coefficients(-1.0, (CONFIG2["beta"] - c) / e, m)
+    V = torch.from_numpy(random_normal_block(csr.n, r, 5)).cuda()
+    W = torch.empty_like(V)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        flz.flz_filter_apply(h, c, e, coeffs, m, r, V, W, prec, stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flz.flz_filter_apply(h, c, e, coeffs, m, r, V, W, prec, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    flz.flz_matrix_destroy(h)
+    launches = m + (0 if prec == flz.FLZ_PREC_FP64 else 1)
+    ms = float(np.mean(times)) / m
+    sizes = {flz.FLZ_PREC_FP64: (8, 8, 8), flz.FLZ_PREC_FP32: (4, 4, 4), flz.FLZ_PREC_BF16: (2, 2, 4)}[prec]
+    nbytes = filter_bytes_per_launch(csr.n, csr.nnz, r, *sizes)
+    hbm, src = peaks()
+    print(json.dumps({"mode": "filter", "precision": args.precision, "n": csr.n, "nnz": csr.nnz, "r": r,
+                      "degree": m, "launches_per_apply": launches, "ms_per_apply": float(np.mean(times)),
+                      "ms_per_degree": ms, "algorithmic_bytes_per_degree": nbytes,
+                      "gbs": nbytes / (ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm, "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm,
+                      "fp64_tflops": filter_flops_per_launch(csr.n, csr.nnz, r) / (ms * 1e-3) / 1e12,
+                      "clocks": clocks}))
 
 
 def e2e_leg(flz, torch, csr, p, alpha, beta, stream, args):

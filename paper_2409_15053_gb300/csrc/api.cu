@@ -54,25 +54,55 @@ void bounds_entry(flz_matrix* A, int steps, int r, uint64_t seed, cudaStream_t s
 
 }  // namespace flz
 
-#define FLZ_API_BEGIN         \
-  ::flz::clear_last_error();  \
-  try {
-#define FLZ_API_END                                     \
-  }                                                     \
-  catch (const ::flz::Failure& f) {                     \
-    return f.status;                                    \
-  }                                                     \
-  catch (const std::bad_alloc&) {                       \
-    ::flz::set_last_error("host allocation failed");    \
-    return FLZ_ERR_OUT_OF_MEMORY;                       \
-  }                                                     \
-  catch (...) {                                         \
-    ::flz::set_last_error("unexpected internal error"); \
-    return FLZ_ERR_CUDA;                                \
-  }                                                     \
-  return FLZ_OK;
 
 using flz::fail;
+
+namespace {
+
+// The filter folds the shift -cI into the stored diagonal, so every row must
+// store a_ii; rows that do not get an explicit zero (same matrix).
+void insert_zero_diagonals(flz_matrix* A) {
+  const int64_t n = A->n, nnz = A->nnz;
+  std::vector<int32_t> rp(n + 1), cl(nnz), rp2(n + 1), cl2;
+  std::vector<double> vl(nnz), vl2;
+  FLZ_CUDA(cudaMemcpy(rp.data(), A->rowptr.p, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
+  if (nnz > 0) {
+    FLZ_CUDA(cudaMemcpy(cl.data(), A->col.p, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+    FLZ_CUDA(cudaMemcpy(vl.data(), A->val.p, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
+  }
+  cl2.reserve(nnz + n);
+  vl2.reserve(nnz + n);
+  rp2[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    bool done = false;
+    for (int32_t j = rp[i]; j < rp[i + 1]; ++j) {
+      if (!done && cl[j] >= i) {
+        if (cl[j] != i) {
+          cl2.push_back((int32_t)i);
+          vl2.push_back(0.0);
+        }
+        done = true;
+      }
+      cl2.push_back(cl[j]);
+      vl2.push_back(vl[j]);
+    }
+    if (!done) {
+      cl2.push_back((int32_t)i);
+      vl2.push_back(0.0);
+    }
+    if ((int64_t)cl2.size() > 2147483647LL) fail(FLZ_ERR_INVALID_ARG, "nnz with diagonals exceeds int32");
+    rp2[i + 1] = (int32_t)cl2.size();
+  }
+  A->nnz = (int64_t)cl2.size();
+  A->col.reserve((size_t)A->nnz);
+  A->val.reserve((size_t)A->nnz);
+  FLZ_CUDA(cudaMemcpy(A->rowptr.p, rp2.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
+  FLZ_CUDA(cudaMemcpy(A->col.p, cl2.data(), sizeof(int32_t) * A->nnz, cudaMemcpyHostToDevice));
+  FLZ_CUDA(cudaMemcpy(A->val.p, vl2.data(), sizeof(double) * A->nnz, cudaMemcpyHostToDevice));
+  if (flz::find_diagonals(A) != 0) fail(FLZ_ERR_BAD_CSR, "diagonal insertion failed");
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -172,7 +202,10 @@ flz_status flz_matrix_create_csr(int64_t n, int64_t nnz, const int32_t* rowptr, 
     const flz_status vs = flz::validate_csr(A, check_symmetry);
     if (vs == FLZ_ERR_BAD_CSR) fail(vs, "CSR structure invalid (rowptr, column range or column order)");
     if (vs == FLZ_ERR_NOT_SYMMETRIC) fail(vs, "matrix is not symmetric");
+    A->nnz_user = nnz;
+    if (flz::find_diagonals(A) > 0) insert_zero_diagonals(A);
     flz::gershgorin(A, &A->glo, &A->ghi, &A->max_row_nnz);
+    A->max_cta_nnz = flz::max_block_nnz(A, 256);
   } catch (...) {
     delete A;
     throw;
@@ -191,7 +224,7 @@ flz_status flz_matrix_info(const flz_matrix* A, int64_t* n, int64_t* nnz, double
   FLZ_API_BEGIN
   if (!A) fail(FLZ_ERR_INVALID_ARG, "matrix is NULL");
   if (n) *n = A->n;
-  if (nnz) *nnz = A->nnz;
+  if (nnz) *nnz = A->nnz_user;
   if (glo) *glo = A->glo;
   if (ghi) *ghi = A->ghi;
   FLZ_API_END

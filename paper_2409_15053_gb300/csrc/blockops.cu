@@ -277,6 +277,44 @@ __global__ void validate_kernel(long long n, long long nnz, const int* __restric
   }
 }
 
+// diag_pos[i] = index of column i within row i (binary search; columns are sorted), -1 if absent.
+__global__ void find_diagonal_kernel(long long n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                     int* __restrict__ diag_pos, unsigned long long* __restrict__ missing) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    int lo = rowptr[i], hi = rowptr[i + 1] - 1, pos = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const int cm = col[mid];
+      if (cm == i) {
+        pos = mid;
+        break;
+      }
+      if (cm < i) lo = mid + 1;
+      else hi = mid - 1;
+    }
+    diag_pos[i] = pos;
+    if (pos < 0) atomicAdd(missing, 1ull);
+  }
+}
+
+template <class S>
+__device__ __forceinline__ S round_to(double x);
+template <>
+__device__ __forceinline__ double round_to<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float round_to<float>(double x) { return (float)x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 round_to<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
+
+template <class S>
+__global__ void scale_values_kernel(long long n, const int* __restrict__ rowptr, const int* __restrict__ diag_pos,
+                                    const double* __restrict__ val, double s, double shift, S* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int d = diag_pos[i];
+    for (int j = rowptr[i], je = rowptr[i + 1]; j < je; ++j) out[j] = round_to<S>(s * (val[j] - (j == d ? shift : 0.0)));
+  }
+}
+
 inline unsigned gs_blocks(long long count) {
   return (unsigned)std::max<long long>(1, std::min<long long>((count + 255) / 256, 152 * 16));
 }
@@ -412,6 +450,46 @@ void gershgorin(const flz_matrix* A, double* glo, double* ghi, int32_t* max_row_
   *ghi = *std::max_element(hhi.begin(), hhi.end());
   *max_row_nnz = *std::max_element(hlen.begin(), hlen.end());
 }
+
+__global__ void block_nnz_kernel(long long n, int rows, const int* __restrict__ rowptr, int* __restrict__ best) {
+  const long long nblk = (n + rows - 1) / rows;
+  for (long long bk = (long long)blockIdx.x * blockDim.x + threadIdx.x; bk < nblk; bk += (long long)gridDim.x * blockDim.x) {
+    const long long r0 = bk * rows, r1 = min(n, r0 + rows);
+    atomicMax(best, rowptr[r1] - rowptr[r0]);
+  }
+}
+
+int32_t max_block_nnz(const flz_matrix* A, int rows) {
+  DevBuf<int> best;
+  best.reserve(1);
+  FLZ_CUDA(cudaMemset(best.p, 0, sizeof(int)));
+  block_nnz_kernel<<<gs_blocks((A->n + rows - 1) / rows), 256>>>(A->n, rows, A->rowptr.p, best.p);
+  FLZ_LAUNCH_CHECK();
+  int h = 0;
+  FLZ_CUDA(cudaMemcpy(&h, best.p, sizeof(int), cudaMemcpyDeviceToHost));
+  return h;
+}
+
+int64_t find_diagonals(flz_matrix* A) {
+  A->diag_pos.reserve((size_t)A->n);
+  DevBuf<unsigned long long> missing;
+  missing.reserve(1);
+  FLZ_CUDA(cudaMemset(missing.p, 0, sizeof(unsigned long long)));
+  find_diagonal_kernel<<<gs_blocks(A->n), 256>>>(A->n, A->rowptr.p, A->col.p, A->diag_pos.p, missing.p);
+  FLZ_LAUNCH_CHECK();
+  unsigned long long h = 0;
+  FLZ_CUDA(cudaMemcpy(&h, missing.p, sizeof(h), cudaMemcpyDeviceToHost));
+  return (int64_t)h;
+}
+
+template <class S>
+void scale_values(const flz_matrix* A, double c, double e, S* out, cudaStream_t st) {
+  scale_values_kernel<S><<<gs_blocks(A->n), 256, 0, st>>>(A->n, A->rowptr.p, A->diag_pos.p, A->val.p, 2.0 / e, c, out);
+  FLZ_LAUNCH_CHECK();
+}
+template void scale_values<double>(const flz_matrix*, double, double, double*, cudaStream_t);
+template void scale_values<float>(const flz_matrix*, double, double, float*, cudaStream_t);
+template void scale_values<__nv_bfloat16>(const flz_matrix*, double, double, __nv_bfloat16*, cudaStream_t);
 
 flz_status validate_csr(const flz_matrix* A, int check_symmetry) {
   DevBuf<int> flags;

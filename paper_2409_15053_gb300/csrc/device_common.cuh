@@ -1,0 +1,202 @@
+// Device helpers shared by the filter kernels: the arithmetic type of each
+// storage type, conversions, and R-wide row loads/stores (one thread owns a
+// whole row of an n x R row-major block).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
+namespace flz {
+namespace dev {
+
+template <class S>
+struct Arith {
+  using type = float;
+};
+template <>
+struct Arith<double> {
+  using type = double;
+};
+
+__device__ __forceinline__ double to_arith(double x) { return x; }
+__device__ __forceinline__ float to_arith(float x) { return x; }
+__device__ __forceinline__ float to_arith(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <class S>
+__device__ __forceinline__ S from_arith(typename Arith<S>::type x);
+template <>
+__device__ __forceinline__ double from_arith<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float from_arith<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_arith<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+template <class O, class A>
+__device__ __forceinline__ O store_as(A x) { return static_cast<O>(x); }
+
+// ---- R-wide row I/O: one thread owns a whole row of an n x R block ----------
+template <class S, int R>
+struct RowIO;
+
+template <int R>
+struct RowIO<double, R> {
+  static __device__ __forceinline__ void load(const double* p, double (&v)[R]) {
+    if constexpr (R == 1) {
+      v[0] = p[0];
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; i += 2) {
+        const double2 t = *reinterpret_cast<const double2*>(p + i);
+        v[i] = t.x;
+        v[i + 1] = t.y;
+      }
+    }
+  }
+  static __device__ __forceinline__ void store(double* p, const double (&v)[R]) {
+    if constexpr (R == 1) {
+      p[0] = v[0];
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; i += 2) *reinterpret_cast<double2*>(p + i) = make_double2(v[i], v[i + 1]);
+    }
+  }
+};
+
+template <int R>
+struct RowIO<float, R> {
+  static __device__ __forceinline__ void load(const float* p, float (&v)[R]) {
+    if constexpr (R == 1) {
+      v[0] = p[0];
+    } else if constexpr (R == 2) {
+      const float2 t = *reinterpret_cast<const float2*>(p);
+      v[0] = t.x;
+      v[1] = t.y;
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; i += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(p + i);
+        v[i] = t.x;
+        v[i + 1] = t.y;
+        v[i + 2] = t.z;
+        v[i + 3] = t.w;
+      }
+    }
+  }
+  static __device__ __forceinline__ void store(float* p, const float (&v)[R]) {
+    if constexpr (R == 1) {
+      p[0] = v[0];
+    } else if constexpr (R == 2) {
+      *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; i += 4) *reinterpret_cast<float4*>(p + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    }
+  }
+};
+
+template <int R>
+struct RowIO<__nv_bfloat16, R> {
+  // loads/stores R bf16 values widened to / narrowed from float
+  static __device__ __forceinline__ void load(const __nv_bfloat16* p, float (&v)[R]) {
+    if constexpr (R == 1) {
+      v[0] = __bfloat162float(p[0]);
+    } else if constexpr (R == 2) {
+      const float2 t = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+      v[0] = t.x;
+      v[1] = t.y;
+    } else if constexpr (R == 4) {
+      const uint2 u = *reinterpret_cast<const uint2*>(p);
+      const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+      const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+      v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; i += 8) {
+        const uint4 u = *reinterpret_cast<const uint4*>(p + i);
+        const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[q]));
+          v[i + 2 * q] = f.x;
+          v[i + 2 * q + 1] = f.y;
+        }
+      }
+    }
+  }
+  // rounds to bf16, stores, and returns the rounded values in v
+  static __device__ __forceinline__ void store(__nv_bfloat16* p, float (&v)[R]) {
+    __nv_bfloat162 h[(R + 1) / 2];
+#pragma unroll
+    for (int i = 0; i < R; i += 2) {
+      h[i / 2] = __floats2bfloat162_rn(v[i], i + 1 < R ? v[i + 1] : 0.f);
+      const float2 f = __bfloat1622float2(h[i / 2]);
+      v[i] = f.x;
+      if (i + 1 < R) v[i + 1] = f.y;
+    }
+    if constexpr (R == 1) {
+      p[0] = h[0].x;
+    } else if constexpr (R == 2) {
+      *reinterpret_cast<__nv_bfloat162*>(p) = h[0];
+    } else if constexpr (R == 4) {
+      uint2 u;
+      u.x = *reinterpret_cast<unsigned*>(&h[0]);
+      u.y = *reinterpret_cast<unsigned*>(&h[1]);
+      *reinterpret_cast<uint2*>(p) = u;
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; i += 8) {
+        uint4 u;
+        u.x = *reinterpret_cast<unsigned*>(&h[i / 2]);
+        u.y = *reinterpret_cast<unsigned*>(&h[i / 2 + 1]);
+        u.z = *reinterpret_cast<unsigned*>(&h[i / 2 + 2]);
+        u.w = *reinterpret_cast<unsigned*>(&h[i / 2 + 3]);
+        *reinterpret_cast<uint4*>(p + i) = u;
+      }
+    }
+  }
+};
+
+template <class S, int R>
+__device__ __forceinline__ void store_row_rounded(S* p, typename Arith<S>::type (&v)[R]) {
+  if constexpr (std::is_same<S, __nv_bfloat16>::value) {
+    RowIO<S, R>::store(p, v);
+  } else {
+    RowIO<S, R>::store(p, v);  // FP64 / FP32 storage is the arithmetic type: no rounding
+  }
+}
+
+template <class S, int R>
+__device__ __forceinline__ void load_row(const S* p, typename Arith<S>::type (&v)[R]) {
+  RowIO<S, R>::load(p, v);
+}
+
+// Running-sum output row: FP64 W (the last launch) or the working sum type.
+template <int R, class A>
+__device__ __forceinline__ void store_acc(double* p, const A (&v)[R]) {
+  double d[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) d[t] = (double)v[t];
+  RowIO<double, R>::store(p, d);
+}
+template <int R>
+__device__ __forceinline__ void store_acc(float* p, const float (&v)[R]) {
+  float f[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) f[t] = v[t];
+  RowIO<float, R>::store(p, f);
+}
+template <int R, class A>
+__device__ __forceinline__ void load_acc(const double* p, A (&v)[R]) {
+  double d[R];
+  RowIO<double, R>::load(p, d);
+#pragma unroll
+  for (int t = 0; t < R; ++t) v[t] = (A)d[t];
+}
+template <int R>
+__device__ __forceinline__ void load_acc(const float* p, float (&v)[R]) {
+  RowIO<float, R>::load(p, v);
+}
+
+}  // namespace dev
+}  // namespace flz

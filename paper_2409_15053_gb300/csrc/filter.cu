@@ -16,50 +16,32 @@
 // is r contiguous elements (one 32-byte sector for r = 4 in FP64). The CSR
 // index/value loads of a row are shared by its r lanes (same address, one
 // transaction). Y_{k-1} is overwritten in place by Y_{k+1}.
+#include "device_common.cuh"
 #include "flz_internal.h"
 
 namespace flz {
 
+using namespace dev;
+
 namespace {
-
-template <class S>
-struct Arith {
-  using type = float;
-};
-template <>
-struct Arith<double> {
-  using type = double;
-};
-
-__device__ __forceinline__ double to_arith(double x) { return x; }
-__device__ __forceinline__ float to_arith(float x) { return x; }
-__device__ __forceinline__ float to_arith(__nv_bfloat16 x) { return __bfloat162float(x); }
-
-template <class S>
-__device__ __forceinline__ S from_arith(typename Arith<S>::type x);
-template <>
-__device__ __forceinline__ double from_arith<double>(double x) { return x; }
-template <>
-__device__ __forceinline__ float from_arith<float>(float x) { return x; }
-template <>
-__device__ __forceinline__ __nv_bfloat16 from_arith<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
-
-template <class O, class A>
-__device__ __forceinline__ O store_as(A x) { return static_cast<O>(x); }
 
 constexpr int kThreads = 256;
 
 // One fused Chebyshev degree step over the whole matrix.
-//   MS: matrix value storage, VS: recurrence vector storage,
-//   AccS: running-sum input storage, OutS: running-sum output storage.
+//   MS: storage of the scaled values 2 Ahat = (2/e)(A - cI) (the shift is
+//       folded into the stored diagonal, the 2/e into every value), VS:
+//       recurrence vector storage, AccS / OutS: running-sum input / output.
+//   FIRST:  Y_1 = Ahat V = (1/2)(2 Ahat) V,      acc  = b_0 V + b_1 Y_1
+//   else:   Y_{k+1} = (2 Ahat) Y_k - Y_{k-1},    acc += b_{k+1} Y_{k+1}
+// The row sum starts from -Y_{k-1}, so a degree costs one multiply-add per
+// stored entry and column plus one per element for the running sum.
 // ynext may alias yprev; acc_out may alias acc_in (each element is read and
 // written by the same thread).
 template <class MS, class VS, class AccS, class OutS, bool FIRST>
 __global__ void __launch_bounds__(kThreads) cheb_step_kernel(
     int n, int r, int rows_per_warp, const int* __restrict__ rowptr, const int* __restrict__ col,
-    const MS* __restrict__ val, const VS* __restrict__ ycur, const VS* yprev, VS* ynext, const AccS* acc_in,
-    OutS* acc_out, typename Arith<VS>::type alpha, typename Arith<VS>::type beta,
-    typename Arith<VS>::type b_cur, typename Arith<VS>::type b_next) {
+    const MS* __restrict__ sval, const VS* __restrict__ ycur, const VS* yprev, VS* ynext, const AccS* acc_in,
+    OutS* acc_out, typename Arith<VS>::type b_cur, typename Arith<VS>::type b_next) {
   using A = typename Arith<VS>::type;
   const int lane = threadIdx.x & 31;
   const int sub = lane / r;
@@ -67,35 +49,99 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(
   const long long warp = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
   const long long row = warp * rows_per_warp + sub;
   if (sub >= rows_per_warp || row >= n) return;
+  const size_t idx = (size_t)row * r + c;
   int j = __ldg(rowptr + row);
   const int jend = __ldg(rowptr + row + 1);
-  A s0 = A(0), s1 = A(0);
+  A s = FIRST ? A(0) : -to_arith(yprev[idx]);
   for (; j + 4 <= jend; j += 4) {
     const int c0 = __ldg(col + j), c1 = __ldg(col + j + 1), c2 = __ldg(col + j + 2), c3 = __ldg(col + j + 3);
-    const A a0 = to_arith(val[j]), a1 = to_arith(val[j + 1]), a2 = to_arith(val[j + 2]), a3 = to_arith(val[j + 3]);
+    const A a0 = to_arith(sval[j]), a1 = to_arith(sval[j + 1]), a2 = to_arith(sval[j + 2]), a3 = to_arith(sval[j + 3]);
     const A y0 = to_arith(ycur[(size_t)c0 * r + c]);
     const A y1 = to_arith(ycur[(size_t)c1 * r + c]);
     const A y2 = to_arith(ycur[(size_t)c2 * r + c]);
     const A y3 = to_arith(ycur[(size_t)c3 * r + c]);
-    s0 = fma(a0, y0, s0);
-    s1 = fma(a1, y1, s1);
-    s0 = fma(a2, y2, s0);
-    s1 = fma(a3, y3, s1);
+    s = fma(a0, y0, s);
+    s = fma(a1, y1, s);
+    s = fma(a2, y2, s);
+    s = fma(a3, y3, s);
   }
-  for (; j < jend; ++j) {
-    const int cj = __ldg(col + j);
-    s0 = fma(to_arith(val[j]), to_arith(ycur[(size_t)cj * r + c]), s0);
-  }
-  const size_t idx = (size_t)row * r + c;
-  const A yc = to_arith(ycur[idx]);
-  A yn = fma(alpha, s0 + s1, beta * yc);
-  if (!FIRST) yn -= to_arith(yprev[idx]);
+  for (; j < jend; ++j) s = fma(to_arith(sval[j]), to_arith(ycur[(size_t)__ldg(col + j) * r + c]), s);
+  const A yn = FIRST ? A(0.5) * s : s;
   const VS yn_s = from_arith<VS>(yn);
   ynext[idx] = yn_s;
   const A yq = to_arith(yn_s);
-  A acc = FIRST ? b_cur * yc : A(to_arith(acc_in[idx]));
+  A acc = FIRST ? b_cur * to_arith(ycur[idx]) : A(to_arith(acc_in[idx]));
   acc = fma(b_next, yq, acc);
   acc_out[idx] = store_as<OutS>(acc);
+}
+
+constexpr int kRows = 256;  // rows per CTA in the row-per-thread kernel
+
+// The fused degree step with one thread per row (all R columns) for R in
+// {1, 2, 4, 8, 16}. The CTA's contiguous range of CSR indices and scaled
+// values is first staged in shared memory with coalesced loads (when it fits
+// `cap` entries; otherwise each thread reads its row from global memory), so
+// the per-row reads that follow do not scatter across HBM sectors. A gathered
+// row Y[col] is one R-wide vector load. Same arithmetic as cheb_step_kernel.
+template <int R, class MS, class VS, class AccS, class OutS, bool FIRST>
+__global__ void __launch_bounds__(kRows) cheb_rows_kernel(
+    int n, int cap, const int* __restrict__ rowptr, const int* __restrict__ col, const MS* __restrict__ sval,
+    const VS* __restrict__ ycur, const VS* yprev, VS* ynext, const AccS* acc_in, OutS* acc_out,
+    typename Arith<VS>::type b_cur, typename Arith<VS>::type b_next) {
+  using A = typename Arith<VS>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  MS* s_val = reinterpret_cast<MS*>(smem);
+  int* s_col = reinterpret_cast<int*>(smem + (size_t)cap * sizeof(MS));
+  const int row0 = blockIdx.x * kRows;
+  const int rend = min(n, row0 + kRows);
+  const int row = row0 + (int)threadIdx.x;
+  const int j0 = __ldg(rowptr + row0);
+  const int j1 = __ldg(rowptr + rend);
+  const bool staged = (j1 - j0) <= cap;  // uniform over the CTA
+  if (staged) {
+    for (int e = threadIdx.x; e < j1 - j0; e += kRows) {
+      s_col[e] = __ldg(col + j0 + e);
+      s_val[e] = sval[j0 + e];
+    }
+    __syncthreads();
+  }
+  if (row >= n) return;
+  const int jb = __ldg(rowptr + row);
+  const int je = __ldg(rowptr + row + 1);
+  A s[R];
+  if (FIRST) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) s[t] = A(0);
+  } else {
+    load_row<VS, R>(yprev + (size_t)row * R, s);
+#pragma unroll
+    for (int t = 0; t < R; ++t) s[t] = -s[t];
+  }
+  for (int j = jb; j < je; ++j) {
+    const int cj = staged ? s_col[j - j0] : __ldg(col + j);
+    const A a = staged ? to_arith(s_val[j - j0]) : to_arith(sval[j]);
+    A y[R];
+    load_row<VS, R>(ycur + (size_t)cj * R, y);
+#pragma unroll
+    for (int t = 0; t < R; ++t) s[t] = fma(a, y[t], s[t]);
+  }
+  if (FIRST) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) s[t] *= A(0.5);
+  }
+  store_row_rounded<VS, R>(ynext + (size_t)row * R, s);  // s now holds the stored (rounded) Y_next
+  A acc[R];
+  if (FIRST) {
+    A v0[R];
+    load_row<VS, R>(ycur + (size_t)row * R, v0);
+#pragma unroll
+    for (int t = 0; t < R; ++t) acc[t] = b_cur * v0[t];
+  } else {
+    load_acc<R>(acc_in + (size_t)row * R, acc);
+  }
+#pragma unroll
+  for (int t = 0; t < R; ++t) acc[t] = fma(b_next, s[t], acc[t]);
+  store_acc<R>(acc_out + (size_t)row * R, acc);
 }
 
 template <class S>
@@ -121,23 +167,21 @@ inline unsigned grid_stride_blocks(size_t count) {
 }
 
 template <class MS, class VS, class AccT>
-void run_recurrence(const flz_matrix* A, const MS* val, double c, double e, const double* b, int m, int r,
-                    const VS* v, VS* ya, VS* yb, AccT* acc, double* W, cudaStream_t st) {
+void run_lanes(const flz_matrix* A, const MS* val, const double* b, int m, int r, const VS* v, VS* ya, VS* yb,
+               AccT* acc, double* W, cudaStream_t st) {
   using Ar = typename Arith<VS>::type;
   const int n = (int)A->n;
   const int rpw = 32 / r;
   const unsigned grid = grid_for_rows(n, r);
-  const Ar a0 = Ar(1.0 / e), be0 = Ar(-c / e);
-  const Ar a1 = Ar(2.0 / e), be1 = Ar(-2.0 * c / e);
   // step 0: Y_1 = Ahat V, acc = b0 V + b1 Y_1
   if (m == 1) {
     cheb_step_kernel<MS, VS, AccT, double, true><<<grid, kThreads, 0, st>>>(
-        n, r, rpw, A->rowptr.p, A->col.p, val, v, nullptr, ya, nullptr, W, a0, be0, Ar(b[0]), Ar(b[1]));
+        n, r, rpw, A->rowptr.p, A->col.p, val, v, nullptr, ya, nullptr, W, Ar(b[0]), Ar(b[1]));
     FLZ_LAUNCH_CHECK();
     return;
   }
   cheb_step_kernel<MS, VS, AccT, AccT, true><<<grid, kThreads, 0, st>>>(
-      n, r, rpw, A->rowptr.p, A->col.p, val, v, nullptr, ya, nullptr, acc, a0, be0, Ar(b[0]), Ar(b[1]));
+      n, r, rpw, A->rowptr.p, A->col.p, val, v, nullptr, ya, nullptr, acc, Ar(b[0]), Ar(b[1]));
   FLZ_LAUNCH_CHECK();
   // Buffers: V is never written. Y_1 -> ya, Y_2 -> yb, then Y_{k+1}
   // overwrites Y_{k-1} in place.
@@ -147,14 +191,76 @@ void run_recurrence(const flz_matrix* A, const MS* val, double c, double e, cons
     VS* next = (k == 1) ? yb : const_cast<VS*>(prev);
     if (k + 1 == m) {
       cheb_step_kernel<MS, VS, AccT, double, false><<<grid, kThreads, 0, st>>>(
-          n, r, rpw, A->rowptr.p, A->col.p, val, cur, prev, next, acc, W, a1, be1, Ar(0), Ar(b[k + 1]));
+          n, r, rpw, A->rowptr.p, A->col.p, val, cur, prev, next, acc, W, Ar(0), Ar(b[k + 1]));
     } else {
       cheb_step_kernel<MS, VS, AccT, AccT, false><<<grid, kThreads, 0, st>>>(
-          n, r, rpw, A->rowptr.p, A->col.p, val, cur, prev, next, acc, acc, a1, be1, Ar(0), Ar(b[k + 1]));
+          n, r, rpw, A->rowptr.p, A->col.p, val, cur, prev, next, acc, acc, Ar(0), Ar(b[k + 1]));
     }
     FLZ_LAUNCH_CHECK();
     prev = cur;
     cur = next;
+  }
+}
+
+template <int R, class MS, class VS, class AccT>
+void run_rows(const flz_matrix* A, const MS* val, const double* b, int m, const VS* v, VS* ya, VS* yb, AccT* acc,
+              double* W, cudaStream_t st) {
+  using Ar = typename Arith<VS>::type;
+  const int n = (int)A->n;
+  const int cap = std::min<int>(A->max_cta_nnz, 4096);
+  const size_t smem = (size_t)cap * (sizeof(MS) + sizeof(int));
+  const unsigned grid = (unsigned)((n + kRows - 1) / kRows);
+  const int* rp = A->rowptr.p;
+  const int* cl = A->col.p;
+  if (m == 1) {
+    cheb_rows_kernel<R, MS, VS, AccT, double, true><<<grid, kRows, smem, st>>>(
+        n, cap, rp, cl, val, v, nullptr, ya, nullptr, W, Ar(b[0]), Ar(b[1]));
+    FLZ_LAUNCH_CHECK();
+    return;
+  }
+  cheb_rows_kernel<R, MS, VS, AccT, AccT, true><<<grid, kRows, smem, st>>>(
+      n, cap, rp, cl, val, v, nullptr, ya, nullptr, acc, Ar(b[0]), Ar(b[1]));
+  FLZ_LAUNCH_CHECK();
+  const VS* prev = v;
+  const VS* cur = ya;
+  for (int k = 1; k < m; ++k) {
+    VS* next = (k == 1) ? yb : const_cast<VS*>(prev);
+    if (k + 1 == m) {
+      cheb_rows_kernel<R, MS, VS, AccT, double, false><<<grid, kRows, smem, st>>>(
+          n, cap, rp, cl, val, cur, prev, next, acc, W, Ar(0), Ar(b[k + 1]));
+    } else {
+      cheb_rows_kernel<R, MS, VS, AccT, AccT, false><<<grid, kRows, smem, st>>>(
+          n, cap, rp, cl, val, cur, prev, next, acc, acc, Ar(0), Ar(b[k + 1]));
+    }
+    FLZ_LAUNCH_CHECK();
+    prev = cur;
+    cur = next;
+  }
+}
+
+inline bool aligned_to(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Row-per-thread kernel for r in {1, 2, 4, 8, 16} when every block is aligned
+// for R-wide vector access; the lane-per-column kernel otherwise.
+template <class MS, class VS, class AccT>
+void run_recurrence(const flz_matrix* A, const MS* val, const double* b, int m, int r, const VS* v, VS* ya,
+                    VS* yb, AccT* acc, double* W, cudaStream_t st) {
+  const bool pow2 = r == 1 || r == 2 || r == 4 || r == 8 || r == 16;
+  const size_t av = std::min<size_t>(16, r * sizeof(VS));
+  const size_t aa = std::min<size_t>(16, r * sizeof(AccT));
+  const size_t aw = std::min<size_t>(16, r * sizeof(double));
+  const bool ok = pow2 && A->max_cta_nnz > 0 && aligned_to(v, av) && aligned_to(ya, av) && aligned_to(yb, av) &&
+                  aligned_to(acc, aa) && aligned_to(W, aw);
+  if (!ok) {
+    run_lanes<MS, VS, AccT>(A, val, b, m, r, v, ya, yb, acc, W, st);
+    return;
+  }
+  switch (r) {
+    case 1: run_rows<1, MS, VS, AccT>(A, val, b, m, v, ya, yb, acc, W, st); break;
+    case 2: run_rows<2, MS, VS, AccT>(A, val, b, m, v, ya, yb, acc, W, st); break;
+    case 4: run_rows<4, MS, VS, AccT>(A, val, b, m, v, ya, yb, acc, W, st); break;
+    case 8: run_rows<8, MS, VS, AccT>(A, val, b, m, v, ya, yb, acc, W, st); break;
+    default: run_rows<16, MS, VS, AccT>(A, val, b, m, v, ya, yb, acc, W, st); break;
   }
 }
 
@@ -183,6 +289,23 @@ int filter_launch_count(int m, int precision) {
   return m + (precision == FLZ_PREC_FP64 ? 0 : 1);
 }
 
+namespace {
+
+// 2 Ahat in storage precision `prec`, rebuilt only when (c, e) change.
+template <class S>
+const S* scaled(flz_matrix* A, DevBuf<S>& buf, int prec, double c, double e, cudaStream_t st) {
+  if (!(A->sc_ok[prec] && A->sc_c[prec] == c && A->sc_e[prec] == e && buf.p)) {
+    buf.reserve((size_t)A->nnz);
+    scale_values<S>(A, c, e, buf.p, st);
+    A->sc_c[prec] = c;
+    A->sc_e[prec] = e;
+    A->sc_ok[prec] = true;
+  }
+  return buf.p;
+}
+
+}  // namespace
+
 void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m, int r, const double* V,
                   double* W, int precision, cudaStream_t st) {
   const size_t nr = (size_t)A->n * r;
@@ -192,17 +315,14 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
     return;
   }
   if (precision == FLZ_PREC_FP64) {
+    const double* sv = scaled<double>(A, A->sval64, 0, c, e, st);
     A->ws64.reserve(2 * nr);
     double* ya = A->ws64.p;
     double* yb = A->ws64.p + nr;
-    // acc lives in W directly (FP64 output)
-    run_recurrence<double, double, double>(A, A->val.p, c, e, coeffs, m, r, V, ya, yb, W, W, st);
+    // the running sum lives in W directly (FP64 output)
+    run_recurrence<double, double, double>(A, sv, coeffs, m, r, V, ya, yb, W, W, st);
   } else if (precision == FLZ_PREC_FP32) {
-    if (!A->val32.p) {
-      A->val32.reserve((size_t)A->nnz);
-      convert_kernel<float><<<grid_stride_blocks(A->nnz), 256, 0, st>>>(A->val.p, A->val32.p, (size_t)A->nnz);
-      FLZ_LAUNCH_CHECK();
-    }
+    const float* sv = scaled<float>(A, A->sval32, 1, c, e, st);
     A->ws32.reserve(4 * nr);
     float* vs = A->ws32.p;
     float* ya = vs + nr;
@@ -210,14 +330,9 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
     float* acc = yb + nr;
     convert_kernel<float><<<grid_stride_blocks(nr), 256, 0, st>>>(V, vs, nr);
     FLZ_LAUNCH_CHECK();
-    run_recurrence<float, float, float>(A, A->val32.p, c, e, coeffs, m, r, vs, ya, yb, acc, W, st);
+    run_recurrence<float, float, float>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
   } else if (precision == FLZ_PREC_BF16) {
-    if (!A->val16.p) {
-      A->val16.reserve((size_t)A->nnz);
-      convert_kernel<__nv_bfloat16><<<grid_stride_blocks(A->nnz), 256, 0, st>>>(A->val.p, A->val16.p,
-                                                                                (size_t)A->nnz);
-      FLZ_LAUNCH_CHECK();
-    }
+    const __nv_bfloat16* sv = scaled<__nv_bfloat16>(A, A->sval16, 2, c, e, st);
     A->ws16.reserve(3 * nr);
     A->ws32.reserve(nr);
     __nv_bfloat16* vs = A->ws16.p;
@@ -226,8 +341,7 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
     float* acc = A->ws32.p;
     convert_kernel<__nv_bfloat16><<<grid_stride_blocks(nr), 256, 0, st>>>(V, vs, nr);
     FLZ_LAUNCH_CHECK();
-    run_recurrence<__nv_bfloat16, __nv_bfloat16, float>(A, A->val16.p, c, e, coeffs, m, r, vs, ya, yb, acc, W,
-                                                        st);
+    run_recurrence<__nv_bfloat16, __nv_bfloat16, float>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
   } else {
     fail(FLZ_ERR_INVALID_ARG, "unknown precision %d", precision);
   }

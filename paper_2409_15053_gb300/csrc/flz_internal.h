@@ -41,6 +41,25 @@ extern thread_local int64_t g_kernel_launches;
     FLZ_CUDA(cudaGetLastError());  \
   } while (0)
 
+// Entry-point bodies: clear the thread's last error, run, map failures to a status.
+#define FLZ_API_BEGIN         \
+  ::flz::clear_last_error();  \
+  try {
+#define FLZ_API_END                                     \
+  }                                                     \
+  catch (const ::flz::Failure& f) {                     \
+    return f.status;                                    \
+  }                                                     \
+  catch (const std::bad_alloc&) {                       \
+    ::flz::set_last_error("host allocation failed");    \
+    return FLZ_ERR_OUT_OF_MEMORY;                       \
+  }                                                     \
+  catch (...) {                                         \
+    ::flz::set_last_error("unexpected internal error"); \
+    return FLZ_ERR_CUDA;                                \
+  }                                                     \
+  return FLZ_OK;
+
 // Owning device buffer.
 template <class T>
 struct DevBuf {
@@ -69,14 +88,22 @@ struct DevBuf {
 
 // Matrix handle: a device copy of a symmetric CSR matrix (Section 3.2.1).
 struct flz_matrix {
-  int64_t n = 0, nnz = 0;
+  int64_t n = 0, nnz = 0;              // nnz counts the stored entries (explicit zero diagonals included)
+  int64_t nnz_user = 0;                // entries the caller passed
   int device = 0;
   flz::DevBuf<int32_t> rowptr, col;
   flz::DevBuf<double> val;
-  flz::DevBuf<float> val32;            // made on first FP32 filter use
-  flz::DevBuf<__nv_bfloat16> val16;    // made on first BF16 filter use
+  flz::DevBuf<int32_t> diag_pos;       // position of a_ii in col/val for every row
+  // 2 Ahat = (2/e)(A - cI) in each filter storage precision (FP64, FP32, BF16),
+  // rebuilt when (c, e) change: the filter kernels read only these values.
+  flz::DevBuf<double> sval64;
+  flz::DevBuf<float> sval32;
+  flz::DevBuf<__nv_bfloat16> sval16;
+  double sc_c[3] = {0.0, 0.0, 0.0}, sc_e[3] = {0.0, 0.0, 0.0};
+  bool sc_ok[3] = {false, false, false};
   double glo = 0.0, ghi = 0.0;         // Gershgorin interval
   int32_t max_row_nnz = 0;
+  int32_t max_cta_nnz = 0;             // most stored entries in any 256 consecutive rows
   // Scratch of flz_filter_apply: recurrence vectors and the running sum.
   flz::DevBuf<double> ws64;
   flz::DevBuf<float> ws32;
@@ -133,6 +160,13 @@ void rows_to_columns(const double* X, int64_t n, int s, int ld, double* out, int
 void gershgorin(const flz_matrix* A, double* glo, double* ghi, int32_t* max_row_nnz);
 // Structural/symmetry validation on the device; returns status (BAD_CSR, NOT_SYMMETRIC, OK).
 flz_status validate_csr(const flz_matrix* A, int check_symmetry);
+// Most stored entries in any `rows` consecutive rows starting at a multiple of `rows`.
+int32_t max_block_nnz(const flz_matrix* A, int rows);
+// Fills A->diag_pos; returns the number of rows without a stored diagonal entry.
+int64_t find_diagonals(flz_matrix* A);
+// out[j] = (2/e)(val[j] - c [j is a diagonal position]) rounded to S.
+template <class S>
+void scale_values(const flz_matrix* A, double c, double e, S* out, cudaStream_t st);
 
 // ---- hostla.cpp -------------------------------------------------------------------------
 // Eigenvalues (ascending) of a symmetric band matrix (dense K x K storage,

@@ -329,6 +329,13 @@ flz_status solve(flz_solver* s, cudaStream_t st) {
   int64_t prev_count = -1;
   bool converged = false;
   int k = 0;
+  // Pairs the last walk visited: the next check first requires at least this
+  // many leading Ritz pairs to pass the cheap p(A) residual gate.
+  int gate_len = 16;
+  // If x has ||Ax - lambda x|| <= tol ||A|| then ||p(A)x - theta x|| <=
+  // max|p'| tol ||A|| / e, and max|p'| <= 1.1 m^2 on [-1, 1] (Markov, |p| <= 1.1):
+  // a pair whose p(A) residual exceeds this cannot pass the A-residual test.
+  const double p_gate = std::min(1e-2, 10.0 * 1.1 * (double)m * m * p.tol * anorm / e);
   std::vector<double> found_vals, found_res;
   int64_t found = 0;
   for (int j = 0; j < nb_cap; ++j) {
@@ -352,25 +359,34 @@ flz_status solve(flz_solver* s, cudaStream_t st) {
     found_vals.clear();
     found_res.clear();
     found = 0;
-    const double p_gate = std::min(1e-2, std::max(1e3 * p.tol, 1e-8) * (double)m * m * anorm / e);
-    for (int pos = 0; pos < K && !walk_done; pos += 16) {
+    auto p_residual = [&](const double* y) {  // ||S_k y_bottom|| of a unit eigenvector y of T_k
+      double s2 = 0.0;
+      for (int i = 0; i < r; ++i) {
+        double v = 0.0;
+        for (int a = 0; a < r; ++a) v += Sk[i * r + a] * y[(size_t)(k - 1) * r + a];
+        s2 += v * v;
+      }
+      return std::sqrt(s2);
+    };
+    {
+      // cheap host gate: the leading gate_len pairs must all pass before any GPU work
+      const int g_cnt = std::min(gate_len, K);
+      std::vector<int> gidx(order.begin(), order.begin() + g_cnt);
+      std::vector<double> Yg;
+      band_eigenvectors(T, K, r, theta, gidx, Yg, p.seed);
+      for (int t = 0; t < g_cnt && all_small; ++t)
+        if (p_residual(&Yg[(size_t)t * K]) > p_gate) all_small = false;
+    }
+    int walked = 0;
+    for (int pos = 0; pos < K && !walk_done && all_small; pos += 16) {
       const int cnt = std::min(16, K - pos);
       std::vector<int> idx(order.begin() + pos, order.begin() + pos + cnt);
       std::vector<double> Y;
       band_eigenvectors(T, K, r, theta, idx, Y, p.seed + (uint64_t)pos);
-      // cheap gate on the p(A) residual ||S_k y_bottom|| of the leading pair
-      {
-        const double* y = &Y[(size_t)(k - 1) * r];
-        double s2 = 0.0;
-        for (int i = 0; i < r; ++i) {
-          double v = 0.0;
-          for (int a = 0; a < r; ++a) v += Sk[i * r + a] * y[a];
-          s2 += v * v;
-        }
-        if (std::sqrt(s2) > p_gate) {
-          all_small = false;
-          break;
-        }
+      // a pair failing the gate ends the walk before its Ritz vector is formed
+      if (p_residual(&Y[0]) > p_gate) {
+        all_small = false;
+        break;
       }
       // Ritz vectors X = Q_k Y (n x 16, zero-padded columns)
       std::vector<double> Cy((size_t)K * 16, 0.0);
@@ -393,6 +409,7 @@ flz_status solve(flz_solver* s, cudaStream_t st) {
       FLZ_CUDA(cudaMemcpyAsync(h + 48, dev + 48, sizeof(double) * 16, cudaMemcpyDeviceToHost, st));
       FLZ_CUDA(cudaStreamSynchronize(st));
       for (int t = 0; t < cnt; ++t) {
+        ++walked;
         const double xx = h[t];
         const double lam = h[32 + t];
         const double res = std::sqrt(std::max(h[48 + t], 0.0) / std::max(xx, 1e-300)) / anorm;
@@ -431,6 +448,7 @@ flz_status solve(flz_solver* s, cudaStream_t st) {
       }
       if (!walk_done && pos + cnt >= K) walk_done = true;
     }
+    if (walked > 0) gate_len = std::max(16, walked);
     const bool complete = all_small && outside >= guard;
     converged = complete && prev_count >= 0 && inside == prev_count;
     prev_count = complete ? inside : -1;

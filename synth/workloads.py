@@ -14,8 +14,9 @@ CONFIG2 = {
     "seed": 2025,
     "potential_scale": 0.5,
     "alpha": 0.0,
-    "beta": 0.2885,
-    "count": 100,
+    "beta": 0.28699178286577987,
+    "count": 105,
     "degree": 60,
-    "reference_iters": 90,
+    "check_every": 10,
+    "reference_iters": 120,
 }

@@ -177,3 +177,24 @@ def test_full_size_config2_filter_matches_oracle():
     got = run_filter(M, c, e, coeffs, V)
     ref = chebyshev.clenshaw_apply(csr.to_scipy(), c, e, coeffs, V)
     assert np.max(np.abs(got - ref)) <= bound(csr, c, e, m, V, U64)
+
+
+def test_rows_without_stored_diagonal():
+    # The filter folds -cI into the stored diagonal; rows that store no a_ii get
+    # an explicit zero at creation. A symmetric matrix with most diagonals absent:
+    S = laplacian_2d(23, 19).to_scipy().tolil()
+    for i in range(0, 23 * 19, 3):
+        S[i, i] = 0.0
+    S = S.tocsr()
+    S.eliminate_zeros()
+    from synth.matrices import CSR
+    csr = CSR(S.shape[0], S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.astype(np.float64))
+    M = Mat(csr)
+    n, nnz, glo, ghi = flz.flz_matrix_info(M.h)
+    assert nnz == csr.nnz  # reports the caller's entries
+    c, e = gershgorin_map(csr)
+    coeffs = chebyshev.filter_coefficients(-0.5, 0.1, 41)
+    V = random_normal_block(csr.n, 3, 9)
+    got = run_filter(M, c, e, coeffs, V)
+    ref = chebyshev.clenshaw_apply(S, c, e, coeffs, V)
+    assert np.max(np.abs(got - ref)) <= bound(csr, c, e, 41, V, U64)

@@ -211,3 +211,23 @@ def test_device_resident_csr_input():
     n, nnz, glo, ghi = flz.flz_matrix_info(h)
     flz.flz_matrix_destroy(h)
     assert (n, nnz, glo, ghi) == (900, csr.nnz, 0.0, 8.0)
+
+
+def test_full_size_config2_matches_oracle_reference():
+    # n = 1e6, nnz = 6.94e6, r = 4, m = 60: the benchmark's configuration,
+    # against the eigenvalues the CPU oracle computed (tests/golden).
+    import json
+    import os
+    from synth.workloads import CONFIG2
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "config2_reference.json")))
+    rng = np.random.Generator(np.random.PCG64(CONFIG2["seed"]))
+    g = CONFIG2["grid"]
+    csr = laplacian_3d_7pt(g, g, g, CONFIG2["potential_scale"] * rng.random(g ** 3))
+    out = solve(csr, CONFIG2["alpha"], CONFIG2["beta"], block_size=4, degree=CONFIG2["degree"],
+                check_every=CONFIG2["check_every"])
+    want = np.array(ref["eigenvalues"])
+    assert out["status"] == flz.FLZ_OK
+    assert out["vals"].shape == want.shape == (CONFIG2["count"],)
+    norm_a = max(abs(out["stats"]["lmin"]), abs(out["stats"]["lmax"]))
+    assert np.max(np.abs(out["vals"] - want)) < 1e-10 * norm_a
+    check_pairs(csr, out, 1e-10)

@@ -1,0 +1,49 @@
+"""The seeded generators: closed-form structure counts, symmetry, and
+bit-stable output (the checksum recorded when the config-2 reference was
+computed by the oracle must be reproduced on any host)."""
+
+import json
+import os
+
+import numpy as np
+
+from synth import (csr_checksum, fd4_laplacian_3d, laplacian_2d, laplacian_3d_7pt, powerlaw_graph_laplacian,
+                   uneven_batch)
+from synth.workloads import CONFIG2
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_stencil_nnz_closed_forms():
+    assert laplacian_2d(50, 50).nnz == 5 * 2500 - 4 * 50
+    assert laplacian_3d_7pt(10, 11, 12).nnz == 7 * 1320 - 2 * (11 * 12 + 10 * 12 + 10 * 11)
+    N = 12
+    assert fd4_laplacian_3d(N).nnz == N ** 3 + 3 * N * N * (2 * (N - 1) + 2 * (N - 2))
+
+
+def test_generators_are_symmetric():
+    for A in (laplacian_3d_7pt(7, 8, 9, np.linspace(0, 1, 504)), fd4_laplacian_3d(9),
+              powerlaw_graph_laplacian(5000, seed=1)):
+        S = A.to_scipy()
+        assert abs(S - S.T).max() == 0.0
+
+
+def test_graph_laplacian_annihilates_constants():
+    A = powerlaw_graph_laplacian(20000, seed=4).to_scipy()
+    assert np.max(np.abs(A @ np.ones(A.shape[0]))) < 1e-10
+
+
+def test_uneven_batch_shapes():
+    mats = uneven_batch(8, seed=3)
+    assert len(mats) == 8
+    for A, kind, dims in mats:
+        assert A.n == int(np.prod(dims)) and kind in ("2d", "3d")
+
+
+def test_config2_matrix_matches_the_oracle_reference():
+    ref = json.load(open(os.path.join(GOLD, "config2_reference.json")))
+    rng = np.random.Generator(np.random.PCG64(CONFIG2["seed"]))
+    g = CONFIG2["grid"]
+    A = laplacian_3d_7pt(g, g, g, CONFIG2["potential_scale"] * rng.random(g ** 3))
+    assert csr_checksum(A) == ref["matrix_checksum"]
+    assert CONFIG2["beta"] == ref["beta"] and CONFIG2["count"] == ref["count"] == len(ref["eigenvalues"])
