@@ -197,6 +197,12 @@ flz_status flz_band_eigenvalues(int32_t K, int32_t b, const double* T, double* t
 flz_status flz_band_eigenvectors(int32_t K, int32_t b, const double* T, const double* theta, int32_t count,
                                  const int32_t* idx, double* Y, uint64_t seed);
 
+/* Dense symmetric eigen-decomposition of the n x n row-major matrix S (host):
+ * w[n] ascending eigenvalues, Z[n*n] row-major with column k the unit
+ * eigenvector of w[k]. Householder tridiagonalization + implicit QL. Used for
+ * the Rayleigh-Ritz refinement on A of the reduced-precision filters. */
+flz_status flz_sym_eig(int32_t n, const double* S, double* w, double* Z);
+
 /* ---- solver (Sections 2.3 and 3.2.2) ---------------------------------------- */
 
 /* Creates a solver bound to A (which must outlive it). params may be NULL
@@ -223,6 +229,34 @@ flz_status flz_get_eigenvectors(const flz_solver* s, double* out, int64_t ld, in
 /* ||A x_j - lambda_j x_j|| / ||A|| per pair into host out[cap]. */
 flz_status flz_get_residuals(const flz_solver* s, double* out, int64_t cap);
 flz_status flz_get_stats(const flz_solver* s, flz_stats* out);
+
+/* ---- batches of independent problems --------------------------------------- */
+
+/* A batch of `count` independent problems (not in the paper, which solves one
+ * matrix per call): problem i is all eigenpairs of mats[i] in
+ * [alphas[i], betas[i]] (A's units). Every matrix must outlive the batch.
+ * params (NULL = defaults) apply to all problems; block_size = 0 picks r in
+ * {4, 8, 16} by timing the filter kernel at each width (autotuning). The
+ * problems are concatenated into one block-diagonal device matrix and run in
+ * lockstep: each kernel of a block Lanczos step serves every problem at once,
+ * with per-problem bounds, filter degree and coefficients, and per-problem
+ * (segmented) reorthogonalization, block QR and convergence. One whole block
+ * step is captured once as a CUDA graph and replayed. Problems stop when they
+ * converge. Host arrays alphas/betas have `count` entries. */
+flz_status flz_batch_create(int32_t count, flz_matrix* const* mats, const double* alphas, const double* betas,
+                            const flz_params* params, flz_batch** out);
+flz_status flz_batch_destroy(flz_batch* b);
+/* Solves every problem; synchronous like flz_solve. FLZ_ERR_NOT_CONVERGED if
+ * any problem did not converge (each problem's stats say which). */
+flz_status flz_batch_solve(flz_batch* b, void* stream);
+/* Per-problem results, index in [0, count): same meaning and errors as the
+ * single-problem getters. */
+flz_status flz_batch_get_count(const flz_batch* b, int32_t index, int64_t* count);
+flz_status flz_batch_get_eigenvalues(const flz_batch* b, int32_t index, double* out, int64_t cap);
+flz_status flz_batch_get_residuals(const flz_batch* b, int32_t index, double* out, int64_t cap);
+flz_status flz_batch_get_eigenvectors(const flz_batch* b, int32_t index, double* out, int64_t ld, int64_t cap_cols,
+                                      flz_memspace where);
+flz_status flz_batch_get_stats(const flz_batch* b, int32_t index, flz_stats* out);
 
 #ifdef __cplusplus
 }

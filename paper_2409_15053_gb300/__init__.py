@@ -42,8 +42,10 @@ EXPORTED = (
     "flz_status_string", "flz_last_error", "flz_params_default",
     "flz_matrix_create_csr", "flz_matrix_destroy", "flz_matrix_info",
     "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_filter_degree", "flz_spectrum_bounds",
-    "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve",
+    "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_sym_eig", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve",
     "flz_get_count", "flz_get_eigenvalues", "flz_get_eigenvectors", "flz_get_residuals", "flz_get_stats",
+    "flz_batch_create", "flz_batch_destroy", "flz_batch_solve", "flz_batch_get_count", "flz_batch_get_eigenvalues",
+    "flz_batch_get_residuals", "flz_batch_get_eigenvectors", "flz_batch_get_stats",
 )
 
 
@@ -109,6 +111,7 @@ def lib() -> ctypes.CDLL:
         "flz_spectrum_bounds": (ctypes.c_int, [_vp, _i32, _i32, _u64, _pdbl, _pdbl, _vp]),
         "flz_band_eigenvalues": (ctypes.c_int, [_i32, _i32, _vp, _vp]),
         "flz_band_eigenvectors": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp, _vp, _u64]),
+        "flz_sym_eig": (ctypes.c_int, [_i32, _vp, _vp, _vp]),
         "flz_solver_create": (ctypes.c_int, [_vp, ctypes.POINTER(flz_params), ctypes.POINTER(_vp)]),
         "flz_solver_destroy": (ctypes.c_int, [_vp]),
         "flz_solver_set_interval": (ctypes.c_int, [_vp, _dbl, _dbl]),
@@ -118,6 +121,15 @@ def lib() -> ctypes.CDLL:
         "flz_get_eigenvectors": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.c_int]),
         "flz_get_residuals": (ctypes.c_int, [_vp, _vp, _i64]),
         "flz_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(flz_stats)]),
+        "flz_batch_create": (ctypes.c_int, [_i32, ctypes.POINTER(_vp), _vp, _vp, ctypes.POINTER(flz_params),
+                                            ctypes.POINTER(_vp)]),
+        "flz_batch_destroy": (ctypes.c_int, [_vp]),
+        "flz_batch_solve": (ctypes.c_int, [_vp, _vp]),
+        "flz_batch_get_count": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_i64)]),
+        "flz_batch_get_eigenvalues": (ctypes.c_int, [_vp, _i32, _vp, _i64]),
+        "flz_batch_get_residuals": (ctypes.c_int, [_vp, _i32, _vp, _i64]),
+        "flz_batch_get_eigenvectors": (ctypes.c_int, [_vp, _i32, _vp, _i64, _i64, ctypes.c_int]),
+        "flz_batch_get_stats": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(flz_stats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -240,6 +252,16 @@ def flz_band_eigenvectors(T: np.ndarray, b: int, theta: np.ndarray, idx, seed: i
     return Y.T
 
 
+def flz_sym_eig(S: np.ndarray):
+    """(w, Z): ascending eigenvalues and eigenvectors (columns) of a dense symmetric matrix."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    n = S.shape[0]
+    w = np.empty(n)
+    Z = np.empty((n, n))
+    _check(lib().flz_sym_eig(n, _ptr(S), _ptr(w), _ptr(Z)))
+    return w, Z
+
+
 def flz_solver_create(A, params: flz_params | None = None):
     h = _vp()
     _check(lib().flz_solver_create(A, ctypes.byref(params) if params is not None else None, ctypes.byref(h)))
@@ -296,4 +318,63 @@ def get_eigenvectors_host(s, n: int) -> np.ndarray:
 def flz_get_stats(s) -> dict:
     st = flz_stats()
     _check(lib().flz_get_stats(s, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def flz_batch_create(mats, alphas, betas, params: flz_params | None = None):
+    """Batch of independent problems; `mats` are matrix handles that must outlive the batch."""
+    count = len(mats)
+    arr = (_vp * count)(*[m.value if isinstance(m, _vp) else m for m in mats])
+    a = np.ascontiguousarray(alphas, dtype=np.float64)
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    h = _vp()
+    _check(lib().flz_batch_create(count, arr, _ptr(a), _ptr(b), ctypes.byref(params) if params is not None else None,
+                                  ctypes.byref(h)))
+    return h
+
+
+def flz_batch_destroy(b):
+    _check(lib().flz_batch_destroy(b))
+
+
+def flz_batch_solve(b, stream=None) -> int:
+    return _check(lib().flz_batch_solve(b, _stream(stream)), allow=(FLZ_ERR_NOT_CONVERGED,))
+
+
+def flz_batch_get_count(b, index) -> int:
+    c = _i64()
+    _check(lib().flz_batch_get_count(b, int(index), ctypes.byref(c)))
+    return c.value
+
+
+def flz_batch_get_eigenvalues(b, index) -> np.ndarray:
+    cnt = flz_batch_get_count(b, index)
+    out = np.empty(max(cnt, 1))
+    _check(lib().flz_batch_get_eigenvalues(b, int(index), _ptr(out), int(out.shape[0])))
+    return out[:cnt]
+
+
+def flz_batch_get_residuals(b, index) -> np.ndarray:
+    cnt = flz_batch_get_count(b, index)
+    out = np.empty(max(cnt, 1))
+    _check(lib().flz_batch_get_residuals(b, int(index), _ptr(out), int(out.shape[0])))
+    return out[:cnt]
+
+
+def flz_batch_get_eigenvectors(b, index, out, ld, cap_cols, where=FLZ_HOST):
+    _check(lib().flz_batch_get_eigenvectors(b, int(index), _ptr(out), int(ld), int(cap_cols), int(where)))
+    return out
+
+
+def batch_eigenvectors_host(b, index, n: int) -> np.ndarray:
+    """(n, count) eigenvectors of problem `index` copied to the host."""
+    cnt = flz_batch_get_count(b, index)
+    buf = np.empty((max(cnt, 1), n))
+    _check(lib().flz_batch_get_eigenvectors(b, int(index), _ptr(buf), int(n), int(max(cnt, 1)), FLZ_HOST))
+    return buf[:cnt].T
+
+
+def flz_batch_get_stats(b, index) -> dict:
+    st = flz_stats()
+    _check(lib().flz_batch_get_stats(b, int(index), ctypes.byref(st)))
     return st.as_dict()

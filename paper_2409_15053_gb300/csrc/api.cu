@@ -206,6 +206,15 @@ flz_status flz_matrix_create_csr(int64_t n, int64_t nnz, const int32_t* rowptr, 
     if (flz::find_diagonals(A) > 0) insert_zero_diagonals(A);
     flz::gershgorin(A, &A->glo, &A->ghi, &A->max_row_nnz);
     A->max_cta_nnz = flz::max_block_nnz(A, 256);
+    if (A->max_row_nnz > flz::kLongRow) {
+      std::vector<int32_t> rp(A->n + 1), lr;
+      FLZ_CUDA(cudaMemcpy(rp.data(), A->rowptr.p, sizeof(int32_t) * (A->n + 1), cudaMemcpyDeviceToHost));
+      for (int64_t i = 0; i < A->n; ++i)
+        if (rp[i + 1] - rp[i] > flz::kLongRow) lr.push_back((int32_t)i);
+      A->n_long = (int32_t)lr.size();
+      A->long_rows.reserve(lr.size());
+      FLZ_CUDA(cudaMemcpy(A->long_rows.p, lr.data(), sizeof(int32_t) * lr.size(), cudaMemcpyHostToDevice));
+    }
   } catch (...) {
     delete A;
     throw;
@@ -273,6 +282,16 @@ flz_status flz_band_eigenvectors(int32_t K, int32_t b, const double* T, const do
     if (v < 0 || v >= K) fail(FLZ_ERR_INVALID_ARG, "eigenvalue index out of range");
   flz::band_eigenvectors(t, K, std::min<int32_t>(std::max<int32_t>(b, 1), K), th, ix, y, seed);
   for (size_t i = 0; i < y.size(); ++i) Y[i] = y[i];
+  FLZ_API_END
+}
+
+flz_status flz_sym_eig(int32_t n, const double* S, double* w, double* Z) {
+  FLZ_API_BEGIN
+  if (n < 1 || !S || !w || !Z) fail(FLZ_ERR_INVALID_ARG, "bad arguments");
+  std::vector<double> A(S, S + (size_t)n * n), ww, zz;
+  flz::dense_sym_eig(A, n, ww, zz);
+  std::copy(ww.begin(), ww.end(), w);
+  std::copy(zz.begin(), zz.end(), Z);
   FLZ_API_END
 }
 

@@ -85,7 +85,7 @@ constexpr int kRows = 256;  // rows per CTA in the row-per-thread kernel
 // row Y[col] is one R-wide vector load. Same arithmetic as cheb_step_kernel.
 template <int R, class MS, class VS, class AccS, class OutS, bool FIRST>
 __global__ void __launch_bounds__(kRows) cheb_rows_kernel(
-    int n, int cap, const int* __restrict__ rowptr, const int* __restrict__ col, const MS* __restrict__ sval,
+    int n, int cap, int long_row, const int* __restrict__ rowptr, const int* __restrict__ col, const MS* __restrict__ sval,
     const VS* __restrict__ ycur, const VS* yprev, VS* ynext, const AccS* acc_in, OutS* acc_out,
     typename Arith<VS>::type b_cur, typename Arith<VS>::type b_next) {
   using A = typename Arith<VS>::type;
@@ -108,7 +108,9 @@ __global__ void __launch_bounds__(kRows) cheb_rows_kernel(
   if (row >= n) return;
   const int jb = __ldg(rowptr + row);
   const int je = __ldg(rowptr + row + 1);
+  if (je - jb > long_row) return;  // rows longer than long_row belong to cheb_long_kernel
   A s[R];
+  A acc[R];
   if (FIRST) {
 #pragma unroll
     for (int t = 0; t < R; ++t) s[t] = A(0);
@@ -116,8 +118,30 @@ __global__ void __launch_bounds__(kRows) cheb_rows_kernel(
     load_row<VS, R>(yprev + (size_t)row * R, s);
 #pragma unroll
     for (int t = 0; t < R; ++t) s[t] = -s[t];
+    load_acc<R>(acc_in + (size_t)row * R, acc);  // issued early: it overlaps the gathers
   }
-  for (int j = jb; j < je; ++j) {
+  // U independent row gathers in flight per thread (fewer for wide rows to
+  // bound register use)
+  constexpr int kRowBytes = R * (int)sizeof(A);
+  constexpr int U = kRowBytes <= 16 ? 4 : (kRowBytes <= 32 ? 2 : 1);
+  int j = jb;
+  for (; j + U <= je; j += U) {
+    int cj[U];
+    A a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      cj[u] = staged ? s_col[j + u - j0] : __ldg(col + j + u);
+      a[u] = staged ? to_arith(s_val[j + u - j0]) : to_arith(sval[j + u]);
+    }
+    A y[U][R];
+#pragma unroll
+    for (int u = 0; u < U; ++u) load_row<VS, R>(ycur + (size_t)cj[u] * R, y[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int t = 0; t < R; ++t) s[t] = fma(a[u], y[u][t], s[t]);
+  }
+  for (; j < je; ++j) {
     const int cj = staged ? s_col[j - j0] : __ldg(col + j);
     const A a = staged ? to_arith(s_val[j - j0]) : to_arith(sval[j]);
     A y[R];
@@ -130,17 +154,70 @@ __global__ void __launch_bounds__(kRows) cheb_rows_kernel(
     for (int t = 0; t < R; ++t) s[t] *= A(0.5);
   }
   store_row_rounded<VS, R>(ynext + (size_t)row * R, s);  // s now holds the stored (rounded) Y_next
-  A acc[R];
   if (FIRST) {
     A v0[R];
     load_row<VS, R>(ycur + (size_t)row * R, v0);
 #pragma unroll
     for (int t = 0; t < R; ++t) acc[t] = b_cur * v0[t];
-  } else {
-    load_acc<R>(acc_in + (size_t)row * R, acc);
   }
 #pragma unroll
   for (int t = 0; t < R; ++t) acc[t] = fma(b_next, s[t], acc[t]);
+  store_acc<R>(acc_out + (size_t)row * R, acc);
+}
+
+// The same degree step for rows with more than `long_row` stored entries
+// (hubs of irregular graphs): one CTA per long row, its threads take strided
+// entries and the partial sums are combined in shared memory, so a hub costs
+// about (entries / 256) gathers of latency instead of `entries`.
+template <int R, class MS, class VS, class AccS, class OutS, bool FIRST>
+__global__ void __launch_bounds__(kRows) cheb_long_kernel(
+    const int* __restrict__ long_rows, const int* __restrict__ rowptr, const int* __restrict__ col,
+    const MS* __restrict__ sval, const VS* __restrict__ ycur, const VS* yprev, VS* ynext, const AccS* acc_in,
+    OutS* acc_out, typename Arith<VS>::type b_cur, typename Arith<VS>::type b_next) {
+  using A = typename Arith<VS>::type;
+  __shared__ A red[kRows * R];
+  const int row = long_rows[blockIdx.x];
+  const int jb = __ldg(rowptr + row), je = __ldg(rowptr + row + 1);
+  A s[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) s[t] = A(0);
+  for (int j = jb + (int)threadIdx.x; j < je; j += kRows) {
+    const A a = to_arith(sval[j]);
+    A y[R];
+    load_row<VS, R>(ycur + (size_t)__ldg(col + j) * R, y);
+#pragma unroll
+    for (int t = 0; t < R; ++t) s[t] = fma(a, y[t], s[t]);
+  }
+#pragma unroll
+  for (int t = 0; t < R; ++t) red[t * kRows + threadIdx.x] = s[t];
+  __syncthreads();
+  for (int h = kRows / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h)
+#pragma unroll
+      for (int t = 0; t < R; ++t) red[t * kRows + threadIdx.x] += red[t * kRows + threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  A yn[R], acc[R];
+  if (FIRST) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) yn[t] = A(0.5) * red[t * kRows];
+  } else {
+    A yp[R];
+    load_row<VS, R>(yprev + (size_t)row * R, yp);
+#pragma unroll
+    for (int t = 0; t < R; ++t) yn[t] = red[t * kRows] - yp[t];
+    load_acc<R>(acc_in + (size_t)row * R, acc);
+  }
+  store_row_rounded<VS, R>(ynext + (size_t)row * R, yn);
+  if (FIRST) {
+    A v0[R];
+    load_row<VS, R>(ycur + (size_t)row * R, v0);
+#pragma unroll
+    for (int t = 0; t < R; ++t) acc[t] = b_cur * v0[t];
+  }
+#pragma unroll
+  for (int t = 0; t < R; ++t) acc[t] = fma(b_next, yn[t], acc[t]);
   store_acc<R>(acc_out + (size_t)row * R, acc);
 }
 
@@ -212,27 +289,36 @@ void run_rows(const flz_matrix* A, const MS* val, const double* b, int m, const 
   const unsigned grid = (unsigned)((n + kRows - 1) / kRows);
   const int* rp = A->rowptr.p;
   const int* cl = A->col.p;
-  if (m == 1) {
-    cheb_rows_kernel<R, MS, VS, AccT, double, true><<<grid, kRows, smem, st>>>(
-        n, cap, rp, cl, val, v, nullptr, ya, nullptr, W, Ar(b[0]), Ar(b[1]));
-    FLZ_LAUNCH_CHECK();
-    return;
-  }
-  cheb_rows_kernel<R, MS, VS, AccT, AccT, true><<<grid, kRows, smem, st>>>(
-      n, cap, rp, cl, val, v, nullptr, ya, nullptr, acc, Ar(b[0]), Ar(b[1]));
-  FLZ_LAUNCH_CHECK();
+  const int nl = A->n_long;
+  const int thr = nl > 0 ? kLongRow : 0x7fffffff;
+  const int* lr = A->long_rows.p;
+  auto step = [&](bool first, bool last, const VS* cur, const VS* prev, VS* next, Ar bc, Ar bn) {
+    if (first && last) {
+      cheb_rows_kernel<R, MS, VS, AccT, double, true><<<grid, kRows, smem, st>>>(n, cap, thr, rp, cl, val, cur, prev, next, acc, W, bc, bn);
+      FLZ_LAUNCH_CHECK();
+      if (nl) cheb_long_kernel<R, MS, VS, AccT, double, true><<<nl, kRows, 0, st>>>(lr, rp, cl, val, cur, prev, next, acc, W, bc, bn);
+    } else if (first) {
+      cheb_rows_kernel<R, MS, VS, AccT, AccT, true><<<grid, kRows, smem, st>>>(n, cap, thr, rp, cl, val, cur, prev, next, acc, acc, bc, bn);
+      FLZ_LAUNCH_CHECK();
+      if (nl) cheb_long_kernel<R, MS, VS, AccT, AccT, true><<<nl, kRows, 0, st>>>(lr, rp, cl, val, cur, prev, next, acc, acc, bc, bn);
+    } else if (last) {
+      cheb_rows_kernel<R, MS, VS, AccT, double, false><<<grid, kRows, smem, st>>>(n, cap, thr, rp, cl, val, cur, prev, next, acc, W, bc, bn);
+      FLZ_LAUNCH_CHECK();
+      if (nl) cheb_long_kernel<R, MS, VS, AccT, double, false><<<nl, kRows, 0, st>>>(lr, rp, cl, val, cur, prev, next, acc, W, bc, bn);
+    } else {
+      cheb_rows_kernel<R, MS, VS, AccT, AccT, false><<<grid, kRows, smem, st>>>(n, cap, thr, rp, cl, val, cur, prev, next, acc, acc, bc, bn);
+      FLZ_LAUNCH_CHECK();
+      if (nl) cheb_long_kernel<R, MS, VS, AccT, AccT, false><<<nl, kRows, 0, st>>>(lr, rp, cl, val, cur, prev, next, acc, acc, bc, bn);
+    }
+    if (nl) FLZ_LAUNCH_CHECK();
+  };
+  // step 0 reads V, writes Y_1 to ya; then Y_{k+1} overwrites Y_{k-1} in place
+  step(true, m == 1, v, nullptr, ya, Ar(b[0]), Ar(b[1]));
   const VS* prev = v;
   const VS* cur = ya;
   for (int k = 1; k < m; ++k) {
     VS* next = (k == 1) ? yb : const_cast<VS*>(prev);
-    if (k + 1 == m) {
-      cheb_rows_kernel<R, MS, VS, AccT, double, false><<<grid, kRows, smem, st>>>(
-          n, cap, rp, cl, val, cur, prev, next, acc, W, Ar(0), Ar(b[k + 1]));
-    } else {
-      cheb_rows_kernel<R, MS, VS, AccT, AccT, false><<<grid, kRows, smem, st>>>(
-          n, cap, rp, cl, val, cur, prev, next, acc, acc, Ar(0), Ar(b[k + 1]));
-    }
-    FLZ_LAUNCH_CHECK();
+    step(false, k + 1 == m, cur, prev, next, Ar(0), Ar(b[k + 1]));
     prev = cur;
     cur = next;
   }

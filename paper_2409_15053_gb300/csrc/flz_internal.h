@@ -104,6 +104,8 @@ struct flz_matrix {
   double glo = 0.0, ghi = 0.0;         // Gershgorin interval
   int32_t max_row_nnz = 0;
   int32_t max_cta_nnz = 0;             // most stored entries in any 256 consecutive rows
+  flz::DevBuf<int32_t> long_rows;      // rows with more than kLongRow entries (filter's CTA-per-row tier)
+  int32_t n_long = 0;
   // Scratch of flz_filter_apply: recurrence vectors and the running sum.
   flz::DevBuf<double> ws64;
   flz::DevBuf<float> ws32;
@@ -126,6 +128,9 @@ struct flz_solver {
 };
 
 namespace flz {
+
+// Rows with more stored entries than this are filtered by one CTA each.
+constexpr int kLongRow = 256;
 
 // ---- filter.cu ----------------------------------------------------------------
 // W = p_m((A - cI)/e) V, V and W device FP64 n x r row-major.
@@ -177,6 +182,9 @@ void band_eigenvalues(const std::vector<double>& T, int K, int b, std::vector<do
 // orthogonalized against each other. Y is K x count column-major.
 void band_eigenvectors(const std::vector<double>& T, int K, int b, const std::vector<double>& theta,
                        const std::vector<int>& idx, std::vector<double>& Y, uint64_t seed);
+// Dense symmetric eigen-decomposition: A (n x n row-major, destroyed), w
+// ascending, Z row-major with column k the eigenvector of w[k].
+void dense_sym_eig(std::vector<double>& A, int n, std::vector<double>& w, std::vector<double>& Z);
 // Eigenvalues of a symmetric tridiagonal (d, e) by implicit QL; d overwritten ascending.
 void tridiagonal_eigenvalues(std::vector<double>& d, std::vector<double>& e);
 // Upper Cholesky factor R (G = R^T R) of an s x s SPD matrix, row-major; false if not SPD.

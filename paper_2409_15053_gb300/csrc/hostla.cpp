@@ -20,41 +20,12 @@ namespace flz {
 
 namespace {
 
-inline void rotate_rows(double* T, int K, int p, int q, double c, double s, int j0, int j1) {
-  double* rp = T + (size_t)p * K;
-  double* rq = T + (size_t)q * K;
-  for (int j = j0; j <= j1; ++j) {
-    const double x = rp[j], y = rq[j];
-    rp[j] = c * x + s * y;
-    rq[j] = -s * x + c * y;
-  }
-}
-
-inline void rotate_cols(double* T, int K, int p, int q, double c, double s, int i0, int i1) {
-  for (int i = i0; i <= i1; ++i) {
-    double* row = T + (size_t)i * K;
-    const double x = row[p], y = row[q];
-    row[p] = c * x + s * y;
-    row[q] = -s * x + c * y;
-  }
-}
-
-// Zero T[k][j] (and T[j][k]) by a rotation in the plane (k-1, k) applied as a
-// similarity transform; entries outside [k-1-w, k+w] of rows/cols k-1, k are 0.
-inline void annihilate(double* T, int K, int k, int j, int w) {
-  const double x = T[(size_t)(k - 1) * K + j];
-  const double y = T[(size_t)k * K + j];
-  if (y == 0.0) return;
-  const double r = std::hypot(x, y);
-  const double c = x / r, s = y / r;
-  const int lo = std::max(0, k - 1 - w), hi = std::min(K - 1, k + w);
-  rotate_rows(T, K, k - 1, k, c, s, lo, hi);
-  rotate_cols(T, K, k - 1, k, c, s, lo, hi);
-  T[(size_t)k * K + j] = 0.0;
-  T[(size_t)j * K + k] = 0.0;
-}
-
 }  // namespace
+
+// sqrt(x^2 + y^2); the projected matrices have entries of order ||p(A)|| or
+// ||A||, far from the overflow range that std::hypot guards against (and
+// std::hypot costs several times more, in the innermost QL loop).
+static inline double pyth(double x, double y) { return std::sqrt(x * x + y * y); }
 
 void tridiagonal_eigenvalues(std::vector<double>& d, std::vector<double>& e) {
   // Implicit QL with the Wilkinson shift. e[i] couples i and i+1; e.size() >= d.size().
@@ -72,14 +43,14 @@ void tridiagonal_eigenvalues(std::vector<double>& d, std::vector<double>& e) {
       if (m == l) break;
       // Shift: eigenvalue of the leading 2x2 of the unreduced block closest to d[l].
       double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-      double r = std::hypot(g, 1.0);
+      double r = pyth(g, 1.0);
       g = d[m] - d[l] + e[l] / (g + std::copysign(r, g));
       double s = 1.0, c = 1.0, p = 0.0;
       bool deflated = false;
       for (int i = m - 1; i >= l; --i) {
         const double f = s * e[i];
         const double bb = c * e[i];
-        r = std::hypot(f, g);
+        r = pyth(f, g);
         e[i + 1] = r;
         if (r == 0.0) {
           d[i + 1] -= p;
@@ -105,27 +76,57 @@ void tridiagonal_eigenvalues(std::vector<double>& d, std::vector<double>& e) {
 }
 
 void band_eigenvalues(const std::vector<double>& Tin, int K, int b, std::vector<double>& theta) {
-  std::vector<double> T(Tin);
-  const int w = 2 * b + 2;
+  // Compact lower-band storage with one extra diagonal for the bulge:
+  // A[i*W + d] = T[i][i-d], d in [0, b+1].
+  const int W = b + 2;
+  std::vector<double> A((size_t)K * W, 0.0);
+  for (int i = 0; i < K; ++i)
+    for (int d = 0; d <= std::min(b, i); ++d) A[(size_t)i * W + d] = Tin[(size_t)i * K + (i - d)];
+  auto at = [&](int i, int d) -> double& { return A[(size_t)i * W + d]; };
+  // Similarity rotation in the plane (q, q+1) chosen to zero T[q+1][jj]; the
+  // rows and columns it touches hold nonzeros only in [jj, q+1+b].
+  auto rotate = [&](int q, int jj) {
+    const int p = q + 1;
+    const double x = at(q, q - jj), y = at(p, p - jj);
+    if (y == 0.0) return;
+    const double r = pyth(x, y), c = x / r, s = y / r;
+    for (int xc = jj + 1; xc <= q - 1; ++xc) {
+      const double u = at(q, q - xc), v = at(p, p - xc);
+      at(q, q - xc) = c * u + s * v;
+      at(p, p - xc) = -s * u + c * v;
+    }
+    at(q, q - jj) = r;
+    at(p, p - jj) = 0.0;
+    const double a = at(q, 0), bb = at(p, 1), d = at(p, 0);
+    at(q, 0) = c * c * a + 2.0 * c * s * bb + s * s * d;
+    at(p, 0) = s * s * a - 2.0 * c * s * bb + c * c * d;
+    at(p, 1) = -c * s * a + (c * c - s * s) * bb + c * s * d;
+    const int xe = std::min(K - 1, p + b);
+    for (int xr = p + 1; xr <= xe; ++xr) {
+      const double u = at(xr, xr - q), v = at(xr, xr - p);
+      at(xr, xr - q) = c * u + s * v;
+      at(xr, xr - p) = -s * u + c * v;
+    }
+  };
   if (b > 1) {
     for (int j = 0; j + 2 < K; ++j) {
       for (int k = std::min(j + b, K - 1); k >= j + 2; --k) {
-        annihilate(T.data(), K, k, j, w);
-        // Chase the bulge created at (k + b, k - 1) down the band.
-        int col = k - 1, q = k + b;
-        while (q < K) {
-          annihilate(T.data(), K, q, col, w);
-          col = q - 1;
+        rotate(k - 1, j);
+        // chase the bulge at (k + b, k - 1) down the band
+        int col = k - 1, q = k + b - 1;
+        while (q + 1 < K) {
+          rotate(q, col);
+          col = q;
           q += b;
         }
       }
     }
   }
-  std::vector<double> d(K), e(K, 0.0);
-  for (int i = 0; i < K; ++i) d[i] = T[(size_t)i * K + i];
-  for (int i = 0; i + 1 < K; ++i) e[i] = T[(size_t)(i + 1) * K + i];
-  tridiagonal_eigenvalues(d, e);
-  theta = d;
+  std::vector<double> dg(K), e(K, 0.0);
+  for (int i = 0; i < K; ++i) dg[i] = at(i, 0);
+  for (int i = 0; i + 1 < K; ++i) e[i] = at(i + 1, 1);
+  tridiagonal_eigenvalues(dg, e);
+  theta = dg;
 }
 
 namespace {
@@ -275,6 +276,115 @@ void upper_inverse(const double* R, int s, double* Rinv) {
       Rinv[i * s + j] = -v / R[i * s + i];
     }
   }
+}
+
+}  // namespace flz
+
+namespace flz {
+
+// Dense symmetric eigen-decomposition (Golub & Van Loan: Householder
+// tridiagonalization with the orthogonal factor accumulated, then implicit QL
+// with the Wilkinson shift, every rotation applied to the accumulated basis).
+// A: n x n row-major symmetric (destroyed). w: eigenvalues ascending;
+// Z: n x n row-major with column k the unit eigenvector of w[k].
+void dense_sym_eig(std::vector<double>& A, int n, std::vector<double>& w, std::vector<double>& Z) {
+  Z.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Z[(size_t)i * n + i] = 1.0;
+  std::vector<double> v(n), p(n), q(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    // reflector H = I - beta v v^T mapping A[k+1:, k] to a multiple of e_1
+    double sigma = 0.0;
+    for (int i = k + 2; i < n; ++i) sigma += A[(size_t)i * n + k] * A[(size_t)i * n + k];
+    const double x0 = A[(size_t)(k + 1) * n + k];
+    if (sigma == 0.0) continue;
+    const double mu = std::sqrt(x0 * x0 + sigma);
+    const double v0 = x0 <= 0.0 ? x0 - mu : -sigma / (x0 + mu);
+    const double beta = 2.0 * v0 * v0 / (sigma + v0 * v0);
+    v[k + 1] = 1.0;
+    for (int i = k + 2; i < n; ++i) v[i] = A[(size_t)i * n + k] / v0;
+    // p = beta * A22 v ; w = p - (beta/2)(p^T v) v ; A22 -= v w^T + w v^T
+    for (int i = k + 1; i < n; ++i) {
+      double s = 0.0;
+      const double* row = &A[(size_t)i * n];
+      for (int j = k + 1; j < n; ++j) s += row[j] * v[j];
+      p[i] = beta * s;
+    }
+    double pv = 0.0;
+    for (int i = k + 1; i < n; ++i) pv += p[i] * v[i];
+    for (int i = k + 1; i < n; ++i) q[i] = p[i] - 0.5 * beta * pv * v[i];
+    for (int i = k + 1; i < n; ++i) {
+      double* row = &A[(size_t)i * n];
+      for (int j = k + 1; j < n; ++j) row[j] -= v[i] * q[j] + q[i] * v[j];
+    }
+    const double newsub = mu;  // H x = ||x|| e_1 for either form of v_1
+    A[(size_t)(k + 1) * n + k] = newsub;
+    A[(size_t)k * n + k + 1] = newsub;
+    for (int i = k + 2; i < n; ++i) A[(size_t)i * n + k] = A[(size_t)k * n + i] = 0.0;
+    // Z <- Z H (columns k+1..n-1)
+    for (int i = 0; i < n; ++i) {
+      double* zr = &Z[(size_t)i * n];
+      double s = 0.0;
+      for (int j = k + 1; j < n; ++j) s += zr[j] * v[j];
+      s *= beta;
+      for (int j = k + 1; j < n; ++j) zr[j] -= s * v[j];
+    }
+  }
+  std::vector<double> d(n), e(n, 0.0);
+  for (int i = 0; i < n; ++i) d[i] = A[(size_t)i * n + i];
+  for (int i = 0; i + 1 < n; ++i) e[i] = A[(size_t)(i + 1) * n + i];
+  const double eps = 2.220446049250313e-16;
+  for (int l = 0; l < n; ++l) {
+    for (int iter = 0; iter < 200; ++iter) {
+      int m = l;
+      for (; m < n - 1; ++m)
+        if (std::fabs(e[m]) <= eps * (std::fabs(d[m]) + std::fabs(d[m + 1]))) break;
+      if (m == l) break;
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = pyth(g, 1.0);
+      g = d[m] - d[l] + e[l] / (g + std::copysign(r, g));
+      double s = 1.0, c = 1.0, pp = 0.0;
+      bool deflated = false;
+      for (int i = m - 1; i >= l; --i) {
+        const double f = s * e[i], bb = c * e[i];
+        r = pyth(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {
+          d[i + 1] -= pp;
+          e[m] = 0.0;
+          deflated = true;
+          break;
+        }
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - pp;
+        r = (d[i] - g) * s + 2.0 * c * bb;
+        pp = s * r;
+        d[i + 1] = g + pp;
+        g = c * r - bb;
+        for (int k2 = 0; k2 < n; ++k2) {  // rotate columns i, i+1 of Z
+          double* zr = &Z[(size_t)k2 * n];
+          const double zf = zr[i + 1];
+          zr[i + 1] = s * zr[i] + c * zf;
+          zr[i] = c * zr[i] - s * zf;
+        }
+      }
+      if (deflated) continue;
+      d[l] -= pp;
+      e[l] = g;
+      e[m] = 0.0;
+    }
+  }
+  // sort ascending with the columns of Z
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return d[a] < d[b]; });
+  w.resize(n);
+  std::vector<double> Zs((size_t)n * n);
+  for (int k = 0; k < n; ++k) {
+    w[k] = d[ord[k]];
+    for (int i = 0; i < n; ++i) Zs[(size_t)i * n + k] = Z[(size_t)i * n + ord[k]];
+  }
+  Z.swap(Zs);
 }
 
 }  // namespace flz

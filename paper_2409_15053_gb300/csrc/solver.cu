@@ -370,12 +370,15 @@ flz_status solve(flz_solver* s, cudaStream_t st) {
     };
     {
       // cheap host gate: the leading gate_len pairs must all pass before any GPU work
+      // in batches of 8 from the largest theta down, stopping at the first failure
       const int g_cnt = std::min(gate_len, K);
-      std::vector<int> gidx(order.begin(), order.begin() + g_cnt);
-      std::vector<double> Yg;
-      band_eigenvectors(T, K, r, theta, gidx, Yg, p.seed);
-      for (int t = 0; t < g_cnt && all_small; ++t)
-        if (p_residual(&Yg[(size_t)t * K]) > p_gate) all_small = false;
+      for (int g0 = 0; g0 < g_cnt && all_small; g0 += 8) {
+        std::vector<int> gidx(order.begin() + g0, order.begin() + std::min(g_cnt, g0 + 8));
+        std::vector<double> Yg;
+        band_eigenvectors(T, K, r, theta, gidx, Yg, p.seed + (uint64_t)g0);
+        for (size_t t = 0; t < gidx.size() && all_small; ++t)
+          if (!(p_residual(&Yg[t * K]) <= p_gate)) all_small = false;
+      }
     }
     int walked = 0;
     for (int pos = 0; pos < K && !walk_done && all_small; pos += 16) {
@@ -384,7 +387,7 @@ flz_status solve(flz_solver* s, cudaStream_t st) {
       std::vector<double> Y;
       band_eigenvectors(T, K, r, theta, idx, Y, p.seed + (uint64_t)pos);
       // a pair failing the gate ends the walk before its Ritz vector is formed
-      if (p_residual(&Y[0]) > p_gate) {
+      if (!(p_residual(&Y[0]) <= p_gate)) {
         all_small = false;
         break;
       }
@@ -413,7 +416,7 @@ flz_status solve(flz_solver* s, cudaStream_t st) {
         const double xx = h[t];
         const double lam = h[32 + t];
         const double res = std::sqrt(std::max(h[48 + t], 0.0) / std::max(xx, 1e-300)) / anorm;
-        if (res > p.tol) {
+        if (!(res <= p.tol)) {
           all_small = false;
           walk_done = true;
           break;

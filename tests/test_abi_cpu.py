@@ -118,3 +118,28 @@ def test_laplacian_tridiagonal_closed_form():
     got = flz.flz_band_eigenvalues(T, 1)
     ref = np.sort(2 - 2 * np.cos(np.arange(1, K + 1) * np.pi / (K + 1)))
     assert np.max(np.abs(got - ref)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [1, 3, 40, 200])
+def test_dense_symmetric_eigensolver_matches_numpy(n):
+    rng = np.random.default_rng(n)
+    M = rng.standard_normal((n, n))
+    M = M + M.T
+    w, Z = flz.flz_sym_eig(M)
+    assert np.max(np.abs(w - np.linalg.eigvalsh(M))) < 1e-12 * max(1.0, np.max(np.abs(w)))
+    assert np.max(np.abs(M @ Z - Z * w)) < 1e-12 * max(1.0, np.max(np.abs(w)))
+    assert np.max(np.abs(Z.T @ Z - np.eye(n))) < 1e-13
+
+
+def test_dense_symmetric_eigensolver_on_laplacian_closed_form():
+    K = 80
+    T = 2 * np.eye(K) - np.eye(K, k=1) - np.eye(K, k=-1)
+    w, Z = flz.flz_sym_eig(T)
+    ref = np.sort(2 - 2 * np.cos(np.arange(1, K + 1) * np.pi / (K + 1)))
+    assert np.max(np.abs(w - ref)) < 1e-13
+    # eigenvector k is sin(k i pi/(K+1)) up to sign and norm
+    i = np.arange(1, K + 1)
+    for k in (1, 17, 80):
+        u = np.sin(k * i * np.pi / (K + 1))
+        u /= np.linalg.norm(u)
+        assert abs(abs(u @ Z[:, k - 1]) - 1.0) < 1e-12

@@ -1,0 +1,112 @@
+"""Batches of independent problems (uneven 2D/3D Laplacians with potentials,
+each with its own interval) solved in lockstep, against dense eigensolves of
+every problem: exact counts, eigenvalues within 1e-10 ||A|| (FP64 filter) and
+residuals recomputed on the CPU."""
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+import paper_2409_15053_gb300 as flz
+from synth import laplacian_2d, laplacian_3d_7pt, uneven_batch
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+    assert torch.cuda.is_available()
+
+
+def gap_interval(w, lo, cnt):
+    a = 0.5 * (w[lo - 1] + w[lo]) if lo > 0 else w[0] - 1.0
+    b = 0.5 * (w[lo + cnt - 1] + w[lo + cnt])
+    return a, b
+
+
+def run_batch(csrs, intervals, **kw):
+    hs = [flz.flz_matrix_create_csr(c.n, c.nnz, c.rowptr, c.col, c.val) for c in csrs]
+    p = flz.flz_params_default()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    b = flz.flz_batch_create(hs, [a for a, _ in intervals], [z for _, z in intervals], p)
+    st = flz.flz_batch_solve(b)
+    out = []
+    for i, c in enumerate(csrs):
+        out.append({"vals": flz.flz_batch_get_eigenvalues(b, i), "res": flz.flz_batch_get_residuals(b, i),
+                    "vecs": flz.batch_eigenvectors_host(b, i, c.n), "stats": flz.flz_batch_get_stats(b, i)})
+    flz.flz_batch_destroy(b)
+    for h in hs:
+        flz.flz_matrix_destroy(h)
+    return st, out
+
+
+def check(csrs, intervals, out, tol):
+    for c, (a, z), o in zip(csrs, intervals, out):
+        w = np.linalg.eigvalsh(c.to_dense())
+        ref = w[(w >= a) & (w <= z)]
+        assert o["vals"].shape == ref.shape, (o["vals"].shape, ref.shape, o["stats"])
+        norm_a = max(abs(o["stats"]["lmin"]), abs(o["stats"]["lmax"]))
+        assert np.max(np.abs(o["vals"] - ref)) < 1e-10 * norm_a
+        X = o["vecs"]
+        R = c.to_scipy() @ X - X * o["vals"]
+        assert np.max(np.linalg.norm(R, axis=0)) / norm_a <= tol
+        assert np.max(np.abs(X.T @ X - np.eye(X.shape[1]))) < 1e-10
+
+
+def small_batch(seed, count):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    csrs, intervals = [], []
+    for i in range(count):
+        if i % 2 == 0:
+            s = int(rng.integers(9, 14))
+            c = laplacian_3d_7pt(s, s, s, rng.random(s ** 3))
+        else:
+            s = int(rng.integers(25, 45))
+            c = laplacian_2d(s, s, rng.random(s * s))
+        w = np.linalg.eigvalsh(c.to_dense())
+        cnt = int(rng.integers(10, 25))
+        lo = int(rng.integers(0, 40))
+        csrs.append(c)
+        intervals.append(gap_interval(w, lo, cnt))
+    return csrs, intervals
+
+
+@pytest.mark.parametrize("r", [4, 8])
+def test_batch_fp64_matches_dense(r):
+    csrs, intervals = small_batch(3, 6)
+    st, out = run_batch(csrs, intervals, block_size=r, degree=40, check_every=5)
+    assert st == flz.FLZ_OK
+    check(csrs, intervals, out, 1e-10)
+
+
+def test_batch_autotuned_block_width_and_auto_degree():
+    csrs, intervals = small_batch(5, 4)
+    st, out = run_batch(csrs, intervals, block_size=0, degree=0, check_every=5)
+    assert st == flz.FLZ_OK
+    assert all(o["stats"]["block_size"] in (4, 8, 16) for o in out)
+    check(csrs, intervals, out, 1e-10)
+
+
+def test_batch_of_one_matches_single_solver():
+    csrs, intervals = small_batch(7, 1)
+    st, out = run_batch(csrs, intervals, block_size=4, degree=50, check_every=5)
+    assert st == flz.FLZ_OK
+    check(csrs, intervals, out, 1e-10)
+
+
+def test_batch_rejects_bad_arguments():
+    c = laplacian_2d(10, 10)
+    h = flz.flz_matrix_create_csr(c.n, c.nnz, c.rowptr, c.col, c.val)
+    p = flz.flz_params_default()
+    p.block_size = 3
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_batch_create([h], [0.0], [1.0], p)
+    assert e.value.status == flz.FLZ_ERR_INVALID_ARG
+    p.block_size = 4
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_batch_create([h], [1.0], [0.5], p)
+    assert e.value.status == flz.FLZ_ERR_INVALID_ARG
+    flz.flz_matrix_destroy(h)

@@ -198,3 +198,20 @@ def test_rows_without_stored_diagonal():
     got = run_filter(M, c, e, coeffs, V)
     ref = chebyshev.clenshaw_apply(S, c, e, coeffs, V)
     assert np.max(np.abs(got - ref)) <= bound(csr, c, e, 41, V, U64)
+
+
+@pytest.mark.parametrize("r", [1, 4, 16])
+@pytest.mark.parametrize("precision,u", [(flz.FLZ_PREC_FP64, U64), (flz.FLZ_PREC_FP32, U32)])
+def test_hub_rows_use_the_long_row_tier(r, precision, u):
+    # A power-law graph with i0 = 1 has hubs with thousands of entries, far
+    # above the 256-entry threshold of the row-per-thread kernel.
+    csr = powerlaw_graph_laplacian(20000, seed=11, i0=1)
+    assert np.diff(csr.rowptr).max() > 1000
+    c, e = gershgorin_map(csr)
+    M = Mat(csr)
+    m = 25
+    coeffs = chebyshev.filter_coefficients(-0.95, -0.7, m)
+    V = random_normal_block(csr.n, r, 13)
+    got = run_filter(M, c, e, coeffs, V, precision)
+    ref = chebyshev.clenshaw_apply(csr.to_scipy(), c, e, coeffs, V)
+    assert np.max(np.abs(got - ref)) <= bound(csr, c, e, m, V, u)
