@@ -39,6 +39,10 @@ from synth import laplacian_3d_7pt, random_normal_block  # noqa: E402
 from synth.workloads import CONFIG2  # noqa: E402
 
 METRIC = "eigenpairs/s at residual 1e-8 (3D 7-point Laplacian 100^3 + potential, FP64)"
+# Filter degree of the timed solve: among the degrees 40, 60, 100 and 150 on
+# this workload, 100 gave the shortest time to solution (fewer block steps and
+# reorthogonalizations at a moderate cost per step, as in Tables 2 and 3).
+BENCH_DEGREE = 100
 
 
 def peaks():
@@ -109,10 +113,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def filter_bytes_per_launch(n, nnz, r, s_val=8, s_vec=8, s_acc=8):
-    # CSR once (values + int32 columns + int32 row pointers) and five vector
-    # streams: gather Y_k, read Y_{k-1}, write Y_{k+1}, read and write the sum.
-    return nnz * (s_val + 4) + 4 * (n + 1) + r * n * (3 * s_vec + 2 * s_acc)
+def filter_bytes_per_launch(n, nnz, r, s_val=8, s_vec=8, s_acc=8, recurrence="forward"):
+    # CSR once (values + int32 columns + int32 row pointers) and the vector
+    # streams. Forward: gather Y_k, read Y_{k-1}, write Y_{k+1}, read and
+    # write the sum. Clenshaw: read V, gather B_{k+1}, read B_{k+2}, write B_k.
+    csr = nnz * (s_val + 4) + 4 * (n + 1)
+    if recurrence == "clenshaw":
+        return csr + r * n * 4 * s_vec
+    return csr + r * n * (3 * s_vec + 2 * s_acc)
 
 
 def filter_flops_per_launch(n, nnz, r):
@@ -201,7 +209,7 @@ def config_dict(csr, args):
                         "all eigenpairs in [alpha, beta] at the low end of the spectrum",
             "n": csr.n, "nnz": csr.nnz, "alpha": CONFIG2["alpha"], "beta": CONFIG2["beta"],
             "block_size": args.block_size, "degree": args.degree, "precision": args.precision, "tol": args.tol,
-            "check_every": args.check_every,
+            "check_every": args.check_every, "recurrence": args.recurrence,
             "l2": "flushed (512 MiB write) before each timed step", "parallelism": "single GPU"}
 
 
@@ -211,14 +219,17 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--degree", type=int, default=CONFIG2["degree"])
+    ap.add_argument("--degree", type=int, default=BENCH_DEGREE)
     ap.add_argument("--block-size", type=int, default=4)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16", "df64"])
+    ap.add_argument("--recurrence", default="forward", choices=["forward", "clenshaw"])
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--check-every", type=int, default=CONFIG2["check_every"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP32/BF16-filter solves reported under 'variants'")
     ap.add_argument("--mode", default="solve", choices=["solve", "filter"],
                     help="solve: whole flz_solve per step (default); filter: only flz_filter_apply at the "
                          "solver's shape, for the kernel roofline and profiling")
@@ -243,7 +254,8 @@ def main():
     __graft_entry__.build()
     import paper_2409_15053_gb300 as flz
 
-    prec = {"fp64": flz.FLZ_PREC_FP64, "fp32": flz.FLZ_PREC_FP32, "bf16": flz.FLZ_PREC_BF16}[args.precision]
+    prec = {"fp64": flz.FLZ_PREC_FP64, "fp32": flz.FLZ_PREC_FP32, "bf16": flz.FLZ_PREC_BF16,
+            "df64": flz.FLZ_PREC_DF64}[args.precision]
     csr = make_matrix()
     if args.mode == "filter":
         return filter_mode(flz, torch, csr, prec, args)
@@ -257,6 +269,7 @@ def main():
     p.tol = args.tol
     p.check_every = args.check_every
     p.precision = prec
+    p.recurrence = {"forward": flz.FLZ_REC_FORWARD, "clenshaw": flz.FLZ_REC_CLENSHAW}[args.recurrence]
     p.seed = 1 + rank
     s = flz.flz_solver_create(h, p)
     flz.flz_solver_set_interval(s, alpha, beta)
@@ -304,14 +317,16 @@ def main():
     # solver's own CUDA-event timing of its filter applications.
     launches_filter = st["iters"] * st["degree"]
     ms_per_launch = st["ms_filter"] / max(launches_filter, 1)
-    nbytes = filter_bytes_per_launch(csr.n, csr.nnz, args.block_size)
+    sizes = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "bf16": (2, 2, 4), "df64": (8, 8, 8)}[args.precision]
+    nbytes = filter_bytes_per_launch(csr.n, csr.nnz, args.block_size, *sizes, recurrence=args.recurrence)
     nflops = filter_flops_per_launch(csr.n, csr.nnz, args.block_size)
     hbm, hbm_src = peaks()
     achieved_gbs = nbytes / (ms_per_launch * 1e-3) / 1e9
     achieved_tflops = nflops / (ms_per_launch * 1e-3) / 1e12
     fp64_peak = 1.25  # TFLOP/s: GB300's nominal dense FP64 rate (the FP64 step is bound by it)
     roofline = {
-        "kernel": "cheb_rows_kernel (fused Chebyshev degree step)",
+        "kernel": ("clen_rows_kernel (Clenshaw degree step)" if args.recurrence == "clenshaw"
+                   else "cheb_rows_kernel (fused Chebyshev degree step)"),
         "bound": "alu" if args.precision == "fp64" else "hbm",
         "achieved": achieved_tflops if args.precision == "fp64" else achieved_gbs,
         "peak": fp64_peak if args.precision == "fp64" else hbm,
@@ -322,6 +337,11 @@ def main():
         "hbm_peak_source": hbm_src, "algorithmic_bytes_per_launch": nbytes, "flops_per_launch": nflops,
         "ms_per_launch": ms_per_launch,
     }
+
+    fp64_vals = flz.flz_get_eigenvalues(s).copy()
+    variants = None
+    if not args.no_variants and args.precision == "fp64":
+        variants = variant_leg(flz, torch, h, p, alpha, beta, stream, flush, fp64_vals, args)
 
     e2e = None
     if not args.no_e2e:
@@ -339,9 +359,9 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_time / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[args.precision],
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "df64": "f32x2"}[args.precision],
             "data": "synthetic", "config": config_dict(csr, args), "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": e2e, "gpu_launches": int(sum(x["kernel_launches"] for x in stats_list)), "clocks": clocks,
+            "e2e": e2e, "variants": variants, "gpu_launches": int(sum(x["kernel_launches"] for x in stats_list)), "clocks": clocks,
             "solver": {k: st[k] for k in ("iters", "matvecs", "count", "degree", "checks", "lmin", "lmax",
                                           "max_residual", "ms_bounds", "ms_filter", "ms_orth", "ms_check",
                                           "ms_total", "basis_vectors", "kernel_launches")},
@@ -352,6 +372,59 @@ def main():
         dist.destroy_process_group()
 
 
+def variant_leg(flz, torch, h, p, alpha, beta, stream, flush, ref_vals, args):
+    """Filter variants versus the FP64 forward recurrence on the same workload
+    (everything but the filter stays FP64): double-FP32 (hi + lo FP32 pairs)
+    and the Clenshaw recurrence at the FP64 tolerance, and FP32 / BF16 storage
+    at the residual those reach (1e-6, 1e-3), each with its eigenvalue
+    difference to the FP64 run. Times 2 solves after 1 warm-up, device time per
+    solve. `value` counts pairs with residual <= 1e-8."""
+    out = {}
+    # the reduced-precision filters at the residual they can reach, double-FP32 at the FP64 tolerance
+    F, C = flz.FLZ_REC_FORWARD, flz.FLZ_REC_CLENSHAW
+    for name, prec, tol, rec in (("df64_filter", flz.FLZ_PREC_DF64, p.tol, F),
+                                 ("fp64_clenshaw", flz.FLZ_PREC_FP64, p.tol, C),
+                                 ("df64_clenshaw", flz.FLZ_PREC_DF64, p.tol, C),
+                                 ("fp32_filter", flz.FLZ_PREC_FP32, 1e-6, F),
+                                 ("bf16_filter", flz.FLZ_PREC_BF16, 1e-3, F),
+                                 ("bf16_clenshaw", flz.FLZ_PREC_BF16, 1e-3, C)):
+        q = flz.flz_params_default()
+        for f, _ in q._fields_:
+            setattr(q, f, getattr(p, f))
+        q.precision = prec
+        q.recurrence = rec
+        q.tol = max(tol, p.tol)
+        sv = flz.flz_solver_create(h, q)
+        flz.flz_solver_set_interval(sv, alpha, beta)
+        flz.flz_solve(sv, stream)
+        times, st = [], None
+        for _ in range(2):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = flz.flz_solve(sv, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        vals = flz.flz_get_eigenvalues(sv)
+        res = flz.flz_get_residuals(sv)
+        stats = flz.flz_get_stats(sv)
+        flz.flz_solver_destroy(sv)
+        same = vals.shape == ref_vals.shape
+        out[name] = {
+            "status": flz.flz_status_string(st), "value": float(np.sum(res <= 1e-8)) / float(np.mean(times)),
+            "unit": "eigenpairs/s", "ms_per_solve": 1e3 * float(np.mean(times)), "count": int(vals.shape[0]),
+            "tol": q.tol, "solves_per_s": 1.0 / float(np.mean(times)),
+            "max_abs_eig_diff_vs_fp64": float(np.max(np.abs(vals - ref_vals))) if same and vals.size else None,
+            "max_residual": float(np.max(res)) if res.size else None,
+            "ms_filter": stats["ms_filter"], "ms_orth": stats["ms_orth"], "ms_check": stats["ms_check"],
+            "iters": stats["iters"],
+        }
+    return out
+
+
 def filter_mode(flz, torch, csr, prec, args):
     """Times flz_filter_apply alone (p_m(Ahat) on an n x r block) with CUDA events per call."""
     r, m = args.block_size, args.degree
@@ -359,12 +432,13 @@ def filter_mode(flz, torch, csr, prec, args):
     lmin, lmax = 0.0, 12.5
     c, e = 0.5 * (lmin + lmax), 0.5 * (lmax - lmin)
     coeffs = flz.flz_filter_coefficients(-1.0, (CONFIG2["beta"] - c) / e, m)
+    rec = {"forward": flz.FLZ_REC_FORWARD, "clenshaw": flz.FLZ_REC_CLENSHAW}[args.recurrence]
     V = torch.from_numpy(random_normal_block(csr.n, r, 5)).cuda()
     W = torch.empty_like(V)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
-        flz.flz_filter_apply(h, c, e, coeffs, m, r, V, W, prec, stream)
+        flz.flz_filter_apply(h, c, e, coeffs, m, r, V, W, prec, stream, rec)
     torch.cuda.synchronize()
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     sampler.start()
@@ -374,7 +448,7 @@ def filter_mode(flz, torch, csr, prec, args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        flz.flz_filter_apply(h, c, e, coeffs, m, r, V, W, prec, stream)
+        flz.flz_filter_apply(h, c, e, coeffs, m, r, V, W, prec, stream, rec)
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -382,10 +456,12 @@ def filter_mode(flz, torch, csr, prec, args):
     flz.flz_matrix_destroy(h)
     launches = m + (0 if prec == flz.FLZ_PREC_FP64 else 1)
     ms = float(np.mean(times)) / m
-    sizes = {flz.FLZ_PREC_FP64: (8, 8, 8), flz.FLZ_PREC_FP32: (4, 4, 4), flz.FLZ_PREC_BF16: (2, 2, 4)}[prec]
-    nbytes = filter_bytes_per_launch(csr.n, csr.nnz, r, *sizes)
+    sizes = {flz.FLZ_PREC_FP64: (8, 8, 8), flz.FLZ_PREC_FP32: (4, 4, 4), flz.FLZ_PREC_BF16: (2, 2, 4),
+             flz.FLZ_PREC_DF64: (8, 8, 8)}[prec]
+    nbytes = filter_bytes_per_launch(csr.n, csr.nnz, r, *sizes, recurrence=args.recurrence)
     hbm, src = peaks()
-    print(json.dumps({"mode": "filter", "precision": args.precision, "n": csr.n, "nnz": csr.nnz, "r": r,
+    print(json.dumps({"mode": "filter", "precision": args.precision, "recurrence": args.recurrence,
+                      "n": csr.n, "nnz": csr.nnz, "r": r,
                       "degree": m, "launches_per_apply": launches, "ms_per_apply": float(np.mean(times)),
                       "ms_per_degree": ms, "algorithmic_bytes_per_degree": nbytes,
                       "gbs": nbytes / (ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm, "hbm_frac": nbytes / (ms * 1e-3) / 1e9 / hbm,

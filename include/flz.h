@@ -50,15 +50,32 @@ typedef enum flz_status {
 typedef enum flz_dtype { FLZ_F64 = 0, FLZ_F32 = 1, FLZ_BF16 = 2 } flz_dtype;
 typedef enum flz_memspace { FLZ_HOST = 0, FLZ_DEVICE = 1 } flz_memspace;
 
-/* Arithmetic of the filter recurrence (p(A) applied to a block).
- * FP64: IEEE FP64 storage and arithmetic everywhere (the paper's setting).
- * FP32: matrix values and recurrence vectors stored and combined in FP32; the
- *       filtered block is handed to the Lanczos step in FP64 and everything
- *       after it (reorthogonalization, Rayleigh-Ritz, residuals) is FP64,
- *       followed by FP64 refinement of the converged eigenpairs.
- * BF16: as FP32 but matrix values and recurrence vectors stored in bfloat16
- *       with FP32 accumulation. */
-typedef enum flz_precision { FLZ_PREC_FP64 = 0, FLZ_PREC_FP32 = 1, FLZ_PREC_BF16 = 2 } flz_precision;
+/* Arithmetic of the filter recurrence (p(A) applied to a block); the rest of
+ * the solver (reorthogonalization, Rayleigh-Ritz, Rayleigh quotients,
+ * residuals) is FP64 in every mode.
+ * FP64: IEEE FP64 storage and arithmetic (the paper's setting).
+ * FP32: matrix values and recurrence vectors stored and combined in FP32. The
+ *       filtered Lanczos relation then holds to FP32 rounding, which bounds
+ *       the attainable residual (about 1e-7 relative); eigenvalues come from
+ *       FP64 Rayleigh quotients and are far more accurate than that.
+ * BF16: as FP32 with values and vectors stored in bfloat16, FP32 sums
+ *       (attainable residual about 1e-4).
+ * DF64: double-FP32: every value is a pair of FP32 words (hi + lo, about 48
+ *       significant bits, the same 8 bytes as FP64) combined on the FP32 pipes
+ *       with error-free transformations; residuals reach the FP64 range on
+ *       GPUs whose FP64 rate is a small fraction of their FP32 rate. Not
+ *       available for batches. */
+typedef enum flz_precision { FLZ_PREC_FP64 = 0, FLZ_PREC_FP32 = 1, FLZ_PREC_BF16 = 2, FLZ_PREC_DF64 = 3 } flz_precision;
+
+/* How p_m(Ahat) V is evaluated; both give the same polynomial and differ
+ * only in rounding.
+ * FORWARD:  three-term recurrence T_{i+1} = 2 z T_i - T_{i-1} (eq. def:cheb1)
+ *           with the running sum in the same pass: per degree one pass over A
+ *           and five vector streams (gathered T_i, T_{i-1}, T_{i+1}, sum in/out).
+ * CLENSHAW: the backward recurrence B_k = b_k V + 2 Ahat B_{k+1} - B_{k+2}
+ *           the paper uses (Section 2.2): four vector streams (V, gathered
+ *           B_{k+1}, B_{k+2}, B_k) and no running sum. */
+typedef enum flz_recurrence { FLZ_REC_FORWARD = 0, FLZ_REC_CLENSHAW = 1 } flz_recurrence;
 
 typedef struct flz_matrix flz_matrix;
 typedef struct flz_solver flz_solver;
@@ -78,6 +95,8 @@ typedef struct flz_params {
   int32_t bounds_steps; /* Lanczos vectors for the spectrum bounds (Section 2.2); default 60 */
   uint64_t seed;        /* seed of the random start blocks; default 1 */
   double lmin, lmax;    /* if lmin < lmax these bounds are used and no estimate is made */
+  int32_t damping;      /* 0: plain truncation (Section 2.2, default); 1: Jackson damping g_k b_k */
+  int32_t recurrence;   /* flz_recurrence; default FLZ_REC_FORWARD; batches use FORWARD only */
 } flz_params;
 
 /* Per-solve statistics (the columns of Tables 2 and 3, plus bounds). */
@@ -135,9 +154,8 @@ flz_status flz_matrix_info(const flz_matrix* A, int64_t* n, int64_t* nnz, double
 /* ---- the hot path: p_m((A - cI)/e) applied to a block --------------------- */
 
 /* W = p_m(Ahat) V with Ahat = (A - cI)/e (eq. transf) and
- * p_m = sum_{i=0..m} coeffs[i] T_i (Section 2.2), evaluated by the three-term
- * Chebyshev recurrence T_{i+1} = 2 z T_i - T_{i-1} (eq. def:cheb1) with the
- * running sum accumulated in the same pass over A as each new term.
+ * p_m = sum_{i=0..m} coeffs[i] T_i (Section 2.2), evaluated by the recurrence
+ * `recurrence` selects (flz_recurrence): one kernel pass over A per degree.
  * V, W: device FP64, n x r row-major, must not overlap; 1 <= r <= 16;
  * coeffs: host FP64[degree+1]; degree >= 0; e > 0. precision selects the
  * recurrence arithmetic (flz_precision); W is always FP64. Scratch of
@@ -145,7 +163,8 @@ flz_status flz_matrix_info(const flz_matrix* A, int64_t* n, int64_t* nnz, double
  * matrix handle and reused across calls, so calls on one matrix must not
  * overlap in time. Asynchronous on `stream`. */
 flz_status flz_filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int32_t degree,
-                            int32_t r, const double* V, double* W, int32_t precision, void* stream);
+                            int32_t r, const double* V, double* W, int32_t precision, int32_t recurrence,
+                            void* stream);
 
 /* The same FP64 filter for callers that cannot allocate device memory. (The
  * paper has no counterpart; this is an addition of this library.) Callers
@@ -172,6 +191,11 @@ flz_status flz_filter_apply_noalloc(int64_t n, int64_t nnz, const int32_t* rowpt
  * 2 (sin(i acos a) - sin(i acos b))/(i pi). Host only; out has degree+1 slots.
  * Requires -1 <= alpha < beta <= 1. */
 flz_status flz_filter_coefficients(double alpha, double beta, int32_t degree, double* out);
+/* Jackson damping factors g_0..g_degree (host; out has degree+1 slots):
+ * g_k = ((m-k+1) cos(k pi/(m+1)) + sin(k pi/(m+1)) cot(pi/(m+1))) / (m+1).
+ * The paper truncates without damping; damping (params.damping = 1) removes
+ * the Gibbs overshoot of the filter at the cost of a wider transition. */
+flz_status flz_jackson_factors(int32_t degree, double* out);
 /* Eq. (optimaldegree): least m >= 1 with ||p_m - phi|| < eps ||phi|| in the
  * weighted Chebyshev 2-norm. Host only. CAPACITY if no m <= max_degree fits. */
 flz_status flz_filter_degree(double alpha, double beta, double eps, int32_t max_degree, int32_t* degree);

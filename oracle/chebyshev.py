@@ -103,3 +103,20 @@ def clenshaw_apply(A, c: float, e: float, b: np.ndarray, V: np.ndarray) -> np.nd
     for k in range(len(b) - 1, 0, -1):
         u1, u2 = b[k] * V + 2.0 * apply_mapped(A, c, e, u1) - u2, u1
     return b[0] * V + apply_mapped(A, c, e, u1) - u2
+
+
+def jackson_factors(m: int) -> np.ndarray:
+    """Jackson damping factors g_0..g_m for a degree-m Chebyshev series.
+
+    g_k = ((m - k + 1) cos(k pi/(m+1)) + sin(k pi/(m+1)) cot(pi/(m+1))) / (m + 1).
+    The paper truncates without damping (Section 2.2); damping is an option of
+    this library (FILTLAN-style smoothing of the Gibbs oscillations).
+    """
+    k = np.arange(m + 1, dtype=np.float64)
+    a = np.pi / (m + 1)
+    return ((m - k + 1) * np.cos(k * a) + np.sin(k * a) / np.tan(a)) / (m + 1)
+
+
+def damped_filter_coefficients(alpha: float, beta: float, m: int) -> np.ndarray:
+    """Jackson-damped coefficients g_k b_k of the ideal filter on [alpha, beta]."""
+    return filter_coefficients(alpha, beta, m) * jackson_factors(m)

@@ -35,13 +35,14 @@ FLZ_ERR_NOT_SOLVED = 11
 
 FLZ_F64, FLZ_F32, FLZ_BF16 = 0, 1, 2
 FLZ_HOST, FLZ_DEVICE = 0, 1
-FLZ_PREC_FP64, FLZ_PREC_FP32, FLZ_PREC_BF16 = 0, 1, 2
+FLZ_PREC_FP64, FLZ_PREC_FP32, FLZ_PREC_BF16, FLZ_PREC_DF64 = 0, 1, 2, 3
+FLZ_REC_FORWARD, FLZ_REC_CLENSHAW = 0, 1
 
 # Every symbol include/flz.h declares.
 EXPORTED = (
     "flz_status_string", "flz_last_error", "flz_params_default",
     "flz_matrix_create_csr", "flz_matrix_destroy", "flz_matrix_info",
-    "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_filter_degree", "flz_spectrum_bounds",
+    "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_jackson_factors", "flz_filter_degree", "flz_spectrum_bounds",
     "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_sym_eig", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve",
     "flz_get_count", "flz_get_eigenvalues", "flz_get_eigenvectors", "flz_get_residuals", "flz_get_stats",
     "flz_batch_create", "flz_batch_destroy", "flz_batch_solve", "flz_batch_get_count", "flz_batch_get_eigenvalues",
@@ -55,7 +56,8 @@ class flz_params(ctypes.Structure):
         ("max_degree", ctypes.c_int32), ("tol", ctypes.c_double), ("check_every", ctypes.c_int32),
         ("max_basis", ctypes.c_int32), ("guard", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("bounds_steps", ctypes.c_int32), ("seed", ctypes.c_uint64), ("lmin", ctypes.c_double),
-        ("lmax", ctypes.c_double),
+        ("lmax", ctypes.c_double), ("damping", ctypes.c_int32),
+        ("recurrence", ctypes.c_int32),
     ]
 
 
@@ -103,10 +105,11 @@ def lib() -> ctypes.CDLL:
                                                  ctypes.POINTER(_vp)]),
         "flz_matrix_destroy": (ctypes.c_int, [_vp]),
         "flz_matrix_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _pdbl, _pdbl]),
-        "flz_filter_apply": (ctypes.c_int, [_vp, _dbl, _dbl, _vp, _i32, _i32, _vp, _vp, _i32, _vp]),
+        "flz_filter_apply": (ctypes.c_int, [_vp, _dbl, _dbl, _vp, _i32, _i32, _vp, _vp, _i32, _i32, _vp]),
         "flz_filter_apply_noalloc": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, _dbl, _dbl, _vp, _i32, _i32, _vp,
                                                     _vp, _vp]),
         "flz_filter_coefficients": (ctypes.c_int, [_dbl, _dbl, _i32, _vp]),
+        "flz_jackson_factors": (ctypes.c_int, [_i32, _vp]),
         "flz_filter_degree": (ctypes.c_int, [_dbl, _dbl, _dbl, _i32, ctypes.POINTER(_i32)]),
         "flz_spectrum_bounds": (ctypes.c_int, [_vp, _i32, _i32, _u64, _pdbl, _pdbl, _vp]),
         "flz_band_eigenvalues": (ctypes.c_int, [_i32, _i32, _vp, _vp]),
@@ -200,10 +203,11 @@ def flz_matrix_info(A):
     return n.value, nnz.value, glo.value, ghi.value
 
 
-def flz_filter_apply(A, c, e, coeffs, degree, r, V, W, precision=FLZ_PREC_FP64, stream=None):
+def flz_filter_apply(A, c, e, coeffs, degree, r, V, W, precision=FLZ_PREC_FP64, stream=None,
+                     recurrence=FLZ_REC_FORWARD):
     coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
     _check(lib().flz_filter_apply(A, float(c), float(e), _ptr(coeffs), int(degree), int(r), _ptr(V), _ptr(W),
-                                  int(precision), _stream(stream)))
+                                  int(precision), int(recurrence), _stream(stream)))
 
 
 def flz_filter_apply_noalloc(n, nnz, rowptr, col, val, c, e, coeffs, degree, r, V, W, stream=None):
@@ -216,6 +220,12 @@ def flz_filter_apply_noalloc(n, nnz, rowptr, col, val, c, e, coeffs, degree, r, 
 def flz_filter_coefficients(alpha, beta, degree) -> np.ndarray:
     out = np.empty(int(degree) + 1)
     _check(lib().flz_filter_coefficients(float(alpha), float(beta), int(degree), _ptr(out)))
+    return out
+
+
+def flz_jackson_factors(degree) -> np.ndarray:
+    out = np.empty(int(degree) + 1)
+    _check(lib().flz_jackson_factors(int(degree), _ptr(out)))
     return out
 
 

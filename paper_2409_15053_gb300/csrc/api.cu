@@ -36,6 +36,11 @@ void chebyshev_coefficients(double a, double b, int m, double* out) {
 // Eq. (optimaldegree): least m with ||p_m - phi||^2 < eps^2 ||phi||^2 in the
 // weighted Chebyshev norm, the error by Parseval: ||phi||^2 = acos a - acos b,
 // ||p_m||^2 = pi b_0^2 + (pi/2) sum_{i=1..m} b_i^2. Returns -1 if none <= max_degree.
+void jackson_factors(int m, double* g) {
+  const double a = M_PI / (m + 1);
+  for (int k = 0; k <= m; ++k) g[k] = ((m - k + 1) * std::cos(k * a) + std::sin(k * a) / std::tan(a)) / (m + 1);
+}
+
 int auto_degree(double a, double b, double eps, int max_degree) {
   const double ta = std::acos(a), tb = std::acos(b);
   const double phi2 = ta - tb;
@@ -142,6 +147,8 @@ flz_status flz_params_default(flz_params* p) {
   p->seed = 1;
   p->lmin = 0.0;
   p->lmax = 0.0;
+  p->damping = 0;
+  p->recurrence = FLZ_REC_FORWARD;
   return FLZ_OK;
 }
 
@@ -150,6 +157,13 @@ flz_status flz_filter_coefficients(double alpha, double beta, int32_t degree, do
   if (!out || degree < 0) fail(FLZ_ERR_INVALID_ARG, "out is NULL or degree < 0");
   if (!(alpha >= -1.0 && beta <= 1.0 && alpha < beta)) fail(FLZ_ERR_INVALID_ARG, "need -1 <= alpha < beta <= 1");
   flz::chebyshev_coefficients(alpha, beta, degree, out);
+  FLZ_API_END
+}
+
+flz_status flz_jackson_factors(int32_t degree, double* out) {
+  FLZ_API_BEGIN
+  if (!out || degree < 0) fail(FLZ_ERR_INVALID_ARG, "out is NULL or degree < 0");
+  flz::jackson_factors(degree, out);
   FLZ_API_END
 }
 
@@ -240,16 +254,17 @@ flz_status flz_matrix_info(const flz_matrix* A, int64_t* n, int64_t* nnz, double
 }
 
 flz_status flz_filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int32_t degree, int32_t r,
-                            const double* V, double* W, int32_t precision, void* stream) {
+                            const double* V, double* W, int32_t precision, int32_t recurrence, void* stream) {
   FLZ_API_BEGIN
   if (!A || !coeffs || !V || !W) fail(FLZ_ERR_INVALID_ARG, "null argument");
+  if (recurrence != FLZ_REC_FORWARD && recurrence != FLZ_REC_CLENSHAW) fail(FLZ_ERR_INVALID_ARG, "bad recurrence");
   if (degree < 0 || r < 1 || r > 16 || !(e > 0.0)) fail(FLZ_ERR_INVALID_ARG, "need degree >= 0, 1 <= r <= 16, e > 0");
-  if (precision < FLZ_PREC_FP64 || precision > FLZ_PREC_BF16) fail(FLZ_ERR_INVALID_ARG, "bad precision");
+  if (precision < FLZ_PREC_FP64 || precision > FLZ_PREC_DF64) fail(FLZ_ERR_INVALID_ARG, "bad precision");
   const size_t bytes = sizeof(double) * (size_t)A->n * r;
   const char* v = reinterpret_cast<const char*>(V);
   const char* w = reinterpret_cast<const char*>(W);
   if (v < w + bytes && w < v + bytes) fail(FLZ_ERR_INVALID_ARG, "V and W overlap");
-  flz::filter_apply(A, c, e, coeffs, degree, r, V, W, precision, static_cast<cudaStream_t>(stream));
+  flz::filter_apply(A, c, e, coeffs, degree, r, V, W, precision, recurrence, static_cast<cudaStream_t>(stream));
   FLZ_API_END
 }
 
@@ -303,9 +318,10 @@ flz_status flz_solver_create(flz_matrix* A, const flz_params* params, flz_solver
   else flz_params_default(&p);
   if (p.block_size < 1 || p.block_size > 16 || p.block_size > A->n) fail(FLZ_ERR_INVALID_ARG, "block_size must be in [1, min(16, n)]");
   if (p.degree < 0 || p.max_degree < 1 || p.check_every < 1 || !(p.tol > 0.0) || !(p.degree_eps > 0.0) ||
-      p.bounds_steps < 1 || p.max_basis < 0 || p.guard < 0)
+      p.bounds_steps < 1 || p.max_basis < 0 || p.guard < 0 || p.damping < 0 || p.damping > 1 ||
+      (p.recurrence != FLZ_REC_FORWARD && p.recurrence != FLZ_REC_CLENSHAW))
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
-  if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_BF16) fail(FLZ_ERR_INVALID_ARG, "bad precision");
+  if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_DF64) fail(FLZ_ERR_INVALID_ARG, "bad precision");
   flz_solver* s = new flz_solver();
   s->A = A;
   s->p = p;

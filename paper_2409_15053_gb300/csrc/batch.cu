@@ -859,6 +859,11 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
     if (m < 1) fail(FLZ_ERR_CAPACITY, "problem %d: no degree <= %d meets the degree rule", i, p.max_degree);
     coeffs[i].resize(m + 1);
     chebyshev_coefficients(am, bm, m, coeffs[i].data());
+    if (p.damping == 1) {
+      std::vector<double> g(m + 1);
+      jackson_factors(m, g.data());
+      for (int q = 0; q <= m; ++q) coeffs[i][q] *= g[q];
+    }
     s.c = c;
     s.e = e;
     s.alpha_mapped = am;
@@ -1224,8 +1229,12 @@ flz_status flz_batch_create(int32_t count, flz_matrix* const* mats, const double
   if (!(p.block_size == 0 || p.block_size == 1 || p.block_size == 2 || p.block_size == 4 || p.block_size == 8 ||
         p.block_size == 16))
     fail(FLZ_ERR_INVALID_ARG, "batch block_size must be 0 (autotune) or one of 1, 2, 4, 8, 16");
-  if (p.degree < 0 || p.max_degree < 1 || p.check_every < 1 || !(p.tol > 0.0) || p.bounds_steps < 1)
+  if (p.degree < 0 || p.max_degree < 1 || p.check_every < 1 || !(p.tol > 0.0) || p.bounds_steps < 1 ||
+      p.damping < 0 || p.damping > 1)
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
+  if (p.recurrence != FLZ_REC_FORWARD) fail(FLZ_ERR_INVALID_ARG, "batches use the forward recurrence only");
+  if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_BF16)
+    fail(FLZ_ERR_INVALID_ARG, "batches support the FP64, FP32 and BF16 filters");
   std::unique_ptr<flz_batch> B(new flz_batch());
   B->count = count;
   B->p = p;

@@ -305,6 +305,8 @@ template <>
 __device__ __forceinline__ float round_to<float>(double x) { return (float)x; }
 template <>
 __device__ __forceinline__ __nv_bfloat16 round_to<__nv_bfloat16>(double x) { return __double2bfloat16(x); }
+template <>
+__device__ __forceinline__ dev::dfloat round_to<dev::dfloat>(double x) { return dev::dfloat(x); }
 
 template <class S>
 __global__ void scale_values_kernel(long long n, const int* __restrict__ rowptr, const int* __restrict__ diag_pos,
@@ -490,6 +492,7 @@ void scale_values(const flz_matrix* A, double c, double e, S* out, cudaStream_t 
 template void scale_values<double>(const flz_matrix*, double, double, double*, cudaStream_t);
 template void scale_values<float>(const flz_matrix*, double, double, float*, cudaStream_t);
 template void scale_values<__nv_bfloat16>(const flz_matrix*, double, double, __nv_bfloat16*, cudaStream_t);
+template void scale_values<dev::dfloat>(const flz_matrix*, double, double, dev::dfloat*, cudaStream_t);
 
 flz_status validate_csr(const flz_matrix* A, int check_symmetry) {
   DevBuf<int> flags;

@@ -10,6 +10,51 @@
 namespace flz {
 namespace dev {
 
+using ::fma;  // the dfloat overload below joins the built-in ones, it must not hide them
+
+// Double-FP32 number hi + lo (|lo| <= ulp(hi)/2): about 48 significant bits
+// carried in two FP32 words and combined on the FP32 pipes with error-free
+// transformations (TwoSum, Knuth; TwoProduct via FMA, Ogita-Rump-Oishi).
+struct __align__(8) dfloat {
+  float hi, lo;
+  dfloat() = default;
+  __host__ __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ explicit dfloat(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+#if defined(__CUDACC__)
+
+__device__ __forceinline__ dfloat two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return dfloat(s, e);
+}
+__device__ __forceinline__ dfloat quick_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return dfloat(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+// a * b + c
+__device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  const dfloat s = two_sum(p, c.hi);
+  const float lo = __fadd_rn(__fadd_rn(s.lo, e), c.lo);
+  return quick_two_sum(s.hi, lo);
+}
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) { return fma(a, b, dfloat(0.f, 0.f)); }
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+  const dfloat s = two_sum(a.hi, b.hi);
+  return quick_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, a.lo), b.lo));
+}
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + dfloat(-b.hi, -b.lo); }
+__device__ __forceinline__ dfloat& operator+=(dfloat& a, dfloat b) { return a = a + b; }
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+__device__ __forceinline__ dfloat& operator*=(dfloat& a, dfloat b) { return a = a * b; }
+__device__ __forceinline__ double to_double(dfloat a) { return (double)a.hi + (double)a.lo; }
+
 template <class S>
 struct Arith {
   using type = float;
@@ -18,10 +63,15 @@ template <>
 struct Arith<double> {
   using type = double;
 };
+template <>
+struct Arith<dfloat> {
+  using type = dfloat;
+};
 
 __device__ __forceinline__ double to_arith(double x) { return x; }
 __device__ __forceinline__ float to_arith(float x) { return x; }
 __device__ __forceinline__ float to_arith(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ dfloat to_arith(dfloat x) { return x; }
 
 template <class S>
 __device__ __forceinline__ S from_arith(typename Arith<S>::type x);
@@ -31,6 +81,8 @@ template <>
 __device__ __forceinline__ float from_arith<float>(float x) { return x; }
 template <>
 __device__ __forceinline__ __nv_bfloat16 from_arith<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <>
+__device__ __forceinline__ dfloat from_arith<dfloat>(dfloat x) { return x; }
 
 template <class O, class A>
 __device__ __forceinline__ O store_as(A x) { return static_cast<O>(x); }
@@ -91,6 +143,32 @@ struct RowIO<float, R> {
     } else {
 #pragma unroll
       for (int i = 0; i < R; i += 4) *reinterpret_cast<float4*>(p + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+    }
+  }
+};
+
+template <int R>
+struct RowIO<dfloat, R> {
+  static __device__ __forceinline__ void load(const dfloat* p, dfloat (&v)[R]) {
+    if constexpr (R == 1) {
+      const float2 t = *reinterpret_cast<const float2*>(p);
+      v[0] = dfloat(t.x, t.y);
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; i += 2) {
+        const float4 t = *reinterpret_cast<const float4*>(p + i);
+        v[i] = dfloat(t.x, t.y);
+        v[i + 1] = dfloat(t.z, t.w);
+      }
+    }
+  }
+  static __device__ __forceinline__ void store(dfloat* p, const dfloat (&v)[R]) {
+    if constexpr (R == 1) {
+      *reinterpret_cast<float2*>(p) = make_float2(v[0].hi, v[0].lo);
+    } else {
+#pragma unroll
+      for (int i = 0; i < R; i += 2)
+        *reinterpret_cast<float4*>(p + i) = make_float4(v[i].hi, v[i].lo, v[i + 1].hi, v[i + 1].lo);
     }
   }
 };
@@ -197,6 +275,23 @@ template <int R>
 __device__ __forceinline__ void load_acc(const float* p, float (&v)[R]) {
   RowIO<float, R>::load(p, v);
 }
+template <int R>
+__device__ __forceinline__ void store_acc(double* p, const dfloat (&v)[R]) {
+  double d[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) d[t] = to_double(v[t]);
+  RowIO<double, R>::store(p, d);
+}
+template <int R>
+__device__ __forceinline__ void store_acc(dfloat* p, const dfloat (&v)[R]) {
+  RowIO<dfloat, R>::store(p, v);
+}
+template <int R>
+__device__ __forceinline__ void load_acc(const dfloat* p, dfloat (&v)[R]) {
+  RowIO<dfloat, R>::load(p, v);
+}
+
+#endif  // __CUDACC__
 
 }  // namespace dev
 }  // namespace flz

@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(int n, int s, int ld, in
 
 }  // namespace
 
-int filter_launch_count(int m, int precision) {
+int filter_launch_count(int m, int precision) {  // degree steps + the conversion of V
   if (m <= 0) return 1;
   return m + (precision == FLZ_PREC_FP64 ? 0 : 1);
 }
@@ -393,20 +393,23 @@ const S* scaled(flz_matrix* A, DevBuf<S>& buf, int prec, double c, double e, cud
 }  // namespace
 
 void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m, int r, const double* V,
-                  double* W, int precision, cudaStream_t st) {
+                  double* W, int precision, int recurrence, cudaStream_t st) {
   const size_t nr = (size_t)A->n * r;
   if (m == 0) {
     scale_kernel<<<grid_stride_blocks(nr), 256, 0, st>>>(V, W, coeffs[0], nr);
     FLZ_LAUNCH_CHECK();
     return;
   }
+  const bool clen = recurrence == FLZ_REC_CLENSHAW;
   if (precision == FLZ_PREC_FP64) {
     const double* sv = scaled<double>(A, A->sval64, 0, c, e, st);
     A->ws64.reserve(2 * nr);
     double* ya = A->ws64.p;
     double* yb = A->ws64.p + nr;
-    // the running sum lives in W directly (FP64 output)
-    run_recurrence<double, double, double>(A, sv, coeffs, m, r, V, ya, yb, W, W, st);
+    if (clen)
+      run_clenshaw<double, double>(A, sv, coeffs, m, r, V, ya, yb, W, st);
+    else  // the running sum lives in W directly (FP64 output)
+      run_recurrence<double, double, double>(A, sv, coeffs, m, r, V, ya, yb, W, W, st);
   } else if (precision == FLZ_PREC_FP32) {
     const float* sv = scaled<float>(A, A->sval32, 1, c, e, st);
     A->ws32.reserve(4 * nr);
@@ -416,18 +419,38 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
     float* acc = yb + nr;
     convert_kernel<float><<<grid_stride_blocks(nr), 256, 0, st>>>(V, vs, nr);
     FLZ_LAUNCH_CHECK();
-    run_recurrence<float, float, float>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
+    if (clen)
+      run_clenshaw<float, float>(A, sv, coeffs, m, r, vs, ya, yb, W, st);
+    else
+      run_recurrence<float, float, float>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
   } else if (precision == FLZ_PREC_BF16) {
     const __nv_bfloat16* sv = scaled<__nv_bfloat16>(A, A->sval16, 2, c, e, st);
     A->ws16.reserve(3 * nr);
-    A->ws32.reserve(nr);
     __nv_bfloat16* vs = A->ws16.p;
     __nv_bfloat16* ya = vs + nr;
     __nv_bfloat16* yb = ya + nr;
-    float* acc = A->ws32.p;
     convert_kernel<__nv_bfloat16><<<grid_stride_blocks(nr), 256, 0, st>>>(V, vs, nr);
     FLZ_LAUNCH_CHECK();
-    run_recurrence<__nv_bfloat16, __nv_bfloat16, float>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
+    if (clen) {
+      run_clenshaw<__nv_bfloat16, __nv_bfloat16>(A, sv, coeffs, m, r, vs, ya, yb, W, st);
+    } else {
+      A->ws32.reserve(nr);
+      float* acc = A->ws32.p;
+      run_recurrence<__nv_bfloat16, __nv_bfloat16, float>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
+    }
+  } else if (precision == FLZ_PREC_DF64) {
+    const dfloat* sv = scaled<dfloat>(A, A->svaldf, 3, c, e, st);
+    A->wsdf.reserve(4 * nr);
+    dfloat* vs = A->wsdf.p;
+    dfloat* ya = vs + nr;
+    dfloat* yb = ya + nr;
+    dfloat* acc = yb + nr;
+    convert_kernel<dfloat><<<grid_stride_blocks(nr), 256, 0, st>>>(V, vs, nr);
+    FLZ_LAUNCH_CHECK();
+    if (clen)
+      run_clenshaw<dfloat, dfloat>(A, sv, coeffs, m, r, vs, ya, yb, W, st);
+    else
+      run_recurrence<dfloat, dfloat, dfloat>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
   } else {
     fail(FLZ_ERR_INVALID_ARG, "unknown precision %d", precision);
   }

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "flz.h"
+#include "device_common.cuh"
 
 namespace flz {
 
@@ -99,8 +100,9 @@ struct flz_matrix {
   flz::DevBuf<double> sval64;
   flz::DevBuf<float> sval32;
   flz::DevBuf<__nv_bfloat16> sval16;
-  double sc_c[3] = {0.0, 0.0, 0.0}, sc_e[3] = {0.0, 0.0, 0.0};
-  bool sc_ok[3] = {false, false, false};
+  flz::DevBuf<flz::dev::dfloat> svaldf;  // double-FP32 (hi, lo) values
+  double sc_c[4] = {0.0, 0.0, 0.0, 0.0}, sc_e[4] = {0.0, 0.0, 0.0, 0.0};
+  bool sc_ok[4] = {false, false, false, false};
   double glo = 0.0, ghi = 0.0;         // Gershgorin interval
   int32_t max_row_nnz = 0;
   int32_t max_cta_nnz = 0;             // most stored entries in any 256 consecutive rows
@@ -110,6 +112,7 @@ struct flz_matrix {
   flz::DevBuf<double> ws64;
   flz::DevBuf<float> ws32;
   flz::DevBuf<__nv_bfloat16> ws16;
+  flz::DevBuf<flz::dev::dfloat> wsdf;
 };
 
 // Solver handle: parameters, interval, results of the last solve and workspace.
@@ -135,9 +138,16 @@ constexpr int kLongRow = 256;
 // ---- filter.cu ----------------------------------------------------------------
 // W = p_m((A - cI)/e) V, V and W device FP64 n x r row-major.
 void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m, int r,
-                  const double* V, double* W, int precision, cudaStream_t st);
+                  const double* V, double* W, int precision, int recurrence, cudaStream_t st);
 // Number of kernel launches filter_apply issues for degree m at `precision`.
 int filter_launch_count(int m, int precision);
+// ---- clenshaw.cu ----------------------------------------------------------------
+// W = p_m(Ahat) V by the Clenshaw recurrence with 2 Ahat stored in `val`
+// (MS) and the recurrence vectors in VS; v is V in VS, ba and bb are n x r
+// scratch, m >= 1.
+template <class MS, class VS>
+void run_clenshaw(const flz_matrix* A, const MS* val, const double* b, int m, int r, const VS* v, VS* ba, VS* bb,
+                  double* W, cudaStream_t st);
 // Y = A X for an n x s block with row stride ld (s <= 16), FP64.
 void spmm(const flz_matrix* A, const double* X, double* Y, int s, int ld, cudaStream_t st);
 
@@ -194,6 +204,7 @@ void upper_inverse(const double* R, int s, double* Rinv);
 
 // ---- coefficients (api.cu) --------------------------------------------------------------
 void chebyshev_coefficients(double a, double b, int m, double* out);
+void jackson_factors(int m, double* g);
 int auto_degree(double a, double b, double eps, int max_degree);
 
 }  // namespace flz

@@ -297,6 +297,11 @@ flz_status solve(flz_solver* s, cudaStream_t st) {
   stats.degree = m;
   std::vector<double> coeffs(m + 1);
   chebyshev_coefficients(am, bm, m, coeffs.data());
+  if (p.damping == 1) {
+    std::vector<double> g(m + 1);
+    jackson_factors(m, g.data());
+    for (int k = 0; k <= m; ++k) coeffs[k] *= g[k];
+  }
   const double anorm = std::max(std::fabs(lmin), std::fabs(lmax));
 
   // 4. basis capacity
@@ -323,7 +328,7 @@ flz_status solve(flz_solver* s, cudaStream_t st) {
   P.r = r;
   const int guard = p.guard > 0 ? p.guard : std::max(r, 3);
   auto filt = [&](const double* X, double* Y) {
-    filter_apply(A, c, e, coeffs.data(), m, r, X, Y, p.precision, st);
+    filter_apply(A, c, e, coeffs.data(), m, r, X, Y, p.precision, p.recurrence, st);
   };
   double ms_check = 0.0;
   int64_t prev_count = -1;

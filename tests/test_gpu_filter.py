@@ -1,8 +1,9 @@
 """Parity of the hot path, W = p_m((A - cI)/e) V, against the CPU oracle.
 
-The CUDA kernels evaluate the filter by the forward three-term recurrence
-fused with the running sum; the oracle uses the paper's Clenshaw recurrence.
-Both are the same polynomial, so in FP64 they differ only by rounding.
+The CUDA kernels evaluate the filter either by the forward three-term
+recurrence fused with the running sum or by the Clenshaw recurrence; the
+oracle uses the paper's Clenshaw recurrence in plain FP64 sparse products.
+All are the same polynomial, so in FP64 they differ only by rounding.
 
 Tolerance (FP64): a perturbation of size u in step j of a Chebyshev
 recurrence reaches step k multiplied by a Chebyshev polynomial of the second
@@ -31,6 +32,7 @@ pytestmark = pytest.mark.gpu
 U64 = 2.0 ** -53
 U32 = 2.0 ** -24
 UBF = 2.0 ** -8
+UDF = 2.0 ** -44  # double-FP32: 48 stored bits, a few bits lost per compensated operation
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -51,10 +53,10 @@ class Mat:
             pass
 
 
-def run_filter(M, c, e, coeffs, V, precision=flz.FLZ_PREC_FP64):
+def run_filter(M, c, e, coeffs, V, precision=flz.FLZ_PREC_FP64, rec=flz.FLZ_REC_FORWARD):
     Vd = torch.from_numpy(np.ascontiguousarray(V)).cuda()
     Wd = torch.full_like(Vd, float("nan"))
-    flz.flz_filter_apply(M.h, c, e, coeffs, len(coeffs) - 1, V.shape[1], Vd, Wd, precision)
+    flz.flz_filter_apply(M.h, c, e, coeffs, len(coeffs) - 1, V.shape[1], Vd, Wd, precision, recurrence=rec)
     torch.cuda.synchronize()
     return Wd.cpu().numpy()
 
@@ -73,6 +75,9 @@ def gershgorin_map(csr):
     return 0.5 * (lo + hi), 0.5 * (hi - lo)
 
 
+RECS = [flz.FLZ_REC_FORWARD, flz.FLZ_REC_CLENSHAW]
+REC_IDS = ["forward", "clenshaw"]
+
 CASES = [
     ("lap2d_37x41", lambda: laplacian_2d(37, 41)),
     ("lap3d_pot_13x9x11", lambda: laplacian_3d_7pt(13, 9, 11, 0.5 * np.linspace(0, 1, 1287))),
@@ -83,32 +88,35 @@ CASES = [
 
 @pytest.mark.parametrize("name,make", CASES, ids=[x[0] for x in CASES])
 @pytest.mark.parametrize("r", [1, 2, 3, 4, 5, 8, 16])
-def test_fp64_filter_matches_oracle(name, make, r):
+@pytest.mark.parametrize("rec", RECS, ids=REC_IDS)
+def test_fp64_filter_matches_oracle(name, make, r, rec):
     csr = make()
     c, e = gershgorin_map(csr)
     M = Mat(csr)
     m = 37
     coeffs = chebyshev.filter_coefficients(-0.8, -0.35, m)
     V = random_normal_block(csr.n, r, 100 + r)
-    got = run_filter(M, c, e, coeffs, V)
+    got = run_filter(M, c, e, coeffs, V, rec=rec)
     ref = chebyshev.clenshaw_apply(csr.to_scipy(), c, e, coeffs, V)
     assert np.all(np.isfinite(got))
     assert np.max(np.abs(got - ref)) <= bound(csr, c, e, m, V, U64)
 
 
-@pytest.mark.parametrize("m", [0, 1, 2, 3, 50, 200])
-def test_fp64_filter_degrees(m):
+@pytest.mark.parametrize("m", [0, 1, 2, 3, 4, 50, 200])
+@pytest.mark.parametrize("rec", RECS, ids=REC_IDS)
+def test_fp64_filter_degrees(m, rec):
     csr = laplacian_3d_7pt(12, 12, 12)
     M = Mat(csr)
     coeffs = chebyshev.filter_coefficients(-1.0, -0.9, m)
     V = random_normal_block(csr.n, 4, 7)
-    got = run_filter(M, 6.0, 6.0, coeffs, V)
+    got = run_filter(M, 6.0, 6.0, coeffs, V, rec=rec)
     ref = chebyshev.clenshaw_apply(csr.to_scipy(), 6.0, 6.0, coeffs, V)
     assert np.max(np.abs(got - ref)) <= bound(csr, 6.0, 6.0, m, V, U64)
 
 
 @pytest.mark.parametrize("k", [0, 1, 2, 9, 64])
-def test_single_term_is_cosine_on_a_diagonal_matrix(k):
+@pytest.mark.parametrize("rec", RECS, ids=REC_IDS)
+def test_single_term_is_cosine_on_a_diagonal_matrix(k, rec):
     # T_k(x) = cos(k arccos x): with b = e_k the kernel must return cos(k acos d) * V
     n = 5000
     d = np.cos(np.linspace(0.0, np.pi, n))
@@ -116,7 +124,7 @@ def test_single_term_is_cosine_on_a_diagonal_matrix(k):
     b = np.zeros(k + 1)
     b[k] = 1.0
     V = random_normal_block(n, 4, 1)
-    got = run_filter(M, 0.0, 1.0, b, V)
+    got = run_filter(M, 0.0, 1.0, b, V, rec=rec)
     want = np.cos(k * np.arccos(d))[:, None] * V
     assert np.max(np.abs(got - want)) <= 64 * (k + 1) ** 2 * U64 * np.max(np.abs(V))
 
@@ -140,14 +148,15 @@ def test_laplacian_eigenvector_identity():
     assert np.max(np.abs(got - np.stack(want, axis=1))) < 1e-11
 
 
-@pytest.mark.parametrize("precision,u", [(flz.FLZ_PREC_FP32, U32), (flz.FLZ_PREC_BF16, UBF)])
-def test_reduced_precision_filter_within_bound(precision, u):
+@pytest.mark.parametrize("precision,u", [(flz.FLZ_PREC_FP32, U32), (flz.FLZ_PREC_BF16, UBF), (flz.FLZ_PREC_DF64, UDF)])
+@pytest.mark.parametrize("rec", RECS, ids=REC_IDS)
+def test_reduced_precision_filter_within_bound(precision, u, rec):
     csr = laplacian_3d_7pt(16, 16, 16, 0.5 * np.linspace(0, 1, 4096))
     M = Mat(csr)
     m = 30
     coeffs = chebyshev.filter_coefficients(-1.0, -0.9, m)
     V = random_normal_block(csr.n, 4, 5)
-    got = run_filter(M, 6.25, 6.25, coeffs, V, precision)
+    got = run_filter(M, 6.25, 6.25, coeffs, V, precision, rec)
     ref = chebyshev.clenshaw_apply(csr.to_scipy(), 6.25, 6.25, coeffs, V)
     err = np.max(np.abs(got - ref))
     assert err <= bound(csr, 6.25, 6.25, m, V, u)
@@ -162,9 +171,14 @@ def test_filter_rejects_overlapping_buffers():
     with pytest.raises(flz.FlzError) as e:
         flz.flz_filter_apply(M.h, 4.0, 4.0, np.ones(3), 2, 4, Vd, Vd)
     assert e.value.status == flz.FLZ_ERR_INVALID_ARG
+    Wd = torch.zeros_like(Vd)
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_filter_apply(M.h, 4.0, 4.0, np.ones(3), 2, 4, Vd, Wd, recurrence=2)
+    assert e.value.status == flz.FLZ_ERR_INVALID_ARG
 
 
-def test_full_size_config2_filter_matches_oracle():
+@pytest.mark.parametrize("rec", RECS, ids=REC_IDS)
+def test_full_size_config2_filter_matches_oracle(rec):
     # 100^3 grid (n = 1e6, 6.94e6 nnz), r = 4, the launch shape the solver uses
     rng = np.random.Generator(np.random.PCG64(2025))
     csr = laplacian_3d_7pt(100, 100, 100, 0.5 * rng.random(100 ** 3))
@@ -174,12 +188,13 @@ def test_full_size_config2_filter_matches_oracle():
     c, e = 0.5 * (lmin + lmax), 0.5 * (lmax - lmin)
     coeffs = chebyshev.filter_coefficients(-1.0, (0.2885 - c) / e, m)
     V = random_normal_block(csr.n, 4, 77)
-    got = run_filter(M, c, e, coeffs, V)
+    got = run_filter(M, c, e, coeffs, V, rec=rec)
     ref = chebyshev.clenshaw_apply(csr.to_scipy(), c, e, coeffs, V)
     assert np.max(np.abs(got - ref)) <= bound(csr, c, e, m, V, U64)
 
 
-def test_rows_without_stored_diagonal():
+@pytest.mark.parametrize("rec", RECS, ids=REC_IDS)
+def test_rows_without_stored_diagonal(rec):
     # The filter folds -cI into the stored diagonal; rows that store no a_ii get
     # an explicit zero at creation. A symmetric matrix with most diagonals absent:
     S = laplacian_2d(23, 19).to_scipy().tolil()
@@ -195,14 +210,15 @@ def test_rows_without_stored_diagonal():
     c, e = gershgorin_map(csr)
     coeffs = chebyshev.filter_coefficients(-0.5, 0.1, 41)
     V = random_normal_block(csr.n, 3, 9)
-    got = run_filter(M, c, e, coeffs, V)
+    got = run_filter(M, c, e, coeffs, V, rec=rec)
     ref = chebyshev.clenshaw_apply(S, c, e, coeffs, V)
     assert np.max(np.abs(got - ref)) <= bound(csr, c, e, 41, V, U64)
 
 
 @pytest.mark.parametrize("r", [1, 4, 16])
 @pytest.mark.parametrize("precision,u", [(flz.FLZ_PREC_FP64, U64), (flz.FLZ_PREC_FP32, U32)])
-def test_hub_rows_use_the_long_row_tier(r, precision, u):
+@pytest.mark.parametrize("rec", RECS, ids=REC_IDS)
+def test_hub_rows_use_the_long_row_tier(r, precision, u, rec):
     # A power-law graph with i0 = 1 has hubs with thousands of entries, far
     # above the 256-entry threshold of the row-per-thread kernel.
     csr = powerlaw_graph_laplacian(20000, seed=11, i0=1)
@@ -212,6 +228,37 @@ def test_hub_rows_use_the_long_row_tier(r, precision, u):
     m = 25
     coeffs = chebyshev.filter_coefficients(-0.95, -0.7, m)
     V = random_normal_block(csr.n, r, 13)
-    got = run_filter(M, c, e, coeffs, V, precision)
+    got = run_filter(M, c, e, coeffs, V, precision, rec)
     ref = chebyshev.clenshaw_apply(csr.to_scipy(), c, e, coeffs, V)
     assert np.max(np.abs(got - ref)) <= bound(csr, c, e, m, V, u)
+
+
+@pytest.mark.parametrize("r", [1, 3, 4, 16])
+@pytest.mark.parametrize("rec", RECS, ids=REC_IDS)
+def test_double_fp32_filter_matches_oracle(r, rec):
+    csr = fd4_laplacian_3d(10, gaussian_wells_potential(10, 5, seed=3))
+    c, e = gershgorin_map(csr)
+    M = Mat(csr)
+    m = 80
+    coeffs = chebyshev.filter_coefficients(-0.9, -0.6, m)
+    V = random_normal_block(csr.n, r, 40 + r)
+    got = run_filter(M, c, e, coeffs, V, flz.FLZ_PREC_DF64, rec)
+    ref = chebyshev.clenshaw_apply(csr.to_scipy(), c, e, coeffs, V)
+    assert np.max(np.abs(got - ref)) <= bound(csr, c, e, m, V, UDF)
+
+
+@pytest.mark.parametrize("r", [1, 4])
+@pytest.mark.parametrize("rec", RECS, ids=REC_IDS)
+def test_jackson_damped_filter_matches_oracle(r, rec):
+    # The kernels take any coefficient vector; the damped one comes from the
+    # library's own factors and is checked against the oracle's series.
+    csr = laplacian_3d_7pt(13, 9, 11, 0.5 * np.linspace(0, 1, 1287))
+    c, e = gershgorin_map(csr)
+    m = 90
+    coeffs = flz.flz_filter_coefficients(-0.6, -0.3, m) * flz.flz_jackson_factors(m)
+    ref_coeffs = chebyshev.damped_filter_coefficients(-0.6, -0.3, m)
+    assert np.max(np.abs(coeffs - ref_coeffs)) < 1e-14
+    V = random_normal_block(csr.n, r, 29)
+    W = run_filter(Mat(csr), c, e, coeffs, V, rec=rec)
+    ref = chebyshev.clenshaw_apply(csr.to_scipy(), c, e, ref_coeffs, V)
+    assert np.max(np.abs(W - ref)) < bound(csr, c, e, m, V, U64)

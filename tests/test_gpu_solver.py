@@ -71,12 +71,13 @@ def check_pairs(csr, out, tol):
     assert np.max(np.abs(X.T @ X - np.eye(X.shape[1]))) < 1e-10
 
 
+@pytest.mark.parametrize("rec", [flz.FLZ_REC_FORWARD, flz.FLZ_REC_CLENSHAW], ids=["forward", "clenshaw"])
 @pytest.mark.parametrize("r", [1, 2])
-def test_config1_window_matches_closed_form(r):
+def test_config1_window_matches_closed_form(r, rec):
     csr = laplacian_2d(50, 50)
     lam = lap2d_eigs(50, 50)
     ref = lam[(lam >= CFG1_ALPHA) & (lam <= CFG1_BETA)]
-    out = solve(csr, CFG1_ALPHA, CFG1_BETA, block_size=r, degree=50)
+    out = solve(csr, CFG1_ALPHA, CFG1_BETA, block_size=r, degree=50, recurrence=rec)
     assert out["status"] == flz.FLZ_OK
     assert out["vals"].shape == ref.shape == (20,)
     assert np.max(np.abs(out["vals"] - ref)) < 1e-10 * 8.0
@@ -112,9 +113,18 @@ def test_powerlaw_graph_vs_dense():
     _dense_case(powerlaw_graph_laplacian(2000, seed=7), 40, 15, block_size=4, degree=60)
 
 
-def test_interior_window_block3_vs_dense():
+@pytest.mark.parametrize("rec", [flz.FLZ_REC_FORWARD, flz.FLZ_REC_CLENSHAW], ids=["forward", "clenshaw"])
+def test_interior_window_block3_vs_dense(rec):
     rng = np.random.Generator(np.random.PCG64(8))
-    _dense_case(laplacian_3d_7pt(10, 11, 12, rng.random(1320)), 500, 30, block_size=3, degree=80)
+    _dense_case(laplacian_3d_7pt(10, 11, 12, rng.random(1320)), 500, 30, block_size=3, degree=80, recurrence=rec)
+
+
+def test_jackson_damped_filter_vs_dense():
+    # Damping widens the filter's transition band but keeps p_m in [0, 1]; the
+    # solver must still return every eigenvalue of the window.
+    rng = np.random.Generator(np.random.PCG64(8))
+    out = _dense_case(laplacian_3d_7pt(10, 11, 12, rng.random(1320)), 500, 30, block_size=3, degree=120, damping=1)
+    assert out["stats"]["degree"] == 120
 
 
 def test_count_matches_inertia_midsize():
@@ -180,6 +190,11 @@ def test_call_order_and_capacity_errors():
         flz.flz_get_eigenvalues(s, np.empty(2))
     assert e.value.status == flz.FLZ_ERR_CAPACITY
     flz.flz_solver_destroy(s)
+    p = flz.flz_params_default()
+    p.damping = 2
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_solver_create(h, p)
+    assert e.value.status == flz.FLZ_ERR_INVALID_ARG
     flz.flz_matrix_destroy(h)
 
 
@@ -213,7 +228,11 @@ def test_device_resident_csr_input():
     assert (n, nnz, glo, ghi) == (900, csr.nnz, 0.0, 8.0)
 
 
-def test_full_size_config2_matches_oracle_reference():
+@pytest.mark.parametrize("precision,rec", [(flz.FLZ_PREC_FP64, flz.FLZ_REC_FORWARD), (flz.FLZ_PREC_DF64, flz.FLZ_REC_FORWARD),
+                                           (flz.FLZ_PREC_FP64, flz.FLZ_REC_CLENSHAW),
+                                           (flz.FLZ_PREC_DF64, flz.FLZ_REC_CLENSHAW)],
+                         ids=["fp64-forward", "df64-forward", "fp64-clenshaw", "df64-clenshaw"])
+def test_full_size_config2_matches_oracle_reference(precision, rec):
     # n = 1e6, nnz = 6.94e6, r = 4, m = 60: the benchmark's configuration,
     # against the eigenvalues the CPU oracle computed (tests/golden).
     import json
@@ -224,10 +243,31 @@ def test_full_size_config2_matches_oracle_reference():
     g = CONFIG2["grid"]
     csr = laplacian_3d_7pt(g, g, g, CONFIG2["potential_scale"] * rng.random(g ** 3))
     out = solve(csr, CONFIG2["alpha"], CONFIG2["beta"], block_size=4, degree=CONFIG2["degree"],
-                check_every=CONFIG2["check_every"])
+                check_every=CONFIG2["check_every"], precision=precision, recurrence=rec)
     want = np.array(ref["eigenvalues"])
     assert out["status"] == flz.FLZ_OK
     assert out["vals"].shape == want.shape == (CONFIG2["count"],)
     norm_a = max(abs(out["stats"]["lmin"]), abs(out["stats"]["lmax"]))
     assert np.max(np.abs(out["vals"] - want)) < 1e-10 * norm_a
     check_pairs(csr, out, 1e-10)
+
+
+@pytest.mark.parametrize("precision,tol,eig_tol", [(flz.FLZ_PREC_FP32, 1e-6, 1e-9), (flz.FLZ_PREC_BF16, 1e-3, 2e-3),
+                                                   (flz.FLZ_PREC_DF64, 1e-10, 1e-10)])
+def test_reduced_precision_filter(precision, tol, eig_tol):
+    # The filter runs in FP32 (or BF16 storage with FP32 sums); everything else
+    # is FP64. The filtered Lanczos relation holds only to the filter's
+    # rounding, which bounds the attainable residual (about 1e-7 in FP32); the
+    # Rayleigh quotients are computed with A in FP64, so eigenvalue errors are
+    # of the order of the squared residual. Count exact, residuals <= tol.
+    rng = np.random.Generator(np.random.PCG64(15))
+    csr = laplacian_3d_7pt(14, 14, 14, 0.5 * rng.random(14 ** 3))
+    w = np.linalg.eigvalsh(csr.to_dense())
+    a, b = gap_interval(w, 0, 30)
+    out = solve(csr, a, b, block_size=4, degree=60, precision=precision, tol=tol, check_every=10)
+    ref = w[(w >= a) & (w <= b)]
+    assert out["status"] == flz.FLZ_OK
+    assert out["vals"].shape == ref.shape
+    norm_a = max(abs(out["stats"]["lmin"]), abs(out["stats"]["lmax"]))
+    assert np.max(np.abs(out["vals"] - ref)) < eig_tol * norm_a
+    check_pairs(csr, out, tol)

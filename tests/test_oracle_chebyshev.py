@@ -177,3 +177,29 @@ def test_planted_dropped_term_in_clenshaw_is_caught():
     b = ch.filter_coefficients(-0.2, 0.2, 20)
     pd = sum(b[i] * cheb_T(i, d) for i in range(len(b)))
     assert np.max(np.abs(bad_apply(A, 0.0, 1.0, b, V) - pd[:, None] * V)) > 1e-3
+
+
+def test_jackson_factors_limits():
+    for m in (1, 7, 80):
+        g = ch.jackson_factors(m)
+        assert abs(g[0] - 1.0) < 1e-14
+        assert np.all(np.diff(g) < 0) and g[-1] > 0  # decreasing, positive
+    # large m: g_k -> 1 for fixed k
+    assert abs(ch.jackson_factors(4000)[3] - 1.0) < 1e-5
+
+
+@pytest.mark.parametrize("a,b", [(0.1, 0.3), (-1.0, -0.5), (-0.95, -0.9)])
+def test_jackson_damped_filter_has_no_gibbs_overshoot(a, b):
+    # The Jackson kernel is nonnegative, so the damped series of an indicator
+    # stays in [0, 1]; the plain truncation overshoots by about 9 %.
+    z = np.cos(np.linspace(0.0, np.pi, 20001))
+    for m in (30, 120):
+        damped = ch.clenshaw_scalar(ch.damped_filter_coefficients(a, b, m), z)
+        plain = ch.clenshaw_scalar(ch.filter_coefficients(a, b, m), z)
+        assert damped.min() > -1e-12 and damped.max() < 1.0 + 1e-12
+        assert plain.max() > 1.05 or plain.min() < -0.05
+        # and it still separates: near 1 inside, near 0 far outside
+        mid = 0.5 * (a + b)
+        far = b + 0.5 if b + 0.5 <= 1 else a - 0.5
+        vals = ch.clenshaw_scalar(ch.damped_filter_coefficients(a, b, 400), np.array([mid, far]))
+        assert vals[0] > 0.9 and abs(vals[1]) < 0.05
