@@ -35,8 +35,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synth import laplacian_3d_7pt, random_normal_block  # noqa: E402
-from synth.workloads import CONFIG2  # noqa: E402
+from synth import laplacian_3d_7pt, random_normal_block, uneven_batch  # noqa: E402
+from synth.workloads import BATCH64, CONFIG2  # noqa: E402
 
 METRIC = "eigenpairs/s at residual 1e-8 (3D 7-point Laplacian 100^3 + potential, FP64)"
 # Filter degree of the timed solve: among the degrees 40, 60, 100 and 150 on
@@ -230,7 +230,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32/BF16-filter solves reported under 'variants'")
-    ap.add_argument("--mode", default="solve", choices=["solve", "filter"],
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch-of-64 leg")
+    ap.add_argument("--mode", default="solve", choices=["solve", "filter", "batch"],
                     help="solve: whole flz_solve per step (default); filter: only flz_filter_apply at the "
                          "solver's shape, for the kernel roofline and profiling")
     args = ap.parse_args()
@@ -256,6 +257,9 @@ def main():
 
     prec = {"fp64": flz.FLZ_PREC_FP64, "fp32": flz.FLZ_PREC_FP32, "bf16": flz.FLZ_PREC_BF16,
             "df64": flz.FLZ_PREC_DF64}[args.precision]
+    if args.mode == "batch":
+        print(json.dumps({"mode": "batch", **batch_leg(flz, torch, torch.cuda.current_stream())}))
+        return
     csr = make_matrix()
     if args.mode == "filter":
         return filter_mode(flz, torch, csr, prec, args)
@@ -343,6 +347,10 @@ def main():
     if not args.no_variants and args.precision == "fp64":
         variants = variant_leg(flz, torch, h, p, alpha, beta, stream, flush, fp64_vals, args)
 
+    batch = None
+    if not args.no_batch and rank == 0:
+        batch = batch_leg(flz, torch, stream)
+
     e2e = None
     if not args.no_e2e:
         e2e = e2e_leg(flz, torch, csr, p, alpha, beta, stream, args)
@@ -361,7 +369,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * total_time / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "df64": "f32x2"}[args.precision],
             "data": "synthetic", "config": config_dict(csr, args), "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": e2e, "variants": variants, "gpu_launches": int(sum(x["kernel_launches"] for x in stats_list)), "clocks": clocks,
+            "e2e": e2e, "variants": variants, "batch64": batch, "gpu_launches": int(sum(x["kernel_launches"] for x in stats_list)), "clocks": clocks,
             "solver": {k: st[k] for k in ("iters", "matvecs", "count", "degree", "checks", "lmin", "lmax",
                                           "max_residual", "ms_bounds", "ms_filter", "ms_orth", "ms_check",
                                           "ms_total", "basis_vectors", "kernel_launches")},
@@ -386,8 +394,7 @@ def variant_leg(flz, torch, h, p, alpha, beta, stream, flush, ref_vals, args):
                                  ("fp64_clenshaw", flz.FLZ_PREC_FP64, p.tol, C),
                                  ("df64_clenshaw", flz.FLZ_PREC_DF64, p.tol, C),
                                  ("fp32_filter", flz.FLZ_PREC_FP32, 1e-6, F),
-                                 ("bf16_filter", flz.FLZ_PREC_BF16, 1e-3, F),
-                                 ("bf16_clenshaw", flz.FLZ_PREC_BF16, 1e-3, C)):
+                                 ("bf16_filter", flz.FLZ_PREC_BF16, 1e-3, F)):
         q = flz.flz_params_default()
         for f, _ in q._fields_:
             setattr(q, f, getattr(p, f))
@@ -422,6 +429,94 @@ def variant_leg(flz, torch, h, p, alpha, beta, stream, flush, ref_vals, args):
             "ms_filter": stats["ms_filter"], "ms_orth": stats["ms_orth"], "ms_check": stats["ms_check"],
             "iters": stats["iters"],
         }
+    return out
+
+
+def batch_leg(flz, torch, stream):
+    """The batched form against one-at-a-time FP64 solves on the same GPU.
+
+    Workload: 64 independent 2D/3D Laplacians with U(0,1) potentials, n
+    log-uniform in [1e4, 2e5], each with the interval [0, beta_i] and the
+    eigenvalue counts the CPU oracle computed (tests/golden/batch64_reference.json).
+    Times (CUDA events, after one warm-up solve each): the batch with the FP32
+    filter (tol 1e-6, its attainable residual), the batch with the FP64 filter
+    (tol 1e-10), and the 64 problems solved one after another with the FP64
+    filter (r = 4). Each result is checked against the oracle's counts and
+    eigenvalues."""
+    ref = json.load(open(os.path.join(ROOT, "tests", "golden", "batch64_reference.json")))["problems"]
+    items = uneven_batch(BATCH64["count"], seed=BATCH64["seed"], n_lo=BATCH64["n_lo"], n_hi=BATCH64["n_hi"])
+    hs = [flz.flz_matrix_create_csr(c.n, c.nnz, c.rowptr, c.col, c.val) for c, _, _ in items]
+    alphas = [p["alpha"] for p in ref]
+    betas = [p["beta"] for p in ref]
+    want = [np.array(p["eigenvalues"]) for p in ref]
+    total = int(sum(w.shape[0] for w in want))
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    def score(vals_list, res_list, norms, tol):
+        counts_ok = all(v.shape == w.shape for v, w in zip(vals_list, want))
+        err = max((float(np.max(np.abs(v - w)) / nrm) if v.shape == w.shape and v.size else 0.0)
+                  for v, w, nrm in zip(vals_list, want, norms))
+        good = int(sum(np.sum(r <= tol) for r in res_list))
+        return counts_ok, err, good
+
+    out = {"problems": len(items), "sum_n": int(sum(c.n for c, _, _ in items)), "eigenpairs": total}
+    for name, prec, tol in (("batch_fp32", flz.FLZ_PREC_FP32, 1e-6), ("batch_fp64", flz.FLZ_PREC_FP64, 1e-10)):
+        p = flz.flz_params_default()
+        p.block_size = 0
+        p.degree = 0
+        p.precision = prec
+        p.tol = tol
+        p.check_every = 5
+        bt = flz.flz_batch_create(hs, alphas, betas, p)
+        flz.flz_batch_solve(bt, stream)
+        st, sec = timed(lambda: flz.flz_batch_solve(bt, stream))
+        vals = [flz.flz_batch_get_eigenvalues(bt, i) for i in range(len(items))]
+        res = [flz.flz_batch_get_residuals(bt, i) for i in range(len(items))]
+        stats = [flz.flz_batch_get_stats(bt, i) for i in range(len(items))]
+        norms = [max(abs(x["lmin"]), abs(x["lmax"])) for x in stats]
+        ok, err, good = score(vals, res, norms, tol)
+        out[name] = {"status": flz.flz_status_string(st), "seconds": sec, "eigenpairs_per_s": good / sec,
+                     "tol": tol, "counts_match_oracle": ok, "max_rel_eig_err_vs_oracle": err,
+                     "block_size": stats[0]["block_size"], "max_iters": max(x["iters"] for x in stats)}
+        flz.flz_batch_destroy(bt)
+    p = flz.flz_params_default()
+    p.block_size = 4
+    p.degree = 0
+    p.check_every = 5
+    solvers = []
+    for h, a, z in zip(hs, alphas, betas):
+        sv = flz.flz_solver_create(h, p)
+        flz.flz_solver_set_interval(sv, a, z)
+        flz.flz_solve(sv, stream)
+        solvers.append(sv)
+
+    def all_solves():
+        return [flz.flz_solve(sv, stream) for sv in solvers]
+
+    sts, sec = timed(all_solves)
+    vals = [flz.flz_get_eigenvalues(sv) for sv in solvers]
+    res = [flz.flz_get_residuals(sv) for sv in solvers]
+    norms = []
+    for sv in solvers:
+        x = flz.flz_get_stats(sv)
+        norms.append(max(abs(x["lmin"]), abs(x["lmax"])))
+    ok, err, good = score(vals, res, norms, 1e-10)
+    out["sequential_fp64"] = {"status": "FLZ_OK" if all(x == flz.FLZ_OK for x in sts) else "some not converged",
+                              "seconds": sec, "eigenpairs_per_s": good / sec, "tol": 1e-10,
+                              "counts_match_oracle": ok, "max_rel_eig_err_vs_oracle": err, "block_size": 4}
+    for sv in solvers:
+        flz.flz_solver_destroy(sv)
+    for h in hs:
+        flz.flz_matrix_destroy(h)
     return out
 
 

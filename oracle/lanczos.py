@@ -45,7 +45,8 @@ def lanczos_bounds(A, v0: np.ndarray, steps: int = 60):
     Full reorthogonalization (twice) keeps the basis orthonormal. The extreme
     Ritz values are padded by their residual bounds |beta_k s_k| and the result
     is clamped to the Gershgorin interval, which always contains the spectrum.
-    Returns (lmin, lmax, info).
+    Returns (lmin, lmax, info); info["ritz"] holds all Ritz values, ascending
+    (by Cauchy interlacing the j-th smallest is >= the j-th smallest eigenvalue).
     """
     n = A.shape[0]
     k = min(int(steps), n)
@@ -73,7 +74,8 @@ def lanczos_bounds(A, v0: np.ndarray, steps: int = 60):
     lo = theta[0] - res[0]
     hi = theta[-1] + res[-1]
     g_lo, g_hi = gershgorin_interval(A)
-    return max(lo, g_lo), min(hi, g_hi), {"steps": kk, "theta": (theta[0], theta[-1]), "res": (res[0], res[-1])}
+    return max(lo, g_lo), min(hi, g_hi), {"steps": kk, "theta": (theta[0], theta[-1]), "res": (res[0], res[-1]),
+                                          "ritz": theta}
 
 
 @dataclass

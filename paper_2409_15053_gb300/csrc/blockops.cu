@@ -20,27 +20,57 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kSub = 128;  // rows of W staged in shared memory per sub-chunk
 
+using dev::dfloat;
+
+// Arithmetic of the basis kernels: FP64, or double-FP32 pairs (hi + lo) on the
+// FP32 pipes for a basis stored as dfloat (the FP64 rate is a small fraction
+// of the FP32 rate on this GPU, and these kernels do r FMAs per loaded word).
+template <class T>
+__device__ __forceinline__ T zero_of();
+template <>
+__device__ __forceinline__ double zero_of<double>() { return 0.0; }
+template <>
+__device__ __forceinline__ dfloat zero_of<dfloat>() { return dfloat(0.f, 0.f); }
+__device__ __forceinline__ double ld_ro(const double* p) { return __ldg(p); }
+__device__ __forceinline__ dfloat ld_ro(const dfloat* p) {
+  const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+  return dfloat(t.x, t.y);
+}
+__device__ __forceinline__ double shfl_down(double v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ dfloat shfl_down(dfloat v, int d) {
+  return dfloat(__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d));
+}
+__device__ __forceinline__ double as_double(double x) { return x; }
+__device__ __forceinline__ double as_double(dfloat x) { return dev::to_double(x); }
+template <class T>
+__device__ __forceinline__ T from_double(double x) { return T(x); }
+template <class O, class A>
+__device__ __forceinline__ O out_as(A x) { return x; }
+template <>
+__device__ __forceinline__ double out_as<double, dfloat>(dfloat x) { return dev::to_double(x); }
+
 // Partial C = Q^T W over one row range (blockIdx.x) for a group of basis
 // blocks (blockIdx.y). Warp w handles BPW blocks; lane l owns column
 // a = l % R of rows l / R, l / R + 32/R, ... of the staged sub-chunk.
-template <int R>
-__global__ void __launch_bounds__(kThreads) basis_dot_kernel(const double* __restrict__ Q, int nb, long long n,
-                                                             const double* __restrict__ W, int ldw,
+// T is the storage and arithmetic type of Q and W; partials are FP64.
+template <int R, class T>
+__global__ void __launch_bounds__(kThreads) basis_dot_kernel(const T* __restrict__ Q, int nb, long long n,
+                                                             const T* __restrict__ W, int ldw,
                                                              long long rows_per_cta, double* __restrict__ part) {
   constexpr int BPW = (8 / R) > 0 ? (8 / R) : 1;
   constexpr int RPI = 32 / R;  // rows per warp iteration
-  __shared__ double wsm[kSub * R];
+  __shared__ T wsm[kSub * R];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a = lane % R, k = lane / R;
   const bool active = k < RPI;
   const long long r0 = (long long)blockIdx.x * rows_per_cta;
   const long long r1 = min(n, r0 + rows_per_cta);
   const int bbase = blockIdx.y * (8 * BPW) + warp * BPW;
-  double acc[BPW][R];
+  T acc[BPW][R];
 #pragma unroll
   for (int bi = 0; bi < BPW; ++bi)
 #pragma unroll
-    for (int t = 0; t < R; ++t) acc[bi][t] = 0.0;
+    for (int t = 0; t < R; ++t) acc[bi][t] = zero_of<T>();
   for (long long s0 = r0; s0 < r1; s0 += kSub) {
     const int rows = (int)min((long long)kSub, r1 - s0);
     for (int e = threadIdx.x; e < rows * R; e += kThreads) {
@@ -53,9 +83,9 @@ __global__ void __launch_bounds__(kThreads) basis_dot_kernel(const double* __res
       for (int bi = 0; bi < BPW; ++bi) {
         const int b = bbase + bi;
         if (b < nb) {
-          const double* qb = Q + (size_t)b * n * R + (size_t)s0 * R;
+          const T* qb = Q + (size_t)b * n * R + (size_t)s0 * R;
           for (int i = k; i < rows; i += RPI) {
-            const double q = __ldg(qb + (size_t)i * R + a);
+            const T q = ld_ro(qb + (size_t)i * R + a);
 #pragma unroll
             for (int t = 0; t < R; ++t) acc[bi][t] = fma(q, wsm[i * R + t], acc[bi][t]);
           }
@@ -69,10 +99,10 @@ __global__ void __launch_bounds__(kThreads) basis_dot_kernel(const double* __res
   for (int bi = 0; bi < BPW; ++bi) {
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      double v = acc[bi][t];
+      T v = acc[bi][t];
       for (int s = 1; s < RPI; s <<= 1) {
-        const double o = __shfl_down_sync(0xffffffffu, v, s * R);
-        if ((k & (2 * s - 1)) == 0 && k + s < RPI) v += o;
+        const T o = shfl_down(v, s * R);
+        if ((k & (2 * s - 1)) == 0 && k + s < RPI) v = v + o;
       }
       acc[bi][t] = v;
     }
@@ -84,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) basis_dot_kernel(const double* __res
       if (b < nb) {
         double* p = part + ((size_t)blockIdx.x * nb + b) * R * R + a * R;
 #pragma unroll
-        for (int t = 0; t < R; ++t) p[t] = acc[bi][t];
+        for (int t = 0; t < R; ++t) p[t] = as_double(acc[bi][t]);
       }
     }
   }
@@ -100,27 +130,29 @@ __global__ void sum_partials_kernel(const double* __restrict__ part, int parts, 
 }
 
 // Out[i, t] = beta Out[i, t] + alpha sum_{b,a} Q_b[i, a] C[(b r + a) S + t], one thread per row.
-template <int S>
-__global__ void __launch_bounds__(kThreads) basis_update_kernel(const double* Q, int nb, long long n, int r,
+// T: storage and arithmetic type of Q; O: storage type of Out; C is FP64.
+template <int S, class T, class O>
+__global__ void __launch_bounds__(kThreads) basis_update_kernel(const T* Q, int nb, long long n, int r,
                                                                 const double* __restrict__ C, double alpha,
-                                                                double beta, double* Out, int ldo) {
-  extern __shared__ double csm[];
+                                                                double beta, O* Out, int ldo) {
+  extern __shared__ __align__(16) unsigned char csm_raw[];
+  T* csm = reinterpret_cast<T*>(csm_raw);
   const int cb = max(1, 256 / r);  // basis blocks per staged chunk of C
   const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
-  double acc[S];
+  T acc[S];
 #pragma unroll
-  for (int t = 0; t < S; ++t) acc[t] = 0.0;
+  for (int t = 0; t < S; ++t) acc[t] = zero_of<T>();
   for (int b0 = 0; b0 < nb; b0 += cb) {
     const int nbc = min(cb, nb - b0);
     __syncthreads();
-    for (int e = threadIdx.x; e < nbc * r * S; e += kThreads) csm[e] = C[(size_t)b0 * r * S + e];
+    for (int e = threadIdx.x; e < nbc * r * S; e += kThreads) csm[e] = from_double<T>(C[(size_t)b0 * r * S + e]);
     __syncthreads();
     if (i < n) {
       for (int bl = 0; bl < nbc; ++bl) {
-        const double* qrow = Q + (size_t)(b0 + bl) * n * r + (size_t)i * r;
+        const T* qrow = Q + (size_t)(b0 + bl) * n * r + (size_t)i * r;
         for (int a = 0; a < r; ++a) {
-          const double q = qrow[a];
-          const double* cr = csm + (bl * r + a) * S;
+          const T q = qrow[a];
+          const T* cr = csm + (bl * r + a) * S;
 #pragma unroll
           for (int t = 0; t < S; ++t) acc[t] = fma(q, cr[t], acc[t]);
         }
@@ -128,13 +160,18 @@ __global__ void __launch_bounds__(kThreads) basis_update_kernel(const double* Q,
     }
   }
   if (i < n) {
-    double* o = Out + (size_t)i * ldo;
+    O* o = Out + (size_t)i * ldo;
+    const T al = from_double<T>(alpha);
     if (beta == 0.0) {
 #pragma unroll
-      for (int t = 0; t < S; ++t) o[t] = alpha * acc[t];
+      for (int t = 0; t < S; ++t) o[t] = out_as<O>(al * acc[t]);
     } else {
+      const T be = from_double<T>(beta);
 #pragma unroll
-      for (int t = 0; t < S; ++t) o[t] = fma(alpha, acc[t], beta * o[t]);
+      for (int t = 0; t < S; ++t) {
+        const T old = from_double<T>(as_double(o[t]));
+        o[t] = out_as<O>(fma(al, acc[t], be * old));
+      }
     }
   }
 }
@@ -182,13 +219,14 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 }
 
 // N(0,1) by Box-Muller on two counter-based uniforms (splitmix64 of seed and index).
-__global__ void random_normal_kernel(double* __restrict__ X, long long count, uint64_t seed, uint64_t offset) {
+template <class T>
+__global__ void random_normal_kernel(T* __restrict__ X, long long count, uint64_t seed, uint64_t offset) {
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < count;
        k += (long long)gridDim.x * blockDim.x) {
     const uint64_t base = mix64(seed) ^ (2ull * (offset + (uint64_t)k));
     const double u1 = ((double)(mix64(base) >> 11) + 1.0) * (1.0 / 9007199254740992.0);  // (0, 1]
     const double u2 = (double)(mix64(base + 1) >> 11) * (1.0 / 9007199254740992.0);
-    X[k] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    X[k] = from_double<T>(sqrt(-2.0 * log(u1)) * cospi(2.0 * u2));
   }
 }
 
@@ -338,26 +376,26 @@ DotShape dot_shape(int64_t n, int nb, int r) {
   return d;
 }
 
-template <int R>
-void launch_basis_dot(const double* Q, int nb, int64_t n, const double* W, int ldw, double* C, double* part,
-                      cudaStream_t st) {
+template <int R, class T>
+void launch_basis_dot(const T* Q, int nb, int64_t n, const T* W, int ldw, double* C, double* part, cudaStream_t st) {
   const DotShape d = dot_shape(n, nb, R);
-  basis_dot_kernel<R><<<dim3(d.gx, d.gy), kThreads, 0, st>>>(Q, nb, n, W, ldw, d.rows_per_cta, part);
+  basis_dot_kernel<R, T><<<dim3(d.gx, d.gy), kThreads, 0, st>>>(Q, nb, n, W, ldw, d.rows_per_cta, part);
   FLZ_LAUNCH_CHECK();
   const size_t len = (size_t)nb * R * R;
   sum_partials_kernel<<<gs_blocks((long long)len), 256, 0, st>>>(part, d.gx, len, C);
   FLZ_LAUNCH_CHECK();
 }
 
-template <int S>
-void launch_basis_update(const double* Q, int nb, int64_t n, int r, const double* C, double alpha, double beta,
-                         double* Out, int ldo, cudaStream_t st) {
+template <int S, class T, class O>
+void launch_basis_update(const T* Q, int nb, int64_t n, int r, const double* C, double alpha, double beta, O* Out,
+                         int ldo, cudaStream_t st) {
   const int cb = std::max(1, 256 / r);
-  const size_t smem = sizeof(double) * (size_t)std::min(cb, nb) * r * S;
+  const size_t smem = sizeof(T) * (size_t)std::min(cb, nb) * r * S;
   if (smem > 48 * 1024)
-    FLZ_CUDA(cudaFuncSetAttribute(basis_update_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FLZ_CUDA(cudaFuncSetAttribute(basis_update_kernel<S, T, O>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
   const unsigned grid = (unsigned)((n + kThreads - 1) / kThreads);
-  basis_update_kernel<S><<<grid, kThreads, smem, st>>>(Q, nb, n, r, C, alpha, beta, Out, ldo);
+  basis_update_kernel<S, T, O><<<grid, kThreads, smem, st>>>(Q, nb, n, r, C, alpha, beta, Out, ldo);
   FLZ_LAUNCH_CHECK();
 }
 
@@ -374,38 +412,67 @@ size_t basis_dot_scratch(int64_t n, int nb, int r, int s) {
   return best;
 }
 
-#define FLZ_DISPATCH_16(X, FN, ...)  \
-  switch (X) {                       \
-    case 1: FN<1>(__VA_ARGS__); break;   \
-    case 2: FN<2>(__VA_ARGS__); break;   \
-    case 3: FN<3>(__VA_ARGS__); break;   \
-    case 4: FN<4>(__VA_ARGS__); break;   \
-    case 5: FN<5>(__VA_ARGS__); break;   \
-    case 6: FN<6>(__VA_ARGS__); break;   \
-    case 7: FN<7>(__VA_ARGS__); break;   \
-    case 8: FN<8>(__VA_ARGS__); break;   \
-    case 9: FN<9>(__VA_ARGS__); break;   \
-    case 10: FN<10>(__VA_ARGS__); break; \
-    case 11: FN<11>(__VA_ARGS__); break; \
-    case 12: FN<12>(__VA_ARGS__); break; \
-    case 13: FN<13>(__VA_ARGS__); break; \
-    case 14: FN<14>(__VA_ARGS__); break; \
-    case 15: FN<15>(__VA_ARGS__); break; \
-    case 16: FN<16>(__VA_ARGS__); break; \
+// Runs STMT with the compile-time width K = X (1..16).
+#define FLZ_WITH_WIDTH(X, STMT) \
+  switch (X) { \
+    case 1: { constexpr int K = 1; STMT; } break; \
+    case 2: { constexpr int K = 2; STMT; } break; \
+    case 3: { constexpr int K = 3; STMT; } break; \
+    case 4: { constexpr int K = 4; STMT; } break; \
+    case 5: { constexpr int K = 5; STMT; } break; \
+    case 6: { constexpr int K = 6; STMT; } break; \
+    case 7: { constexpr int K = 7; STMT; } break; \
+    case 8: { constexpr int K = 8; STMT; } break; \
+    case 9: { constexpr int K = 9; STMT; } break; \
+    case 10: { constexpr int K = 10; STMT; } break; \
+    case 11: { constexpr int K = 11; STMT; } break; \
+    case 12: { constexpr int K = 12; STMT; } break; \
+    case 13: { constexpr int K = 13; STMT; } break; \
+    case 14: { constexpr int K = 14; STMT; } break; \
+    case 15: { constexpr int K = 15; STMT; } break; \
+    case 16: { constexpr int K = 16; STMT; } break; \
     default: fail(FLZ_ERR_INVALID_ARG, "block width %d out of range 1..16", (int)(X)); \
   }
 
-void basis_dot(const double* Q, int nb, int64_t n, int r, const double* W, int s, int ldw, double* C,
-               double* part, cudaStream_t st) {
+namespace {
+
+template <class T>
+void basis_dot_t(const T* Q, int nb, int64_t n, int r, const T* W, int s, int ldw, double* C, double* part,
+                 cudaStream_t st) {
   if (s != r) fail(FLZ_ERR_INVALID_ARG, "basis_dot needs s == r");
   if (nb <= 0) return;
-  FLZ_DISPATCH_16(r, launch_basis_dot, Q, nb, n, W, ldw, C, part, st);
+  FLZ_WITH_WIDTH(r, (launch_basis_dot<K, T>(Q, nb, n, W, ldw, C, part, st)));
+}
+
+template <class T, class O>
+void basis_update_t(const T* Q, int nb, int64_t n, int r, const double* C, int s, double alpha, double beta, O* Out,
+                    int ldo, cudaStream_t st) {
+  if (nb <= 0) return;
+  FLZ_WITH_WIDTH(s, (launch_basis_update<K, T, O>(Q, nb, n, r, C, alpha, beta, Out, ldo, st)));
+}
+
+}  // namespace
+
+void basis_dot(const double* Q, int nb, int64_t n, int r, const double* W, int s, int ldw, double* C,
+               double* part, cudaStream_t st) {
+  basis_dot_t<double>(Q, nb, n, r, W, s, ldw, C, part, st);
+}
+void basis_dot(const dfloat* Q, int nb, int64_t n, int r, const dfloat* W, int s, int ldw, double* C,
+               double* part, cudaStream_t st) {
+  basis_dot_t<dfloat>(Q, nb, n, r, W, s, ldw, C, part, st);
 }
 
 void basis_update(const double* Q, int nb, int64_t n, int r, const double* C, int s, double alpha, double beta,
                   double* Out, int ldo, cudaStream_t st) {
-  if (nb <= 0) return;
-  FLZ_DISPATCH_16(s, launch_basis_update, Q, nb, n, r, C, alpha, beta, Out, ldo, st);
+  basis_update_t<double, double>(Q, nb, n, r, C, s, alpha, beta, Out, ldo, st);
+}
+void basis_update(const dfloat* Q, int nb, int64_t n, int r, const double* C, int s, double alpha, double beta,
+                  dfloat* Out, int ldo, cudaStream_t st) {
+  basis_update_t<dfloat, dfloat>(Q, nb, n, r, C, s, alpha, beta, Out, ldo, st);
+}
+void basis_update(const dfloat* Q, int nb, int64_t n, int r, const double* C, int s, double alpha, double beta,
+                  double* Out, int ldo, cudaStream_t st) {
+  basis_update_t<dfloat, double>(Q, nb, n, r, C, s, alpha, beta, Out, ldo, st);
 }
 
 size_t column_sums_scratch(int64_t n, int s) {
@@ -425,7 +492,11 @@ void column_sums(const double* X, const double* Y, const double* lam, int64_t n,
 }
 
 void random_normal(double* X, int64_t count, uint64_t seed, uint64_t offset, cudaStream_t st) {
-  random_normal_kernel<<<gs_blocks(count), 256, 0, st>>>(X, count, seed, offset);
+  random_normal_kernel<double><<<gs_blocks(count), 256, 0, st>>>(X, count, seed, offset);
+  FLZ_LAUNCH_CHECK();
+}
+void random_normal(dfloat* X, int64_t count, uint64_t seed, uint64_t offset, cudaStream_t st) {
+  random_normal_kernel<dfloat><<<gs_blocks(count), 256, 0, st>>>(X, count, seed, offset);
   FLZ_LAUNCH_CHECK();
 }
 

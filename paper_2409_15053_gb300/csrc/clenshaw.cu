@@ -58,10 +58,12 @@ __global__ void __launch_bounds__(kRows) clen_rows_kernel(
     }
     __syncthreads();
   }
+  allow_dependents();
   if (row >= n) return;
   const int jb = __ldg(rowptr + row);
   const int je = __ldg(rowptr + row + 1);
   if (je - jb > long_row) return;  // rows longer than long_row belong to clen_long_kernel
+  grid_dependency_wait();  // B_{k+1}, B_{k+2} are earlier launches' output
   A base[R];
   load_row<VS, R>(v + (size_t)row * R, base);
 #pragma unroll
@@ -208,9 +210,10 @@ struct Launch {
   void* out;
   double alpha, g;
   bool unit, to_w;
+  bool dependent;  // follows another launch of this recurrence on the stream
 };
 
-template <int R, class MS, class VS>
+template <int R, class MS, class VS, class WT>
 void launch_rows(const flz_matrix* A, const MS* val, const VS* v, const Launch& L, cudaStream_t st) {
   using Ar = typename Arith<VS>::type;
   const int n = (int)A->n;
@@ -223,18 +226,25 @@ void launch_rows(const flz_matrix* A, const MS* val, const VS* v, const Launch& 
   const VS* z = static_cast<const VS*>(L.z);
   const Ar al = Ar(L.alpha), g = Ar(L.g);
   if (L.to_w) {
-    double* out = static_cast<double*>(L.out);
-    clen_rows_kernel<R, MS, VS, double, false><<<grid, kRows, smem, st>>>(n, cap, thr, A->rowptr.p, A->col.p, val, x, v, z, out, al, g);
+    WT* out = static_cast<WT*>(L.out);
+    if (L.dependent)
+      launch_dependent(clen_rows_kernel<R, MS, VS, WT, false>, grid, kRows, smem, st, n, cap, thr, A->rowptr.p,
+                       A->col.p, val, x, v, z, out, al, g);
+    else
+      clen_rows_kernel<R, MS, VS, WT, false><<<grid, kRows, smem, st>>>(n, cap, thr, A->rowptr.p, A->col.p, val, x, v, z, out, al, g);
     FLZ_LAUNCH_CHECK();
     if (nl) {
-      clen_long_kernel<R, MS, VS, double><<<nl, kRows, 0, st>>>(A->long_rows.p, A->rowptr.p, A->col.p, val, x, v, z, out, al, g);
+      clen_long_kernel<R, MS, VS, WT><<<nl, kRows, 0, st>>>(A->long_rows.p, A->rowptr.p, A->col.p, val, x, v, z, out, al, g);
       FLZ_LAUNCH_CHECK();
     }
     return;
   }
   VS* out = static_cast<VS*>(L.out);
   if (L.unit) {
-    clen_rows_kernel<R, MS, VS, VS, true><<<grid, kRows, smem, st>>>(n, cap, thr, A->rowptr.p, A->col.p, val, x, v, z, out, al, g);
+    // launches after the first overlap their CSR staging with the previous
+    // launch's tail (programmatic dependent launch)
+    launch_dependent(clen_rows_kernel<R, MS, VS, VS, true>, grid, kRows, smem, st, n, cap, thr, A->rowptr.p, A->col.p,
+                     val, x, v, z, out, al, g);
   } else {
     clen_rows_kernel<R, MS, VS, VS, false><<<grid, kRows, smem, st>>>(n, cap, thr, A->rowptr.p, A->col.p, val, x, v, z, out, al, g);
   }
@@ -245,7 +255,7 @@ void launch_rows(const flz_matrix* A, const MS* val, const VS* v, const Launch& 
   }
 }
 
-template <class MS, class VS>
+template <class MS, class VS, class WT>
 void launch_lanes(const flz_matrix* A, const MS* val, int r, const VS* v, const Launch& L, cudaStream_t st) {
   using Ar = typename Arith<VS>::type;
   const int n = (int)A->n;
@@ -256,8 +266,8 @@ void launch_lanes(const flz_matrix* A, const MS* val, int r, const VS* v, const 
   const VS* z = static_cast<const VS*>(L.z);
   const Ar al = Ar(L.alpha), g = Ar(L.g);
   if (L.to_w) {
-    clen_lanes_kernel<MS, VS, double><<<grid, kLanes, 0, st>>>(n, r, rpw, A->rowptr.p, A->col.p, val, x, v, z,
-                                                               static_cast<double*>(L.out), al, g);
+    clen_lanes_kernel<MS, VS, WT><<<grid, kLanes, 0, st>>>(n, r, rpw, A->rowptr.p, A->col.p, val, x, v, z,
+                                                           static_cast<WT*>(L.out), al, g);
   } else {
     clen_lanes_kernel<MS, VS, VS><<<grid, kLanes, 0, st>>>(n, r, rpw, A->rowptr.p, A->col.p, val, x, v, z,
                                                            static_cast<VS*>(L.out), al, g);
@@ -269,62 +279,64 @@ inline bool aligned_to(const void* p, size_t a) { return (reinterpret_cast<uintp
 
 }  // namespace
 
-template <class MS, class VS>
+template <class MS, class VS, class WT>
 void run_clenshaw(const flz_matrix* A, const MS* val, const double* b, int m, int r, const VS* v, VS* ba, VS* bb,
-                  double* W, cudaStream_t st) {
+                  WT* W, cudaStream_t st) {
   const bool pow2 = r == 1 || r == 2 || r == 4 || r == 8 || r == 16;
   const size_t av = std::min<size_t>(16, r * sizeof(VS));
-  const size_t aw = std::min<size_t>(16, r * sizeof(double));
+  const size_t aw = std::min<size_t>(16, r * sizeof(WT));
   const bool rows = pow2 && A->max_cta_nnz > 0 && aligned_to(v, av) && aligned_to(ba, av) && aligned_to(bb, av) &&
                     aligned_to(W, aw);
   auto go = [&](const Launch& L) {
     if (!rows) {
-      launch_lanes<MS, VS>(A, val, r, v, L, st);
+      launch_lanes<MS, VS, WT>(A, val, r, v, L, st);
       return;
     }
     switch (r) {
-      case 1: launch_rows<1, MS, VS>(A, val, v, L, st); break;
-      case 2: launch_rows<2, MS, VS>(A, val, v, L, st); break;
-      case 4: launch_rows<4, MS, VS>(A, val, v, L, st); break;
-      case 8: launch_rows<8, MS, VS>(A, val, v, L, st); break;
-      default: launch_rows<16, MS, VS>(A, val, v, L, st); break;
+      case 1: launch_rows<1, MS, VS, WT>(A, val, v, L, st); break;
+      case 2: launch_rows<2, MS, VS, WT>(A, val, v, L, st); break;
+      case 4: launch_rows<4, MS, VS, WT>(A, val, v, L, st); break;
+      case 8: launch_rows<8, MS, VS, WT>(A, val, v, L, st); break;
+      default: launch_rows<16, MS, VS, WT>(A, val, v, L, st); break;
     }
   };
   if (m == 1) {
-    go({v, nullptr, W, b[0], 0.5 * b[1], false, true});
+    go({v, nullptr, W, b[0], 0.5 * b[1], false, true, false});
     return;
   }
   // B_{m-1} = b_{m-1} V + b_m (2 Ahat) V
-  go({v, nullptr, ba, b[m - 1], b[m], false, false});
+  go({v, nullptr, ba, b[m - 1], b[m], false, false, false});
   const VS* cur = ba;   // B_{k+1}
   VS* prev = nullptr;   // B_{k+2} (B_m = b_m V is implicit)
   for (int k = m - 2; k >= 1; --k) {
     VS* out;
     if (k == m - 2) {
       out = bb;
-      go({cur, nullptr, out, b[k] - b[m], 1.0, true, false});
+      go({cur, nullptr, out, b[k] - b[m], 1.0, true, false, true});
     } else {
       out = prev;  // B_k overwrites B_{k+2}
-      go({cur, prev, out, b[k], 1.0, true, false});
+      go({cur, prev, out, b[k], 1.0, true, false, true});
     }
     prev = const_cast<VS*>(cur);
     cur = out;
   }
   if (m == 2) {
-    go({cur, nullptr, W, b[0] - b[2], 0.5, false, true});
+    go({cur, nullptr, W, b[0] - b[2], 0.5, false, true, true});
   } else {
-    go({cur, prev, W, b[0], 0.5, false, true});
+    go({cur, prev, W, b[0], 0.5, false, true, true});
   }
 }
 
-template void run_clenshaw<double, double>(const flz_matrix*, const double*, const double*, int, int, const double*,
-                                           double*, double*, double*, cudaStream_t);
-template void run_clenshaw<float, float>(const flz_matrix*, const float*, const double*, int, int, const float*,
-                                         float*, float*, double*, cudaStream_t);
-template void run_clenshaw<__nv_bfloat16, __nv_bfloat16>(const flz_matrix*, const __nv_bfloat16*, const double*, int,
-                                                         int, const __nv_bfloat16*, __nv_bfloat16*, __nv_bfloat16*,
-                                                         double*, cudaStream_t);
-template void run_clenshaw<dfloat, dfloat>(const flz_matrix*, const dfloat*, const double*, int, int, const dfloat*,
-                                           dfloat*, dfloat*, double*, cudaStream_t);
+template void run_clenshaw<double, double, double>(const flz_matrix*, const double*, const double*, int, int,
+                                                   const double*, double*, double*, double*, cudaStream_t);
+template void run_clenshaw<float, float, double>(const flz_matrix*, const float*, const double*, int, int, const float*,
+                                                 float*, float*, double*, cudaStream_t);
+template void run_clenshaw<__nv_bfloat16, __nv_bfloat16, double>(const flz_matrix*, const __nv_bfloat16*,
+                                                                 const double*, int, int, const __nv_bfloat16*,
+                                                                 __nv_bfloat16*, __nv_bfloat16*, double*, cudaStream_t);
+template void run_clenshaw<dfloat, dfloat, double>(const flz_matrix*, const dfloat*, const double*, int, int,
+                                                   const dfloat*, dfloat*, dfloat*, double*, cudaStream_t);
+template void run_clenshaw<dfloat, dfloat, dfloat>(const flz_matrix*, const dfloat*, const double*, int, int,
+                                                   const dfloat*, dfloat*, dfloat*, dfloat*, cudaStream_t);
 
 }  // namespace flz

@@ -55,6 +55,15 @@ __device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.
 __device__ __forceinline__ dfloat& operator*=(dfloat& a, dfloat b) { return a = a * b; }
 __device__ __forceinline__ double to_double(dfloat a) { return (double)a.hi + (double)a.lo; }
 
+// Programmatic dependent launch (sm_90+): a kernel launched with programmatic
+// stream serialization may start while its predecessor drains. It must not
+// read anything the predecessor writes before grid_dependency_wait(), which
+// returns once the predecessor has completed and its writes are visible (a
+// no-op for a normal launch). allow_dependents() lets the next kernel be
+// scheduled once every CTA of this grid has started.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 template <class S>
 struct Arith {
   using type = float;

@@ -105,10 +105,12 @@ __global__ void __launch_bounds__(kRows) cheb_rows_kernel(
     }
     __syncthreads();
   }
+  allow_dependents();
   if (row >= n) return;
   const int jb = __ldg(rowptr + row);
   const int je = __ldg(rowptr + row + 1);
   if (je - jb > long_row) return;  // rows longer than long_row belong to cheb_long_kernel
+  grid_dependency_wait();  // the vectors below are the previous degree's output
   A s[R];
   A acc[R];
   if (FIRST) {
@@ -227,7 +229,8 @@ __global__ void convert_kernel(const double* __restrict__ in, S* __restrict__ ou
     out[i] = from_arith<S>((typename Arith<S>::type)in[i]);
 }
 
-__global__ void scale_kernel(const double* __restrict__ in, double* __restrict__ out, double s, size_t count) {
+template <class T>
+__global__ void scale_kernel(const T* __restrict__ in, T* __restrict__ out, T s, size_t count) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
     out[i] = s * in[i];
 }
@@ -243,16 +246,16 @@ inline unsigned grid_stride_blocks(size_t count) {
   return (unsigned)std::min<size_t>(b, 152 * 16);
 }
 
-template <class MS, class VS, class AccT>
+template <class MS, class VS, class AccT, class WT>
 void run_lanes(const flz_matrix* A, const MS* val, const double* b, int m, int r, const VS* v, VS* ya, VS* yb,
-               AccT* acc, double* W, cudaStream_t st) {
+               AccT* acc, WT* W, cudaStream_t st) {
   using Ar = typename Arith<VS>::type;
   const int n = (int)A->n;
   const int rpw = 32 / r;
   const unsigned grid = grid_for_rows(n, r);
   // step 0: Y_1 = Ahat V, acc = b0 V + b1 Y_1
   if (m == 1) {
-    cheb_step_kernel<MS, VS, AccT, double, true><<<grid, kThreads, 0, st>>>(
+    cheb_step_kernel<MS, VS, AccT, WT, true><<<grid, kThreads, 0, st>>>(
         n, r, rpw, A->rowptr.p, A->col.p, val, v, nullptr, ya, nullptr, W, Ar(b[0]), Ar(b[1]));
     FLZ_LAUNCH_CHECK();
     return;
@@ -267,7 +270,7 @@ void run_lanes(const flz_matrix* A, const MS* val, const double* b, int m, int r
   for (int k = 1; k < m; ++k) {
     VS* next = (k == 1) ? yb : const_cast<VS*>(prev);
     if (k + 1 == m) {
-      cheb_step_kernel<MS, VS, AccT, double, false><<<grid, kThreads, 0, st>>>(
+      cheb_step_kernel<MS, VS, AccT, WT, false><<<grid, kThreads, 0, st>>>(
           n, r, rpw, A->rowptr.p, A->col.p, val, cur, prev, next, acc, W, Ar(0), Ar(b[k + 1]));
     } else {
       cheb_step_kernel<MS, VS, AccT, AccT, false><<<grid, kThreads, 0, st>>>(
@@ -279,9 +282,9 @@ void run_lanes(const flz_matrix* A, const MS* val, const double* b, int m, int r
   }
 }
 
-template <int R, class MS, class VS, class AccT>
+template <int R, class MS, class VS, class AccT, class WT>
 void run_rows(const flz_matrix* A, const MS* val, const double* b, int m, const VS* v, VS* ya, VS* yb, AccT* acc,
-              double* W, cudaStream_t st) {
+              WT* W, cudaStream_t st) {
   using Ar = typename Arith<VS>::type;
   const int n = (int)A->n;
   const int cap = std::min<int>(A->max_cta_nnz, 4096);
@@ -294,19 +297,23 @@ void run_rows(const flz_matrix* A, const MS* val, const double* b, int m, const 
   const int* lr = A->long_rows.p;
   auto step = [&](bool first, bool last, const VS* cur, const VS* prev, VS* next, Ar bc, Ar bn) {
     if (first && last) {
-      cheb_rows_kernel<R, MS, VS, AccT, double, true><<<grid, kRows, smem, st>>>(n, cap, thr, rp, cl, val, cur, prev, next, acc, W, bc, bn);
+      cheb_rows_kernel<R, MS, VS, AccT, WT, true><<<grid, kRows, smem, st>>>(n, cap, thr, rp, cl, val, cur, prev, next, acc, W, bc, bn);
       FLZ_LAUNCH_CHECK();
-      if (nl) cheb_long_kernel<R, MS, VS, AccT, double, true><<<nl, kRows, 0, st>>>(lr, rp, cl, val, cur, prev, next, acc, W, bc, bn);
+      if (nl) cheb_long_kernel<R, MS, VS, AccT, WT, true><<<nl, kRows, 0, st>>>(lr, rp, cl, val, cur, prev, next, acc, W, bc, bn);
     } else if (first) {
       cheb_rows_kernel<R, MS, VS, AccT, AccT, true><<<grid, kRows, smem, st>>>(n, cap, thr, rp, cl, val, cur, prev, next, acc, acc, bc, bn);
       FLZ_LAUNCH_CHECK();
       if (nl) cheb_long_kernel<R, MS, VS, AccT, AccT, true><<<nl, kRows, 0, st>>>(lr, rp, cl, val, cur, prev, next, acc, acc, bc, bn);
     } else if (last) {
-      cheb_rows_kernel<R, MS, VS, AccT, double, false><<<grid, kRows, smem, st>>>(n, cap, thr, rp, cl, val, cur, prev, next, acc, W, bc, bn);
+      // degree steps after the first overlap their CSR staging with the
+      // previous step's tail (programmatic dependent launch)
+      launch_dependent(cheb_rows_kernel<R, MS, VS, AccT, WT, false>, grid, kRows, smem, st, n, cap, thr, rp, cl, val,
+                       cur, prev, next, acc, W, bc, bn);
       FLZ_LAUNCH_CHECK();
-      if (nl) cheb_long_kernel<R, MS, VS, AccT, double, false><<<nl, kRows, 0, st>>>(lr, rp, cl, val, cur, prev, next, acc, W, bc, bn);
+      if (nl) cheb_long_kernel<R, MS, VS, AccT, WT, false><<<nl, kRows, 0, st>>>(lr, rp, cl, val, cur, prev, next, acc, W, bc, bn);
     } else {
-      cheb_rows_kernel<R, MS, VS, AccT, AccT, false><<<grid, kRows, smem, st>>>(n, cap, thr, rp, cl, val, cur, prev, next, acc, acc, bc, bn);
+      launch_dependent(cheb_rows_kernel<R, MS, VS, AccT, AccT, false>, grid, kRows, smem, st, n, cap, thr, rp, cl,
+                       val, cur, prev, next, acc, acc, bc, bn);
       FLZ_LAUNCH_CHECK();
       if (nl) cheb_long_kernel<R, MS, VS, AccT, AccT, false><<<nl, kRows, 0, st>>>(lr, rp, cl, val, cur, prev, next, acc, acc, bc, bn);
     }
@@ -328,25 +335,25 @@ inline bool aligned_to(const void* p, size_t a) { return (reinterpret_cast<uintp
 
 // Row-per-thread kernel for r in {1, 2, 4, 8, 16} when every block is aligned
 // for R-wide vector access; the lane-per-column kernel otherwise.
-template <class MS, class VS, class AccT>
+template <class MS, class VS, class AccT, class WT>
 void run_recurrence(const flz_matrix* A, const MS* val, const double* b, int m, int r, const VS* v, VS* ya,
-                    VS* yb, AccT* acc, double* W, cudaStream_t st) {
+                    VS* yb, AccT* acc, WT* W, cudaStream_t st) {
   const bool pow2 = r == 1 || r == 2 || r == 4 || r == 8 || r == 16;
   const size_t av = std::min<size_t>(16, r * sizeof(VS));
   const size_t aa = std::min<size_t>(16, r * sizeof(AccT));
-  const size_t aw = std::min<size_t>(16, r * sizeof(double));
+  const size_t aw = std::min<size_t>(16, r * sizeof(WT));
   const bool ok = pow2 && A->max_cta_nnz > 0 && aligned_to(v, av) && aligned_to(ya, av) && aligned_to(yb, av) &&
                   aligned_to(acc, aa) && aligned_to(W, aw);
   if (!ok) {
-    run_lanes<MS, VS, AccT>(A, val, b, m, r, v, ya, yb, acc, W, st);
+    run_lanes<MS, VS, AccT, WT>(A, val, b, m, r, v, ya, yb, acc, W, st);
     return;
   }
   switch (r) {
-    case 1: run_rows<1, MS, VS, AccT>(A, val, b, m, v, ya, yb, acc, W, st); break;
-    case 2: run_rows<2, MS, VS, AccT>(A, val, b, m, v, ya, yb, acc, W, st); break;
-    case 4: run_rows<4, MS, VS, AccT>(A, val, b, m, v, ya, yb, acc, W, st); break;
-    case 8: run_rows<8, MS, VS, AccT>(A, val, b, m, v, ya, yb, acc, W, st); break;
-    default: run_rows<16, MS, VS, AccT>(A, val, b, m, v, ya, yb, acc, W, st); break;
+    case 1: run_rows<1, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
+    case 2: run_rows<2, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
+    case 4: run_rows<4, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
+    case 8: run_rows<8, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
+    default: run_rows<16, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
   }
 }
 
@@ -396,7 +403,7 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
                   double* W, int precision, int recurrence, cudaStream_t st) {
   const size_t nr = (size_t)A->n * r;
   if (m == 0) {
-    scale_kernel<<<grid_stride_blocks(nr), 256, 0, st>>>(V, W, coeffs[0], nr);
+    scale_kernel<double><<<grid_stride_blocks(nr), 256, 0, st>>>(V, W, coeffs[0], nr);
     FLZ_LAUNCH_CHECK();
     return;
   }
@@ -407,9 +414,9 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
     double* ya = A->ws64.p;
     double* yb = A->ws64.p + nr;
     if (clen)
-      run_clenshaw<double, double>(A, sv, coeffs, m, r, V, ya, yb, W, st);
+      run_clenshaw<double, double, double>(A, sv, coeffs, m, r, V, ya, yb, W, st);
     else  // the running sum lives in W directly (FP64 output)
-      run_recurrence<double, double, double>(A, sv, coeffs, m, r, V, ya, yb, W, W, st);
+      run_recurrence<double, double, double, double>(A, sv, coeffs, m, r, V, ya, yb, W, W, st);
   } else if (precision == FLZ_PREC_FP32) {
     const float* sv = scaled<float>(A, A->sval32, 1, c, e, st);
     A->ws32.reserve(4 * nr);
@@ -420,9 +427,9 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
     convert_kernel<float><<<grid_stride_blocks(nr), 256, 0, st>>>(V, vs, nr);
     FLZ_LAUNCH_CHECK();
     if (clen)
-      run_clenshaw<float, float>(A, sv, coeffs, m, r, vs, ya, yb, W, st);
+      run_clenshaw<float, float, double>(A, sv, coeffs, m, r, vs, ya, yb, W, st);
     else
-      run_recurrence<float, float, float>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
+      run_recurrence<float, float, float, double>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
   } else if (precision == FLZ_PREC_BF16) {
     const __nv_bfloat16* sv = scaled<__nv_bfloat16>(A, A->sval16, 2, c, e, st);
     A->ws16.reserve(3 * nr);
@@ -432,11 +439,11 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
     convert_kernel<__nv_bfloat16><<<grid_stride_blocks(nr), 256, 0, st>>>(V, vs, nr);
     FLZ_LAUNCH_CHECK();
     if (clen) {
-      run_clenshaw<__nv_bfloat16, __nv_bfloat16>(A, sv, coeffs, m, r, vs, ya, yb, W, st);
+      run_clenshaw<__nv_bfloat16, __nv_bfloat16, double>(A, sv, coeffs, m, r, vs, ya, yb, W, st);
     } else {
       A->ws32.reserve(nr);
       float* acc = A->ws32.p;
-      run_recurrence<__nv_bfloat16, __nv_bfloat16, float>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
+      run_recurrence<__nv_bfloat16, __nv_bfloat16, float, double>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
     }
   } else if (precision == FLZ_PREC_DF64) {
     const dfloat* sv = scaled<dfloat>(A, A->svaldf, 3, c, e, st);
@@ -448,12 +455,30 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
     convert_kernel<dfloat><<<grid_stride_blocks(nr), 256, 0, st>>>(V, vs, nr);
     FLZ_LAUNCH_CHECK();
     if (clen)
-      run_clenshaw<dfloat, dfloat>(A, sv, coeffs, m, r, vs, ya, yb, W, st);
+      run_clenshaw<dfloat, dfloat, double>(A, sv, coeffs, m, r, vs, ya, yb, W, st);
     else
-      run_recurrence<dfloat, dfloat, dfloat>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
+      run_recurrence<dfloat, dfloat, dfloat, double>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
   } else {
     fail(FLZ_ERR_INVALID_ARG, "unknown precision %d", precision);
   }
+}
+
+void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m, int r, const dfloat* V,
+                  dfloat* W, int recurrence, cudaStream_t st) {
+  const size_t nr = (size_t)A->n * r;
+  if (m == 0) {
+    scale_kernel<dfloat><<<grid_stride_blocks(nr), 256, 0, st>>>(V, W, dfloat(coeffs[0]), nr);
+    FLZ_LAUNCH_CHECK();
+    return;
+  }
+  const dfloat* sv = scaled<dfloat>(A, A->svaldf, 3, c, e, st);
+  A->wsdf.reserve(2 * nr);
+  dfloat* ya = A->wsdf.p;
+  dfloat* yb = ya + nr;
+  if (recurrence == FLZ_REC_CLENSHAW)
+    run_clenshaw<dfloat, dfloat, dfloat>(A, sv, coeffs, m, r, V, ya, yb, W, st);
+  else  // the running sum lives in W directly
+    run_recurrence<dfloat, dfloat, dfloat, dfloat>(A, sv, coeffs, m, r, V, ya, yb, W, W, st);
 }
 
 void spmm(const flz_matrix* A, const double* X, double* Y, int s, int ld, cudaStream_t st) {

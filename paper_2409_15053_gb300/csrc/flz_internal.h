@@ -42,6 +42,24 @@ extern thread_local int64_t g_kernel_launches;
     FLZ_CUDA(cudaGetLastError());  \
   } while (0)
 
+// Launches kernel K with programmatic stream serialization: it may begin (and
+// run its prologue up to grid_dependency_wait()) while the previous kernel on
+// the stream is still finishing.
+template <class... P, class... Args>
+inline void launch_dependent(void (*K)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  FLZ_CUDA(cudaLaunchKernelEx(&cfg, K, static_cast<P>(args)...));
+}
+
 // Entry-point bodies: clear the thread's last error, run, map failures to a status.
 #define FLZ_API_BEGIN         \
   ::flz::clear_last_error();  \
@@ -139,15 +157,19 @@ constexpr int kLongRow = 256;
 // W = p_m((A - cI)/e) V, V and W device FP64 n x r row-major.
 void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m, int r,
                   const double* V, double* W, int precision, int recurrence, cudaStream_t st);
+// The double-FP32 filter on blocks already stored as double-FP32 pairs (no
+// conversion of V, W written as pairs).
+void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m, int r,
+                  const dev::dfloat* V, dev::dfloat* W, int recurrence, cudaStream_t st);
 // Number of kernel launches filter_apply issues for degree m at `precision`.
 int filter_launch_count(int m, int precision);
 // ---- clenshaw.cu ----------------------------------------------------------------
 // W = p_m(Ahat) V by the Clenshaw recurrence with 2 Ahat stored in `val`
 // (MS) and the recurrence vectors in VS; v is V in VS, ba and bb are n x r
 // scratch, m >= 1.
-template <class MS, class VS>
+template <class MS, class VS, class WT>
 void run_clenshaw(const flz_matrix* A, const MS* val, const double* b, int m, int r, const VS* v, VS* ba, VS* bb,
-                  double* W, cudaStream_t st);
+                  WT* W, cudaStream_t st);
 // Y = A X for an n x s block with row stride ld (s <= 16), FP64.
 void spmm(const flz_matrix* A, const double* X, double* Y, int s, int ld, cudaStream_t st);
 
@@ -158,9 +180,17 @@ void spmm(const flz_matrix* A, const double* X, double* Y, int s, int ld, cudaSt
 size_t basis_dot_scratch(int64_t n, int nb, int r, int s);
 void basis_dot(const double* Q, int nb, int64_t n, int r, const double* W, int s, int ldw, double* C,
                double* part, cudaStream_t st);
+// The same with the basis and W stored as double-FP32 pairs and the products
+// and sums formed on the FP32 pipes; C stays FP64.
+void basis_dot(const dev::dfloat* Q, int nb, int64_t n, int r, const dev::dfloat* W, int s, int ldw, double* C,
+               double* part, cudaStream_t st);
 // Out[i, t] = beta * Out[i, t] + alpha * sum_{b, a} Q_b[i, a] C[(b*r + a)*s + t], t < s.
 // Out has row stride ldo; Out may equal Q's block 0 when nb == 1 (in-place).
 void basis_update(const double* Q, int nb, int64_t n, int r, const double* C, int s, double alpha,
+                  double beta, double* Out, int ldo, cudaStream_t st);
+void basis_update(const dev::dfloat* Q, int nb, int64_t n, int r, const double* C, int s, double alpha,
+                  double beta, dev::dfloat* Out, int ldo, cudaStream_t st);
+void basis_update(const dev::dfloat* Q, int nb, int64_t n, int r, const double* C, int s, double alpha,
                   double beta, double* Out, int ldo, cudaStream_t st);
 // Per-column sums over rows: out[t] = sum_i X[i,t] Y[i,t] (mode 0) or
 // sum_i (Y[i,t] - lam[t] X[i,t])^2 (mode 1); X, Y n x s with stride ld.
@@ -169,6 +199,7 @@ void column_sums(const double* X, const double* Y, const double* lam, int64_t n,
 size_t column_sums_scratch(int64_t n, int s);
 // n x r block of N(0,1) numbers from a counter-based generator (seed, offset).
 void random_normal(double* X, int64_t count, uint64_t seed, uint64_t offset, cudaStream_t st);
+void random_normal(dev::dfloat* X, int64_t count, uint64_t seed, uint64_t offset, cudaStream_t st);
 // Column j of a row-major n x s block (stride ld) into column-major out (stride ldo).
 void rows_to_columns(const double* X, int64_t n, int s, int ld, double* out, int64_t ldo, cudaStream_t st);
 // Gershgorin interval and max row length on the device.

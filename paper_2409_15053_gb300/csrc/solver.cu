@@ -57,14 +57,18 @@ struct Projected {
   }
 };
 
+// One block Lanczos engine over a basis stored as T: FP64, or double-FP32
+// pairs (dev::dfloat) whose inner products and updates run on the FP32 pipes.
+// The small matrices (C, D_j, S_j, R^{-1}) are FP64 throughout.
+template <class T>
 struct Engine {
   flz_matrix* A;
   int64_t n;
   int r;
   cudaStream_t st;
-  double* Q;     // basis, nb_cap blocks
+  T* Q;          // basis, nb_cap blocks
   int nb_cap;
-  double* W;     // n x r
+  T* W;          // n x r
   double* C;     // nb_cap*r x r
   double* C2;
   double* part;  // basis_dot scratch
@@ -72,9 +76,9 @@ struct Engine {
   double ms_orth = 0.0, ms_op = 0.0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
 
-  double* block(int b) const { return Q + (size_t)b * n * r; }
+  T* block(int b) const { return Q + (size_t)b * n * r; }
 
-  void gram(const double* X, std::vector<double>& G) {
+  void gram(const T* X, std::vector<double>& G) {
     basis_dot(X, 1, n, r, X, r, r, C2, part, st);
     G.resize((size_t)r * r);
     FLZ_CUDA(cudaMemcpyAsync(G.data(), C2, sizeof(double) * r * r, cudaMemcpyDeviceToHost, st));
@@ -82,18 +86,18 @@ struct Engine {
   }
 
   // Out = X R^{-1} (in place allowed).
-  void right_solve(const double* X, const std::vector<double>& Rinv, double* Out) {
+  void right_solve(const T* X, const std::vector<double>& Rinv, T* Out) {
     FLZ_CUDA(cudaMemcpyAsync(small, Rinv.data(), sizeof(double) * r * r, cudaMemcpyHostToDevice, st));
     basis_update(X, 1, n, r, small, r, 1.0, 0.0, Out, r, st);
   }
 
   // Block QR of the n x r block X into Out (CholeskyQR2, shifted CholeskyQR3
   // when the first Cholesky fails); returns S (upper triangular, row-major).
-  std::vector<double> block_qr(const double* X, double* Out) {
+  std::vector<double> block_qr(const T* X, T* Out) {
     std::vector<double> G, R((size_t)r * r), Rinv((size_t)r * r), S((size_t)r * r, 0.0), tmp((size_t)r * r);
     for (int i = 0; i < r; ++i) S[i * r + i] = 1.0;
     gram(X, G);
-    const double* src = X;
+    const T* src = X;
     int passes = 2;
     if (!cholesky_upper(G.data(), r, R.data())) {
       // shifted Cholesky keeps the factorization defined for ill-conditioned X
@@ -133,7 +137,7 @@ struct Engine {
 
   // Classical Gram-Schmidt twice of X against blocks 0..nb-1; returns the
   // total projection coefficients of the last block (r x r, row-major) in Dlast.
-  void cgs2(double* X, int nb, std::vector<double>* Dlast) {
+  void cgs2(T* X, int nb, std::vector<double>* Dlast) {
     basis_dot(Q, nb, n, r, X, r, r, C, part, st);
     basis_update(Q, nb, n, r, C, r, -1.0, 1.0, X, r, st);
     basis_dot(Q, nb, n, r, X, r, r, C2, part, st);
@@ -151,7 +155,7 @@ struct Engine {
 
   // One block Lanczos step j: W = op(Q_j), reorthogonalize, QR into Q_{j+1}.
   // Returns false if the new block could not be formed (no slot).
-  void step(int j, const std::function<void(const double*, double*)>& op, Projected& P, double op_norm) {
+  void step(int j, const std::function<void(const T*, T*)>& op, Projected& P, double op_norm) {
     if (!ev[0])
       for (auto& x : ev) FLZ_CUDA(cudaEventCreate(&x));
     FLZ_CUDA(cudaEventRecord(ev[0], st));
@@ -160,8 +164,8 @@ struct Engine {
     std::vector<double> D;
     cgs2(W, j + 1, &D);
     P.D.push_back(D);
-    double* next = (j + 1 < nb_cap) ? block(j + 1) : nullptr;
-    double* dst = next ? next : W;
+    T* next = (j + 1 < nb_cap) ? block(j + 1) : nullptr;
+    T* dst = next ? next : W;
     std::vector<double> S = block_qr(W, dst);
     // breakdown: the new block is (nearly) dependent on the basis; its
     // directions are rounding noise and must be made orthogonal to the basis.
@@ -186,7 +190,8 @@ struct Engine {
   }
 };
 
-void orthonormal_start(Engine& E, uint64_t seed) {
+template <class T>
+void orthonormal_start(Engine<T>& E, uint64_t seed) {
   random_normal(E.block(0), E.n * E.r, seed, 0, E.st);
   E.block_qr(E.block(0), E.block(0));
 }
@@ -203,7 +208,7 @@ void estimate_bounds(flz_matrix* A, int steps, int r, uint64_t seed, cudaStream_
   C2b.reserve((size_t)(nb + 1) * r * r);
   partb.reserve(std::max(basis_dot_scratch(n, nb + 1, r, r), (size_t)1));
   smallb.reserve((size_t)r * r);
-  Engine E{A, n, r, st, Qb.p, nb + 1, Wb.p, Cb.p, C2b.p, partb.p, smallb.p};
+  Engine<double> E{A, n, r, st, Qb.p, nb + 1, Wb.p, Cb.p, C2b.p, partb.p, smallb.p};
   orthonormal_start(E, seed ^ 0x5bd1e995ull);
   Projected P;
   P.r = r;
@@ -253,7 +258,20 @@ void bounds_entry(flz_matrix* A, int steps, int r, uint64_t seed, cudaStream_t s
   estimate_bounds(A, steps, r, seed, st, lmin, lmax);
 }
 
-flz_status solve(flz_solver* s, cudaStream_t st) {
+namespace {
+
+// W = p_m(Ahat) X on the engine's storage type.
+void apply_filter(flz_matrix* A, double c, double e, const std::vector<double>& coeffs, int m, int r,
+                  const flz_params& p, const double* X, double* Y, cudaStream_t st) {
+  filter_apply(A, c, e, coeffs.data(), m, r, X, Y, p.precision, p.recurrence, st);
+}
+void apply_filter(flz_matrix* A, double c, double e, const std::vector<double>& coeffs, int m, int r,
+                  const flz_params& p, const dev::dfloat* X, dev::dfloat* Y, cudaStream_t st) {
+  filter_apply(A, c, e, coeffs.data(), m, r, X, Y, p.recurrence, st);
+}
+
+template <class BT>
+flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   const auto t_start = Clock::now();
   const int64_t launches0 = g_kernel_launches;
   flz_matrix* A = s->A;
@@ -321,15 +339,15 @@ flz_status solve(flz_solver* s, cudaStream_t st) {
   s->X.reserve((size_t)n * 16);
   s->AX.reserve((size_t)n * 16);
   s->colpart.reserve(column_sums_scratch(n, 16) + 64);
-  Engine E{A, n, r, st, s->Q.p, nb_cap, s->W.p, s->C.p, s->C2.p, s->part.p, s->small.p};
+  static_assert(sizeof(BT) == sizeof(double), "basis storage reuses the FP64 buffers");
+  BT* Qt = reinterpret_cast<BT*>(s->Q.p);
+  Engine<BT> E{A, n, r, st, Qt, nb_cap, reinterpret_cast<BT*>(s->W.p), s->C.p, s->C2.p, s->part.p, s->small.p};
   orthonormal_start(E, p.seed);
 
   Projected P;
   P.r = r;
   const int guard = p.guard > 0 ? p.guard : std::max(r, 3);
-  auto filt = [&](const double* X, double* Y) {
-    filter_apply(A, c, e, coeffs.data(), m, r, X, Y, p.precision, p.recurrence, st);
-  };
+  auto filt = [&](const BT* X, BT* Y) { apply_filter(A, c, e, coeffs, m, r, p, X, Y, st); };
   double ms_check = 0.0;
   int64_t prev_count = -1;
   bool converged = false;
@@ -403,7 +421,7 @@ flz_status solve(flz_solver* s, cudaStream_t st) {
       s->C2.reserve(std::max(s->C2.count, (size_t)K * 16));
       E.C2 = s->C2.p;
       FLZ_CUDA(cudaMemcpyAsync(s->C2.p, Cy.data(), sizeof(double) * K * 16, cudaMemcpyHostToDevice, st));
-      basis_update(s->Q.p, k, n, r, s->C2.p, 16, 1.0, 0.0, s->X.p, 16, st);
+      basis_update(Qt, k, n, r, s->C2.p, 16, 1.0, 0.0, s->X.p, 16, st);
       spmm(A, s->X.p, s->AX.p, 16, 16, st);
       double* dev = s->small.p;  // [0,16) xx, [16,32) xAx, [32,48) lam, [48,64) res2, [64] scale
       column_sums(s->X.p, s->X.p, nullptr, n, 16, 16, 0, dev, s->colpart.p, st);
@@ -503,6 +521,16 @@ flz_status solve(flz_solver* s, cudaStream_t st) {
   stats.ms_total = ms_since(t_start);
   stats.kernel_launches = g_kernel_launches - launches0;
   return converged ? FLZ_OK : FLZ_ERR_NOT_CONVERGED;
+}
+
+}  // namespace
+
+// The double-FP32 precision keeps the whole Krylov basis as double-FP32
+// pairs: filter, reorthogonalization and block QR run on the FP32 pipes;
+// Rayleigh-Ritz, Rayleigh quotients and residuals stay FP64.
+flz_status solve(flz_solver* s, cudaStream_t st) {
+  if (s->p.precision == FLZ_PREC_DF64) return solve_impl<dev::dfloat>(s, st);
+  return solve_impl<double>(s, st);
 }
 
 }  // namespace flz

@@ -7,6 +7,22 @@ the widest spectral gap among eigenvalues 95..110 and `count` is the number of
 eigenvalues in [alpha, beta]; both were computed by the CPU oracle with
 tests/golden/make_config2_reference.py (tests/golden/config2_reference.json).
 `reference_iters` is the oracle run's block-step count at degree 60, r = 4.
+
+CONFIG3: real-space Hamiltonian stand-in: 4th-order 13-point FD -Laplacian on
+a 120^3 grid (n = 1.728e6, nnz = 22,204,800) plus 64 negative Gaussian wells
+(synth.matrices.gaussian_wells_potential, seed 3); the lowest ~200
+eigenpairs. alpha lies below the Gershgorin interval; beta sits at the
+midpoint of the widest gap among eigenvalues 195..205 and was computed with
+the count by the CPU oracle (tests/golden/make_config3_reference.py,
+tests/golden/config3_reference.json).
+
+BATCH64: 64 independent 2D/3D Dirichlet Laplacians with U(0,1) diagonal
+potentials (synth.matrices.uneven_batch, n log-uniform in [1e4, 2e5]), each
+with the interval [0, beta_i] holding a target count drawn uniformly from
+10..50. beta_i sits at the midpoint of the widest gap among the eigenvalues
+around the target count; beta_i and the counts were computed by the CPU
+oracle with tests/golden/make_batch64_reference.py
+(tests/golden/batch64_reference.json).
 """
 
 CONFIG2 = {
@@ -19,4 +35,23 @@ CONFIG2 = {
     "degree": 60,
     "check_every": 10,
     "reference_iters": 120,
+}
+
+CONFIG3 = {
+    "grid": 120,
+    "wells": 64,
+    "seed": 3,
+    "alpha": -6.0,
+    "degree": 200,
+    "target": 200,
+}
+
+BATCH64 = {
+    "count": 64,
+    "seed": 4,
+    "n_lo": 1e4,
+    "n_hi": 2e5,
+    "target_lo": 10,
+    "target_hi": 50,
+    "target_seed": 5,
 }

@@ -110,3 +110,34 @@ def test_batch_rejects_bad_arguments():
         flz.flz_batch_create([h], [1.0], [0.5], p)
     assert e.value.status == flz.FLZ_ERR_INVALID_ARG
     flz.flz_matrix_destroy(h)
+
+
+@pytest.mark.parametrize("precision,tol", [(flz.FLZ_PREC_FP32, 1e-6), (flz.FLZ_PREC_FP64, 1e-10)],
+                         ids=["fp32", "fp64"])
+def test_full_size_batch64_matches_oracle_reference(precision, tol):
+    # 64 problems, n log-uniform in [1e4, 2e5] (sum ~4.7e6), autotuned r, auto
+    # degree: the batched launch shape the benchmark times, against the
+    # eigenvalues the CPU oracle computed for every problem (tests/golden).
+    # Counts exact; every eigenvalue within tol ||A|| of the oracle's (each
+    # Rayleigh quotient with residual <= tol lies within tol ||A|| of an
+    # eigenvalue, and the counts pin which); residuals recomputed here.
+    import json
+    import os
+    from synth.workloads import BATCH64
+    from synth import csr_checksum
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "batch64_reference.json")))["problems"]
+    items = uneven_batch(BATCH64["count"], seed=BATCH64["seed"], n_lo=BATCH64["n_lo"], n_hi=BATCH64["n_hi"])
+    csrs = [c for c, _, _ in items]
+    assert [csr_checksum(c) for c in csrs] == [p["matrix_checksum"] for p in ref]
+    intervals = [(p["alpha"], p["beta"]) for p in ref]
+    st, out = run_batch(csrs, intervals, block_size=0, degree=0, check_every=5, precision=precision, tol=tol)
+    assert st == flz.FLZ_OK
+    for c, p, o in zip(csrs, ref, out):
+        want = np.array(p["eigenvalues"])
+        assert o["vals"].shape == want.shape, (p["index"], o["vals"].shape, want.shape)
+        norm_a = max(abs(o["stats"]["lmin"]), abs(o["stats"]["lmax"]))
+        assert np.max(np.abs(o["vals"] - want)) <= tol * norm_a
+        X = o["vecs"]
+        R = c.to_scipy() @ X - X * o["vals"]
+        assert np.max(np.linalg.norm(R, axis=0)) / norm_a <= tol
+        assert np.max(np.abs(X.T @ X - np.eye(X.shape[1]))) < 1e-10

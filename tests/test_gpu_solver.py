@@ -252,14 +252,18 @@ def test_full_size_config2_matches_oracle_reference(precision, rec):
     check_pairs(csr, out, 1e-10)
 
 
-@pytest.mark.parametrize("precision,tol,eig_tol", [(flz.FLZ_PREC_FP32, 1e-6, 1e-9), (flz.FLZ_PREC_BF16, 1e-3, 2e-3),
+@pytest.mark.parametrize("precision,tol,eig_tol", [(flz.FLZ_PREC_FP32, 1e-6, 1e-9), (flz.FLZ_PREC_BF16, 1e-2, 1e-2),
                                                    (flz.FLZ_PREC_DF64, 1e-10, 1e-10)])
 def test_reduced_precision_filter(precision, tol, eig_tol):
-    # The filter runs in FP32 (or BF16 storage with FP32 sums); everything else
-    # is FP64. The filtered Lanczos relation holds only to the filter's
-    # rounding, which bounds the attainable residual (about 1e-7 in FP32); the
-    # Rayleigh quotients are computed with A in FP64, so eigenvalue errors are
-    # of the order of the squared residual. Count exact, residuals <= tol.
+    # FP32 / BF16: the filter runs in FP32 (or BF16 storage with FP32 sums);
+    # everything else is FP64. The filtered Lanczos relation then holds only to
+    # the filter's rounding, which bounds the attainable residual: about 1e-7
+    # in FP32; in BF16 the stored values of 2 Ahat alone perturb A by up to
+    # 2^-9 of its row sums (about 2e-3 ||A|| here), so 1e-2 is the tolerance
+    # the arithmetic supports. FP32 eigenvalue errors are of the order of the
+    # squared residual (FP64 Rayleigh quotients); for BF16 the bound is Kahan's,
+    # |lambda - lambda_i| <= ||r|| (residual tol times ||A||). DF64: the whole
+    # basis in double-FP32, FP64-class results. Count exact, residuals <= tol.
     rng = np.random.Generator(np.random.PCG64(15))
     csr = laplacian_3d_7pt(14, 14, 14, 0.5 * rng.random(14 ** 3))
     w = np.linalg.eigvalsh(csr.to_dense())
