@@ -35,7 +35,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synth import laplacian_3d_7pt, random_normal_block, uneven_batch  # noqa: E402
+from synth import laplacian_3d_7pt, parsec_like_hamiltonian, random_normal_block, uneven_batch  # noqa: E402
 from synth.workloads import BATCH64, CONFIG2  # noqa: E402
 
 METRIC = "eigenpairs/s at residual 1e-8 (3D 7-point Laplacian 100^3 + potential, FP64)"
@@ -43,6 +43,7 @@ METRIC = "eigenpairs/s at residual 1e-8 (3D 7-point Laplacian 100^3 + potential,
 # this workload, 100 gave the shortest time to solution (fewer block steps and
 # reorthogonalizations at a moderate cost per step, as in Tables 2 and 3).
 BENCH_DEGREE = 100
+BATCH_DEGREE = 60
 
 
 def peaks():
@@ -223,6 +224,8 @@ def main():
     ap.add_argument("--block-size", type=int, default=4)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16", "df64"])
     ap.add_argument("--recurrence", default="forward", choices=["forward", "clenshaw"])
+    ap.add_argument("--damping", default="none", choices=["none", "jackson"],
+                    help="filter damping (the paper uses none)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--check-every", type=int, default=CONFIG2["check_every"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
@@ -231,7 +234,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32/BF16-filter solves reported under 'variants'")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch-of-64 leg")
-    ap.add_argument("--mode", default="solve", choices=["solve", "filter", "batch"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "filter", "batch", "table2"],
                     help="solve: whole flz_solve per step (default); filter: only flz_filter_apply at the "
                          "solver's shape, for the kernel roofline and profiling")
     args = ap.parse_args()
@@ -260,6 +263,8 @@ def main():
     if args.mode == "batch":
         print(json.dumps({"mode": "batch", **batch_leg(flz, torch, torch.cuda.current_stream())}))
         return
+    if args.mode == "table2":
+        return table2_mode(flz, torch, prec, args)
     csr = make_matrix()
     if args.mode == "filter":
         return filter_mode(flz, torch, csr, prec, args)
@@ -274,6 +279,7 @@ def main():
     p.check_every = args.check_every
     p.precision = prec
     p.recurrence = {"forward": flz.FLZ_REC_FORWARD, "clenshaw": flz.FLZ_REC_CLENSHAW}[args.recurrence]
+    p.damping = 1 if args.damping == "jackson" else 0
     p.seed = 1 + rank
     s = flz.flz_solver_create(h, p)
     flz.flz_solver_set_interval(s, alpha, beta)
@@ -327,16 +333,20 @@ def main():
     hbm, hbm_src = peaks()
     achieved_gbs = nbytes / (ms_per_launch * 1e-3) / 1e9
     achieved_tflops = nflops / (ms_per_launch * 1e-3) / 1e12
-    fp64_peak = 1.25  # TFLOP/s: GB300's nominal dense FP64 rate (the FP64 step is bound by it)
+    # FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
+    # DRAM bytes per launch of the FP64 forward SELL-32 step on this workload, from
+    # one ncu capture (profiles/cheb_sell_kernel_fp64_laplacian3d_100cubed_r4.md)
+    traffic = 179.70e6 + 36.53e6 if (args.precision == "fp64" and args.recurrence == "forward") else None
     roofline = {
-        "kernel": ("clen_rows_kernel (Clenshaw degree step)" if args.recurrence == "clenshaw"
-                   else "cheb_rows_kernel (fused Chebyshev degree step)"),
+        "kernel": ("clen_sell_kernel (Clenshaw degree step, SELL-32)" if args.recurrence == "clenshaw"
+                   else "cheb_sell_kernel (fused Chebyshev degree step, SELL-32)"),
         "bound": "alu" if args.precision == "fp64" else "hbm",
         "achieved": achieved_tflops if args.precision == "fp64" else achieved_gbs,
         "peak": fp64_peak if args.precision == "fp64" else hbm,
         "unit": "TFLOP/s" if args.precision == "fp64" else "GB/s",
         "frac": (achieved_tflops / fp64_peak) if args.precision == "fp64" else achieved_gbs / hbm,
-        "traffic": None,
+        "traffic": traffic,
         "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm, "hbm_frac": achieved_gbs / hbm,
         "hbm_peak_source": hbm_src, "algorithmic_bytes_per_launch": nbytes, "flops_per_launch": nflops,
         "ms_per_launch": ms_per_launch,
@@ -441,8 +451,9 @@ def batch_leg(flz, torch, stream):
     Times (CUDA events, after one warm-up solve each): the batch with the FP32
     filter (tol 1e-6, its attainable residual), the batch with the FP64 filter
     (tol 1e-10), and the 64 problems solved one after another with the FP64
-    filter (r = 4). Each result is checked against the oracle's counts and
-    eigenvalues."""
+    filter (r = 4); filter degree 60 throughout (the eps-rule's degrees of
+    17-23 would need up to 480 block steps). Each result is checked against
+    the oracle's counts and eigenvalues."""
     ref = json.load(open(os.path.join(ROOT, "tests", "golden", "batch64_reference.json")))["problems"]
     items = uneven_batch(BATCH64["count"], seed=BATCH64["seed"], n_lo=BATCH64["n_lo"], n_hi=BATCH64["n_hi"])
     hs = [flz.flz_matrix_create_csr(c.n, c.nnz, c.rowptr, c.col, c.val) for c, _, _ in items]
@@ -472,7 +483,7 @@ def batch_leg(flz, torch, stream):
     for name, prec, tol in (("batch_fp32", flz.FLZ_PREC_FP32, 1e-6), ("batch_fp64", flz.FLZ_PREC_FP64, 1e-10)):
         p = flz.flz_params_default()
         p.block_size = 0
-        p.degree = 0
+        p.degree = BATCH_DEGREE
         p.precision = prec
         p.tol = tol
         p.check_every = 5
@@ -490,7 +501,7 @@ def batch_leg(flz, torch, stream):
         flz.flz_batch_destroy(bt)
     p = flz.flz_params_default()
     p.block_size = 4
-    p.degree = 0
+    p.degree = BATCH_DEGREE
     p.check_every = 5
     solvers = []
     for h, a, z in zip(hs, alphas, betas):
@@ -518,6 +529,64 @@ def batch_leg(flz, torch, stream):
     for h in hs:
         flz.flz_matrix_destroy(h)
     return out
+
+
+# Table 2's Ge87H76 rows (K40, Cucheb, r = 3): degree -> (iters, MV, seconds, max residual)
+TABLE2_GE87H76 = {50: (210, 31500, 31, 1.7e-14), 100: (180, 54000, 40, 4.0e-13), 150: (150, 67500, 44, 7.4e-14),
+                  200: (150, 90000, 56, 6.3e-14), "auto (49)": (210, 30870, 31, 9.0e-14)}
+
+
+def table2_mode(flz, torch, prec, args):
+    """Table 2's sweep on a synthetic stand-in shaped like Ge87H76.
+
+    The PARSEC matrices are not available; parsec_like_hamiltonian() builds a
+    real-space Hamiltonian of the same size, density and spectral interval
+    (12th-order finite differences on a sphere, Gaussian local potentials,
+    dense non-local projector blocks). Interval [-0.645, -0.0053] as in
+    Table 2, block size 3, degrees 50, 100, 150, 200 and automatic, checks every
+    30 block steps; one warm-up solve per degree, then one timed solve (CUDA
+    events). The paper's K40 numbers for Ge87H76 are printed beside each row
+    for context (a different matrix of the same shape, on other hardware)."""
+    csr = parsec_like_hamiltonian()
+    h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for m in (50, 100, 150, 200, 0):
+        p = flz.flz_params_default()
+        p.block_size = 3
+        p.degree = m
+        p.precision = prec
+        p.tol = args.tol
+        p.check_every = 30
+        p.recurrence = {"forward": flz.FLZ_REC_FORWARD, "clenshaw": flz.FLZ_REC_CLENSHAW}[args.recurrence]
+        p.damping = 1 if args.damping == "jackson" else 0
+        s = flz.flz_solver_create(h, p)
+        flz.flz_solver_set_interval(s, -0.645, -0.0053)
+        flz.flz_solve(s, stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = flz.flz_solve(s, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        x = flz.flz_get_stats(s)
+        res = flz.flz_get_residuals(s)
+        key = m if m else "auto (%d)" % x["degree"]
+        paper = TABLE2_GE87H76.get(m if m else "auto (49)")
+        rows.append({"m": key, "status": flz.flz_status_string(st), "eigs": int(x["count"]), "iters": int(x["iters"]),
+                     "MV": int(x["matvecs"]), "seconds": e0.elapsed_time(e1) / 1e3,
+                     "residual": float(res.max()) if res.size else None,
+                     "PREPROC_ORTH_MV_percent": [round(100 * x["ms_bounds"] / x["ms_total"]),
+                                                 round(100 * x["ms_orth"] / x["ms_total"]),
+                                                 round(100 * x["ms_filter"] / x["ms_total"])],
+                     "paper_K40": {"iters": paper[0], "MV": paper[1], "seconds": paper[2], "residual": paper[3]}})
+        flz.flz_solver_destroy(s)
+    flz.flz_matrix_destroy(h)
+    print(json.dumps({"mode": "table2", "matrix": "synthetic Ge87H76-shaped stand-in", "n": csr.n, "nnz": csr.nnz,
+                      "interval": [-0.645, -0.0053], "block_size": 3, "precision": args.precision,
+                      "recurrence": args.recurrence, "damping": args.damping,
+                      "tol": args.tol, "rows": rows}))
 
 
 def filter_mode(flz, torch, csr, prec, args):

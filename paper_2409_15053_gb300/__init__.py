@@ -41,7 +41,7 @@ FLZ_REC_FORWARD, FLZ_REC_CLENSHAW = 0, 1
 # Every symbol include/flz.h declares.
 EXPORTED = (
     "flz_status_string", "flz_last_error", "flz_params_default",
-    "flz_matrix_create_csr", "flz_matrix_destroy", "flz_matrix_info",
+    "flz_matrix_create_csr", "flz_matrix_destroy", "flz_matrix_info", "flz_matrix_format",
     "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_jackson_factors", "flz_filter_degree", "flz_spectrum_bounds",
     "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_sym_eig", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve",
     "flz_get_count", "flz_get_eigenvalues", "flz_get_eigenvectors", "flz_get_residuals", "flz_get_stats",
@@ -105,6 +105,7 @@ def lib() -> ctypes.CDLL:
                                                  ctypes.POINTER(_vp)]),
         "flz_matrix_destroy": (ctypes.c_int, [_vp]),
         "flz_matrix_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), _pdbl, _pdbl]),
+        "flz_matrix_format": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i32)]),
         "flz_filter_apply": (ctypes.c_int, [_vp, _dbl, _dbl, _vp, _i32, _i32, _vp, _vp, _i32, _i32, _vp]),
         "flz_filter_apply_noalloc": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, _dbl, _dbl, _vp, _i32, _i32, _vp,
                                                     _vp, _vp]),
@@ -201,6 +202,13 @@ def flz_matrix_info(A):
     n, nnz, glo, ghi = _i64(), _i64(), _dbl(), _dbl()
     _check(lib().flz_matrix_info(A, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(glo), ctypes.byref(ghi)))
     return n.value, nnz.value, glo.value, ghi.value
+
+
+def flz_matrix_format(A):
+    """(sell, sell_entries, long_rows) of the filter's storage of A."""
+    sell, entries, long_rows = _i32(), _i64(), _i32()
+    _check(lib().flz_matrix_format(A, ctypes.byref(sell), ctypes.byref(entries), ctypes.byref(long_rows)))
+    return sell.value, entries.value, long_rows.value
 
 
 def flz_filter_apply(A, c, e, coeffs, degree, r, V, W, precision=FLZ_PREC_FP64, stream=None,

@@ -220,6 +220,7 @@ flz_status flz_matrix_create_csr(int64_t n, int64_t nnz, const int32_t* rowptr, 
     if (flz::find_diagonals(A) > 0) insert_zero_diagonals(A);
     flz::gershgorin(A, &A->glo, &A->ghi, &A->max_row_nnz);
     A->max_cta_nnz = flz::max_block_nnz(A, 256);
+    flz::build_sell(A);
     if (A->max_row_nnz > flz::kLongRow) {
       std::vector<int32_t> rp(A->n + 1), lr;
       FLZ_CUDA(cudaMemcpy(rp.data(), A->rowptr.p, sizeof(int32_t) * (A->n + 1), cudaMemcpyDeviceToHost));
@@ -250,6 +251,15 @@ flz_status flz_matrix_info(const flz_matrix* A, int64_t* n, int64_t* nnz, double
   if (nnz) *nnz = A->nnz_user;
   if (glo) *glo = A->glo;
   if (ghi) *ghi = A->ghi;
+  FLZ_API_END
+}
+
+flz_status flz_matrix_format(const flz_matrix* A, int32_t* sell, int64_t* sell_entries, int32_t* long_rows) {
+  FLZ_API_BEGIN
+  if (!A) fail(FLZ_ERR_INVALID_ARG, "matrix is NULL");
+  if (sell) *sell = A->sell ? 1 : 0;
+  if (sell_entries) *sell_entries = A->sell ? A->sell_len : 0;
+  if (long_rows) *long_rows = A->n_long;
   FLZ_API_END
 }
 

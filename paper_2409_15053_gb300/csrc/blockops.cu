@@ -18,7 +18,18 @@ namespace flz {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSub = 128;  // rows of W staged in shared memory per sub-chunk
+// Rows of W staged in shared memory per sub-chunk, and the unrolling of the
+// row loop: the FP64 form is bound by the FP64 pipe and keeps one row per
+// lane in flight; the double-FP32 form is bound by memory latency and keeps
+// four rows per lane (and twice the CTAs) in flight.
+template <class T>
+struct DotTune {
+  static constexpr int kSub = 128, kRows = 1, kCtasPerSm = 4;
+};
+template <>
+struct DotTune<dev::dfloat> {
+  static constexpr int kSub = 256, kRows = 4, kCtasPerSm = 8;
+};
 
 using dev::dfloat;
 
@@ -59,6 +70,8 @@ __global__ void __launch_bounds__(kThreads) basis_dot_kernel(const T* __restrict
                                                              long long rows_per_cta, double* __restrict__ part) {
   constexpr int BPW = (8 / R) > 0 ? (8 / R) : 1;
   constexpr int RPI = 32 / R;  // rows per warp iteration
+  constexpr int kSub = DotTune<T>::kSub;
+  constexpr int UR = DotTune<T>::kRows;
   __shared__ T wsm[kSub * R];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a = lane % R, k = lane / R;
@@ -79,15 +92,47 @@ __global__ void __launch_bounds__(kThreads) basis_dot_kernel(const T* __restrict
     }
     __syncthreads();
     if (active) {
+      if constexpr (UR == 1) {
+        // FP64: bound by the FP64 pipe; one row per lane per step
 #pragma unroll
-      for (int bi = 0; bi < BPW; ++bi) {
-        const int b = bbase + bi;
-        if (b < nb) {
-          const T* qb = Q + (size_t)b * n * R + (size_t)s0 * R;
-          for (int i = k; i < rows; i += RPI) {
-            const T q = ld_ro(qb + (size_t)i * R + a);
+        for (int bi = 0; bi < BPW; ++bi) {
+          const int b = bbase + bi;
+          if (b < nb) {
+            const T* qb = Q + (size_t)b * n * R + (size_t)s0 * R;
+            for (int i = k; i < rows; i += RPI) {
+              const T q = ld_ro(qb + (size_t)i * R + a);
 #pragma unroll
-            for (int t = 0; t < R; ++t) acc[bi][t] = fma(q, wsm[i * R + t], acc[bi][t]);
+              for (int t = 0; t < R; ++t) acc[bi][t] = fma(q, wsm[i * R + t], acc[bi][t]);
+            }
+          }
+        }
+      } else {
+        // double-FP32: UR rows per lane and every block of the warp in flight before use
+        int i = k;
+        for (; i + (UR - 1) * RPI < rows; i += UR * RPI) {
+          T q[BPW][UR];
+#pragma unroll
+          for (int bi = 0; bi < BPW; ++bi) {
+            const T* qb = Q + (size_t)(bbase + bi) * n * R + (size_t)s0 * R;
+#pragma unroll
+            for (int u = 0; u < UR; ++u)
+              q[bi][u] = (bbase + bi < nb) ? ld_ro(qb + (size_t)(i + u * RPI) * R + a) : zero_of<T>();
+          }
+#pragma unroll
+          for (int bi = 0; bi < BPW; ++bi)
+#pragma unroll
+            for (int u = 0; u < UR; ++u)
+#pragma unroll
+              for (int t = 0; t < R; ++t) acc[bi][t] = fma(q[bi][u], wsm[(i + u * RPI) * R + t], acc[bi][t]);
+        }
+        for (; i < rows; i += RPI) {
+#pragma unroll
+          for (int bi = 0; bi < BPW; ++bi) {
+            if (bbase + bi < nb) {
+              const T q = ld_ro(Q + (size_t)(bbase + bi) * n * R + (size_t)(s0 + i) * R + a);
+#pragma unroll
+              for (int t = 0; t < R; ++t) acc[bi][t] = fma(q, wsm[i * R + t], acc[bi][t]);
+            }
           }
         }
       }
@@ -120,13 +165,28 @@ __global__ void __launch_bounds__(kThreads) basis_dot_kernel(const T* __restrict
   }
 }
 
-__global__ void sum_partials_kernel(const double* __restrict__ part, int parts, size_t len,
-                                    double* __restrict__ out) {
-  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < len; o += (size_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int p = 0; p < parts; ++p) s += part[(size_t)p * len + o];
-    out[o] = s;
+// out[o] = sum_p part[p][o]: 32 outputs per CTA, its 8 warps split the parts.
+__global__ void __launch_bounds__(256) sum_partials_kernel(const double* __restrict__ part, int parts, size_t len,
+                                                           double* __restrict__ out) {
+  __shared__ double red[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const size_t o = (size_t)blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (o < len)
+    for (int p = w; p < parts; p += 8) s += part[(size_t)p * len + o];
+  red[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && o < len) {
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v += red[q][lane];
+    out[o] = v;
   }
+}
+
+inline void sum_partials(const double* part, int parts, size_t len, double* out, cudaStream_t st) {
+  sum_partials_kernel<<<(unsigned)((len + 31) / 32), 256, 0, st>>>(part, parts, len, out);
+  FLZ_LAUNCH_CHECK();
 }
 
 // Out[i, t] = beta Out[i, t] + alpha sum_{b,a} Q_b[i, a] C[(b r + a) S + t], one thread per row.
@@ -364,13 +424,15 @@ struct DotShape {
   long long rows_per_cta;
 };
 
+template <class T>
 DotShape dot_shape(int64_t n, int nb, int r) {
+  constexpr int kSub = DotTune<T>::kSub;
   const int bpw = std::max(1, 8 / r);
   const int bpc = 8 * bpw;
   DotShape d;
   d.gy = (nb + bpc - 1) / bpc;
   const long long max_gx = std::max<long long>(1, (n + kSub - 1) / kSub);
-  d.gx = (int)std::min<long long>(max_gx, std::max(1, 4 * 152 / d.gy));
+  d.gx = (int)std::min<long long>(max_gx, std::max(1, DotTune<T>::kCtasPerSm * 152 / d.gy));
   d.rows_per_cta = ((n + d.gx - 1) / d.gx + kSub - 1) / kSub * kSub;
   d.gx = (int)((n + d.rows_per_cta - 1) / d.rows_per_cta);
   return d;
@@ -378,12 +440,10 @@ DotShape dot_shape(int64_t n, int nb, int r) {
 
 template <int R, class T>
 void launch_basis_dot(const T* Q, int nb, int64_t n, const T* W, int ldw, double* C, double* part, cudaStream_t st) {
-  const DotShape d = dot_shape(n, nb, R);
+  const DotShape d = dot_shape<T>(n, nb, R);
   basis_dot_kernel<R, T><<<dim3(d.gx, d.gy), kThreads, 0, st>>>(Q, nb, n, W, ldw, d.rows_per_cta, part);
   FLZ_LAUNCH_CHECK();
-  const size_t len = (size_t)nb * R * R;
-  sum_partials_kernel<<<gs_blocks((long long)len), 256, 0, st>>>(part, d.gx, len, C);
-  FLZ_LAUNCH_CHECK();
+  sum_partials(part, d.gx, (size_t)nb * R * R, C, st);
 }
 
 template <int S, class T, class O>
@@ -406,8 +466,9 @@ size_t basis_dot_scratch(int64_t n, int nb, int r, int s) {
   // the largest partial-sum buffer any call with 1..nb blocks needs
   size_t best = 0;
   for (int b = 1; b <= nb; ++b) {
-    const DotShape d = dot_shape(n, b, r);
-    best = std::max(best, (size_t)d.gx * b * r * r);
+    const DotShape d = dot_shape<double>(n, b, r);
+    const DotShape e = dot_shape<dev::dfloat>(n, b, r);
+    best = std::max(best, (size_t)std::max(d.gx, e.gx) * b * r * r);
   }
   return best;
 }
@@ -487,8 +548,7 @@ void column_sums(const double* X, const double* Y, const double* lam, int64_t n,
   const int grid = (int)std::max<long long>(1, std::min<long long>(152 * 4, (warps + 7) / 8));
   column_sums_kernel<<<grid, kThreads, 0, st>>>(X, Y, lam, n, s, ld, mode, part);
   FLZ_LAUNCH_CHECK();
-  sum_partials_kernel<<<1, 32, 0, st>>>(part, grid, (size_t)s, out);
-  FLZ_LAUNCH_CHECK();
+  sum_partials(part, grid, (size_t)s, out, st);
 }
 
 void random_normal(double* X, int64_t count, uint64_t seed, uint64_t offset, cudaStream_t st) {
@@ -542,6 +602,98 @@ int32_t max_block_nnz(const flz_matrix* A, int rows) {
   FLZ_CUDA(cudaMemcpy(&h, best.p, sizeof(int), cudaMemcpyDeviceToHost));
   return h;
 }
+
+// Slice widths of the SELL-32 layout: the longest row of each 32-row slice,
+// counting a row longer than `long_row` as one marker entry.
+__global__ void sell_width_kernel(long long n, const int* __restrict__ rowptr, int long_row, int* __restrict__ width) {
+  const long long nsl = (n + 31) / 32;
+  for (long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x; sl < nsl; sl += (long long)gridDim.x * blockDim.x) {
+    int w = 1;
+    for (long long i = sl * 32; i < min(n, sl * 32 + 32); ++i) {
+      const int len = rowptr[i + 1] - rowptr[i];
+      w = max(w, len > long_row ? 1 : len);
+    }
+    width[sl] = w;
+  }
+}
+
+// SELL-32 columns: a row's entries in order, then padding with its own index;
+// a long row gets the marker -1 in its first slot.
+__global__ void sell_fill_col_kernel(long long n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                     int long_row, const int* __restrict__ off, int* __restrict__ scol) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long sl = i >> 5;
+    const int lane = (int)(i & 31);
+    const int base = off[sl] + lane;
+    const int w = (off[sl + 1] - off[sl]) >> 5;
+    const int j0 = rowptr[i], len = rowptr[i + 1] - j0;
+    const bool is_long = len > long_row;
+    for (int j = 0; j < w; ++j) {
+      int c = (int)i;
+      if (is_long) c = j == 0 ? -1 : (int)i;
+      else if (j < len) c = col[j0 + j];
+      scol[base + 32 * j] = c;
+    }
+  }
+}
+
+template <class S>
+__global__ void scale_values_sell_kernel(long long n, const int* __restrict__ rowptr, const int* __restrict__ diag_pos,
+                                         const double* __restrict__ val, int long_row, const int* __restrict__ off,
+                                         double s, double shift, S* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long sl = i >> 5;
+    const int lane = (int)(i & 31);
+    const int base = off[sl] + lane;
+    const int w = (off[sl + 1] - off[sl]) >> 5;
+    const int j0 = rowptr[i], len = rowptr[i + 1] - j0;
+    const int d = diag_pos[i];
+    for (int j = 0; j < w; ++j) {
+      double v = 0.0;
+      if (len <= long_row && j < len) v = s * (val[j0 + j] - (j0 + j == d ? shift : 0.0));
+      out[base + 32 * j] = round_to<S>(v);
+    }
+  }
+}
+
+void build_sell(flz_matrix* A) {
+  A->sell = false;
+  const int64_t nsl = (A->n + 31) / 32;
+  DevBuf<int> width;
+  width.reserve((size_t)nsl);
+  sell_width_kernel<<<gs_blocks(nsl), 256>>>(A->n, A->rowptr.p, kLongRow, width.p);
+  FLZ_LAUNCH_CHECK();
+  std::vector<int> hw(nsl);
+  FLZ_CUDA(cudaMemcpy(hw.data(), width.p, sizeof(int) * nsl, cudaMemcpyDeviceToHost));
+  std::vector<int32_t> off(nsl + 1);
+  int64_t total = 0;
+  for (int64_t sl = 0; sl < nsl; ++sl) {
+    off[sl] = (int32_t)std::min<int64_t>(total, 0x7fffffff);
+    total += 32 * (int64_t)hw[sl];
+  }
+  off[nsl] = (int32_t)std::min<int64_t>(total, 0x7fffffff);
+  // worthwhile only when the padding is small (regular stencils, not power-law graphs)
+  if (total >= 0x7fffffff || (double)total > 1.3 * (double)std::max<int64_t>(A->nnz, 1)) return;
+  A->sell_off.reserve((size_t)nsl + 1);
+  FLZ_CUDA(cudaMemcpy(A->sell_off.p, off.data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice));
+  A->sell_col.reserve((size_t)std::max<int64_t>(total, 1));
+  sell_fill_col_kernel<<<gs_blocks(A->n), 256>>>(A->n, A->rowptr.p, A->col.p, kLongRow, A->sell_off.p, A->sell_col.p);
+  FLZ_LAUNCH_CHECK();
+  FLZ_CUDA(cudaDeviceSynchronize());
+  A->sell_len = total;
+  A->sell = true;
+}
+
+template <class S>
+void scale_values_sell(const flz_matrix* A, double c, double e, S* out, cudaStream_t st) {
+  scale_values_sell_kernel<S><<<gs_blocks(A->n), 256, 0, st>>>(A->n, A->rowptr.p, A->diag_pos.p, A->val.p, kLongRow,
+                                                               A->sell_off.p, 2.0 / e, c, out);
+  FLZ_LAUNCH_CHECK();
+}
+template void scale_values_sell<double>(const flz_matrix*, double, double, double*, cudaStream_t);
+template void scale_values_sell<float>(const flz_matrix*, double, double, float*, cudaStream_t);
+template void scale_values_sell<__nv_bfloat16>(const flz_matrix*, double, double, __nv_bfloat16*, cudaStream_t);
+template void scale_values_sell<dev::dfloat>(const flz_matrix*, double, double, dev::dfloat*, cudaStream_t);
 
 int64_t find_diagonals(flz_matrix* A) {
   A->diag_pos.reserve((size_t)A->n);

@@ -115,6 +115,48 @@ __global__ void __launch_bounds__(kRows) clen_rows_kernel(
   }
 }
 
+// The same launch on the SELL-32 layout (see cheb_sell_kernel): coalesced,
+// independent loads of a row's indices and values, no staging.
+template <int R, class MS, class VS, class OutS, bool UNIT>
+__global__ void __launch_bounds__(kRows) clen_sell_kernel(
+    int n, const int* __restrict__ off, const int* __restrict__ scol, const MS* __restrict__ sval,
+    const VS* __restrict__ x, const VS* __restrict__ v, const VS* z, OutS* out, typename Arith<VS>::type alpha,
+    typename Arith<VS>::type g) {
+  using A = typename Arith<VS>::type;
+  allow_dependents();
+  const int row = blockIdx.x * kRows + (int)threadIdx.x;
+  if (row >= n) return;
+  const int sl = row >> 5;
+  const int o = __ldg(off + sl);
+  const int w = (__ldg(off + sl + 1) - o) >> 5;
+  const int base = o + (row & 31);
+  if (__ldg(scol + base) < 0) return;  // long row: clen_long_kernel
+  grid_dependency_wait();  // B_{k+1}, B_{k+2} are earlier launches' output
+  A base_v[R];
+  load_row<VS, R>(v + (size_t)row * R, base_v);
+#pragma unroll
+  for (int t = 0; t < R; ++t) base_v[t] = alpha * base_v[t];
+  if (z) {
+    A zz[R];
+    load_row<VS, R>(z + (size_t)row * R, zz);
+#pragma unroll
+    for (int t = 0; t < R; ++t) base_v[t] = base_v[t] - zz[t];
+  }
+  A s[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) s[t] = UNIT ? base_v[t] : A(0);
+  sell_row_sum<R, MS, VS, A>(scol, sval, base, w, x, s);
+  if (!UNIT) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) s[t] = fma(g, s[t], base_v[t]);
+  }
+  if constexpr (std::is_same<OutS, VS>::value) {
+    store_row_rounded<VS, R>(out + (size_t)row * R, s);
+  } else {
+    store_acc<R>(out + (size_t)row * R, s);
+  }
+}
+
 // The same launch for rows with more than `long_row` entries: one CTA per
 // row, strided entries, tree reduction in shared memory.
 template <int R, class MS, class VS, class OutS>
@@ -214,45 +256,50 @@ struct Launch {
 };
 
 template <int R, class MS, class VS, class WT>
-void launch_rows(const flz_matrix* A, const MS* val, const VS* v, const Launch& L, cudaStream_t st) {
+void launch_rows(const flz_matrix* A, const MS* vsell, const MS* val, const VS* v, const Launch& L, cudaStream_t st) {
   using Ar = typename Arith<VS>::type;
   const int n = (int)A->n;
   const int cap = std::min<int>(A->max_cta_nnz, 4096);
-  const size_t smem = (size_t)cap * (sizeof(MS) + sizeof(int));
+  const size_t smem = vsell ? 0 : (size_t)cap * (sizeof(MS) + sizeof(int));
   const unsigned grid = (unsigned)((n + kRows - 1) / kRows);
   const int nl = A->n_long;
   const int thr = nl > 0 ? kLongRow : 0x7fffffff;
   const VS* x = static_cast<const VS*>(L.x);
   const VS* z = static_cast<const VS*>(L.z);
   const Ar al = Ar(L.alpha), g = Ar(L.g);
-  if (L.to_w) {
-    WT* out = static_cast<WT*>(L.out);
-    if (L.dependent)
-      launch_dependent(clen_rows_kernel<R, MS, VS, WT, false>, grid, kRows, smem, st, n, cap, thr, A->rowptr.p,
-                       A->col.p, val, x, v, z, out, al, g);
-    else
-      clen_rows_kernel<R, MS, VS, WT, false><<<grid, kRows, smem, st>>>(n, cap, thr, A->rowptr.p, A->col.p, val, x, v, z, out, al, g);
+  const int* rp = A->rowptr.p;
+  const int* cl = A->col.p;
+  const int* of = A->sell_off.p;
+  const int* sc = A->sell_col.p;
+  // one launch of the row kernel (SELL-32 or staged CSR), as a programmatic
+  // dependent launch when it follows another launch of this recurrence
+  auto go = [&](auto out, auto unit_tag) {
+    using O = std::remove_pointer_t<decltype(out)>;
+    constexpr bool U = decltype(unit_tag)::value;
+    if (vsell) {
+      if (L.dependent)
+        launch_dependent(clen_sell_kernel<R, MS, VS, O, U>, grid, kRows, 0, st, n, of, sc, vsell, x, v, z, out, al, g);
+      else
+        clen_sell_kernel<R, MS, VS, O, U><<<grid, kRows, 0, st>>>(n, of, sc, vsell, x, v, z, out, al, g);
+    } else {
+      if (L.dependent)
+        launch_dependent(clen_rows_kernel<R, MS, VS, O, U>, grid, kRows, smem, st, n, cap, thr, rp, cl, val, x, v, z,
+                         out, al, g);
+      else
+        clen_rows_kernel<R, MS, VS, O, U><<<grid, kRows, smem, st>>>(n, cap, thr, rp, cl, val, x, v, z, out, al, g);
+    }
     FLZ_LAUNCH_CHECK();
     if (nl) {
-      clen_long_kernel<R, MS, VS, WT><<<nl, kRows, 0, st>>>(A->long_rows.p, A->rowptr.p, A->col.p, val, x, v, z, out, al, g);
+      clen_long_kernel<R, MS, VS, O><<<nl, kRows, 0, st>>>(A->long_rows.p, rp, cl, val, x, v, z, out, al, g);
       FLZ_LAUNCH_CHECK();
     }
-    return;
-  }
-  VS* out = static_cast<VS*>(L.out);
-  if (L.unit) {
-    // launches after the first overlap their CSR staging with the previous
-    // launch's tail (programmatic dependent launch)
-    launch_dependent(clen_rows_kernel<R, MS, VS, VS, true>, grid, kRows, smem, st, n, cap, thr, A->rowptr.p, A->col.p,
-                     val, x, v, z, out, al, g);
-  } else {
-    clen_rows_kernel<R, MS, VS, VS, false><<<grid, kRows, smem, st>>>(n, cap, thr, A->rowptr.p, A->col.p, val, x, v, z, out, al, g);
-  }
-  FLZ_LAUNCH_CHECK();
-  if (nl) {
-    clen_long_kernel<R, MS, VS, VS><<<nl, kRows, 0, st>>>(A->long_rows.p, A->rowptr.p, A->col.p, val, x, v, z, out, al, g);
-    FLZ_LAUNCH_CHECK();
-  }
+  };
+  if (L.to_w)
+    go(static_cast<WT*>(L.out), std::false_type{});
+  else if (L.unit)
+    go(static_cast<VS*>(L.out), std::true_type{});
+  else
+    go(static_cast<VS*>(L.out), std::false_type{});
 }
 
 template <class MS, class VS, class WT>
@@ -280,24 +327,24 @@ inline bool aligned_to(const void* p, size_t a) { return (reinterpret_cast<uintp
 }  // namespace
 
 template <class MS, class VS, class WT>
-void run_clenshaw(const flz_matrix* A, const MS* val, const double* b, int m, int r, const VS* v, VS* ba, VS* bb,
-                  WT* W, cudaStream_t st) {
+void run_clenshaw(const flz_matrix* A, const MS* vsell, const MS* val, const double* b, int m, int r, const VS* v,
+                  VS* ba, VS* bb, WT* W, cudaStream_t st) {
   const bool pow2 = r == 1 || r == 2 || r == 4 || r == 8 || r == 16;
   const size_t av = std::min<size_t>(16, r * sizeof(VS));
   const size_t aw = std::min<size_t>(16, r * sizeof(WT));
-  const bool rows = pow2 && A->max_cta_nnz > 0 && aligned_to(v, av) && aligned_to(ba, av) && aligned_to(bb, av) &&
-                    aligned_to(W, aw);
+  const bool rows = vsell || (pow2 && A->max_cta_nnz > 0 && aligned_to(v, av) && aligned_to(ba, av) &&
+                              aligned_to(bb, av) && aligned_to(W, aw));
   auto go = [&](const Launch& L) {
     if (!rows) {
       launch_lanes<MS, VS, WT>(A, val, r, v, L, st);
       return;
     }
     switch (r) {
-      case 1: launch_rows<1, MS, VS, WT>(A, val, v, L, st); break;
-      case 2: launch_rows<2, MS, VS, WT>(A, val, v, L, st); break;
-      case 4: launch_rows<4, MS, VS, WT>(A, val, v, L, st); break;
-      case 8: launch_rows<8, MS, VS, WT>(A, val, v, L, st); break;
-      default: launch_rows<16, MS, VS, WT>(A, val, v, L, st); break;
+      case 1: launch_rows<1, MS, VS, WT>(A, vsell, val, v, L, st); break;
+      case 2: launch_rows<2, MS, VS, WT>(A, vsell, val, v, L, st); break;
+      case 4: launch_rows<4, MS, VS, WT>(A, vsell, val, v, L, st); break;
+      case 8: launch_rows<8, MS, VS, WT>(A, vsell, val, v, L, st); break;
+      default: launch_rows<16, MS, VS, WT>(A, vsell, val, v, L, st); break;
     }
   };
   if (m == 1) {
@@ -327,16 +374,13 @@ void run_clenshaw(const flz_matrix* A, const MS* val, const double* b, int m, in
   }
 }
 
-template void run_clenshaw<double, double, double>(const flz_matrix*, const double*, const double*, int, int,
-                                                   const double*, double*, double*, double*, cudaStream_t);
-template void run_clenshaw<float, float, double>(const flz_matrix*, const float*, const double*, int, int, const float*,
-                                                 float*, float*, double*, cudaStream_t);
-template void run_clenshaw<__nv_bfloat16, __nv_bfloat16, double>(const flz_matrix*, const __nv_bfloat16*,
-                                                                 const double*, int, int, const __nv_bfloat16*,
-                                                                 __nv_bfloat16*, __nv_bfloat16*, double*, cudaStream_t);
-template void run_clenshaw<dfloat, dfloat, double>(const flz_matrix*, const dfloat*, const double*, int, int,
-                                                   const dfloat*, dfloat*, dfloat*, double*, cudaStream_t);
-template void run_clenshaw<dfloat, dfloat, dfloat>(const flz_matrix*, const dfloat*, const double*, int, int,
-                                                   const dfloat*, dfloat*, dfloat*, dfloat*, cudaStream_t);
+#define FLZ_CLENSHAW_INST(MS, VS, WT)                                                                         \
+  template void run_clenshaw<MS, VS, WT>(const flz_matrix*, const MS*, const MS*, const double*, int, int, const VS*, \
+                                         VS*, VS*, WT*, cudaStream_t);
+FLZ_CLENSHAW_INST(double, double, double)
+FLZ_CLENSHAW_INST(float, float, double)
+FLZ_CLENSHAW_INST(__nv_bfloat16, __nv_bfloat16, double)
+FLZ_CLENSHAW_INST(dfloat, dfloat, double)
+FLZ_CLENSHAW_INST(dfloat, dfloat, dfloat)
 
 }  // namespace flz

@@ -300,6 +300,42 @@ __device__ __forceinline__ void load_acc(const dfloat* p, dfloat (&v)[R]) {
   RowIO<dfloat, R>::load(p, v);
 }
 
+// Row sum s[t] += sum_j (2 Ahat)_{row, j} X[j, t] over one row of the SELL-32
+// layout: entry j of the row sits at base + 32 j (base = slice offset + lane),
+// so a warp's loads of column indices and values are coalesced and
+// independent of each other; U entries are in flight per thread.
+template <int R, class MS, class VS, class A>
+__device__ __forceinline__ void sell_row_sum(const int* __restrict__ scol, const MS* __restrict__ sval, int base,
+                                             int w, const VS* __restrict__ x, A (&s)[R]) {
+  constexpr int kRowBytes = R * (int)sizeof(A);
+  constexpr int U = kRowBytes <= 16 ? 8 : (kRowBytes <= 32 ? 4 : 2);
+  int j = 0;
+  for (; j + U <= w; j += U) {
+    int cj[U];
+    A a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      cj[u] = __ldg(scol + base + 32 * (j + u));
+      a[u] = to_arith(sval[base + 32 * (j + u)]);
+    }
+    A y[U][R];
+#pragma unroll
+    for (int u = 0; u < U; ++u) load_row<VS, R>(x + (size_t)cj[u] * R, y[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int t = 0; t < R; ++t) s[t] = fma(a[u], y[u][t], s[t]);
+  }
+  for (; j < w; ++j) {
+    const int cj = __ldg(scol + base + 32 * j);
+    const A a = to_arith(sval[base + 32 * j]);
+    A y[R];
+    load_row<VS, R>(x + (size_t)cj * R, y);
+#pragma unroll
+    for (int t = 0; t < R; ++t) s[t] = fma(a, y[t], s[t]);
+  }
+}
+
 #endif  // __CUDACC__
 
 }  // namespace dev

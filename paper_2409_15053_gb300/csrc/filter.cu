@@ -167,6 +167,54 @@ __global__ void __launch_bounds__(kRows) cheb_rows_kernel(
   store_acc<R>(acc_out + (size_t)row * R, acc);
 }
 
+// The fused degree step on the SELL-32 layout (one warp per 32-row slice, one
+// thread per row and all R columns): no shared-memory staging and no row
+// pointers; a row's column indices and values are coalesced loads that do not
+// depend on each other. Rows carrying the long-row marker are left to
+// cheb_long_kernel. Same arithmetic as cheb_rows_kernel.
+template <int R, class MS, class VS, class AccS, class OutS, bool FIRST>
+__global__ void __launch_bounds__(kRows) cheb_sell_kernel(
+    int n, const int* __restrict__ off, const int* __restrict__ scol, const MS* __restrict__ sval,
+    const VS* __restrict__ ycur, const VS* yprev, VS* ynext, const AccS* acc_in, OutS* acc_out,
+    typename Arith<VS>::type b_cur, typename Arith<VS>::type b_next) {
+  using A = typename Arith<VS>::type;
+  allow_dependents();
+  const int row = blockIdx.x * kRows + (int)threadIdx.x;
+  if (row >= n) return;
+  const int sl = row >> 5;
+  const int o = __ldg(off + sl);
+  const int w = (__ldg(off + sl + 1) - o) >> 5;
+  const int base = o + (row & 31);
+  if (__ldg(scol + base) < 0) return;  // long row: cheb_long_kernel
+  grid_dependency_wait();  // the vectors below are the previous degree's output
+  A s[R];
+  A acc[R];
+  if (FIRST) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) s[t] = A(0);
+  } else {
+    load_row<VS, R>(yprev + (size_t)row * R, s);
+#pragma unroll
+    for (int t = 0; t < R; ++t) s[t] = -s[t];
+    load_acc<R>(acc_in + (size_t)row * R, acc);
+  }
+  sell_row_sum<R, MS, VS, A>(scol, sval, base, w, ycur, s);
+  if (FIRST) {
+#pragma unroll
+    for (int t = 0; t < R; ++t) s[t] *= A(0.5);
+  }
+  store_row_rounded<VS, R>(ynext + (size_t)row * R, s);
+  if (FIRST) {
+    A v0[R];
+    load_row<VS, R>(ycur + (size_t)row * R, v0);
+#pragma unroll
+    for (int t = 0; t < R; ++t) acc[t] = b_cur * v0[t];
+  }
+#pragma unroll
+  for (int t = 0; t < R; ++t) acc[t] = fma(b_next, s[t], acc[t]);
+  store_acc<R>(acc_out + (size_t)row * R, acc);
+}
+
 // The same degree step for rows with more than `long_row` stored entries
 // (hubs of irregular graphs): one CTA per long row, its threads take strided
 // entries and the partial sums are combined in shared memory, so a hub costs
@@ -331,13 +379,68 @@ void run_rows(const flz_matrix* A, const MS* val, const double* b, int m, const 
   }
 }
 
+template <int R, class MS, class VS, class AccT, class WT>
+void run_sell(const flz_matrix* A, const MS* vsell, const MS* val, const double* b, int m, const VS* v, VS* ya,
+              VS* yb, AccT* acc, WT* W, cudaStream_t st) {
+  using Ar = typename Arith<VS>::type;
+  const int n = (int)A->n;
+  const unsigned grid = (unsigned)((n + kRows - 1) / kRows);
+  const int* of = A->sell_off.p;
+  const int* sc = A->sell_col.p;
+  const int* rp = A->rowptr.p;
+  const int* cl = A->col.p;
+  const int nl = A->n_long;
+  const int* lr = A->long_rows.p;
+  auto step = [&](bool first, bool last, const VS* cur, const VS* prev, VS* next, Ar bc, Ar bn) {
+    if (first && last) {
+      cheb_sell_kernel<R, MS, VS, AccT, WT, true><<<grid, kRows, 0, st>>>(n, of, sc, vsell, cur, prev, next, acc, W, bc, bn);
+      FLZ_LAUNCH_CHECK();
+      if (nl) cheb_long_kernel<R, MS, VS, AccT, WT, true><<<nl, kRows, 0, st>>>(lr, rp, cl, val, cur, prev, next, acc, W, bc, bn);
+    } else if (first) {
+      cheb_sell_kernel<R, MS, VS, AccT, AccT, true><<<grid, kRows, 0, st>>>(n, of, sc, vsell, cur, prev, next, acc, acc, bc, bn);
+      FLZ_LAUNCH_CHECK();
+      if (nl) cheb_long_kernel<R, MS, VS, AccT, AccT, true><<<nl, kRows, 0, st>>>(lr, rp, cl, val, cur, prev, next, acc, acc, bc, bn);
+    } else if (last) {
+      launch_dependent(cheb_sell_kernel<R, MS, VS, AccT, WT, false>, grid, kRows, 0, st, n, of, sc, vsell, cur, prev,
+                       next, acc, W, bc, bn);
+      FLZ_LAUNCH_CHECK();
+      if (nl) cheb_long_kernel<R, MS, VS, AccT, WT, false><<<nl, kRows, 0, st>>>(lr, rp, cl, val, cur, prev, next, acc, W, bc, bn);
+    } else {
+      launch_dependent(cheb_sell_kernel<R, MS, VS, AccT, AccT, false>, grid, kRows, 0, st, n, of, sc, vsell, cur,
+                       prev, next, acc, acc, bc, bn);
+      FLZ_LAUNCH_CHECK();
+      if (nl) cheb_long_kernel<R, MS, VS, AccT, AccT, false><<<nl, kRows, 0, st>>>(lr, rp, cl, val, cur, prev, next, acc, acc, bc, bn);
+    }
+    if (nl) FLZ_LAUNCH_CHECK();
+  };
+  step(true, m == 1, v, nullptr, ya, Ar(b[0]), Ar(b[1]));
+  const VS* prev = v;
+  const VS* cur = ya;
+  for (int k = 1; k < m; ++k) {
+    VS* next = (k == 1) ? yb : const_cast<VS*>(prev);
+    step(false, k + 1 == m, cur, prev, next, Ar(0), Ar(b[k + 1]));
+    prev = cur;
+    cur = next;
+  }
+}
+
 inline bool aligned_to(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 // Row-per-thread kernel for r in {1, 2, 4, 8, 16} when every block is aligned
 // for R-wide vector access; the lane-per-column kernel otherwise.
 template <class MS, class VS, class AccT, class WT>
-void run_recurrence(const flz_matrix* A, const MS* val, const double* b, int m, int r, const VS* v, VS* ya,
-                    VS* yb, AccT* acc, WT* W, cudaStream_t st) {
+void run_recurrence(const flz_matrix* A, const MS* vsell, const MS* val, const double* b, int m, int r, const VS* v,
+                    VS* ya, VS* yb, AccT* acc, WT* W, cudaStream_t st) {
+  if (vsell) {  // SELL-32 layout (the caller checked width and alignment)
+    switch (r) {
+      case 1: run_sell<1, MS, VS, AccT, WT>(A, vsell, val, b, m, v, ya, yb, acc, W, st); break;
+      case 2: run_sell<2, MS, VS, AccT, WT>(A, vsell, val, b, m, v, ya, yb, acc, W, st); break;
+      case 4: run_sell<4, MS, VS, AccT, WT>(A, vsell, val, b, m, v, ya, yb, acc, W, st); break;
+      case 8: run_sell<8, MS, VS, AccT, WT>(A, vsell, val, b, m, v, ya, yb, acc, W, st); break;
+      default: run_sell<16, MS, VS, AccT, WT>(A, vsell, val, b, m, v, ya, yb, acc, W, st); break;
+    }
+    return;
+  }
   const bool pow2 = r == 1 || r == 2 || r == 4 || r == 8 || r == 16;
   const size_t av = std::min<size_t>(16, r * sizeof(VS));
   const size_t aa = std::min<size_t>(16, r * sizeof(AccT));
@@ -397,6 +500,45 @@ const S* scaled(flz_matrix* A, DevBuf<S>& buf, int prec, double c, double e, cud
   return buf.p;
 }
 
+// The same in the SELL-32 layout.
+template <class S>
+const S* scaled_sell(flz_matrix* A, DevBuf<S>& buf, int prec, double c, double e, cudaStream_t st) {
+  if (!(A->ss_ok[prec] && A->ss_c[prec] == c && A->ss_e[prec] == e && buf.p)) {
+    buf.reserve((size_t)A->sell_len);
+    scale_values_sell<S>(A, c, e, buf.p, st);
+    A->ss_c[prec] = c;
+    A->ss_e[prec] = e;
+    A->ss_ok[prec] = true;
+  }
+  return buf.p;
+}
+
+// The filter's view of 2 Ahat: the SELL-32 values when that kernel runs
+// (power-of-two r, aligned blocks, a matrix with little padding), the CSR
+// values for the other kernels (and for long rows next to SELL).
+template <class S>
+struct ScaledMatrix {
+  const S* sell = nullptr;
+  const S* csr = nullptr;
+};
+
+template <class S>
+ScaledMatrix<S> prepare(flz_matrix* A, DevBuf<S>& csr_buf, DevBuf<S>& sell_buf, int prec, double c, double e,
+                        bool use_sell, cudaStream_t st) {
+  ScaledMatrix<S> out;
+  if (use_sell) out.sell = scaled_sell<S>(A, sell_buf, prec, c, e, st);
+  if (!use_sell || A->n_long > 0) out.csr = scaled<S>(A, csr_buf, prec, c, e, st);
+  return out;
+}
+
+// SELL-32 needs the row-per-thread form: r a power of two and R-wide aligned
+// access to the caller's blocks (the library's own scratch is always aligned).
+bool sell_usable(const flz_matrix* A, int r, const void* v, size_t v_elem, const void* w, size_t w_elem) {
+  const bool pow2 = r == 1 || r == 2 || r == 4 || r == 8 || r == 16;
+  return A->sell && pow2 && aligned_to(v, std::min<size_t>(16, r * v_elem)) &&
+         aligned_to(w, std::min<size_t>(16, r * w_elem));
+}
+
 }  // namespace
 
 void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m, int r, const double* V,
@@ -409,55 +551,56 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
   }
   const bool clen = recurrence == FLZ_REC_CLENSHAW;
   if (precision == FLZ_PREC_FP64) {
-    const double* sv = scaled<double>(A, A->sval64, 0, c, e, st);
+    const auto M = prepare<double>(A, A->sval64, A->ssell64, 0, c, e, sell_usable(A, r, V, 8, W, 8), st);
     A->ws64.reserve(2 * nr);
     double* ya = A->ws64.p;
     double* yb = A->ws64.p + nr;
     if (clen)
-      run_clenshaw<double, double, double>(A, sv, coeffs, m, r, V, ya, yb, W, st);
+      run_clenshaw<double, double, double>(A, M.sell, M.csr, coeffs, m, r, V, ya, yb, W, st);
     else  // the running sum lives in W directly (FP64 output)
-      run_recurrence<double, double, double, double>(A, sv, coeffs, m, r, V, ya, yb, W, W, st);
+      run_recurrence<double, double, double, double>(A, M.sell, M.csr, coeffs, m, r, V, ya, yb, W, W, st);
   } else if (precision == FLZ_PREC_FP32) {
-    const float* sv = scaled<float>(A, A->sval32, 1, c, e, st);
     A->ws32.reserve(4 * nr);
     float* vs = A->ws32.p;
     float* ya = vs + nr;
     float* yb = ya + nr;
     float* acc = yb + nr;
+    const auto M = prepare<float>(A, A->sval32, A->ssell32, 1, c, e, sell_usable(A, r, vs, 4, W, 8), st);
     convert_kernel<float><<<grid_stride_blocks(nr), 256, 0, st>>>(V, vs, nr);
     FLZ_LAUNCH_CHECK();
     if (clen)
-      run_clenshaw<float, float, double>(A, sv, coeffs, m, r, vs, ya, yb, W, st);
+      run_clenshaw<float, float, double>(A, M.sell, M.csr, coeffs, m, r, vs, ya, yb, W, st);
     else
-      run_recurrence<float, float, float, double>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
+      run_recurrence<float, float, float, double>(A, M.sell, M.csr, coeffs, m, r, vs, ya, yb, acc, W, st);
   } else if (precision == FLZ_PREC_BF16) {
-    const __nv_bfloat16* sv = scaled<__nv_bfloat16>(A, A->sval16, 2, c, e, st);
     A->ws16.reserve(3 * nr);
     __nv_bfloat16* vs = A->ws16.p;
     __nv_bfloat16* ya = vs + nr;
     __nv_bfloat16* yb = ya + nr;
+    const auto M = prepare<__nv_bfloat16>(A, A->sval16, A->ssell16, 2, c, e, sell_usable(A, r, vs, 2, W, 8), st);
     convert_kernel<__nv_bfloat16><<<grid_stride_blocks(nr), 256, 0, st>>>(V, vs, nr);
     FLZ_LAUNCH_CHECK();
     if (clen) {
-      run_clenshaw<__nv_bfloat16, __nv_bfloat16, double>(A, sv, coeffs, m, r, vs, ya, yb, W, st);
+      run_clenshaw<__nv_bfloat16, __nv_bfloat16, double>(A, M.sell, M.csr, coeffs, m, r, vs, ya, yb, W, st);
     } else {
       A->ws32.reserve(nr);
       float* acc = A->ws32.p;
-      run_recurrence<__nv_bfloat16, __nv_bfloat16, float, double>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
+      run_recurrence<__nv_bfloat16, __nv_bfloat16, float, double>(A, M.sell, M.csr, coeffs, m, r, vs, ya, yb, acc, W,
+                                                                  st);
     }
   } else if (precision == FLZ_PREC_DF64) {
-    const dfloat* sv = scaled<dfloat>(A, A->svaldf, 3, c, e, st);
     A->wsdf.reserve(4 * nr);
     dfloat* vs = A->wsdf.p;
     dfloat* ya = vs + nr;
     dfloat* yb = ya + nr;
     dfloat* acc = yb + nr;
+    const auto M = prepare<dfloat>(A, A->svaldf, A->sselldf, 3, c, e, sell_usable(A, r, vs, 8, W, 8), st);
     convert_kernel<dfloat><<<grid_stride_blocks(nr), 256, 0, st>>>(V, vs, nr);
     FLZ_LAUNCH_CHECK();
     if (clen)
-      run_clenshaw<dfloat, dfloat, double>(A, sv, coeffs, m, r, vs, ya, yb, W, st);
+      run_clenshaw<dfloat, dfloat, double>(A, M.sell, M.csr, coeffs, m, r, vs, ya, yb, W, st);
     else
-      run_recurrence<dfloat, dfloat, dfloat, double>(A, sv, coeffs, m, r, vs, ya, yb, acc, W, st);
+      run_recurrence<dfloat, dfloat, dfloat, double>(A, M.sell, M.csr, coeffs, m, r, vs, ya, yb, acc, W, st);
   } else {
     fail(FLZ_ERR_INVALID_ARG, "unknown precision %d", precision);
   }
@@ -471,14 +614,14 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
     FLZ_LAUNCH_CHECK();
     return;
   }
-  const dfloat* sv = scaled<dfloat>(A, A->svaldf, 3, c, e, st);
+  const auto M = prepare<dfloat>(A, A->svaldf, A->sselldf, 3, c, e, sell_usable(A, r, V, 8, W, 8), st);
   A->wsdf.reserve(2 * nr);
   dfloat* ya = A->wsdf.p;
   dfloat* yb = ya + nr;
   if (recurrence == FLZ_REC_CLENSHAW)
-    run_clenshaw<dfloat, dfloat, dfloat>(A, sv, coeffs, m, r, V, ya, yb, W, st);
+    run_clenshaw<dfloat, dfloat, dfloat>(A, M.sell, M.csr, coeffs, m, r, V, ya, yb, W, st);
   else  // the running sum lives in W directly
-    run_recurrence<dfloat, dfloat, dfloat, dfloat>(A, sv, coeffs, m, r, V, ya, yb, W, W, st);
+    run_recurrence<dfloat, dfloat, dfloat, dfloat>(A, M.sell, M.csr, coeffs, m, r, V, ya, yb, W, W, st);
 }
 
 void spmm(const flz_matrix* A, const double* X, double* Y, int s, int ld, cudaStream_t st) {

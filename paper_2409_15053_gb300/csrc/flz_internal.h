@@ -126,6 +126,21 @@ struct flz_matrix {
   int32_t max_cta_nnz = 0;             // most stored entries in any 256 consecutive rows
   flz::DevBuf<int32_t> long_rows;      // rows with more than kLongRow entries (filter's CTA-per-row tier)
   int32_t n_long = 0;
+  // SELL-32 copy of the structure for the filter (sliced ELLPACK: slice s =
+  // rows 32s..32s+31, entry j of lane l at sell_off[s] + 32 j + l; padding
+  // has column = own row and value 0; a row longer than kLongRow keeps one
+  // marker entry with column -1 and is filtered by the CTA-per-row kernel).
+  // Built when the padding stays below 30 % of the stored entries.
+  bool sell = false;
+  int64_t sell_len = 0;
+  flz::DevBuf<int32_t> sell_off;  // n_slices + 1 element offsets
+  flz::DevBuf<int32_t> sell_col;
+  flz::DevBuf<double> ssell64;
+  flz::DevBuf<float> ssell32;
+  flz::DevBuf<__nv_bfloat16> ssell16;
+  flz::DevBuf<flz::dev::dfloat> sselldf;
+  double ss_c[4] = {0.0, 0.0, 0.0, 0.0}, ss_e[4] = {0.0, 0.0, 0.0, 0.0};
+  bool ss_ok[4] = {false, false, false, false};
   // Scratch of flz_filter_apply: recurrence vectors and the running sum.
   flz::DevBuf<double> ws64;
   flz::DevBuf<float> ws32;
@@ -165,11 +180,11 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
 int filter_launch_count(int m, int precision);
 // ---- clenshaw.cu ----------------------------------------------------------------
 // W = p_m(Ahat) V by the Clenshaw recurrence with 2 Ahat stored in `val`
-// (MS) and the recurrence vectors in VS; v is V in VS, ba and bb are n x r
-// scratch, m >= 1.
+// (MS; `vsell` in the SELL-32 layout or null, `val` in CSR order) and the
+// recurrence vectors in VS; v is V in VS, ba and bb are n x r scratch, m >= 1.
 template <class MS, class VS, class WT>
-void run_clenshaw(const flz_matrix* A, const MS* val, const double* b, int m, int r, const VS* v, VS* ba, VS* bb,
-                  WT* W, cudaStream_t st);
+void run_clenshaw(const flz_matrix* A, const MS* vsell, const MS* val, const double* b, int m, int r, const VS* v,
+                  VS* ba, VS* bb, WT* W, cudaStream_t st);
 // Y = A X for an n x s block with row stride ld (s <= 16), FP64.
 void spmm(const flz_matrix* A, const double* X, double* Y, int s, int ld, cudaStream_t st);
 
@@ -208,6 +223,12 @@ void gershgorin(const flz_matrix* A, double* glo, double* ghi, int32_t* max_row_
 flz_status validate_csr(const flz_matrix* A, int check_symmetry);
 // Most stored entries in any `rows` consecutive rows starting at a multiple of `rows`.
 int32_t max_block_nnz(const flz_matrix* A, int rows);
+// Builds the SELL-32 structure of A (sell_off, sell_col) if its padding is
+// below 30 % of the stored entries; sets A->sell.
+void build_sell(flz_matrix* A);
+// 2 Ahat = (2/e)(A - cI) in storage type S in the SELL-32 layout.
+template <class S>
+void scale_values_sell(const flz_matrix* A, double c, double e, S* out, cudaStream_t st);
 // Fills A->diag_pos; returns the number of rows without a stored diagonal entry.
 int64_t find_diagonals(flz_matrix* A);
 // out[j] = (2/e)(val[j] - c [j is a diagonal position]) rounded to S.

@@ -19,6 +19,7 @@ from .matrices import (  # noqa: F401
     fd4_laplacian_3d,
     gaussian_wells_potential,
     powerlaw_graph_laplacian,
+    parsec_like_hamiltonian,
     uneven_batch,
     random_normal_block,
     diagonal_csr,

@@ -230,3 +230,103 @@ def csr_checksum(A: CSR) -> str:
     for arr in (A.rowptr, A.col, A.val):
         h.update(np.ascontiguousarray(arr).tobytes())
     return h.hexdigest()[:16]
+
+
+def fd_second_derivative_weights(half_order: int) -> np.ndarray:
+    """Central-difference weights c_0..c_N of f'' of order 2N on a unit grid.
+
+    c_k = 2 (-1)^(k+1) (N!)^2 / (k^2 (N-k)! (N+k)!) for k >= 1 and
+    c_0 = -2 sum_k c_k, so f''(x) ~ c_0 f(x) + sum_k c_k (f(x+k) + f(x-k)).
+    """
+    from math import factorial
+    N = int(half_order)
+    c = np.zeros(N + 1)
+    for k in range(1, N + 1):
+        c[k] = 2.0 * (-1) ** (k + 1) * factorial(N) ** 2 / (k * k * factorial(N - k) * factorial(N + k))
+    c[0] = -2.0 * c[1:].sum()
+    return c
+
+
+def parsec_like_hamiltonian(radius: float = 30.0, h: float = 0.563, half_order: int = 6, heavy: int = 87,
+                            light: int = 76, nl_radius: float = 3.8, seed: int = 0,
+                            heavy_depth: float = 0.9, heavy_width: float = 3.0, light_depth: float = 0.55,
+                            light_width: float = 2.0, nl_strength: float = 0.6, cluster: float = 0.85) -> CSR:
+    """A real-space Hamiltonian stand-in shaped like the PARSEC matrices of Table 1.
+
+    Grid points of a cubic lattice (spacing h) inside a sphere of ``radius``
+    grid units; kinetic term -1/2 Laplacian by central differences of order
+    2 * half_order (Dirichlet outside the sphere); a local potential that is a
+    sum of Gaussian wells at ``heavy`` + ``light`` atom sites (depths and
+    widths per species, widths in grid units); and for every heavy atom a
+    rank-one non-local term s p p^T, p the Gaussian of width nl_radius / 2
+    truncated to the ball of radius nl_radius around the atom (these dense
+    blocks carry most of the stored entries, as the paper's non-local term
+    does). Atom sites are drawn uniformly in the ball of radius
+    ``cluster`` * radius.
+
+    The defaults give the shape of Ge87H76 (Table 1: n = 112,985, nnz/n = 69.9,
+    spectrum [-1.21, 32.8]; Table 2: 212 eigenvalues in [-0.645, -0.0053]):
+    n = 113,081, nnz = 7,955,253 (70.4 per row), spectrum about [-1.25, 33.1]
+    and about 214 eigenvalues in that interval (a Chebyshev-moment estimate).
+    """
+    g = _rng(seed)
+    R = float(radius)
+    m = int(np.ceil(R))
+    ax = np.arange(-m, m + 1)
+    X, Y, Z = np.meshgrid(ax, ax, ax, indexing="ij")
+    inside = (X * X + Y * Y + Z * Z) <= R * R
+    pts = np.stack([Z[inside], Y[inside], X[inside]], axis=1)  # sorted lexicographically (z, y, x)
+    order = np.lexsort((pts[:, 2], pts[:, 1], pts[:, 0]))
+    pts = pts[order]
+    n = pts.shape[0]
+    side = 2 * m + 1
+    index = -np.ones(side ** 3, dtype=np.int64)
+    key = ((pts[:, 0] + m) * side + (pts[:, 1] + m)) * side + (pts[:, 2] + m)
+    index[key] = np.arange(n)
+    c = fd_second_derivative_weights(half_order)
+    rows, cols, vals = [np.arange(n)], [np.arange(n)], [np.full(n, -0.5 * 3.0 * c[0] / (h * h))]
+    for a in range(3):
+        for k in range(1, half_order + 1):
+            for sgn in (-1, 1):
+                q = pts.copy()
+                q[:, a] += sgn * k
+                ok = np.all(np.abs(q) <= m, axis=1)
+                kk = ((q[:, 0] + m) * side + (q[:, 1] + m)) * side + (q[:, 2] + m)
+                tgt = np.where(ok, index[np.where(ok, kk, 0)], -1)
+                sel = tgt >= 0
+                rows.append(np.nonzero(sel)[0])
+                cols.append(tgt[sel])
+                vals.append(np.full(int(sel.sum()), -0.5 * c[k] / (h * h)))
+    # atoms: uniform in the inner ball (rejection sampling on the cube)
+    def sites(count):
+        out = []
+        while len(out) < count:
+            u = (2.0 * g.random(3) - 1.0) * cluster * R
+            if u @ u <= (cluster * R) ** 2:
+                out.append(u)
+        return np.array(out).reshape(-1, 3)
+    heavy_xyz = sites(heavy)
+    light_xyz = sites(light)
+    fp = pts.astype(np.float64)
+    pot = np.zeros(n)
+    for xyz, depth, width in ((heavy_xyz, heavy_depth, heavy_width), (light_xyz, light_depth, light_width)):
+        for a in xyz:
+            d2 = np.sum((fp - a) ** 2, axis=1)
+            pot -= depth * np.exp(-d2 / (2.0 * width * width))
+    vals[0] = vals[0] + pot
+    for a in heavy_xyz:
+        d2 = np.sum((fp - a) ** 2, axis=1)
+        ball = np.nonzero(d2 <= nl_radius * nl_radius)[0]
+        p = np.exp(-d2[ball] / (2.0 * (0.5 * nl_radius) ** 2))
+        p /= np.linalg.norm(p)
+        rows.append(np.repeat(ball, ball.shape[0]))
+        cols.append(np.tile(ball, ball.shape[0]))
+        vals.append(nl_strength * np.outer(p, p).ravel())
+    import scipy.sparse as sp
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n)).tocsr()
+    A.sum_duplicates()
+    A.sort_indices()
+    A = (A + A.T) * 0.5  # exact symmetry of the assembled sum
+    A = A.tocsr()
+    A.sort_indices()
+    return CSR(n, A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.astype(np.float64))

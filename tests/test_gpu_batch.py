@@ -115,8 +115,8 @@ def test_batch_rejects_bad_arguments():
 @pytest.mark.parametrize("precision,tol", [(flz.FLZ_PREC_FP32, 1e-6), (flz.FLZ_PREC_FP64, 1e-10)],
                          ids=["fp32", "fp64"])
 def test_full_size_batch64_matches_oracle_reference(precision, tol):
-    # 64 problems, n log-uniform in [1e4, 2e5] (sum ~4.7e6), autotuned r, auto
-    # degree: the batched launch shape the benchmark times, against the
+    # 64 problems, n log-uniform in [1e4, 2e5] (sum ~4.7e6), autotuned r,
+    # degree 60: the batched launch shape the benchmark times, against the
     # eigenvalues the CPU oracle computed for every problem (tests/golden).
     # Counts exact; every eigenvalue within tol ||A|| of the oracle's (each
     # Rayleigh quotient with residual <= tol lies within tol ||A|| of an
@@ -130,7 +130,7 @@ def test_full_size_batch64_matches_oracle_reference(precision, tol):
     csrs = [c for c, _, _ in items]
     assert [csr_checksum(c) for c in csrs] == [p["matrix_checksum"] for p in ref]
     intervals = [(p["alpha"], p["beta"]) for p in ref]
-    st, out = run_batch(csrs, intervals, block_size=0, degree=0, check_every=5, precision=precision, tol=tol)
+    st, out = run_batch(csrs, intervals, block_size=0, degree=60, check_every=5, precision=precision, tol=tol)
     assert st == flz.FLZ_OK
     for c, p, o in zip(csrs, ref, out):
         want = np.array(p["eigenvalues"])

@@ -262,3 +262,54 @@ def test_jackson_damped_filter_matches_oracle(r, rec):
     W = run_filter(Mat(csr), c, e, coeffs, V, rec=rec)
     ref = chebyshev.clenshaw_apply(csr.to_scipy(), c, e, ref_coeffs, V)
     assert np.max(np.abs(W - ref)) < bound(csr, c, e, m, V, U64)
+
+
+def _stencil_with_hub(g=20, hub_degree=400, seed=17):
+    # 3D Laplacian (regular rows: the SELL-32 layout applies) plus one hub
+    # vertex joined to `hub_degree` grid points (a row far above 256 entries,
+    # left to the CTA-per-row kernel next to SELL).
+    import scipy.sparse as sp
+    from synth.matrices import CSR
+    S = laplacian_3d_7pt(g, g, g, 0.5 * np.linspace(0, 1, g ** 3)).to_scipy().tolil()
+    n = g ** 3
+    S.resize((n + 1, n + 1))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nb = rng.choice(n, hub_degree, replace=False)
+    w = 0.1 + 0.9 * rng.random(hub_degree)
+    for j, x in zip(nb, w):
+        S[n, j] = -x
+        S[j, n] = -x
+        S[j, j] = S[j, j] + x
+    S[n, n] = w.sum()
+    S = sp.csr_matrix(S)
+    S.sort_indices()
+    return CSR(n + 1, S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.astype(np.float64))
+
+
+@pytest.mark.parametrize("rec", RECS, ids=REC_IDS)
+@pytest.mark.parametrize("precision,u", [(flz.FLZ_PREC_FP64, U64), (flz.FLZ_PREC_FP32, U32), (flz.FLZ_PREC_DF64, UDF)])
+@pytest.mark.parametrize("r", [1, 4, 16])
+def test_regular_rows_with_a_hub(r, precision, u, rec):
+    csr = _stencil_with_hub()
+    assert np.diff(csr.rowptr).max() > 256
+    c, e = gershgorin_map(csr)
+    M = Mat(csr)
+    sell, entries, long_rows = flz.flz_matrix_format(M.h)
+    assert sell == 1 and long_rows == 1 and csr.nnz <= entries <= 1.3 * csr.nnz
+    m = 45
+    coeffs = chebyshev.filter_coefficients(-0.9, -0.5, m)
+    V = random_normal_block(csr.n, r, 23)
+    got = run_filter(M, c, e, coeffs, V, precision, rec)
+    ref = chebyshev.clenshaw_apply(csr.to_scipy(), c, e, coeffs, V)
+    assert np.max(np.abs(got - ref)) <= bound(csr, c, e, m, V, u)
+
+
+def test_storage_format_choice():
+    # regular stencils get the SELL-32 layout; power-law graphs (rows from 2 to
+    # thousands of entries) stay in CSR with their hubs in the long-row tier
+    M = Mat(laplacian_3d_7pt(30, 30, 30))
+    sell, entries, long_rows = flz.flz_matrix_format(M.h)
+    assert sell == 1 and long_rows == 0 and entries >= M.csr.nnz
+    G = Mat(powerlaw_graph_laplacian(20000, seed=11, i0=1))
+    sell, entries, long_rows = flz.flz_matrix_format(G.h)
+    assert sell == 0 and entries == 0 and long_rows > 0

@@ -47,3 +47,33 @@ def test_config2_matrix_matches_the_oracle_reference():
     A = laplacian_3d_7pt(g, g, g, CONFIG2["potential_scale"] * rng.random(g ** 3))
     assert csr_checksum(A) == ref["matrix_checksum"]
     assert CONFIG2["beta"] == ref["beta"] and CONFIG2["count"] == ref["count"] == len(ref["eigenvalues"])
+
+
+def test_fd_weights_are_exact_on_polynomials():
+    from synth.matrices import fd_second_derivative_weights
+    assert np.allclose(fd_second_derivative_weights(1), [-2.0, 1.0])
+    assert np.allclose(fd_second_derivative_weights(2), [-2.5, 4.0 / 3.0, -1.0 / 12.0])
+    for N in (3, 6):
+        c = fd_second_derivative_weights(N)
+        k = np.arange(1, N + 1)
+        # f = x^(2j) at x = 0: f'' = 2 for j = 1, 0 for 2 <= j <= N
+        for j in range(1, N + 1):
+            got = 2.0 * np.sum(c[1:] * k.astype(float) ** (2 * j))
+            assert abs(got - (2.0 if j == 1 else 0.0)) < 1e-9
+
+
+def test_parsec_like_hamiltonian_shape():
+    from synth.matrices import parsec_like_hamiltonian
+    A = parsec_like_hamiltonian(radius=12.0, heavy=10, light=8, seed=3)
+    S = A.to_scipy()
+    assert abs(S - S.T).max() == 0.0
+    assert np.all(np.diff(A.rowptr) > 0)
+    for i in range(0, A.n, 97):  # columns sorted within rows
+        row = A.col[A.rowptr[i]:A.rowptr[i + 1]]
+        assert np.all(np.diff(row) > 0)
+    # n = lattice points in the ball of radius 12
+    ax = np.arange(-12, 13)
+    X, Y, Z = np.meshgrid(ax, ax, ax, indexing="ij")
+    assert A.n == int(np.sum(X * X + Y * Y + Z * Z <= 144))
+    # the kinetic stencil alone gives 1 + 36 entries per interior row; the non-local blocks add more
+    assert A.nnz / A.n > 30
