@@ -35,7 +35,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from synth import laplacian_3d_7pt, parsec_like_hamiltonian, random_normal_block, uneven_batch  # noqa: E402
+from synth import (laplacian_3d_7pt, parsec_like_hamiltonian, powerlaw_graph_laplacian,  # noqa: E402
+                   random_normal_block, uneven_batch)
 from synth.workloads import BATCH64, CONFIG2  # noqa: E402
 
 METRIC = "eigenpairs/s at residual 1e-8 (3D 7-point Laplacian 100^3 + potential, FP64)"
@@ -234,7 +235,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32/BF16-filter solves reported under 'variants'")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch-of-64 leg")
-    ap.add_argument("--mode", default="solve", choices=["solve", "filter", "batch", "table2"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "filter", "batch", "table2", "graph"],
                     help="solve: whole flz_solve per step (default); filter: only flz_filter_apply at the "
                          "solver's shape, for the kernel roofline and profiling")
     args = ap.parse_args()
@@ -265,6 +266,8 @@ def main():
         return
     if args.mode == "table2":
         return table2_mode(flz, torch, prec, args)
+    if args.mode == "graph":
+        return graph_mode(flz, torch, args)
     csr = make_matrix()
     if args.mode == "filter":
         return filter_mode(flz, torch, csr, prec, args)
@@ -587,6 +590,68 @@ def table2_mode(flz, torch, prec, args):
                       "interval": [-0.645, -0.0053], "block_size": 3, "precision": args.precision,
                       "recurrence": args.recurrence, "damping": args.damping,
                       "tol": args.tol, "rows": rows}))
+
+
+def graph_mode(flz, torch, args):
+    """The irregular workload: a power-law graph Laplacian, n = 4e6.
+
+    Chung-Lu expected degrees (exponent 2.5, mean 15), weights U(0.1, 1), plus
+    a ring (seed 5): about 64e6 stored entries, rows from 3 to ~8200 entries.
+    Interval [alpha, beta] at the top of the spectrum holding about 500
+    eigenpairs (the modes localized on the heaviest hubs): alpha is the
+    520th-largest weighted degree, beta lies above the spectrum. Block size
+    16. The FP32-storage filter (tol 1e-6, its attainable residual) and the
+    double-FP32 mode (tol 1e-10) against plain FP64 (tol 1e-10), one timed
+    solve each after a warm-up; eigenvalue differences to the FP64 run."""
+    t0 = time.time()
+    csr = powerlaw_graph_laplacian(4_000_000, seed=5)
+    gen_s = time.time() - t0
+    deg = np.diff(csr.rowptr)
+    S_diag = np.zeros(csr.n)
+    rows = np.repeat(np.arange(csr.n), deg)
+    on = rows == csr.col
+    S_diag[rows[on]] = csr.val[on]
+    alpha = float(np.sort(S_diag)[-520])
+    h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+    stream = torch.cuda.current_stream()
+    out = {"mode": "graph", "n": csr.n, "nnz": csr.nnz, "max_row": int(deg.max()), "generate_s": gen_s,
+           "alpha": alpha, "block_size": 16, "degree": args.degree}
+    ref = None
+    for name, prec, tol in (("fp64", flz.FLZ_PREC_FP64, 1e-10), ("fp32_filter", flz.FLZ_PREC_FP32, 1e-6),
+                            ("df64", flz.FLZ_PREC_DF64, 1e-10)):
+        p = flz.flz_params_default()
+        p.block_size = 16
+        p.degree = args.degree
+        p.precision = prec
+        p.tol = tol
+        p.check_every = 10
+        p.max_basis = 1600
+        s = flz.flz_solver_create(h, p)
+        flz.flz_solver_set_interval(s, alpha, 1e9)
+        flz.flz_solve(s, stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = flz.flz_solve(s, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        x = flz.flz_get_stats(s)
+        vals = flz.flz_get_eigenvalues(s)
+        res = flz.flz_get_residuals(s)
+        if name == "fp64":
+            ref = vals.copy()
+        out[name] = {"status": flz.flz_status_string(st), "seconds": e0.elapsed_time(e1) / 1e3,
+                     "count": int(vals.shape[0]), "iters": int(x["iters"]), "degree": int(x["degree"]),
+                     "max_residual": float(res.max()) if res.size else None,
+                     "eigenpairs_per_s_at_1e-8": float(np.sum(res <= 1e-8)) / (e0.elapsed_time(e1) / 1e3),
+                     "ms_filter": x["ms_filter"], "ms_orth": x["ms_orth"], "ms_check": x["ms_check"],
+                     "lmin": x["lmin"], "lmax": x["lmax"],
+                     "max_abs_eig_diff_vs_fp64": (float(np.max(np.abs(vals - ref)))
+                                                  if ref is not None and vals.shape == ref.shape and vals.size else None)}
+        flz.flz_solver_destroy(s)
+    flz.flz_matrix_destroy(h)
+    print(json.dumps(out))
 
 
 def filter_mode(flz, torch, csr, prec, args):
