@@ -249,6 +249,22 @@ flz_status flz_solver_set_interval(flz_solver* s, double alpha, double beta);
  * Synchronous: returns when the result is ready. EMPTY_INTERVAL,
  * NOT_CONVERGED (partial results readable), OUT_OF_MEMORY, CUDA_ERROR. */
 flz_status flz_solve(flz_solver* s, void* stream);
+/* Spectrum slicing (Section 5 names it as future work): [alpha, beta] is cut
+ * into nslices equal-width sub-intervals, solved one after another on the
+ * same matrix (bounds estimated once; each slice with its own, smaller
+ * Krylov basis and the solver's parameters), and the results are merged in
+ * ascending order into this solver's results. A pair found by two adjacent
+ * slices (an eigenvalue on a shared endpoint) is kept once: results count as
+ * the same pair when their eigenvalues agree to 10 tol ||A|| and their
+ * eigenvectors overlap by more than 1/2; when two slices hold different
+ * vectors of one multiple eigenspace, the second is orthogonalized against
+ * the first. Eigenvectors from different slices come from different Krylov
+ * bases: they are orthogonal to within (r_i + r_j) / gap (r the residuals in
+ * A's units), not to rounding. nslices = 1 is flz_solve. Stats add
+ * up the slices' steps, products and phase times. INVALID_ARG if
+ * nslices < 1; otherwise the statuses of flz_solve (NOT_CONVERGED if any
+ * slice did not converge; the other slices' results are readable). */
+flz_status flz_solve_sliced(flz_solver* s, int32_t nslices, void* stream);
 /* Number of eigenpairs found in [alpha, beta]. */
 flz_status flz_get_count(const flz_solver* s, int64_t* count);
 /* Ascending eigenvalues into host out[cap]; CAPACITY if cap < count. */

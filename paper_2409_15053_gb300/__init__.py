@@ -43,7 +43,7 @@ EXPORTED = (
     "flz_status_string", "flz_last_error", "flz_params_default",
     "flz_matrix_create_csr", "flz_matrix_destroy", "flz_matrix_info", "flz_matrix_format",
     "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_jackson_factors", "flz_filter_degree", "flz_spectrum_bounds",
-    "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_sym_eig", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve",
+    "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_sym_eig", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve", "flz_solve_sliced",
     "flz_get_count", "flz_get_eigenvalues", "flz_get_eigenvectors", "flz_get_residuals", "flz_get_stats",
     "flz_batch_create", "flz_batch_destroy", "flz_batch_solve", "flz_batch_get_count", "flz_batch_get_eigenvalues",
     "flz_batch_get_residuals", "flz_batch_get_eigenvectors", "flz_batch_get_stats",
@@ -120,6 +120,7 @@ def lib() -> ctypes.CDLL:
         "flz_solver_destroy": (ctypes.c_int, [_vp]),
         "flz_solver_set_interval": (ctypes.c_int, [_vp, _dbl, _dbl]),
         "flz_solve": (ctypes.c_int, [_vp, _vp]),
+        "flz_solve_sliced": (ctypes.c_int, [_vp, _i32, _vp]),
         "flz_get_count": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
         "flz_get_eigenvalues": (ctypes.c_int, [_vp, _vp, _i64]),
         "flz_get_eigenvectors": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.c_int]),
@@ -297,6 +298,11 @@ def flz_solver_set_interval(s, alpha, beta):
 def flz_solve(s, stream=None) -> int:
     """Returns FLZ_OK or FLZ_ERR_NOT_CONVERGED (partial results readable); raises on other failures."""
     return _check(lib().flz_solve(s, _stream(stream)), allow=(FLZ_ERR_NOT_CONVERGED,))
+
+
+def flz_solve_sliced(s, nslices, stream=None) -> int:
+    """Spectrum slicing over nslices equal-width sub-intervals; results merged into s."""
+    return _check(lib().flz_solve_sliced(s, int(nslices), _stream(stream)), allow=(FLZ_ERR_NOT_CONVERGED,))
 
 
 def flz_get_count(s) -> int:

@@ -55,6 +55,7 @@ int auto_degree(double a, double b, double eps, int max_degree) {
 }
 
 flz_status solve(flz_solver* s, cudaStream_t st);
+flz_status solve_sliced(flz_solver* s, int nslices, cudaStream_t st);
 void bounds_entry(flz_matrix* A, int steps, int r, uint64_t seed, cudaStream_t st, double* lmin, double* lmax);
 
 }  // namespace flz
@@ -361,6 +362,25 @@ flz_status flz_solve(flz_solver* s, void* stream) {
     if (!s->has_interval) fail(FLZ_ERR_NO_INTERVAL, "set the interval first");
     const flz_status st = flz::solve(s, static_cast<cudaStream_t>(stream));
     if (st == FLZ_ERR_NOT_CONVERGED) flz::set_last_error("basis capacity reached before convergence; partial results");
+    return st;
+  } catch (const ::flz::Failure& f) {
+    return f.status;
+  } catch (const std::bad_alloc&) {
+    ::flz::set_last_error("host allocation failed");
+    return FLZ_ERR_OUT_OF_MEMORY;
+  } catch (...) {
+    ::flz::set_last_error("unexpected internal error");
+    return FLZ_ERR_CUDA;
+  }
+}
+
+flz_status flz_solve_sliced(flz_solver* s, int32_t nslices, void* stream) {
+  ::flz::clear_last_error();
+  try {
+    if (!s) fail(FLZ_ERR_INVALID_ARG, "solver is NULL");
+    if (!s->has_interval) fail(FLZ_ERR_NO_INTERVAL, "set the interval first");
+    const flz_status st = flz::solve_sliced(s, nslices, static_cast<cudaStream_t>(stream));
+    if (st == FLZ_ERR_NOT_CONVERGED) flz::set_last_error("a slice reached its basis capacity; partial results");
     return st;
   } catch (const ::flz::Failure& f) {
     return f.status;

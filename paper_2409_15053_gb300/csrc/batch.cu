@@ -98,10 +98,12 @@ __global__ void __launch_bounds__(kRowsB) seg_cheb_kernel(
     }
   }
   __syncthreads();
+  allow_dependents();
   if (row >= N) return;
   const int pi = problem_of(s_off, count, row);
   if (!active[pi] || k + 1 > mdeg[pi]) return;
   const int jb = __ldg(rowptr + row), je = __ldg(rowptr + row + 1);
+  grid_dependency_wait();  // the vectors below are the previous degree's output
   A s[R];
   if (FIRST) {
 #pragma unroll
@@ -111,7 +113,27 @@ __global__ void __launch_bounds__(kRowsB) seg_cheb_kernel(
 #pragma unroll
     for (int t = 0; t < R; ++t) s[t] = -s[t];
   }
-  for (int j = jb; j < je; ++j) {
+  // U independent row gathers in flight per thread (fewer for wide rows)
+  constexpr int kRowBytes = R * (int)sizeof(A);
+  constexpr int U = kRowBytes <= 16 ? 4 : (kRowBytes <= 32 ? 2 : 1);
+  int j = jb;
+  for (; j + U <= je; j += U) {
+    int cj[U];
+    A a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      cj[u] = staged ? s_col[j + u - j0] : __ldg(col + j + u);
+      a[u] = staged ? to_arith(s_val[j + u - j0]) : to_arith(sval[j + u]);
+    }
+    A y[U][R];
+#pragma unroll
+    for (int u = 0; u < U; ++u) load_row<VS, R>(ycur + (size_t)cj[u] * R, y[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int t = 0; t < R; ++t) s[t] = fma(a[u], y[u][t], s[t]);
+  }
+  for (; j < je; ++j) {
     const int cj = staged ? s_col[j - j0] : __ldg(col + j);
     const A a = staged ? to_arith(s_val[j - j0]) : to_arith(sval[j]);
     A y[R];
@@ -491,6 +513,7 @@ struct BatchEngine {
   DevBuf<__nv_bfloat16> sval16;
   DevBuf<int> jdev, active, mdeg, fail;
   int mmax = 0;
+  bool pdl = true;  // degree steps as programmatic dependent launches
   int n_chunks = 0;
 
   void setup(flz_batch* b, int r_, int nbmax_, int prec, cudaStream_t s) {
@@ -605,8 +628,14 @@ struct BatchEngine {
     const VS* cur = ya;
     for (int k = 1; k < mmax; ++k) {
       VS* next = (k == 1) ? yb : const_cast<VS*>(prev);
-      seg_cheb_kernel<R, MS, VS, AccS, false><<<grid, kRowsB, sm, st>>>((int)N, cap, rp, cl, sv, B->d_off.p, count, coef.p,
-                                                                        k, mdeg.p, active.p, cur, prev, next, acc);
+      // degrees after the first overlap their staging with the previous
+      // degree's tail (programmatic dependent launch, captured into the graph)
+      if (pdl)
+        launch_dependent(seg_cheb_kernel<R, MS, VS, AccS, false>, grid, kRowsB, sm, st, (int)N, cap, rp, cl, sv,
+                         B->d_off.p, count, coef.p, k, mdeg.p, active.p, cur, prev, next, acc);
+      else
+        seg_cheb_kernel<R, MS, VS, AccS, false><<<grid, kRowsB, sm, st>>>((int)N, cap, rp, cl, sv, B->d_off.p, count,
+                                                                          coef.p, k, mdeg.p, active.p, cur, prev, next, acc);
       FLZ_LAUNCH_CHECK();
       prev = cur;
       cur = next;
@@ -767,7 +796,7 @@ void run_lockstep(BatchEngine& E, int steps) {
 // allocates or synchronizes; if anything fails the capture is ended before
 // the error propagates, so the stream is usable again.
 template <int R>
-cudaGraphExec_t capture_step(BatchEngine& E) {
+cudaGraphExec_t capture_step_once(BatchEngine& E) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ge = nullptr;
   FLZ_CUDA(cudaStreamBeginCapture(E.st, cudaStreamCaptureModeThreadLocal));
@@ -787,6 +816,20 @@ cudaGraphExec_t capture_step(BatchEngine& E) {
   return ge;
 }
 
+// Captures one block step; if the programmatic dependent launches cannot be
+// captured, captures again with plain launches.
+template <int R>
+cudaGraphExec_t capture_step(BatchEngine& E) {
+  try {
+    return capture_step_once<R>(E);
+  } catch (const Failure&) {
+    if (!E.pdl) throw;
+    cudaGetLastError();
+    E.pdl = false;
+    return capture_step_once<R>(E);
+  }
+}
+
 template <int R>
 void batch_solve_r(flz_batch* B, cudaStream_t st) {
   const int count = B->count;
@@ -802,7 +845,10 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
 
   // ---- bounds: lockstep block Lanczos on A itself (degree-1 "filter" p(z) = z, c = 0, e = 1)
   {
-    const int nbk = std::max(2, (p.bounds_steps + R - 1) / R);
+    // at least 15 block steps (see estimate_bounds), within the smallest problem
+    int64_t nmin = B->off[1] - B->off[0];
+    for (int i = 1; i < count; ++i) nmin = std::min<int64_t>(nmin, B->off[i + 1] - B->off[i]);
+    const int nbk = (int)std::max<int64_t>(2, std::min<int64_t>(std::max(15, (p.bounds_steps + R - 1) / R), nmin / R - 1));
     BatchEngine E;
     E.setup(B, R, nbk + 1, FLZ_PREC_FP64, st);
     E.set_active(act);
@@ -850,9 +896,16 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
     flz_stats& s = B->stats[i];
     s.block_size = R;
     s.ms_bounds = ms_bounds;
+    // emptiness by the Gershgorin interval; an estimate that missed an extreme
+    // eigenvalue is widened to cover the interval (as in the single solver)
+    const flz_matrix* Ai = B->mats[i];
+    if (B->beta[i] < Ai->glo || B->alpha[i] > Ai->ghi)
+      fail(FLZ_ERR_EMPTY_INTERVAL, "problem %d: [%g, %g] misses the Gershgorin interval [%g, %g]", i, B->alpha[i],
+           B->beta[i], Ai->glo, Ai->ghi);
+    if (B->beta[i] < s.lmin) s.lmin = std::max(B->alpha[i], Ai->glo);
+    if (B->alpha[i] > s.lmax) s.lmax = std::min(B->beta[i], Ai->ghi);
     const double c = 0.5 * (s.lmin + s.lmax), e = 0.5 * (s.lmax - s.lmin);
     double am = (B->alpha[i] - c) / e, bm = (B->beta[i] - c) / e;
-    if (bm < -1.0 || am > 1.0) fail(FLZ_ERR_EMPTY_INTERVAL, "problem %d: [%g, %g] misses [%g, %g]", i, B->alpha[i], B->beta[i], s.lmin, s.lmax);
     am = std::max(am, -1.0);
     bm = std::min(bm, 1.0);
     const int m = p.degree > 0 ? p.degree : auto_degree(am, bm, p.degree_eps, p.max_degree);
@@ -1168,7 +1221,10 @@ flz_status batch_solve(flz_batch* B, cudaStream_t user) {
 }
 
 // Picks r in {4, 8, 16}: times one filter degree of the concatenated matrix at
-// each width and keeps the lowest time per vector.
+// each width; a wider block is taken only if it is at least 25 % cheaper per
+// vector than the current choice (a wider block reaches a lower Krylov degree
+// within the same basis capacity, and near-equal timings must not flip the
+// choice from run to run).
 int batch_autotune(flz_batch* B, cudaStream_t st) {
   double best = 1e300;
   int best_r = 4;
@@ -1199,7 +1255,7 @@ int batch_autotune(flz_batch* B, cudaStream_t st) {
     float ms = 0.f;
     FLZ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     const double per_vec = ms / r;
-    if (per_vec < best) {
+    if (per_vec < 0.75 * best) {
       best = per_vec;
       best_r = r;
     }

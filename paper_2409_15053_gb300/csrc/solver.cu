@@ -199,7 +199,9 @@ void orthonormal_start(Engine<T>& E, uint64_t seed) {
 // Spectrum bounds by block Lanczos on A (Section 2.2 after eq. transf).
 void estimate_bounds(flz_matrix* A, int steps, int r, uint64_t seed, cudaStream_t st, double* lmin, double* lmax) {
   const int64_t n = A->n;
-  int nb = std::max(2, (steps + r - 1) / r);
+  // at least 15 block steps: with wide blocks a fixed vector count would leave
+  // too low a Krylov degree to reach the extreme eigenvalues
+  int nb = std::max(15, (steps + r - 1) / r);
   nb = (int)std::min<int64_t>(nb, std::max<int64_t>(1, n / r));
   DevBuf<double> Qb, Wb, Cb, C2b, partb, smallb;
   Qb.reserve((size_t)(nb + 1) * n * r);
@@ -297,6 +299,13 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
     estimate_bounds(A, p.bounds_steps, r, p.seed * 7919u + 17u, st, &lmin, &lmax);
   }
   stats.ms_bounds = ms_since(t0);
+  // The Gershgorin interval contains the spectrum: an interval outside it is
+  // empty. One inside it but outside the Lanczos estimate means the estimate
+  // missed an extreme eigenvalue; the estimate is widened to cover it.
+  if (s->beta < A->glo || s->alpha > A->ghi)
+    fail(FLZ_ERR_EMPTY_INTERVAL, "[%g, %g] misses the Gershgorin interval [%g, %g]", s->alpha, s->beta, A->glo, A->ghi);
+  if (s->beta < lmin) lmin = std::max(s->alpha, A->glo);
+  if (s->alpha > lmax) lmax = std::min(s->beta, A->ghi);
   stats.lmin = lmin;
   stats.lmax = lmax;
   // 2. map (eq. transf)
@@ -531,6 +540,208 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
 flz_status solve(flz_solver* s, cudaStream_t st) {
   if (s->p.precision == FLZ_PREC_DF64) return solve_impl<dev::dfloat>(s, st);
   return solve_impl<double>(s, st);
+}
+
+// Spectrum slicing (named as future work in Section 5): [alpha, beta] is cut
+// into `nslices` equal-width sub-intervals solved one after another on the
+// same matrix with the same bounds (estimated once), each with its own
+// smaller Krylov basis. A pair found by two adjacent slices (an eigenvalue
+// on a shared endpoint) is kept once: two results count as the same pair
+// when their eigenvalues agree to 10 tol ||A|| and their eigenvectors
+// overlap by more than 1/2; the one with the smaller residual stays.
+flz_status solve_sliced(flz_solver* s, int nslices, cudaStream_t st) {
+  if (nslices < 1) fail(FLZ_ERR_INVALID_ARG, "nslices must be >= 1");
+  if (nslices == 1) return solve(s, st);
+  const auto t_start = Clock::now();
+  flz_matrix* A = s->A;
+  const int64_t n = A->n;
+  const flz_params& p = s->p;
+  if (p.block_size < 1 || p.block_size > 16 || p.block_size > n) fail(FLZ_ERR_INVALID_ARG, "block size invalid");
+  s->solved = false;
+  s->count = 0;
+  s->evals.clear();
+  s->resid.clear();
+  double lmin, lmax;
+  const auto tb = Clock::now();
+  if (p.lmin < p.lmax) {
+    lmin = p.lmin;
+    lmax = p.lmax;
+  } else {
+    estimate_bounds(A, p.bounds_steps, p.block_size, p.seed * 7919u + 17u, st, &lmin, &lmax);
+  }
+  const double ms_bounds = ms_since(tb);
+  if (s->beta < A->glo || s->alpha > A->ghi)
+    fail(FLZ_ERR_EMPTY_INTERVAL, "[%g, %g] misses the Gershgorin interval [%g, %g]", s->alpha, s->beta, A->glo, A->ghi);
+  if (s->beta < lmin) lmin = std::max(s->alpha, A->glo);
+  if (s->alpha > lmax) lmax = std::min(s->beta, A->ghi);
+  const double lo = std::max(s->alpha, lmin), hi = std::min(s->beta, lmax);
+  const double anorm = std::max(std::fabs(lmin), std::fabs(lmax));
+
+  flz_solver sub;
+  sub.A = A;
+  sub.p = p;
+  sub.p.lmin = lmin;
+  sub.p.lmax = lmax;
+  sub.has_interval = true;
+  std::vector<double> vals, res;
+  std::vector<int> slice_of;
+  DevBuf<double> vecs;  // n x total, column-major
+  flz_stats agg{};
+  agg.block_size = p.block_size;
+  agg.lmin = lmin;
+  agg.lmax = lmax;
+  agg.converged = 1;
+  bool all_ok = true;
+  for (int i = 0; i < nslices; ++i) {
+    sub.alpha = lo + (hi - lo) * i / nslices;
+    sub.beta = (i + 1 == nslices) ? hi : lo + (hi - lo) * (i + 1) / nslices;
+    sub.p.seed = p.seed + 104729ull * (uint64_t)i;
+    const flz_status si = solve(&sub, st);
+    if (si != FLZ_OK) all_ok = false;
+    const int64_t c = sub.count;
+    if (c > 0) {
+      const size_t have = vals.size();
+      DevBuf<double> grown;
+      grown.reserve((have + c) * (size_t)n);
+      if (have > 0) FLZ_CUDA(cudaMemcpyAsync(grown.p, vecs.p, sizeof(double) * have * n, cudaMemcpyDeviceToDevice, st));
+      FLZ_CUDA(cudaMemcpyAsync(grown.p + have * n, sub.evecs.p, sizeof(double) * c * n, cudaMemcpyDeviceToDevice, st));
+      FLZ_CUDA(cudaStreamSynchronize(st));
+      std::swap(grown.p, vecs.p);
+      std::swap(grown.count, vecs.count);
+      for (int64_t j = 0; j < c; ++j) {
+        vals.push_back(sub.evals[j]);
+        res.push_back(sub.resid[j]);
+        slice_of.push_back(i);
+      }
+    }
+    const flz_stats& x = sub.stats;
+    agg.iters += x.iters;
+    agg.matvecs += x.matvecs;
+    agg.degree = std::max(agg.degree, x.degree);
+    agg.checks += x.checks;
+    agg.converged = agg.converged && x.converged;
+    agg.ms_filter += x.ms_filter;
+    agg.ms_orth += x.ms_orth;
+    agg.ms_check += x.ms_check;
+    agg.basis_vectors = std::max(agg.basis_vectors, x.basis_vectors);
+    agg.kernel_launches += x.kernel_launches;
+    agg.max_residual = std::max(agg.max_residual, x.max_residual);
+  }
+  // merge: ascending order, pairs shared by adjacent slices kept once
+  const int64_t total = (int64_t)vals.size();
+  std::vector<int> order(total);
+  for (int64_t i = 0; i < total; ++i) order[i] = (int)i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return vals[a] < vals[b]; });
+  std::vector<char> drop(total, 0);
+  DevBuf<double> part, out1;
+  part.reserve(column_sums_scratch(n, 1) + 64);
+  out1.reserve(1);
+  auto overlap = [&](int ia, int ib) {
+    column_sums(vecs.p + (size_t)ia * n, vecs.p + (size_t)ib * n, nullptr, n, 1, 1, 0, out1.p, part.p, st);
+    double ov = 0.0;
+    FLZ_CUDA(cudaMemcpyAsync(&ov, out1.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    FLZ_CUDA(cudaStreamSynchronize(st));
+    return ov;
+  };
+  // clusters of eigenvalues that agree to 10 tol ||A||: when one holds results
+  // of several slices, the slice with the most members is kept whole; a result
+  // of another slice is dropped if its eigenvector lies mostly in the span of
+  // the kept ones (a repeated copy, possibly rotated inside a multiple
+  // eigenspace), and otherwise kept after orthogonalization against them
+  // (its Rayleigh quotient and residual recomputed): the two slices may each
+  // hold a different vector of one multiple eigenspace whose Rayleigh
+  // quotients fall on either side of the shared endpoint.
+  DevBuf<double> ax, scal;
+  ax.reserve((size_t)n);
+  scal.reserve(4);
+  auto put = [&](double v) {
+    FLZ_CUDA(cudaMemcpyAsync(scal.p, &v, sizeof(double), cudaMemcpyHostToDevice, st));
+  };
+  auto refresh = [&](int m) {  // unit-normalize vector m; recompute its Rayleigh quotient and residual
+    double* x = vecs.p + (size_t)m * n;
+    const double nrm = std::sqrt(std::max(overlap(m, m), 1e-300));
+    put(1.0 / nrm);
+    basis_update(x, 1, n, 1, scal.p, 1, 1.0, 0.0, x, 1, st);
+    spmm(A, x, ax.p, 1, 1, st);
+    column_sums(x, ax.p, nullptr, n, 1, 1, 0, out1.p, part.p, st);
+    double lam = 0.0;
+    FLZ_CUDA(cudaMemcpyAsync(&lam, out1.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    FLZ_CUDA(cudaStreamSynchronize(st));
+    put(lam);
+    column_sums(x, ax.p, scal.p, n, 1, 1, 1, out1.p, part.p, st);
+    double r2 = 0.0;
+    FLZ_CUDA(cudaMemcpyAsync(&r2, out1.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    FLZ_CUDA(cudaStreamSynchronize(st));
+    vals[m] = lam;
+    res[m] = std::sqrt(std::max(r2, 0.0)) / anorm;
+  };
+  const double close = 10.0 * p.tol * anorm;
+  for (int64_t a = 0; a < total;) {
+    int64_t b = a + 1;
+    while (b < total && vals[order[b]] - vals[order[b - 1]] <= close) ++b;
+    std::vector<int> members(order.begin() + a, order.begin() + b);
+    std::vector<int> per_slice(nslices, 0);
+    for (int m : members) per_slice[slice_of[m]]++;
+    int primary = 0;
+    for (int i = 1; i < nslices; ++i)
+      if (per_slice[i] > per_slice[primary]) primary = i;
+    int slices_present = 0;
+    for (int i = 0; i < nslices; ++i) slices_present += per_slice[i] > 0;
+    if (slices_present > 1) {
+      std::vector<int> kept;
+      for (int m : members)
+        if (slice_of[m] == primary) kept.push_back(m);
+      for (int m : members) {
+        if (slice_of[m] == primary) continue;
+        std::vector<double> ovs;
+        double proj2 = 0.0;
+        for (int u : kept) {
+          ovs.push_back(overlap(m, u));
+          proj2 += ovs.back() * ovs.back();
+        }
+        if (proj2 > 0.5) {
+          drop[m] = 1;
+          continue;
+        }
+        double* x = vecs.p + (size_t)m * n;
+        for (int pass = 0; pass < 2; ++pass) {  // Gram-Schmidt twice against the kept vectors
+          for (size_t q = 0; q < kept.size(); ++q) {
+            const double ov = pass == 0 ? ovs[q] : overlap(m, kept[q]);
+            put(-ov);
+            basis_update(vecs.p + (size_t)kept[q] * n, 1, n, 1, scal.p, 1, 1.0, 1.0, x, 1, st);
+          }
+        }
+        refresh(m);
+        kept.push_back(m);
+      }
+    }
+    a = b;
+  }
+  // the refreshed Rayleigh quotients may reorder neighbours
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return vals[x] < vals[y]; });
+  std::vector<int> keep;
+  for (int64_t a = 0; a < total; ++a)
+    if (!drop[order[a]]) keep.push_back(order[a]);
+  const int64_t found = (int64_t)keep.size();
+  s->evecs.reserve((size_t)std::max<int64_t>(found, 1) * n);
+  s->evals.resize(found);
+  s->resid.resize(found);
+  for (int64_t i = 0; i < found; ++i) {
+    FLZ_CUDA(cudaMemcpyAsync(s->evecs.p + (size_t)i * n, vecs.p + (size_t)keep[i] * n, sizeof(double) * n,
+                             cudaMemcpyDeviceToDevice, st));
+    s->evals[i] = vals[keep[i]];
+    s->resid[i] = res[keep[i]];
+  }
+  FLZ_CUDA(cudaStreamSynchronize(st));
+  s->count = found;
+  s->solved = true;
+  agg.count = found;
+  agg.ms_bounds = ms_bounds;
+  agg.c = 0.5 * (lmin + lmax);
+  agg.e = 0.5 * (lmax - lmin);
+  agg.ms_total = ms_since(t_start);
+  s->stats = agg;
+  return all_ok ? FLZ_OK : FLZ_ERR_NOT_CONVERGED;
 }
 
 }  // namespace flz

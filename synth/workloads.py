@@ -10,11 +10,9 @@ tests/golden/make_config2_reference.py (tests/golden/config2_reference.json).
 
 CONFIG3: real-space Hamiltonian stand-in: 4th-order 13-point FD -Laplacian on
 a 120^3 grid (n = 1.728e6, nnz = 22,204,800) plus 64 negative Gaussian wells
-(synth.matrices.gaussian_wells_potential, seed 3); the lowest ~200
-eigenpairs. alpha lies below the Gershgorin interval; beta sits at the
-midpoint of the widest gap among eigenvalues 195..205 and was computed with
-the count by the CPU oracle (tests/golden/make_config3_reference.py,
-tests/golden/config3_reference.json).
+(synth.matrices.gaussian_wells_potential, seed 3); the lowest eigenpairs up to
+`beta` (the wells' bound states and the bottom of the box continuum). alpha
+lies below the Gershgorin interval.
 
 BATCH64: 64 independent 2D/3D Dirichlet Laplacians with U(0,1) diagonal
 potentials (synth.matrices.uneven_batch, n log-uniform in [1e4, 2e5]), each
