@@ -329,9 +329,9 @@ inline bool aligned_to(const void* p, size_t a) { return (reinterpret_cast<uintp
 template <class MS, class VS, class WT>
 void run_clenshaw(const flz_matrix* A, const MS* vsell, const MS* val, const double* b, int m, int r, const VS* v,
                   VS* ba, VS* bb, WT* W, cudaStream_t st) {
-  const bool pow2 = r == 1 || r == 2 || r == 4 || r == 8 || r == 16;
-  const size_t av = std::min<size_t>(16, r * sizeof(VS));
-  const size_t aw = std::min<size_t>(16, r * sizeof(WT));
+  const bool pow2 = row_kernel_width(r);
+  const size_t av = row_alignment(r, sizeof(VS));
+  const size_t aw = row_alignment(r, sizeof(WT));
   const bool rows = vsell || (pow2 && A->max_cta_nnz > 0 && aligned_to(v, av) && aligned_to(ba, av) &&
                               aligned_to(bb, av) && aligned_to(W, aw));
   auto go = [&](const Launch& L) {
@@ -342,6 +342,7 @@ void run_clenshaw(const flz_matrix* A, const MS* vsell, const MS* val, const dou
     switch (r) {
       case 1: launch_rows<1, MS, VS, WT>(A, vsell, val, v, L, st); break;
       case 2: launch_rows<2, MS, VS, WT>(A, vsell, val, v, L, st); break;
+      case 3: launch_rows<3, MS, VS, WT>(A, vsell, val, v, L, st); break;
       case 4: launch_rows<4, MS, VS, WT>(A, vsell, val, v, L, st); break;
       case 8: launch_rows<8, MS, VS, WT>(A, vsell, val, v, L, st); break;
       default: launch_rows<16, MS, VS, WT>(A, vsell, val, v, L, st); break;

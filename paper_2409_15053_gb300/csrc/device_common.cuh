@@ -103,8 +103,9 @@ struct RowIO;
 template <int R>
 struct RowIO<double, R> {
   static __device__ __forceinline__ void load(const double* p, double (&v)[R]) {
-    if constexpr (R == 1) {
-      v[0] = p[0];
+    if constexpr (R == 1 || (R & (R - 1)) != 0) {  // one element at a time (odd widths: no aligned vectors)
+#pragma unroll
+      for (int i = 0; i < R; ++i) v[i] = p[i];
     } else {
 #pragma unroll
       for (int i = 0; i < R; i += 2) {
@@ -115,8 +116,9 @@ struct RowIO<double, R> {
     }
   }
   static __device__ __forceinline__ void store(double* p, const double (&v)[R]) {
-    if constexpr (R == 1) {
-      p[0] = v[0];
+    if constexpr (R == 1 || (R & (R - 1)) != 0) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) p[i] = v[i];
     } else {
 #pragma unroll
       for (int i = 0; i < R; i += 2) *reinterpret_cast<double2*>(p + i) = make_double2(v[i], v[i + 1]);
@@ -127,8 +129,9 @@ struct RowIO<double, R> {
 template <int R>
 struct RowIO<float, R> {
   static __device__ __forceinline__ void load(const float* p, float (&v)[R]) {
-    if constexpr (R == 1) {
-      v[0] = p[0];
+    if constexpr (R == 1 || (R & (R - 1)) != 0) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) v[i] = p[i];
     } else if constexpr (R == 2) {
       const float2 t = *reinterpret_cast<const float2*>(p);
       v[0] = t.x;
@@ -145,8 +148,9 @@ struct RowIO<float, R> {
     }
   }
   static __device__ __forceinline__ void store(float* p, const float (&v)[R]) {
-    if constexpr (R == 1) {
-      p[0] = v[0];
+    if constexpr (R == 1 || (R & (R - 1)) != 0) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) p[i] = v[i];
     } else if constexpr (R == 2) {
       *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
     } else {
@@ -159,9 +163,12 @@ struct RowIO<float, R> {
 template <int R>
 struct RowIO<dfloat, R> {
   static __device__ __forceinline__ void load(const dfloat* p, dfloat (&v)[R]) {
-    if constexpr (R == 1) {
-      const float2 t = *reinterpret_cast<const float2*>(p);
-      v[0] = dfloat(t.x, t.y);
+    if constexpr (R == 1 || (R & (R - 1)) != 0) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const float2 t = *reinterpret_cast<const float2*>(p + i);
+        v[i] = dfloat(t.x, t.y);
+      }
     } else {
 #pragma unroll
       for (int i = 0; i < R; i += 2) {
@@ -172,8 +179,9 @@ struct RowIO<dfloat, R> {
     }
   }
   static __device__ __forceinline__ void store(dfloat* p, const dfloat (&v)[R]) {
-    if constexpr (R == 1) {
-      *reinterpret_cast<float2*>(p) = make_float2(v[0].hi, v[0].lo);
+    if constexpr (R == 1 || (R & (R - 1)) != 0) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) *reinterpret_cast<float2*>(p + i) = make_float2(v[i].hi, v[i].lo);
     } else {
 #pragma unroll
       for (int i = 0; i < R; i += 2)
@@ -186,8 +194,9 @@ template <int R>
 struct RowIO<__nv_bfloat16, R> {
   // loads/stores R bf16 values widened to / narrowed from float
   static __device__ __forceinline__ void load(const __nv_bfloat16* p, float (&v)[R]) {
-    if constexpr (R == 1) {
-      v[0] = __bfloat162float(p[0]);
+    if constexpr (R == 1 || (R & (R - 1)) != 0) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) v[i] = __bfloat162float(p[i]);
     } else if constexpr (R == 2) {
       const float2 t = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
       v[0] = t.x;
@@ -213,6 +222,19 @@ struct RowIO<__nv_bfloat16, R> {
   }
   // rounds to bf16, stores, and returns the rounded values in v
   static __device__ __forceinline__ void store(__nv_bfloat16* p, float (&v)[R]) {
+    if constexpr (R != 1 && (R & (R - 1)) != 0) {  // odd widths: element by element, rounded values back in v
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v[i]);
+        p[i] = h;
+        v[i] = __bfloat162float(h);
+      }
+    } else {
+      store_pow2(p, v);
+    }
+  }
+  // rounds to bf16, stores, and returns the rounded values in v (R a power of two)
+  static __device__ __forceinline__ void store_pow2(__nv_bfloat16* p, float (&v)[R]) {
     __nv_bfloat162 h[(R + 1) / 2];
 #pragma unroll
     for (int i = 0; i < R; i += 2) {

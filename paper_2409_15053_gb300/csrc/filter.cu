@@ -435,16 +435,17 @@ void run_recurrence(const flz_matrix* A, const MS* vsell, const MS* val, const d
     switch (r) {
       case 1: run_sell<1, MS, VS, AccT, WT>(A, vsell, val, b, m, v, ya, yb, acc, W, st); break;
       case 2: run_sell<2, MS, VS, AccT, WT>(A, vsell, val, b, m, v, ya, yb, acc, W, st); break;
+      case 3: run_sell<3, MS, VS, AccT, WT>(A, vsell, val, b, m, v, ya, yb, acc, W, st); break;
       case 4: run_sell<4, MS, VS, AccT, WT>(A, vsell, val, b, m, v, ya, yb, acc, W, st); break;
       case 8: run_sell<8, MS, VS, AccT, WT>(A, vsell, val, b, m, v, ya, yb, acc, W, st); break;
       default: run_sell<16, MS, VS, AccT, WT>(A, vsell, val, b, m, v, ya, yb, acc, W, st); break;
     }
     return;
   }
-  const bool pow2 = r == 1 || r == 2 || r == 4 || r == 8 || r == 16;
-  const size_t av = std::min<size_t>(16, r * sizeof(VS));
-  const size_t aa = std::min<size_t>(16, r * sizeof(AccT));
-  const size_t aw = std::min<size_t>(16, r * sizeof(WT));
+  const bool pow2 = row_kernel_width(r);
+  const size_t av = row_alignment(r, sizeof(VS));
+  const size_t aa = row_alignment(r, sizeof(AccT));
+  const size_t aw = row_alignment(r, sizeof(WT));
   const bool ok = pow2 && A->max_cta_nnz > 0 && aligned_to(v, av) && aligned_to(ya, av) && aligned_to(yb, av) &&
                   aligned_to(acc, aa) && aligned_to(W, aw);
   if (!ok) {
@@ -454,6 +455,7 @@ void run_recurrence(const flz_matrix* A, const MS* vsell, const MS* val, const d
   switch (r) {
     case 1: run_rows<1, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
     case 2: run_rows<2, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
+    case 3: run_rows<3, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
     case 4: run_rows<4, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
     case 8: run_rows<8, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
     default: run_rows<16, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
@@ -531,12 +533,11 @@ ScaledMatrix<S> prepare(flz_matrix* A, DevBuf<S>& csr_buf, DevBuf<S>& sell_buf, 
   return out;
 }
 
-// SELL-32 needs the row-per-thread form: r a power of two and R-wide aligned
+// SELL-32 needs the row-per-thread form: r in {1, 2, 3, 4, 8, 16} and aligned
 // access to the caller's blocks (the library's own scratch is always aligned).
 bool sell_usable(const flz_matrix* A, int r, const void* v, size_t v_elem, const void* w, size_t w_elem) {
-  const bool pow2 = r == 1 || r == 2 || r == 4 || r == 8 || r == 16;
-  return A->sell && pow2 && aligned_to(v, std::min<size_t>(16, r * v_elem)) &&
-         aligned_to(w, std::min<size_t>(16, r * w_elem));
+  return A->sell && row_kernel_width(r) && aligned_to(v, row_alignment(r, v_elem)) &&
+         aligned_to(w, row_alignment(r, w_elem));
 }
 
 }  // namespace

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -167,6 +168,15 @@ namespace flz {
 
 // Rows with more stored entries than this are filtered by one CTA each.
 constexpr int kLongRow = 256;
+
+// Block widths with a row-per-thread filter kernel (one thread owns a row and
+// all its columns): powers of two with vector loads, and 3 (the paper's block
+// size) element by element.
+inline bool row_kernel_width(int r) { return r == 1 || r == 2 || r == 3 || r == 4 || r == 8 || r == 16; }
+// Alignment a row-per-thread kernel needs of a block of `elem`-byte values.
+inline size_t row_alignment(int r, size_t elem) {
+  return (r & (r - 1)) ? elem : std::min<size_t>(16, (size_t)r * elem);
+}
 
 // ---- filter.cu ----------------------------------------------------------------
 // W = p_m((A - cI)/e) V, V and W device FP64 n x r row-major.

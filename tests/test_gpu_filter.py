@@ -150,12 +150,13 @@ def test_laplacian_eigenvector_identity():
 
 @pytest.mark.parametrize("precision,u", [(flz.FLZ_PREC_FP32, U32), (flz.FLZ_PREC_BF16, UBF), (flz.FLZ_PREC_DF64, UDF)])
 @pytest.mark.parametrize("rec", RECS, ids=REC_IDS)
-def test_reduced_precision_filter_within_bound(precision, u, rec):
+@pytest.mark.parametrize("r", [3, 4])
+def test_reduced_precision_filter_within_bound(precision, u, rec, r):
     csr = laplacian_3d_7pt(16, 16, 16, 0.5 * np.linspace(0, 1, 4096))
     M = Mat(csr)
     m = 30
     coeffs = chebyshev.filter_coefficients(-1.0, -0.9, m)
-    V = random_normal_block(csr.n, 4, 5)
+    V = random_normal_block(csr.n, r, 5)
     got = run_filter(M, 6.25, 6.25, coeffs, V, precision, rec)
     ref = chebyshev.clenshaw_apply(csr.to_scipy(), 6.25, 6.25, coeffs, V)
     err = np.max(np.abs(got - ref))
@@ -288,7 +289,7 @@ def _stencil_with_hub(g=20, hub_degree=400, seed=17):
 
 @pytest.mark.parametrize("rec", RECS, ids=REC_IDS)
 @pytest.mark.parametrize("precision,u", [(flz.FLZ_PREC_FP64, U64), (flz.FLZ_PREC_FP32, U32), (flz.FLZ_PREC_DF64, UDF)])
-@pytest.mark.parametrize("r", [1, 4, 16])
+@pytest.mark.parametrize("r", [1, 3, 4, 16])
 def test_regular_rows_with_a_hub(r, precision, u, rec):
     csr = _stencil_with_hub()
     assert np.diff(csr.rowptr).max() > 256

@@ -68,7 +68,9 @@ def check_pairs(csr, out, tol, ortho=1e-10):
     R = S @ X - X * lam
     res = np.linalg.norm(R, axis=0) / norm_a
     assert np.all(res <= tol), res.max()
-    assert np.max(np.abs(X.T @ X - np.eye(X.shape[1]))) < ortho
+    G = np.abs(X.T @ X - np.eye(X.shape[1]))
+    i, j = np.unravel_index(np.argmax(G), G.shape)
+    assert G[i, j] < ortho, (int(i), int(j), float(lam[i]), float(lam[j]), float(G[i, j]), float(res[i]), float(res[j]))
 
 
 def sliced_ortho_bound(eigs, tol, norm_a):
