@@ -154,7 +154,8 @@ flz_status flz_matrix_info(const flz_matrix* A, int64_t* n, int64_t* nnz, double
 /* The filter's storage of A (an addition of this library; the paper uses plain
  * CSR): *sell = 1 if the SELL-32 layout (sliced ELLPACK, 32 rows per slice)
  * was built because its padding is below 30 % of the stored entries (regular
- * stencils; the filter then uses it for power-of-two r), *sell_entries its
+ * stencils; the filter then uses it for r in {1, 2, 3, 4, 8, 16}, in FP64
+ * only when the padding is at most 10 %), *sell_entries its
  * stored entries with padding, *long_rows the rows above 256 entries that a
  * CTA-per-row kernel filters. Any pointer may be NULL. */
 flz_status flz_matrix_format(const flz_matrix* A, int32_t* sell, int64_t* sell_entries, int32_t* long_rows);

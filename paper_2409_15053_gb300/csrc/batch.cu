@@ -1032,11 +1032,13 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
         WalkState& w = ws[i];
         const int cnt = std::min(16, K - pos);
         cnts[i] = cnt;
-        std::vector<int> idx(w.order.begin() + pos, w.order.begin() + pos + cnt);
+        // the walk so far plus this chunk in one call (see the single solver):
+        // copies of a multiple eigenvalue that straddle two chunks stay orthogonal
+        std::vector<int> idx(w.order.begin(), w.order.begin() + pos + cnt);
         std::vector<double> Y;
-        band_eigenvectors(w.T, K, R, w.theta, idx, Y, p.seed + (uint64_t)pos);
+        band_eigenvectors(w.T, K, R, w.theta, idx, Y, p.seed);
         for (int t = 0; t < cnt; ++t)
-          for (int q = 0; q < K; ++q) tab[((size_t)i * K + q) * 16 + t] = Y[(size_t)t * K + q];
+          for (int q = 0; q < K; ++q) tab[((size_t)i * K + q) * 16 + t] = Y[(size_t)(pos + t) * K + q];
       });
       Ytab.reserve(tab.size());
       FLZ_CUDA(cudaMemcpyAsync(Ytab.p, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st));

@@ -329,7 +329,7 @@ inline bool aligned_to(const void* p, size_t a) { return (reinterpret_cast<uintp
 template <class MS, class VS, class WT>
 void run_clenshaw(const flz_matrix* A, const MS* vsell, const MS* val, const double* b, int m, int r, const VS* v,
                   VS* ba, VS* bb, WT* W, cudaStream_t st) {
-  const bool pow2 = row_kernel_width(r);
+  const bool pow2 = row_kernel_width(r) && r != 3;  // r = 3: SELL-32 or the lane kernel
   const size_t av = row_alignment(r, sizeof(VS));
   const size_t aw = row_alignment(r, sizeof(WT));
   const bool rows = vsell || (pow2 && A->max_cta_nnz > 0 && aligned_to(v, av) && aligned_to(ba, av) &&

@@ -442,7 +442,9 @@ void run_recurrence(const flz_matrix* A, const MS* vsell, const MS* val, const d
     }
     return;
   }
-  const bool pow2 = row_kernel_width(r);
+  // the staged-CSR row kernel serves power-of-two widths; r = 3 runs row per
+  // thread only in the SELL-32 layout (else the lane-per-column kernel)
+  const bool pow2 = row_kernel_width(r) && r != 3;
   const size_t av = row_alignment(r, sizeof(VS));
   const size_t aa = row_alignment(r, sizeof(AccT));
   const size_t aw = row_alignment(r, sizeof(WT));
@@ -455,7 +457,6 @@ void run_recurrence(const flz_matrix* A, const MS* vsell, const MS* val, const d
   switch (r) {
     case 1: run_rows<1, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
     case 2: run_rows<2, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
-    case 3: run_rows<3, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
     case 4: run_rows<4, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
     case 8: run_rows<8, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
     default: run_rows<16, MS, VS, AccT, WT>(A, val, b, m, v, ya, yb, acc, W, st); break;
@@ -535,7 +536,13 @@ ScaledMatrix<S> prepare(flz_matrix* A, DevBuf<S>& csr_buf, DevBuf<S>& sell_buf, 
 
 // SELL-32 needs the row-per-thread form: r in {1, 2, 3, 4, 8, 16} and aligned
 // access to the caller's blocks (the library's own scratch is always aligned).
-bool sell_usable(const flz_matrix* A, int r, const void* v, size_t v_elem, const void* w, size_t w_elem) {
+// The FP64 step is bound by the FP64 pipe, where every padding entry costs a
+// multiply-add like a stored one: FP64 takes SELL-32 only when the padding is
+// at most 10 % of the stored entries (the memory-bound precisions up to the
+// layout's own 30 %).
+bool sell_usable(const flz_matrix* A, int r, const void* v, size_t v_elem, const void* w, size_t w_elem,
+                 bool fp64 = false) {
+  if (fp64 && (double)A->sell_len > 1.10 * (double)A->nnz) return false;
   return A->sell && row_kernel_width(r) && aligned_to(v, row_alignment(r, v_elem)) &&
          aligned_to(w, row_alignment(r, w_elem));
 }
@@ -552,7 +559,7 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
   }
   const bool clen = recurrence == FLZ_REC_CLENSHAW;
   if (precision == FLZ_PREC_FP64) {
-    const auto M = prepare<double>(A, A->sval64, A->ssell64, 0, c, e, sell_usable(A, r, V, 8, W, 8), st);
+    const auto M = prepare<double>(A, A->sval64, A->ssell64, 0, c, e, sell_usable(A, r, V, 8, W, 8, true), st);
     A->ws64.reserve(2 * nr);
     double* ya = A->ws64.p;
     double* yb = A->ws64.p + nr;

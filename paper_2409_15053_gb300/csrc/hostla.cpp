@@ -212,15 +212,14 @@ void band_eigenvectors(const std::vector<double>& T, int K, int b, const std::ve
   const double eps = 2.220446049250313e-16;
   const double tiny = eps * tnorm;
   const double close = 1e-3 * tnorm;
-  // Process in order of the requested eigenvalues; vectors of eigenvalues
-  // within `close` of each other are orthogonalized against earlier ones.
-  std::vector<int> order(cnt);
-  for (int t = 0; t < cnt; ++t) order[t] = t;
-  std::sort(order.begin(), order.end(), [&](int x, int y) { return theta[idx[x]] < theta[idx[y]]; });
+  // Vectors are computed in the order of `idx`, each orthogonalized against
+  // every earlier one whose eigenvalue lies within `close` (the copies of a
+  // multiple or tightly clustered eigenvalue). The start vector of index i
+  // depends only on `seed` and i, so a call whose idx begins with the idx of
+  // an earlier call reproduces that call's vectors exactly.
   BandLU f;
   std::vector<double> x(K);
-  for (int oi = 0; oi < cnt; ++oi) {
-    const int t = order[oi];
+  for (int t = 0; t < cnt; ++t) {
     const double lam = theta[idx[t]];
     band_lu(T, K, b, lam, tiny, f);
     uint64_t st = mix64(seed ^ (uint64_t)(idx[t] + 1) * 0x2545F4914F6CDD1Dull);
@@ -230,10 +229,8 @@ void band_eigenvectors(const std::vector<double>& T, int K, int b, const std::ve
     }
     for (int it = 0; it < 4; ++it) {
       band_solve(f, x.data());
-      // orthogonalize against already computed vectors of close eigenvalues
-      for (int pj = oi - 1; pj >= 0; --pj) {
-        const int tp = order[pj];
-        if (lam - theta[idx[tp]] > close) break;
+      for (int tp = 0; tp < t; ++tp) {
+        if (std::fabs(lam - theta[idx[tp]]) > close) continue;
         const double* yp = &Y[(size_t)tp * K];
         double dot = 0.0;
         for (int i = 0; i < K; ++i) dot += yp[i] * x[i];

@@ -415,9 +415,14 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
     int walked = 0;
     for (int pos = 0; pos < K && !walk_done && all_small; pos += 16) {
       const int cnt = std::min(16, K - pos);
-      std::vector<int> idx(order.begin() + pos, order.begin() + pos + cnt);
-      std::vector<double> Y;
-      band_eigenvectors(T, K, r, theta, idx, Y, p.seed + (uint64_t)pos);
+      // eigenvectors of T for the walk so far plus this chunk in one call:
+      // the earlier ones are reproduced exactly and the new ones are kept
+      // orthogonal to them (copies of a multiple eigenvalue may straddle two
+      // chunks); this chunk's vectors are the last `cnt` columns
+      std::vector<int> idx(order.begin(), order.begin() + pos + cnt);
+      std::vector<double> Yall;
+      band_eigenvectors(T, K, r, theta, idx, Yall, p.seed);
+      std::vector<double> Y(Yall.begin() + (size_t)pos * K, Yall.end());
       // a pair failing the gate ends the walk before its Ritz vector is formed
       if (!(p_residual(&Y[0]) <= p_gate)) {
         all_small = false;

@@ -377,3 +377,19 @@ def test_full_size_fd4_hamiltonian_fp64_and_df64():
     assert np.max(np.abs(a["vals"] - b["vals"])) < 1e-10 * norm_a
     check_pairs(csr, a, 1e-10)
     check_pairs(csr, b, 1e-10)
+
+
+def test_multiple_eigenvalues_stay_orthonormal_across_walk_chunks():
+    # Triple eigenvalues (a diagonal matrix, each value three times): the
+    # convergence walk forms Ritz vectors 16 at a time, so some triples are
+    # split between two chunks; their eigenvectors must still be orthonormal.
+    from synth import diagonal_csr
+    d = np.repeat(np.linspace(0.0, 1.0, 101), 3)
+    csr = diagonal_csr(d)
+    a, b = 0.2025, 0.4975  # 30 distinct values, 90 eigenvalues, endpoints in gaps
+    ref = d[(d >= a) & (d <= b)]
+    out = solve(csr, a, b, block_size=3, degree=80, check_every=10, lmin=-0.001, lmax=1.001)
+    assert out["status"] == flz.FLZ_OK
+    assert out["vals"].shape == ref.shape == (90,)
+    assert np.max(np.abs(out["vals"] - ref)) < 1e-10
+    check_pairs(csr, out, 1e-10)
