@@ -225,7 +225,7 @@ def main():
     ap.add_argument("--block-size", type=int, default=4)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16", "df64"])
     ap.add_argument("--recurrence", default="forward", choices=["forward", "clenshaw"])
-    ap.add_argument("--damping", default="none", choices=["none", "jackson"],
+    ap.add_argument("--damping", default="none", choices=["none", "jackson", "sigma"],
                     help="filter damping (the paper uses none)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--check-every", type=int, default=CONFIG2["check_every"])
@@ -284,7 +284,7 @@ def main():
     p.check_every = args.check_every
     p.precision = prec
     p.recurrence = {"forward": flz.FLZ_REC_FORWARD, "clenshaw": flz.FLZ_REC_CLENSHAW}[args.recurrence]
-    p.damping = 1 if args.damping == "jackson" else 0
+    p.damping = {"none": 0, "jackson": 1, "sigma": 2}[args.damping]
     p.seed = 1 + rank
     s = flz.flz_solver_create(h, p)
     flz.flz_solver_set_interval(s, alpha, beta)
@@ -564,7 +564,7 @@ def table2_mode(flz, torch, prec, args):
         p.tol = args.tol
         p.check_every = 30
         p.recurrence = {"forward": flz.FLZ_REC_FORWARD, "clenshaw": flz.FLZ_REC_CLENSHAW}[args.recurrence]
-        p.damping = 1 if args.damping == "jackson" else 0
+        p.damping = {"none": 0, "jackson": 1, "sigma": 2}[args.damping]
         s = flz.flz_solver_create(h, p)
         flz.flz_solver_set_interval(s, -0.645, -0.0053)
         flz.flz_solve(s, stream)

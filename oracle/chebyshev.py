@@ -120,3 +120,22 @@ def jackson_factors(m: int) -> np.ndarray:
 def damped_filter_coefficients(alpha: float, beta: float, m: int) -> np.ndarray:
     """Jackson-damped coefficients g_k b_k of the ideal filter on [alpha, beta]."""
     return filter_coefficients(alpha, beta, m) * jackson_factors(m)
+
+
+def lanczos_sigma_factors(m: int) -> np.ndarray:
+    """Lanczos sigma factors sigma_0..sigma_m: sigma_k = sin(k pi/(m+1)) / (k pi/(m+1)), sigma_0 = 1.
+
+    Another damping of the truncated series (not used by the paper): it
+    averages the partial sum over one period of its highest term, which
+    shrinks the Gibbs overshoot without removing it.
+    """
+    k = np.arange(m + 1, dtype=np.float64)
+    x = k * np.pi / (m + 1)
+    out = np.ones(m + 1)
+    out[1:] = np.sin(x[1:]) / x[1:]
+    return out
+
+
+def sigma_damped_filter_coefficients(alpha: float, beta: float, m: int) -> np.ndarray:
+    """Lanczos-sigma-damped coefficients sigma_k b_k of the ideal filter on [alpha, beta]."""
+    return filter_coefficients(alpha, beta, m) * lanczos_sigma_factors(m)

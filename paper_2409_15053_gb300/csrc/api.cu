@@ -41,6 +41,23 @@ void jackson_factors(int m, double* g) {
   for (int k = 0; k <= m; ++k) g[k] = ((m - k + 1) * std::cos(k * a) + std::sin(k * a) / std::tan(a)) / (m + 1);
 }
 
+void lanczos_sigma_factors(int m, double* g) {
+  g[0] = 1.0;
+  for (int k = 1; k <= m; ++k) {
+    const double x = k * M_PI / (m + 1);
+    g[k] = std::sin(x) / x;
+  }
+}
+
+void damping_factors(int damping, int m, double* g) {
+  if (damping == 1)
+    jackson_factors(m, g);
+  else if (damping == 2)
+    lanczos_sigma_factors(m, g);
+  else
+    for (int k = 0; k <= m; ++k) g[k] = 1.0;
+}
+
 int auto_degree(double a, double b, double eps, int max_degree) {
   const double ta = std::acos(a), tb = std::acos(b);
   const double phi2 = ta - tb;
@@ -165,6 +182,13 @@ flz_status flz_jackson_factors(int32_t degree, double* out) {
   FLZ_API_BEGIN
   if (!out || degree < 0) fail(FLZ_ERR_INVALID_ARG, "out is NULL or degree < 0");
   flz::jackson_factors(degree, out);
+  FLZ_API_END
+}
+
+flz_status flz_lanczos_sigma_factors(int32_t degree, double* out) {
+  FLZ_API_BEGIN
+  if (!out || degree < 0) fail(FLZ_ERR_INVALID_ARG, "out is NULL or degree < 0");
+  flz::lanczos_sigma_factors(degree, out);
   FLZ_API_END
 }
 
@@ -329,7 +353,7 @@ flz_status flz_solver_create(flz_matrix* A, const flz_params* params, flz_solver
   else flz_params_default(&p);
   if (p.block_size < 1 || p.block_size > 16 || p.block_size > A->n) fail(FLZ_ERR_INVALID_ARG, "block_size must be in [1, min(16, n)]");
   if (p.degree < 0 || p.max_degree < 1 || p.check_every < 1 || !(p.tol > 0.0) || !(p.degree_eps > 0.0) ||
-      p.bounds_steps < 1 || p.max_basis < 0 || p.guard < 0 || p.damping < 0 || p.damping > 1 ||
+      p.bounds_steps < 1 || p.max_basis < 0 || p.guard < 0 || p.damping < 0 || p.damping > 2 ||
       (p.recurrence != FLZ_REC_FORWARD && p.recurrence != FLZ_REC_CLENSHAW))
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_DF64) fail(FLZ_ERR_INVALID_ARG, "bad precision");

@@ -723,6 +723,8 @@ struct WalkState {
   std::vector<int> order;
   std::vector<double> theta, T;
   int K = 0;
+  std::vector<double> walkY;  // eigenvectors of T formed so far in this check
+  std::vector<int> walkIdx;
 };
 
 }  // namespace
@@ -912,9 +914,9 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
     if (m < 1) fail(FLZ_ERR_CAPACITY, "problem %d: no degree <= %d meets the degree rule", i, p.max_degree);
     coeffs[i].resize(m + 1);
     chebyshev_coefficients(am, bm, m, coeffs[i].data());
-    if (p.damping == 1) {
+    if (p.damping != 0) {
       std::vector<double> g(m + 1);
-      jackson_factors(m, g.data());
+      damping_factors(p.damping, m, g.data());
       for (int q = 0; q <= m; ++q) coeffs[i][q] *= g[q];
     }
     s.c = c;
@@ -1032,13 +1034,15 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
         WalkState& w = ws[i];
         const int cnt = std::min(16, K - pos);
         cnts[i] = cnt;
-        // the walk so far plus this chunk in one call (see the single solver):
-        // copies of a multiple eigenvalue that straddle two chunks stay orthogonal
-        std::vector<int> idx(w.order.begin(), w.order.begin() + pos + cnt);
+        // kept orthogonal to the earlier chunks' vectors of nearby eigenvalues
+        // (copies of a multiple eigenvalue may straddle two chunks)
+        std::vector<int> idx(w.order.begin() + pos, w.order.begin() + pos + cnt);
         std::vector<double> Y;
-        band_eigenvectors(w.T, K, R, w.theta, idx, Y, p.seed);
+        band_eigenvectors(w.T, K, R, w.theta, idx, Y, p.seed, &w.walkY, &w.walkIdx);
+        w.walkY.insert(w.walkY.end(), Y.begin(), Y.end());
+        w.walkIdx.insert(w.walkIdx.end(), idx.begin(), idx.end());
         for (int t = 0; t < cnt; ++t)
-          for (int q = 0; q < K; ++q) tab[((size_t)i * K + q) * 16 + t] = Y[(size_t)(pos + t) * K + q];
+          for (int q = 0; q < K; ++q) tab[((size_t)i * K + q) * 16 + t] = Y[(size_t)t * K + q];
       });
       Ytab.reserve(tab.size());
       FLZ_CUDA(cudaMemcpyAsync(Ytab.p, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st));
@@ -1288,7 +1292,7 @@ flz_status flz_batch_create(int32_t count, flz_matrix* const* mats, const double
         p.block_size == 16))
     fail(FLZ_ERR_INVALID_ARG, "batch block_size must be 0 (autotune) or one of 1, 2, 4, 8, 16");
   if (p.degree < 0 || p.max_degree < 1 || p.check_every < 1 || !(p.tol > 0.0) || p.bounds_steps < 1 ||
-      p.damping < 0 || p.damping > 1)
+      p.damping < 0 || p.damping > 2)
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.recurrence != FLZ_REC_FORWARD) fail(FLZ_ERR_INVALID_ARG, "batches use the forward recurrence only");
   if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_BF16)

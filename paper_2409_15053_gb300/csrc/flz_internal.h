@@ -253,7 +253,8 @@ void band_eigenvalues(const std::vector<double>& T, int K, int b, std::vector<do
 // the band matrix with partial pivoting; vectors of close eigenvalues are
 // orthogonalized against each other. Y is K x count column-major.
 void band_eigenvectors(const std::vector<double>& T, int K, int b, const std::vector<double>& theta,
-                       const std::vector<int>& idx, std::vector<double>& Y, uint64_t seed);
+                       const std::vector<int>& idx, std::vector<double>& Y, uint64_t seed,
+                       const std::vector<double>* prevY = nullptr, const std::vector<int>* prevIdx = nullptr);
 // Dense symmetric eigen-decomposition: A (n x n row-major, destroyed), w
 // ascending, Z row-major with column k the eigenvector of w[k].
 void dense_sym_eig(std::vector<double>& A, int n, std::vector<double>& w, std::vector<double>& Z);
@@ -267,6 +268,9 @@ void upper_inverse(const double* R, int s, double* Rinv);
 // ---- coefficients (api.cu) --------------------------------------------------------------
 void chebyshev_coefficients(double a, double b, int m, double* out);
 void jackson_factors(int m, double* g);
+void lanczos_sigma_factors(int m, double* g);
+// Damping factors of params.damping (0: all ones, 1: Jackson, 2: Lanczos sigma).
+void damping_factors(int damping, int m, double* g);
 int auto_degree(double a, double b, double eps, int max_degree);
 
 }  // namespace flz

@@ -199,7 +199,9 @@ inline uint64_t mix64(uint64_t z) {
 }  // namespace
 
 void band_eigenvectors(const std::vector<double>& T, int K, int b, const std::vector<double>& theta,
-                       const std::vector<int>& idx, std::vector<double>& Y, uint64_t seed) {
+                       const std::vector<int>& idx, std::vector<double>& Y, uint64_t seed,
+                       const std::vector<double>* prevY, const std::vector<int>* prevIdx) {
+  const int nprev = prevIdx ? (int)prevIdx->size() : 0;
   const int cnt = (int)idx.size();
   Y.assign((size_t)K * cnt, 0.0);
   double tnorm = 0.0;
@@ -213,10 +215,10 @@ void band_eigenvectors(const std::vector<double>& T, int K, int b, const std::ve
   const double tiny = eps * tnorm;
   const double close = 1e-3 * tnorm;
   // Vectors are computed in the order of `idx`, each orthogonalized against
-  // every earlier one whose eigenvalue lies within `close` (the copies of a
-  // multiple or tightly clustered eigenvalue). The start vector of index i
-  // depends only on `seed` and i, so a call whose idx begins with the idx of
-  // an earlier call reproduces that call's vectors exactly.
+  // every earlier one -- of this call, and the given vectors of earlier calls
+  // (prevY, columns for prevIdx) -- whose eigenvalue lies within `close`: the
+  // copies of a multiple or tightly clustered eigenvalue stay orthogonal when
+  // they are requested in different calls.
   BandLU f;
   std::vector<double> x(K);
   for (int t = 0; t < cnt; ++t) {
@@ -229,6 +231,13 @@ void band_eigenvectors(const std::vector<double>& T, int K, int b, const std::ve
     }
     for (int it = 0; it < 4; ++it) {
       band_solve(f, x.data());
+      for (int tp = 0; tp < nprev; ++tp) {
+        if (std::fabs(lam - theta[(*prevIdx)[tp]]) > close) continue;
+        const double* yp = &(*prevY)[(size_t)tp * K];
+        double dot = 0.0;
+        for (int i = 0; i < K; ++i) dot += yp[i] * x[i];
+        for (int i = 0; i < K; ++i) x[i] -= dot * yp[i];
+      }
       for (int tp = 0; tp < t; ++tp) {
         if (std::fabs(lam - theta[idx[tp]]) > close) continue;
         const double* yp = &Y[(size_t)tp * K];

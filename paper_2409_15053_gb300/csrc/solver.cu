@@ -324,9 +324,9 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   stats.degree = m;
   std::vector<double> coeffs(m + 1);
   chebyshev_coefficients(am, bm, m, coeffs.data());
-  if (p.damping == 1) {
+  if (p.damping != 0) {
     std::vector<double> g(m + 1);
-    jackson_factors(m, g.data());
+    damping_factors(p.damping, m, g.data());
     for (int k = 0; k <= m; ++k) coeffs[k] *= g[k];
   }
   const double anorm = std::max(std::fabs(lmin), std::fabs(lmax));
@@ -413,16 +413,18 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
       }
     }
     int walked = 0;
+    std::vector<double> walkY;  // eigenvectors of T formed so far in this check
+    std::vector<int> walkIdx;
     for (int pos = 0; pos < K && !walk_done && all_small; pos += 16) {
       const int cnt = std::min(16, K - pos);
-      // eigenvectors of T for the walk so far plus this chunk in one call:
-      // the earlier ones are reproduced exactly and the new ones are kept
-      // orthogonal to them (copies of a multiple eigenvalue may straddle two
-      // chunks); this chunk's vectors are the last `cnt` columns
-      std::vector<int> idx(order.begin(), order.begin() + pos + cnt);
-      std::vector<double> Yall;
-      band_eigenvectors(T, K, r, theta, idx, Yall, p.seed);
-      std::vector<double> Y(Yall.begin() + (size_t)pos * K, Yall.end());
+      // eigenvectors of T for this chunk, kept orthogonal to the earlier
+      // chunks' vectors of nearby eigenvalues (copies of a multiple
+      // eigenvalue may straddle two chunks)
+      std::vector<int> idx(order.begin() + pos, order.begin() + pos + cnt);
+      std::vector<double> Y;
+      band_eigenvectors(T, K, r, theta, idx, Y, p.seed, &walkY, &walkIdx);
+      walkY.insert(walkY.end(), Y.begin(), Y.end());
+      walkIdx.insert(walkIdx.end(), idx.begin(), idx.end());
       // a pair failing the gate ends the walk before its Ritz vector is formed
       if (!(p_residual(&Y[0]) <= p_gate)) {
         all_small = false;

@@ -56,6 +56,11 @@ def test_jackson_factors_match_oracle(m):
     assert np.max(np.abs(flz.flz_jackson_factors(m) - chebyshev.jackson_factors(m))) < 1e-14
 
 
+@pytest.mark.parametrize("m", [0, 1, 9, 100])
+def test_lanczos_sigma_factors_match_oracle(m):
+    assert np.max(np.abs(flz.flz_lanczos_sigma_factors(m) - chebyshev.lanczos_sigma_factors(m))) < 1e-15
+
+
 def test_degree_rule_reproduces_table2():
     import json
     rows = json.load(open(os.path.join(ROOT, "tests", "golden", "table2_auto_degree.json")))["rows"]

@@ -131,11 +131,13 @@ def test_interior_window_block3_vs_dense(rec):
     _dense_case(laplacian_3d_7pt(10, 11, 12, rng.random(1320)), 500, 30, block_size=3, degree=80, recurrence=rec)
 
 
-def test_jackson_damped_filter_vs_dense():
-    # Damping widens the filter's transition band but keeps p_m in [0, 1]; the
-    # solver must still return every eigenvalue of the window.
+@pytest.mark.parametrize("damping", [1, 2], ids=["jackson", "sigma"])
+def test_damped_filter_vs_dense(damping):
+    # Damping widens the filter's transition band and tames the Gibbs
+    # oscillations; the solver must still return every eigenvalue of the window.
     rng = np.random.Generator(np.random.PCG64(8))
-    out = _dense_case(laplacian_3d_7pt(10, 11, 12, rng.random(1320)), 500, 30, block_size=3, degree=120, damping=1)
+    out = _dense_case(laplacian_3d_7pt(10, 11, 12, rng.random(1320)), 500, 30, block_size=3, degree=120,
+                      damping=damping)
     assert out["stats"]["degree"] == 120
 
 
@@ -203,7 +205,7 @@ def test_call_order_and_capacity_errors():
     assert e.value.status == flz.FLZ_ERR_CAPACITY
     flz.flz_solver_destroy(s)
     p = flz.flz_params_default()
-    p.damping = 2
+    p.damping = 3
     with pytest.raises(flz.FlzError) as e:
         flz.flz_solver_create(h, p)
     assert e.value.status == flz.FLZ_ERR_INVALID_ARG
@@ -386,10 +388,10 @@ def test_multiple_eigenvalues_stay_orthonormal_across_walk_chunks():
     from synth import diagonal_csr
     d = np.repeat(np.linspace(0.0, 1.0, 101), 3)
     csr = diagonal_csr(d)
-    a, b = 0.2025, 0.4975  # 30 distinct values, 90 eigenvalues, endpoints in gaps
+    a, b = 0.2025, 0.4975  # 29 distinct values (0.21 ... 0.49), 87 eigenvalues, endpoints in gaps
     ref = d[(d >= a) & (d <= b)]
     out = solve(csr, a, b, block_size=3, degree=80, check_every=10, lmin=-0.001, lmax=1.001)
     assert out["status"] == flz.FLZ_OK
-    assert out["vals"].shape == ref.shape == (90,)
+    assert out["vals"].shape == ref.shape == (87,)
     assert np.max(np.abs(out["vals"] - ref)) < 1e-10
     check_pairs(csr, out, 1e-10)

@@ -203,3 +203,26 @@ def test_jackson_damped_filter_has_no_gibbs_overshoot(a, b):
         far = b + 0.5 if b + 0.5 <= 1 else a - 0.5
         vals = ch.clenshaw_scalar(ch.damped_filter_coefficients(a, b, 400), np.array([mid, far]))
         assert vals[0] > 0.9 and abs(vals[1]) < 0.05
+
+
+def test_lanczos_sigma_factors_are_the_sinc_of_the_grid():
+    for m in (1, 9, 60):
+        g = ch.lanczos_sigma_factors(m)
+        assert g[0] == 1.0 and np.all(np.diff(g) < 0) and g[-1] > 0
+        k = np.arange(1, m + 1)
+        # sinc via numpy's own normalized sinc: sin(pi x)/(pi x) at x = k/(m+1)
+        assert np.max(np.abs(g[1:] - np.sinc(k / (m + 1)))) < 1e-15
+
+
+@pytest.mark.parametrize("a,b", [(0.1, 0.3), (-1.0, -0.5)])
+def test_sigma_damping_shrinks_the_gibbs_overshoot(a, b):
+    # The sigma-damped partial sum of a unit jump overshoots by about 1.2 %
+    # (against about 9 % for plain truncation): smaller, not removed.
+    z = np.cos(np.linspace(0.0, np.pi, 40001))
+    m = 200
+    plain = ch.clenshaw_scalar(ch.filter_coefficients(a, b, m), z)
+    sig = ch.clenshaw_scalar(ch.sigma_damped_filter_coefficients(a, b, m), z)
+    over_plain = max(plain.max() - 1.0, -plain.min())
+    over_sig = max(sig.max() - 1.0, -sig.min())
+    assert over_plain > 0.07
+    assert 0.002 < over_sig < 0.03
