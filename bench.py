@@ -115,6 +115,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_ranks(seconds, pairs, dist=None, device="cpu"):
+    """Whole-job totals over the ranks: the slowest rank's time (every rank's
+    timed region starts after a barrier) and the eigenpairs all ranks found.
+    Single process: the inputs."""
+    if dist is None:
+        return seconds, pairs
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    c = torch.tensor([pairs], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
+
+
 def filter_bytes_per_launch(n, nnz, r, s_val=8, s_vec=8, s_acc=8, recurrence="forward"):
     # CSR once (values + int32 columns + int32 row pointers) and the vector
     # streams. Forward: gather Y_k, read Y_{k-1}, write Y_{k+1}, read and
@@ -319,12 +333,7 @@ def main():
         stats_list.append(flz.flz_get_stats(s))
         assert st == flz.FLZ_OK, flz.flz_status_string(st)
     clocks = sampler.stop()
-    total_time = float(np.sum(times))
-    if dist is not None:
-        t = torch.tensor([total_time], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_time = float(t.item())
-    total_pairs = sum(found) * world
+    total_time, total_pairs = aggregate_ranks(float(np.sum(times)), int(sum(found)), dist, "cuda")
     value = total_pairs / total_time
     st = stats_list[-1]
 
