@@ -253,7 +253,11 @@ flz_status flz_solver_set_interval(flz_solver* s, double alpha, double beta);
 /* Runs the filtered Lanczos procedure: bounds, map, degree, coefficients,
  * block Lanczos on p(A) with full reorthogonalization, periodic Rayleigh-Ritz
  * and residual checks, Rayleigh quotients of the converged Ritz vectors.
- * Synchronous: returns when the result is ready. EMPTY_INTERVAL,
+ * Synchronous: returns when the result is ready. An interval that covers the
+ * whole spectrum makes the filter constant, which cannot separate
+ * eigenvectors; that case runs unfiltered block Lanczos (p(z) = z). When the
+ * basis spans the whole space (K = n) and every Ritz pair passed, the solve
+ * has converged. EMPTY_INTERVAL (outside the Gershgorin interval),
  * NOT_CONVERGED (partial results readable), OUT_OF_MEMORY, CUDA_ERROR. */
 flz_status flz_solve(flz_solver* s, void* stream);
 /* Spectrum slicing (Section 5 names it as future work): [alpha, beta] is cut

@@ -306,6 +306,11 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
     fail(FLZ_ERR_EMPTY_INTERVAL, "[%g, %g] misses the Gershgorin interval [%g, %g]", s->alpha, s->beta, A->glo, A->ghi);
   if (s->beta < lmin) lmin = std::max(s->alpha, A->glo);
   if (s->alpha > lmax) lmax = std::min(s->beta, A->ghi);
+  if (!(lmax > lmin)) {  // a single-point spectrum (n = 1, A = cI): any enclosing interval maps it
+    const double pad = 1e-3 * std::max(1.0, std::fabs(lmin));
+    lmin -= pad;
+    lmax += pad;
+  }
   stats.lmin = lmin;
   stats.lmax = lmax;
   // 2. map (eq. transf)
@@ -318,13 +323,22 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   bm = std::min(bm, 1.0);
   stats.alpha_mapped = am;
   stats.beta_mapped = bm;
-  // 3. degree and coefficients
-  const int m = p.degree > 0 ? p.degree : auto_degree(am, bm, p.degree_eps, p.max_degree);
+  // 3. degree and coefficients. A window that covers the whole mapped
+  // spectrum makes the filter constant (p = 1), which separates nothing in
+  // the Rayleigh-Ritz step on p(A); it runs unfiltered block Lanczos instead
+  // (the degree-1 operator p(z) = z, whose Ritz values are monotone in lambda).
+  const bool whole = am <= -1.0 && bm >= 1.0;
+  const int m = whole ? 1 : (p.degree > 0 ? p.degree : auto_degree(am, bm, p.degree_eps, p.max_degree));
   if (m < 0) fail(FLZ_ERR_CAPACITY, "no degree <= %d meets the degree rule", p.max_degree);
   stats.degree = m;
   std::vector<double> coeffs(m + 1);
-  chebyshev_coefficients(am, bm, m, coeffs.data());
-  if (p.damping != 0) {
+  if (whole) {
+    coeffs[0] = 0.0;
+    coeffs[1] = 1.0;
+  } else {
+    chebyshev_coefficients(am, bm, m, coeffs.data());
+  }
+  if (p.damping != 0 && !whole) {
     std::vector<double> g(m + 1);
     damping_factors(p.damping, m, g.data());
     for (int k = 0; k <= m; ++k) coeffs[k] *= g[k];
@@ -491,8 +505,12 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
       if (!walk_done && pos + cnt >= K) walk_done = true;
     }
     if (walked > 0) gate_len = std::max(16, walked);
-    const bool complete = all_small && outside >= guard;
-    converged = complete && prev_count >= 0 && inside == prev_count;
+    // A basis spanning the whole space (K = n) whose every Ritz pair passed
+    // holds all eigenpairs: no guard pairs outside the interval need exist
+    // (a window covering the whole spectrum, tiny matrices).
+    const bool full_space = walked == K && (int64_t)K >= n;
+    const bool complete = all_small && (outside >= guard || full_space);
+    converged = complete && (full_space || (prev_count >= 0 && inside == prev_count));
     prev_count = complete ? inside : -1;
     ms_check += ms_since(tc);
     if (converged || last) break;
@@ -581,6 +599,11 @@ flz_status solve_sliced(flz_solver* s, int nslices, cudaStream_t st) {
     fail(FLZ_ERR_EMPTY_INTERVAL, "[%g, %g] misses the Gershgorin interval [%g, %g]", s->alpha, s->beta, A->glo, A->ghi);
   if (s->beta < lmin) lmin = std::max(s->alpha, A->glo);
   if (s->alpha > lmax) lmax = std::min(s->beta, A->ghi);
+  if (!(lmax > lmin)) {
+    const double pad = 1e-3 * std::max(1.0, std::fabs(lmin));
+    lmin -= pad;
+    lmax += pad;
+  }
   const double lo = std::max(s->alpha, lmin), hi = std::min(s->beta, lmax);
   const double anorm = std::max(std::fabs(lmin), std::fabs(lmax));
 

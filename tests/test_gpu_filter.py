@@ -314,3 +314,23 @@ def test_storage_format_choice():
     G = Mat(powerlaw_graph_laplacian(20000, seed=11, i0=1))
     sell, entries, long_rows = flz.flz_matrix_format(G.h)
     assert sell == 0 and entries == 0 and long_rows > 0
+
+
+@pytest.mark.slow
+def test_full_size_power_law_graph_filter_matches_oracle():
+    # The irregular workload at full size (n = 4e6, 64e6 stored entries, 9211
+    # rows above 256 entries), r = 16 as the graph benchmark runs it: staged
+    # CSR rows plus the CTA-per-row tier for the hubs, against the oracle's
+    # Clenshaw evaluation (low degree keeps the CPU side to seconds).
+    csr = powerlaw_graph_laplacian(4_000_000, seed=5)
+    assert np.diff(csr.rowptr).max() > 256
+    c, e = gershgorin_map(csr)
+    M = Mat(csr)
+    sell, _, long_rows = flz.flz_matrix_format(M.h)
+    assert sell == 0 and long_rows > 1000
+    m = 6
+    coeffs = chebyshev.filter_coefficients(0.6, 1.0, m)
+    V = random_normal_block(csr.n, 16, 61)
+    got = run_filter(M, c, e, coeffs, V)
+    ref = chebyshev.clenshaw_apply(csr.to_scipy(), c, e, coeffs, V)
+    assert np.max(np.abs(got - ref)) <= bound(csr, c, e, m, V, U64)

@@ -395,3 +395,41 @@ def test_multiple_eigenvalues_stay_orthonormal_across_walk_chunks():
     assert out["vals"].shape == ref.shape == (87,)
     assert np.max(np.abs(out["vals"] - ref)) < 1e-10
     check_pairs(csr, out, 1e-10)
+
+
+def test_interval_covering_the_whole_spectrum():
+    # Degenerate window: [alpha, beta] contains every eigenvalue, so the filter
+    # is the identity on the spectrum and the Krylov space must exhaust R^n:
+    # all 64 eigenvalues of the 8 x 8 Laplacian, with their multiplicities.
+    csr = laplacian_2d(8, 8)
+    w = lap2d_eigs(8, 8)
+    out = solve(csr, -1.0, 9.0, block_size=4, degree=20, check_every=2)
+    assert out["status"] == flz.FLZ_OK
+    assert out["vals"].shape == (64,)
+    assert np.max(np.abs(out["vals"] - w)) < 1e-10 * 8.0
+    check_pairs(csr, out, 1e-10)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5])
+def test_tiny_matrices(n):
+    # n = 1, 2, 5 with r = 1: the whole-space Krylov basis is reached in n steps.
+    from synth import diagonal_csr
+    d = np.arange(1.0, n + 1.0)
+    csr = diagonal_csr(d)
+    out = solve(csr, 0.5, n + 0.5, block_size=1, degree=10, check_every=1)
+    assert out["status"] == flz.FLZ_OK
+    assert np.max(np.abs(out["vals"] - d)) < 1e-10 * n
+    X = out["vecs"]
+    assert np.max(np.abs(np.abs(X) - np.eye(n))) < 1e-8
+
+
+def test_block_wider_than_the_matrix_is_rejected():
+    from synth import diagonal_csr
+    csr = diagonal_csr(np.arange(1.0, 4.0))
+    h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+    p = flz.flz_params_default()
+    p.block_size = 4
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_solver_create(h, p)  # r > n is refused when the solver is created
+    assert e.value.status == flz.FLZ_ERR_INVALID_ARG
+    flz.flz_matrix_destroy(h)
