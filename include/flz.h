@@ -98,6 +98,9 @@ typedef struct flz_params {
   int32_t damping;      /* 0: plain truncation (Section 2.2, default); 1: Jackson damping g_k b_k;
                            2: Lanczos sigma damping sigma_k b_k (flz_lanczos_sigma_factors) */
   int32_t recurrence;   /* flz_recurrence; default FLZ_REC_FORWARD; batches use FORWARD only */
+  double transition;    /* 0: the indicator of [alpha, beta] (Section 2.2, default); > 0: the least-squares
+                           smoothed step with linear ramps this wide (mapped units), see
+                           flz_smoothed_step_coefficients */
 } flz_params;
 
 /* Per-solve statistics (the columns of Tables 2 and 3, plus bounds). */
@@ -201,6 +204,14 @@ flz_status flz_filter_apply_noalloc(int64_t n, int64_t nnz, const int32_t* rowpt
  * 2 (sin(i acos a) - sin(i acos b))/(i pi). Host only; out has degree+1 slots.
  * Requires -1 <= alpha < beta <= 1. */
 flz_status flz_filter_coefficients(double alpha, double beta, int32_t degree, double* out);
+/* Least-squares filter with a transition band (not in the paper; a filter in
+ * the spirit of FILTLAN's, the paper's CPU comparison): the truncated
+ * Chebyshev series -- the best degree-`degree` approximation in the weighted
+ * Chebyshev 2-norm of eq. (optimaldegree) -- of the smoothed step that is 1 on
+ * [alpha, beta], falls linearly to 0 over a width delta on each side and is 0
+ * elsewhere on [-1, 1]. delta = 0 gives flz_filter_coefficients. Host only;
+ * requires -1 <= alpha < beta <= 1, delta >= 0. */
+flz_status flz_smoothed_step_coefficients(double alpha, double beta, double delta, int32_t degree, double* out);
 /* Jackson damping factors g_0..g_degree (host; out has degree+1 slots):
  * g_k = ((m-k+1) cos(k pi/(m+1)) + sin(k pi/(m+1)) cot(pi/(m+1))) / (m+1).
  * The paper truncates without damping; damping (params.damping = 1) removes

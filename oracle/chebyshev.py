@@ -139,3 +139,54 @@ def lanczos_sigma_factors(m: int) -> np.ndarray:
 def sigma_damped_filter_coefficients(alpha: float, beta: float, m: int) -> np.ndarray:
     """Lanczos-sigma-damped coefficients sigma_k b_k of the ideal filter on [alpha, beta]."""
     return filter_coefficients(alpha, beta, m) * lanczos_sigma_factors(m)
+
+
+def _cos_integral(k: int, t: float) -> float:
+    """Antiderivative of cos(k t) at t."""
+    return t if k == 0 else np.sin(k * t) / k
+
+
+def _zcos_integral(k: int, t: float) -> float:
+    """Antiderivative of cos(t) cos(k t) at t (the weighted integral of z T_k)."""
+    if k == 1:
+        return 0.5 * (t + 0.5 * np.sin(2.0 * t))
+    return 0.5 * (np.sin((k - 1) * t) / (k - 1) + np.sin((k + 1) * t) / (k + 1))
+
+
+def smoothed_step_coefficients(alpha: float, beta: float, delta: float, m: int) -> np.ndarray:
+    """Least-squares polynomial filter of degree m for a smoothed step.
+
+    The target is 1 on [alpha, beta], falls linearly to 0 over [alpha - delta,
+    alpha] and [beta, beta + delta], and is 0 elsewhere on [-1, 1]. In the
+    weighted Chebyshev 2-norm of the degree rule the best approximation of
+    degree m is the truncated Chebyshev series, whose coefficients
+    c_k = (2 - [k = 0]) / pi * integral_0^pi f(cos t) cos(k t) dt have closed
+    forms piece by piece (t = arccos z): the flat part gives the indicator's
+    coefficients, a ramp (z - z0) / (z1 - z0) gives integrals of cos t cos kt
+    and cos kt. (A least-squares filter with a transition band, in the spirit of
+    FILTLAN's; the paper itself uses the plain indicator.)
+    """
+    pieces = []  # (z_lo, z_hi, kind): kind 1 = constant 1, ('ramp', z0, z1)
+    lo_flat, hi_flat = max(alpha, -1.0), min(beta, 1.0)
+    if hi_flat > lo_flat:
+        pieces.append((lo_flat, hi_flat, None))
+    if delta > 0:
+        zl0, zl1 = max(alpha - delta, -1.0), min(alpha, 1.0)
+        if zl1 > zl0:
+            pieces.append((zl0, zl1, (alpha - delta, alpha)))   # rises from 0 at alpha - delta to 1 at alpha
+        zr0, zr1 = max(beta, -1.0), min(beta + delta, 1.0)
+        if zr1 > zr0:
+            pieces.append((zr0, zr1, (beta + delta, beta)))    # falls from 1 at beta to 0 at beta + delta
+    c = np.zeros(m + 1)
+    for k in range(m + 1):
+        acc = 0.0
+        for z_lo, z_hi, ramp in pieces:
+            t_lo, t_hi = np.arccos(z_hi), np.arccos(z_lo)  # t increases as z decreases
+            if ramp is None:
+                acc += _cos_integral(k, t_hi) - _cos_integral(k, t_lo)
+            else:
+                z0, z1 = ramp  # f = (z - z0) / (z1 - z0)
+                acc += ((_zcos_integral(k, t_hi) - _zcos_integral(k, t_lo))
+                        - z0 * (_cos_integral(k, t_hi) - _cos_integral(k, t_lo))) / (z1 - z0)
+        c[k] = (2.0 - (k == 0)) / np.pi * acc
+    return c

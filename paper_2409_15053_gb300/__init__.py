@@ -42,7 +42,7 @@ FLZ_REC_FORWARD, FLZ_REC_CLENSHAW = 0, 1
 EXPORTED = (
     "flz_status_string", "flz_last_error", "flz_params_default",
     "flz_matrix_create_csr", "flz_matrix_destroy", "flz_matrix_info", "flz_matrix_format",
-    "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_jackson_factors", "flz_lanczos_sigma_factors", "flz_filter_degree", "flz_spectrum_bounds",
+    "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_smoothed_step_coefficients", "flz_jackson_factors", "flz_lanczos_sigma_factors", "flz_filter_degree", "flz_spectrum_bounds",
     "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_sym_eig", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve", "flz_solve_sliced",
     "flz_get_count", "flz_get_eigenvalues", "flz_get_eigenvectors", "flz_get_residuals", "flz_get_stats",
     "flz_batch_create", "flz_batch_destroy", "flz_batch_solve", "flz_batch_get_count", "flz_batch_get_eigenvalues",
@@ -57,7 +57,7 @@ class flz_params(ctypes.Structure):
         ("max_basis", ctypes.c_int32), ("guard", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("bounds_steps", ctypes.c_int32), ("seed", ctypes.c_uint64), ("lmin", ctypes.c_double),
         ("lmax", ctypes.c_double), ("damping", ctypes.c_int32),
-        ("recurrence", ctypes.c_int32),
+        ("recurrence", ctypes.c_int32), ("transition", ctypes.c_double),
     ]
 
 
@@ -111,6 +111,7 @@ def lib() -> ctypes.CDLL:
                                                     _vp, _vp]),
         "flz_filter_coefficients": (ctypes.c_int, [_dbl, _dbl, _i32, _vp]),
         "flz_jackson_factors": (ctypes.c_int, [_i32, _vp]),
+        "flz_smoothed_step_coefficients": (ctypes.c_int, [_dbl, _dbl, _dbl, _i32, _vp]),
         "flz_lanczos_sigma_factors": (ctypes.c_int, [_i32, _vp]),
         "flz_filter_degree": (ctypes.c_int, [_dbl, _dbl, _dbl, _i32, ctypes.POINTER(_i32)]),
         "flz_spectrum_bounds": (ctypes.c_int, [_vp, _i32, _i32, _u64, _pdbl, _pdbl, _vp]),
@@ -230,6 +231,12 @@ def flz_filter_apply_noalloc(n, nnz, rowptr, col, val, c, e, coeffs, degree, r, 
 def flz_filter_coefficients(alpha, beta, degree) -> np.ndarray:
     out = np.empty(int(degree) + 1)
     _check(lib().flz_filter_coefficients(float(alpha), float(beta), int(degree), _ptr(out)))
+    return out
+
+
+def flz_smoothed_step_coefficients(alpha, beta, delta, degree) -> np.ndarray:
+    out = np.empty(int(degree) + 1)
+    _check(lib().flz_smoothed_step_coefficients(float(alpha), float(beta), float(delta), int(degree), _ptr(out)))
     return out
 
 

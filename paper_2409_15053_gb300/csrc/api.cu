@@ -33,9 +33,47 @@ void chebyshev_coefficients(double a, double b, int m, double* out) {
   for (int i = 1; i <= m; ++i) out[i] = 2.0 * (std::sin(i * ta) - std::sin(i * tb)) / (i * M_PI);
 }
 
-// Eq. (optimaldegree): least m with ||p_m - phi||^2 < eps^2 ||phi||^2 in the
-// weighted Chebyshev norm, the error by Parseval: ||phi||^2 = acos a - acos b,
-// ||p_m||^2 = pi b_0^2 + (pi/2) sum_{i=1..m} b_i^2. Returns -1 if none <= max_degree.
+namespace {
+// integral of cos(k t) dt and of cos(t) cos(k t) dt (antiderivatives at t)
+double int_cos(int k, double t) { return k == 0 ? t : std::sin(k * t) / k; }
+double int_zcos(int k, double t) {
+  if (k == 1) return 0.5 * (t + 0.5 * std::sin(2.0 * t));
+  return 0.5 * (std::sin((k - 1) * t) / (k - 1) + std::sin((k + 1) * t) / (k + 1));
+}
+}  // namespace
+
+// Weighted least-squares (truncated Chebyshev series) coefficients of the
+// smoothed step: 1 on [a, b], linear ramps of width d down to 0 outside,
+// clipped to [-1, 1]; piecewise closed forms in t = arccos z.
+void smoothed_step_coefficients(double a, double b, double d, int m, double* out) {
+  struct Piece {
+    double z_lo, z_hi;
+    bool ramp;
+    double z0, z1;  // ramp value (z - z0) / (z1 - z0)
+  };
+  std::vector<Piece> pieces;
+  const double flo = std::max(a, -1.0), fhi = std::min(b, 1.0);
+  if (fhi > flo) pieces.push_back({flo, fhi, false, 0.0, 0.0});
+  if (d > 0.0) {
+    const double l0 = std::max(a - d, -1.0), l1 = std::min(a, 1.0);
+    if (l1 > l0) pieces.push_back({l0, l1, true, a - d, a});
+    const double r0 = std::max(b, -1.0), r1 = std::min(b + d, 1.0);
+    if (r1 > r0) pieces.push_back({r0, r1, true, b + d, b});
+  }
+  for (int k = 0; k <= m; ++k) {
+    double acc = 0.0;
+    for (const Piece& pc : pieces) {
+      const double t_lo = std::acos(pc.z_hi), t_hi = std::acos(pc.z_lo);
+      const double ic = int_cos(k, t_hi) - int_cos(k, t_lo);
+      if (!pc.ramp)
+        acc += ic;
+      else
+        acc += ((int_zcos(k, t_hi) - int_zcos(k, t_lo)) - pc.z0 * ic) / (pc.z1 - pc.z0);
+    }
+    out[k] = (k == 0 ? 1.0 : 2.0) / M_PI * acc;
+  }
+}
+
 void jackson_factors(int m, double* g) {
   const double a = M_PI / (m + 1);
   for (int k = 0; k <= m; ++k) g[k] = ((m - k + 1) * std::cos(k * a) + std::sin(k * a) / std::tan(a)) / (m + 1);
@@ -49,6 +87,18 @@ void lanczos_sigma_factors(int m, double* g) {
   }
 }
 
+void filter_coeffs_for(const flz_params& p, double a, double b, int m, double* out) {
+  if (p.transition > 0.0)
+    smoothed_step_coefficients(a, b, p.transition, m, out);
+  else
+    chebyshev_coefficients(a, b, m, out);
+  if (p.damping != 0) {
+    std::vector<double> g(m + 1);
+    damping_factors(p.damping, m, g.data());
+    for (int k = 0; k <= m; ++k) out[k] *= g[k];
+  }
+}
+
 void damping_factors(int damping, int m, double* g) {
   if (damping == 1)
     jackson_factors(m, g);
@@ -58,6 +108,9 @@ void damping_factors(int damping, int m, double* g) {
     for (int k = 0; k <= m; ++k) g[k] = 1.0;
 }
 
+// Eq. (optimaldegree): least m with ||p_m - phi||^2 < eps^2 ||phi||^2 in the
+// weighted Chebyshev norm, the error by Parseval: ||phi||^2 = acos a - acos b,
+// ||p_m||^2 = pi b_0^2 + (pi/2) sum_{i=1..m} b_i^2. Returns -1 if none <= max_degree.
 int auto_degree(double a, double b, double eps, int max_degree) {
   const double ta = std::acos(a), tb = std::acos(b);
   const double phi2 = ta - tb;
@@ -167,6 +220,7 @@ flz_status flz_params_default(flz_params* p) {
   p->lmax = 0.0;
   p->damping = 0;
   p->recurrence = FLZ_REC_FORWARD;
+  p->transition = 0.0;
   return FLZ_OK;
 }
 
@@ -175,6 +229,15 @@ flz_status flz_filter_coefficients(double alpha, double beta, int32_t degree, do
   if (!out || degree < 0) fail(FLZ_ERR_INVALID_ARG, "out is NULL or degree < 0");
   if (!(alpha >= -1.0 && beta <= 1.0 && alpha < beta)) fail(FLZ_ERR_INVALID_ARG, "need -1 <= alpha < beta <= 1");
   flz::chebyshev_coefficients(alpha, beta, degree, out);
+  FLZ_API_END
+}
+
+flz_status flz_smoothed_step_coefficients(double alpha, double beta, double delta, int32_t degree, double* out) {
+  FLZ_API_BEGIN
+  if (!out || degree < 0) fail(FLZ_ERR_INVALID_ARG, "out is NULL or degree < 0");
+  if (!(alpha >= -1.0 && beta <= 1.0 && alpha < beta && delta >= 0.0))
+    fail(FLZ_ERR_INVALID_ARG, "need -1 <= alpha < beta <= 1 and delta >= 0");
+  flz::smoothed_step_coefficients(alpha, beta, delta, degree, out);
   FLZ_API_END
 }
 
@@ -353,7 +416,7 @@ flz_status flz_solver_create(flz_matrix* A, const flz_params* params, flz_solver
   else flz_params_default(&p);
   if (p.block_size < 1 || p.block_size > 16 || p.block_size > A->n) fail(FLZ_ERR_INVALID_ARG, "block_size must be in [1, min(16, n)]");
   if (p.degree < 0 || p.max_degree < 1 || p.check_every < 1 || !(p.tol > 0.0) || !(p.degree_eps > 0.0) ||
-      p.bounds_steps < 1 || p.max_basis < 0 || p.guard < 0 || p.damping < 0 || p.damping > 2 ||
+      p.bounds_steps < 1 || p.max_basis < 0 || p.guard < 0 || p.damping < 0 || p.damping > 2 || !(p.transition >= 0.0) ||
       (p.recurrence != FLZ_REC_FORWARD && p.recurrence != FLZ_REC_CLENSHAW))
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_DF64) fail(FLZ_ERR_INVALID_ARG, "bad precision");

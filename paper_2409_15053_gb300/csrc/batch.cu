@@ -913,12 +913,7 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
     const int m = p.degree > 0 ? p.degree : auto_degree(am, bm, p.degree_eps, p.max_degree);
     if (m < 1) fail(FLZ_ERR_CAPACITY, "problem %d: no degree <= %d meets the degree rule", i, p.max_degree);
     coeffs[i].resize(m + 1);
-    chebyshev_coefficients(am, bm, m, coeffs[i].data());
-    if (p.damping != 0) {
-      std::vector<double> g(m + 1);
-      damping_factors(p.damping, m, g.data());
-      for (int q = 0; q <= m; ++q) coeffs[i][q] *= g[q];
-    }
+    filter_coeffs_for(p, am, bm, m, coeffs[i].data());
     s.c = c;
     s.e = e;
     s.alpha_mapped = am;
@@ -1292,7 +1287,7 @@ flz_status flz_batch_create(int32_t count, flz_matrix* const* mats, const double
         p.block_size == 16))
     fail(FLZ_ERR_INVALID_ARG, "batch block_size must be 0 (autotune) or one of 1, 2, 4, 8, 16");
   if (p.degree < 0 || p.max_degree < 1 || p.check_every < 1 || !(p.tol > 0.0) || p.bounds_steps < 1 ||
-      p.damping < 0 || p.damping > 2)
+      p.damping < 0 || p.damping > 2 || !(p.transition >= 0.0))
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.recurrence != FLZ_REC_FORWARD) fail(FLZ_ERR_INVALID_ARG, "batches use the forward recurrence only");
   if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_BF16)

@@ -267,6 +267,10 @@ void upper_inverse(const double* R, int s, double* Rinv);
 
 // ---- coefficients (api.cu) --------------------------------------------------------------
 void chebyshev_coefficients(double a, double b, int m, double* out);
+void smoothed_step_coefficients(double a, double b, double d, int m, double* out);
+// The filter's coefficients for mapped [a, b]: the indicator's (Section 2.2)
+// or, if transition > 0, the least-squares smoothed step's; then damping.
+void filter_coeffs_for(const flz_params& p, double a, double b, int m, double* out);
 void jackson_factors(int m, double* g);
 void lanczos_sigma_factors(int m, double* g);
 // Damping factors of params.damping (0: all ones, 1: Jackson, 2: Lanczos sigma).

@@ -336,12 +336,7 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
     coeffs[0] = 0.0;
     coeffs[1] = 1.0;
   } else {
-    chebyshev_coefficients(am, bm, m, coeffs.data());
-  }
-  if (p.damping != 0 && !whole) {
-    std::vector<double> g(m + 1);
-    damping_factors(p.damping, m, g.data());
-    for (int k = 0; k <= m; ++k) coeffs[k] *= g[k];
+    filter_coeffs_for(p, am, bm, m, coeffs.data());
   }
   const double anorm = std::max(std::fabs(lmin), std::fabs(lmax));
 

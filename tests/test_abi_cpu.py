@@ -61,6 +61,12 @@ def test_lanczos_sigma_factors_match_oracle(m):
     assert np.max(np.abs(flz.flz_lanczos_sigma_factors(m) - chebyshev.lanczos_sigma_factors(m))) < 1e-15
 
 
+@pytest.mark.parametrize("a,b,d", [(0.1, 0.3, 0.05), (-1.0, -0.6, 0.1), (-0.2, 0.9, 0.2), (0.2, 0.4, 0.0)])
+def test_smoothed_step_coefficients_match_oracle(a, b, d):
+    got = flz.flz_smoothed_step_coefficients(a, b, d, 60)
+    assert np.max(np.abs(got - chebyshev.smoothed_step_coefficients(a, b, d, 60))) < 1e-14
+
+
 def test_degree_rule_reproduces_table2():
     import json
     rows = json.load(open(os.path.join(ROOT, "tests", "golden", "table2_auto_degree.json")))["rows"]

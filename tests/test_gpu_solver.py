@@ -131,13 +131,15 @@ def test_interior_window_block3_vs_dense(rec):
     _dense_case(laplacian_3d_7pt(10, 11, 12, rng.random(1320)), 500, 30, block_size=3, degree=80, recurrence=rec)
 
 
-@pytest.mark.parametrize("damping", [1, 2], ids=["jackson", "sigma"])
-def test_damped_filter_vs_dense(damping):
-    # Damping widens the filter's transition band and tames the Gibbs
-    # oscillations; the solver must still return every eigenvalue of the window.
+@pytest.mark.parametrize("damping,transition", [(1, 0.0), (2, 0.0), (0, 0.02)],
+                         ids=["jackson", "sigma", "smoothed-step"])
+def test_damped_filter_vs_dense(damping, transition):
+    # Damping and the least-squares smoothed step widen the filter's
+    # transition band and tame the Gibbs oscillations; the solver must still
+    # return every eigenvalue of the window.
     rng = np.random.Generator(np.random.PCG64(8))
     out = _dense_case(laplacian_3d_7pt(10, 11, 12, rng.random(1320)), 500, 30, block_size=3, degree=120,
-                      damping=damping)
+                      damping=damping, transition=transition)
     assert out["stats"]["degree"] == 120
 
 

@@ -226,3 +226,34 @@ def test_sigma_damping_shrinks_the_gibbs_overshoot(a, b):
     over_sig = max(sig.max() - 1.0, -sig.min())
     assert over_plain > 0.07
     assert 0.002 < over_sig < 0.03
+
+
+def _quadrature_of(f, m, nodes=400000):
+    t = (2 * np.arange(1, nodes + 1) - 1) * np.pi / (2 * nodes)
+    fz = f(np.cos(t))
+    return np.array([(2.0 - (i == 0)) / np.pi * (np.pi / nodes) * np.sum(fz * np.cos(i * t)) for i in range(m + 1)])
+
+
+@pytest.mark.parametrize("a,b,d", [(0.1, 0.3, 0.05), (-1.0, -0.6, 0.1), (-0.2, 0.9, 0.2), (0.5, 0.95, 0.1)])
+def test_smoothed_step_coefficients_match_quadrature(a, b, d):
+    def target(z):
+        return np.clip(np.minimum((z - (a - d)) / d, ((b + d) - z) / d), 0.0, 1.0)
+    got = ch.smoothed_step_coefficients(a, b, d, 40)
+    ref = _quadrature_of(target, 40)
+    assert np.max(np.abs(got - ref)) < 2e-6
+
+
+def test_smoothed_step_without_transition_is_the_indicator():
+    assert np.max(np.abs(ch.smoothed_step_coefficients(0.1, 0.3, 0.0, 30) - ch.filter_coefficients(0.1, 0.3, 30))) < 1e-15
+
+
+def test_smoothed_step_series_is_closer_to_its_target_than_the_indicator_series():
+    # the ramp removes the jump: the degree-60 series of the smoothed step has
+    # a far smaller maximum error against its own target than the indicator's
+    a, b, d = 0.1, 0.3, 0.1
+    z = np.cos(np.linspace(0.0, np.pi, 20001))
+    target = np.clip(np.minimum((z - (a - d)) / d, ((b + d) - z) / d), 0.0, 1.0)
+    err_s = np.max(np.abs(ch.clenshaw_scalar(ch.smoothed_step_coefficients(a, b, d, 60), z) - target))
+    ind = ((z >= a) & (z <= b)).astype(float)
+    err_i = np.max(np.abs(ch.clenshaw_scalar(ch.filter_coefficients(a, b, 60), z) - ind))
+    assert err_s < 0.05 and err_i > 0.4
