@@ -120,7 +120,6 @@ typedef struct flz_stats {
   double ms_filter;     /* p(A) applications ("MV" of Table 3) */
   double ms_orth;       /* full reorthogonalization and block QR ("ORTH" of Table 3) */
   double ms_check;      /* Rayleigh-Ritz, Ritz vectors, residuals */
-  double ms_refine;     /* FP64 refinement (FLZ_PREC_FP32 / FLZ_PREC_BF16) */
   double ms_total;      /* wall time of flz_solve */
   int64_t basis_vectors;/* final Krylov basis size */
   int64_t kernel_launches; /* CUDA kernels this solve launched */

@@ -69,7 +69,7 @@ class flz_stats(ctypes.Structure):
         ("c", ctypes.c_double), ("e", ctypes.c_double), ("alpha_mapped", ctypes.c_double),
         ("beta_mapped", ctypes.c_double), ("max_residual", ctypes.c_double), ("ms_bounds", ctypes.c_double),
         ("ms_filter", ctypes.c_double), ("ms_orth", ctypes.c_double), ("ms_check", ctypes.c_double),
-        ("ms_refine", ctypes.c_double), ("ms_total", ctypes.c_double), ("basis_vectors", ctypes.c_int64),
+        ("ms_total", ctypes.c_double), ("basis_vectors", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),
     ]
 

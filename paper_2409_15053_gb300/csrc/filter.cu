@@ -481,15 +481,6 @@ __global__ void __launch_bounds__(kThreads) spmm_kernel(int n, int s, int ld, in
   Y[(size_t)row * ld + c] = acc;
 }
 
-}  // namespace
-
-int filter_launch_count(int m, int precision) {  // degree steps + the conversion of V
-  if (m <= 0) return 1;
-  return m + (precision == FLZ_PREC_FP64 ? 0 : 1);
-}
-
-namespace {
-
 // 2 Ahat in storage precision `prec`, rebuilt only when (c, e) change.
 template <class S>
 const S* scaled(flz_matrix* A, DevBuf<S>& buf, int prec, double c, double e, cudaStream_t st) {

@@ -186,8 +186,6 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
 // conversion of V, W written as pairs).
 void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m, int r,
                   const dev::dfloat* V, dev::dfloat* W, int recurrence, cudaStream_t st);
-// Number of kernel launches filter_apply issues for degree m at `precision`.
-int filter_launch_count(int m, int precision);
 // ---- clenshaw.cu ----------------------------------------------------------------
 // W = p_m(Ahat) V by the Clenshaw recurrence with 2 Ahat stored in `val`
 // (MS; `vsell` in the SELL-32 layout or null, `val` in CSR order) and the
