@@ -351,7 +351,7 @@ def main():
     fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
     # DRAM bytes per launch of the FP64 forward SELL-32 step on this workload, from
     # one ncu capture (profiles/cheb_sell_kernel_fp64_laplacian3d_100cubed_r4.md)
-    traffic = 179.70e6 + 36.53e6 if (args.precision == "fp64" and args.recurrence == "forward") else None
+    traffic = 179.70e6 + 34.64e6 if (args.precision == "fp64" and args.recurrence == "forward") else None
     roofline = {
         "kernel": ("clen_sell_kernel (Clenshaw degree step, SELL-32)" if args.recurrence == "clenshaw"
                    else "cheb_sell_kernel (fused Chebyshev degree step, SELL-32)"),
