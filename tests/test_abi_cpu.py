@@ -80,6 +80,9 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     with pytest.raises(flz.FlzError) as e:
         flz.flz_filter_coefficients(0.5, 0.1, 10)
     assert e.value.status == flz.FLZ_ERR_INVALID_ARG
+    assert "alpha < beta" in flz.flz_last_error()  # the thread's last failure message
+    flz.flz_filter_coefficients(0.1, 0.5, 10)
+    assert flz.flz_last_error() == ""  # cleared by the next successful call
     with pytest.raises(flz.FlzError) as e:
         flz.flz_filter_degree(-1.0, -0.99999999, 0.3123, 5)
     assert e.value.status == flz.FLZ_ERR_CAPACITY

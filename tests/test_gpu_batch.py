@@ -35,6 +35,7 @@ def run_batch(csrs, intervals, **kw):
     st = flz.flz_batch_solve(b)
     out = []
     for i, c in enumerate(csrs):
+        assert flz.flz_batch_get_count(b, i) == flz.flz_batch_get_eigenvalues(b, i).shape[0]
         out.append({"vals": flz.flz_batch_get_eigenvalues(b, i), "res": flz.flz_batch_get_residuals(b, i),
                     "vecs": flz.batch_eigenvectors_host(b, i, c.n), "stats": flz.flz_batch_get_stats(b, i)})
     flz.flz_batch_destroy(b)
