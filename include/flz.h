@@ -59,12 +59,15 @@ typedef enum flz_memspace { FLZ_HOST = 0, FLZ_DEVICE = 1 } flz_memspace;
  *       the attainable residual (about 1e-7 relative); eigenvalues come from
  *       FP64 Rayleigh quotients and are far more accurate than that.
  * BF16: as FP32 with values and vectors stored in bfloat16, FP32 sums
- *       (attainable residual about 1e-4).
+ *       (attainable residual 1e-4 to 1e-2: the rounded matrix values alone
+ *       perturb A by up to 2^-9 of its row sums).
  * DF64: double-FP32: every value is a pair of FP32 words (hi + lo, about 48
  *       significant bits, the same 8 bytes as FP64) combined on the FP32 pipes
  *       with error-free transformations; residuals reach the FP64 range on
- *       GPUs whose FP64 rate is a small fraction of their FP32 rate. Not
- *       available for batches. */
+ *       GPUs whose FP64 rate is a small fraction of their FP32 rate. The single
+ *       solver also keeps its Krylov basis in double-FP32 (reorthogonalization
+ *       on the FP32 pipes); a batch uses the double-FP32 filter with an FP64
+ *       basis. */
 typedef enum flz_precision { FLZ_PREC_FP64 = 0, FLZ_PREC_FP32 = 1, FLZ_PREC_BF16 = 2, FLZ_PREC_DF64 = 3 } flz_precision;
 
 /* How p_m(Ahat) V is evaluated; both give the same polynomial and differ

@@ -171,6 +171,11 @@ __global__ void load_block_kernel(const double* __restrict__ Q, const int* __res
     vbuf[i] = from_arith<VS>((typename Arith<VS>::type)src[i]);
 }
 
+__global__ void narrow_df_kernel(const dev::dfloat* __restrict__ in, double* __restrict__ out, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    out[i] = dev::to_double(in[i]);
+}
+
 __global__ void widen_kernel(const float* __restrict__ in, double* __restrict__ out, long long count) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
     out[i] = (double)in[i];
@@ -408,6 +413,7 @@ __global__ void seg_scale_kernel(long long N, const int* __restrict__ rowptr, co
       const double v = s * (val[j] - (j == d ? c : 0.0));
       if constexpr (std::is_same<S, double>::value) out[j] = v;
       else if constexpr (std::is_same<S, float>::value) out[j] = (float)v;
+      else if constexpr (std::is_same<S, dev::dfloat>::value) out[j] = dev::dfloat(v);
       else out[j] = __double2bfloat16(v);
     }
   }
@@ -511,6 +517,7 @@ struct BatchEngine {
   DevBuf<double> ya64, yb64, sval64;
   DevBuf<float> sval32;
   DevBuf<__nv_bfloat16> sval16;
+  DevBuf<dev::dfloat> svaldf, vdf, yadf, ybdf, accdf;  // double-FP32 filter
   DevBuf<int> jdev, active, mdeg, fail;
   int mmax = 0;
   bool pdl = true;  // degree steps as programmatic dependent launches
@@ -554,6 +561,12 @@ struct BatchEngine {
       ya32.reserve(nr);
       yb32.reserve(nr);
       sval32.reserve((size_t)b->nnz);
+    } else if (prec == FLZ_PREC_DF64) {
+      accdf.reserve(nr);
+      vdf.reserve(nr);
+      yadf.reserve(nr);
+      ybdf.reserve(nr);
+      svaldf.reserve((size_t)b->nnz);
     } else {
       acc32.reserve(nr);
       v16.reserve(nr);
@@ -582,6 +595,8 @@ struct BatchEngine {
       seg_scale_kernel<double><<<gsb(N), 256, sm, st>>>(N, B->rowptr.p, B->diag_pos.p, B->val.p, B->d_off.p, count, cc.p, ee.p, sval64.p);
     else if (precision == FLZ_PREC_FP32)
       seg_scale_kernel<float><<<gsb(N), 256, sm, st>>>(N, B->rowptr.p, B->diag_pos.p, B->val.p, B->d_off.p, count, cc.p, ee.p, sval32.p);
+    else if (precision == FLZ_PREC_DF64)
+      seg_scale_kernel<dev::dfloat><<<gsb(N), 256, sm, st>>>(N, B->rowptr.p, B->diag_pos.p, B->val.p, B->d_off.p, count, cc.p, ee.p, svaldf.p);
     else
       seg_scale_kernel<__nv_bfloat16><<<gsb(N), 256, sm, st>>>(N, B->rowptr.p, B->diag_pos.p, B->val.p, B->d_off.p, count, cc.p, ee.p, sval16.p);
     FLZ_LAUNCH_CHECK();
@@ -656,6 +671,12 @@ struct BatchEngine {
       FLZ_LAUNCH_CHECK();
       filter_steps<R, float, float, float>(sval32.p, v32.p, ya32.p, yb32.p, acc32.p);
       widen_kernel<<<gsb(nr), 256, 0, st>>>(acc32.p, W.p, nr);
+      FLZ_LAUNCH_CHECK();
+    } else if (precision == FLZ_PREC_DF64) {
+      load_block_kernel<dev::dfloat><<<gsb(nr), 256, 0, st>>>(Q.p, jdev.p, nr, vdf.p);
+      FLZ_LAUNCH_CHECK();
+      filter_steps<R, dev::dfloat, dev::dfloat, dev::dfloat>(svaldf.p, vdf.p, yadf.p, ybdf.p, accdf.p);
+      narrow_df_kernel<<<gsb(nr), 256, 0, st>>>(accdf.p, W.p, nr);
       FLZ_LAUNCH_CHECK();
     } else {
       load_block_kernel<__nv_bfloat16><<<gsb(nr), 256, 0, st>>>(Q.p, jdev.p, nr, v16.p);
@@ -1290,7 +1311,7 @@ flz_status flz_batch_create(int32_t count, flz_matrix* const* mats, const double
       p.damping < 0 || p.damping > 2 || !(p.transition >= 0.0))
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.recurrence != FLZ_REC_FORWARD) fail(FLZ_ERR_INVALID_ARG, "batches use the forward recurrence only");
-  if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_BF16)
+  if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_DF64)
     fail(FLZ_ERR_INVALID_ARG, "batches support the FP64, FP32 and BF16 filters");
   std::unique_ptr<flz_batch> B(new flz_batch());
   B->count = count;

@@ -83,6 +83,14 @@ def test_batch_fp64_matches_dense(r):
     check(csrs, intervals, out, 1e-10)
 
 
+def test_batch_double_fp32_filter_matches_dense():
+    # the double-FP32 filter (FP32 pipes, FP64-class accuracy) with the batch's FP64 basis
+    csrs, intervals = small_batch(11, 5)
+    st, out = run_batch(csrs, intervals, block_size=4, degree=50, check_every=5, precision=flz.FLZ_PREC_DF64)
+    assert st == flz.FLZ_OK
+    check(csrs, intervals, out, 1e-10)
+
+
 def test_batch_autotuned_block_width_and_auto_degree():
     csrs, intervals = small_batch(5, 4)
     st, out = run_batch(csrs, intervals, block_size=0, degree=0, check_every=5)
