@@ -463,8 +463,9 @@ def batch_leg(flz, torch, stream):
     log-uniform in [1e4, 2e5], each with the interval [0, beta_i] and the
     eigenvalue counts the CPU oracle computed (tests/golden/batch64_reference.json).
     Times (CUDA events, after one warm-up solve each): the batch with the FP32
-    filter (tol 1e-6, its attainable residual), the batch with the FP64 filter
-    (tol 1e-10), and the 64 problems solved one after another with the FP64
+    filter (tol 1e-6, its attainable residual), the batch with the FP64 and
+    with the double-FP32 filter (tol 1e-10), and the 64 problems solved one
+    after another with the FP64
     filter (r = 4); filter degree 60 throughout (the eps-rule's degrees of
     17-23 would need up to 480 block steps). Each result is checked against
     the oracle's counts and eigenvalues."""
@@ -494,7 +495,8 @@ def batch_leg(flz, torch, stream):
         return counts_ok, err, good
 
     out = {"problems": len(items), "sum_n": int(sum(c.n for c, _, _ in items)), "eigenpairs": total}
-    for name, prec, tol in (("batch_fp32", flz.FLZ_PREC_FP32, 1e-6), ("batch_fp64", flz.FLZ_PREC_FP64, 1e-10)):
+    for name, prec, tol in (("batch_fp32", flz.FLZ_PREC_FP32, 1e-6), ("batch_fp64", flz.FLZ_PREC_FP64, 1e-10),
+                            ("batch_df64", flz.FLZ_PREC_DF64, 1e-10)):
         p = flz.flz_params_default()
         p.block_size = 0
         p.degree = BATCH_DEGREE
