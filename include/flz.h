@@ -80,6 +80,26 @@ typedef enum flz_precision { FLZ_PREC_FP64 = 0, FLZ_PREC_FP32 = 1, FLZ_PREC_BF16
  *           B_{k+1}, B_{k+2}, B_k) and no running sum. */
 typedef enum flz_recurrence { FLZ_REC_FORWARD = 0, FLZ_REC_CLENSHAW = 1 } flz_recurrence;
 
+/* Where the full reorthogonalization of an FP64 basis runs (classical
+ * Gram-Schmidt twice against the whole basis, Section 3.2.2).
+ * CUDA_CORES: FP64 inner products and updates on the FP64 pipes.
+ * TENSOR:     the basis is also held as eight base-256 digits per value
+ *             (64-bit fixed point in 2^-62 units; the FP64 basis is rounded
+ *             to the same grid, so both copies hold the same numbers), each
+ *             digit an integer that BF16 represents exactly. The projections
+ *             Q^T W and the updates W - Q H run as BF16 tcgen05 MMAs whose
+ *             FP32 accumulations stay exact integers (at most 256 products of
+ *             at most 2^14 between drains of tensor memory) and are
+ *             recombined exactly. The inner products are exact up to the
+ *             rounding of W (or H) to 62 fractional bits of its column scale
+ *             and a final FP64 rounding, i.e. more accurate than FP64
+ *             arithmetic. Block widths 1..4; 16 bytes per basis value of
+ *             device memory besides the FP64 basis.
+ * AUTO:       TENSOR where it applies (FP64 basis, r <= 4, enough device
+ *             memory), else CUDA_CORES. The double-FP32 precision keeps its
+ *             own basis and always uses the FP32 pipes. */
+typedef enum flz_ortho { FLZ_ORTHO_AUTO = 0, FLZ_ORTHO_CUDA_CORES = 1, FLZ_ORTHO_TENSOR = 2 } flz_ortho;
+
 typedef struct flz_matrix flz_matrix;
 typedef struct flz_solver flz_solver;
 typedef struct flz_batch flz_batch;
@@ -104,6 +124,7 @@ typedef struct flz_params {
   double transition;    /* 0: the indicator of [alpha, beta] (Section 2.2, default); > 0: the least-squares
                            smoothed step with linear ramps this wide (mapped units), see
                            flz_smoothed_step_coefficients */
+  int32_t ortho;        /* flz_ortho; default FLZ_ORTHO_AUTO */
 } flz_params;
 
 /* Per-solve statistics (the columns of Tables 2 and 3, plus bounds). */
@@ -126,6 +147,7 @@ typedef struct flz_stats {
   double ms_total;      /* wall time of flz_solve */
   int64_t basis_vectors;/* final Krylov basis size */
   int64_t kernel_launches; /* CUDA kernels this solve launched */
+  int32_t ortho;        /* flz_ortho the reorthogonalization ran on (CUDA_CORES or TENSOR) */
 } flz_stats;
 
 /* ---- status and parameters ------------------------------------------------ */
@@ -251,9 +273,37 @@ flz_status flz_band_eigenvectors(int32_t K, int32_t b, const double* T, const do
 
 /* Dense symmetric eigen-decomposition of the n x n row-major matrix S (host):
  * w[n] ascending eigenvalues, Z[n*n] row-major with column k the unit
- * eigenvector of w[k]. Householder tridiagonalization + implicit QL. Used for
- * the Rayleigh-Ritz refinement on A of the reduced-precision filters. */
+ * eigenvector of w[k]. Householder tridiagonalization + implicit QL. */
 flz_status flz_sym_eig(int32_t n, const double* S, double* w, double* Z);
+
+/* ---- full reorthogonalization (Section 3.2.2) ------------------------------ */
+
+/* Projection C = Q^T W of the n x r block W (device) on a basis Q of nb
+ * blocks (device; block b at Q + b n r, each n x r row-major; K = nb r
+ * columns); C is K x r row-major (device). `method` is FLZ_ORTHO_CUDA_CORES
+ * or FLZ_ORTHO_TENSOR (see flz_ortho; TENSOR needs r <= 4 and |Q| < 1.9, and
+ * uses Q rounded to the 2^-62 grid, the rounding a solver's basis already
+ * has; Q itself is not modified). Synchronous with respect to `stream`;
+ * allocates and frees its own scratch. */
+flz_status flz_basis_project(int64_t n, int32_t nb, int32_t r, const double* Q, const double* W, double* C,
+                             int32_t method, void* stream);
+/* Classical Gram-Schmidt twice of W (device n x r, overwritten) against the
+ * same basis: W <- (I - Q Q^T)(I - Q Q^T) W, and C = C_1 + C_2 (K x r,
+ * device) the total projection coefficients of the two passes. Same methods
+ * and conditions as flz_basis_project. */
+flz_status flz_basis_orthogonalize(int64_t n, int32_t nb, int32_t r, const double* Q, double* W, double* C,
+                                   int32_t method, void* stream);
+/* Layout check of the tensor-core path: one tcgen05.mma (M = 128, N = n in
+ * {16, 32}, K = 16, BF16 operands, FP32 accumulator in tensor memory) of a
+ * 128 x 16 A operand and an n x 16 B operand given as shared-memory images
+ * (host; a_bytes <= 36864, b_bytes <= 20480, multiples of 16; both K-major
+ * unless a_mn_major) and the descriptors' leading and stride byte offsets
+ * (multiples of 16 whose reach, under either reading of the two fields, stays
+ * inside the images' regions). d (host) receives D as 128 x n row-major FP32.
+ * TIMEOUT if the MMA's completion wait expired. Synchronizes the device. */
+flz_status flz_tc_mma_probe(const uint16_t* a_img, int64_t a_bytes, const uint16_t* b_img, int64_t b_bytes,
+                            int32_t n, int32_t a_mn_major, int32_t a_lbo, int32_t a_sbo, int32_t b_lbo,
+                            int32_t b_sbo, float* d);
 
 /* ---- solver (Sections 2.3 and 3.2.2) ---------------------------------------- */
 

@@ -37,13 +37,15 @@ FLZ_F64, FLZ_F32, FLZ_BF16 = 0, 1, 2
 FLZ_HOST, FLZ_DEVICE = 0, 1
 FLZ_PREC_FP64, FLZ_PREC_FP32, FLZ_PREC_BF16, FLZ_PREC_DF64 = 0, 1, 2, 3
 FLZ_REC_FORWARD, FLZ_REC_CLENSHAW = 0, 1
+FLZ_ORTHO_AUTO, FLZ_ORTHO_CUDA_CORES, FLZ_ORTHO_TENSOR = 0, 1, 2
 
 # Every symbol include/flz.h declares.
 EXPORTED = (
     "flz_status_string", "flz_last_error", "flz_params_default",
     "flz_matrix_create_csr", "flz_matrix_destroy", "flz_matrix_info", "flz_matrix_format",
     "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_smoothed_step_coefficients", "flz_jackson_factors", "flz_lanczos_sigma_factors", "flz_filter_degree", "flz_spectrum_bounds",
-    "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_sym_eig", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve", "flz_solve_sliced",
+    "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_sym_eig",
+    "flz_basis_project", "flz_basis_orthogonalize", "flz_tc_mma_probe", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve", "flz_solve_sliced",
     "flz_get_count", "flz_get_eigenvalues", "flz_get_eigenvectors", "flz_get_residuals", "flz_get_stats",
     "flz_batch_create", "flz_batch_destroy", "flz_batch_solve", "flz_batch_get_count", "flz_batch_get_eigenvalues",
     "flz_batch_get_residuals", "flz_batch_get_eigenvectors", "flz_batch_get_stats",
@@ -57,7 +59,7 @@ class flz_params(ctypes.Structure):
         ("max_basis", ctypes.c_int32), ("guard", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("bounds_steps", ctypes.c_int32), ("seed", ctypes.c_uint64), ("lmin", ctypes.c_double),
         ("lmax", ctypes.c_double), ("damping", ctypes.c_int32),
-        ("recurrence", ctypes.c_int32), ("transition", ctypes.c_double),
+        ("recurrence", ctypes.c_int32), ("transition", ctypes.c_double), ("ortho", ctypes.c_int32),
     ]
 
 
@@ -70,7 +72,7 @@ class flz_stats(ctypes.Structure):
         ("beta_mapped", ctypes.c_double), ("max_residual", ctypes.c_double), ("ms_bounds", ctypes.c_double),
         ("ms_filter", ctypes.c_double), ("ms_orth", ctypes.c_double), ("ms_check", ctypes.c_double),
         ("ms_total", ctypes.c_double), ("basis_vectors", ctypes.c_int64),
-        ("kernel_launches", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64), ("ortho", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -118,6 +120,9 @@ def lib() -> ctypes.CDLL:
         "flz_band_eigenvalues": (ctypes.c_int, [_i32, _i32, _vp, _vp]),
         "flz_band_eigenvectors": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp, _vp, _u64]),
         "flz_sym_eig": (ctypes.c_int, [_i32, _vp, _vp, _vp]),
+        "flz_basis_project": (ctypes.c_int, [_i64, _i32, _i32, _vp, _vp, _vp, _i32, _vp]),
+        "flz_basis_orthogonalize": (ctypes.c_int, [_i64, _i32, _i32, _vp, _vp, _vp, _i32, _vp]),
+        "flz_tc_mma_probe": (ctypes.c_int, [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _i32, _i32, _i32, _vp]),
         "flz_solver_create": (ctypes.c_int, [_vp, ctypes.POINTER(flz_params), ctypes.POINTER(_vp)]),
         "flz_solver_destroy": (ctypes.c_int, [_vp]),
         "flz_solver_set_interval": (ctypes.c_int, [_vp, _dbl, _dbl]),
@@ -294,6 +299,28 @@ def flz_sym_eig(S: np.ndarray):
     _check(lib().flz_sym_eig(n, _ptr(S), _ptr(w), _ptr(Z)))
     return w, Z
 
+
+
+def flz_basis_project(n, nb, r, Q, W, C, method=FLZ_ORTHO_TENSOR, stream=None):
+    """C = Q^T W for a basis of nb device blocks (n x r each, contiguous) and device W, C."""
+    _check(lib().flz_basis_project(int(n), int(nb), int(r), _ptr(Q), _ptr(W), _ptr(C), int(method),
+                                   _stream(stream)))
+
+
+def flz_basis_orthogonalize(n, nb, r, Q, W, C, method=FLZ_ORTHO_TENSOR, stream=None):
+    """W <- (I - QQ^T)^2 W in place; C = total projection coefficients (device)."""
+    _check(lib().flz_basis_orthogonalize(int(n), int(nb), int(r), _ptr(Q), _ptr(W), _ptr(C), int(method),
+                                         _stream(stream)))
+
+
+def flz_tc_mma_probe(a_img, b_img, n, a_mn_major, a_lbo, a_sbo, b_lbo, b_sbo):
+    """One tcgen05 MMA of shared-memory images (uint16 arrays); returns D (128 x n, float32)."""
+    a_img = np.ascontiguousarray(a_img, dtype=np.uint16)
+    b_img = np.ascontiguousarray(b_img, dtype=np.uint16)
+    d = np.zeros((128, int(n)), dtype=np.float32)
+    _check(lib().flz_tc_mma_probe(_ptr(a_img), a_img.nbytes, _ptr(b_img), b_img.nbytes, int(n), int(a_mn_major),
+                                  int(a_lbo), int(a_sbo), int(b_lbo), int(b_sbo), _ptr(d)))
+    return d
 
 def flz_solver_create(A, params: flz_params | None = None):
     h = _vp()

@@ -221,6 +221,7 @@ flz_status flz_params_default(flz_params* p) {
   p->damping = 0;
   p->recurrence = FLZ_REC_FORWARD;
   p->transition = 0.0;
+  p->ortho = FLZ_ORTHO_AUTO;
   return FLZ_OK;
 }
 
@@ -408,6 +409,96 @@ flz_status flz_sym_eig(int32_t n, const double* S, double* w, double* Z) {
   FLZ_API_END
 }
 
+namespace {
+
+void check_basis_args(int64_t n, int32_t nb, int32_t r, const double* Q, const double* W, const double* C,
+                      int32_t method) {
+  if (n < 1 || nb < 1 || r < 1 || r > 16 || !Q || !W || !C) fail(FLZ_ERR_INVALID_ARG, "bad arguments");
+  if (method != FLZ_ORTHO_CUDA_CORES && method != FLZ_ORTHO_TENSOR) fail(FLZ_ERR_INVALID_ARG, "bad method");
+  if (method == FLZ_ORTHO_TENSOR && !flz::TcBasis::supported(r))
+    fail(FLZ_ERR_INVALID_ARG, "the tensor-core path takes block widths 1..4");
+}
+
+// Digit copy of a caller's basis (the caller's FP64 values stay untouched).
+void digits_of(flz::TcBasis& B, int64_t n, int32_t nb, int32_t r, const double* Q, cudaStream_t st) {
+  B.reserve(n, (int64_t)nb * r);
+  flz::DevBuf<double> tmp;
+  tmp.reserve((size_t)n * r);
+  for (int b = 0; b < nb; ++b) {
+    FLZ_CUDA(cudaMemcpyAsync(tmp.p, Q + (size_t)b * n * r, sizeof(double) * n * r, cudaMemcpyDeviceToDevice, st));
+    B.append(tmp.p, r, b * r, st);
+  }
+  FLZ_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+
+flz_status flz_basis_project(int64_t n, int32_t nb, int32_t r, const double* Q, const double* W, double* C,
+                             int32_t method, void* stream) {
+  FLZ_API_BEGIN
+  check_basis_args(n, nb, r, Q, W, C, method);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (method == FLZ_ORTHO_CUDA_CORES) {
+    flz::DevBuf<double> part;
+    part.reserve(std::max(flz::basis_dot_scratch(n, nb, r, r), (size_t)1));
+    flz::basis_dot(Q, nb, n, r, W, r, r, C, part.p, st);
+    FLZ_CUDA(cudaStreamSynchronize(st));
+  } else {
+    flz::TcBasis B;
+    digits_of(B, n, nb, r, Q, st);
+    B.column_max(W, r, r, B.wmax.p, st);
+    B.project(nb * r, W, r, r, B.wmax.p, C, r, st);
+    FLZ_CUDA(cudaMemcpyAsync(B.status_host, B.status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FLZ_CUDA(cudaStreamSynchronize(st));
+    B.check_status();
+  }
+  FLZ_API_END
+}
+
+flz_status flz_basis_orthogonalize(int64_t n, int32_t nb, int32_t r, const double* Q, double* W, double* C,
+                                   int32_t method, void* stream) {
+  FLZ_API_BEGIN
+  check_basis_args(n, nb, r, Q, W, C, method);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t kr = (size_t)nb * r * r;
+  flz::DevBuf<double> C2;
+  C2.reserve(kr);
+  if (method == FLZ_ORTHO_CUDA_CORES) {
+    flz::DevBuf<double> part;
+    part.reserve(std::max(flz::basis_dot_scratch(n, nb, r, r), (size_t)1));
+    flz::basis_dot(Q, nb, n, r, W, r, r, C, part.p, st);
+    flz::basis_update(Q, nb, n, r, C, r, -1.0, 1.0, W, r, st);
+    flz::basis_dot(Q, nb, n, r, W, r, r, C2.p, part.p, st);
+    flz::basis_update(Q, nb, n, r, C2.p, r, -1.0, 1.0, W, r, st);
+    FLZ_CUDA(cudaStreamSynchronize(st));
+  } else {
+    flz::TcBasis B;
+    digits_of(B, n, nb, r, Q, st);
+    B.cgs2(nb * r, W, r, C, C2.p, st);
+    FLZ_CUDA(cudaStreamSynchronize(st));
+    B.check_status();
+  }
+  std::vector<double> c1(kr), c2(kr);
+  FLZ_CUDA(cudaMemcpy(c1.data(), C, sizeof(double) * kr, cudaMemcpyDeviceToHost));
+  FLZ_CUDA(cudaMemcpy(c2.data(), C2.p, sizeof(double) * kr, cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < kr; ++i) c1[i] += c2[i];
+  FLZ_CUDA(cudaMemcpy(C, c1.data(), sizeof(double) * kr, cudaMemcpyHostToDevice));
+  FLZ_API_END
+}
+
+flz_status flz_tc_mma_probe(const uint16_t* a_img, int64_t a_bytes, const uint16_t* b_img, int64_t b_bytes,
+                            int32_t n, int32_t a_mn_major, int32_t a_lbo, int32_t a_sbo, int32_t b_lbo,
+                            int32_t b_sbo, float* d) {
+  FLZ_API_BEGIN
+  if (!a_img || !b_img || !d || a_bytes < 16 || b_bytes < 16 || a_lbo < 0 || a_sbo < 0 || b_lbo < 0 || b_sbo < 0 ||
+      (a_mn_major != 0 && a_mn_major != 1))
+    fail(FLZ_ERR_INVALID_ARG, "bad arguments");
+  const int st = flz::tc_probe(a_img, (size_t)a_bytes, b_img, (size_t)b_bytes, n, a_mn_major, (uint32_t)a_lbo,
+                               (uint32_t)a_sbo, (uint32_t)b_lbo, (uint32_t)b_sbo, d);
+  if (st) fail(FLZ_ERR_TIMEOUT, "the MMA's completion wait expired");
+  FLZ_API_END
+}
+
 flz_status flz_solver_create(flz_matrix* A, const flz_params* params, flz_solver** out) {
   FLZ_API_BEGIN
   if (!A || !out) fail(FLZ_ERR_INVALID_ARG, "null argument");
@@ -417,8 +508,11 @@ flz_status flz_solver_create(flz_matrix* A, const flz_params* params, flz_solver
   if (p.block_size < 1 || p.block_size > 16 || p.block_size > A->n) fail(FLZ_ERR_INVALID_ARG, "block_size must be in [1, min(16, n)]");
   if (p.degree < 0 || p.max_degree < 1 || p.check_every < 1 || !(p.tol > 0.0) || !(p.degree_eps > 0.0) ||
       p.bounds_steps < 1 || p.max_basis < 0 || p.guard < 0 || p.damping < 0 || p.damping > 2 || !(p.transition >= 0.0) ||
-      (p.recurrence != FLZ_REC_FORWARD && p.recurrence != FLZ_REC_CLENSHAW))
+      (p.recurrence != FLZ_REC_FORWARD && p.recurrence != FLZ_REC_CLENSHAW) || p.ortho < FLZ_ORTHO_AUTO ||
+      p.ortho > FLZ_ORTHO_TENSOR)
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
+  if (p.ortho == FLZ_ORTHO_TENSOR && (!flz::TcBasis::supported(p.block_size) || p.precision == FLZ_PREC_DF64))
+    fail(FLZ_ERR_INVALID_ARG, "tensor-core reorthogonalization needs an FP64 basis and block_size <= 4");
   if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_DF64) fail(FLZ_ERR_INVALID_ARG, "bad precision");
   flz_solver* s = new flz_solver();
   s->A = A;

@@ -104,6 +104,49 @@ struct DevBuf {
   }
 };
 
+// ---- tc_ortho.cu ----------------------------------------------------------------
+// The Krylov basis as eight BF16-exact base-256 digits per value (64-bit fixed
+// point, 2^-62 units) for full reorthogonalization on the tensor cores, with
+// the scratch of its projection and update kernels. Columns are appended
+// block by block; appending rounds the FP64 block to the same 2^-62 grid so
+// the FP64 and digit copies hold the same numbers.
+struct TcBasis {
+  DevBuf<uint8_t> q;        // digit strips, zero outside the written columns and rows
+  DevBuf<int32_t> part;     // projection partials
+  DevBuf<uint16_t> hs;      // digits of the coefficient matrix of an update
+  DevBuf<int> hexp;         // its column scale exponents
+  DevBuf<uint32_t> wmax;    // column maxima of W (two sets of 16)
+  DevBuf<int> status;       // first failed wait of any launch (0 = none)
+  int* status_host = nullptr;  // pinned copy, refreshed at the end of every cgs2
+  int64_t n = 0, n_pad = 0, n_oct = 0;
+  int groups_cap = 0;
+  TcBasis() = default;
+  TcBasis(const TcBasis&) = delete;
+  TcBasis& operator=(const TcBasis&) = delete;
+  ~TcBasis() { release(); }
+  static bool supported(int r);                       // block widths the kernels take (1..4)
+  static size_t bytes_for(int64_t n, int64_t kcap);   // digit storage for kcap columns
+  void release();
+  void reserve(int64_t n, int64_t kcap);
+  // rounds X (n x r, row-major) to the 2^-62 grid in place; its digits become columns col0..col0+r-1
+  void append(double* X, int r, int col0, cudaStream_t st);
+  // out[j] = largest |W[i, j]| (as the upper word of the FP64 bits), j < r
+  void column_max(const double* W, int r, int ldw, uint32_t* out, cudaStream_t st);
+  // C[kb, j] = sum_i Q[i, kb] W[i, j], kb < K (row stride ldc), from W's digits at the scales in wmax
+  void project(int K, const double* W, int r, int ldw, const uint32_t* wmax, double* C, int ldc, cudaStream_t st);
+  // W -= Q[:, :K] C; records the new column maxima of W in wmax_out if not null
+  void subtract(int K, const double* C, int ldc, double* W, int r, int ldw, uint32_t* wmax_out, cudaStream_t st);
+  // classical Gram-Schmidt twice of W (n x r) against columns 0..K-1; C, C2 the two projections
+  void cgs2(int K, double* W, int r, double* C, double* C2, cudaStream_t st);
+  // raises FLZ_ERR_TIMEOUT if a kernel recorded an expired wait (after a stream sync)
+  void check_status();
+};
+// One tcgen05 MMA (M = 128, N = np, K = 16, BF16 in, FP32 out) of shared-memory
+// images with explicit descriptor strides; out is 128 x np row-major. Returns
+// the kernel's wait status (0 = completed).
+int tc_probe(const uint16_t* a_img, size_t a_bytes, const uint16_t* b_img, size_t b_bytes, int np, int a_mn_major,
+             uint32_t a_lbo, uint32_t a_sbo, uint32_t b_lbo, uint32_t b_sbo, float* out_host);
+
 }  // namespace flz
 
 // Matrix handle: a device copy of a symmetric CSR matrix (Section 3.2.1).
@@ -162,6 +205,7 @@ struct flz_solver {
   flz_stats stats{};
   // workspace
   flz::DevBuf<double> Q, W, C, C2, part, X, AX, small, colpart;
+  flz::TcBasis tcb;  // digit copy of the basis when reorthogonalization runs on the tensor cores
 };
 
 namespace flz {

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <type_traits>
 
 #include "flz_internal.h"
 
@@ -75,8 +76,15 @@ struct Engine {
   double* small; // device r x r scratch (R^{-1})
   double ms_orth = 0.0, ms_op = 0.0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  TcBasis* tcb = nullptr;  // digit copy of an FP64 basis: reorthogonalization on the tensor cores
 
   T* block(int b) const { return Q + (size_t)b * n * r; }
+
+  // Block b of the basis is final: round it to the digit grid and record its digits.
+  void seal(int b) {
+    if constexpr (std::is_same<T, double>::value)
+      if (tcb) tcb->append(block(b), r, b * r, st);
+  }
 
   void gram(const T* X, std::vector<double>& G) {
     basis_dot(X, 1, n, r, X, r, r, C2, part, st);
@@ -138,10 +146,18 @@ struct Engine {
   // Classical Gram-Schmidt twice of X against blocks 0..nb-1; returns the
   // total projection coefficients of the last block (r x r, row-major) in Dlast.
   void cgs2(T* X, int nb, std::vector<double>* Dlast) {
-    basis_dot(Q, nb, n, r, X, r, r, C, part, st);
-    basis_update(Q, nb, n, r, C, r, -1.0, 1.0, X, r, st);
-    basis_dot(Q, nb, n, r, X, r, r, C2, part, st);
-    basis_update(Q, nb, n, r, C2, r, -1.0, 1.0, X, r, st);
+    bool done = false;
+    if constexpr (std::is_same<T, double>::value)
+      if (tcb) {
+        tcb->cgs2(nb * r, X, r, C, C2, st);
+        done = true;
+      }
+    if (!done) {
+      basis_dot(Q, nb, n, r, X, r, r, C, part, st);
+      basis_update(Q, nb, n, r, C, r, -1.0, 1.0, X, r, st);
+      basis_dot(Q, nb, n, r, X, r, r, C2, part, st);
+      basis_update(Q, nb, n, r, C2, r, -1.0, 1.0, X, r, st);
+    }
     if (Dlast) {
       std::vector<double> d1((size_t)r * r), d2((size_t)r * r);
       const size_t off = (size_t)(nb - 1) * r * r;
@@ -175,9 +191,11 @@ struct Engine {
       cgs2(next, j + 1, nullptr);
       block_qr(next, next);
     }
+    if (next) seal(j + 1);
     P.S.push_back(S);
     FLZ_CUDA(cudaEventRecord(ev[2], st));
     FLZ_CUDA(cudaEventSynchronize(ev[2]));
+    if (tcb) tcb->check_status();
     float a = 0.f, b = 0.f;
     FLZ_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
     FLZ_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
@@ -194,6 +212,7 @@ template <class T>
 void orthonormal_start(Engine<T>& E, uint64_t seed) {
   random_normal(E.block(0), E.n * E.r, seed, 0, E.st);
   E.block_qr(E.block(0), E.block(0));
+  E.seal(0);
 }
 
 // Spectrum bounds by block Lanczos on A (Section 2.2 after eq. transf).
@@ -345,8 +364,26 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   kcap = std::min<int64_t>(kcap, n);
   size_t free_b = 0, total_b = 0;
   FLZ_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  const int64_t mem_cap = (int64_t)(0.6 * (double)free_b / (8.0 * (double)n));
-  kcap = std::min(kcap, std::max<int64_t>(mem_cap, 2 * r));
+  // Reorthogonalization on the tensor cores where it applies; AUTO keeps the
+  // FP64 pipes when the digit copy (16 bytes per value) would shrink the basis.
+  bool use_tc = false;
+  if constexpr (std::is_same<BT, double>::value)
+    use_tc = p.ortho == FLZ_ORTHO_TENSOR || (p.ortho == FLZ_ORTHO_AUTO && TcBasis::supported(r));
+  if (use_tc) {
+    const double budget = 0.6 * (double)free_b + (double)s->tcb.q.count;
+    const int64_t tc_cap =
+        (int64_t)(budget / (8.0 * (double)n + (double)TcBasis::bytes_for(n, 16) / 16.0));
+    if (p.ortho == FLZ_ORTHO_AUTO && tc_cap < kcap)
+      use_tc = false;
+    else
+      kcap = std::min(kcap, std::max<int64_t>(tc_cap, 2 * r));
+  }
+  if (!use_tc) {
+    s->tcb.release();
+    const int64_t mem_cap = (int64_t)(0.6 * (double)free_b / (8.0 * (double)n));
+    kcap = std::min(kcap, std::max<int64_t>(mem_cap, 2 * r));
+  }
+  stats.ortho = use_tc ? FLZ_ORTHO_TENSOR : FLZ_ORTHO_CUDA_CORES;
   const int nb_cap = (int)std::max<int64_t>(2, kcap / r);
   s->Q.reserve((size_t)nb_cap * n * r);
   s->W.reserve((size_t)n * r);
@@ -360,6 +397,10 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   static_assert(sizeof(BT) == sizeof(double), "basis storage reuses the FP64 buffers");
   BT* Qt = reinterpret_cast<BT*>(s->Q.p);
   Engine<BT> E{A, n, r, st, Qt, nb_cap, reinterpret_cast<BT*>(s->W.p), s->C.p, s->C2.p, s->part.p, s->small.p};
+  if (use_tc) {
+    s->tcb.reserve(n, (int64_t)nb_cap * r);
+    E.tcb = &s->tcb;
+  }
   orthonormal_start(E, p.seed);
 
   Projected P;
@@ -651,6 +692,7 @@ flz_status solve_sliced(flz_solver* s, int nslices, cudaStream_t st) {
     agg.basis_vectors = std::max(agg.basis_vectors, x.basis_vectors);
     agg.kernel_launches += x.kernel_launches;
     agg.max_residual = std::max(agg.max_residual, x.max_residual);
+    agg.ortho = x.ortho;
   }
   // merge: ascending order, pairs shared by adjacent slices kept once
   const int64_t total = (int64_t)vals.size();

@@ -1,0 +1,256 @@
+"""Full reorthogonalization on the tensor cores (Section 3.2.2, classical
+Gram-Schmidt twice) against exact arithmetic and the FP64 path.
+
+The tensor-core path splits the basis (rounded to the 2^-62 grid) and W
+(rounded to 62 fractional bits of its column scale) into eight base-256
+digits and forms every digit product exactly, so its projections are the
+exact inner products of those rounded values up to one final FP64 rounding.
+The references here are Python integers (exact) and the FP64 CUDA-core path.
+
+The first tests check the shared-memory descriptor layouts of one tcgen05
+MMA on small integer tiles; they run first so that a layout mismatch stops
+the run before the projection kernels (which rely on the same layouts).
+"""
+
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import paper_2409_15053_gb300 as flz
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+
+
+def bf16_bits(x):
+    """uint16 bfloat16 bit patterns of small integers (exact)."""
+    f = np.asarray(x, dtype=np.float32)
+    return (f.view(np.uint32) >> 16).astype(np.uint16)
+
+
+def image(mat, lead_stride, strided_stride, k_major, nbytes):
+    """Shared-memory image of a (rows x 16) operand as 8 x 16-byte core matrices.
+
+    k_major: core-matrix rows are operand rows (16 bytes = 8 consecutive K);
+    otherwise core-matrix rows are K indices (16 bytes = 8 consecutive rows).
+    lead_stride: bytes between core matrices adjacent along K;
+    strided_stride: bytes between core matrices adjacent along the rows.
+    """
+    img = np.zeros(nbytes // 2, dtype=np.uint16)
+    bits = bf16_bits(mat)
+    rows, K = mat.shape
+    for m in range(rows):
+        for k in range(K):
+            if k_major:
+                off = (m // 8) * strided_stride + (k // 8) * lead_stride + (m % 8) * 16 + (k % 8) * 2
+            else:
+                off = (m // 8) * strided_stride + (k // 8) * lead_stride + (k % 8) * 16 + (m % 8) * 2
+            img[off // 2] = bits[m, k]
+    return img
+
+
+def probe(A, B, a_mn_major, a_lbo, a_sbo, b_lbo, b_sbo, a_bytes, b_bytes):
+    a_img = image(A, a_lbo, a_sbo, not a_mn_major, a_bytes)
+    b_img = image(B, b_lbo, b_sbo, True, b_bytes)
+    return flz.flz_tc_mma_probe(a_img, b_img, B.shape[0], a_mn_major, a_lbo, a_sbo, b_lbo, b_sbo)
+
+
+@pytest.mark.parametrize("np_", [32, 16])
+def test_mma_layout_of_the_projection(np_):
+    # projection: A K-major (digit x column rows, 16 strips 2048 B apart, row
+    # octets 128 B apart), B K-major (W columns x digits, octets 128 B apart,
+    # column blocks 4096 B apart)
+    rng = np.random.default_rng(np_)
+    A = rng.integers(-9, 10, size=(128, 16)).astype(np.float32)
+    B = rng.integers(-9, 10, size=(np_, 16)).astype(np.float32)
+    D = probe(A, B, 0, 128, 2048, 128, 4096, 32768, (np_ // 8) * 4096)
+    want = A @ B.T
+    if not np.array_equal(D, want):
+        # diagnosis: the same images with the two stride fields exchanged
+        a_img = image(A, 128, 2048, True, 32768)
+        b_img = image(B, 128, 4096, True, (np_ // 8) * 4096)
+        Ds = flz.flz_tc_mma_probe(a_img, b_img, np_, 0, 2048, 128, 4096, 128)
+        pytest.fail(f"max diff {np.max(np.abs(D - want))}; exchanged fields match: {np.array_equal(Ds, want)}")
+
+
+@pytest.mark.parametrize("np_", [32, 16])
+def test_mma_layout_of_the_update(np_):
+    # update: A MN-major (row octets 128 B apart along M, column halves 2048 B
+    # apart along K), B K-major (column halves 128 B apart, j blocks 256 B apart)
+    rng = np.random.default_rng(100 + np_)
+    A = rng.integers(-9, 10, size=(128, 16)).astype(np.float32)
+    B = rng.integers(-9, 10, size=(np_, 16)).astype(np.float32)
+    D = probe(A, B, 1, 2048, 128, 128, 256, 4096, (np_ // 8) * 256)
+    want = A @ B.T
+    if not np.array_equal(D, want):
+        a_img = image(A, 2048, 128, False, 4096)
+        b_img = image(B, 128, 256, True, (np_ // 8) * 256)
+        Ds = flz.flz_tc_mma_probe(a_img, b_img, np_, 1, 128, 2048, 128, 256)
+        pytest.fail(f"max diff {np.max(np.abs(D - want))}; exchanged A fields match: {np.array_equal(Ds, want)}")
+
+
+def test_mma_holds_exact_integer_sums():
+    # digits up to the bound the kernels use: products up to 2^14, sums of 16
+    A = np.full((128, 16), -128.0, dtype=np.float32)
+    B = np.full((32, 16), -128.0, dtype=np.float32)
+    A[1::2] = 127.0
+    D = probe(A, B, 0, 128, 2048, 128, 4096, 32768, 4 * 4096)
+    assert np.array_equal(D, A @ B.T)
+
+
+# ---------------------------------------------------------------------------
+def orthonormal_blocks(n, nb, r, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, nb * r)))
+    # the basis lives on the 2^-62 grid (what the solver's basis holds)
+    Q = np.rint(Q * 2.0**62) * 2.0**-62
+    blocks = np.ascontiguousarray(Q.reshape(n, nb, r).transpose(1, 0, 2))  # nb x n x r
+    return Q, blocks
+
+
+def exact_projection(Q, W):
+    """Q^T W̃ exactly, W̃ = W rounded to 62 fractional bits of each column's scale."""
+    K, r = Q.shape[1], W.shape[1]
+    vq = np.rint(Q * 2.0**62).astype(np.int64).astype(object)
+    out = np.zeros((K, r))
+    for j in range(r):
+        m = np.max(np.abs(W[:, j]))
+        E = int(np.frexp(m)[1]) if m > 0 else 0  # m < 2^E
+        vw = np.rint(W[:, j] * 2.0**(62 - E)).astype(np.int64).astype(object)
+        col = vq.T.dot(vw)  # Python integers: exact
+        for k in range(K):
+            out[k, j] = float(Fraction(int(col[k])) * Fraction(2) ** (E - 124))
+    return out
+
+
+@pytest.mark.parametrize("n,nb,r", [(4000, 6, 4), (2777, 13, 3), (1000, 9, 2), (513, 20, 1), (3000, 75, 4)])
+def test_projection_is_exact_up_to_the_final_rounding(n, nb, r):
+    Q, blocks = orthonormal_blocks(n, nb, r, n + nb)
+    rng = np.random.default_rng(7)
+    W = rng.standard_normal((n, r)) * np.array([1.0, 1e-3, 37.0, 2.0**-40])[:r]
+    Qd = torch.from_numpy(blocks).cuda()
+    Wd = torch.from_numpy(W).cuda()
+    C = torch.zeros(nb * r, r, dtype=torch.float64, device="cuda")
+    C64 = torch.zeros_like(C)
+    flz.flz_basis_project(n, nb, r, Qd, Wd, C, flz.FLZ_ORTHO_TENSOR)
+    flz.flz_basis_project(n, nb, r, Qd, Wd, C64, flz.FLZ_ORTHO_CUDA_CORES)
+    ref = exact_projection(Q, W)
+    scale = np.linalg.norm(Q, axis=0)[:, None] * np.linalg.norm(W, axis=0)[None, :]
+    err_tc = np.max(np.abs(C.cpu().numpy() - ref) / scale)
+    err_64 = np.max(np.abs(C64.cpu().numpy() - ref) / scale)
+    assert err_tc <= 2.0**-50, (err_tc, err_64)
+    # no worse than the FP64 inner products (which carry n-term rounding)
+    assert err_tc <= max(err_64, 2.0**-52)
+
+
+@pytest.mark.parametrize("n,nb,r", [(4000, 6, 4), (2777, 13, 3), (3000, 75, 4), (300, 1, 2), (8, 1, 1)])
+def test_orthogonalize_matches_fp64_and_leaves_w_orthogonal(n, nb, r):
+    Q, blocks = orthonormal_blocks(n, nb, r, 3 * n + nb)
+    rng = np.random.default_rng(11)
+    # W with a large component in span(Q): the second pass must clean it up
+    W = Q @ rng.standard_normal((nb * r, r)) * 1e3 + rng.standard_normal((n, r))
+    W = np.ascontiguousarray(W)
+    Qd = torch.from_numpy(blocks).cuda()
+    out = {}
+    for method in (flz.FLZ_ORTHO_TENSOR, flz.FLZ_ORTHO_CUDA_CORES):
+        Wd = torch.from_numpy(W.copy()).cuda()
+        C = torch.zeros(nb * r, r, dtype=torch.float64, device="cuda")
+        flz.flz_basis_orthogonalize(n, nb, r, Qd, Wd, C, method)
+        out[method] = (Wd.cpu().numpy(), C.cpu().numpy())
+    Wt, Ct = out[flz.FLZ_ORTHO_TENSOR]
+    W6, C6 = out[flz.FLZ_ORTHO_CUDA_CORES]
+    nw = np.linalg.norm(Wt, axis=0)
+    assert np.max(np.abs(Q.T @ Wt) / nw) < 1e-14
+    assert np.max(np.abs(Wt - W6)) < 1e-12 * np.max(np.abs(W))
+    assert np.max(np.abs(Ct - C6)) < 1e-12 * np.max(np.abs(C6))
+
+
+def test_full_size_projection_grid():
+    # the benchmark's row count: many CTAs per group set, 256-row ranges
+    n, nb, r = 1_000_000, 30, 4
+    g = torch.Generator(device="cuda").manual_seed(5)
+    Q = torch.randn(n, nb * r, dtype=torch.float64, device="cuda", generator=g)
+    Q, _ = torch.linalg.qr(Q)
+    Q = torch.round(Q * 2.0**62) * 2.0**-62
+    blocks = Q.reshape(n, nb, r).permute(1, 0, 2).contiguous()
+    W = torch.randn(n, r, dtype=torch.float64, device="cuda", generator=g) + Q[:, :r] * 50.0
+    C = torch.zeros(nb * r, r, dtype=torch.float64, device="cuda")
+    C64 = torch.zeros_like(C)
+    Wt = W.clone()
+    flz.flz_basis_orthogonalize(n, nb, r, blocks, Wt, C, flz.FLZ_ORTHO_TENSOR)
+    W6 = W.clone()
+    flz.flz_basis_orthogonalize(n, nb, r, blocks, W6, C64, flz.FLZ_ORTHO_CUDA_CORES)
+    torch.cuda.synchronize()
+    proj = (Q.T @ Wt) / torch.linalg.norm(Wt, dim=0)
+    assert float(proj.abs().max()) < 1e-14
+    assert float((Wt - W6).abs().max()) < 1e-11 * float(W.abs().max())
+    assert float((C - C64).abs().max()) < 1e-11 * float(C64.abs().max())
+
+
+# ---------------------------------------------------------------------------
+def test_solver_on_the_tensor_cores_matches_the_fp64_path():
+    from synth import laplacian_3d_7pt
+    A = laplacian_3d_7pt(24, 24, 24)
+    h = flz.flz_matrix_create_csr(A.n, A.nnz, A.rowptr, A.col, A.val)
+    try:
+        vals = {}
+        for ortho in (flz.FLZ_ORTHO_TENSOR, flz.FLZ_ORTHO_CUDA_CORES, flz.FLZ_ORTHO_AUTO):
+            p = flz.flz_params_default()
+            p.block_size = 4
+            p.degree = 60
+            p.check_every = 10
+            p.ortho = ortho
+            s = flz.flz_solver_create(h, p)
+            try:
+                flz.flz_solver_set_interval(s, 0.0, 0.436)
+                assert flz.flz_solve(s) == flz.FLZ_OK
+                st = flz.flz_get_stats(s)
+                vals[ortho] = (flz.flz_get_eigenvalues(s), flz.flz_get_residuals(s), st.ortho)
+            finally:
+                flz.flz_solver_destroy(s)
+        t, c, a = vals[flz.FLZ_ORTHO_TENSOR], vals[flz.FLZ_ORTHO_CUDA_CORES], vals[flz.FLZ_ORTHO_AUTO]
+        assert t[2] == flz.FLZ_ORTHO_TENSOR and c[2] == flz.FLZ_ORTHO_CUDA_CORES
+        assert a[2] == flz.FLZ_ORTHO_TENSOR  # AUTO picks the tensor cores for r <= 4
+        assert t[0].shape == c[0].shape and t[0].shape[0] > 20
+        assert np.max(np.abs(t[0] - c[0])) < 1e-12
+        assert np.max(t[1]) < 1e-10
+        # closed form: 6 - 2 sum cos(k pi / 25)
+        k = np.arange(1, 25)
+        lam = np.sort((6 - 2 * (np.cos(k[:, None, None] * np.pi / 25) + np.cos(k[None, :, None] * np.pi / 25) +
+                                np.cos(k[None, None, :] * np.pi / 25))).ravel())
+        want = lam[(lam >= 0.0) & (lam <= 0.436)]
+        assert t[0].shape == want.shape and np.max(np.abs(t[0] - want)) < 1e-12
+    finally:
+        flz.flz_matrix_destroy(h)
+
+
+def test_block_width_above_four_falls_back_under_auto():
+    from synth import laplacian_2d
+    A = laplacian_2d(40, 40)
+    h = flz.flz_matrix_create_csr(A.n, A.nnz, A.rowptr, A.col, A.val)
+    try:
+        p = flz.flz_params_default()
+        p.block_size = 8
+        p.degree = 40
+        s = flz.flz_solver_create(h, p)
+        try:
+            flz.flz_solver_set_interval(s, 0.0, 0.3)
+            assert flz.flz_solve(s) == flz.FLZ_OK
+            assert flz.flz_get_stats(s).ortho == flz.FLZ_ORTHO_CUDA_CORES
+        finally:
+            flz.flz_solver_destroy(s)
+        p.ortho = flz.FLZ_ORTHO_TENSOR
+        with pytest.raises(flz.FlzError) as e:
+            flz.flz_solver_create(h, p)
+        assert e.value.status == flz.FLZ_ERR_INVALID_ARG
+    finally:
+        flz.flz_matrix_destroy(h)
