@@ -43,6 +43,7 @@ METRIC = "eigenpairs/s at residual 1e-8 (3D 7-point Laplacian 100^3 + potential,
 # Filter degree of the timed solve: among the degrees 40, 60, 100 and 150 on
 # this workload, 100 gave the shortest time to solution (fewer block steps and
 # reorthogonalizations at a moderate cost per step, as in Tables 2 and 3).
+ORTHO = {"auto": 0, "cuda_cores": 1, "tensor": 2}
 BENCH_DEGREE = 100
 BATCH_DEGREE = 60
 
@@ -220,12 +221,29 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def ortho_summary(st, n, r, hbm):
+    """The reorthogonalization phase as a whole (CGS2 + block QR + the small
+    kernels between them) against HBM: on the tensor cores each of the four
+    passes of a step reads the digit copy of the K-column basis once (16 bytes
+    per value), so the algorithmic bytes of a solve are 4 * 16 * n * sum_j K_j
+    with K_j = r (j + 1) at block step j. On the CUDA cores the same passes read
+    the FP64 basis (8 bytes per value) and are FP64-pipe bound (r / 4 flop/B)."""
+    iters = int(st["iters"])
+    cols = r * iters * (iters + 1) // 2
+    tensor = st["ortho"] == 2
+    nbytes = 4 * (16 if tensor else 8) * n * cols
+    gbs = nbytes / (st["ms_orth"] * 1e-3) / 1e9 if st["ms_orth"] > 0 else None
+    return {"path": "tensor" if tensor else "cuda_cores", "ms": st["ms_orth"],
+            "basis_bytes_read": nbytes, "achieved_gbs": gbs, "hbm_frac": (gbs / hbm) if gbs else None,
+            "flops": 4 * 2 * n * cols * r}
+
+
 def config_dict(csr, args):
     return {"workload": "3D 7-point Dirichlet Laplacian 100^3 + 0.5*U(0,1) potential (seed 2025), "
                         "all eigenpairs in [alpha, beta] at the low end of the spectrum",
             "n": csr.n, "nnz": csr.nnz, "alpha": CONFIG2["alpha"], "beta": CONFIG2["beta"],
             "block_size": args.block_size, "degree": args.degree, "precision": args.precision, "tol": args.tol,
-            "check_every": args.check_every, "recurrence": args.recurrence,
+            "check_every": args.check_every, "recurrence": args.recurrence, "ortho": args.ortho,
             "l2": "flushed (512 MiB write) before each timed step", "parallelism": "single GPU"}
 
 
@@ -241,6 +259,8 @@ def main():
     ap.add_argument("--recurrence", default="forward", choices=["forward", "clenshaw"])
     ap.add_argument("--damping", default="none", choices=["none", "jackson", "sigma"],
                     help="filter damping (the paper uses none)")
+    ap.add_argument("--ortho", default="auto", choices=["auto", "cuda_cores", "tensor"],
+                    help="where the full reorthogonalization runs (auto: tensor cores for r <= 4)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--check-every", type=int, default=CONFIG2["check_every"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
@@ -299,6 +319,7 @@ def main():
     p.precision = prec
     p.recurrence = {"forward": flz.FLZ_REC_FORWARD, "clenshaw": flz.FLZ_REC_CLENSHAW}[args.recurrence]
     p.damping = {"none": 0, "jackson": 1, "sigma": 2}[args.damping]
+    p.ortho = ORTHO[args.ortho]
     p.seed = 1 + rank
     s = flz.flz_solver_create(h, p)
     flz.flz_solver_set_interval(s, alpha, beta)
@@ -396,7 +417,8 @@ def main():
             "e2e": e2e, "variants": variants, "batch64": batch, "gpu_launches": int(sum(x["kernel_launches"] for x in stats_list)), "clocks": clocks,
             "solver": {k: st[k] for k in ("iters", "matvecs", "count", "degree", "checks", "lmin", "lmax",
                                           "max_residual", "ms_bounds", "ms_filter", "ms_orth", "ms_check",
-                                          "ms_total", "basis_vectors", "kernel_launches")},
+                                          "ms_total", "basis_vectors", "kernel_launches", "ortho")},
+            "ortho": ortho_summary(st, csr.n, args.block_size, hbm),
             "found_per_step": found,
         }
         print(json.dumps(line))
@@ -414,16 +436,19 @@ def variant_leg(flz, torch, h, p, alpha, beta, stream, flush, ref_vals, args):
     out = {}
     # the reduced-precision filters at the residual they can reach, double-FP32 at the FP64 tolerance
     F, C = flz.FLZ_REC_FORWARD, flz.FLZ_REC_CLENSHAW
-    for name, prec, tol, rec in (("df64_filter", flz.FLZ_PREC_DF64, p.tol, F),
-                                 ("fp64_clenshaw", flz.FLZ_PREC_FP64, p.tol, C),
-                                 ("df64_clenshaw", flz.FLZ_PREC_DF64, p.tol, C),
-                                 ("fp32_filter", flz.FLZ_PREC_FP32, 1e-6, F),
-                                 ("bf16_filter", flz.FLZ_PREC_BF16, 1e-3, F)):
+    T, CC = flz.FLZ_ORTHO_AUTO, flz.FLZ_ORTHO_CUDA_CORES
+    for name, prec, tol, rec, ortho in (("fp64_cuda_core_ortho", flz.FLZ_PREC_FP64, p.tol, F, CC),
+                                        ("fp64_clenshaw", flz.FLZ_PREC_FP64, p.tol, C, T),
+                                        ("df64_filter", flz.FLZ_PREC_DF64, p.tol, F, T),
+                                        ("df64_clenshaw", flz.FLZ_PREC_DF64, p.tol, C, T),
+                                        ("fp32_filter", flz.FLZ_PREC_FP32, 1e-6, F, T),
+                                        ("bf16_filter", flz.FLZ_PREC_BF16, 1e-3, F, T)):
         q = flz.flz_params_default()
         for f, _ in q._fields_:
             setattr(q, f, getattr(p, f))
         q.precision = prec
         q.recurrence = rec
+        q.ortho = ortho
         q.tol = max(tol, p.tol)
         sv = flz.flz_solver_create(h, q)
         flz.flz_solver_set_interval(sv, alpha, beta)
@@ -451,7 +476,7 @@ def variant_leg(flz, torch, h, p, alpha, beta, stream, flush, ref_vals, args):
             "max_abs_eig_diff_vs_fp64": float(np.max(np.abs(vals - ref_vals))) if same and vals.size else None,
             "max_residual": float(np.max(res)) if res.size else None,
             "ms_filter": stats["ms_filter"], "ms_orth": stats["ms_orth"], "ms_check": stats["ms_check"],
-            "iters": stats["iters"],
+            "iters": stats["iters"], "ortho": ["auto", "cuda_cores", "tensor"][stats["ortho"]],
         }
     return out
 

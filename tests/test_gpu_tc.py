@@ -214,7 +214,7 @@ def test_solver_on_the_tensor_cores_matches_the_fp64_path():
                 flz.flz_solver_set_interval(s, 0.0, 0.436)
                 assert flz.flz_solve(s) == flz.FLZ_OK
                 st = flz.flz_get_stats(s)
-                vals[ortho] = (flz.flz_get_eigenvalues(s), flz.flz_get_residuals(s), st.ortho)
+                vals[ortho] = (flz.flz_get_eigenvalues(s), flz.flz_get_residuals(s), st["ortho"])
             finally:
                 flz.flz_solver_destroy(s)
         t, c, a = vals[flz.FLZ_ORTHO_TENSOR], vals[flz.FLZ_ORTHO_CUDA_CORES], vals[flz.FLZ_ORTHO_AUTO]
@@ -245,7 +245,7 @@ def test_block_width_above_four_falls_back_under_auto():
         try:
             flz.flz_solver_set_interval(s, 0.0, 0.3)
             assert flz.flz_solve(s) == flz.FLZ_OK
-            assert flz.flz_get_stats(s).ortho == flz.FLZ_ORTHO_CUDA_CORES
+            assert flz.flz_get_stats(s)["ortho"] == flz.FLZ_ORTHO_CUDA_CORES
         finally:
             flz.flz_solver_destroy(s)
         p.ortho = flz.FLZ_ORTHO_TENSOR
