@@ -269,7 +269,10 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32/BF16-filter solves reported under 'variants'")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch-of-64 leg")
-    ap.add_argument("--mode", default="solve", choices=["solve", "filter", "batch", "table2", "graph", "slices"],
+    ap.add_argument("--ortho-n", type=int, default=1_000_000, help="rows of the --mode ortho basis")
+    ap.add_argument("--ortho-basis", type=int, default=120, help="columns of the --mode ortho basis")
+    ap.add_argument("--mode", default="solve", choices=["solve", "filter", "batch", "table2", "graph", "slices",
+                                                        "ortho"],
                     help="solve: whole flz_solve per step (default); filter: only flz_filter_apply at the "
                          "solver's shape, for the kernel roofline and profiling")
     args = ap.parse_args()
@@ -304,6 +307,8 @@ def main():
         return graph_mode(flz, torch, args)
     if args.mode == "slices":
         return slices_mode(flz, torch, prec, args)
+    if args.mode == "ortho":
+        return ortho_mode(flz, torch, args)
     csr = make_matrix()
     if args.mode == "filter":
         return filter_mode(flz, torch, csr, prec, args)
@@ -730,6 +735,39 @@ def graph_mode(flz, torch, args):
         flz.flz_solver_destroy(s)
     flz.flz_matrix_destroy(h)
     print(json.dumps(out))
+
+
+def ortho_mode(flz, torch, args):
+    """Full reorthogonalization alone: classical Gram-Schmidt twice of an n x r
+    block against a K-column orthonormal basis (on the 2^-62 grid), on the
+    tensor cores and on the CUDA cores, each call checked for orthogonality and
+    against the other path. The small case the kernel profiles are taken on
+    (about 3 GB on the device for the defaults). Each flz_basis_orthogonalize
+    call also builds the digit copy of the caller's basis, so its wall time is
+    not the solver's per-step cost; the kernels' own times come from ncu."""
+    n, K, r = args.ortho_n, args.ortho_basis, args.block_size
+    nb = K // r
+    g = torch.Generator(device="cuda").manual_seed(9)
+    Q = torch.randn(n, nb * r, dtype=torch.float64, device="cuda", generator=g)
+    Q, _ = torch.linalg.qr(Q)
+    Q = torch.round(Q * 2.0**62) * 2.0**-62
+    blocks = Q.reshape(n, nb, r).permute(1, 0, 2).contiguous()
+    W0 = torch.randn(n, r, dtype=torch.float64, device="cuda", generator=g) + 30.0 * Q[:, :r]
+    out = {}
+    for name, method in (("tensor", flz.FLZ_ORTHO_TENSOR), ("cuda_cores", flz.FLZ_ORTHO_CUDA_CORES)):
+        for _ in range(max(args.steps, 2)):
+            W = W0.clone()
+            C = torch.zeros(nb * r, r, dtype=torch.float64, device="cuda")
+            flz.flz_basis_orthogonalize(n, nb, r, blocks, W, C, method)
+        torch.cuda.synchronize()
+        proj = (Q.T @ W) / torch.linalg.norm(W, dim=0)
+        out[name] = {"max_rel_projection_after": float(proj.abs().max()), "W": W}
+    diff = float((out["tensor"]["W"] - out["cuda_cores"]["W"]).abs().max() / W0.abs().max())
+    print(json.dumps({"mode": "ortho", "n": n, "basis": nb * r, "r": r,
+                      "digit_bytes_per_pass": 16 * n * nb * r, "fp64_bytes_per_pass": 8 * n * nb * r,
+                      "tensor_max_rel_projection_after": out["tensor"]["max_rel_projection_after"],
+                      "cuda_cores_max_rel_projection_after": out["cuda_cores"]["max_rel_projection_after"],
+                      "max_rel_diff_tensor_vs_cuda_cores": diff}))
 
 
 def filter_mode(flz, torch, csr, prec, args):
