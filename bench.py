@@ -749,7 +749,9 @@ def ortho_mode(flz, torch, args):
     nb = K // r
     g = torch.Generator(device="cuda").manual_seed(9)
     Q = torch.randn(n, nb * r, dtype=torch.float64, device="cuda", generator=g)
-    Q, _ = torch.linalg.qr(Q)
+    for _ in range(2):  # CholeskyQR2 (matrix products on the GPU, the small Cholesky on the host)
+        R = np.linalg.cholesky((Q.T @ Q).cpu().numpy()).T
+        Q = Q @ torch.from_numpy(np.linalg.inv(R)).cuda()
     Q = torch.round(Q * 2.0**62) * 2.0**-62
     blocks = Q.reshape(n, nb, r).permute(1, 0, 2).contiguous()
     W0 = torch.randn(n, r, dtype=torch.float64, device="cuda", generator=g) + 30.0 * Q[:, :r]

@@ -146,7 +146,8 @@ __global__ void basis_digits_kernel(double* __restrict__ X, int64_t n, int r, in
 // W, digit t), K = 16 rows, 16 instructions per range and group into a
 // double-buffered tensor-memory accumulator; the epilogue warps add each
 // drained range (exact integers <= 2^22) into int32 registers (<= 256 ranges
-// per CTA, so <= 2^30) and write them once per CTA as partials.
+// per CTA, so <= 2^30) and add those once per CTA into 64-bit integer
+// accumulators in global memory (reductions without a return value).
 struct DotArgs {
   const uint8_t* q;
   int64_t n_oct, n;
@@ -154,7 +155,7 @@ struct DotArgs {
   const double* W;
   int r, ldw;
   const uint32_t* wmax;
-  int32_t* part;
+  unsigned long long* acc;  // Gtot x 128 x NP integer sums, zero on entry
   int* status;
 };
 
@@ -347,14 +348,16 @@ __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
       tc::mbar_arrive(acc_empty + buf);
     }
     const int m = q4 * 32 + lane;
+    if (nloc > 0) {
 #pragma unroll
-    for (int g = 0; g < GPC; ++g) {
-      if (g < gcount) {
-        const int G = gs * GPC + g;
-        int4* dst = reinterpret_cast<int4*>(a.part + (((size_t)blockIdx.x * a.Gtot + G) * 128 + m) * NP);
+      for (int g = 0; g < GPC; ++g) {
+        if (g < gcount) {
+          const int G = gs * GPC + g;
+          unsigned long long* dst = a.acc + ((size_t)G * 128 + m) * NP;
 #pragma unroll
-        for (int x = 0; x < NP / 4; ++x)
-          dst[x] = make_int4(acc[g][4 * x], acc[g][4 * x + 1], acc[g][4 * x + 2], acc[g][4 * x + 3]);
+          for (int x = 0; x < NP; ++x)  // two's-complement sums: exact for |total| < 2^63
+            if (acc[g][x]) atomicAdd(dst + x, (unsigned long long)(long long)acc[g][x]);
+        }
       }
     }
   }
@@ -374,18 +377,18 @@ __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
   }
 }
 
-// Sums the partials of group G over the CTAs, recombines the 64 digit pairs
-// (diagonal by diagonal, exact until the last few FP64 additions) and writes
-// C[kb, j] for the group's columns kb < K.
+// Reads group G's integer sums (and clears them for the next projection),
+// recombines the 64 digit pairs (diagonal by diagonal, exact until the last
+// few FP64 additions) and writes C[kb, j] for the group's columns kb < K.
 template <int NP>
-__global__ void tc_dot_reduce_kernel(const int32_t* __restrict__ part, int RS, int Gtot, int K, int r,
-                                     const uint32_t* wmax, double* C, int ldc) {
+__global__ void tc_dot_reduce_kernel(unsigned long long* __restrict__ acc, int K, int r, const uint32_t* wmax,
+                                     double* C, int ldc) {
   __shared__ double P[128 * NP];
   const int G = blockIdx.x;
+  unsigned long long* src = acc + (size_t)G * 128 * NP;
   for (int e = threadIdx.x; e < 128 * NP; e += blockDim.x) {
-    long long s = 0;
-    for (int b = 0; b < RS; ++b) s += part[((size_t)b * Gtot + G) * 128 * NP + e];
-    P[e] = (double)s;  // |s| <= RS 2^30: exact
+    P[e] = (double)(long long)src[e];  // |sum| <= (CTAs) 2^30 < 2^53: exact
+    src[e] = 0ull;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < 16 * r; t += blockDim.x) {
@@ -714,17 +717,15 @@ void launch_dot(TcBasis& B, int K, const double* W, int r, int ldw, const uint32
   const int waves = std::max(1, (minRS * GS + sms - 1) / sms);
   int RS = std::max(minRS, (waves * sms) / GS);
   RS = std::max(1, std::min(RS, nR));
-  const size_t need = (size_t)RS * Gtot * 128 * NP;
-  if (B.part.count < need) B.part.reserve(need);
   static bool attr = false;
   if (!attr) {
     allow_smem(tc_dot_kernel<NP>, dot_smem(NP));
     attr = true;
   }
-  DotArgs a{B.q.p, B.n_oct, B.n, Gtot, nR, RS, W, r, ldw, wmax, B.part.p, B.status.p};
+  DotArgs a{B.q.p, B.n_oct, B.n, Gtot, nR, RS, W, r, ldw, wmax, B.acc.p, B.status.p};
   tc_dot_kernel<NP><<<dim3(RS, GS), 256, dot_smem(NP), st>>>(a);
   FLZ_LAUNCH_CHECK();
-  tc_dot_reduce_kernel<NP><<<Gtot, 256, 0, st>>>(B.part.p, RS, Gtot, K, r, wmax, C, ldc);
+  tc_dot_reduce_kernel<NP><<<Gtot, 256, 0, st>>>(B.acc.p, K, r, wmax, C, ldc);
   FLZ_LAUNCH_CHECK();
 }
 
@@ -753,7 +754,7 @@ bool TcBasis::supported(int r) { return r >= 1 && r <= 4; }
 
 void TcBasis::release() {
   q.release();
-  part.release();
+  acc.release();
   hs.release();
   hexp.release();
   wmax.release();
@@ -784,6 +785,8 @@ void TcBasis::reserve(int64_t n_, int64_t kcap) {
   // digits outside the written columns and rows must be finite (zero)
   FLZ_CUDA(cudaMemset(q.p, 0, bytes));
   hs.reserve((size_t)groups_cap * 32 * 16 + 64);
+  acc.reserve((size_t)groups_cap * 128 * 32);  // NP <= 32
+  FLZ_CUDA(cudaMemset(acc.p, 0, sizeof(unsigned long long) * acc.count));
   hexp.reserve(16);
   wmax.reserve(32);
   status.reserve(1);
