@@ -37,7 +37,8 @@ sys.path.insert(0, ROOT)
 
 from synth import (laplacian_3d_7pt, parsec_like_hamiltonian, powerlaw_graph_laplacian,  # noqa: E402
                    random_normal_block, uneven_batch)
-from synth.workloads import BATCH64, CONFIG2  # noqa: E402
+from synth.matrices import fd4_laplacian_3d, gaussian_wells_potential  # noqa: E402
+from synth.workloads import BATCH64, CONFIG2, CONFIG3  # noqa: E402
 
 METRIC = "eigenpairs/s at residual 1e-8 (3D 7-point Laplacian 100^3 + potential, FP64)"
 # Filter degree of the timed solve: among the degrees 40, 60, 100 and 150 on
@@ -272,7 +273,7 @@ def main():
     ap.add_argument("--ortho-n", type=int, default=1_000_000, help="rows of the --mode ortho basis")
     ap.add_argument("--ortho-basis", type=int, default=120, help="columns of the --mode ortho basis")
     ap.add_argument("--mode", default="solve", choices=["solve", "filter", "batch", "table2", "graph", "slices",
-                                                        "ortho"],
+                                                        "ortho", "config3"],
                     help="solve: whole flz_solve per step (default); filter: only flz_filter_apply at the "
                          "solver's shape, for the kernel roofline and profiling")
     args = ap.parse_args()
@@ -309,6 +310,8 @@ def main():
         return slices_mode(flz, torch, prec, args)
     if args.mode == "ortho":
         return ortho_mode(flz, torch, args)
+    if args.mode == "config3":
+        return config3_mode(flz, torch, args)
     csr = make_matrix()
     if args.mode == "filter":
         return filter_mode(flz, torch, csr, prec, args)
@@ -735,6 +738,58 @@ def graph_mode(flz, torch, args):
         flz.flz_solver_destroy(s)
     flz.flz_matrix_destroy(h)
     print(json.dumps(out))
+
+
+def config3_mode(flz, torch, args):
+    """The 4th-order finite-difference Hamiltonian at full size (120^3 grid,
+    64 Gaussian wells, n = 1.728e6, 22.2e6 entries), r = 4, checks every 10
+    block steps, one warm-up then one timed solve per row: the bound states
+    [-6, -0.2] (m = 200), [-6, 0] (m = 300) and [-6, 0.03] reaching into the
+    box continuum (m = 400) in FP64; the widest window also with the CUDA-core
+    reorthogonalization and with the double-FP32 filter and basis; the bound
+    states with double-FP32 Clenshaw."""
+    N = CONFIG3["grid"]
+    csr = fd4_laplacian_3d(N, gaussian_wells_potential(N, CONFIG3["wells"], seed=CONFIG3["seed"]))
+    h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+    stream = torch.cuda.current_stream()
+    F, C = flz.FLZ_REC_FORWARD, flz.FLZ_REC_CLENSHAW
+    rows = []
+    for beta, m, prec, rec, ortho in ((-0.2, 200, flz.FLZ_PREC_FP64, F, ORTHO[args.ortho]),
+                                      (0.0, 300, flz.FLZ_PREC_FP64, F, ORTHO[args.ortho]),
+                                      (0.03, 400, flz.FLZ_PREC_FP64, F, ORTHO[args.ortho]),
+                                      (0.03, 400, flz.FLZ_PREC_FP64, F, flz.FLZ_ORTHO_CUDA_CORES),
+                                      (0.03, 400, flz.FLZ_PREC_DF64, F, ORTHO[args.ortho]),
+                                      (-0.2, 200, flz.FLZ_PREC_DF64, C, ORTHO[args.ortho])):
+        p = flz.flz_params_default()
+        p.block_size = 4
+        p.degree = m
+        p.precision = prec
+        p.recurrence = rec
+        p.ortho = ortho
+        p.check_every = 10
+        p.tol = args.tol
+        s = flz.flz_solver_create(h, p)
+        flz.flz_solver_set_interval(s, CONFIG3["alpha"], beta)
+        flz.flz_solve(s, stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = flz.flz_solve(s, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        x = flz.flz_get_stats(s)
+        res = flz.flz_get_residuals(s)
+        rows.append({"interval": [CONFIG3["alpha"], beta], "m": m,
+                     "precision": {0: "fp64", 3: "df64"}[prec], "recurrence": ["forward", "clenshaw"][rec],
+                     "ortho": ["auto", "cuda_cores", "tensor"][x["ortho"]], "status": flz.flz_status_string(st),
+                     "count": int(x["count"]), "block_steps": int(x["iters"]), "seconds": e0.elapsed_time(e1) / 1e3,
+                     "max_residual": float(res.max()) if res.size else None,
+                     "eigenvalues_head": [float(v) for v in flz.flz_get_eigenvalues(s)[:3]],
+                     "ms_filter": x["ms_filter"], "ms_orth": x["ms_orth"], "ms_check": x["ms_check"]})
+        flz.flz_solver_destroy(s)
+    flz.flz_matrix_destroy(h)
+    print(json.dumps({"mode": "config3", "n": csr.n, "nnz": csr.nnz, "tol": args.tol, "rows": rows}))
 
 
 def ortho_mode(flz, torch, args):

@@ -393,6 +393,7 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   s->small.reserve(16 * 16 + 64);
   s->X.reserve((size_t)n * 16);
   s->AX.reserve((size_t)n * 16);
+  FLZ_CUDA(cudaMemsetAsync(s->X.p, 0, sizeof(double) * n * 16, st));  // columns a short chunk leaves unwritten
   s->colpart.reserve(column_sums_scratch(n, 16) + 64);
   static_assert(sizeof(BT) == sizeof(double), "basis storage reuses the FP64 buffers");
   BT* Qt = reinterpret_cast<BT*>(s->Q.p);
@@ -487,7 +488,13 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
       s->C2.reserve(std::max(s->C2.count, (size_t)K * 16));
       E.C2 = s->C2.p;
       FLZ_CUDA(cudaMemcpyAsync(s->C2.p, Cy.data(), sizeof(double) * K * 16, cudaMemcpyHostToDevice, st));
-      basis_update(Qt, k, n, r, s->C2.p, 16, 1.0, 0.0, s->X.p, 16, st);
+      bool tc_ritz = false;
+      if constexpr (std::is_same<BT, double>::value)
+        if (E.tcb) {
+          E.tcb->multiply(K, s->C2.p, 16, cnt, s->X.p, 16, st);
+          tc_ritz = true;
+        }
+      if (!tc_ritz) basis_update(Qt, k, n, r, s->C2.p, 16, 1.0, 0.0, s->X.p, 16, st);
       spmm(A, s->X.p, s->AX.p, 16, 16, st);
       double* dev = s->small.p;  // [0,16) xx, [16,32) xAx, [32,48) lam, [48,64) res2, [64] scale
       column_sums(s->X.p, s->X.p, nullptr, n, 16, 16, 0, dev, s->colpart.p, st);

@@ -412,9 +412,9 @@ __global__ void tc_dot_reduce_kernel(unsigned long long* __restrict__ acc, int K
 // per group G, the K-major B operand N = NP (column j, digit t) x K = 16
 // (column c of the group) as core matrices (j, c/8) of 8 digits x 8 columns:
 //   halfword G NP 16 + ((j 2 + c/8) 8 + t) 8 + c % 8.
-// Also writes the column scale exponents.
+// Also writes the column scale exponents. sign = -1 stores the digits of -H.
 __global__ void tc_hdigits_kernel(const double* __restrict__ C, int ldc, int K, int r, int Gtot, int NP,
-                                  uint16_t* __restrict__ hs, int* hexp) {
+                                  uint16_t* __restrict__ hs, int* hexp, int sign) {
   __shared__ uint32_t mx[16];
   if (threadIdx.x < 16) mx[threadIdx.x] = 0u;
   __syncthreads();
@@ -428,7 +428,7 @@ __global__ void tc_hdigits_kernel(const double* __restrict__ C, int ldc, int K, 
     const int G = e / (16 * ng), rem = e - G * 16 * ng;
     const int j = rem / 16, c = rem - j * 16, kb = G * 16 + c;
     long long v = 0;
-    if (j < r && kb < K) v = __double2ll_rn(C[(size_t)kb * ldc + j] * pow2i(62 - scale_exponent(mx[j])));
+    if (j < r && kb < K) v = sign * __double2ll_rn(C[(size_t)kb * ldc + j] * pow2i(62 - scale_exponent(mx[j])));
     int d[kDig];
     digits8(v, d);
 #pragma unroll
@@ -457,6 +457,7 @@ struct UpdArgs {
   const int* hexp;
   double* W;
   int r, ldw;
+  int keep;            // 1: W -= Q H; 0: W = -Q H (H the digits' value)
   uint32_t* wmax_out;  // per-column maxima of the updated W, or null
   int* status;
 };
@@ -600,7 +601,7 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(UpdArgs a) {
                 ((small_ll_to_double(P2) * 5.9604644775390625e-08 + small_ll_to_double(P1)) * 5.9604644775390625e-08 +
                  small_ll_to_double(P0)) *
                 hsc[j];
-            const double w = a.W[i * a.ldw + j] - val;
+            const double w = a.keep ? a.W[i * a.ldw + j] - val : -val;
             a.W[i * a.ldw + j] = w;
             wm[j] = max(wm[j], abs_hiword(w));
           }
@@ -729,8 +730,9 @@ void launch_dot(TcBasis& B, int K, const double* W, int r, int ldw, const uint32
   FLZ_LAUNCH_CHECK();
 }
 
+// keep = 1: W -= Q[:, :K] H; keep = 0: W = -Q[:, :K] H in the first window, later windows subtract
 template <int NP>
-void launch_update(TcBasis& B, int K, double* W, int r, int ldw, uint32_t* wmax_out, cudaStream_t st) {
+void launch_update(TcBasis& B, int K, double* W, int r, int ldw, int keep, uint32_t* wmax_out, cudaStream_t st) {
   const int Gtot = (K + 15) / 16;
   const int ntiles = (int)(B.n_pad / kChunk);
   const int grid = std::min(ntiles, num_sms());
@@ -741,7 +743,7 @@ void launch_update(TcBasis& B, int K, double* W, int r, int ldw, uint32_t* wmax_
   }
   for (int G0 = 0; G0 < Gtot; G0 += kWindowGroups) {
     const int G1 = std::min(Gtot, G0 + kWindowGroups);
-    UpdArgs a{B.q.p, B.n_oct, B.n, ntiles, G0, G1, B.hs.p, B.hexp.p, W, r, ldw,
+    UpdArgs a{B.q.p, B.n_oct, B.n, ntiles, G0, G1, B.hs.p, B.hexp.p, W, r, ldw, keep || G0 > 0 ? 1 : 0,
               G1 == Gtot ? wmax_out : nullptr, B.status.p};
     tc_update_kernel<NP><<<grid, 192, upd_smem(NP), st>>>(a);
     FLZ_LAUNCH_CHECK();
@@ -815,12 +817,27 @@ void TcBasis::subtract(int K, const double* C, int ldc, double* W, int r, int ld
                        cudaStream_t st) {
   const int np = padded_np(r);
   const int Gtot = (K + 15) / 16;
-  tc_hdigits_kernel<<<1, 256, 0, st>>>(C, ldc, K, r, Gtot, np, hs.p, hexp.p);
+  tc_hdigits_kernel<<<1, 256, 0, st>>>(C, ldc, K, r, Gtot, np, hs.p, hexp.p, 1);
   FLZ_LAUNCH_CHECK();
   if (np == 16)
-    launch_update<16>(*this, K, W, r, ldw, wmax_out, st);
+    launch_update<16>(*this, K, W, r, ldw, 1, wmax_out, st);
   else
-    launch_update<32>(*this, K, W, r, ldw, wmax_out, st);
+    launch_update<32>(*this, K, W, r, ldw, 1, wmax_out, st);
+}
+
+void TcBasis::multiply(int K, const double* C, int ldc, int s, double* X, int ldx, cudaStream_t st) {
+  const int Gtot = (K + 15) / 16;
+  for (int c0 = 0; c0 < s; c0 += 4) {
+    const int w = std::min(4, s - c0);
+    const int np = padded_np(w);
+    // digits of -C: the first window writes -Q(-C), later windows subtract Q(-C)
+    tc_hdigits_kernel<<<1, 256, 0, st>>>(C + c0, ldc, K, w, Gtot, np, hs.p, hexp.p, -1);
+    FLZ_LAUNCH_CHECK();
+    if (np == 16)
+      launch_update<16>(*this, K, X + c0, w, ldx, 0, nullptr, st);
+    else
+      launch_update<32>(*this, K, X + c0, w, ldx, 0, nullptr, st);
+  }
 }
 
 void TcBasis::column_max(const double* W, int r, int ldw, uint32_t* out, cudaStream_t st) {

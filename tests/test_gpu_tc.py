@@ -215,6 +215,13 @@ def test_solver_on_the_tensor_cores_matches_the_fp64_path():
                 assert flz.flz_solve(s) == flz.FLZ_OK
                 st = flz.flz_get_stats(s)
                 vals[ortho] = (flz.flz_get_eigenvalues(s), flz.flz_get_residuals(s), st["ortho"])
+                if ortho == flz.FLZ_ORTHO_TENSOR:
+                    # Ritz vectors formed on the tensor cores: orthonormal eigenvectors of A
+                    X = flz.get_eigenvectors_host(s, A.n)
+                    lam = vals[ortho][0]
+                    R = A.to_scipy() @ X - X * lam
+                    assert np.max(np.linalg.norm(R, axis=0)) < 1e-10 * 12.0
+                    assert np.max(np.abs(X.T @ X - np.eye(X.shape[1]))) < 1e-12
             finally:
                 flz.flz_solver_destroy(s)
         t, c, a = vals[flz.FLZ_ORTHO_TENSOR], vals[flz.FLZ_ORTHO_CUDA_CORES], vals[flz.FLZ_ORTHO_AUTO]
