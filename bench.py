@@ -732,7 +732,7 @@ def graph_mode(flz, torch, args):
                      "max_residual": float(res.max()) if res.size else None,
                      "eigenpairs_per_s_at_1e-8": float(np.sum(res <= 1e-8)) / (e0.elapsed_time(e1) / 1e3),
                      "ms_filter": x["ms_filter"], "ms_orth": x["ms_orth"], "ms_check": x["ms_check"],
-                     "lmin": x["lmin"], "lmax": x["lmax"],
+                     "ortho": ["auto", "cuda_cores", "tensor"][x["ortho"]], "lmin": x["lmin"], "lmax": x["lmax"],
                      "max_abs_eig_diff_vs_fp64": (float(np.max(np.abs(vals - ref)))
                                                   if ref is not None and vals.shape == ref.shape and vals.size else None)}
         flz.flz_solver_destroy(s)

@@ -93,10 +93,10 @@ typedef enum flz_recurrence { FLZ_REC_FORWARD = 0, FLZ_REC_CLENSHAW = 1 } flz_re
  *             recombined exactly. The inner products are exact up to the
  *             rounding of W (or H) to 62 fractional bits of its column scale
  *             and a final FP64 rounding, i.e. more accurate than FP64
- *             arithmetic. Block widths 1..4; 16 bytes per basis value of
- *             device memory besides the FP64 basis.
- * AUTO:       TENSOR where it applies (FP64 basis, r <= 4, enough device
- *             memory), else CUDA_CORES. The double-FP32 precision keeps its
+ *             arithmetic. 16 bytes per basis value of device memory
+ *             besides the FP64 basis.
+ * AUTO:       TENSOR where it applies (FP64 basis, enough device memory for
+ *             the digit copy at the basis capacity), else CUDA_CORES. The double-FP32 precision keeps its
  *             own basis and always uses the FP32 pipes. */
 typedef enum flz_ortho { FLZ_ORTHO_AUTO = 0, FLZ_ORTHO_CUDA_CORES = 1, FLZ_ORTHO_TENSOR = 2 } flz_ortho;
 
@@ -280,8 +280,8 @@ flz_status flz_sym_eig(int32_t n, const double* S, double* w, double* Z);
 
 /* Projection C = Q^T W of the n x r block W (device) on a basis Q of nb
  * blocks (device; block b at Q + b n r, each n x r row-major; K = nb r
- * columns); C is K x r row-major (device). `method` is FLZ_ORTHO_CUDA_CORES
- * or FLZ_ORTHO_TENSOR (see flz_ortho; TENSOR needs r <= 4 and |Q| < 1.9, and
+ * columns); C is K x r row-major (device), r <= 16. `method` is
+ * FLZ_ORTHO_CUDA_CORES or FLZ_ORTHO_TENSOR (see flz_ortho; TENSOR needs |Q| < 1.9, and
  * uses Q rounded to the 2^-62 grid, the rounding a solver's basis already
  * has; Q itself is not modified). Synchronous with respect to `stream`;
  * allocates and frees its own scratch. */
@@ -294,7 +294,7 @@ flz_status flz_basis_project(int64_t n, int32_t nb, int32_t r, const double* Q, 
 flz_status flz_basis_orthogonalize(int64_t n, int32_t nb, int32_t r, const double* Q, double* W, double* C,
                                    int32_t method, void* stream);
 /* Layout check of the tensor-core path: one tcgen05.mma (M = 128, N = n in
- * {16, 32}, K = 16, BF16 operands, FP32 accumulator in tensor memory) of a
+ * {16, 32, 64, 128}, K = 16, BF16 operands, FP32 accumulator in tensor memory) of a
  * 128 x 16 A operand and an n x 16 B operand given as shared-memory images
  * (host; a_bytes <= 36864, b_bytes <= 20480, multiples of 16; both K-major
  * unless a_mn_major) and the descriptors' leading and stride byte offsets

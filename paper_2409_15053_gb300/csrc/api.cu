@@ -416,7 +416,7 @@ void check_basis_args(int64_t n, int32_t nb, int32_t r, const double* Q, const d
   if (n < 1 || nb < 1 || r < 1 || r > 16 || !Q || !W || !C) fail(FLZ_ERR_INVALID_ARG, "bad arguments");
   if (method != FLZ_ORTHO_CUDA_CORES && method != FLZ_ORTHO_TENSOR) fail(FLZ_ERR_INVALID_ARG, "bad method");
   if (method == FLZ_ORTHO_TENSOR && !flz::TcBasis::supported(r))
-    fail(FLZ_ERR_INVALID_ARG, "the tensor-core path takes block widths 1..4");
+    fail(FLZ_ERR_INVALID_ARG, "the tensor-core path takes block widths 1..16");
 }
 
 // Digit copy of a caller's basis (the caller's FP64 values stay untouched).
@@ -512,7 +512,7 @@ flz_status flz_solver_create(flz_matrix* A, const flz_params* params, flz_solver
       p.ortho > FLZ_ORTHO_TENSOR)
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.ortho == FLZ_ORTHO_TENSOR && (!flz::TcBasis::supported(p.block_size) || p.precision == FLZ_PREC_DF64))
-    fail(FLZ_ERR_INVALID_ARG, "tensor-core reorthogonalization needs an FP64 basis and block_size <= 4");
+    fail(FLZ_ERR_INVALID_ARG, "tensor-core reorthogonalization needs an FP64 basis (not the double-FP32 precision)");
   if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_DF64) fail(FLZ_ERR_INVALID_ARG, "bad precision");
   flz_solver* s = new flz_solver();
   s->A = A;

@@ -124,7 +124,7 @@ struct TcBasis {
   TcBasis(const TcBasis&) = delete;
   TcBasis& operator=(const TcBasis&) = delete;
   ~TcBasis() { release(); }
-  static bool supported(int r);                       // block widths the kernels take (1..4)
+  static bool supported(int r);                       // block widths the kernels take (1..16)
   static size_t bytes_for(int64_t n, int64_t kcap);   // digit storage for kcap columns
   void release();
   void reserve(int64_t n, int64_t kcap);

@@ -370,7 +370,8 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   if constexpr (std::is_same<BT, double>::value)
     use_tc = p.ortho == FLZ_ORTHO_TENSOR || (p.ortho == FLZ_ORTHO_AUTO && TcBasis::supported(r));
   if (use_tc) {
-    const double budget = 0.6 * (double)free_b + (double)s->tcb.q.count;
+    // the FP64 basis and its digit copy (24 bytes per value) may take 3/4 of the free memory
+    const double budget = 0.75 * (double)free_b + (double)s->tcb.q.count;
     const int64_t tc_cap =
         (int64_t)(budget / (8.0 * (double)n + (double)TcBasis::bytes_for(n, 16) / 16.0));
     if (p.ortho == FLZ_ORTHO_AUTO && tc_cap < kcap)

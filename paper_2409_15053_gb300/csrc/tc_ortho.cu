@@ -41,7 +41,6 @@ constexpr int kChunk = 128;          // rows per staged chunk
 constexpr int kWindowGroups = 16;    // groups (256 columns) per exact update window
 constexpr int kStrip = kChunk / 8 * 128;  // 2048 bytes: one strip of a chunk
 constexpr int kAStage = 16 * kStrip;      // 32 KB: all strips of a group's chunk
-constexpr int kDotStages = 4;
 constexpr int kUpdStages = 4;
 // Shared memory the update kernel reserves past its last stage: its A
 // descriptors reach at most 32 KB past a stage under either reading of the
@@ -90,13 +89,15 @@ __device__ __forceinline__ double small_ll_to_double(long long p) {
 // ---------------------------------------------------------------------------
 // Per-column maxima of an n x r block (as upper words); out pre-zeroed.
 __global__ void colmax_kernel(const double* __restrict__ X, int64_t n, int r, int ld, uint32_t* out) {
-  uint32_t m[4] = {0u, 0u, 0u, 0u};
+  uint32_t m[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) m[j] = 0u;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < 16; ++j)
       if (j < r) m[j] = max(m[j], abs_hiword(X[i * ld + j]));
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < 16; ++j) {
     const uint32_t w = __reduce_max_sync(0xffffffffu, m[j]);
     if ((threadIdx.x & 31) == 0 && j < r && w) atomicMax(out + j, w);
   }
@@ -159,9 +160,13 @@ struct DotArgs {
   int* status;
 };
 
+// stages of the projection's ring: three when the W digits of N = 128 take 128 KB
+__host__ __device__ constexpr int dot_stages(int np) { return np == 128 ? 3 : 4; }
+
 template <int NP>
 __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
   constexpr int GPC = 128 / NP;
+  constexpr int kDotStages = dot_stages(NP);
   constexpr int WSLOT = NP * kRange * 2;  // bytes of one range's W digits
   constexpr uint32_t IDESC = tc::idesc_bf16(128, NP, 0, 0);
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -273,13 +278,6 @@ __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
   } else if (warp == 2 || warp == 3) {
     // ---- W digits for each range ----
     const int t2 = tid - 64;
-    int E[4];
-    double sc[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      E[j] = j < a.r ? scale_exponent(a.wmax[j]) : 0;
-      sc[j] = pow2i(62 - E[j]);
-    }
     for (int li = 0; li < nloc; ++li) {
       const int buf = li & 1;
       if (li >= 2 && !tc::mbar_wait(w_empty + buf, ((li >> 1) - 1) & 1, guard, kErrWaitSlicer)) break;
@@ -288,10 +286,7 @@ __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
       uint8_t* slot = sW + buf * WSLOT;
       for (int task = t2; task < (kRange / 8) * a.r; task += 64) {
         const int o = task / a.r, j = task - o * a.r;
-        double scj = sc[0];
-#pragma unroll
-        for (int jj = 1; jj < 4; ++jj)
-          if (j == jj) scj = sc[jj];
+        const double scj = pow2i(62 - scale_exponent(a.wmax[j]));
         uint32_t pack[kDig][4];
 #pragma unroll
         for (int s = 0; s < kDig; ++s) pack[s][0] = pack[s][1] = pack[s][2] = pack[s][3] = 0u;
@@ -336,11 +331,14 @@ __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
 #pragma unroll
             for (int x = 0; x < 16; ++x) acc[g][x] += exact_int(v[x]);
           } else {
-            uint32_t v[32];
-            tc::tmem_ld32(taddr, v);
-            tc::tmem_ld_wait();
 #pragma unroll
-            for (int x = 0; x < 32; ++x) acc[g][x] += exact_int(v[x]);
+            for (int c = 0; c < NP / 32; ++c) {
+              uint32_t v[32];
+              tc::tmem_ld32(taddr + 32 * c, v);
+              tc::tmem_ld_wait();
+#pragma unroll
+              for (int x = 0; x < 32; ++x) acc[g][32 * c + x] += exact_int(v[x]);
+            }
           }
         }
       }
@@ -380,32 +378,30 @@ __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
 // Reads group G's integer sums (and clears them for the next projection),
 // recombines the 64 digit pairs (diagonal by diagonal, exact until the last
 // few FP64 additions) and writes C[kb, j] for the group's columns kb < K.
+// One thread per (column c of the group, column j of W): 16 r threads.
 template <int NP>
 __global__ void tc_dot_reduce_kernel(unsigned long long* __restrict__ acc, int K, int r, const uint32_t* wmax,
                                      double* C, int ldc) {
-  __shared__ double P[128 * NP];
-  const int G = blockIdx.x;
+  const int G = blockIdx.x, t = threadIdx.x;
+  if (t >= 16 * r) return;
+  const int c = t / r, j = t - c * r, kb = G * 16 + c;
   unsigned long long* src = acc + (size_t)G * 128 * NP;
-  for (int e = threadIdx.x; e < 128 * NP; e += blockDim.x) {
-    P[e] = (double)(long long)src[e];  // |sum| <= (CTAs) 2^30 < 2^53: exact
-    src[e] = 0ull;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < 16 * r; t += blockDim.x) {
-    const int c = t / r, j = t - c * r, kb = G * 16 + c;
-    if (kb >= K) continue;
-    double S[2 * kDig - 1];
+  double S[2 * kDig - 1];
 #pragma unroll
-    for (int d = 0; d < 2 * kDig - 1; ++d) S[d] = 0.0;
+  for (int d = 0; d < 2 * kDig - 1; ++d) S[d] = 0.0;
 #pragma unroll
-    for (int s = 0; s < kDig; ++s)
+  for (int s = 0; s < kDig; ++s)
 #pragma unroll
-      for (int u = 0; u < kDig; ++u) S[s + u] += P[(16 * s + c) * NP + j * 8 + u];  // exact (< 2^45)
-    double v = S[2 * kDig - 2];
+    for (int u = 0; u < kDig; ++u) {
+      unsigned long long* e = src + (16 * s + c) * NP + j * 8 + u;
+      S[s + u] += (double)(long long)*e;  // |sum| <= (CTAs) 2^30: exact, and so are the diagonal sums
+      *e = 0ull;
+    }
+  if (kb >= K) return;
+  double v = S[2 * kDig - 2];
 #pragma unroll
-    for (int d = 2 * kDig - 3; d >= 0; --d) v = v * 0.00390625 + S[d];
-    C[(size_t)kb * ldc + j] = v * pow2i(scale_exponent(wmax[j]) - 12);
-  }
+  for (int d = 2 * kDig - 3; d >= 0; --d) v = v * 0.00390625 + S[d];
+  C[(size_t)kb * ldc + j] = v * pow2i(scale_exponent(wmax[j]) - 12);
 }
 
 // Digits of the coefficient matrix H (K x r, row stride ldc) for the update:
@@ -467,7 +463,10 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(UpdArgs a) {
   constexpr int HB = NP * 32;  // bytes of a group's H digits
   constexpr int STAGE = kAStage + HB;
   constexpr uint32_t IDESC = tc::idesc_bf16(128, NP, 1, 0);
-  constexpr int NCOL = 2 * kDig * NP;
+  // two accumulator sets when they fit the 512 tensor-memory columns, else one
+  constexpr int NBUF = 2 * kDig * NP <= 512 ? 2 : 1;
+  constexpr int NCOL = NBUF * kDig * NP;
+  constexpr int NJ = NP / 8;  // columns of W per launch
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kUpdStages * STAGE + kUpdPad);
   uint64_t* full = bars;
@@ -529,8 +528,8 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(UpdArgs a) {
     int k = 0;
     bool ok = true;
     for (int li = 0; li < nloc && ok; ++li) {
-      const int buf = li & 1;
-      if (li >= 2 && !tc::mbar_wait(acc_empty + buf, ((li >> 1) - 1) & 1, guard, kErrWaitMma)) break;
+      const int buf = li % NBUF;
+      if (li >= NBUF && !tc::mbar_wait(acc_empty + buf, ((li / NBUF) - 1) & 1, guard, kErrWaitMma)) break;
       tc::fence_after_sync();
       for (int G = a.G0; G < a.G1; ++G, ++k) {
         const int stage = k % kUpdStages, u = k / kUpdStages;
@@ -559,27 +558,37 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(UpdArgs a) {
   } else if (warp >= 2) {
     const int q4 = warp & 3;
     const int m = q4 * 32 + lane;
-    double hsc[4];
+    double hsc[NJ];
+    uint32_t wm[NJ];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) hsc[j] = j < a.r ? pow2i(a.hexp[j] - 28) : 0.0;
-    uint32_t wm[4] = {0u, 0u, 0u, 0u};
+    for (int j = 0; j < NJ; ++j) {
+      hsc[j] = j < a.r ? pow2i(a.hexp[j] - 28) : 0.0;
+      wm[j] = 0u;
+    }
     for (int li = 0; li < nloc; ++li) {
-      const int buf = li & 1;
-      if (!__all_sync(0xffffffffu, tc::mbar_wait(acc_full + buf, (li >> 1) & 1, guard, kErrWaitEpilogue))) break;
+      const int buf = li % NBUF;
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(acc_full + buf, (li / NBUF) & 1, guard, kErrWaitEpilogue))) break;
       tc::fence_after_sync();
-      int S[4][9];
+      int S[NJ][9];
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < NJ; ++j)
 #pragma unroll
         for (int d = 0; d < 9; ++d) S[j][d] = 0;
 #pragma unroll
       for (int s = 0; s < kDig; ++s) {
         const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * kDig * NP + s * NP);
         uint32_t v[NP];
-        if constexpr (NP == 16)
+        if constexpr (NP == 16) {
           tc::tmem_ld16(taddr, v);
-        else
-          tc::tmem_ld32(taddr, v);
+        } else {
+#pragma unroll
+          for (int c = 0; c < NP / 32; ++c) {
+            uint32_t h[32];
+            tc::tmem_ld32(taddr + 32 * c, h);
+#pragma unroll
+            for (int x = 0; x < 32; ++x) v[32 * c + x] = h[x];
+          }
+        }
         tc::tmem_ld_wait();
 #pragma unroll
         for (int j = 0; j < NP / 8; ++j)
@@ -610,7 +619,7 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(UpdArgs a) {
     }
     if (a.wmax_out) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < NJ; ++j) {
         const uint32_t w = __reduce_max_sync(0xffffffffu, wm[j]);
         if (lane == 0 && j < a.r && w) atomicMax(a.wmax_out + j, w);
       }
@@ -654,8 +663,9 @@ __global__ void tc_probe_kernel(const uint4* a_img, int a_words, const uint4* b_
     *s_abort = 0;
     tc::fence_mbar_init();
   }
+  const uint32_t ncols = np < 32 ? 32 : np;
   if (warp == 0) {
-    tc::tmem_alloc(s_tmem, 32);
+    tc::tmem_alloc(s_tmem, ncols);
     tc::tmem_relinquish();
   }
   tc::fence_before_sync();
@@ -663,7 +673,7 @@ __global__ void tc_probe_kernel(const uint4* a_img, int a_words, const uint4* b_
   tc::fence_after_sync();
   const uint32_t tmem = *s_tmem;
   if (tid == 0) {
-    const uint32_t idesc = np == 16 ? tc::idesc_bf16(128, 16, a_mn_major, 0) : tc::idesc_bf16(128, 32, a_mn_major, 0);
+    const uint32_t idesc = tc::idesc_bf16(128, np, a_mn_major, 0);
     tc::mma_bf16(tmem, tc::smem_desc(tc::smem_u32(sa), a_lbo, a_sbo), tc::smem_desc(tc::smem_u32(sb), b_lbo, b_sbo),
                  idesc, 0);
     tc::mma_commit(bar);
@@ -672,16 +682,19 @@ __global__ void tc_probe_kernel(const uint4* a_img, int a_words, const uint4* b_
   const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(bar, 0, guard, kErrWaitEpilogue));
   tc::fence_after_sync();
   if (ok) {
-    uint32_t v[32];
-    tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
-    tc::tmem_ld_wait();
-    for (int x = 0; x < np; ++x) out[(warp * 32 + lane) * np + x] = __uint_as_float(v[x]);
+    for (int c = 0; c < (np + 31) / 32; ++c) {
+      uint32_t v[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32 * c, v);
+      tc::tmem_ld_wait();
+      for (int x = 0; x < 32 && 32 * c + x < np; ++x)
+        out[(warp * 32 + lane) * np + 32 * c + x] = __uint_as_float(v[x]);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, 32);
+    tc::tmem_dealloc(tmem, ncols);
   }
 }
 
@@ -701,10 +714,11 @@ void allow_smem(K kernel, size_t bytes) {
 }
 
 constexpr size_t kBarBytes = 256;
-size_t dot_smem(int np) { return (size_t)kDotStages * kAStage + 2 * (size_t)np * kRange * 2 + kBarBytes; }
+size_t dot_smem(int np) { return (size_t)dot_stages(np) * kAStage + 2 * (size_t)np * kRange * 2 + kBarBytes; }
 size_t upd_smem(int np) { return (size_t)kUpdStages * (kAStage + np * 32) + kUpdPad + kBarBytes; }
 
-int padded_np(int r) { return r <= 2 ? 16 : 32; }
+// N of an MMA holding r columns x 8 digits: a multiple of 16 (M = 128)
+int padded_np(int r) { return r <= 2 ? 16 : r <= 4 ? 32 : r <= 8 ? 64 : 128; }
 
 template <int NP>
 void launch_dot(TcBasis& B, int K, const double* W, int r, int ldw, const uint32_t* wmax, double* C, int ldc,
@@ -726,7 +740,7 @@ void launch_dot(TcBasis& B, int K, const double* W, int r, int ldw, const uint32
   DotArgs a{B.q.p, B.n_oct, B.n, Gtot, nR, RS, W, r, ldw, wmax, B.acc.p, B.status.p};
   tc_dot_kernel<NP><<<dim3(RS, GS), 256, dot_smem(NP), st>>>(a);
   FLZ_LAUNCH_CHECK();
-  tc_dot_reduce_kernel<NP><<<Gtot, 256, 0, st>>>(B.acc.p, K, r, wmax, C, ldc);
+  tc_dot_reduce_kernel<NP><<<Gtot, 16 * r, 0, st>>>(B.acc.p, K, r, wmax, C, ldc);
   FLZ_LAUNCH_CHECK();
 }
 
@@ -752,7 +766,7 @@ void launch_update(TcBasis& B, int K, double* W, int r, int ldw, int keep, uint3
 
 }  // namespace
 
-bool TcBasis::supported(int r) { return r >= 1 && r <= 4; }
+bool TcBasis::supported(int r) { return r >= 1 && r <= 16; }
 
 void TcBasis::release() {
   q.release();
@@ -786,8 +800,8 @@ void TcBasis::reserve(int64_t n_, int64_t kcap) {
   q.reserve(bytes);
   // digits outside the written columns and rows must be finite (zero)
   FLZ_CUDA(cudaMemset(q.p, 0, bytes));
-  hs.reserve((size_t)groups_cap * 32 * 16 + 64);
-  acc.reserve((size_t)groups_cap * 128 * 32);  // NP <= 32
+  hs.reserve((size_t)groups_cap * 64 * 16 + 64);  // update N <= 64
+  acc.reserve((size_t)groups_cap * 128 * 128);    // 128 x N sums per group, N <= 128
   FLZ_CUDA(cudaMemset(acc.p, 0, sizeof(unsigned long long) * acc.count));
   hexp.reserve(16);
   wmax.reserve(32);
@@ -807,41 +821,45 @@ void TcBasis::append(double* X, int r, int col0, cudaStream_t st) {
 
 void TcBasis::project(int K, const double* W, int r, int ldw, const uint32_t* wmax_in, double* C, int ldc,
                       cudaStream_t st) {
-  if (padded_np(r) == 16)
-    launch_dot<16>(*this, K, W, r, ldw, wmax_in, C, ldc, st);
-  else
-    launch_dot<32>(*this, K, W, r, ldw, wmax_in, C, ldc, st);
-}
-
-void TcBasis::subtract(int K, const double* C, int ldc, double* W, int r, int ldw, uint32_t* wmax_out,
-                       cudaStream_t st) {
-  const int np = padded_np(r);
-  const int Gtot = (K + 15) / 16;
-  tc_hdigits_kernel<<<1, 256, 0, st>>>(C, ldc, K, r, Gtot, np, hs.p, hexp.p, 1);
-  FLZ_LAUNCH_CHECK();
-  if (np == 16)
-    launch_update<16>(*this, K, W, r, ldw, 1, wmax_out, st);
-  else
-    launch_update<32>(*this, K, W, r, ldw, 1, wmax_out, st);
-}
-
-void TcBasis::multiply(int K, const double* C, int ldc, int s, double* X, int ldx, cudaStream_t st) {
-  const int Gtot = (K + 15) / 16;
-  for (int c0 = 0; c0 < s; c0 += 4) {
-    const int w = std::min(4, s - c0);
-    const int np = padded_np(w);
-    // digits of -C: the first window writes -Q(-C), later windows subtract Q(-C)
-    tc_hdigits_kernel<<<1, 256, 0, st>>>(C + c0, ldc, K, w, Gtot, np, hs.p, hexp.p, -1);
-    FLZ_LAUNCH_CHECK();
-    if (np == 16)
-      launch_update<16>(*this, K, X + c0, w, ldx, 0, nullptr, st);
-    else
-      launch_update<32>(*this, K, X + c0, w, ldx, 0, nullptr, st);
+  switch (padded_np(r)) {
+    case 16: launch_dot<16>(*this, K, W, r, ldw, wmax_in, C, ldc, st); break;
+    case 32: launch_dot<32>(*this, K, W, r, ldw, wmax_in, C, ldc, st); break;
+    case 64: launch_dot<64>(*this, K, W, r, ldw, wmax_in, C, ldc, st); break;
+    default: launch_dot<128>(*this, K, W, r, ldw, wmax_in, C, ldc, st); break;
   }
 }
 
+namespace {
+// W[:, c0:c0+w] op= Q H[:, c0:c0+w] for w <= 8 columns (one digit set of H)
+void update_columns(TcBasis& B, int K, const double* C, int ldc, int w, double* W, int ldw, int keep, int sign,
+                    uint32_t* wmax_out, cudaStream_t st) {
+  const int np = std::min(padded_np(w), 64);
+  const int Gtot = (K + 15) / 16;
+  tc_hdigits_kernel<<<1, 256, 0, st>>>(C, ldc, K, w, Gtot, np, B.hs.p, B.hexp.p, sign);
+  FLZ_LAUNCH_CHECK();
+  switch (np) {
+    case 16: launch_update<16>(B, K, W, w, ldw, keep, wmax_out, st); break;
+    case 32: launch_update<32>(B, K, W, w, ldw, keep, wmax_out, st); break;
+    default: launch_update<64>(B, K, W, w, ldw, keep, wmax_out, st); break;
+  }
+}
+}  // namespace
+
+void TcBasis::subtract(int K, const double* C, int ldc, double* W, int r, int ldw, uint32_t* wmax_out,
+                       cudaStream_t st) {
+  for (int c0 = 0; c0 < r; c0 += 8)  // at most 8 columns (N = 64) per pass over the digits
+    update_columns(*this, K, C + c0, ldc, std::min(8, r - c0), W + c0, ldw, 1, 1,
+                   wmax_out ? wmax_out + c0 : nullptr, st);
+}
+
+void TcBasis::multiply(int K, const double* C, int ldc, int s, double* X, int ldx, cudaStream_t st) {
+  // digits of -C: the first window writes -Q(-C), later windows subtract Q(-C)
+  for (int c0 = 0; c0 < s; c0 += 8)
+    update_columns(*this, K, C + c0, ldc, std::min(8, s - c0), X + c0, ldx, 0, -1, nullptr, st);
+}
+
 void TcBasis::column_max(const double* W, int r, int ldw, uint32_t* out, cudaStream_t st) {
-  FLZ_CUDA(cudaMemsetAsync(out, 0, sizeof(uint32_t) * 4, st));
+  FLZ_CUDA(cudaMemsetAsync(out, 0, sizeof(uint32_t) * 16, st));
   colmax_kernel<<<2 * num_sms(), 256, 0, st>>>(W, n, r, ldw, out);
   FLZ_LAUNCH_CHECK();
 }
@@ -851,7 +869,7 @@ void TcBasis::cgs2(int K, double* W, int r, double* C, double* C2, cudaStream_t 
   uint32_t* m1 = wmax.p + 16;
   column_max(W, r, r, m0, st);
   project(K, W, r, r, m0, C, r, st);
-  FLZ_CUDA(cudaMemsetAsync(m1, 0, sizeof(uint32_t) * 4, st));
+  FLZ_CUDA(cudaMemsetAsync(m1, 0, sizeof(uint32_t) * 16, st));
   subtract(K, C, r, W, r, r, m1, st);
   project(K, W, r, r, m1, C2, r, st);
   subtract(K, C2, r, W, r, r, nullptr, st);
@@ -867,7 +885,7 @@ void TcBasis::check_status() {
 
 int tc_probe(const uint16_t* a_img, size_t a_bytes, const uint16_t* b_img, size_t b_bytes, int np, int a_mn_major,
              uint32_t a_lbo, uint32_t a_sbo, uint32_t b_lbo, uint32_t b_sbo, float* out_host) {
-  if (np != 16 && np != 32) fail(FLZ_ERR_INVALID_ARG, "np must be 16 or 32");
+  if (np != 16 && np != 32 && np != 64 && np != 128) fail(FLZ_ERR_INVALID_ARG, "np must be 16, 32, 64 or 128");
   if (a_bytes % 16 || b_bytes % 16 || a_bytes > (size_t)kProbeA || b_bytes > (size_t)kProbeB)
     fail(FLZ_ERR_INVALID_ARG, "images must be multiples of 16 bytes, at most %d and %d bytes", kProbeA, kProbeB);
   for (uint32_t x : {a_lbo, a_sbo, b_lbo, b_sbo})

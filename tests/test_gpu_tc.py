@@ -98,6 +98,18 @@ def test_mma_layout_of_the_update(np_):
         pytest.fail(f"max diff {np.max(np.abs(D - want))}; exchanged A fields match: {np.array_equal(Ds, want)}")
 
 
+@pytest.mark.parametrize("np_", [64, 128])
+def test_mma_layout_with_wide_n(np_):
+    # N = 64 and 128 (blocks of 5..16 columns): more column blocks along N
+    rng = np.random.default_rng(200 + np_)
+    A = rng.integers(-9, 10, size=(128, 16)).astype(np.float32)
+    B = rng.integers(-9, 10, size=(np_, 16)).astype(np.float32)
+    D = probe(A, B, 0, 128, 2048, 128, 256, 32768, (np_ // 8) * 256)
+    assert np.array_equal(D, A @ B.T)
+    D = probe(A, B, 1, 2048, 128, 128, 256, 4096, (np_ // 8) * 256)
+    assert np.array_equal(D, A @ B.T)
+
+
 def test_mma_holds_exact_integer_sums():
     # digits up to the bound the kernels use: products up to 2^14, sums of 16
     A = np.full((128, 16), -128.0, dtype=np.float32)
@@ -132,11 +144,12 @@ def exact_projection(Q, W):
     return out
 
 
-@pytest.mark.parametrize("n,nb,r", [(4000, 6, 4), (2777, 13, 3), (1000, 9, 2), (513, 20, 1), (3000, 75, 4)])
+@pytest.mark.parametrize("n,nb,r", [(4000, 6, 4), (2777, 13, 3), (1000, 9, 2), (513, 20, 1), (3000, 75, 4),
+                                    (3000, 5, 8), (1500, 7, 6), (2000, 3, 16), (700, 2, 13)])
 def test_projection_is_exact_up_to_the_final_rounding(n, nb, r):
     Q, blocks = orthonormal_blocks(n, nb, r, n + nb)
     rng = np.random.default_rng(7)
-    W = rng.standard_normal((n, r)) * np.array([1.0, 1e-3, 37.0, 2.0**-40])[:r]
+    W = rng.standard_normal((n, r)) * np.resize(np.array([1.0, 1e-3, 37.0, 2.0**-40]), r)
     Qd = torch.from_numpy(blocks).cuda()
     Wd = torch.from_numpy(W).cuda()
     C = torch.zeros(nb * r, r, dtype=torch.float64, device="cuda")
@@ -152,7 +165,8 @@ def test_projection_is_exact_up_to_the_final_rounding(n, nb, r):
     assert err_tc <= max(err_64, 2.0**-52)
 
 
-@pytest.mark.parametrize("n,nb,r", [(4000, 6, 4), (2777, 13, 3), (3000, 75, 4), (300, 1, 2), (8, 1, 1)])
+@pytest.mark.parametrize("n,nb,r", [(4000, 6, 4), (2777, 13, 3), (3000, 75, 4), (300, 1, 2), (8, 1, 1),
+                                    (3000, 20, 8), (2000, 20, 16), (1000, 9, 11)])
 def test_orthogonalize_matches_fp64_and_leaves_w_orthogonal(n, nb, r):
     Q, blocks = orthonormal_blocks(n, nb, r, 3 * n + nb)
     rng = np.random.default_rng(11)
@@ -240,14 +254,37 @@ def test_solver_on_the_tensor_cores_matches_the_fp64_path():
         flz.flz_matrix_destroy(h)
 
 
-def test_block_width_above_four_falls_back_under_auto():
+def test_wide_blocks_and_double_fp32_paths():
+    # r = 8 and 16 take the tensor cores under AUTO and match the CUDA cores;
+    # the double-FP32 precision keeps its own basis on the FP32 pipes
     from synth import laplacian_2d
-    A = laplacian_2d(40, 40)
+    A = laplacian_2d(60, 60)
     h = flz.flz_matrix_create_csr(A.n, A.nnz, A.rowptr, A.col, A.val)
     try:
+        for r in (8, 16):
+            out = {}
+            for ortho in (flz.FLZ_ORTHO_AUTO, flz.FLZ_ORTHO_CUDA_CORES):
+                p = flz.flz_params_default()
+                p.block_size = r
+                p.degree = 40
+                p.ortho = ortho
+                s = flz.flz_solver_create(h, p)
+                try:
+                    flz.flz_solver_set_interval(s, 0.0, 0.3)
+                    assert flz.flz_solve(s) == flz.FLZ_OK
+                    out[ortho] = (flz.flz_get_eigenvalues(s), flz.flz_get_stats(s)["ortho"],
+                                  flz.flz_get_residuals(s))
+                finally:
+                    flz.flz_solver_destroy(s)
+            assert out[flz.FLZ_ORTHO_AUTO][1] == flz.FLZ_ORTHO_TENSOR
+            assert out[flz.FLZ_ORTHO_CUDA_CORES][1] == flz.FLZ_ORTHO_CUDA_CORES
+            a, c = out[flz.FLZ_ORTHO_AUTO][0], out[flz.FLZ_ORTHO_CUDA_CORES][0]
+            assert a.shape == c.shape and np.max(np.abs(a - c)) < 1e-12
+            assert np.max(out[flz.FLZ_ORTHO_AUTO][2]) < 1e-10
         p = flz.flz_params_default()
-        p.block_size = 8
+        p.block_size = 4
         p.degree = 40
+        p.precision = flz.FLZ_PREC_DF64
         s = flz.flz_solver_create(h, p)
         try:
             flz.flz_solver_set_interval(s, 0.0, 0.3)
