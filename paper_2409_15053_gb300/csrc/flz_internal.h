@@ -112,7 +112,8 @@ struct DevBuf {
 // the FP64 and digit copies hold the same numbers.
 struct TcBasis {
   DevBuf<uint8_t> q;        // digit strips, zero outside the written columns and rows
-  DevBuf<unsigned long long> acc;  // projection sums per group (128 x 32 each), zero between projections
+  DevBuf<unsigned long long> acc;  // projection sums per group (128 x N each), zero between projections
+  DevBuf<uint8_t> wd;       // digits of the block being projected (n_pad x N x 2 bytes)
   DevBuf<uint16_t> hs;      // digits of the coefficient matrix of an update
   DevBuf<int> hexp;         // its column scale exponents
   DevBuf<uint32_t> wmax;    // column maxima of W (two sets of 16)

@@ -64,18 +64,20 @@ __device__ __forceinline__ int scale_exponent(uint32_t hi) {
   const int E = (int)((hi >> 20) & 0x7FF) - 1022;
   return min(max(E, -960), 1000);
 }
-// balanced base-256 digits of v, most significant first
-__device__ __forceinline__ void digits8(long long v, int (&d)[kDig]) {
+// The balanced base-256 digits of v (most significant first, d_1..d_7 in
+// [-128, 127]) as BF16 bit patterns, on full-rate integer and FP32 pipes:
+// adding 128 to every base-256 position turns the balanced digits into the
+// bytes of one 64-bit sum (no carries: each d_s + 128 is in [0, 255] for
+// |v| < 1.9 2^62); d = byte - 128 becomes an exact FP32 through the
+// 1.5 * 2^23 offset, whose upper 16 bits are its BF16 (d has at most 8
+// significant bits).
+__device__ __forceinline__ void digit_bits(long long v, uint32_t (&b)[kDig]) {
+  const unsigned long long u = (unsigned long long)v + 0x8080808080808080ull;
 #pragma unroll
-  for (int s = kDig - 1; s >= 1; --s) {
-    const int lo = (int)((v & 0xFF) ^ 0x80) - 0x80;
-    d[s] = lo;
-    v = (v - lo) >> 8;
+  for (int s = 0; s < kDig; ++s) {
+    const int d = (int)((u >> (8 * (kDig - 1 - s))) & 0xFFu) - 128;
+    b[s] = __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f) >> 16;
   }
-  d[0] = (int)v;
-}
-__device__ __forceinline__ uint32_t bf16_bits(int d) {  // exact for |d| <= 256
-  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)d));
 }
 // an FP32 accumulator value that is an integer of magnitude <= 2^22, as int
 __device__ __forceinline__ int exact_int(uint32_t bits) {
@@ -125,10 +127,10 @@ __global__ void basis_digits_kernel(double* __restrict__ X, int64_t n, int r, in
       v = __double2ll_rn(x * 4611686018427387904.0);  // 2^62
       X[i * r + j] = __ll2double_rn(v) * 2.168404344971009e-19;  // 2^-62, exact
     }
-    int d[kDig];
-    digits8(v, d);
+    uint32_t bits[kDig];
+    digit_bits(v, bits);
 #pragma unroll
-    for (int s = 0; s < kDig; ++s) pack[s][k >> 1] |= bf16_bits(d[s]) << (16 * (k & 1));
+    for (int s = 0; s < kDig; ++s) pack[s][k >> 1] |= bits[s] << (16 * (k & 1));
   }
 #pragma unroll
   for (int s = 0; s < kDig; ++s) {
@@ -138,24 +140,58 @@ __global__ void basis_digits_kernel(double* __restrict__ X, int64_t n, int r, in
 }
 
 // ---------------------------------------------------------------------------
+// Digits of W for the projection, one image per 256-row range exactly as the
+// projection stages it in shared memory: the K-major B operand N = NP (column
+// j of W, digit t) x K = 256 rows as core matrices (j, row octet o) of 8
+// digits x 8 rows: byte rr WSLOT + ((j 32 + o) 8 + t) 16 + (i % 8) 2, WSLOT =
+// NP 512. Columns j >= r are zero. One thread per (row octet, column block).
+__global__ void w_digits_kernel(const double* __restrict__ W, int64_t n, int r, int ldw, const uint32_t* wmax,
+                                int np, int64_t n_oct, uint8_t* __restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int nj = np / 8;
+  if (t >= n_oct * nj) return;
+  const int j = (int)(t % nj);
+  const int64_t og = t / nj, rr = og / (kRange / 8);
+  const int o = (int)(og % (kRange / 8));
+  uint32_t pack[kDig][4];
+#pragma unroll
+  for (int s = 0; s < kDig; ++s) pack[s][0] = pack[s][1] = pack[s][2] = pack[s][3] = 0u;
+  if (j < r) {
+    const double sc = pow2i(62 - scale_exponent(wmax[j]));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int64_t i = og * 8 + k;
+      const long long v = i < n ? __double2ll_rn(W[i * ldw + j] * sc) : 0;
+      uint32_t b[kDig];
+      digit_bits(v, b);
+#pragma unroll
+      for (int s = 0; s < kDig; ++s) pack[s][k >> 1] |= b[s] << (16 * (k & 1));
+    }
+  }
+  uint8_t* dst = out + (size_t)rr * np * kRange * 2 + (size_t)((j * (kRange / 8) + o) * 8) * 16;
+#pragma unroll
+  for (int s = 0; s < kDig; ++s)
+    *reinterpret_cast<uint4*>(dst + s * 16) = make_uint4(pack[s][0], pack[s][1], pack[s][2], pack[s][3]);
+}
+
 // Projection C = Q^T W on the tensor cores.
 //
-// CTA (x, y): group set y (GPC groups of 16 columns), row ranges x, x + RS,
-// ... of 256 rows. Per range and 128-row chunk and group, one stage of 32 KB
-// (the group's 16 strips); per range the W digits (NP x 256, built by two
-// warps from FP64 W). MMA: M = 128 (digit s, column c), N = NP (column j of
-// W, digit t), K = 16 rows, 16 instructions per range and group into a
-// double-buffered tensor-memory accumulator; the epilogue warps add each
-// drained range (exact integers <= 2^22) into int32 registers (<= 256 ranges
-// per CTA, so <= 2^30) and add those once per CTA into 64-bit integer
-// accumulators in global memory (reductions without a return value).
+// CTA (x, y): group set x (GPC groups of 16 columns), row ranges y, y + RS,
+// ... of 256 rows; the group sets of one range split run side by side, so
+// the W digits of a range come from HBM once and from L2 for the others. Per
+// range, one bulk copy of its W digits (NP x 256); per 128-row chunk and
+// group, one stage of 32 KB (the group's 16 strips). MMA: M = 128 (digit s,
+// column c), N = NP (column j of W, digit t), K = 16 rows, 16 instructions
+// per range and group into a double-buffered tensor-memory accumulator. The
+// epilogue warps add each drained range (exact integers <= 2^22) into int32
+// registers (<= 256 ranges per CTA, so <= 2^30) and add those once per CTA
+// into 64-bit integer accumulators in global memory (reductions without a
+// return value).
 struct DotArgs {
   const uint8_t* q;
-  int64_t n_oct, n;
+  const uint8_t* wd;  // W digits, one NP x 256 image per range
+  int64_t n_oct;
   int Gtot, nR, RS;
-  const double* W;
-  int r, ldw;
-  const uint32_t* wmax;
   unsigned long long* acc;  // Gtot x 128 x NP integer sums, zero on entry
   int* status;
 };
@@ -164,7 +200,7 @@ struct DotArgs {
 __host__ __device__ constexpr int dot_stages(int np) { return np == 128 ? 3 : 4; }
 
 template <int NP>
-__global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
+__global__ void __launch_bounds__(192, 1) tc_dot_kernel(DotArgs a) {
   constexpr int GPC = 128 / NP;
   constexpr int kDotStages = dot_stages(NP);
   constexpr int WSLOT = NP * kRange * 2;  // bytes of one range's W digits
@@ -184,11 +220,13 @@ __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
   int* s_abort = reinterpret_cast<int*>(s_tmem + 1);
   int* s_issued = s_abort + 1;
   int* s_consumed = s_abort + 2;
+  int* s_wissued = s_abort + 3;
+  int* s_wconsumed = s_abort + 4;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int gs = blockIdx.y;
+  const int gs = blockIdx.x, split = blockIdx.y;
   const int gcount = min(GPC, a.Gtot - gs * GPC);
-  const int nloc = blockIdx.x < a.nR ? (a.nR - 1 - blockIdx.x) / a.RS + 1 : 0;
+  const int nloc = split < a.nR ? (a.nR - 1 - split) / a.RS + 1 : 0;
   const tc::Guard guard{s_abort, a.status};
 
   if (tid == 0) {
@@ -197,20 +235,16 @@ __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
       tc::mbar_init(a_empty + i, 1);
     }
     for (int i = 0; i < 2; ++i) {
-      tc::mbar_init(w_full + i, 64);
+      tc::mbar_init(w_full + i, 1);
       tc::mbar_init(w_empty + i, 1);
       tc::mbar_init(acc_full + i, 1);
       tc::mbar_init(acc_empty + i, 128);
     }
     tc::mbar_init(fin, 1);
     *s_abort = 0;
-    *s_issued = 0;
-    *s_consumed = 0;
+    *s_issued = *s_consumed = *s_wissued = *s_wconsumed = 0;
     tc::fence_mbar_init();
   }
-  // zero the W slots once: the padding columns (j >= r) stay zero
-  for (int i = tid; i < 2 * WSLOT / 16; i += blockDim.x) reinterpret_cast<uint4*>(sW)[i] = make_uint4(0, 0, 0, 0);
-  tc::fence_proxy_async_smem();
   if (warp == 0) {
     tc::tmem_alloc(s_tmem, 2 * GPC * NP);
     tc::tmem_relinquish();
@@ -221,10 +255,15 @@ __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
   const uint32_t tmem = *s_tmem;
 
   if (warp == 0 && lane == 0) {
-    // ---- producer: bulk copies of the digit strips ----
-    int k = 0;
-    for (int li = 0; li < nloc && !*s_abort; ++li) {
-      const int64_t rr = blockIdx.x + (int64_t)li * a.RS;
+    // ---- producer: bulk copies of the W digits and the basis digit strips ----
+    int k = 0, li = 0;
+    for (; li < nloc && !*s_abort; ++li) {
+      const int64_t rr = split + (int64_t)li * a.RS;
+      const int wslot = li & 1;
+      if (li >= 2 && !tc::mbar_wait(w_empty + wslot, ((li >> 1) - 1) & 1, guard, kErrWaitProducer)) break;
+      tc::mbar_expect_tx(w_full + wslot, WSLOT);
+      tc::bulk_g2s(sW + wslot * WSLOT, a.wd + (size_t)rr * WSLOT, WSLOT, w_full + wslot);
+      *s_wissued = li + 1;
       for (int h = 0; h < 2; ++h)
         for (int g = 0; g < gcount; ++g, ++k) {
           const int stage = k % kDotStages, u = k / kDotStages;
@@ -235,10 +274,10 @@ __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
           for (int mg = 0; mg < 16; ++mg)
             tc::bulk_g2s(sA + stage * kAStage + mg * kStrip, a.q + ((size_t)(G * 16 + mg) * a.n_oct + o0) * 128,
                          kStrip, a_full + stage);
+          *s_issued = k + 1;
         }
     }
-  produced:
-    *s_issued = k;
+  produced:;
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
     int k = 0;
@@ -246,6 +285,7 @@ __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
       const int buf = li & 1;
       if (li >= 2 && !tc::mbar_wait(acc_empty + buf, ((li >> 1) - 1) & 1, guard, kErrWaitMma)) break;
       if (!tc::mbar_wait(w_full + buf, (li >> 1) & 1, guard, kErrWaitMma)) break;
+      *s_wconsumed = li + 1;
       tc::fence_after_sync();
       const uint32_t wbase = tc::smem_u32(sW + buf * WSLOT);
       bool ok = true;
@@ -256,6 +296,7 @@ __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
             ok = false;
             break;
           }
+          *s_consumed = k + 1;
           tc::fence_after_sync();
           const uint32_t abase = tc::smem_u32(sA + stage * kAStage);
           const uint32_t d = tmem + (uint32_t)(buf * GPC * NP + g * NP);
@@ -273,41 +314,8 @@ __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
       tc::mma_commit(w_empty + buf);
       tc::mma_commit(acc_full + buf);
     }
-    *s_consumed = k;
     tc::mma_commit(fin);
-  } else if (warp == 2 || warp == 3) {
-    // ---- W digits for each range ----
-    const int t2 = tid - 64;
-    for (int li = 0; li < nloc; ++li) {
-      const int buf = li & 1;
-      if (li >= 2 && !tc::mbar_wait(w_empty + buf, ((li >> 1) - 1) & 1, guard, kErrWaitSlicer)) break;
-      if (*s_abort) break;
-      const int64_t rr = blockIdx.x + (int64_t)li * a.RS;
-      uint8_t* slot = sW + buf * WSLOT;
-      for (int task = t2; task < (kRange / 8) * a.r; task += 64) {
-        const int o = task / a.r, j = task - o * a.r;
-        const double scj = pow2i(62 - scale_exponent(a.wmax[j]));
-        uint32_t pack[kDig][4];
-#pragma unroll
-        for (int s = 0; s < kDig; ++s) pack[s][0] = pack[s][1] = pack[s][2] = pack[s][3] = 0u;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int64_t i = rr * kRange + o * 8 + k;
-          const long long v = i < a.n ? __double2ll_rn(a.W[i * a.ldw + j] * scj) : 0;
-          int d[kDig];
-          digits8(v, d);
-#pragma unroll
-          for (int s = 0; s < kDig; ++s) pack[s][k >> 1] |= bf16_bits(d[s]) << (16 * (k & 1));
-        }
-#pragma unroll
-        for (int s = 0; s < kDig; ++s)
-          *reinterpret_cast<uint4*>(slot + ((j * (kRange / 8) + o) * 8 + s) * 16) =
-              make_uint4(pack[s][0], pack[s][1], pack[s][2], pack[s][3]);
-      }
-      tc::fence_proxy_async_smem();
-      tc::mbar_arrive(w_full + buf);
-    }
-  } else if (warp >= 4) {
+  } else if (warp >= 2) {
     // ---- epilogue: drain each range into int32 sums ----
     const int q4 = warp & 3;
     int acc[GPC][NP];
@@ -366,6 +374,8 @@ __global__ void __launch_bounds__(256, 1) tc_dot_kernel(DotArgs a) {
     tc::mbar_wait_drain(fin, 0);  // every MMA this CTA issued has completed
     for (int k = *s_consumed; k < *s_issued; ++k)  // copies issued but never consumed (abort only)
       tc::mbar_wait_drain(a_full + (k % kDotStages), (k / kDotStages) & 1);
+    for (int li = *s_wconsumed; li < *s_wissued; ++li)
+      tc::mbar_wait_drain(w_full + (li & 1), (li >> 1) & 1);
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -425,11 +435,11 @@ __global__ void tc_hdigits_kernel(const double* __restrict__ C, int ldc, int K, 
     const int j = rem / 16, c = rem - j * 16, kb = G * 16 + c;
     long long v = 0;
     if (j < r && kb < K) v = sign * __double2ll_rn(C[(size_t)kb * ldc + j] * pow2i(62 - scale_exponent(mx[j])));
-    int d[kDig];
-    digits8(v, d);
+    uint32_t bits[kDig];
+    digit_bits(v, bits);
 #pragma unroll
     for (int t = 0; t < kDig; ++t)
-      hs[(size_t)G * NP * 16 + ((j * 2 + (c >> 3)) * 8 + t) * 8 + (c & 7)] = (uint16_t)bf16_bits(d[t]);
+      hs[(size_t)G * NP * 16 + ((j * 2 + (c >> 3)) * 8 + t) * 8 + (c & 7)] = (uint16_t)bits[t];
   }
   if (threadIdx.x < r) hexp[threadIdx.x] = scale_exponent(mx[threadIdx.x]);
 }
@@ -732,13 +742,18 @@ void launch_dot(TcBasis& B, int K, const double* W, int r, int ldw, const uint32
   const int waves = std::max(1, (minRS * GS + sms - 1) / sms);
   int RS = std::max(minRS, (waves * sms) / GS);
   RS = std::max(1, std::min(RS, nR));
+  const size_t wbytes = (size_t)B.n_pad * NP * 2;
+  if (B.wd.count < wbytes) B.wd.reserve(wbytes);
   static bool attr = false;
   if (!attr) {
     allow_smem(tc_dot_kernel<NP>, dot_smem(NP));
     attr = true;
   }
-  DotArgs a{B.q.p, B.n_oct, B.n, Gtot, nR, RS, W, r, ldw, wmax, B.acc.p, B.status.p};
-  tc_dot_kernel<NP><<<dim3(RS, GS), 256, dot_smem(NP), st>>>(a);
+  const int64_t tasks = B.n_oct * (NP / 8);
+  w_digits_kernel<<<(unsigned)((tasks + 255) / 256), 256, 0, st>>>(W, B.n, r, ldw, wmax, NP, B.n_oct, B.wd.p);
+  FLZ_LAUNCH_CHECK();
+  DotArgs a{B.q.p, B.wd.p, B.n_oct, Gtot, nR, RS, B.acc.p, B.status.p};
+  tc_dot_kernel<NP><<<dim3(GS, RS), 192, dot_smem(NP), st>>>(a);
   FLZ_LAUNCH_CHECK();
   tc_dot_reduce_kernel<NP><<<Gtot, 16 * r, 0, st>>>(B.acc.p, K, r, wmax, C, ldc);
   FLZ_LAUNCH_CHECK();
@@ -771,6 +786,7 @@ bool TcBasis::supported(int r) { return r >= 1 && r <= 16; }
 void TcBasis::release() {
   q.release();
   acc.release();
+  wd.release();
   hs.release();
   hexp.release();
   wmax.release();
