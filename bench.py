@@ -711,7 +711,9 @@ def graph_mode(flz, torch, args):
         p.precision = prec
         p.tol = tol
         p.check_every = 10
-        p.max_basis = 2000
+        # 110 block steps of 16: room for the ~100 the solve takes, and for the
+        # basis's digit copy (24 bytes per value with the FP64 basis) in HBM
+        p.max_basis = 1760
         s = flz.flz_solver_create(h, p)
         flz.flz_solver_set_interval(s, alpha, 1e9)
         flz.flz_solve(s, stream)
