@@ -18,6 +18,9 @@ scipy FP64, following the paper's steps in its order and notation:
   test (Sections 2.3 and 3.2.2).
 - ``dense``: the result by definition for small matrices (all eigenpairs of
   A inside [alpha, beta]) and a Sylvester-inertia eigenvalue count.
+- ``reorth``: the inner products and updates of the full reorthogonalization
+  (Section 3.2.2) evaluated exactly in integer arithmetic, on the fixed-point
+  input rounding the tensor-core path uses.
 
 Library primitives used as single steps: scipy sparse matrix products,
 numpy matrix products, ``numpy.linalg.qr`` (Householder QR) and
@@ -28,4 +31,4 @@ paper prints (Table 2 filter degrees), closed forms (Chebyshev identities,
 Laplacian spectra), brute force on tiny inputs and library routines.
 """
 
-from . import chebyshev, dense, lanczos  # noqa: F401
+from . import chebyshev, dense, lanczos, reorth  # noqa: F401

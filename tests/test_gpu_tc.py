@@ -5,19 +5,19 @@ The tensor-core path splits the basis (rounded to the 2^-62 grid) and W
 (rounded to 62 fractional bits of its column scale) into eight base-256
 digits and forms every digit product exactly, so its projections are the
 exact inner products of those rounded values up to one final FP64 rounding.
-The references here are Python integers (exact) and the FP64 CUDA-core path.
+The references are the oracle's exact products (oracle/reorth.py, Python
+integers) and the FP64 CUDA-core path.
 
 The first tests check the shared-memory descriptor layouts of one tcgen05
 MMA on small integer tiles; they run first so that a layout mismatch stops
 the run before the projection kernels (which rely on the same layouts).
 """
 
-from fractions import Fraction
-
 import numpy as np
 import pytest
 
 import paper_2409_15053_gb300 as flz
+from oracle import reorth
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -124,24 +124,9 @@ def orthonormal_blocks(n, nb, r, seed):
     rng = np.random.default_rng(seed)
     Q, _ = np.linalg.qr(rng.standard_normal((n, nb * r)))
     # the basis lives on the 2^-62 grid (what the solver's basis holds)
-    Q = np.rint(Q * 2.0**62) * 2.0**-62
+    Q = reorth.grid_round(Q)
     blocks = np.ascontiguousarray(Q.reshape(n, nb, r).transpose(1, 0, 2))  # nb x n x r
     return Q, blocks
-
-
-def exact_projection(Q, W):
-    """Q^T W̃ exactly, W̃ = W rounded to 62 fractional bits of each column's scale."""
-    K, r = Q.shape[1], W.shape[1]
-    vq = np.rint(Q * 2.0**62).astype(np.int64).astype(object)
-    out = np.zeros((K, r))
-    for j in range(r):
-        m = np.max(np.abs(W[:, j]))
-        E = int(np.frexp(m)[1]) if m > 0 else 0  # m < 2^E
-        vw = np.rint(W[:, j] * 2.0**(62 - E)).astype(np.int64).astype(object)
-        col = vq.T.dot(vw)  # Python integers: exact
-        for k in range(K):
-            out[k, j] = float(Fraction(int(col[k])) * Fraction(2) ** (E - 124))
-    return out
 
 
 @pytest.mark.parametrize("n,nb,r", [(4000, 6, 4), (2777, 13, 3), (1000, 9, 2), (513, 20, 1), (3000, 75, 4),
@@ -156,7 +141,7 @@ def test_projection_is_exact_up_to_the_final_rounding(n, nb, r):
     C64 = torch.zeros_like(C)
     flz.flz_basis_project(n, nb, r, Qd, Wd, C, flz.FLZ_ORTHO_TENSOR)
     flz.flz_basis_project(n, nb, r, Qd, Wd, C64, flz.FLZ_ORTHO_CUDA_CORES)
-    ref = exact_projection(Q, W)
+    ref = reorth.exact_projection(Q, W)
     scale = np.linalg.norm(Q, axis=0)[:, None] * np.linalg.norm(W, axis=0)[None, :]
     err_tc = np.max(np.abs(C.cpu().numpy() - ref) / scale)
     err_64 = np.max(np.abs(C64.cpu().numpy() - ref) / scale)
