@@ -88,6 +88,44 @@ def test_invalid_arguments_are_rejected_without_a_gpu():
     assert e.value.status == flz.FLZ_ERR_CAPACITY
 
 
+def test_reorthogonalization_entry_points_reject_bad_arguments_without_a_gpu():
+    # argument checks run before any device call
+    assert flz.flz_params_default().ortho == flz.FLZ_ORTHO_AUTO
+    fake = 16  # never dereferenced: every call below fails its checks first
+    cases = [
+        dict(n=100, nb=2, r=17, method=flz.FLZ_ORTHO_TENSOR),    # block wider than 16
+        dict(n=100, nb=2, r=4, method=7),                        # unknown method
+        dict(n=100, nb=2, r=4, method=flz.FLZ_ORTHO_AUTO),       # AUTO is a solver setting only
+        dict(n=0, nb=2, r=4, method=flz.FLZ_ORTHO_TENSOR),       # empty basis
+        dict(n=100, nb=0, r=4, method=flz.FLZ_ORTHO_CUDA_CORES),
+    ]
+    for c in cases:
+        for fn in (flz.flz_basis_project, flz.flz_basis_orthogonalize):
+            with pytest.raises(flz.FlzError) as e:
+                fn(c["n"], c["nb"], c["r"], fake, fake, fake, c["method"])
+            assert e.value.status == flz.FLZ_ERR_INVALID_ARG
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_basis_project(100, 2, 4, None, fake, fake, flz.FLZ_ORTHO_TENSOR)
+    assert e.value.status == flz.FLZ_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("np_,a_bytes,b_bytes,strides", [
+    (24, 4096, 1024, (128, 2048, 128, 256)),       # N not one of 16, 32, 64, 128
+    (32, 4008, 1024, (128, 2048, 128, 256)),       # image not a multiple of 16 bytes
+    (32, 40960, 1024, (128, 2048, 128, 256)),      # A image larger than its 36 KB region
+    (32, 4096, 1024, (128, 2056, 128, 256)),       # stride not a multiple of 16
+    (32, 4096, 1024, (2048, 4096, 128, 256)),      # A reach past 36 KB under one reading
+    (128, 4096, 4096, (128, 2048, 128, 4096)),     # B reach past 20 KB
+])
+def test_mma_probe_rejects_out_of_range_layouts_without_a_gpu(np_, a_bytes, b_bytes, strides):
+    a = np.zeros(a_bytes // 2 + (a_bytes % 2), dtype=np.uint16)
+    b = np.zeros(b_bytes // 2, dtype=np.uint16)
+    L = flz.lib()
+    d = np.zeros((128, max(np_, 16)), dtype=np.float32)
+    st = L.flz_tc_mma_probe(flz._ptr(a), a_bytes, flz._ptr(b), b_bytes, np_, 0, *strides, flz._ptr(d))
+    assert st == flz.FLZ_ERR_INVALID_ARG, flz.flz_last_error()
+
+
 def _random_band(K, b, seed, scale=1.0):
     rng = np.random.default_rng(seed)
     T = np.zeros((K, K))
