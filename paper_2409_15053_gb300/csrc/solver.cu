@@ -560,6 +560,10 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
     if (converged || last) break;
   }
   FLZ_CUDA(cudaStreamSynchronize(st));
+  if (E.tcb) {  // the last check's Ritz vectors ran after the last step's status read
+    FLZ_CUDA(cudaMemcpy(E.tcb->status_host, E.tcb->status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    E.tcb->check_status();
+  }
 
   // sort ascending
   std::vector<int> perm(found);

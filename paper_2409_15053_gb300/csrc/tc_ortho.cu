@@ -895,6 +895,9 @@ void TcBasis::cgs2(int K, double* W, int r, double* C, double* C2, cudaStream_t 
 void TcBasis::check_status() {
   if (status_host && *status_host) {
     const int code = *status_host;
+    // reported once: the next call starts from a clear status
+    *status_host = 0;
+    cudaMemset(status.p, 0, sizeof(int));
     fail(FLZ_ERR_TIMEOUT, "tensor-core reorthogonalization: a wait expired (role %d)", code);
   }
 }
