@@ -77,3 +77,19 @@ def test_parsec_like_hamiltonian_shape():
     assert A.n == int(np.sum(X * X + Y * Y + Z * Z <= 144))
     # the kinetic stencil alone gives 1 + 36 entries per interior row; the non-local blocks add more
     assert A.nnz / A.n > 30
+
+
+def test_powerlaw_graph_zero_mode_is_simple_with_constant_eigenvector():
+    # the ring keeps the graph connected: 0 is a simple eigenvalue of L = D - W
+    # with eigenvector 1/sqrt(n); everything else is positive (L is PSD)
+    from oracle import dense
+    from synth import powerlaw_graph_laplacian
+    n = 600
+    L = powerlaw_graph_laplacian(n, seed=5).to_scipy().toarray()
+    assert np.allclose(L, L.T)
+    assert np.max(np.abs(L.sum(axis=1))) < 1e-12  # rows of a Laplacian sum to zero
+    w, V = dense.eigenpairs_in_interval(L, -1.0, 1e-9)
+    assert w.shape == (1,) and abs(w[0]) < 1e-10
+    assert np.max(np.abs(np.abs(V[:, 0]) - 1.0 / np.sqrt(n))) < 1e-10
+    w_all = np.linalg.eigvalsh(L)
+    assert w_all[1] > 1e-6 and w_all[0] > -1e-10
