@@ -4,11 +4,12 @@
 // Number format. Every basis value x (|x| <= 1 in an orthonormal basis) is
 // rounded to the 64-bit fixed-point integer v = round(x 2^62) and split into
 // eight balanced base-256 digits, v = sum_s d_s 256^(7-s), d_1..d_7 in
-// [-128, 127] and |d_0| <= 66. Each digit is an integer that BF16 holds
-// exactly. The FP64 basis itself is replaced by v 2^-62 (exact in FP64), so
-// the two copies are the same numbers. A block W (or a coefficient matrix H)
-// is split the same way after scaling each column by 2^(62-E), E the
-// smallest power of two above the column's largest magnitude.
+// [-128, 127] and |d_0| <= 66 (<= 123 for any |x| < 1.9). Each digit is an
+// integer that BF16 holds exactly. The FP64 basis itself is replaced by
+// v 2^-62 (exact in FP64), so the two copies are the same numbers. A block W
+// (or a coefficient matrix H) is split the same way after scaling each column
+// by 2^(62-E), 2^E the smallest power of two above the column's largest
+// magnitude; W's digits are built once per projection by a pre-pass.
 //
 // Exact products. The product of two digits is at most 2^14 in magnitude, so
 // a BF16 x BF16 tensor-core accumulation over at most 256 terms stays below
@@ -49,7 +50,7 @@ constexpr int kUpdStages = 4;
 constexpr int kUpdPad = 32 * 1024;
 
 // status codes written by the kernels (first failure wins)
-constexpr int kErrWaitProducer = 1, kErrWaitMma = 2, kErrWaitSlicer = 3, kErrWaitEpilogue = 4;
+constexpr int kErrWaitProducer = 1, kErrWaitMma = 2, kErrWaitEpilogue = 4;
 
 __device__ __forceinline__ double pow2i(int e) {  // 2^e, -1022 <= e <= 1023
   return __longlong_as_double((long long)(e + 1023) << 52);
@@ -451,10 +452,12 @@ __global__ void tc_hdigits_kernel(const double* __restrict__ C, int ldc, int K, 
 // Persistent CTAs over 128-row tiles. Per tile and group one stage (the 16
 // strips, 32 KB, plus the group's H digits, NP x 16); per stage 8 MMAs, one
 // per basis digit s: M = 128 rows (A MN-major: strip pair 2s, 2s+1), N = NP
-// (column j, digit t), K = 16 columns, into accumulator s of a
-// double-buffered set of 8. The epilogue warps (one row per thread) sum the
-// digit pairs by diagonal s + t <= 8 in int32, combine the diagonals exactly
-// into three integers below 2^43 and subtract the FP64 result from W.
+// (column j, digit t), K = 16 columns, into accumulator s of a set of 8
+// (two sets, double-buffered, when 16 NP <= 512 tensor-memory columns, i.e.
+// up to 4 columns of W; one set for 5..8). The epilogue warps (one row per
+// thread) sum the digit pairs by diagonal s + t <= 8 in int32, combine the
+// diagonals exactly into three integers below 2^43 and subtract the FP64
+// result from W, or (keep = 0) store its negative.
 struct UpdArgs {
   const uint8_t* q;
   int64_t n_oct, n;
