@@ -293,6 +293,17 @@ flz_status flz_basis_project(int64_t n, int32_t nb, int32_t r, const double* Q, 
  * and conditions as flz_basis_project. */
 flz_status flz_basis_orthogonalize(int64_t n, int32_t nb, int32_t r, const double* Q, double* W, double* C,
                                    int32_t method, void* stream);
+/* Combination X = Q H of basis columns (the Ritz vectors of Section 2.3 are
+ * X = Q_k Y with Y eigenvectors of T_k): Q as in flz_basis_project (nb device
+ * blocks, K = nb r columns), H K x s row-major (device), X n x s row-major
+ * (device, overwritten, not overlapping Q or H), 1 <= s <= 16. TENSOR forms
+ * the products from the digits of Q (rounded to the 2^-62 grid) and of H
+ * (62 fractional bits of each column's scale), summed exactly but for digit
+ * pairs below 2^-64 of the column scale, with at most one FP64 rounding per
+ * 256 basis columns; CUDA_CORES uses FP64 arithmetic. Synchronous with
+ * respect to `stream`; allocates and frees its own scratch. */
+flz_status flz_basis_multiply(int64_t n, int32_t nb, int32_t r, const double* Q, const double* H, int32_t s,
+                              double* X, int32_t method, void* stream);
 /* Layout check of the tensor-core path: one tcgen05.mma (M = 128, N = n in
  * {16, 32, 64, 128}, K = 16, BF16 operands, FP32 accumulator in tensor memory) of a
  * 128 x 16 A operand and an n x 16 B operand given as shared-memory images

@@ -19,8 +19,8 @@ scipy FP64, following the paper's steps in its order and notation:
 - ``dense``: the result by definition for small matrices (all eigenpairs of
   A inside [alpha, beta]) and a Sylvester-inertia eigenvalue count.
 - ``reorth``: the inner products and updates of the full reorthogonalization
-  (Section 3.2.2) evaluated exactly in integer arithmetic, on the fixed-point
-  input rounding the tensor-core path uses.
+  (Section 3.2.2) and the Ritz-vector combinations (Section 2.3) evaluated
+  exactly in integer arithmetic on the FP64 inputs as given, rounded once.
 
 Library primitives used as single steps: scipy sparse matrix products,
 numpy matrix products, ``numpy.linalg.qr`` (Householder QR) and

@@ -45,7 +45,7 @@ EXPORTED = (
     "flz_matrix_create_csr", "flz_matrix_destroy", "flz_matrix_info", "flz_matrix_format",
     "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_smoothed_step_coefficients", "flz_jackson_factors", "flz_lanczos_sigma_factors", "flz_filter_degree", "flz_spectrum_bounds",
     "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_sym_eig",
-    "flz_basis_project", "flz_basis_orthogonalize", "flz_tc_mma_probe", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve", "flz_solve_sliced",
+    "flz_basis_project", "flz_basis_orthogonalize", "flz_basis_multiply", "flz_tc_mma_probe", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve", "flz_solve_sliced",
     "flz_get_count", "flz_get_eigenvalues", "flz_get_eigenvectors", "flz_get_residuals", "flz_get_stats",
     "flz_batch_create", "flz_batch_destroy", "flz_batch_solve", "flz_batch_get_count", "flz_batch_get_eigenvalues",
     "flz_batch_get_residuals", "flz_batch_get_eigenvectors", "flz_batch_get_stats",
@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
         "flz_band_eigenvectors": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp, _vp, _u64]),
         "flz_sym_eig": (ctypes.c_int, [_i32, _vp, _vp, _vp]),
         "flz_basis_project": (ctypes.c_int, [_i64, _i32, _i32, _vp, _vp, _vp, _i32, _vp]),
+        "flz_basis_multiply": (ctypes.c_int, [_i64, _i32, _i32, _vp, _vp, _i32, _vp, _i32, _vp]),
         "flz_basis_orthogonalize": (ctypes.c_int, [_i64, _i32, _i32, _vp, _vp, _vp, _i32, _vp]),
         "flz_tc_mma_probe": (ctypes.c_int, [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _i32, _i32, _i32, _vp]),
         "flz_solver_create": (ctypes.c_int, [_vp, ctypes.POINTER(flz_params), ctypes.POINTER(_vp)]),
@@ -311,6 +312,12 @@ def flz_basis_orthogonalize(n, nb, r, Q, W, C, method=FLZ_ORTHO_TENSOR, stream=N
     """W <- (I - QQ^T)^2 W in place; C = total projection coefficients (device)."""
     _check(lib().flz_basis_orthogonalize(int(n), int(nb), int(r), _ptr(Q), _ptr(W), _ptr(C), int(method),
                                          _stream(stream)))
+
+
+def flz_basis_multiply(n, nb, r, Q, H, s, X, method=FLZ_ORTHO_TENSOR, stream=None):
+    """X = Q H for a basis of nb device blocks, H (nb r x s) and X (n x s) device, row-major."""
+    _check(lib().flz_basis_multiply(int(n), int(nb), int(r), _ptr(Q), _ptr(H), int(s), _ptr(X), int(method),
+                                    _stream(stream)))
 
 
 def flz_tc_mma_probe(a_img, b_img, n, a_mn_major, a_lbo, a_sbo, b_lbo, b_sbo):

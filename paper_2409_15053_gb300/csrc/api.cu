@@ -486,6 +486,26 @@ flz_status flz_basis_orthogonalize(int64_t n, int32_t nb, int32_t r, const doubl
   FLZ_API_END
 }
 
+flz_status flz_basis_multiply(int64_t n, int32_t nb, int32_t r, const double* Q, const double* H, int32_t s,
+                              double* X, int32_t method, void* stream) {
+  FLZ_API_BEGIN
+  check_basis_args(n, nb, r, Q, H, X, method);
+  if (s < 1 || s > 16) fail(FLZ_ERR_INVALID_ARG, "s must be in 1..16");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (method == FLZ_ORTHO_CUDA_CORES) {
+    flz::basis_update(Q, nb, n, r, H, s, 1.0, 0.0, X, s, st);
+    FLZ_CUDA(cudaStreamSynchronize(st));
+  } else {
+    flz::TcBasis B;
+    digits_of(B, n, nb, r, Q, st);
+    B.multiply(nb * r, H, s, s, X, s, st);
+    FLZ_CUDA(cudaMemcpyAsync(B.status_host, B.status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    FLZ_CUDA(cudaStreamSynchronize(st));
+    B.check_status();
+  }
+  FLZ_API_END
+}
+
 flz_status flz_tc_mma_probe(const uint16_t* a_img, int64_t a_bytes, const uint16_t* b_img, int64_t b_bytes,
                             int32_t n, int32_t a_mn_major, int32_t a_lbo, int32_t a_sbo, int32_t b_lbo,
                             int32_t b_sbo, float* d) {

@@ -1,12 +1,12 @@
 """Full reorthogonalization on the tensor cores (Section 3.2.2, classical
 Gram-Schmidt twice) against exact arithmetic and the FP64 path.
 
-The tensor-core path splits the basis (rounded to the 2^-62 grid) and W
-(rounded to 62 fractional bits of its column scale) into eight base-256
-digits and forms every digit product exactly, so its projections are the
-exact inner products of those rounded values up to one final FP64 rounding.
-The references are the oracle's exact products (oracle/reorth.py, Python
-integers) and the FP64 CUDA-core path.
+The tensor-core path rounds the basis to the 2^-62 grid and W (or a
+coefficient matrix H) to 62 fractional bits of each column's scale, splits
+both into eight base-256 digits and sums the digit products exactly. The
+references are the oracle's exact products of the UNROUNDED FP64 inputs
+(oracle/reorth.py); the tests bound the difference by that number format's
+error model, written out below, and compare with the FP64 CUDA-core path.
 
 The first tests check the shared-memory descriptor layouts of one tcgen05
 MMA on small integer tiles; they run first so that a layout mismatch stops
@@ -121,17 +121,52 @@ def test_mma_holds_exact_integer_sums():
 
 # ---------------------------------------------------------------------------
 def orthonormal_blocks(n, nb, r, seed):
+    """An orthonormal FP64 basis (Householder QR of a normal matrix), as is and as nb row-major n x r blocks."""
     rng = np.random.default_rng(seed)
     Q, _ = np.linalg.qr(rng.standard_normal((n, nb * r)))
-    # the basis lives on the 2^-62 grid (what the solver's basis holds)
-    Q = reorth.grid_round(Q)
     blocks = np.ascontiguousarray(Q.reshape(n, nb, r).transpose(1, 0, 2))  # nb x n x r
     return Q, blocks
 
 
+U = 2.0**-53        # FP64 unit roundoff
+GRID = 2.0**-62     # spacing of the basis grid
+TOP_DROPPED = 2.0**-66  # digit pairs s + t >= 9 an update leaves out, per basis column, times the column scale
+
+
+def column_scale(X):
+    """2^E per column, E the least integer with max |column| < 2^E (1 for a zero column)."""
+    m = np.max(np.abs(X), axis=0)
+    return np.where(m > 0, np.ldexp(1.0, np.frexp(m)[1]), 1.0)
+
+
+def projection_error_bound(Q, W):
+    """|C_tc - Q^T W| elementwise: the basis rounded to the 2^-62 grid (|dq| <= 2^-63), each W column
+    rounded to 62 fractional bits of its scale 2^E (|dw| <= 2^(E-63)), their product, and the FP64
+    recombination of the 15 exact digit-diagonal sums (at most 16 roundings of partial sums bounded
+    by sum |q| |w|)."""
+    n = Q.shape[0]
+    dw = column_scale(W) * 2.0**-63
+    aQ, aW = np.abs(Q), np.abs(W)
+    grid = GRID / 2 * aW.sum(axis=0)[None, :] + aQ.sum(axis=0)[:, None] * dw[None, :] + n * GRID / 2 * dw[None, :]
+    return grid + 16 * U * ((aQ + GRID).T @ (aW + dw[None, :]))
+
+
+def combination_error_bound(Q, H):
+    """|X_tc - Q H| elementwise: the basis grid (2^-63 per value), each H column rounded to 62 fractional
+    bits of its scale 2^F, the digit pairs below 2^-64 of the scale the kernel leaves out, and per window
+    of 256 basis columns three FP64 roundings of partial sums bounded by |Q| |H|."""
+    K = Q.shape[1]
+    windows = (K + 255) // 256
+    dh = column_scale(H) * 2.0**-63
+    aQ, aH = np.abs(Q), np.abs(H)
+    grid = GRID / 2 * aH.sum(axis=0)[None, :] + aQ.sum(axis=1)[:, None] * dh[None, :] + K * GRID / 2 * dh[None, :]
+    dropped = K * TOP_DROPPED * column_scale(H)[None, :]
+    return grid + dropped + 3 * windows * U * ((aQ + GRID) @ (aH + dh[None, :]))
+
+
 @pytest.mark.parametrize("n,nb,r", [(4000, 6, 4), (2777, 13, 3), (1000, 9, 2), (513, 20, 1), (3000, 75, 4),
                                     (3000, 5, 8), (1500, 7, 6), (2000, 3, 16), (700, 2, 13)])
-def test_projection_is_exact_up_to_the_final_rounding(n, nb, r):
+def test_projection_within_the_fixed_point_error_bound(n, nb, r):
     Q, blocks = orthonormal_blocks(n, nb, r, n + nb)
     rng = np.random.default_rng(7)
     W = rng.standard_normal((n, r)) * np.resize(np.array([1.0, 1e-3, 37.0, 2.0**-40]), r)
@@ -141,13 +176,38 @@ def test_projection_is_exact_up_to_the_final_rounding(n, nb, r):
     C64 = torch.zeros_like(C)
     flz.flz_basis_project(n, nb, r, Qd, Wd, C, flz.FLZ_ORTHO_TENSOR)
     flz.flz_basis_project(n, nb, r, Qd, Wd, C64, flz.FLZ_ORTHO_CUDA_CORES)
-    ref = reorth.exact_projection(Q, W)
+    assert np.array_equal(blocks, Qd.cpu().numpy())  # the caller's basis is not modified
+    exact = reorth.exact_projection(Q, W)
+    err_tc = np.abs(C.cpu().numpy() - exact)
+    bound = projection_error_bound(Q, W)
+    assert np.all(err_tc <= bound), float(np.max(err_tc / bound))
+    # and the bound is tighter than the FP64 inner products' own (n-term rounding)
+    assert np.all(bound <= n * U * (np.abs(Q).T @ np.abs(W)) + 64 * U * np.abs(exact) + 2.0**-1000)
     scale = np.linalg.norm(Q, axis=0)[:, None] * np.linalg.norm(W, axis=0)[None, :]
-    err_tc = np.max(np.abs(C.cpu().numpy() - ref) / scale)
-    err_64 = np.max(np.abs(C64.cpu().numpy() - ref) / scale)
-    assert err_tc <= 2.0**-50, (err_tc, err_64)
-    # no worse than the FP64 inner products (which carry n-term rounding)
-    assert err_tc <= max(err_64, 2.0**-52)
+    err_64 = np.max(np.abs(C64.cpu().numpy() - exact) / scale)
+    assert np.max(err_tc / scale) <= max(err_64, 2.0**-52)
+
+
+@pytest.mark.parametrize("n,nb,r,s", [(3000, 6, 4, 4), (2777, 13, 3, 16), (1000, 90, 4, 9), (513, 20, 1, 1),
+                                      (700, 2, 13, 5)])
+def test_combination_within_the_fixed_point_error_bound(n, nb, r, s):
+    # X = Q H, the Ritz vectors' product (Section 2.3), on the update kernel
+    Q, blocks = orthonormal_blocks(n, nb, r, 5 * n + nb)
+    rng = np.random.default_rng(13)
+    K = nb * r
+    H = rng.standard_normal((K, s)) * np.resize(np.array([1.0, 3e-4, 20.0, 2.0**-30]), s)
+    Qd = torch.from_numpy(blocks).cuda()
+    Hd = torch.from_numpy(np.ascontiguousarray(H)).cuda()
+    X = torch.full((n, s), 7.0, dtype=torch.float64, device="cuda")  # overwritten, not accumulated into
+    X64 = torch.zeros_like(X)
+    flz.flz_basis_multiply(n, nb, r, Qd, Hd, s, X, flz.FLZ_ORTHO_TENSOR)
+    flz.flz_basis_multiply(n, nb, r, Qd, Hd, s, X64, flz.FLZ_ORTHO_CUDA_CORES)
+    exact = reorth.exact_combination(Q, H)
+    err_tc = np.abs(X.cpu().numpy() - exact)
+    bound = combination_error_bound(Q, H)
+    assert np.all(err_tc <= bound), float(np.max(err_tc / bound))
+    err_64 = np.abs(X64.cpu().numpy() - exact)
+    assert np.all(err_64 <= K * U * (np.abs(Q) @ np.abs(H)) + 2.0**-1000)
 
 
 @pytest.mark.parametrize("n,nb,r", [(4000, 6, 4), (2777, 13, 3), (3000, 75, 4), (300, 1, 2), (8, 1, 1),
@@ -179,7 +239,6 @@ def test_full_size_projection_grid():
     g = torch.Generator(device="cuda").manual_seed(5)
     Q = torch.randn(n, nb * r, dtype=torch.float64, device="cuda", generator=g)
     Q, _ = torch.linalg.qr(Q)
-    Q = torch.round(Q * 2.0**62) * 2.0**-62
     blocks = Q.reshape(n, nb, r).permute(1, 0, 2).contiguous()
     W = torch.randn(n, r, dtype=torch.float64, device="cuda", generator=g) + Q[:, :r] * 50.0
     C = torch.zeros(nb * r, r, dtype=torch.float64, device="cuda")
