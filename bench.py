@@ -256,7 +256,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--degree", type=int, default=BENCH_DEGREE)
     ap.add_argument("--block-size", type=int, default=4)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16", "df64"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16", "df64", "fx64"])
     ap.add_argument("--recurrence", default="forward", choices=["forward", "clenshaw"])
     ap.add_argument("--damping", default="none", choices=["none", "jackson", "sigma"],
                     help="filter damping (the paper uses none)")
@@ -298,7 +298,7 @@ def main():
     import paper_2409_15053_gb300 as flz
 
     prec = {"fp64": flz.FLZ_PREC_FP64, "fp32": flz.FLZ_PREC_FP32, "bf16": flz.FLZ_PREC_BF16,
-            "df64": flz.FLZ_PREC_DF64}[args.precision]
+            "df64": flz.FLZ_PREC_DF64, "fx64": flz.FLZ_PREC_FX64}[args.precision]
     if args.mode == "batch":
         print(json.dumps({"mode": "batch", **batch_leg(flz, torch, torch.cuda.current_stream())}))
         return
@@ -370,7 +370,7 @@ def main():
     # solver's own CUDA-event timing of its filter applications.
     launches_filter = st["iters"] * st["degree"]
     ms_per_launch = st["ms_filter"] / max(launches_filter, 1)
-    sizes = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "bf16": (2, 2, 4), "df64": (8, 8, 8)}[args.precision]
+    sizes = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "bf16": (2, 2, 4), "df64": (8, 8, 8), "fx64": (8, 8, 8)}[args.precision]
     nbytes = filter_bytes_per_launch(csr.n, csr.nnz, args.block_size, *sizes, recurrence=args.recurrence)
     nflops = filter_flops_per_launch(csr.n, csr.nnz, args.block_size)
     hbm, hbm_src = peaks()
@@ -420,7 +420,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_time / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "df64": "f32x2"}[args.precision],
+            "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "df64": "f32x2", "fx64": "i64"}[args.precision],
             "data": "synthetic", "config": config_dict(csr, args), "roofline": roofline, "cpu_baseline": cpu,
             "e2e": e2e, "variants": variants, "batch64": batch, "gpu_launches": int(sum(x["kernel_launches"] for x in stats_list)), "clocks": clocks,
             "solver": {k: st[k] for k in ("iters", "matvecs", "count", "degree", "checks", "lmin", "lmax",
@@ -861,7 +861,7 @@ def filter_mode(flz, torch, csr, prec, args):
     launches = m + (0 if prec == flz.FLZ_PREC_FP64 else 1)
     ms = float(np.mean(times)) / m
     sizes = {flz.FLZ_PREC_FP64: (8, 8, 8), flz.FLZ_PREC_FP32: (4, 4, 4), flz.FLZ_PREC_BF16: (2, 2, 4),
-             flz.FLZ_PREC_DF64: (8, 8, 8)}[prec]
+             flz.FLZ_PREC_DF64: (8, 8, 8), flz.FLZ_PREC_FX64: (8, 8, 8)}[prec]
     nbytes = filter_bytes_per_launch(csr.n, csr.nnz, r, *sizes, recurrence=args.recurrence)
     hbm, src = peaks()
     print(json.dumps({"mode": "filter", "precision": args.precision, "recurrence": args.recurrence,

@@ -67,8 +67,21 @@ typedef enum flz_memspace { FLZ_HOST = 0, FLZ_DEVICE = 1 } flz_memspace;
  *       GPUs whose FP64 rate is a small fraction of their FP32 rate. The single
  *       solver also keeps its Krylov basis in double-FP32 (reorthogonalization
  *       on the FP32 pipes); a batch uses the double-FP32 filter with an FP64
- *       basis. */
-typedef enum flz_precision { FLZ_PREC_FP64 = 0, FLZ_PREC_FP32 = 1, FLZ_PREC_BF16 = 2, FLZ_PREC_DF64 = 3 } flz_precision;
+ *       basis.
+ * FX64: 64-bit fixed point on the integer pipes (forward recurrence only):
+ *       the recurrence vectors and the running sum are integers in units of
+ *       2^-60 of a power-of-two scale near each column's 2-norm, the entries
+ *       of 2 Ahat and the coefficients integers in units of 2^-61; every row
+ *       sum of products is formed in 96-bit integers and rounded once, so each
+ *       degree adds one rounding of 2^-61 (relative to the column's norm) per
+ *       entry where FP64 adds one of 2^-53 relative per partial sum. Needs
+ *       the spectrum of Ahat inside [-1, 1] (a recurrence value above 1.25 of
+ *       its column scale is reported as FLZ_ERR_INVALID_ARG instead of
+ *       overflowing) and rows of 2 Ahat with absolute sums at most 3.9; block
+ *       widths 1, 2, 3, 4, 8, 16. Where these do not hold the filter runs in
+ *       FP64 (flz_stats.filter_precision says which ran). */
+typedef enum flz_precision { FLZ_PREC_FP64 = 0, FLZ_PREC_FP32 = 1, FLZ_PREC_BF16 = 2, FLZ_PREC_DF64 = 3,
+                             FLZ_PREC_FX64 = 4 } flz_precision;
 
 /* How p_m(Ahat) V is evaluated; both give the same polynomial and differ
  * only in rounding.
@@ -148,6 +161,7 @@ typedef struct flz_stats {
   int64_t basis_vectors;/* final Krylov basis size */
   int64_t kernel_launches; /* CUDA kernels this solve launched */
   int32_t ortho;        /* flz_ortho the reorthogonalization ran on (CUDA_CORES or TENSOR) */
+  int32_t filter_precision; /* flz_precision the filter ran in (FX64 requested may run as FP64) */
 } flz_stats;
 
 /* ---- status and parameters ------------------------------------------------ */
@@ -196,9 +210,11 @@ flz_status flz_matrix_format(const flz_matrix* A, int32_t* sell, int64_t* sell_e
  * V, W: device FP64, n x r row-major, must not overlap; 1 <= r <= 16;
  * coeffs: host FP64[degree+1]; degree >= 0; e > 0. precision selects the
  * recurrence arithmetic (flz_precision); W is always FP64. Scratch of
- * 2 n r elements (plus n r FP32 for reduced precision) is owned by the
- * matrix handle and reused across calls, so calls on one matrix must not
- * overlap in time. Asynchronous on `stream`. */
+ * 2 n r elements (plus n r FP32 for reduced precision, 3 n r 64-bit integers
+ * for FX64) is owned by the matrix handle and reused across calls, so calls
+ * on one matrix must not overlap in time. Asynchronous on `stream`, except
+ * FX64, which synchronizes it to report a range overflow (INVALID_ARG); FX64
+ * with the Clenshaw recurrence is INVALID_ARG. */
 flz_status flz_filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int32_t degree,
                             int32_t r, const double* V, double* W, int32_t precision, int32_t recurrence,
                             void* stream);
@@ -304,6 +320,13 @@ flz_status flz_basis_orthogonalize(int64_t n, int32_t nb, int32_t r, const doubl
  * respect to `stream`; allocates and frees its own scratch. */
 flz_status flz_basis_multiply(int64_t n, int32_t nb, int32_t r, const double* Q, const double* H, int32_t s,
                               double* X, int32_t method, void* stream);
+/* Measured arithmetic rate of the current device (not in the paper; the
+ * denominator of the filter kernels' ALU fractions): kind 0 times FP64 FMAs,
+ * kind 1 32-bit integer multiply-adds (the fixed-point filter's limb
+ * products), each counted as 2 operations, in *ops_per_s. Independent
+ * multiply-add chains on 8 CTAs per SM, timed with CUDA events (fastest of
+ * three runs after a warm-up). Synchronizes the device; about 0.1 s. */
+flz_status flz_measure_alu_peak(int32_t kind, double* ops_per_s);
 /* Layout check of the tensor-core path: one tcgen05.mma (M = 128, N = n in
  * {16, 32, 64, 128}, K = 16, BF16 operands, FP32 accumulator in tensor memory) of a
  * 128 x 16 A operand and an n x 16 B operand given as shared-memory images

@@ -190,3 +190,82 @@ def smoothed_step_coefficients(alpha: float, beta: float, delta: float, m: int) 
                         - z0 * (_cos_integral(k, t_hi) - _cos_integral(k, t_lo))) / (z1 - z0)
         c[k] = (2.0 - (k == 0)) / np.pi * acc
     return c
+
+
+def _dyadic(x: float) -> tuple[int, int]:
+    """(m, e) with x = m 2^e exactly."""
+    if x == 0.0:
+        return 0, 0
+    f, e = np.frexp(x)
+    return int(f * 2.0**53), int(e) - 53
+
+
+class _Dyadic:
+    """A vector of exact dyadic rationals N_i 2^E with one shared exponent."""
+
+    def __init__(self, N, E):
+        self.N, self.E = N, E
+
+    @staticmethod
+    def of(x):
+        parts = [_dyadic(float(v)) for v in x]
+        E = min((e for m, e in parts if m), default=0)
+        return _Dyadic([m << (e - E) if m else 0 for m, e in parts], E)
+
+    def aligned(self, E):
+        return [v << (self.E - E) for v in self.N]
+
+
+def clenshaw_apply_exact(S2, b: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """p_m(Ahat) V for the matrix 2 Ahat given with FP64 entries, in exact arithmetic, rounded once.
+
+    Clenshaw's recurrence of Section 2.2 with nothing rounded in between:
+    U_{m+1} = U_{m+2} = 0; U_k = b_k V + (2 Ahat) U_{k+1} - U_{k+2}; p = b_0 V +
+    (1/2)(2 Ahat) U_1 - U_2. Every FP64 number is an integer times a power of
+    two, so each U_k is held as integers with a shared power of two. S2 is a
+    scipy CSR matrix holding 2 Ahat; the result is p_m(Ahat) V rounded to FP64
+    entry by entry (the reference for measuring a kernel's rounding error).
+    Slow: for small matrices and degrees.
+    """
+    S2 = S2.tocsr()
+    n = S2.shape[0]
+    V = np.asarray(V, dtype=np.float64)
+    vals = _Dyadic.of(S2.data)
+    out = np.empty_like(V)
+    bd = [_dyadic(float(x)) for x in b]
+    for t in range(V.shape[1]):
+        v = _Dyadic.of(V[:, t])
+
+        def times_2ahat(u):
+            E = vals.E + u.E
+            N = [0] * n
+            for i in range(n):
+                acc = 0
+                for j in range(S2.indptr[i], S2.indptr[i + 1]):
+                    acc += vals.N[j] * u.N[S2.indices[j]]
+                N[i] = acc
+            return _Dyadic(N, E)
+
+        def combine(terms):  # sum of (sign, vector) pairs, exactly
+            E = min(x.E for _, x in terms)
+            acc = [0] * n
+            for sg, x in terms:
+                for i, val in enumerate(x.aligned(E)):
+                    acc[i] += sg * val
+            return _Dyadic(acc, E)
+
+        def scaled(k):  # b_k V
+            mb, eb = bd[k]
+            return _Dyadic([mb * x for x in v.N], v.E + eb)
+
+        zero = _Dyadic([0] * n, 0)
+        u1, u2 = zero, zero
+        for k in range(len(b) - 1, 0, -1):
+            u1, u2 = combine([(1, scaled(k)), (1, times_2ahat(u1)), (-1, u2)]), u1
+        half = times_2ahat(u1)
+        half.E -= 1
+        p = combine([(1, scaled(0)), (1, half), (-1, u2)])
+        for i in range(n):
+            N, E = p.N[i], p.E
+            out[i, t] = float(N << E) if E >= 0 else N / (1 << -E)
+    return out

@@ -35,7 +35,7 @@ FLZ_ERR_NOT_SOLVED = 11
 
 FLZ_F64, FLZ_F32, FLZ_BF16 = 0, 1, 2
 FLZ_HOST, FLZ_DEVICE = 0, 1
-FLZ_PREC_FP64, FLZ_PREC_FP32, FLZ_PREC_BF16, FLZ_PREC_DF64 = 0, 1, 2, 3
+FLZ_PREC_FP64, FLZ_PREC_FP32, FLZ_PREC_BF16, FLZ_PREC_DF64, FLZ_PREC_FX64 = 0, 1, 2, 3, 4
 FLZ_REC_FORWARD, FLZ_REC_CLENSHAW = 0, 1
 FLZ_ORTHO_AUTO, FLZ_ORTHO_CUDA_CORES, FLZ_ORTHO_TENSOR = 0, 1, 2
 
@@ -45,7 +45,7 @@ EXPORTED = (
     "flz_matrix_create_csr", "flz_matrix_destroy", "flz_matrix_info", "flz_matrix_format",
     "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_smoothed_step_coefficients", "flz_jackson_factors", "flz_lanczos_sigma_factors", "flz_filter_degree", "flz_spectrum_bounds",
     "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_sym_eig",
-    "flz_basis_project", "flz_basis_orthogonalize", "flz_basis_multiply", "flz_tc_mma_probe", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve", "flz_solve_sliced",
+    "flz_basis_project", "flz_basis_orthogonalize", "flz_basis_multiply", "flz_measure_alu_peak", "flz_tc_mma_probe", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve", "flz_solve_sliced",
     "flz_get_count", "flz_get_eigenvalues", "flz_get_eigenvectors", "flz_get_residuals", "flz_get_stats",
     "flz_batch_create", "flz_batch_destroy", "flz_batch_solve", "flz_batch_get_count", "flz_batch_get_eigenvalues",
     "flz_batch_get_residuals", "flz_batch_get_eigenvectors", "flz_batch_get_stats",
@@ -72,7 +72,7 @@ class flz_stats(ctypes.Structure):
         ("beta_mapped", ctypes.c_double), ("max_residual", ctypes.c_double), ("ms_bounds", ctypes.c_double),
         ("ms_filter", ctypes.c_double), ("ms_orth", ctypes.c_double), ("ms_check", ctypes.c_double),
         ("ms_total", ctypes.c_double), ("basis_vectors", ctypes.c_int64),
-        ("kernel_launches", ctypes.c_int64), ("ortho", ctypes.c_int32),
+        ("kernel_launches", ctypes.c_int64), ("ortho", ctypes.c_int32), ("filter_precision", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -122,6 +122,7 @@ def lib() -> ctypes.CDLL:
         "flz_sym_eig": (ctypes.c_int, [_i32, _vp, _vp, _vp]),
         "flz_basis_project": (ctypes.c_int, [_i64, _i32, _i32, _vp, _vp, _vp, _i32, _vp]),
         "flz_basis_multiply": (ctypes.c_int, [_i64, _i32, _i32, _vp, _vp, _i32, _vp, _i32, _vp]),
+        "flz_measure_alu_peak": (ctypes.c_int, [_i32, _pdbl]),
         "flz_basis_orthogonalize": (ctypes.c_int, [_i64, _i32, _i32, _vp, _vp, _vp, _i32, _vp]),
         "flz_tc_mma_probe": (ctypes.c_int, [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _i32, _i32, _i32, _vp]),
         "flz_solver_create": (ctypes.c_int, [_vp, ctypes.POINTER(flz_params), ctypes.POINTER(_vp)]),
@@ -220,16 +221,23 @@ def flz_matrix_format(A):
     return sell.value, entries.value, long_rows.value
 
 
+def _coefficients(coeffs, degree):
+    coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
+    if coeffs.ndim != 1 or coeffs.shape[0] < int(degree) + 1:
+        raise ValueError(f"need degree + 1 = {int(degree) + 1} coefficients, got {coeffs.size}")
+    return coeffs
+
+
 def flz_filter_apply(A, c, e, coeffs, degree, r, V, W, precision=FLZ_PREC_FP64, stream=None,
                      recurrence=FLZ_REC_FORWARD):
-    coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
+    coeffs = _coefficients(coeffs, degree)
     _check(lib().flz_filter_apply(A, float(c), float(e), _ptr(coeffs), int(degree), int(r), _ptr(V), _ptr(W),
                                   int(precision), int(recurrence), _stream(stream)))
 
 
 def flz_filter_apply_noalloc(n, nnz, rowptr, col, val, c, e, coeffs, degree, r, V, W, stream=None):
     """FP64 filter from caller-owned device CSR arrays and blocks; allocates no device memory."""
-    coeffs = np.ascontiguousarray(coeffs, dtype=np.float64)
+    coeffs = _coefficients(coeffs, degree)
     _check(lib().flz_filter_apply_noalloc(int(n), int(nnz), _ptr(rowptr), _ptr(col), _ptr(val), float(c), float(e),
                                           _ptr(coeffs), int(degree), int(r), _ptr(V), _ptr(W), _stream(stream)))
 
@@ -318,6 +326,13 @@ def flz_basis_multiply(n, nb, r, Q, H, s, X, method=FLZ_ORTHO_TENSOR, stream=Non
     """X = Q H for a basis of nb device blocks, H (nb r x s) and X (n x s) device, row-major."""
     _check(lib().flz_basis_multiply(int(n), int(nb), int(r), _ptr(Q), _ptr(H), int(s), _ptr(X), int(method),
                                     _stream(stream)))
+
+
+def flz_measure_alu_peak(kind) -> float:
+    """Measured FP64 FMA (kind 0) or 32-bit integer multiply-add (kind 1) rate, operations per second."""
+    out = ctypes.c_double()
+    _check(lib().flz_measure_alu_peak(int(kind), ctypes.byref(out)))
+    return out.value
 
 
 def flz_tc_mma_probe(a_img, b_img, n, a_mn_major, a_lbo, a_sbo, b_lbo, b_sbo):

@@ -358,12 +358,16 @@ flz_status flz_filter_apply(flz_matrix* A, double c, double e, const double* coe
   if (!A || !coeffs || !V || !W) fail(FLZ_ERR_INVALID_ARG, "null argument");
   if (recurrence != FLZ_REC_FORWARD && recurrence != FLZ_REC_CLENSHAW) fail(FLZ_ERR_INVALID_ARG, "bad recurrence");
   if (degree < 0 || r < 1 || r > 16 || !(e > 0.0)) fail(FLZ_ERR_INVALID_ARG, "need degree >= 0, 1 <= r <= 16, e > 0");
-  if (precision < FLZ_PREC_FP64 || precision > FLZ_PREC_DF64) fail(FLZ_ERR_INVALID_ARG, "bad precision");
+  if (precision < FLZ_PREC_FP64 || precision > FLZ_PREC_FX64) fail(FLZ_ERR_INVALID_ARG, "bad precision");
   const size_t bytes = sizeof(double) * (size_t)A->n * r;
   const char* v = reinterpret_cast<const char*>(V);
   const char* w = reinterpret_cast<const char*>(W);
   if (v < w + bytes && w < v + bytes) fail(FLZ_ERR_INVALID_ARG, "V and W overlap");
   flz::filter_apply(A, c, e, coeffs, degree, r, V, W, precision, recurrence, static_cast<cudaStream_t>(stream));
+  if (precision == FLZ_PREC_FX64) {  // a range overflow is reported here, not by a later call
+    FLZ_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    flz::fx_check_flag(A);
+  }
   FLZ_API_END
 }
 
@@ -506,6 +510,13 @@ flz_status flz_basis_multiply(int64_t n, int32_t nb, int32_t r, const double* Q,
   FLZ_API_END
 }
 
+flz_status flz_measure_alu_peak(int32_t kind, double* ops_per_s) {
+  FLZ_API_BEGIN
+  if (!ops_per_s || (kind != 0 && kind != 1)) fail(FLZ_ERR_INVALID_ARG, "kind must be 0 (FP64 FMA) or 1 (integer)");
+  *ops_per_s = flz::measure_alu_peak(kind);
+  FLZ_API_END
+}
+
 flz_status flz_tc_mma_probe(const uint16_t* a_img, int64_t a_bytes, const uint16_t* b_img, int64_t b_bytes,
                             int32_t n, int32_t a_mn_major, int32_t a_lbo, int32_t a_sbo, int32_t b_lbo,
                             int32_t b_sbo, float* d) {
@@ -533,7 +544,9 @@ flz_status flz_solver_create(flz_matrix* A, const flz_params* params, flz_solver
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.ortho == FLZ_ORTHO_TENSOR && (!flz::TcBasis::supported(p.block_size) || p.precision == FLZ_PREC_DF64))
     fail(FLZ_ERR_INVALID_ARG, "tensor-core reorthogonalization needs an FP64 basis (not the double-FP32 precision)");
-  if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_DF64) fail(FLZ_ERR_INVALID_ARG, "bad precision");
+  if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_FX64) fail(FLZ_ERR_INVALID_ARG, "bad precision");
+  if (p.precision == FLZ_PREC_FX64 && p.recurrence != FLZ_REC_FORWARD)
+    fail(FLZ_ERR_INVALID_ARG, "the fixed-point filter evaluates the forward recurrence only");
   flz_solver* s = new flz_solver();
   s->A = A;
   s->p = p;

@@ -681,6 +681,11 @@ void build_sell(flz_matrix* A) {
   FLZ_LAUNCH_CHECK();
   FLZ_CUDA(cudaDeviceSynchronize());
   A->sell_len = total;
+  // the most entries any CTA of 256 rows (8 slices) holds: the shared-memory
+  // stage of the staged SELL kernels
+  int64_t cta_max = 0;
+  for (int64_t s0 = 0; s0 < nsl; s0 += 8) cta_max = std::max<int64_t>(cta_max, off[std::min(nsl, s0 + 8)] - off[s0]);
+  A->sell_cta_entries = cta_max;
   A->sell = true;
 }
 

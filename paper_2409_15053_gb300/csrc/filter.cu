@@ -549,6 +549,15 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
     return;
   }
   const bool clen = recurrence == FLZ_REC_CLENSHAW;
+  if (precision == FLZ_PREC_FX64) {
+    if (clen) fail(FLZ_ERR_INVALID_ARG, "the fixed-point filter evaluates the forward recurrence only");
+    if (fx_filter_apply(A, c, e, coeffs, m, r, V, W, st)) {
+      A->last_filter_precision = FLZ_PREC_FX64;
+      return;
+    }
+    precision = FLZ_PREC_FP64;  // the format does not apply to this matrix or block: FP64 arithmetic
+  }
+  A->last_filter_precision = precision;
   if (precision == FLZ_PREC_FP64) {
     const auto M = prepare<double>(A, A->sval64, A->ssell64, 0, c, e, sell_usable(A, r, V, 8, W, 8, true), st);
     A->ws64.reserve(2 * nr);

@@ -152,6 +152,27 @@ int tc_probe(const uint16_t* a_img, size_t a_bytes, const uint16_t* b_img, size_
 
 }  // namespace flz
 
+namespace flz {
+// State of the 64-bit fixed-point filter on a matrix handle: 2 Ahat as
+// offset-binary integers (units 2^-61) in CSR order (slot 0) and in the
+// SELL-32 layout (slot 1) for the (c, e) they were built for, the largest
+// absolute row sum of 2 Ahat, the recurrence scratch and a few device words
+// (column exponents, overflow flag).
+struct FxValues {
+  DevBuf<uint64_t> csr, sell, ws, scratch;
+  DevBuf<double> part;
+  double c[2] = {0.0, 0.0}, e[2] = {0.0, 0.0}, rowsum[2] = {0.0, 0.0};
+  bool ok[2] = {false, false};
+  unsigned* flag_host = nullptr;
+  FxValues() = default;
+  FxValues(const FxValues&) = delete;
+  FxValues& operator=(const FxValues&) = delete;
+  ~FxValues() {
+    if (flag_host) cudaFreeHost(flag_host);
+  }
+};
+}  // namespace flz
+
 // Matrix handle: a device copy of a symmetric CSR matrix (Section 3.2.1).
 struct flz_matrix {
   int64_t n = 0, nnz = 0;              // nnz counts the stored entries (explicit zero diagonals included)
@@ -180,6 +201,7 @@ struct flz_matrix {
   // Built when the padding stays below 30 % of the stored entries.
   bool sell = false;
   int64_t sell_len = 0;
+  int64_t sell_cta_entries = 0;  // most entries in 8 consecutive slices (256 rows)
   flz::DevBuf<int32_t> sell_off;  // n_slices + 1 element offsets
   flz::DevBuf<int32_t> sell_col;
   flz::DevBuf<double> ssell64;
@@ -193,6 +215,8 @@ struct flz_matrix {
   flz::DevBuf<float> ws32;
   flz::DevBuf<__nv_bfloat16> ws16;
   flz::DevBuf<flz::dev::dfloat> wsdf;
+  flz::FxValues fx;  // the fixed-point filter's values and scratch
+  int32_t last_filter_precision = 0;  // flz_precision the last filter application ran in
 };
 
 // Solver handle: parameters, interval, results of the last solve and workspace.
@@ -233,6 +257,22 @@ void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m
 // conversion of V, W written as pairs).
 void filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m, int r,
                   const dev::dfloat* V, dev::dfloat* W, int recurrence, cudaStream_t st);
+// ---- fixed.cu -------------------------------------------------------------------
+// W = p_m(Ahat) V in 64-bit fixed point on the integer pipes (forward
+// recurrence). Returns false, doing nothing, where the format does not apply
+// (block width without a row kernel, a W not 16-byte aligned for even r, a
+// row of 2 Ahat with absolute sum above 3.9, or coefficients too large):
+// the caller then runs the FP64 filter. The overflow flag is fetched to the
+// handle's host copy after the launches; read it with fx_check_flag after a
+// synchronization of st.
+bool fx_filter_apply(flz_matrix* A, double c, double e, const double* coeffs, int m, int r, const double* V,
+                     double* W, cudaStream_t st);
+bool fx_supported(int r);
+void fx_check_flag(flz_matrix* A);
+// ---- probe.cu ----------------------------------------------------------------------
+// Measured throughput of FP64 FMAs (kind 0, flop/s) or 32-bit integer
+// multiply-adds (kind 1, 2 ops each) on the current device.
+double measure_alu_peak(int kind);
 // ---- clenshaw.cu ----------------------------------------------------------------
 // W = p_m(Ahat) V by the Clenshaw recurrence with 2 Ahat stored in `val`
 // (MS; `vsell` in the SELL-32 layout or null, `val` in CSR order) and the

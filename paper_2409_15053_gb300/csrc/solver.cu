@@ -77,6 +77,7 @@ struct Engine {
   double ms_orth = 0.0, ms_op = 0.0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   TcBasis* tcb = nullptr;  // digit copy of an FP64 basis: reorthogonalization on the tensor cores
+  bool fx = false;         // the filter runs in fixed point: check its overflow flag after each step
 
   T* block(int b) const { return Q + (size_t)b * n * r; }
 
@@ -196,6 +197,7 @@ struct Engine {
     FLZ_CUDA(cudaEventRecord(ev[2], st));
     FLZ_CUDA(cudaEventSynchronize(ev[2]));
     if (tcb) tcb->check_status();
+    if (fx) fx_check_flag(A);
     float a = 0.f, b = 0.f;
     FLZ_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
     FLZ_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
@@ -403,6 +405,7 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
     s->tcb.reserve(n, (int64_t)nb_cap * r);
     E.tcb = &s->tcb;
   }
+  E.fx = p.precision == FLZ_PREC_FX64;
   orthonormal_start(E, p.seed);
 
   Projected P;
@@ -602,6 +605,7 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   stats.basis_vectors = (int64_t)k * r;
   stats.ms_total = ms_since(t_start);
   stats.kernel_launches = g_kernel_launches - launches0;
+  stats.filter_precision = A->last_filter_precision;
   return converged ? FLZ_OK : FLZ_ERR_NOT_CONVERGED;
 }
 
@@ -705,6 +709,7 @@ flz_status solve_sliced(flz_solver* s, int nslices, cudaStream_t st) {
     agg.kernel_launches += x.kernel_launches;
     agg.max_residual = std::max(agg.max_residual, x.max_residual);
     agg.ortho = x.ortho;
+    agg.filter_precision = x.filter_precision;
   }
   // merge: ascending order, pairs shared by adjacent slices kept once
   const int64_t total = (int64_t)vals.size();

@@ -8,6 +8,12 @@ spectral gap among eigenvalues 95..110 (so the count is about 100 and no
 eigenvalue sits near an endpoint) and records the eigenvalues in [alpha, beta].
 
 Run from the repository root:  python tests/golden/make_config2_reference.py
+
+With --bench-degree M the script instead loads the stored reference and runs
+the oracle once more on the stored [alpha, beta] at the benchmark's settings
+(degree M, checks every 10 block steps), recording its block-step and check
+counts under "oracle_at_bench_degree": the CPU timings of bench.py scale their
+sampled per-step costs to that run.
 """
 
 import json
@@ -63,5 +69,31 @@ def main():
     print(json.dumps({k: v for k, v in out.items() if k != "eigenvalues"}, indent=1))
 
 
+def bench_degree(m):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "config2_reference.json")
+    ref = json.load(open(path))
+    rng = np.random.Generator(np.random.PCG64(SEED))
+    Acsr = laplacian_3d_7pt(100, 100, 100, 0.5 * rng.random(100 ** 3))
+    assert csr_checksum(Acsr) == ref["matrix_checksum"]
+    t0 = time.time()
+    res = lanczos.filtered_lanczos(Acsr.to_scipy(), ref["alpha"], ref["beta"], random_normal_block(Acsr.n, 4, 11),
+                                   bounds_start=random_normal_block(Acsr.n, 1, 12)[:, 0],
+                                   degree=m, tol=1e-10, check_every=10, max_blocks=400)
+    wall = time.time() - t0
+    assert res.converged and res.eigenvalues.shape[0] == ref["count"]
+    ref["oracle_at_bench_degree"] = {
+        "degree": m, "block_size": 4, "check_every": 10, "iters": res.iters, "checks": len(res.history),
+        "count": int(res.eigenvalues.shape[0]), "max_residual": float(np.max(res.residuals)),
+        "max_abs_diff_to_reference": float(np.max(np.abs(np.sort(res.eigenvalues) - np.array(ref["eigenvalues"])))),
+        "wall_s": wall,
+    }
+    with open(path, "w") as f:
+        json.dump(ref, f, indent=1)
+    print(json.dumps(ref["oracle_at_bench_degree"], indent=1))
+
+
 if __name__ == "__main__":
-    main()
+    if len(sys.argv) == 3 and sys.argv[1] == "--bench-degree":
+        bench_degree(int(sys.argv[2]))
+    else:
+        main()

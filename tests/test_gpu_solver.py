@@ -246,8 +246,9 @@ def test_device_resident_csr_input():
 
 @pytest.mark.parametrize("precision,rec", [(flz.FLZ_PREC_FP64, flz.FLZ_REC_FORWARD), (flz.FLZ_PREC_DF64, flz.FLZ_REC_FORWARD),
                                            (flz.FLZ_PREC_FP64, flz.FLZ_REC_CLENSHAW),
-                                           (flz.FLZ_PREC_DF64, flz.FLZ_REC_CLENSHAW)],
-                         ids=["fp64-forward", "df64-forward", "fp64-clenshaw", "df64-clenshaw"])
+                                           (flz.FLZ_PREC_DF64, flz.FLZ_REC_CLENSHAW),
+                                           (flz.FLZ_PREC_FX64, flz.FLZ_REC_FORWARD)],
+                         ids=["fp64-forward", "df64-forward", "fp64-clenshaw", "df64-clenshaw", "fx64-forward"])
 def test_full_size_config2_matches_oracle_reference(precision, rec):
     # n = 1e6, nnz = 6.94e6, r = 4, m = 60: the benchmark's configuration,
     # against the eigenvalues the CPU oracle computed (tests/golden).
@@ -358,29 +359,32 @@ def test_sliced_rejects_bad_count():
     flz.flz_matrix_destroy(h)
 
 
-def test_full_size_fd4_hamiltonian_fp64_and_df64():
+def test_full_size_fd4_hamiltonian_fp64_df64_and_fixed_point():
     # The 120^3 4th-order FD Hamiltonian with 64 Gaussian wells (n = 1.728e6,
     # nnz = 22.2e6), all eigenpairs in [-6, 0] (the wells' bound states): at
     # this size no dense or oracle count is affordable, so the checks are the
     # properties that hold at any size -- residuals recomputed here, orthonormal
     # eigenvectors (k orthonormal vectors with residuals <= tol ||A|| certify k
     # eigenvalues within tol ||A|| of the computed ones) -- and the agreement of
-    # two independent arithmetics: FP64 and double-FP32 must return the same
-    # count and eigenvalues. Scaled-down instances are checked against dense
+    # three independent arithmetics: FP64, double-FP32 and the 64-bit fixed-point
+    # filter must return the same count and eigenvalues. Scaled-down instances are checked against dense
     # eigensolves (test_fd4_hamiltonian_vs_dense).
     from synth.workloads import CONFIG3
     N = CONFIG3["grid"]
     csr = fd4_laplacian_3d(N, gaussian_wells_potential(N, CONFIG3["wells"], seed=CONFIG3["seed"]))
     outs = {}
-    for prec in (flz.FLZ_PREC_FP64, flz.FLZ_PREC_DF64):
+    for prec in (flz.FLZ_PREC_FP64, flz.FLZ_PREC_DF64, flz.FLZ_PREC_FX64):
         outs[prec] = solve(csr, CONFIG3["alpha"], 0.0, block_size=4, degree=300, check_every=10, precision=prec)
         assert outs[prec]["status"] == flz.FLZ_OK
-    a, b = outs[flz.FLZ_PREC_FP64], outs[flz.FLZ_PREC_DF64]
-    assert a["vals"].shape == b["vals"].shape and a["vals"].shape[0] > 40
+    a, b, f = outs[flz.FLZ_PREC_FP64], outs[flz.FLZ_PREC_DF64], outs[flz.FLZ_PREC_FX64]
+    assert f["stats"]["filter_precision"] == flz.FLZ_PREC_FX64
+    assert a["vals"].shape == b["vals"].shape == f["vals"].shape and a["vals"].shape[0] > 40
     norm_a = max(abs(a["stats"]["lmin"]), abs(a["stats"]["lmax"]))
     assert np.max(np.abs(a["vals"] - b["vals"])) < 1e-10 * norm_a
+    assert np.max(np.abs(a["vals"] - f["vals"])) < 1e-10 * norm_a
     check_pairs(csr, a, 1e-10)
     check_pairs(csr, b, 1e-10)
+    check_pairs(csr, f, 1e-10)
 
 
 def test_multiple_eigenvalues_stay_orthonormal_across_walk_chunks():

@@ -257,3 +257,77 @@ def test_smoothed_step_series_is_closer_to_its_target_than_the_indicator_series(
     ind = ((z >= a) & (z <= b)).astype(float)
     err_i = np.max(np.abs(ch.clenshaw_scalar(ch.filter_coefficients(a, b, 60), z) - ind))
     assert err_s < 0.05 and err_i > 0.4
+
+
+# ---- the exact filter reference ---------------------------------------------
+def _chebyshev_power_coefficients(k):
+    """Integer coefficients of T_k in the power basis, by T_{k+1} = 2x T_k - T_{k-1}."""
+    t0, t1 = [1], [0, 1]
+    if k == 0:
+        return t0
+    for _ in range(k - 1):
+        t2 = [0] + [2 * c for c in t1]
+        for i, c in enumerate(t0):
+            t2[i] -= c
+        t0, t1 = t1, t2
+    return t1
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 7, 25])
+def test_exact_filter_single_term_on_a_dyadic_diagonal(k):
+    # b = e_k on diag(d) with dyadic d: p(Ahat) V = T_k(d) V, T_k from its integer power-basis coefficients
+    from fractions import Fraction
+    import scipy.sparse as sp
+    d = np.array([-1.0, -0.75, -0.3125, 0.0, 0.5, 0.875, 1.0, 0.015625])
+    V = np.array([[1.0, -3.0], [0.5, 2.0], [7.0, 1.0], [1.0, 1.0], [-2.0, 0.25], [1.0, 5.0], [3.0, -1.0], [1.0, 9.0]])
+    b = np.zeros(k + 1)
+    b[k] = 1.0
+    got = ch.clenshaw_apply_exact(sp.diags(2.0 * d).tocsr(), b, V)
+    coef = _chebyshev_power_coefficients(k)
+    for i, x in enumerate(d):
+        tk = sum(c * Fraction(x) ** j for j, c in enumerate(coef))
+        for t in range(2):
+            assert got[i, t] == float(tk * Fraction(V[i, t]))
+
+
+def test_exact_filter_matches_matrix_powers_on_a_small_matrix():
+    # sum_i b_i T_i(Ahat) by the power basis in rationals, on a dense 5 x 5 symmetric matrix with dyadic entries
+    from fractions import Fraction
+    import scipy.sparse as sp
+    rng = np.random.default_rng(8)
+    H = rng.integers(-8, 9, size=(5, 5)) / 32.0
+    H = (H + H.T) / 2.0
+    V = rng.integers(-4, 5, size=(5, 2)).astype(float)
+    b = np.array([0.5, -0.25, 0.125, 1.0, -0.375])
+    got = ch.clenshaw_apply_exact(sp.csr_matrix(2.0 * H), b, V)
+    Hf = [[Fraction(x) for x in row] for row in H]
+
+    def matmul(X, Y):
+        return [[sum(X[i][l] * Y[l][j] for l in range(len(Y))) for j in range(len(Y[0]))] for i in range(len(X))]
+
+    powers = [[[Fraction(int(i == j)) for j in range(5)] for i in range(5)]]
+    for _ in range(len(b)):
+        powers.append(matmul(powers[-1], Hf))
+    P = [[Fraction(0)] * 5 for _ in range(5)]
+    for i, bi in enumerate(b):
+        for j, c in enumerate(_chebyshev_power_coefficients(i)):
+            for r_ in range(5):
+                for s_ in range(5):
+                    P[r_][s_] += Fraction(bi) * c * powers[j][r_][s_]
+    want = matmul(P, [[Fraction(x) for x in row] for row in V])
+    for i in range(5):
+        for t in range(2):
+            assert got[i, t] == float(want[i][t])
+
+
+def test_exact_filter_within_fp64_error_of_the_fp64_clenshaw():
+    import scipy.sparse as sp
+    A = laplacian_2d(9, 11).to_scipy()
+    c, e = 4.0, 4.0
+    b = ch.filter_coefficients(-0.6, -0.1, 30)
+    V = random_normal_block(A.shape[0], 2, 4)
+    S2 = ((2.0 / e) * (A - c * sp.eye(A.shape[0]))).tocsr()
+    exact = ch.clenshaw_apply_exact(S2, b, V)
+    fp64 = ch.clenshaw_apply(A, c, e, b, V)
+    err = np.max(np.abs(exact - fp64))
+    assert 0 < err < 32 * 31**2 * 2.0**-53 * 3.0 * np.max(np.abs(V))
