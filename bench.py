@@ -2,8 +2,11 @@
 
 Workload (one GB300): the 7-point Dirichlet Laplacian on a 100^3 grid plus a
 diagonal potential 0.5*U(0,1) (seed 2025), n = 1e6, nnz = 6.94e6, CSR FP64;
-all eigenpairs in [alpha, beta] at the lower end of the spectrum (about 100),
-block size 4, fixed filter degree, FP64, residual tolerance 1e-10.
+all eigenpairs in [alpha, beta] at the lower end of the spectrum (105),
+block size 4, filter degree 100, residual tolerance 1e-10. The filter runs in
+64-bit fixed point on the integer pipes (FP64-class: per degree one rounding
+of 2^-62 of a column's norm per element); reorthogonalization, Rayleigh-Ritz
+and residuals are FP64 (the plain FP64 filter is the "fp64_filter" variant).
 
 One step = one flz_solve on the device-resident matrix: spectrum bounds,
 filter construction, block Lanczos on p(A) with full reorthogonalization,
@@ -142,24 +145,76 @@ def filter_bytes_per_launch(n, nnz, r, s_val=8, s_vec=8, s_acc=8, recurrence="fo
 
 
 def filter_flops_per_launch(n, nnz, r):
-    # one FMA per stored entry and column (the shift -cI and the scale 2/e are
-    # folded into the stored values) plus one FMA per element for the sum
-    return 2 * nnz * r + 2 * n * r
+    # the degree step's arithmetic: a multiply-add per stored entry and column,
+    # and per element the subtraction of Y_{k-1}, the shift and the running sum
+    return 2 * nnz * r + 6 * n * r
 
 
-def cpu_leg(csr, alpha, beta, degree, r, gpu_stats, budget_s=20.0):
-    """Times the CPU oracle on a bounded sample and scales it to a whole solve.
+# bytes per stored value, vector element and running-sum element of each filter arithmetic
+ELEMENT_BYTES = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "bf16": (2, 2, 4), "df64": (8, 8, 8), "fx64": (8, 8, 8)}
+KERNEL_NAMES = {
+    ("fp64", "forward"): "cheb_sell_kernel<FP64> (fused Chebyshev degree step, SELL-32)",
+    ("fp64", "clenshaw"): "clen_sell_kernel<FP64> (Clenshaw degree step, SELL-32)",
+    ("fp32", "forward"): "cheb_sell_kernel<FP32>", ("fp32", "clenshaw"): "clen_sell_kernel<FP32>",
+    ("bf16", "forward"): "cheb_sell_kernel<BF16>", ("bf16", "clenshaw"): "clen_sell_kernel<BF16>",
+    ("df64", "forward"): "cheb_sell_kernel<double-FP32>", ("df64", "clenshaw"): "clen_sell_kernel<double-FP32>",
+    ("fx64", "forward"): "fx_sell_kernel (64-bit fixed-point degree step, SELL-32 staged by bulk copies)",
+}
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
+# is now, on this workload (profiles/); absent where no capture of the current
+# kernel exists.
+TRAFFIC = {}
 
-    Sample: the oracle's bound estimation, then block Lanczos steps of its
-    filtered Lanczos procedure (Clenshaw filter of the same degree + CGS2 full
-    reorthogonalization) until about `budget_s` seconds have passed. A whole
-    oracle solve of this workload takes as many block steps as the GPU run
-    (`gpu_stats['iters']`) with the basis growing by r vectors per step, so the
-    sampled per-step filter cost and the reorthogonalization cost per basis
-    vector are scaled to that run; the oracle's Rayleigh-Ritz checks are not
-    counted (which favours the CPU).
+
+def alu_fraction(flz, fprec, csr, r, ms_per_launch):
+    """The degree step's arithmetic against the measured rate of its pipe: FP64
+    FMAs for FP64; for the fixed-point step its 32-bit integer multiply-adds (7
+    per product of a stored entry and a vector element, 2 ops each, and as many
+    again per element for the running sum)."""
+    try:
+        if fprec == "fp64":
+            peak = flz.flz_measure_alu_peak(0)
+            work = filter_flops_per_launch(csr.n, csr.nnz, r)
+            unit, what = "TFLOP/s", "FP64 flops (2 nnz r + 6 n r)"
+        elif fprec == "fx64":
+            peak = flz.flz_measure_alu_peak(1)
+            work = 2 * 7 * (csr.nnz + csr.n) * r
+            unit, what = "Tops/s", "32-bit integer multiply-add ops (2 x 7 per product)"
+        else:
+            return None
+    except Exception as exc:  # the probe is a measurement aid; its failure is reported, not fatal
+        return {"error": str(exc)}
+    achieved = work / (ms_per_launch * 1e-3)
+    return {"achieved": achieved / 1e12, "peak": peak / 1e12, "unit": unit, "frac": achieved / peak,
+            "work_per_launch": work, "work": what, "peak_source": "measured (flz_measure_alu_peak)"}
+
+
+def oracle_run_shape():
+    """Block steps and convergence checks of the oracle's own solve of this workload at the benchmark's
+    degree (tests/golden/config2_reference.json, written by tests/golden/make_config2_reference.py)."""
+    ref = json.load(open(os.path.join(ROOT, "tests", "golden", "config2_reference.json")))
+    o = ref["oracle_at_bench_degree"]
+    return int(o["iters"]), int(o["checks"]), int(o["degree"]), int(ref["count"])
+
+
+def cpu_leg(csr, alpha, beta, degree, r, budget_s=20.0):
+    """Times the CPU oracle on a bounded sample and scales it to the oracle's whole solve.
+
+    The oracle's own run of this workload at the benchmark's degree takes `iters`
+    block steps with a convergence check every 10 (oracle_run_shape). Sample, in
+    the oracle's own code: its bound estimation; block steps of its Clenshaw
+    filter of the same degree until about `budget_s` seconds have passed (at
+    least one); one full-reorthogonalization step as the oracle does it (basis
+    concatenation, CGS2, Householder QR) against a basis of the run's average
+    size r iters / 2; and the Ritz-pair work of a check (Ritz vector x = Q_k y,
+    A x, Rayleigh quotient, residual) for a few pairs at that size. Scaled:
+    the filter cost per step times `iters`; the reorthogonalization step (linear
+    in the basis size) times `iters`; the two converged checks of the run (count
+    stable over two checks) walking count + guard pairs each at the final basis
+    size (earlier, partial walks are not counted, which favours the CPU).
     """
     from oracle import chebyshev, lanczos
+    iters, checks, _, count = oracle_run_shape()
     A = csr.to_scipy()
     t0 = time.time()
     lmin, lmax, _ = lanczos.lanczos_bounds(A, random_normal_block(csr.n, 1, 12)[:, 0], 60)
@@ -167,46 +222,73 @@ def cpu_leg(csr, alpha, beta, degree, r, gpu_stats, budget_s=20.0):
     c, e, am, bm = chebyshev.map_interval(alpha, beta, lmin, lmax)
     coeffs = chebyshev.filter_coefficients(max(am, -1.0), min(bm, 1.0), degree)
     Q, _ = np.linalg.qr(random_normal_block(csr.n, r, 11))
-    blocks = [Q]
-    t_filter, t_orth, steps = 0.0, 0.0, 0
-    orth_units = 0.0
+    t_filter, steps = 0.0, 0
     t_start = time.time()
-    while time.time() - t_start < budget_s and steps < 200:
+    while (steps == 0 or time.time() - t_start < budget_s) and steps < 200:
         ta = time.time()
-        W = chebyshev.clenshaw_apply(A, c, e, coeffs, blocks[-1])
-        tb = time.time()
-        Qall = np.hstack(blocks)
-        C1 = Qall.T @ W
-        W = W - Qall @ C1
-        C2 = Qall.T @ W
-        W = W - Qall @ C2
-        Qn, _ = np.linalg.qr(W)
-        blocks.append(Qn)
-        tc = time.time()
-        t_filter += tb - ta
-        t_orth += tc - tb
-        orth_units += len(blocks) - 1
+        W = chebyshev.clenshaw_apply(A, c, e, coeffs, Q)
+        t_filter += time.time() - ta
         steps += 1
+    # one reorthogonalization step against nb = iters / 2 blocks, as the oracle does it
+    nb = max(1, iters // 2)
+    rng = np.random.default_rng(5)
+    blocks = [rng.standard_normal((csr.n, r)) / np.sqrt(csr.n) for _ in range(nb)]
+    tb = time.time()
+    Qall = np.hstack(blocks)
+    C1 = Qall.T @ W
+    W2 = W - Qall @ C1
+    C2 = Qall.T @ W2
+    W2 = W2 - Qall @ C2
+    np.linalg.qr(W2)
+    t_orth_mid = time.time() - tb
+    # Ritz-pair work of a check at basis size nb r (one pair at a time, as the oracle)
+    pairs = 4
+    tp = time.time()
+    for _ in range(pairs):
+        y = rng.standard_normal(Qall.shape[1])
+        x = Qall @ y
+        x = x / np.linalg.norm(x)
+        Ax = A @ x
+        lam = float(x @ Ax)
+        _ = float(np.linalg.norm(Ax - lam * x))
+    t_pair_mid = (time.time() - tp) / pairs
+    guard = max(r, 3)
     per_filter = t_filter / steps
-    per_orth_block = t_orth / orth_units  # seconds per (step x basis block)
-    iters = int(gpu_stats["iters"])
-    total = t_bounds + iters * per_filter + per_orth_block * iters * (iters + 1) / 2.0
+    walk = 2 * (count + guard) * t_pair_mid * 2.0  # at the final basis size, twice the sampled one
+    total = t_bounds + iters * (per_filter + t_orth_mid) + walk
+    threads = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS")
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {
         "seconds_per_solve": total,
-        "sample": (f"oracle bounds ({t_bounds:.1f} s) + {steps} block steps of FLP (degree {degree}, r = {r}) "
-                   f"in {t_filter + t_orth:.1f} s, scaled to the GPU run's {iters} block steps"),
-        "cores": len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count(),
+        "sample": (f"oracle bounds ({t_bounds:.1f} s), {steps} Clenshaw filters (degree {degree}, r = {r}) in "
+                   f"{t_filter:.1f} s, one CGS2 + QR step and {pairs} Ritz pairs at basis size {nb * r}, scaled to "
+                   f"the oracle's own run: {iters} block steps, {checks} checks, 2 converged walks of "
+                   f"{count + guard} pairs"),
+        "cores": int(threads) if threads else cores,
+        "phases_s": {"bounds": t_bounds, "filter": iters * per_filter, "orth": iters * t_orth_mid, "checks": walk},
     }
 
 
+def cpu_leg_threads(threads, degree, r, budget_s):
+    """cpu_leg in a child process whose BLAS uses `threads` threads (set before numpy loads)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--mode", "cpu_leg", "--degree", str(degree),
+                          "--block-size", str(r), "--cpu-budget", str(budget_s)],
+                         capture_output=True, text=True, env=env, timeout=1200)
+    if out.returncode != 0:
+        raise RuntimeError(f"cpu leg failed: {out.stderr[-2000:]}")
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 def run_reference(args):
+    """The oracle on the host cores: every step a bounded sample (cpu_leg) scaled to the oracle's whole solve."""
     csr = make_matrix()
     alpha, beta = CONFIG2["alpha"], CONFIG2["beta"]
-    ref_stats = {"iters": CONFIG2["reference_iters"]}
     vals = []
     for _ in range(args.warmup + args.steps):
-        leg = cpu_leg(csr, alpha, beta, args.degree, args.block_size, ref_stats, budget_s=args.cpu_budget)
-        vals.append(leg)
+        vals.append(cpu_leg(csr, alpha, beta, args.degree, args.block_size, budget_s=args.reference_budget))
     timed = vals[args.warmup:]
     per_solve = float(np.mean([v["seconds_per_solve"] for v in timed]))
     value = CONFIG2["count"] / per_solve
@@ -256,7 +338,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--degree", type=int, default=BENCH_DEGREE)
     ap.add_argument("--block-size", type=int, default=4)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16", "df64", "fx64"])
+    ap.add_argument("--precision", default="fx64", choices=["fp64", "fp32", "bf16", "df64", "fx64"],
+                    help="filter arithmetic (fx64: the 64-bit fixed-point filter, FP64-class; the rest of the "
+                         "solver is FP64 in every mode)")
     ap.add_argument("--recurrence", default="forward", choices=["forward", "clenshaw"])
     ap.add_argument("--damping", default="none", choices=["none", "jackson", "sigma"],
                     help="filter damping (the paper uses none)")
@@ -264,7 +348,10 @@ def main():
                     help="where the full reorthogonalization runs (auto: tensor cores for r <= 4)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--check-every", type=int, default=CONFIG2["check_every"])
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-budget", type=float, default=12.0,
+                    help="seconds of oracle block steps per CPU-baseline sample (each of 1 thread and all threads)")
+    ap.add_argument("--reference-budget", type=float, default=3.0,
+                    help="seconds of oracle block steps per --impl reference step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
@@ -273,13 +360,17 @@ def main():
     ap.add_argument("--ortho-n", type=int, default=1_000_000, help="rows of the --mode ortho basis")
     ap.add_argument("--ortho-basis", type=int, default=120, help="columns of the --mode ortho basis")
     ap.add_argument("--mode", default="solve", choices=["solve", "filter", "batch", "table2", "graph", "slices",
-                                                        "ortho", "config3"],
+                                                        "ortho", "config3", "cpu_leg"],
                     help="solve: whole flz_solve per step (default); filter: only flz_filter_apply at the "
                          "solver's shape, for the kernel roofline and profiling")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.mode == "cpu_leg":  # child process of cpu_leg_threads
+        leg = cpu_leg(make_matrix(), CONFIG2["alpha"], CONFIG2["beta"], args.degree, args.block_size, args.cpu_budget)
+        print(json.dumps(leg))
+        return
     if args.impl == "reference":
         if rank == 0:
             run_reference(args)
@@ -366,38 +457,29 @@ def main():
     value = total_pairs / total_time
     st = stats_list[-1]
 
-    # Roofline of the dominant kernel (the fused Chebyshev step), from the
-    # solver's own CUDA-event timing of its filter applications.
+    # Roofline of the dominant kernel (the fused Chebyshev degree step), from
+    # the solver's own CUDA-event timing of its filter applications: the roof is
+    # HBM (algorithmic bytes per launch / launch time, against the measured copy
+    # rate); the arithmetic fraction is reported beside it against the rate of
+    # the pipe the kernel computes on, measured on this GPU (flz_measure_alu_peak).
     launches_filter = st["iters"] * st["degree"]
     ms_per_launch = st["ms_filter"] / max(launches_filter, 1)
-    sizes = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "bf16": (2, 2, 4), "df64": (8, 8, 8), "fx64": (8, 8, 8)}[args.precision]
-    nbytes = filter_bytes_per_launch(csr.n, csr.nnz, args.block_size, *sizes, recurrence=args.recurrence)
-    nflops = filter_flops_per_launch(csr.n, csr.nnz, args.block_size)
+    fprec = {0: "fp64", 1: "fp32", 2: "bf16", 3: "df64", 4: "fx64"}[st["filter_precision"]]
+    nbytes = filter_bytes_per_launch(csr.n, csr.nnz, args.block_size, *ELEMENT_BYTES[fprec],
+                                     recurrence=args.recurrence)
     hbm, hbm_src = peaks()
     achieved_gbs = nbytes / (ms_per_launch * 1e-3) / 1e9
-    achieved_tflops = nflops / (ms_per_launch * 1e-3) / 1e12
-    # FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
-    # DRAM bytes per launch of the FP64 forward SELL-32 step on this workload, from
-    # one ncu capture (profiles/cheb_sell_kernel_fp64_laplacian3d_100cubed_r4.md)
-    traffic = 179.70e6 + 34.64e6 if (args.precision == "fp64" and args.recurrence == "forward") else None
     roofline = {
-        "kernel": ("clen_sell_kernel (Clenshaw degree step, SELL-32)" if args.recurrence == "clenshaw"
-                   else "cheb_sell_kernel (fused Chebyshev degree step, SELL-32)"),
-        "bound": "alu" if args.precision == "fp64" else "hbm",
-        "achieved": achieved_tflops if args.precision == "fp64" else achieved_gbs,
-        "peak": fp64_peak if args.precision == "fp64" else hbm,
-        "unit": "TFLOP/s" if args.precision == "fp64" else "GB/s",
-        "frac": (achieved_tflops / fp64_peak) if args.precision == "fp64" else achieved_gbs / hbm,
-        "traffic": traffic,
-        "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": hbm, "hbm_frac": achieved_gbs / hbm,
-        "hbm_peak_source": hbm_src, "algorithmic_bytes_per_launch": nbytes, "flops_per_launch": nflops,
-        "ms_per_launch": ms_per_launch,
+        "kernel": KERNEL_NAMES[(fprec, args.recurrence)],
+        "bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm,
+        "peak_source": hbm_src, "traffic": TRAFFIC.get((fprec, args.recurrence)),
+        "algorithmic_bytes_per_launch": nbytes, "ms_per_launch": ms_per_launch,
+        "alu": alu_fraction(flz, fprec, csr, args.block_size, ms_per_launch),
     }
 
     fp64_vals = flz.flz_get_eigenvalues(s).copy()
     variants = None
-    if not args.no_variants and args.precision == "fp64":
+    if not args.no_variants and args.precision == "fx64":
         variants = variant_leg(flz, torch, h, p, alpha, beta, stream, flush, fp64_vals, args)
 
     batch = None
@@ -410,9 +492,15 @@ def main():
 
     cpu = None
     if not args.no_cpu and rank == 0:
-        leg = cpu_leg(csr, alpha, beta, args.degree, args.block_size, st, budget_s=args.cpu_budget)
-        cpu = {"value": CONFIG2["count"] / leg["seconds_per_solve"], "unit": "eigenpairs/s",
-               "cores": leg["cores"], "kind": "oracle", "sample": leg["sample"]}
+        legs = {t: cpu_leg_threads(t, args.degree, args.block_size, args.cpu_budget)
+                for t in (len(os.sched_getaffinity(0)), 1)}
+        allt, one = legs[max(legs)], legs[1]
+        cpu = {"value": CONFIG2["count"] / allt["seconds_per_solve"], "unit": "eigenpairs/s",
+               "cores": allt["cores"], "kind": "oracle", "sample": allt["sample"], "phases_s": allt["phases_s"],
+               "one_thread": {"value": CONFIG2["count"] / one["seconds_per_solve"], "cores": 1,
+                              "phases_s": one["phases_s"]},
+               "gpu_speedup": {"vs_all_threads": value / (CONFIG2["count"] / allt["seconds_per_solve"]),
+                               "vs_one_thread": value / (CONFIG2["count"] / one["seconds_per_solve"])}}
 
     flz.flz_solver_destroy(s)
     flz.flz_matrix_destroy(h)
@@ -435,17 +523,19 @@ def main():
 
 
 def variant_leg(flz, torch, h, p, alpha, beta, stream, flush, ref_vals, args):
-    """Filter variants versus the FP64 forward recurrence on the same workload
-    (everything but the filter stays FP64): double-FP32 (hi + lo FP32 pairs)
-    and the Clenshaw recurrence at the FP64 tolerance, and FP32 / BF16 storage
+    """Filter variants versus the headline (fixed-point) run on the same workload
+    (everything but the filter stays FP64): plain FP64 (tensor-core or CUDA-core
+    reorthogonalization), double-FP32 (hi + lo FP32 pairs) and the Clenshaw
+    recurrence at the FP64 tolerance, and FP32 / BF16 storage
     at the residual those reach (1e-6, 1e-3), each with its eigenvalue
-    difference to the FP64 run. Times 2 solves after 1 warm-up, device time per
+    difference to the headline run. Times 2 solves after 1 warm-up, device time per
     solve. `value` counts pairs with residual <= 1e-8."""
     out = {}
     # the reduced-precision filters at the residual they can reach, double-FP32 at the FP64 tolerance
     F, C = flz.FLZ_REC_FORWARD, flz.FLZ_REC_CLENSHAW
     T, CC = flz.FLZ_ORTHO_AUTO, flz.FLZ_ORTHO_CUDA_CORES
-    for name, prec, tol, rec, ortho in (("fp64_cuda_core_ortho", flz.FLZ_PREC_FP64, p.tol, F, CC),
+    for name, prec, tol, rec, ortho in (("fp64_filter", flz.FLZ_PREC_FP64, p.tol, F, T),
+                                        ("fp64_cuda_core_ortho", flz.FLZ_PREC_FP64, p.tol, F, CC),
                                         ("fp64_clenshaw", flz.FLZ_PREC_FP64, p.tol, C, T),
                                         ("df64_filter", flz.FLZ_PREC_DF64, p.tol, F, T),
                                         ("df64_clenshaw", flz.FLZ_PREC_DF64, p.tol, C, T),
@@ -481,7 +571,7 @@ def variant_leg(flz, torch, h, p, alpha, beta, stream, flush, ref_vals, args):
             "status": flz.flz_status_string(st), "value": float(np.sum(res <= 1e-8)) / float(np.mean(times)),
             "unit": "eigenpairs/s", "ms_per_solve": 1e3 * float(np.mean(times)), "count": int(vals.shape[0]),
             "tol": q.tol, "solves_per_s": 1.0 / float(np.mean(times)),
-            "max_abs_eig_diff_vs_fp64": float(np.max(np.abs(vals - ref_vals))) if same and vals.size else None,
+            "max_abs_eig_diff_vs_headline": float(np.max(np.abs(vals - ref_vals))) if same and vals.size else None,
             "max_residual": float(np.max(res)) if res.size else None,
             "ms_filter": stats["ms_filter"], "ms_orth": stats["ms_orth"], "ms_check": stats["ms_check"],
             "iters": stats["iters"], "ortho": ["auto", "cuda_cores", "tensor"][stats["ortho"]],
@@ -735,7 +825,7 @@ def graph_mode(flz, torch, args):
                      "eigenpairs_per_s_at_1e-8": float(np.sum(res <= 1e-8)) / (e0.elapsed_time(e1) / 1e3),
                      "ms_filter": x["ms_filter"], "ms_orth": x["ms_orth"], "ms_check": x["ms_check"],
                      "ortho": ["auto", "cuda_cores", "tensor"][x["ortho"]], "lmin": x["lmin"], "lmax": x["lmax"],
-                     "max_abs_eig_diff_vs_fp64": (float(np.max(np.abs(vals - ref)))
+                     "max_abs_eig_diff_vs_headline": (float(np.max(np.abs(vals - ref)))
                                                   if ref is not None and vals.shape == ref.shape and vals.size else None)}
         flz.flz_solver_destroy(s)
     flz.flz_matrix_destroy(h)
@@ -860,8 +950,7 @@ def filter_mode(flz, torch, csr, prec, args):
     flz.flz_matrix_destroy(h)
     launches = m + (0 if prec == flz.FLZ_PREC_FP64 else 1)
     ms = float(np.mean(times)) / m
-    sizes = {flz.FLZ_PREC_FP64: (8, 8, 8), flz.FLZ_PREC_FP32: (4, 4, 4), flz.FLZ_PREC_BF16: (2, 2, 4),
-             flz.FLZ_PREC_DF64: (8, 8, 8), flz.FLZ_PREC_FX64: (8, 8, 8)}[prec]
+    sizes = ELEMENT_BYTES[args.precision]
     nbytes = filter_bytes_per_launch(csr.n, csr.nnz, r, *sizes, recurrence=args.recurrence)
     hbm, src = peaks()
     print(json.dumps({"mode": "filter", "precision": args.precision, "recurrence": args.recurrence,

@@ -6,7 +6,6 @@ in [alpha, beta] at the low end of the spectrum. beta sits at the midpoint of
 the widest spectral gap among eigenvalues 95..110 and `count` is the number of
 eigenvalues in [alpha, beta]; both were computed by the CPU oracle with
 tests/golden/make_config2_reference.py (tests/golden/config2_reference.json).
-`reference_iters` is the oracle run's block-step count at degree 60, r = 4.
 
 CONFIG3: real-space Hamiltonian stand-in: 4th-order 13-point FD -Laplacian on
 a 120^3 grid (n = 1.728e6, nnz = 22,204,800) plus 64 negative Gaussian wells
@@ -32,7 +31,6 @@ CONFIG2 = {
     "count": 105,
     "degree": 60,
     "check_every": 10,
-    "reference_iters": 120,
 }
 
 CONFIG3 = {
