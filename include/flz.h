@@ -138,6 +138,12 @@ typedef struct flz_params {
                            smoothed step with linear ramps this wide (mapped units), see
                            flz_smoothed_step_coefficients */
   int32_t ortho;        /* flz_ortho; default FLZ_ORTHO_AUTO */
+  int32_t refine;       /* FP32 / BF16 precision only. 0 (default): the solve stops at tol or at the
+                           filter's rounding floor. 1: the filtered Lanczos procedure runs to
+                           max(tol, 1e-6) (FP32) or max(tol, 1e-3) (BF16), then its wanted, guard and
+                           extra Ritz pairs are refined to tol by filtered subspace iteration with the
+                           FX64 filter (FP64 where it does not apply) and Rayleigh-Ritz on A in FP64: the
+                           mixed-precision form (not in the paper). See flz_stats.refine_sweeps. */
 } flz_params;
 
 /* Per-solve statistics (the columns of Tables 2 and 3, plus bounds). */
@@ -162,6 +168,9 @@ typedef struct flz_stats {
   int64_t kernel_launches; /* CUDA kernels this solve launched */
   int32_t ortho;        /* flz_ortho the reorthogonalization ran on (CUDA_CORES or TENSOR) */
   int32_t filter_precision; /* flz_precision the filter ran in (FX64 requested may run as FP64) */
+  int32_t refine_sweeps;    /* refinement sweeps (params.refine), 0 if none */
+  int32_t refine_degree;    /* largest filter degree of a refinement sweep */
+  double ms_refine;         /* refinement time (included in ms_total) */
 } flz_stats;
 
 /* ---- status and parameters ------------------------------------------------ */
@@ -262,6 +271,13 @@ flz_status flz_jackson_factors(int32_t degree, double* out);
  * multiplies the coefficients by them: the Gibbs overshoot shrinks (to about
  * 1 % at high degree) with a narrower transition than Jackson's. */
 flz_status flz_lanczos_sigma_factors(int32_t degree, double* out);
+/* The damping polynomial of the mixed-precision refinement (params.refine;
+ * not in the paper): Chebyshev coefficients out[0..degree] (host) in z on
+ * [-1, 1] of p(z) = T_d(a z + b) / T_d(b - a), where z -> a z + b maps
+ * [zc, 1] onto [-1, 1] (d = degree). p(-1) = 1, |p| <= 1 on [-1, 1], and
+ * |p| <= 1 / |T_d(b - a)| on [zc, 1]: it damps the spectrum above zc relative
+ * to the pairs below it. Requires -1 < zc < 1. */
+flz_status flz_damping_coefficients(double zc, int32_t degree, double* out);
 /* Eq. (optimaldegree): least m >= 1 with ||p_m - phi|| < eps ||phi|| in the
  * weighted Chebyshev 2-norm. Host only. CAPACITY if no m <= max_degree fits. */
 flz_status flz_filter_degree(double alpha, double beta, double eps, int32_t max_degree, int32_t* degree);

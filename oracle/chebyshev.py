@@ -269,3 +269,17 @@ def clenshaw_apply_exact(S2, b: np.ndarray, V: np.ndarray) -> np.ndarray:
             N, E = p.N[i], p.E
             out[i, t] = float(N << E) if E >= 0 else N / (1 << -E)
     return out
+
+
+def damping_filter_coefficients(zc: float, d: int) -> np.ndarray:
+    """Chebyshev coefficients in z of T_d(a z + b) / T_d(b - a), [zc, 1] -> [-1, 1] by z -> a z + b.
+
+    The refinement of the mixed-precision form (not in the paper) damps the
+    spectrum above zc: on [zc, 1] this is a Chebyshev polynomial of that
+    interval, scaled to 1 at z = -1. Computed as numpy's Chebyshev series T_d
+    with domain [zc, 1], re-expanded on [-1, 1]. A library primitive serves as
+    the step.
+    """
+    T = np.polynomial.Chebyshev.basis(d, domain=[zc, 1.0])
+    c = T.convert(domain=[-1.0, 1.0], kind=np.polynomial.Chebyshev).coef
+    return c / T(-1.0)

@@ -43,7 +43,7 @@ FLZ_ORTHO_AUTO, FLZ_ORTHO_CUDA_CORES, FLZ_ORTHO_TENSOR = 0, 1, 2
 EXPORTED = (
     "flz_status_string", "flz_last_error", "flz_params_default",
     "flz_matrix_create_csr", "flz_matrix_destroy", "flz_matrix_info", "flz_matrix_format",
-    "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_smoothed_step_coefficients", "flz_jackson_factors", "flz_lanczos_sigma_factors", "flz_filter_degree", "flz_spectrum_bounds",
+    "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_smoothed_step_coefficients", "flz_jackson_factors", "flz_lanczos_sigma_factors", "flz_filter_degree", "flz_damping_coefficients", "flz_spectrum_bounds",
     "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_sym_eig",
     "flz_basis_project", "flz_basis_orthogonalize", "flz_basis_multiply", "flz_measure_alu_peak", "flz_tc_mma_probe", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve", "flz_solve_sliced",
     "flz_get_count", "flz_get_eigenvalues", "flz_get_eigenvectors", "flz_get_residuals", "flz_get_stats",
@@ -60,6 +60,7 @@ class flz_params(ctypes.Structure):
         ("bounds_steps", ctypes.c_int32), ("seed", ctypes.c_uint64), ("lmin", ctypes.c_double),
         ("lmax", ctypes.c_double), ("damping", ctypes.c_int32),
         ("recurrence", ctypes.c_int32), ("transition", ctypes.c_double), ("ortho", ctypes.c_int32),
+        ("refine", ctypes.c_int32),
     ]
 
 
@@ -73,6 +74,7 @@ class flz_stats(ctypes.Structure):
         ("ms_filter", ctypes.c_double), ("ms_orth", ctypes.c_double), ("ms_check", ctypes.c_double),
         ("ms_total", ctypes.c_double), ("basis_vectors", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64), ("ortho", ctypes.c_int32), ("filter_precision", ctypes.c_int32),
+        ("refine_sweeps", ctypes.c_int32), ("refine_degree", ctypes.c_int32), ("ms_refine", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -116,6 +118,7 @@ def lib() -> ctypes.CDLL:
         "flz_smoothed_step_coefficients": (ctypes.c_int, [_dbl, _dbl, _dbl, _i32, _vp]),
         "flz_lanczos_sigma_factors": (ctypes.c_int, [_i32, _vp]),
         "flz_filter_degree": (ctypes.c_int, [_dbl, _dbl, _dbl, _i32, ctypes.POINTER(_i32)]),
+        "flz_damping_coefficients": (ctypes.c_int, [_dbl, _i32, _vp]),
         "flz_spectrum_bounds": (ctypes.c_int, [_vp, _i32, _i32, _u64, _pdbl, _pdbl, _vp]),
         "flz_band_eigenvalues": (ctypes.c_int, [_i32, _i32, _vp, _vp]),
         "flz_band_eigenvectors": (ctypes.c_int, [_i32, _i32, _vp, _vp, _i32, _vp, _vp, _u64]),
@@ -257,6 +260,12 @@ def flz_smoothed_step_coefficients(alpha, beta, delta, degree) -> np.ndarray:
 def flz_jackson_factors(degree) -> np.ndarray:
     out = np.empty(int(degree) + 1)
     _check(lib().flz_jackson_factors(int(degree), _ptr(out)))
+    return out
+
+
+def flz_damping_coefficients(zc, degree) -> np.ndarray:
+    out = np.empty(int(degree) + 1)
+    _check(lib().flz_damping_coefficients(float(zc), int(degree), _ptr(out)))
     return out
 
 

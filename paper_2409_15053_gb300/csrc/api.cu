@@ -256,6 +256,13 @@ flz_status flz_lanczos_sigma_factors(int32_t degree, double* out) {
   FLZ_API_END
 }
 
+flz_status flz_damping_coefficients(double zc, int32_t degree, double* out) {
+  FLZ_API_BEGIN
+  if (!out || degree < 0 || !(zc > -1.0 && zc < 1.0)) fail(FLZ_ERR_INVALID_ARG, "need -1 < zc < 1, degree >= 0");
+  flz::damping_coefficients(zc, degree, out);
+  FLZ_API_END
+}
+
 flz_status flz_filter_degree(double alpha, double beta, double eps, int32_t max_degree, int32_t* degree) {
   FLZ_API_BEGIN
   if (!degree || max_degree < 1 || !(eps > 0.0)) fail(FLZ_ERR_INVALID_ARG, "bad degree arguments");
@@ -540,7 +547,7 @@ flz_status flz_solver_create(flz_matrix* A, const flz_params* params, flz_solver
   if (p.degree < 0 || p.max_degree < 1 || p.check_every < 1 || !(p.tol > 0.0) || !(p.degree_eps > 0.0) ||
       p.bounds_steps < 1 || p.max_basis < 0 || p.guard < 0 || p.damping < 0 || p.damping > 2 || !(p.transition >= 0.0) ||
       (p.recurrence != FLZ_REC_FORWARD && p.recurrence != FLZ_REC_CLENSHAW) || p.ortho < FLZ_ORTHO_AUTO ||
-      p.ortho > FLZ_ORTHO_TENSOR)
+      p.ortho > FLZ_ORTHO_TENSOR || p.refine < 0 || p.refine > 1)
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.ortho == FLZ_ORTHO_TENSOR && (!flz::TcBasis::supported(p.block_size) || p.precision == FLZ_PREC_DF64))
     fail(FLZ_ERR_INVALID_ARG, "tensor-core reorthogonalization needs an FP64 basis (not the double-FP32 precision)");

@@ -269,6 +269,26 @@ bool fx_filter_apply(flz_matrix* A, double c, double e, const double* coeffs, in
                      double* W, cudaStream_t st);
 bool fx_supported(int r);
 void fx_check_flag(flz_matrix* A);
+// ---- refine.cu ---------------------------------------------------------------------
+// Filtered subspace iteration in FP64-class arithmetic with Rayleigh-Ritz on A,
+// polishing the pairs of a reduced-precision solve (see refine.cu).
+struct RefineArgs {
+  double alpha, beta, lmin, lmax, tol;
+  int max_sweeps, max_degree;
+  std::vector<double> filter;  // the solve's filter coefficients (interior windows)
+};
+struct RefineResult {
+  int sweeps = 0, kp = 0, filter_precision = 0;
+  bool converged = false;
+  std::vector<int> index;          // columns of X holding the wanted pairs
+  std::vector<double> vals, res;   // their Rayleigh quotients and residuals / ||A||
+  std::vector<int> degrees;        // filter degree of each sweep
+  double ms = 0.0;
+};
+// X: n x kp (kp a multiple of 16) as blocks of 16 columns, row-major; refined in place.
+RefineResult refine(flz_matrix* A, const RefineArgs& g, double* X, int kp, cudaStream_t st);
+// Chebyshev coefficients of T_d(a z + b) / T_d(-a + b), [zc, 1] mapped onto [-1, 1] by z -> a z + b.
+void damping_coefficients(double zc, int d, double* out);
 // ---- probe.cu ----------------------------------------------------------------------
 // Measured throughput of FP64 FMAs (kind 0, flop/s) or 32-bit integer
 // multiply-adds (kind 1, 2 ops each) on the current device.

@@ -422,8 +422,13 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   // If x has ||Ax - lambda x|| <= tol ||A|| then ||p(A)x - theta x|| <=
   // max|p'| tol ||A|| / e, and max|p'| <= 1.1 m^2 on [-1, 1] (Markov, |p| <= 1.1):
   // a pair whose p(A) residual exceeds this cannot pass the A-residual test.
-  const double p_gate = std::min(1e-2, 10.0 * 1.1 * (double)m * m * p.tol * anorm / e);
+  // With refinement (reduced-precision filter) the filtered Lanczos phase stops
+  // at the filter's floor and the refinement brings the pairs to p.tol.
+  const bool refining = p.refine == 1 && (p.precision == FLZ_PREC_FP32 || p.precision == FLZ_PREC_BF16);
+  const double tol = refining ? std::max(p.tol, p.precision == FLZ_PREC_FP32 ? 1e-6 : 1e-3) : p.tol;
+  const double p_gate = std::min(1e-2, 10.0 * 1.1 * (double)m * m * tol * anorm / e);
   std::vector<double> found_vals, found_res;
+  std::vector<double> lastT, lastTheta;  // the last check's T_k and its eigenvalues (refinement)
   int64_t found = 0;
   for (int j = 0; j < nb_cap; ++j) {
     E.step(j, filt, P, 1.0);
@@ -516,7 +521,7 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
         const double xx = h[t];
         const double lam = h[32 + t];
         const double res = std::sqrt(std::max(h[48 + t], 0.0) / std::max(xx, 1e-300)) / anorm;
-        if (!(res <= p.tol)) {
+        if (!(res <= tol)) {
           all_small = false;
           walk_done = true;
           break;
@@ -560,6 +565,10 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
     converged = complete && (full_space || (prev_count >= 0 && inside == prev_count));
     prev_count = complete ? inside : -1;
     ms_check += ms_since(tc);
+    if (refining && (converged || last)) {
+      lastT.swap(T);
+      lastTheta.swap(theta);
+    }
     if (converged || last) break;
   }
   FLZ_CUDA(cudaStreamSynchronize(st));
@@ -567,6 +576,64 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
     FLZ_CUDA(cudaMemcpy(E.tcb->status_host, E.tcb->status.p, sizeof(int), cudaMemcpyDeviceToHost));
     E.tcb->check_status();
   }
+  if constexpr (std::is_same<BT, double>::value)
+    if (refining && converged && !lastT.empty()) {
+      // Ritz vectors of the leading kp pairs by p(A) Ritz value: the wanted and
+      // guard pairs and as many again as a third of the wanted (at least 16),
+      // in whole blocks of 16 columns
+      const int K = k * r;
+      int kp = (int)(found + guard + std::max<int64_t>(16, found / 3));
+      kp = std::min((kp + 15) / 16 * 16, K / 16 * 16);
+      if (kp >= 16) {
+        std::vector<int> idx(kp);
+        for (int i = 0; i < kp; ++i) idx[i] = K - 1 - i;  // descending theta
+        std::vector<double> Yt;
+        band_eigenvectors(lastT, K, r, lastTheta, idx, Yt, p.seed);
+        DevBuf<double> Xr, Cb;
+        Xr.reserve((size_t)n * kp);
+        Cb.reserve((size_t)K * 16);
+        std::vector<double> hc((size_t)K * 16);
+        for (int b = 0; b < kp / 16; ++b) {
+          for (int t = 0; t < 16; ++t)
+            for (int i = 0; i < K; ++i) hc[(size_t)i * 16 + t] = Yt[(size_t)(16 * b + t) * K + i];
+          FLZ_CUDA(cudaMemcpyAsync(Cb.p, hc.data(), sizeof(double) * K * 16, cudaMemcpyHostToDevice, st));
+          if (E.tcb)
+            E.tcb->multiply(K, Cb.p, 16, 16, Xr.p + (size_t)b * n * 16, 16, st);
+          else
+            basis_update(Qt, k, n, r, Cb.p, 16, 1.0, 0.0, Xr.p + (size_t)b * n * 16, 16, st);
+          FLZ_CUDA(cudaStreamSynchronize(st));  // hc is reused for the next block
+        }
+        RefineArgs ra{s->alpha, s->beta, lmin, lmax, p.tol, 4, std::max(m, 64), coeffs};
+        const RefineResult rr = refine(A, ra, Xr.p, kp, st);
+        stats.refine_sweeps = rr.sweeps;
+        stats.refine_degree = rr.degrees.empty() ? 0 : *std::max_element(rr.degrees.begin(), rr.degrees.end());
+        stats.ms_refine = rr.ms;
+        converged = rr.converged;
+        found = (int64_t)rr.vals.size();
+        found_vals = rr.vals;
+        found_res = rr.res;
+        s->evecs.reserve((size_t)std::max<int64_t>(found, 1) * n);
+        for (int64_t i = 0; i < found; ++i) {
+          const int col = rr.index[i];
+          rows_to_columns(Xr.p + (size_t)(col / 16) * n * 16 + (col % 16), n, 1, 16, s->evecs.p + (size_t)i * n, n, st);
+        }
+        // unit columns
+        DevBuf<double> dv, prt;
+        dv.reserve(2);
+        prt.reserve(column_sums_scratch(n, 1) + 64);
+        for (int64_t i = 0; i < found; ++i) {
+          double* x = s->evecs.p + (size_t)i * n;
+          column_sums(x, x, nullptr, n, 1, 1, 0, dv.p, prt.p, st);
+          double xx = 0.0;
+          FLZ_CUDA(cudaMemcpyAsync(&xx, dv.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+          FLZ_CUDA(cudaStreamSynchronize(st));
+          const double sc = 1.0 / std::sqrt(std::max(xx, 1e-300));
+          FLZ_CUDA(cudaMemcpyAsync(dv.p + 1, &sc, sizeof(double), cudaMemcpyHostToDevice, st));
+          basis_update(x, 1, n, 1, dv.p + 1, 1, 1.0, 0.0, x, 1, st);
+        }
+        FLZ_CUDA(cudaStreamSynchronize(st));
+      }
+    }
 
   // sort ascending
   std::vector<int> perm(found);

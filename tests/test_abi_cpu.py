@@ -200,3 +200,13 @@ def test_dense_symmetric_eigensolver_on_laplacian_closed_form():
         u = np.sin(k * i * np.pi / (K + 1))
         u /= np.linalg.norm(u)
         assert abs(abs(u @ Z[:, k - 1]) - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("zc,d", [(-0.9, 12), (-0.98, 40), (0.3, 7)])
+def test_damping_coefficients_match_the_oracle(zc, d):
+    from oracle import chebyshev
+    got = flz.flz_damping_coefficients(zc, d)
+    want = chebyshev.damping_filter_coefficients(zc, d)
+    assert got.shape == want.shape and np.max(np.abs(got - want)) < 1e-12
+    with pytest.raises(flz.FlzError):
+        flz.flz_damping_coefficients(1.0, 3)

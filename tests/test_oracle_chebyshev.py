@@ -331,3 +331,22 @@ def test_exact_filter_within_fp64_error_of_the_fp64_clenshaw():
     fp64 = ch.clenshaw_apply(A, c, e, b, V)
     err = np.max(np.abs(exact - fp64))
     assert 0 < err < 32 * 31**2 * 2.0**-53 * 3.0 * np.max(np.abs(V))
+
+
+@pytest.mark.parametrize("zc,d", [(-0.9, 12), (-0.98, 40), (0.3, 7), (-0.5, 1)])
+def test_damping_filter_matches_its_closed_form(zc, d):
+    # p(z) = T_d(a z + b) / T_d(b - a): cos / cosh closed forms of T_d at sample points
+    c = ch.damping_filter_coefficients(zc, d)
+    a, b = 2.0 / (1.0 - zc), -(1.0 + zc) / (1.0 - zc)
+
+    def t(u):
+        return np.cos(d * np.arccos(u)) if abs(u) <= 1 else np.sign(u) ** d * np.cosh(d * np.arccosh(abs(u)))
+
+    z = np.linspace(-1.0, 1.0, 41)
+    got = np.polynomial.chebyshev.chebval(z, c)
+    want = np.array([t(a * x + b) for x in z]) / t(b - a)
+    assert np.max(np.abs(got - want)) < 1e-12
+    assert abs(got[0] - 1.0) < 1e-12
+    assert np.max(np.abs(got)) <= 1.0 + 1e-12
+    inside = z >= zc
+    assert np.max(np.abs(got[inside])) <= 1.0 / abs(t(b - a)) + 1e-12
