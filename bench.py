@@ -526,28 +526,32 @@ def variant_leg(flz, torch, h, p, alpha, beta, stream, flush, ref_vals, args):
     """Filter variants versus the headline (fixed-point) run on the same workload
     (everything but the filter stays FP64): plain FP64 (tensor-core or CUDA-core
     reorthogonalization), double-FP32 (hi + lo FP32 pairs) and the Clenshaw
-    recurrence at the FP64 tolerance, and FP32 / BF16 storage
-    at the residual those reach (1e-6, 1e-3), each with its eigenvalue
+    recurrence at the FP64 tolerance, FP32 / BF16 storage at the residual those
+    reach alone (1e-6, 1e-3), and the same refined to 1e-8 (params.refine: the
+    mixed-precision form), each with its eigenvalue
     difference to the headline run. Times 2 solves after 1 warm-up, device time per
     solve. `value` counts pairs with residual <= 1e-8."""
     out = {}
     # the reduced-precision filters at the residual they can reach, double-FP32 at the FP64 tolerance
     F, C = flz.FLZ_REC_FORWARD, flz.FLZ_REC_CLENSHAW
     T, CC = flz.FLZ_ORTHO_AUTO, flz.FLZ_ORTHO_CUDA_CORES
-    for name, prec, tol, rec, ortho in (("fp64_filter", flz.FLZ_PREC_FP64, p.tol, F, T),
-                                        ("fp64_cuda_core_ortho", flz.FLZ_PREC_FP64, p.tol, F, CC),
-                                        ("fp64_clenshaw", flz.FLZ_PREC_FP64, p.tol, C, T),
-                                        ("df64_filter", flz.FLZ_PREC_DF64, p.tol, F, T),
-                                        ("df64_clenshaw", flz.FLZ_PREC_DF64, p.tol, C, T),
-                                        ("fp32_filter", flz.FLZ_PREC_FP32, 1e-6, F, T),
-                                        ("bf16_filter", flz.FLZ_PREC_BF16, 1e-3, F, T)):
+    for name, prec, tol, rec, ortho, refine in (("fp64_filter", flz.FLZ_PREC_FP64, p.tol, F, T, 0),
+                                                ("fp64_cuda_core_ortho", flz.FLZ_PREC_FP64, p.tol, F, CC, 0),
+                                                ("fp64_clenshaw", flz.FLZ_PREC_FP64, p.tol, C, T, 0),
+                                                ("df64_filter", flz.FLZ_PREC_DF64, p.tol, F, T, 0),
+                                                ("df64_clenshaw", flz.FLZ_PREC_DF64, p.tol, C, T, 0),
+                                                ("fp32_filter", flz.FLZ_PREC_FP32, 1e-6, F, T, 0),
+                                                ("bf16_filter", flz.FLZ_PREC_BF16, 1e-3, F, T, 0),
+                                                ("fp32_filter_refined", flz.FLZ_PREC_FP32, 1e-8, F, T, 1),
+                                                ("bf16_filter_refined", flz.FLZ_PREC_BF16, 1e-8, F, T, 1)):
         q = flz.flz_params_default()
         for f, _ in q._fields_:
             setattr(q, f, getattr(p, f))
         q.precision = prec
         q.recurrence = rec
         q.ortho = ortho
-        q.tol = max(tol, p.tol)
+        q.refine = refine
+        q.tol = tol if refine else max(tol, p.tol)
         sv = flz.flz_solver_create(h, q)
         flz.flz_solver_set_interval(sv, alpha, beta)
         flz.flz_solve(sv, stream)
@@ -575,6 +579,8 @@ def variant_leg(flz, torch, h, p, alpha, beta, stream, flush, ref_vals, args):
             "max_residual": float(np.max(res)) if res.size else None,
             "ms_filter": stats["ms_filter"], "ms_orth": stats["ms_orth"], "ms_check": stats["ms_check"],
             "iters": stats["iters"], "ortho": ["auto", "cuda_cores", "tensor"][stats["ortho"]],
+            "refine_sweeps": stats["refine_sweeps"], "refine_degree": stats["refine_degree"],
+            "ms_refine": stats["ms_refine"],
         }
     return out
 
@@ -837,21 +843,22 @@ def config3_mode(flz, torch, args):
     64 Gaussian wells, n = 1.728e6, 22.2e6 entries), r = 4, checks every 10
     block steps, one warm-up then one timed solve per row: the bound states
     [-6, -0.2] (m = 200), [-6, 0] (m = 300) and [-6, 0.03] reaching into the
-    box continuum (m = 400) in FP64; the widest window also with the CUDA-core
-    reorthogonalization and with the double-FP32 filter and basis; the bound
-    states with double-FP32 Clenshaw."""
+    box continuum (m = 400) with the fixed-point filter; the bound states and
+    the widest window also with the plain FP64 filter, the FP32 filter refined
+    to 1e-8 (params.refine) and the double-FP32 filter and basis."""
     N = CONFIG3["grid"]
     csr = fd4_laplacian_3d(N, gaussian_wells_potential(N, CONFIG3["wells"], seed=CONFIG3["seed"]))
     h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
     stream = torch.cuda.current_stream()
     F, C = flz.FLZ_REC_FORWARD, flz.FLZ_REC_CLENSHAW
     rows = []
-    for beta, m, prec, rec, ortho in ((-0.2, 200, flz.FLZ_PREC_FP64, F, ORTHO[args.ortho]),
-                                      (0.0, 300, flz.FLZ_PREC_FP64, F, ORTHO[args.ortho]),
-                                      (0.03, 400, flz.FLZ_PREC_FP64, F, ORTHO[args.ortho]),
-                                      (0.03, 400, flz.FLZ_PREC_FP64, F, flz.FLZ_ORTHO_CUDA_CORES),
-                                      (0.03, 400, flz.FLZ_PREC_DF64, F, ORTHO[args.ortho]),
-                                      (-0.2, 200, flz.FLZ_PREC_DF64, C, ORTHO[args.ortho])):
+    O = ORTHO[args.ortho]
+    X, D, S, H = flz.FLZ_PREC_FX64, flz.FLZ_PREC_DF64, flz.FLZ_PREC_FP64, flz.FLZ_PREC_FP32
+    for beta, m, prec, rec, ortho, refine in ((-0.2, 200, X, F, O, 0), (-0.2, 200, S, F, O, 0),
+                                              (-0.2, 200, H, F, O, 1), (-0.2, 200, D, C, O, 0),
+                                              (0.0, 300, X, F, O, 0),
+                                              (0.03, 400, X, F, O, 0), (0.03, 400, S, F, O, 0),
+                                              (0.03, 400, H, F, O, 1), (0.03, 400, D, F, O, 0)):
         p = flz.flz_params_default()
         p.block_size = 4
         p.degree = m
@@ -859,7 +866,8 @@ def config3_mode(flz, torch, args):
         p.recurrence = rec
         p.ortho = ortho
         p.check_every = 10
-        p.tol = args.tol
+        p.refine = refine
+        p.tol = 1e-8 if refine else args.tol
         s = flz.flz_solver_create(h, p)
         flz.flz_solver_set_interval(s, CONFIG3["alpha"], beta)
         flz.flz_solve(s, stream)
@@ -873,7 +881,9 @@ def config3_mode(flz, torch, args):
         x = flz.flz_get_stats(s)
         res = flz.flz_get_residuals(s)
         rows.append({"interval": [CONFIG3["alpha"], beta], "m": m,
-                     "precision": {0: "fp64", 3: "df64"}[prec], "recurrence": ["forward", "clenshaw"][rec],
+                     "precision": {0: "fp64", 1: "fp32 refined to 1e-8", 3: "df64", 4: "fx64"}[prec],
+                     "recurrence": ["forward", "clenshaw"][rec], "ms_refine": x["ms_refine"],
+                     "refine_sweeps": x["refine_sweeps"],
                      "ortho": ["auto", "cuda_cores", "tensor"][x["ortho"]], "status": flz.flz_status_string(st),
                      "count": int(x["count"]), "block_steps": int(x["iters"]), "seconds": e0.elapsed_time(e1) / 1e3,
                      "max_residual": float(res.max()) if res.size else None,

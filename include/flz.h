@@ -140,7 +140,7 @@ typedef struct flz_params {
   int32_t ortho;        /* flz_ortho; default FLZ_ORTHO_AUTO */
   int32_t refine;       /* FP32 / BF16 precision only. 0 (default): the solve stops at tol or at the
                            filter's rounding floor. 1: the filtered Lanczos procedure runs to
-                           max(tol, 1e-6) (FP32) or max(tol, 1e-3) (BF16), then its wanted, guard and
+                           max(tol, 1e-5) (FP32) or max(tol, 1e-2) (BF16), then its wanted, guard and
                            extra Ritz pairs are refined to tol by filtered subspace iteration with the
                            FX64 filter (FP64 where it does not apply) and Rayleigh-Ritz on A in FP64: the
                            mixed-precision form (not in the paper). See flz_stats.refine_sweeps. */
@@ -343,6 +343,17 @@ flz_status flz_basis_multiply(int64_t n, int32_t nb, int32_t r, const double* Q,
  * multiply-add chains on 8 CTAs per SM, timed with CUDA events (fastest of
  * three runs after a warm-up). Synchronizes the device; about 0.1 s. */
 flz_status flz_measure_alu_peak(int32_t kind, double* ops_per_s);
+/* Limit, in nanoseconds, of every bounded device-side wait of kernels
+ * launched after this call (the tensor-core reorthogonalization's and the
+ * fixed-point filter's barrier waits; default 2,000,000,000). A wait that
+ * reaches it gives up: the kernel drains the work it has in flight, frees
+ * its tensor memory and returns, and the call reports FLZ_ERR_TIMEOUT; the
+ * device stays usable. A limit of 0 means no waiting at all (a barrier that
+ * has not completed at its first, non-blocking test gives up); a tiny limit
+ * makes those calls time out, which is how that path is tested, and has no
+ * other use. *previous (may be NULL) receives the limit in force before.
+ * Process-wide. */
+flz_status flz_set_wait_limit(uint64_t ns, uint64_t* previous);
 /* Layout check of the tensor-core path: one tcgen05.mma (M = 128, N = n in
  * {16, 32, 64, 128}, K = 16, BF16 operands, FP32 accumulator in tensor memory) of a
  * 128 x 16 A operand and an n x 16 B operand given as shared-memory images

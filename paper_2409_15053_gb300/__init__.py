@@ -45,7 +45,7 @@ EXPORTED = (
     "flz_matrix_create_csr", "flz_matrix_destroy", "flz_matrix_info", "flz_matrix_format",
     "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_smoothed_step_coefficients", "flz_jackson_factors", "flz_lanczos_sigma_factors", "flz_filter_degree", "flz_damping_coefficients", "flz_spectrum_bounds",
     "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_sym_eig",
-    "flz_basis_project", "flz_basis_orthogonalize", "flz_basis_multiply", "flz_measure_alu_peak", "flz_tc_mma_probe", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve", "flz_solve_sliced",
+    "flz_basis_project", "flz_basis_orthogonalize", "flz_basis_multiply", "flz_measure_alu_peak", "flz_set_wait_limit", "flz_tc_mma_probe", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve", "flz_solve_sliced",
     "flz_get_count", "flz_get_eigenvalues", "flz_get_eigenvectors", "flz_get_residuals", "flz_get_stats",
     "flz_batch_create", "flz_batch_destroy", "flz_batch_solve", "flz_batch_get_count", "flz_batch_get_eigenvalues",
     "flz_batch_get_residuals", "flz_batch_get_eigenvectors", "flz_batch_get_stats",
@@ -126,6 +126,7 @@ def lib() -> ctypes.CDLL:
         "flz_basis_project": (ctypes.c_int, [_i64, _i32, _i32, _vp, _vp, _vp, _i32, _vp]),
         "flz_basis_multiply": (ctypes.c_int, [_i64, _i32, _i32, _vp, _vp, _i32, _vp, _i32, _vp]),
         "flz_measure_alu_peak": (ctypes.c_int, [_i32, _pdbl]),
+        "flz_set_wait_limit": (ctypes.c_int, [_u64, ctypes.POINTER(_u64)]),
         "flz_basis_orthogonalize": (ctypes.c_int, [_i64, _i32, _i32, _vp, _vp, _vp, _i32, _vp]),
         "flz_tc_mma_probe": (ctypes.c_int, [_vp, _i64, _vp, _i64, _i32, _i32, _i32, _i32, _i32, _i32, _vp]),
         "flz_solver_create": (ctypes.c_int, [_vp, ctypes.POINTER(flz_params), ctypes.POINTER(_vp)]),
@@ -342,6 +343,13 @@ def flz_measure_alu_peak(kind) -> float:
     out = ctypes.c_double()
     _check(lib().flz_measure_alu_peak(int(kind), ctypes.byref(out)))
     return out.value
+
+
+def flz_set_wait_limit(ns) -> int:
+    """Sets the device wait limit (ns) of later kernels; returns the previous limit."""
+    prev = _u64()
+    _check(lib().flz_set_wait_limit(int(ns), ctypes.byref(prev)))
+    return prev.value
 
 
 def flz_tc_mma_probe(a_img, b_img, n, a_mn_major, a_lbo, a_sbo, b_lbo, b_sbo):

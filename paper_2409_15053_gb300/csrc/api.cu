@@ -1,5 +1,6 @@
 // extern "C" entry points of include/flz.h. Each catches the internal
 // flz::Failure so that no exception crosses the ABI.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
@@ -12,6 +13,8 @@ namespace {
 thread_local std::string g_last_error;
 }
 thread_local int64_t g_kernel_launches = 0;
+std::atomic<uint64_t> g_wait_ns{2000000000ull};
+uint64_t wait_limit_ns() { return g_wait_ns.load(); }
 
 void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 void clear_last_error() { g_last_error.clear(); }
@@ -521,6 +524,13 @@ flz_status flz_measure_alu_peak(int32_t kind, double* ops_per_s) {
   FLZ_API_BEGIN
   if (!ops_per_s || (kind != 0 && kind != 1)) fail(FLZ_ERR_INVALID_ARG, "kind must be 0 (FP64 FMA) or 1 (integer)");
   *ops_per_s = flz::measure_alu_peak(kind);
+  FLZ_API_END
+}
+
+flz_status flz_set_wait_limit(uint64_t ns, uint64_t* previous) {
+  FLZ_API_BEGIN
+  const uint64_t old = flz::g_wait_ns.exchange(ns);
+  if (previous) *previous = old;
   FLZ_API_END
 }
 

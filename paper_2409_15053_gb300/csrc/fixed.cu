@@ -116,7 +116,8 @@ struct FxStep {
   int sum_exp;       // s: the running sum is held in units of 2^(s - F)
   int vec_bits;      // F
   uint64_t limit;    // 1.25 2^F: larger values are flagged
-  unsigned* flag;    // bit 0: a value left the range
+  unsigned* flag;    // bit 0: a value left the range; bit 1: a stage wait expired
+  uint64_t wait_ns;  // limit of each barrier wait
 };
 
 template <int R>
@@ -191,13 +192,19 @@ __device__ __forceinline__ void finish_row_global(size_t idx, const Acc (&S)[R],
   finish_row<R, FIRST, LAST>(idx, S, sa, own, sum, ynext, acc, W, k);
 }
 
-// Bounded wait for phase 0 of a CTA barrier: false after 2 s, with bit 1 of
-// the flag word set (reported as a timeout).
-__device__ __forceinline__ bool stage_wait(uint64_t* bar, unsigned* flag) {
+// Bounded wait for phase 0 of a CTA barrier: false after wait_ns (2 s unless
+// flz_set_wait_limit changed it), with bit 1 of the flag word set (reported as
+// a timeout).
+__device__ __forceinline__ bool stage_wait(uint64_t* bar, unsigned* flag, uint64_t wait_ns) {
+  if (wait_ns == 0) {  // a zero limit: one non-blocking test, no waiting at all
+    if (tc::mbar_test_wait(bar, 0)) return true;
+    atomicOr(flag, 2u);
+    return false;
+  }
   if (tc::mbar_try_wait(bar, 0)) return true;
   const uint64_t t0 = tc::globaltimer();
   while (!tc::mbar_try_wait(bar, 0))
-    if (tc::globaltimer() - t0 > tc::kWaitNs) {
+    if (tc::globaltimer() - t0 > wait_ns) {
       atomicOr(flag, 2u);
       return false;
     }
@@ -260,7 +267,7 @@ __global__ void __launch_bounds__(kThreads) fx_sell_kernel(int n, int nsl, int e
   for (int c = 0; c < R; ++c) acc_init(S[c], FIRST ? kValBits + 1 : kValBits);
   uint64_t sa = 0;
   bool active = row < n;
-  const bool ok0 = stage_wait(&bar[0], k.flag);
+  const bool ok0 = stage_wait(&bar[0], k.flag, k.wait_ns);
   if (active && ok0) {
     const int sl = row >> 5;
     const int so = __ldg(off + sl);
@@ -296,7 +303,7 @@ __global__ void __launch_bounds__(kThreads) fx_sell_kernel(int n, int nsl, int e
       for (int c = 0; c < R; ++c) mac(S[c], a, y[c]);
     }
   }
-  const bool ok1 = vb ? stage_wait(&bar[1], k.flag) : true;
+  const bool ok1 = vb ? stage_wait(&bar[1], k.flag, k.wait_ns) : true;
   if (active && ok0 && ok1) {
     const size_t idx = (size_t)row * R;
     if (vb) {
@@ -669,6 +676,9 @@ bool fx_filter_apply(flz_matrix* A, double c, double e, const double* coeffs, in
   uint64_t* yb = ya + nr2;
   int* cexp = reinterpret_cast<int*>(F.scratch.p + 8);
   unsigned* flag = reinterpret_cast<unsigned*>(F.scratch.p + 16);
+  // the flag reports this application only (an earlier one may have failed
+  // without being checked, when another error ended its call first)
+  FLZ_CUDA(cudaMemsetAsync(flag, 0, sizeof(unsigned), st));
   const int parts = 152;
   F.part.reserve((size_t)parts * 16);
   fx_colsq_kernel<<<parts, kThreads, 0, st>>>(V, A->n, r, F.part.p);
@@ -677,7 +687,7 @@ bool fx_filter_apply(flz_matrix* A, double c, double e, const double* coeffs, in
   FLZ_LAUNCH_CHECK();
   fx_to_fixed_kernel<<<blocks_for(nr), 256, 0, st>>>(V, nr, r, cexp, Fb, y0);
   FLZ_LAUNCH_CHECK();
-  FxStep base{0, 0, cexp, s, Fb, 5ull << (Fb - 2), flag};
+  FxStep base{0, 0, cexp, s, Fb, 5ull << (Fb - 2), flag, wait_limit_ns()};
   uint64_t* acc = reinterpret_cast<uint64_t*>(W);
   const uint64_t* vs = F.sell.p;
   const uint64_t* vc = F.csr.p;
@@ -710,8 +720,10 @@ void fx_fetch_flag(flz_matrix* A, cudaStream_t st) {
 void fx_check_flag(flz_matrix* A) {
   FxValues& F = A->fx;
   if (F.flag_host && *F.flag_host) {
+    const unsigned f = *F.flag_host;
     *F.flag_host = 0;
     cudaMemset(F.scratch.p + 16, 0, sizeof(uint64_t));
+    if (f & 2u) fail(FLZ_ERR_TIMEOUT, "fixed-point filter: a shared-memory stage wait expired");
     fail(FLZ_ERR_INVALID_ARG,
          "fixed-point filter: a recurrence value left [-1.25, 1.25] of its column scale (the spectrum of "
          "(A - cI)/e is not inside [-1, 1])");

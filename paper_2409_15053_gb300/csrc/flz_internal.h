@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -23,6 +24,10 @@ struct Failure {
 };
 
 [[noreturn]] void fail(flz_status st, const char* fmt, ...);
+// Limit of every bounded device-side wait of kernels launched from now on
+// (flz_set_wait_limit; 2 s by default).
+uint64_t wait_limit_ns();
+extern std::atomic<uint64_t> g_wait_ns;
 void set_last_error(const char* msg);
 void clear_last_error();
 
@@ -275,7 +280,9 @@ void fx_check_flag(flz_matrix* A);
 struct RefineArgs {
   double alpha, beta, lmin, lmax, tol;
   int max_sweeps, max_degree;
-  std::vector<double> filter;  // the solve's filter coefficients (interior windows)
+  std::vector<double> filter;       // the solve's filter coefficients (interior windows)
+  std::vector<double> filter_half;  // the same filter at half the degree (first sweep)
+  int wanted;                       // pairs the reduced-precision solve found in the window
 };
 struct RefineResult {
   int sweeps = 0, kp = 0, filter_precision = 0;

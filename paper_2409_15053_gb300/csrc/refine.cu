@@ -19,10 +19,12 @@
 // spectrum; below it for one at the top) the largest Rayleigh quotient of
 // the block: a Chebyshev polynomial T_d of that damping interval, rescaled to
 // be at most 1 in magnitude on the whole spectrum (so the fixed-point kernel
-// can evaluate it), of the least degree that damps the damping interval by a
-// factor D relative to the window's far edge. The extra pairs push the block
-// past the window so that its edge is a gap away from the wanted pairs.
-// Interior windows use the solve's own filter polynomial.
+// can evaluate it). Its degree is the largest whose ratio of values across the
+// window stays below 0.01 / (the current residual): a larger ratio would let
+// the small errors of the pairs it favours swamp the pairs it does not. The
+// extra pairs push the block past the window so that its edge is a gap away
+// from the wanted pairs. Interior windows, and blocks that leave too little
+// room, use the solve's own (flat) filter polynomial.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -101,7 +103,9 @@ RefineResult refine(flz_matrix* A, const RefineArgs& g, double* X, int kp, cudaS
   const auto t0 = Clock::now();
   const int64_t n = A->n;
   RefineResult out;
-  DevBuf<double> Y, AY, Vd, dev, part;
+  DevBuf<double> Y, AY, Vd, dev, part, S4, T4;
+  S4.reserve((size_t)n * 4);
+  T4.reserve((size_t)n * 4);
   Y.reserve((size_t)n * kp);
   AY.reserve((size_t)n * kp);
   dev.reserve(64);
@@ -113,36 +117,63 @@ RefineResult refine(flz_matrix* A, const RefineArgs& g, double* X, int kp, cudaS
   rayleigh(A, X, AY.p, n, kp, dev, part, mu, res, st);
   for (int sweep = 0; sweep < g.max_sweeps; ++sweep) {
     // ---- the filter of this sweep ----
-    double worst = 0.0;  // largest residual of a wanted pair
+    // worst: the largest residual among the `wanted` best pairs in the window
+    // (the block's extra columns may be poor approximations whose Rayleigh
+    // quotients also fall in the window)
+    std::vector<double> inres;
     double lo_blk = 1e300, hi_blk = -1e300;
     for (int j = 0; j < kp; ++j) {
-      if (mu[j] >= g.alpha && mu[j] <= g.beta) worst = std::max(worst, res[j] / anorm);
+      if (mu[j] >= g.alpha && mu[j] <= g.beta) inres.push_back(res[j] / anorm);
       lo_blk = std::min(lo_blk, mu[j]);
       hi_blk = std::max(hi_blk, mu[j]);
     }
+    std::sort(inres.begin(), inres.end());
+    const double worst =
+        inres.empty() ? 1.0 : inres[std::min<size_t>(inres.size(), (size_t)std::max(g.wanted, 1)) - 1];
     std::vector<double> coeffs;
-    const double damp = std::min(1e6, std::max(100.0, 10.0 * worst / g.tol));
+    // A polynomial with a large ratio between its values at the window's two
+    // ends amplifies the errors of the pairs at the far end (about `worst` in
+    // size) relative to those pairs themselves: keep that ratio below
+    // 0.01 / worst, and use the flat solve filter where that leaves less than
+    // a factor 20 of damping beyond the block.
+    const double range_max = std::min(1e6, std::max(10.0, 1e-2 / std::max(worst, 1e-300)));
     if ((lower && !upper && hi_blk > g.beta) || (upper && !lower && lo_blk < g.alpha)) {
-      // damp the spectrum beyond the block's far edge; degree from the window's far edge
       const double edge = lower ? hi_blk : lo_blk;
-      const double zc = lower ? (edge - c) / e : -(edge - c) / e;           // damping interval [zc, 1]
-      const double zw = lower ? (g.beta - c) / e : -(g.alpha - c) / e;      // the wanted pair nearest it
+      const double zc = std::min(lower ? (edge - c) / e : -(edge - c) / e, 1.0 - 1e-12);  // damping interval [zc, 1]
+      const double zw = lower ? (g.beta - c) / e : -(g.alpha - c) / e;   // the wanted end nearest it
       const double a = 2.0 / (1.0 - zc), b = -(1.0 + zc) / (1.0 - zc);
-      const double uw = std::fabs(a * zw + b);
-      int d = uw > 1.0 ? (int)std::ceil(std::acosh(damp) / std::acosh(uw)) : g.max_degree;
-      d = std::max(4, std::min(d, g.max_degree));
-      coeffs.assign(d + 1, 0.0);
-      damping_coefficients(std::min(zc, 1.0 - 1e-12), d, coeffs.data());
-      if (upper)
-        for (int k = 1; k <= d; k += 2) coeffs[k] = -coeffs[k];  // p(z) = q(-z)
-    } else {
-      coeffs = g.filter;  // interior window (or a block not past it): the solve's own filter
+      const double uw = std::fabs(a * zw + b), u0 = std::fabs(b - a);     // at the near and far window ends
+      // the least degree damping the interval by 10 worst / tol relative to
+      // the window's near end, within the ratio bound across the window
+      const double need = std::max(20.0, 10.0 * worst / g.tol);
+      int d = 0;
+      if (uw > 1.0)
+        for (int t = 4; t <= g.max_degree; ++t) {
+          if (t * (std::acosh(u0) - std::acosh(uw)) > std::log(range_max)) break;  // cosh ratio ~ exp of the difference
+          d = t;
+          if (std::cosh(t * std::acosh(uw)) >= need) break;
+        }
+      if (d >= 4 && std::cosh(d * std::acosh(uw)) >= 20.0) {
+        coeffs.assign(d + 1, 0.0);
+        damping_coefficients(zc, d, coeffs.data());
+        if (upper)
+          for (int k = 1; k <= d; k += 2) coeffs[k] = -coeffs[k];  // p(z) = q(-z)
+      }
     }
+    // interior window, or too little room: the solve's own (flat) filter, at
+    // half its degree in the first sweep (FP32 errors need a factor of tens)
+    if (coeffs.empty()) coeffs = (sweep == 0 && g.filter_half.size() > 1) ? g.filter_half : g.filter;
     out.degrees.push_back((int)coeffs.size() - 1);
     const int m = (int)coeffs.size() - 1;
+    // the filter runs on 4-column slices of the 16-column blocks (its fastest width)
     for (int b = 0; b < kp / 16; ++b)
-      filter_apply(A, c, e, coeffs.data(), m, 16, X + (size_t)b * n * 16, Y.p + (size_t)b * n * 16, FLZ_PREC_FX64,
-                   FLZ_REC_FORWARD, st);
+      for (int q = 0; q < 4; ++q) {
+        FLZ_CUDA(cudaMemcpy2DAsync(S4.p, 4 * sizeof(double), X + (size_t)b * n * 16 + 4 * q, 16 * sizeof(double),
+                                   4 * sizeof(double), (size_t)n, cudaMemcpyDeviceToDevice, st));
+        filter_apply(A, c, e, coeffs.data(), m, 4, S4.p, T4.p, FLZ_PREC_FX64, FLZ_REC_FORWARD, st);
+        FLZ_CUDA(cudaMemcpy2DAsync(Y.p + (size_t)b * n * 16 + 4 * q, 16 * sizeof(double), T4.p, 4 * sizeof(double),
+                                   4 * sizeof(double), (size_t)n, cudaMemcpyDeviceToDevice, st));
+      }
     out.filter_precision = A->last_filter_precision;
     // ---- Rayleigh-Ritz on A in the span of Y ----
     TcBasis tb;
@@ -172,18 +203,23 @@ RefineResult refine(flz_matrix* A, const RefineArgs& g, double* X, int kp, cudaS
         M[(size_t)i * kp + j] = M[(size_t)j * kp + i] = 0.5 * (M[(size_t)i * kp + j] + M[(size_t)j * kp + i]);
         H[(size_t)i * kp + j] = H[(size_t)j * kp + i] = 0.5 * (H[(size_t)i * kp + j] + H[(size_t)j * kp + i]);
       }
-    // M = U S U^T; Z = U_kept S^(-1/2) over the numerically independent directions
+    // D M D = U S U^T with D = diag(M)^(-1/2) (unit columns); Z = D U_kept S^(-1/2)
+    // over the numerically independent directions
+    std::vector<double> dsc(kp);
+    for (int i = 0; i < kp; ++i) dsc[i] = 1.0 / std::sqrt(std::max(M[(size_t)i * kp + i], 1e-300));
     std::vector<double> sw, U;
-    std::vector<double> Mc = M;
+    std::vector<double> Mc((size_t)kp * kp);
+    for (int i = 0; i < kp; ++i)
+      for (int j = 0; j < kp; ++j) Mc[(size_t)i * kp + j] = dsc[i] * M[(size_t)i * kp + j] * dsc[j];
     dense_sym_eig(Mc, kp, sw, U);
     const double smax = std::max(sw.back(), 1e-300);
     std::vector<int> keep;
     for (int i = 0; i < kp; ++i)
-      if (sw[i] > 1e-13 * smax) keep.push_back(i);
+      if (sw[i] > 1e-12 * smax) keep.push_back(i);
     const int ke = (int)keep.size();
     std::vector<double> Z((size_t)kp * ke);
     for (int i = 0; i < kp; ++i)
-      for (int q = 0; q < ke; ++q) Z[(size_t)i * ke + q] = U[(size_t)i * kp + keep[q]] / std::sqrt(sw[keep[q]]);
+      for (int q = 0; q < ke; ++q) Z[(size_t)i * ke + q] = dsc[i] * U[(size_t)i * kp + keep[q]] / std::sqrt(sw[keep[q]]);
     // C = Z^T H Z
     std::vector<double> HZ((size_t)kp * ke, 0.0), Cm((size_t)ke * ke, 0.0);
     for (int i = 0; i < kp; ++i)

@@ -425,7 +425,7 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   // With refinement (reduced-precision filter) the filtered Lanczos phase stops
   // at the filter's floor and the refinement brings the pairs to p.tol.
   const bool refining = p.refine == 1 && (p.precision == FLZ_PREC_FP32 || p.precision == FLZ_PREC_BF16);
-  const double tol = refining ? std::max(p.tol, p.precision == FLZ_PREC_FP32 ? 1e-6 : 1e-3) : p.tol;
+  const double tol = refining ? std::max(p.tol, p.precision == FLZ_PREC_FP32 ? 1e-5 : 1e-2) : p.tol;
   const double p_gate = std::min(1e-2, 10.0 * 1.1 * (double)m * m * tol * anorm / e);
   std::vector<double> found_vals, found_res;
   std::vector<double> lastT, lastTheta;  // the last check's T_k and its eigenvalues (refinement)
@@ -603,7 +603,13 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
             basis_update(Qt, k, n, r, Cb.p, 16, 1.0, 0.0, Xr.p + (size_t)b * n * 16, 16, st);
           FLZ_CUDA(cudaStreamSynchronize(st));  // hc is reused for the next block
         }
-        RefineArgs ra{s->alpha, s->beta, lmin, lmax, p.tol, 4, std::max(m, 64), coeffs};
+        std::vector<double> half;
+        if (!whole && m >= 8) {
+          half.resize(m / 2 + 1);
+          filter_coeffs_for(p, am, bm, m / 2, half.data());
+        }
+        RefineArgs ra{s->alpha, s->beta, lmin, lmax, p.tol, p.precision == FLZ_PREC_FP32 ? 4 : 10,
+                      std::max(m, 64), coeffs, half, (int)found};
         const RefineResult rr = refine(A, ra, Xr.p, kp, st);
         stats.refine_sweeps = rr.sweeps;
         stats.refine_degree = rr.degrees.empty() ? 0 : *std::max_element(rr.degrees.begin(), rr.degrees.end());

@@ -195,6 +195,7 @@ struct DotArgs {
   int Gtot, nR, RS;
   unsigned long long* acc;  // Gtot x 128 x NP integer sums, zero on entry
   int* status;
+  uint64_t wait_ns;         // limit of each barrier wait
 };
 
 // stages of the projection's ring: three when the W digits of N = 128 take 128 KB
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(192, 1) tc_dot_kernel(DotArgs a) {
   const int gs = blockIdx.x, split = blockIdx.y;
   const int gcount = min(GPC, a.Gtot - gs * GPC);
   const int nloc = split < a.nR ? (a.nR - 1 - split) / a.RS + 1 : 0;
-  const tc::Guard guard{s_abort, a.status};
+  const tc::Guard guard{s_abort, a.status, a.wait_ns};
 
   if (tid == 0) {
     for (int i = 0; i < kDotStages; ++i) {
@@ -469,6 +470,7 @@ struct UpdArgs {
   int keep;            // 1: W -= Q H; 0: W = -Q H (H the digits' value)
   uint32_t* wmax_out;  // per-column maxima of the updated W, or null
   int* status;
+  uint64_t wait_ns;    // limit of each barrier wait
 };
 
 template <int NP>
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(192, 1) tc_update_kernel(UpdArgs a) {
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nloc = blockIdx.x < a.ntiles ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const tc::Guard guard{s_abort, a.status};
+  const tc::Guard guard{s_abort, a.status, a.wait_ns};
 
   if (tid == 0) {
     for (int i = 0; i < kUpdStages; ++i) {
@@ -659,7 +661,7 @@ constexpr int kProbeA = 36 * 1024, kProbeB = 20 * 1024;
 // images with explicit descriptor strides (the layout check of the C ABI).
 __global__ void tc_probe_kernel(const uint4* a_img, int a_words, const uint4* b_img, int b_words, int np,
                                 int a_mn_major, uint32_t a_lbo, uint32_t a_sbo, uint32_t b_lbo, uint32_t b_sbo,
-                                float* out, int* status) {
+                                float* out, int* status, uint64_t wait_ns) {
   constexpr int ABYTES = kProbeA, BBYTES = kProbeB;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint4* sa = reinterpret_cast<uint4*>(smem);
@@ -691,7 +693,7 @@ __global__ void tc_probe_kernel(const uint4* a_img, int a_words, const uint4* b_
                  idesc, 0);
     tc::mma_commit(bar);
   }
-  const tc::Guard guard{s_abort, status};
+  const tc::Guard guard{s_abort, status, wait_ns};
   const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(bar, 0, guard, kErrWaitEpilogue));
   tc::fence_after_sync();
   if (ok) {
@@ -755,7 +757,7 @@ void launch_dot(TcBasis& B, int K, const double* W, int r, int ldw, const uint32
   const int64_t tasks = B.n_oct * (NP / 8);
   w_digits_kernel<<<(unsigned)((tasks + 255) / 256), 256, 0, st>>>(W, B.n, r, ldw, wmax, NP, B.n_oct, B.wd.p);
   FLZ_LAUNCH_CHECK();
-  DotArgs a{B.q.p, B.wd.p, B.n_oct, Gtot, nR, RS, B.acc.p, B.status.p};
+  DotArgs a{B.q.p, B.wd.p, B.n_oct, Gtot, nR, RS, B.acc.p, B.status.p, wait_limit_ns()};
   tc_dot_kernel<NP><<<dim3(GS, RS), 192, dot_smem(NP), st>>>(a);
   FLZ_LAUNCH_CHECK();
   tc_dot_reduce_kernel<NP><<<Gtot, 16 * r, 0, st>>>(B.acc.p, K, r, wmax, C, ldc);
@@ -776,7 +778,7 @@ void launch_update(TcBasis& B, int K, double* W, int r, int ldw, int keep, uint3
   for (int G0 = 0; G0 < Gtot; G0 += kWindowGroups) {
     const int G1 = std::min(Gtot, G0 + kWindowGroups);
     UpdArgs a{B.q.p, B.n_oct, B.n, ntiles, G0, G1, B.hs.p, B.hexp.p, W, r, ldw, keep || G0 > 0 ? 1 : 0,
-              G1 == Gtot ? wmax_out : nullptr, B.status.p};
+              G1 == Gtot ? wmax_out : nullptr, B.status.p, wait_limit_ns()};
     tc_update_kernel<NP><<<grid, 192, upd_smem(NP), st>>>(a);
     FLZ_LAUNCH_CHECK();
   }
@@ -931,7 +933,8 @@ int tc_probe(const uint16_t* a_img, size_t a_bytes, const uint16_t* b_img, size_
   FLZ_CUDA(cudaMemset(dst.p, 0, sizeof(int)));
   const size_t smem = kProbeA + kProbeB + 64;
   allow_smem(tc_probe_kernel, smem);
-  tc_probe_kernel<<<1, 128, smem>>>(da.p, aw, db.p, bw, np, a_mn_major, a_lbo, a_sbo, b_lbo, b_sbo, dout.p, dst.p);
+  tc_probe_kernel<<<1, 128, smem>>>(da.p, aw, db.p, bw, np, a_mn_major, a_lbo, a_sbo, b_lbo, b_sbo, dout.p, dst.p,
+                                    wait_limit_ns());
   FLZ_LAUNCH_CHECK();
   FLZ_CUDA(cudaDeviceSynchronize());
   int status = 0;

@@ -3,9 +3,11 @@
 // global to shared memory, tensor-memory allocation, tcgen05.mma with
 // shared-memory operand descriptors, commits and tensor-memory loads.
 //
-// Every wait is bounded: after kWaitNs nanoseconds it records a status in a
-// caller-given word and returns false, so a logic error ends the kernel with
-// an error the host reads instead of a hung GPU.
+// Every wait is bounded: after the launch's wait limit (Guard::wait_ns, 2 s
+// unless flz_set_wait_limit changed it) it records a status in a caller-given
+// word and returns false, so a logic error ends the kernel with an error the
+// host reads instead of a hung GPU. Waits that drain work already in flight
+// before a CTA exits keep the fixed kWaitNs bound.
 #pragma once
 
 #include <cstdint>
@@ -57,23 +59,44 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking test of phase `parity` (try_wait may suspend the thread for a
+// while; test_wait returns at once).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Shared state of a CTA's roles: `abort` is raised by the first role whose
 // wait expires so that the others stop at their next wait.
 struct Guard {
   volatile int* abort;  // shared memory
   int* status;          // global: first error code of the launch
+  uint64_t wait_ns;     // limit of each wait
 };
 
 // Waits for completion of phase `parity`. Returns false (and raises the
 // abort flag, recording `code` in the status word) if the wait expires or
 // another role already aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const Guard& g, int code) {
-  if (mbar_try_wait(bar, parity)) return true;
+  // a zero limit: one non-blocking test, no waiting at all
+  if (g.wait_ns == 0 ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)) return true;
+  if (g.wait_ns == 0) {
+    *g.abort = 1;
+    atomicCAS(g.status, 0, code);
+    return false;
+  }
   const uint64_t t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*g.abort) return false;
-    if (globaltimer() - t0 > kWaitNs) {
+    if (globaltimer() - t0 > g.wait_ns) {
       *g.abort = 1;
       atomicCAS(g.status, 0, code);
       return false;
