@@ -348,6 +348,8 @@ def main():
                     help="where the full reorthogonalization runs (auto: tensor cores for r <= 4)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--check-every", type=int, default=CONFIG2["check_every"])
+    ap.add_argument("--table2-check", type=int, default=30,
+                    help="--mode table2: block steps between convergence checks (Table 2's counts are multiples of 30)")
     ap.add_argument("--cpu-budget", type=float, default=12.0,
                     help="seconds of oracle block steps per CPU-baseline sample (each of 1 thread and all threads)")
     ap.add_argument("--reference-budget", type=float, default=3.0,
@@ -360,7 +362,7 @@ def main():
     ap.add_argument("--ortho-n", type=int, default=1_000_000, help="rows of the --mode ortho basis")
     ap.add_argument("--ortho-basis", type=int, default=120, help="columns of the --mode ortho basis")
     ap.add_argument("--mode", default="solve", choices=["solve", "filter", "batch", "table2", "graph", "slices",
-                                                        "ortho", "config3", "cpu_leg"],
+                                                        "ortho", "config3", "cpu_leg", "sequence"],
                     help="solve: whole flz_solve per step (default); filter: only flz_filter_apply at the "
                          "solver's shape, for the kernel roofline and profiling")
     args = ap.parse_args()
@@ -403,6 +405,8 @@ def main():
         return ortho_mode(flz, torch, args)
     if args.mode == "config3":
         return config3_mode(flz, torch, args)
+    if args.mode == "sequence":
+        return sequence_mode(flz, torch, prec, args)
     csr = make_matrix()
     if args.mode == "filter":
         return filter_mode(flz, torch, csr, prec, args)
@@ -689,7 +693,7 @@ def table2_mode(flz, torch, prec, args):
     (12th-order finite differences on a sphere, Gaussian local potentials,
     dense non-local projector blocks). Interval [-0.645, -0.0053] as in
     Table 2, block size 3, degrees 50, 100, 150, 200 and automatic, checks every
-    30 block steps; one warm-up solve per degree, then one timed solve (CUDA
+    30 block steps (--table2-check); one warm-up solve per degree, then one timed solve (CUDA
     events). The paper's K40 numbers for Ge87H76 are printed beside each row
     for context (a different matrix of the same shape, on other hardware)."""
     csr = parsec_like_hamiltonian()
@@ -702,7 +706,7 @@ def table2_mode(flz, torch, prec, args):
         p.degree = m
         p.precision = prec
         p.tol = args.tol
-        p.check_every = 30
+        p.check_every = args.table2_check
         p.recurrence = {"forward": flz.FLZ_REC_FORWARD, "clenshaw": flz.FLZ_REC_CLENSHAW}[args.recurrence]
         p.damping = {"none": 0, "jackson": 1, "sigma": 2}[args.damping]
         s = flz.flz_solver_create(h, p)
@@ -725,11 +729,15 @@ def table2_mode(flz, torch, prec, args):
                      "PREPROC_ORTH_MV_percent": [round(100 * x["ms_bounds"] / x["ms_total"]),
                                                  round(100 * x["ms_orth"] / x["ms_total"]),
                                                  round(100 * x["ms_filter"] / x["ms_total"])],
-                     "paper_K40": {"iters": paper[0], "MV": paper[1], "seconds": paper[2], "residual": paper[3]}})
+                     "paper_K40": {"iters": paper[0], "MV": paper[1], "seconds": paper[2], "residual": paper[3]},
+                     "checks": [[c["block_steps"], c["inside"], c["walked"], c["outside"], c["all_small"]]
+                                for c in flz.flz_get_checks(s)]})
         flz.flz_solver_destroy(s)
     flz.flz_matrix_destroy(h)
     print(json.dumps({"mode": "table2", "matrix": "synthetic Ge87H76-shaped stand-in", "n": csr.n, "nnz": csr.nnz,
                       "interval": [-0.645, -0.0053], "block_size": 3, "precision": args.precision,
+                      "check_every": args.table2_check,
+                      "checks_format": "[block steps, pairs in the window, pairs walked, guard pairs met, all passed]",
                       "recurrence": args.recurrence, "damping": args.damping,
                       "tol": args.tol, "rows": rows}))
 
@@ -892,6 +900,71 @@ def config3_mode(flz, torch, args):
         flz.flz_solver_destroy(s)
     flz.flz_matrix_destroy(h)
     print(json.dumps({"mode": "config3", "n": csr.n, "nnz": csr.nnz, "tol": args.tol, "rows": rows}))
+
+
+def sequence_mode(flz, torch, prec, args):
+    """A sequence of related problems (the self-consistent-field setting of
+    the paper's Section 1): config 2's matrix with the potential moved by
+    0.02 t (U(0,1) - 1/2) at steps t = 0..3, all eigenpairs in [0, beta] with
+    the headline's beta. Each step is solved from a random start block (cold)
+    and from the previous step's eigenvectors (warm,
+    flz_solver_set_start_vectors); both are timed (one solve each, CUDA
+    events) and must return the same eigenvalues."""
+    rng = np.random.Generator(np.random.PCG64(CONFIG2["seed"]))
+    g = CONFIG2["grid"]
+    v0 = CONFIG2["potential_scale"] * rng.random(g ** 3)
+    dv = np.random.Generator(np.random.PCG64(CONFIG2["seed"] + 1)).random(g ** 3) - 0.5
+    stream = torch.cuda.current_stream()
+    rows, prev = [], None
+    for t in range(4):
+        csr = laplacian_3d_7pt(g, g, g, v0 + 0.02 * t * dv)
+        h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+        row = {"step": t}
+        for mode in ("cold", "warm"):
+            if mode == "warm" and prev is None:
+                continue
+            p = flz.flz_params_default()
+            p.block_size = args.block_size
+            p.degree = args.degree
+            p.check_every = args.check_every
+            p.precision = prec
+            p.tol = args.tol
+            s = flz.flz_solver_create(h, p)
+            flz.flz_solver_set_interval(s, CONFIG2["alpha"], CONFIG2["beta"])
+            if mode == "warm":
+                flz.flz_solver_set_start_vectors(s, prev, ld=csr.n)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = flz.flz_solve(s, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            x = flz.flz_get_stats(s)
+            vals = flz.flz_get_eigenvalues(s)
+            row[mode] = {"status": flz.flz_status_string(st), "count": int(x["count"]), "block_steps": int(x["iters"]),
+                         "seconds": e0.elapsed_time(e1) / 1e3, "max_residual": float(flz.flz_get_residuals(s).max())}
+            row[mode + "_vals"] = vals
+            if mode == "warm" or t == 0:
+                nxt = torch.empty((int(x["count"]), csr.n), dtype=torch.float64, device="cuda")
+                flz.lib().flz_get_eigenvectors(s, nxt.data_ptr(), csr.n, int(x["count"]), flz.FLZ_DEVICE)
+                prev_next = nxt
+            flz.flz_solver_destroy(s)
+        if "warm_vals" in row:
+            a, b = row.pop("cold_vals"), row.pop("warm_vals")
+            row["max_abs_eig_diff_warm_vs_cold"] = float(np.max(np.abs(a - b))) if a.shape == b.shape else None
+        else:
+            row.pop("cold_vals")
+        prev = prev_next.T  # n x count view of the column-major eigenvectors (contiguous columns)
+        flz.flz_matrix_destroy(h)
+        rows.append(row)
+    cold = sum(r["cold"]["block_steps"] for r in rows[1:])
+    warm = sum(r["warm"]["block_steps"] for r in rows[1:])
+    print(json.dumps({"mode": "sequence", "workload": config_dict(make_matrix(), args)["workload"],
+                      "potential_step": "0.02 t (U(0,1) - 1/2), t = 0..3", "rows": rows,
+                      "block_steps_cold_steps_1_3": cold, "block_steps_warm_steps_1_3": warm,
+                      "seconds_cold_steps_1_3": sum(r["cold"]["seconds"] for r in rows[1:]),
+                      "seconds_warm_steps_1_3": sum(r["warm"]["seconds"] for r in rows[1:])}))
 
 
 def ortho_mode(flz, torch, args):

@@ -146,6 +146,22 @@ typedef struct flz_params {
                            mixed-precision form (not in the paper). See flz_stats.refine_sweeps. */
 } flz_params;
 
+/* One convergence check of a solve (Section 3.2.2's periodic Rayleigh-Ritz
+ * test): after `block_steps` steps, the walk down the Ritz pairs ranked by
+ * their p(A) Ritz value visited `walked` pairs, `inside` of them in
+ * [alpha, beta] with residual <= tol and `outside` outside it; all_small = 1
+ * if every visited pair passed; converged = 1 if this check ended the solve
+ * (all passed, the guard pairs met and the count equal to the previous
+ * check's). */
+typedef struct flz_check {
+  int64_t block_steps;
+  int64_t inside;
+  int32_t walked;
+  int32_t outside;
+  int32_t all_small;
+  int32_t converged;
+} flz_check;
+
 /* Per-solve statistics (the columns of Tables 2 and 3, plus bounds). */
 typedef struct flz_stats {
   int64_t iters;        /* block Lanczos steps taken (Table 2 "iters") */
@@ -374,6 +390,18 @@ flz_status flz_solver_create(flz_matrix* A, const flz_params* params, flz_solver
 flz_status flz_solver_destroy(flz_solver* s);
 /* [alpha, beta] in A's own units (not mapped); alpha < beta. */
 flz_status flz_solver_set_interval(flz_solver* s, double alpha, double beta);
+/* Warm start for a sequence of related problems (the self-consistent-field
+ * iterations of Section 1 solve one eigenproblem per step with a slowly
+ * changing potential; an addition of this library): the start block of the
+ * solver's following solves is r random combinations of these `cols` vectors
+ * plus noise of 1 % of their size, orthonormalized, instead of a random block.
+ * Pass the eigenvectors of the previous problem (flz_get_eigenvectors): the
+ * filtered Krylov space then reaches the wanted eigenvectors in fewer block
+ * steps. X is n x cols column-major with leading dimension ld >= n, host or
+ * device (`where`); the library copies it. cols = 0 clears it (random start
+ * blocks again). Not for the double-FP32 precision (INVALID_ARG). */
+flz_status flz_solver_set_start_vectors(flz_solver* s, const double* X, int64_t ld, int32_t cols,
+                                        flz_memspace where);
 /* Runs the filtered Lanczos procedure: bounds, map, degree, coefficients,
  * block Lanczos on p(A) with full reorthogonalization, periodic Rayleigh-Ritz
  * and residual checks, Rayleigh quotients of the converged Ritz vectors.
@@ -412,6 +440,10 @@ flz_status flz_get_eigenvectors(const flz_solver* s, double* out, int64_t ld, in
 /* ||A x_j - lambda_j x_j|| / ||A|| per pair into host out[cap]. */
 flz_status flz_get_residuals(const flz_solver* s, double* out, int64_t cap);
 flz_status flz_get_stats(const flz_solver* s, flz_stats* out);
+/* The convergence checks of the last solve, in order, into host out[cap];
+ * *count (may be NULL) receives how many there were (all of them even when
+ * cap is smaller; only min(cap, *count) are written). */
+flz_status flz_get_checks(const flz_solver* s, flz_check* out, int64_t cap, int64_t* count);
 
 /* ---- batches of independent problems --------------------------------------- */
 

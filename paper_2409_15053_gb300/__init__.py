@@ -45,8 +45,8 @@ EXPORTED = (
     "flz_matrix_create_csr", "flz_matrix_destroy", "flz_matrix_info", "flz_matrix_format",
     "flz_filter_apply", "flz_filter_apply_noalloc", "flz_filter_coefficients", "flz_smoothed_step_coefficients", "flz_jackson_factors", "flz_lanczos_sigma_factors", "flz_filter_degree", "flz_damping_coefficients", "flz_spectrum_bounds",
     "flz_band_eigenvalues", "flz_band_eigenvectors", "flz_sym_eig",
-    "flz_basis_project", "flz_basis_orthogonalize", "flz_basis_multiply", "flz_measure_alu_peak", "flz_set_wait_limit", "flz_tc_mma_probe", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solve", "flz_solve_sliced",
-    "flz_get_count", "flz_get_eigenvalues", "flz_get_eigenvectors", "flz_get_residuals", "flz_get_stats",
+    "flz_basis_project", "flz_basis_orthogonalize", "flz_basis_multiply", "flz_measure_alu_peak", "flz_set_wait_limit", "flz_tc_mma_probe", "flz_solver_create", "flz_solver_destroy", "flz_solver_set_interval", "flz_solver_set_start_vectors", "flz_solve", "flz_solve_sliced",
+    "flz_get_count", "flz_get_eigenvalues", "flz_get_eigenvectors", "flz_get_residuals", "flz_get_stats", "flz_get_checks",
     "flz_batch_create", "flz_batch_destroy", "flz_batch_solve", "flz_batch_get_count", "flz_batch_get_eigenvalues",
     "flz_batch_get_residuals", "flz_batch_get_eigenvectors", "flz_batch_get_stats",
 )
@@ -79,6 +79,11 @@ class flz_stats(ctypes.Structure):
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class flz_check(ctypes.Structure):
+    _fields_ = [("block_steps", ctypes.c_int64), ("inside", ctypes.c_int64), ("walked", ctypes.c_int32),
+                ("outside", ctypes.c_int32), ("all_small", ctypes.c_int32), ("converged", ctypes.c_int32)]
 
 
 class FlzError(RuntimeError):
@@ -132,6 +137,7 @@ def lib() -> ctypes.CDLL:
         "flz_solver_create": (ctypes.c_int, [_vp, ctypes.POINTER(flz_params), ctypes.POINTER(_vp)]),
         "flz_solver_destroy": (ctypes.c_int, [_vp]),
         "flz_solver_set_interval": (ctypes.c_int, [_vp, _dbl, _dbl]),
+        "flz_solver_set_start_vectors": (ctypes.c_int, [_vp, _vp, _i64, _i32, ctypes.c_int]),
         "flz_solve": (ctypes.c_int, [_vp, _vp]),
         "flz_solve_sliced": (ctypes.c_int, [_vp, _i32, _vp]),
         "flz_get_count": (ctypes.c_int, [_vp, ctypes.POINTER(_i64)]),
@@ -139,6 +145,7 @@ def lib() -> ctypes.CDLL:
         "flz_get_eigenvectors": (ctypes.c_int, [_vp, _vp, _i64, _i64, ctypes.c_int]),
         "flz_get_residuals": (ctypes.c_int, [_vp, _vp, _i64]),
         "flz_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(flz_stats)]),
+        "flz_get_checks": (ctypes.c_int, [_vp, _vp, _i64, ctypes.POINTER(_i64)]),
         "flz_batch_create": (ctypes.c_int, [_i32, ctypes.POINTER(_vp), _vp, _vp, ctypes.POINTER(flz_params),
                                             ctypes.POINTER(_vp)]),
         "flz_batch_destroy": (ctypes.c_int, [_vp]),
@@ -375,6 +382,24 @@ def flz_solver_set_interval(s, alpha, beta):
     _check(lib().flz_solver_set_interval(s, float(alpha), float(beta)))
 
 
+def flz_solver_set_start_vectors(s, X, ld=None, where=None):
+    """Warm start: the next solves start from combinations of the columns of X (n x cols, column-major).
+
+    X may be a host numpy array of shape (n, cols) (any layout; copied column-major) or a device tensor
+    holding the columns contiguously (ld = n) with where=FLZ_DEVICE; None clears the start vectors."""
+    if X is None:
+        _check(lib().flz_solver_set_start_vectors(s, None, 0, 0, FLZ_HOST))
+        return
+    if isinstance(X, np.ndarray):
+        Xc = np.asfortranarray(X, dtype=np.float64)
+        n, cols = Xc.shape
+        _check(lib().flz_solver_set_start_vectors(s, int(Xc.ctypes.data), int(n), int(cols), FLZ_HOST))
+        return
+    n, cols = int(X.shape[0]), int(X.shape[1])
+    _check(lib().flz_solver_set_start_vectors(s, _ptr(X), int(ld if ld is not None else n), cols,
+                                              FLZ_DEVICE if where is None else int(where)))
+
+
 def flz_solve(s, stream=None) -> int:
     """Returns FLZ_OK or FLZ_ERR_NOT_CONVERGED (partial results readable); raises on other failures."""
     return _check(lib().flz_solve(s, _stream(stream)), allow=(FLZ_ERR_NOT_CONVERGED,))
@@ -417,6 +442,15 @@ def get_eigenvectors_host(s, n: int) -> np.ndarray:
     buf = np.empty((max(cnt, 1), n))  # row t of buf = column t of the column-major result
     _check(lib().flz_get_eigenvectors(s, _ptr(buf), int(n), int(max(cnt, 1)), FLZ_HOST))
     return buf[:cnt].T
+
+
+def flz_get_checks(s) -> list:
+    """The convergence checks of the last solve, as dicts (block_steps, inside, walked, outside, ...)."""
+    cnt = _i64()
+    _check(lib().flz_get_checks(s, None, 0, ctypes.byref(cnt)))
+    arr = (flz_check * max(cnt.value, 1))()
+    _check(lib().flz_get_checks(s, arr, cnt.value, None))
+    return [{name: getattr(arr[i], name) for name, _ in flz_check._fields_} for i in range(cnt.value)]
 
 
 def flz_get_stats(s) -> dict:

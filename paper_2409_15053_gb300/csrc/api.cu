@@ -586,6 +586,27 @@ flz_status flz_solver_set_interval(flz_solver* s, double alpha, double beta) {
   FLZ_API_END
 }
 
+flz_status flz_solver_set_start_vectors(flz_solver* s, const double* X, int64_t ld, int32_t cols,
+                                        flz_memspace where) {
+  FLZ_API_BEGIN
+  if (!s || cols < 0 || (cols > 0 && !X)) fail(FLZ_ERR_INVALID_ARG, "bad arguments");
+  if (where != FLZ_HOST && where != FLZ_DEVICE) fail(FLZ_ERR_INVALID_ARG, "bad memspace");
+  const int64_t n = s->A->n;
+  if (cols > 0 && ld < n) fail(FLZ_ERR_INVALID_ARG, "ld < n");
+  if (s->p.precision == FLZ_PREC_DF64 && cols > 0)
+    fail(FLZ_ERR_INVALID_ARG, "start vectors apply to solves with an FP64 basis (not the double-FP32 precision)");
+  s->start_cols = 0;
+  if (cols == 0) {
+    s->start.release();
+  } else {
+    s->start.reserve((size_t)n * cols);
+    FLZ_CUDA(cudaMemcpy2D(s->start.p, sizeof(double) * n, X, sizeof(double) * ld, sizeof(double) * n, (size_t)cols,
+                          where == FLZ_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice));
+    s->start_cols = cols;
+  }
+  FLZ_API_END
+}
+
 flz_status flz_solve(flz_solver* s, void* stream) {
   ::flz::clear_last_error();
   try {
@@ -662,6 +683,15 @@ flz_status flz_get_eigenvectors(const flz_solver* s, double* out, int64_t ld, in
   const cudaMemcpyKind kind = where == FLZ_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
   FLZ_CUDA(cudaMemcpy2D(out, sizeof(double) * ld, s->evecs.p, sizeof(double) * n, sizeof(double) * n,
                         (size_t)s->count, kind));
+  FLZ_API_END
+}
+
+flz_status flz_get_checks(const flz_solver* s, flz_check* out, int64_t cap, int64_t* count) {
+  FLZ_API_BEGIN
+  if (!s || cap < 0 || (cap > 0 && !out)) fail(FLZ_ERR_INVALID_ARG, "bad arguments");
+  const int64_t nc = (int64_t)s->checks.size();
+  if (count) *count = nc;
+  for (int64_t i = 0; i < std::min(cap, nc); ++i) out[i] = s->checks[i];
   FLZ_API_END
 }
 

@@ -551,6 +551,43 @@ void column_sums(const double* X, const double* Y, const double* lam, int64_t n,
   sum_partials(part, grid, (size_t)s, out, st);
 }
 
+// Out[i, t] = scale * Out[i, t] + sum_j X[i + j ld] G[j r + t] for t < r: r
+// combinations of the `cols` columns of the column-major X added to a
+// (row-major) n x r block. One thread per row; X read with unit stride
+// across the threads of a warp.
+template <int R>
+__global__ void combine_columns_kernel(const double* __restrict__ X, long long n, long long ld, int cols,
+                                       const double* __restrict__ G, double scale, double* __restrict__ Out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double acc[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) acc[t] = scale * Out[i * R + t];
+    for (int j = 0; j < cols; ++j) {
+      const double x = X[(size_t)j * ld + i];
+#pragma unroll
+      for (int t = 0; t < R; ++t) acc[t] = fma(x, __ldg(G + j * R + t), acc[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < R; ++t) Out[i * R + t] = acc[t];
+  }
+}
+
+void combine_columns(const double* X, int64_t n, int64_t ld, int cols, const double* G, int r, double scale,
+                     double* Out, cudaStream_t st) {
+  const unsigned grid = gs_blocks(n);
+  switch (r) {
+#define FLZ_CC(R)                                                                                      \
+  case R:                                                                                              \
+    combine_columns_kernel<R><<<grid, 256, 0, st>>>(X, n, ld, cols, G, scale, Out); \
+    break;
+    FLZ_CC(1) FLZ_CC(2) FLZ_CC(3) FLZ_CC(4) FLZ_CC(5) FLZ_CC(6) FLZ_CC(7) FLZ_CC(8)
+    FLZ_CC(9) FLZ_CC(10) FLZ_CC(11) FLZ_CC(12) FLZ_CC(13) FLZ_CC(14) FLZ_CC(15) FLZ_CC(16)
+#undef FLZ_CC
+    default: fail(FLZ_ERR_INVALID_ARG, "block width %d", r);
+  }
+  FLZ_LAUNCH_CHECK();
+}
+
 void random_normal(double* X, int64_t count, uint64_t seed, uint64_t offset, cudaStream_t st) {
   random_normal_kernel<double><<<gs_blocks(count), 256, 0, st>>>(X, count, seed, offset);
   FLZ_LAUNCH_CHECK();

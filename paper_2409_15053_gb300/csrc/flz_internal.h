@@ -235,9 +235,13 @@ struct flz_solver {
   std::vector<double> evals, resid;
   flz::DevBuf<double> evecs;  // n x count, column-major, ld = n
   flz_stats stats{};
+  std::vector<flz_check> checks;  // the convergence checks of the last solve
   // workspace
   flz::DevBuf<double> Q, W, C, C2, part, X, AX, small, colpart;
   flz::TcBasis tcb;  // digit copy of the basis when reorthogonalization runs on the tensor cores
+  // start vectors of the next solve (flz_solver_set_start_vectors): n x start_cols, column-major
+  flz::DevBuf<double> start;
+  int32_t start_cols = 0;
 };
 
 namespace flz {
@@ -337,6 +341,11 @@ size_t column_sums_scratch(int64_t n, int s);
 // n x r block of N(0,1) numbers from a counter-based generator (seed, offset).
 void random_normal(double* X, int64_t count, uint64_t seed, uint64_t offset, cudaStream_t st);
 void random_normal(dev::dfloat* X, int64_t count, uint64_t seed, uint64_t offset, cudaStream_t st);
+// Out = scale Out + X G: r combinations (G cols x r, row-major, device) of the
+// cols columns of the column-major X (leading dimension ld) into the row-major
+// n x r block Out.
+void combine_columns(const double* X, int64_t n, int64_t ld, int cols, const double* G, int r, double scale,
+                     double* Out, cudaStream_t st);
 // Column j of a row-major n x s block (stride ld) into column-major out (stride ldo).
 void rows_to_columns(const double* X, int64_t n, int s, int ld, double* out, int64_t ldo, cudaStream_t st);
 // Gershgorin interval and max row length on the device.

@@ -217,6 +217,25 @@ void orthonormal_start(Engine<T>& E, uint64_t seed) {
   E.seal(0);
 }
 
+// Warm start: r random combinations of the given start vectors (columns of
+// the column-major X) plus noise of 1 % of their size, orthonormalized. A
+// start block rich in the wanted eigenvectors (those of a nearby earlier
+// problem) lets the filtered Krylov space reach them in fewer block steps; the
+// noise keeps every direction present for eigenvectors that entered the window.
+void warm_start(Engine<double>& E, const double* X, int cols, uint64_t seed) {
+  const int r = E.r;
+  const int64_t n = E.n;
+  DevBuf<double> G;
+  G.reserve((size_t)cols * r);
+  random_normal(G.p, (int64_t)cols * r, seed ^ 0x77a7ull, 0, E.st);
+  random_normal(E.block(0), n * r, seed, 0, E.st);
+  // noise 0.01 / sqrt(n) per entry against combinations of unit columns (size ~ sqrt(cols / n))
+  const double noise = 0.01 * std::sqrt((double)cols / (double)n);
+  combine_columns(X, n, n, cols, G.p, r, noise, E.block(0), E.st);
+  E.block_qr(E.block(0), E.block(0));
+  E.seal(0);
+}
+
 // Spectrum bounds by block Lanczos on A (Section 2.2 after eq. transf).
 void estimate_bounds(flz_matrix* A, int steps, int r, uint64_t seed, cudaStream_t st, double* lmin, double* lmax) {
   const int64_t n = A->n;
@@ -304,6 +323,7 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   flz_stats& stats = s->stats;
   stats = flz_stats{};
   stats.block_size = r;
+  s->checks.clear();
   s->solved = false;
   s->count = 0;
   s->evals.clear();
@@ -406,7 +426,13 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
     E.tcb = &s->tcb;
   }
   E.fx = p.precision == FLZ_PREC_FX64;
-  orthonormal_start(E, p.seed);
+  bool warm = false;
+  if constexpr (std::is_same<BT, double>::value)
+    if (s->start_cols > 0) {
+      warm_start(E, s->start.p, s->start_cols, p.seed);
+      warm = true;
+    }
+  if (!warm) orthonormal_start(E, p.seed);
 
   Projected P;
   P.r = r;
@@ -564,6 +590,7 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
     const bool complete = all_small && (outside >= guard || full_space);
     converged = complete && (full_space || (prev_count >= 0 && inside == prev_count));
     prev_count = complete ? inside : -1;
+    s->checks.push_back(flz_check{(int64_t)k, (int64_t)inside, walked, outside, all_small ? 1 : 0, converged ? 1 : 0});
     ms_check += ms_since(tc);
     if (refining && (converged || last)) {
       lastT.swap(T);

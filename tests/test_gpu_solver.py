@@ -439,3 +439,110 @@ def test_block_wider_than_the_matrix_is_rejected():
         flz.flz_solver_create(h, p)  # r > n is refused when the solver is created
     assert e.value.status == flz.FLZ_ERR_INVALID_ARG
     flz.flz_matrix_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [flz.FLZ_PREC_FP64, flz.FLZ_PREC_FX64], ids=["fp64", "fx64"])
+def test_scaled_down_table2_stand_in_vs_dense(precision):
+    # The Table 2 stand-in's generator at radius 9 (n = 3071, 119 entries per
+    # row, 366 rows above 256 entries from the non-local blocks): r = 3 as in
+    # the paper, CSR with the long-row tier; the negative eigenvalues (the
+    # occupied states of the stand-in) against a dense eigensolve.
+    from synth import parsec_like_hamiltonian
+    csr = parsec_like_hamiltonian(radius=9, heavy=8, light=6, seed=3)
+    lens = np.diff(csr.rowptr)
+    assert (lens > 256).sum() > 100
+    w = np.linalg.eigvalsh(csr.to_dense())
+    k = int((w < 0).sum())
+    a, b = w[0] - 1.0, 0.5 * (w[k - 1] + w[k])
+    out = solve(csr, a, b, block_size=3, degree=80, check_every=10, precision=precision)
+    ref = w[(w >= a) & (w <= b)]
+    assert out["status"] == flz.FLZ_OK
+    assert out["vals"].shape == ref.shape
+    norm_a = max(abs(out["stats"]["lmin"]), abs(out["stats"]["lmax"]))
+    assert np.max(np.abs(out["vals"] - ref)) < 1e-10 * norm_a
+    check_pairs(csr, out, 1e-10)
+
+
+def test_fd4_hamiltonian_count_matches_inertia_midsize():
+    # config 3's generator at 18^3 (n = 5832, beyond the dense sizes): the
+    # count in [-6, -0.3] by two LDL^T inertia counts (Sylvester)
+    csr = fd4_laplacian_3d(18, gaussian_wells_potential(18, 8, seed=4))
+    cnt = dense.count_in_interval(csr.to_scipy(), -6.0, -0.3)
+    assert cnt >= 5
+    for precision in (flz.FLZ_PREC_FP64, flz.FLZ_PREC_FX64):
+        out = solve(csr, -6.0, -0.3, block_size=4, degree=120, check_every=10, precision=precision)
+        assert out["status"] == flz.FLZ_OK
+        assert out["vals"].shape[0] == cnt
+        check_pairs(csr, out, 1e-10)
+
+
+def test_warm_started_sequence_of_perturbed_potentials():
+    # Self-consistent-field-like sequence on config 2's generator at 15^3: the
+    # potential moves a little each step; each solve starts from the previous
+    # step's eigenvectors. Counts and eigenvalues against dense eigensolves;
+    # the warm starts must take fewer block steps than random starts in all.
+    g = 15
+    rng = np.random.Generator(np.random.PCG64(2025))
+    v0 = 0.5 * rng.random(g ** 3)
+    dv = rng.random(g ** 3) - 0.5
+    prev = None
+    steps_cold, steps_warm = 0, 0
+    for t in range(4):
+        csr = laplacian_3d_7pt(g, g, g, v0 + 0.02 * t * dv)
+        w = np.linalg.eigvalsh(csr.to_dense())
+        win = np.arange(35, 46)
+        k = int(win[np.argmax(w[win + 1] - w[win])])
+        beta = 0.5 * (w[k] + w[k + 1])
+        want = w[w <= beta]
+        h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+        try:
+            outs = {}
+            for mode in ("cold", "warm"):
+                p = flz.flz_params_default()
+                p.block_size = 4
+                p.degree = 60
+                p.check_every = 5
+                p.precision = flz.FLZ_PREC_FX64
+                s = flz.flz_solver_create(h, p)
+                try:
+                    flz.flz_solver_set_interval(s, 0.0, beta)
+                    if mode == "warm" and prev is not None:
+                        flz.flz_solver_set_start_vectors(s, prev)
+                    assert flz.flz_solve(s) == flz.FLZ_OK
+                    outs[mode] = (flz.flz_get_eigenvalues(s), flz.flz_get_stats(s)["iters"],
+                                  flz.get_eigenvectors_host(s, csr.n))
+                finally:
+                    flz.flz_solver_destroy(s)
+        finally:
+            flz.flz_matrix_destroy(h)
+        for mode in ("cold", "warm"):
+            vals = outs[mode][0]
+            assert vals.shape == want.shape
+            assert np.max(np.abs(vals - want)) < 1e-10 * 12.5
+        if t > 0:
+            steps_cold += outs["cold"][1]
+            steps_warm += outs["warm"][1]
+        prev = outs["warm"][2]
+    assert steps_warm < steps_cold, (steps_warm, steps_cold)
+
+
+def test_start_vectors_are_validated_and_cleared():
+    A = laplacian_3d_7pt(8, 8, 8)
+    h = flz.flz_matrix_create_csr(A.n, A.nnz, A.rowptr, A.col, A.val)
+    try:
+        s = flz.flz_solver_create(h, None)
+        try:
+            # null vectors with cols > 0, and a leading dimension below n
+            assert flz.lib().flz_solver_set_start_vectors(s, None, A.n, 3, flz.FLZ_HOST) == flz.FLZ_ERR_INVALID_ARG
+            X = np.asfortranarray(np.random.default_rng(0).standard_normal((A.n, 5)))
+            assert flz.lib().flz_solver_set_start_vectors(s, X.ctypes.data, A.n - 1, 5,
+                                                          flz.FLZ_HOST) == flz.FLZ_ERR_INVALID_ARG
+            flz.flz_solver_set_start_vectors(s, X)
+            flz.flz_solver_set_interval(s, 0.0, 0.6)
+            assert flz.flz_solve(s) == flz.FLZ_OK
+            flz.flz_solver_set_start_vectors(s, None)
+            assert flz.flz_solve(s) == flz.FLZ_OK
+        finally:
+            flz.flz_solver_destroy(s)
+    finally:
+        flz.flz_matrix_destroy(h)
