@@ -151,6 +151,7 @@ def filter_flops_per_launch(n, nnz, r):
 
 
 # bytes per stored value, vector element and running-sum element of each filter arithmetic
+PRECISION_NAMES = {0: "fp64", 1: "fp32", 2: "bf16", 3: "df64", 4: "fx64"}  # flz_precision values
 ELEMENT_BYTES = {"fp64": (8, 8, 8), "fp32": (4, 4, 4), "bf16": (2, 2, 4), "df64": (8, 8, 8), "fx64": (8, 8, 8)}
 KERNEL_NAMES = {
     ("fp64", "forward"): "cheb_sell_kernel<FP64> (fused Chebyshev degree step, SELL-32)",
@@ -359,6 +360,11 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32/BF16-filter solves reported under 'variants'")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch-of-64 leg")
+    ap.add_argument("--batch-legs", default="fp32,fp64,df64,fx64,sequential",
+                    help="--mode batch: the legs to run (a single leg with --batch-once runs one solve, no warm-up)")
+    ap.add_argument("--batch-once", action="store_true", help="--mode batch: one solve per leg, no warm-up (profiling)")
+    ap.add_argument("--batch-block-size", type=int, default=0,
+                    help="--mode batch: block width of the batch legs (0: autotuned, which timings under a profiler distort)")
     ap.add_argument("--ortho-n", type=int, default=1_000_000, help="rows of the --mode ortho basis")
     ap.add_argument("--ortho-basis", type=int, default=120, help="columns of the --mode ortho basis")
     ap.add_argument("--mode", default="solve", choices=["solve", "filter", "batch", "table2", "graph", "slices",
@@ -393,7 +399,9 @@ def main():
     prec = {"fp64": flz.FLZ_PREC_FP64, "fp32": flz.FLZ_PREC_FP32, "bf16": flz.FLZ_PREC_BF16,
             "df64": flz.FLZ_PREC_DF64, "fx64": flz.FLZ_PREC_FX64}[args.precision]
     if args.mode == "batch":
-        print(json.dumps({"mode": "batch", **batch_leg(flz, torch, torch.cuda.current_stream())}))
+        print(json.dumps({"mode": "batch", **batch_leg(flz, torch, torch.cuda.current_stream(),
+                                                        legs=args.batch_legs.split(","), once=args.batch_once,
+                                                        block_size=args.batch_block_size)}))
         return
     if args.mode == "table2":
         return table2_mode(flz, torch, prec, args)
@@ -589,7 +597,7 @@ def variant_leg(flz, torch, h, p, alpha, beta, stream, flush, ref_vals, args):
     return out
 
 
-def batch_leg(flz, torch, stream):
+def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "sequential"), once=False, block_size=0):
     """The batched form against one-at-a-time FP64 solves on the same GPU.
 
     Workload: 64 independent 2D/3D Laplacians with U(0,1) potentials, n
@@ -629,15 +637,18 @@ def batch_leg(flz, torch, stream):
 
     out = {"problems": len(items), "sum_n": int(sum(c.n for c, _, _ in items)), "eigenpairs": total}
     for name, prec, tol in (("batch_fp32", flz.FLZ_PREC_FP32, 1e-6), ("batch_fp64", flz.FLZ_PREC_FP64, 1e-10),
-                            ("batch_df64", flz.FLZ_PREC_DF64, 1e-10)):
+                            ("batch_df64", flz.FLZ_PREC_DF64, 1e-10), ("batch_fx64", flz.FLZ_PREC_FX64, 1e-10)):
+        if name[6:] not in legs:
+            continue
         p = flz.flz_params_default()
-        p.block_size = 0
+        p.block_size = block_size
         p.degree = BATCH_DEGREE
         p.precision = prec
         p.tol = tol
         p.check_every = 5
         bt = flz.flz_batch_create(hs, alphas, betas, p)
-        flz.flz_batch_solve(bt, stream)
+        if not once:
+            flz.flz_batch_solve(bt, stream)
         st, sec = timed(lambda: flz.flz_batch_solve(bt, stream))
         vals = [flz.flz_batch_get_eigenvalues(bt, i) for i in range(len(items))]
         res = [flz.flz_batch_get_residuals(bt, i) for i in range(len(items))]
@@ -646,35 +657,42 @@ def batch_leg(flz, torch, stream):
         ok, err, good = score(vals, res, norms, tol)
         out[name] = {"status": flz.flz_status_string(st), "seconds": sec, "eigenpairs_per_s": good / sec,
                      "tol": tol, "counts_match_oracle": ok, "max_rel_eig_err_vs_oracle": err,
-                     "block_size": stats[0]["block_size"], "max_iters": max(x["iters"] for x in stats)}
+                     "block_size": stats[0]["block_size"], "max_iters": max(x["iters"] for x in stats),
+                     "filter_precision": PRECISION_NAMES.get(stats[0]["filter_precision"]),
+                     "ms_bounds": stats[0]["ms_bounds"], "ms_steps": stats[0]["ms_filter"],
+                     "ms_check": stats[0]["ms_check"], "max_checks": max(x["checks"] for x in stats),
+                     # rows and stored entries times block steps, summed over the problems (filter traffic)
+                     "row_steps": int(sum(x["iters"] * c.n for x, (c, _, _) in zip(stats, items))),
+                     "nnz_steps": int(sum(x["iters"] * c.nnz for x, (c, _, _) in zip(stats, items)))}
         flz.flz_batch_destroy(bt)
-    p = flz.flz_params_default()
-    p.block_size = 4
-    p.degree = BATCH_DEGREE
-    p.check_every = 5
-    solvers = []
-    for h, a, z in zip(hs, alphas, betas):
-        sv = flz.flz_solver_create(h, p)
-        flz.flz_solver_set_interval(sv, a, z)
-        flz.flz_solve(sv, stream)
-        solvers.append(sv)
+    if "sequential" in legs:
+        p = flz.flz_params_default()
+        p.block_size = 4
+        p.degree = BATCH_DEGREE
+        p.check_every = 5
+        solvers = []
+        for h, a, z in zip(hs, alphas, betas):
+            sv = flz.flz_solver_create(h, p)
+            flz.flz_solver_set_interval(sv, a, z)
+            flz.flz_solve(sv, stream)
+            solvers.append(sv)
 
-    def all_solves():
-        return [flz.flz_solve(sv, stream) for sv in solvers]
+        def all_solves():
+            return [flz.flz_solve(sv, stream) for sv in solvers]
 
-    sts, sec = timed(all_solves)
-    vals = [flz.flz_get_eigenvalues(sv) for sv in solvers]
-    res = [flz.flz_get_residuals(sv) for sv in solvers]
-    norms = []
-    for sv in solvers:
-        x = flz.flz_get_stats(sv)
-        norms.append(max(abs(x["lmin"]), abs(x["lmax"])))
-    ok, err, good = score(vals, res, norms, 1e-10)
-    out["sequential_fp64"] = {"status": "FLZ_OK" if all(x == flz.FLZ_OK for x in sts) else "some not converged",
-                              "seconds": sec, "eigenpairs_per_s": good / sec, "tol": 1e-10,
-                              "counts_match_oracle": ok, "max_rel_eig_err_vs_oracle": err, "block_size": 4}
-    for sv in solvers:
-        flz.flz_solver_destroy(sv)
+        sts, sec = timed(all_solves)
+        vals = [flz.flz_get_eigenvalues(sv) for sv in solvers]
+        res = [flz.flz_get_residuals(sv) for sv in solvers]
+        norms = []
+        for sv in solvers:
+            x = flz.flz_get_stats(sv)
+            norms.append(max(abs(x["lmin"]), abs(x["lmax"])))
+        ok, err, good = score(vals, res, norms, 1e-10)
+        out["sequential_fp64"] = {"status": "FLZ_OK" if all(x == flz.FLZ_OK for x in sts) else "some not converged",
+                                  "seconds": sec, "eigenpairs_per_s": good / sec, "tol": 1e-10,
+                                  "counts_match_oracle": ok, "max_rel_eig_err_vs_oracle": err, "block_size": 4}
+        for sv in solvers:
+            flz.flz_solver_destroy(sv)
     for h in hs:
         flz.flz_matrix_destroy(h)
     return out
@@ -906,22 +924,25 @@ def sequence_mode(flz, torch, prec, args):
     """A sequence of related problems (the self-consistent-field setting of
     the paper's Section 1): config 2's matrix with the potential moved by
     0.02 t (U(0,1) - 1/2) at steps t = 0..3, all eigenpairs in [0, beta] with
-    the headline's beta. Each step is solved from a random start block (cold)
-    and from the previous step's eigenvectors (warm,
-    flz_solver_set_start_vectors); both are timed (one solve each, CUDA
-    events) and must return the same eigenvalues."""
+    the headline's beta. Each step is solved from a random start block (cold),
+    by filtered Lanczos from combinations of the previous step's eigenvectors
+    (krylov, flz_solver_set_start_vectors), and by filtered subspace iteration
+    on them (subspace, params.start_mode SUBSPACE); each arm carries its own
+    eigenvectors to its next step. All are timed (one solve each, CUDA events)
+    and must return the same eigenvalues."""
     rng = np.random.Generator(np.random.PCG64(CONFIG2["seed"]))
     g = CONFIG2["grid"]
     v0 = CONFIG2["potential_scale"] * rng.random(g ** 3)
     dv = np.random.Generator(np.random.PCG64(CONFIG2["seed"] + 1)).random(g ** 3) - 0.5
     stream = torch.cuda.current_stream()
-    rows, prev = [], None
+    arms = ("cold", "krylov", "subspace")
+    rows, prev = [], {}
     for t in range(4):
         csr = laplacian_3d_7pt(g, g, g, v0 + 0.02 * t * dv)
         h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
-        row = {"step": t}
-        for mode in ("cold", "warm"):
-            if mode == "warm" and prev is None:
+        row, vals = {"step": t}, {}
+        for mode in arms:
+            if mode != "cold" and t == 0:
                 continue
             p = flz.flz_params_default()
             p.block_size = args.block_size
@@ -929,10 +950,11 @@ def sequence_mode(flz, torch, prec, args):
             p.check_every = args.check_every
             p.precision = prec
             p.tol = args.tol
+            p.start_mode = flz.FLZ_START_SUBSPACE if mode == "subspace" else flz.FLZ_START_KRYLOV
             s = flz.flz_solver_create(h, p)
             flz.flz_solver_set_interval(s, CONFIG2["alpha"], CONFIG2["beta"])
-            if mode == "warm":
-                flz.flz_solver_set_start_vectors(s, prev, ld=csr.n)
+            if mode != "cold":
+                flz.flz_solver_set_start_vectors(s, prev[mode].T, ld=csr.n)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -941,30 +963,32 @@ def sequence_mode(flz, torch, prec, args):
             e1.record(stream)
             torch.cuda.synchronize()
             x = flz.flz_get_stats(s)
-            vals = flz.flz_get_eigenvalues(s)
+            vals[mode] = flz.flz_get_eigenvalues(s)
             row[mode] = {"status": flz.flz_status_string(st), "count": int(x["count"]), "block_steps": int(x["iters"]),
-                         "seconds": e0.elapsed_time(e1) / 1e3, "max_residual": float(flz.flz_get_residuals(s).max())}
-            row[mode + "_vals"] = vals
-            if mode == "warm" or t == 0:
-                nxt = torch.empty((int(x["count"]), csr.n), dtype=torch.float64, device="cuda")
-                flz.lib().flz_get_eigenvectors(s, nxt.data_ptr(), csr.n, int(x["count"]), flz.FLZ_DEVICE)
-                prev_next = nxt
+                         "matvecs": int(x["matvecs"] + x["sweep_matvecs"]), "sweeps": int(x["refine_sweeps"]),
+                         "start_used": int(x["start_used"]), "seconds": e0.elapsed_time(e1) / 1e3,
+                         "max_residual": float(flz.flz_get_residuals(s).max())}
+            nxt = torch.empty((int(x["count"]), csr.n), dtype=torch.float64, device="cuda")
+            flz.lib().flz_get_eigenvectors(s, nxt.data_ptr(), csr.n, int(x["count"]), flz.FLZ_DEVICE)
+            if t == 0:
+                for a in arms:
+                    prev[a] = nxt
+            else:
+                prev[mode] = nxt
             flz.flz_solver_destroy(s)
-        if "warm_vals" in row:
-            a, b = row.pop("cold_vals"), row.pop("warm_vals")
-            row["max_abs_eig_diff_warm_vs_cold"] = float(np.max(np.abs(a - b))) if a.shape == b.shape else None
-        else:
-            row.pop("cold_vals")
-        prev = prev_next.T  # n x count view of the column-major eigenvectors (contiguous columns)
+        for mode in arms[1:]:
+            if mode in vals:
+                a, b = vals["cold"], vals[mode]
+                row["max_abs_eig_diff_%s_vs_cold" % mode] = float(np.max(np.abs(a - b))) if a.shape == b.shape else None
         flz.flz_matrix_destroy(h)
         rows.append(row)
-    cold = sum(r["cold"]["block_steps"] for r in rows[1:])
-    warm = sum(r["warm"]["block_steps"] for r in rows[1:])
-    print(json.dumps({"mode": "sequence", "workload": config_dict(make_matrix(), args)["workload"],
-                      "potential_step": "0.02 t (U(0,1) - 1/2), t = 0..3", "rows": rows,
-                      "block_steps_cold_steps_1_3": cold, "block_steps_warm_steps_1_3": warm,
-                      "seconds_cold_steps_1_3": sum(r["cold"]["seconds"] for r in rows[1:]),
-                      "seconds_warm_steps_1_3": sum(r["warm"]["seconds"] for r in rows[1:])}))
+    out = {"mode": "sequence", "workload": config_dict(make_matrix(), args)["workload"],
+           "potential_step": "0.02 t (U(0,1) - 1/2), t = 0..3", "rows": rows}
+    for mode in arms:
+        out["block_steps_%s_steps_1_3" % mode] = sum(r[mode]["block_steps"] for r in rows[1:])
+        out["matvecs_%s_steps_1_3" % mode] = sum(r[mode]["matvecs"] for r in rows[1:])
+        out["seconds_%s_steps_1_3" % mode] = sum(r[mode]["seconds"] for r in rows[1:])
+    print(json.dumps(out))
 
 
 def ortho_mode(flz, torch, args):

@@ -113,6 +113,30 @@ typedef enum flz_recurrence { FLZ_REC_FORWARD = 0, FLZ_REC_CLENSHAW = 1 } flz_re
  *             own basis and always uses the FP32 pipes. */
 typedef enum flz_ortho { FLZ_ORTHO_AUTO = 0, FLZ_ORTHO_CUDA_CORES = 1, FLZ_ORTHO_TENSOR = 2 } flz_ortho;
 
+/* How a solve uses start vectors (flz_solver_set_start_vectors); both are
+ * additions of this library for sequences of related problems.
+ * KRYLOV:   filtered block Lanczos from a start block of random combinations
+ *           of the start vectors (plus 1 % noise).
+ * SUBSPACE: filtered subspace iteration (Chebyshev-filtered subspace
+ *           iteration, the scheme of the dense-sequence solvers that the
+ *           paper's Section 5 points to) on the start vectors plus guard and
+ *           extra columns: the first sweep applies the solve's filter at half
+ *           its degree to the (random) extra columns, later sweeps to all
+ *           columns a Chebyshev polynomial damping the
+ *           spectrum beyond the block (windows at an end of the spectrum) or
+ *           the solve's filter (interior windows), each followed by
+ *           Rayleigh-Ritz on A in FP64. It ends when every Ritz pair in
+ *           [alpha, beta] has residual <= tol and at least `guard` of the
+ *           block's Ritz values lie outside it. It gives up and the solve
+ *           falls back to KRYLOV after 12 sweeps, when a sweep does not halve
+ *           the largest residual, when the sweeps' rate extrapolated to tol
+ *           needs more than 3 (cols + guard) m products of A with a vector
+ *           (about what filtered Lanczos takes), or when the block loses rank.
+ *           It pays where the window's edge is well separated from the
+ *           block's further eigenvalues; in a dense part of the spectrum the
+ *           Krylov space's polynomial acceleration wins. */
+typedef enum flz_start_mode { FLZ_START_KRYLOV = 0, FLZ_START_SUBSPACE = 1 } flz_start_mode;
+
 typedef struct flz_matrix flz_matrix;
 typedef struct flz_solver flz_solver;
 typedef struct flz_batch flz_batch;
@@ -144,6 +168,7 @@ typedef struct flz_params {
                            extra Ritz pairs are refined to tol by filtered subspace iteration with the
                            FX64 filter (FP64 where it does not apply) and Rayleigh-Ritz on A in FP64: the
                            mixed-precision form (not in the paper). See flz_stats.refine_sweeps. */
+  int32_t start_mode;   /* flz_start_mode, used when start vectors are set; default FLZ_START_KRYLOV */
 } flz_params;
 
 /* One convergence check of a solve (Section 3.2.2's periodic Rayleigh-Ritz
@@ -186,7 +211,10 @@ typedef struct flz_stats {
   int32_t filter_precision; /* flz_precision the filter ran in (FX64 requested may run as FP64) */
   int32_t refine_sweeps;    /* refinement sweeps (params.refine), 0 if none */
   int32_t refine_degree;    /* largest filter degree of a refinement sweep */
-  double ms_refine;         /* refinement time (included in ms_total) */
+  double ms_refine;         /* refinement or subspace-start time (included in ms_total) */
+  int64_t sweep_matvecs;    /* products of A with a vector in the subspace sweeps (columns x degree) */
+  int32_t start_used;       /* 0: random start block; 1: Krylov start from the start vectors;
+                               2: the subspace start converged (no block Lanczos steps) */
 } flz_stats;
 
 /* ---- status and parameters ------------------------------------------------ */
@@ -394,10 +422,13 @@ flz_status flz_solver_set_interval(flz_solver* s, double alpha, double beta);
  * iterations of Section 1 solve one eigenproblem per step with a slowly
  * changing potential; an addition of this library): the start block of the
  * solver's following solves is r random combinations of these `cols` vectors
- * plus noise of 1 % of their size, orthonormalized, instead of a random block.
- * Pass the eigenvectors of the previous problem (flz_get_eigenvectors): the
- * filtered Krylov space then reaches the wanted eigenvectors in fewer block
- * steps. X is n x cols column-major with leading dimension ld >= n, host or
+ * plus noise of 1 % of their size, orthonormalized, instead of a random block
+ * (params.start_mode KRYLOV), or the vectors themselves start filtered
+ * subspace iteration (SUBSPACE, see flz_start_mode). Pass the eigenvectors of
+ * the previous problem (flz_get_eigenvectors). With KRYLOV the guard pairs
+ * beyond the window still have to be found from the noise, so the step count
+ * rarely falls; SUBSPACE needs far fewer products of A with a vector when the
+ * problems are close. X is n x cols column-major with leading dimension ld >= n, host or
  * device (`where`); the library copies it. cols = 0 clears it (random start
  * blocks again). Not for the double-FP32 precision (INVALID_ARG). */
 flz_status flz_solver_set_start_vectors(flz_solver* s, const double* X, int64_t ld, int32_t cols,

@@ -38,6 +38,7 @@ FLZ_HOST, FLZ_DEVICE = 0, 1
 FLZ_PREC_FP64, FLZ_PREC_FP32, FLZ_PREC_BF16, FLZ_PREC_DF64, FLZ_PREC_FX64 = 0, 1, 2, 3, 4
 FLZ_REC_FORWARD, FLZ_REC_CLENSHAW = 0, 1
 FLZ_ORTHO_AUTO, FLZ_ORTHO_CUDA_CORES, FLZ_ORTHO_TENSOR = 0, 1, 2
+FLZ_START_KRYLOV, FLZ_START_SUBSPACE = 0, 1
 
 # Every symbol include/flz.h declares.
 EXPORTED = (
@@ -61,6 +62,7 @@ class flz_params(ctypes.Structure):
         ("lmax", ctypes.c_double), ("damping", ctypes.c_int32),
         ("recurrence", ctypes.c_int32), ("transition", ctypes.c_double), ("ortho", ctypes.c_int32),
         ("refine", ctypes.c_int32),
+        ("start_mode", ctypes.c_int32),
     ]
 
 
@@ -75,6 +77,7 @@ class flz_stats(ctypes.Structure):
         ("ms_total", ctypes.c_double), ("basis_vectors", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64), ("ortho", ctypes.c_int32), ("filter_precision", ctypes.c_int32),
         ("refine_sweeps", ctypes.c_int32), ("refine_degree", ctypes.c_int32), ("ms_refine", ctypes.c_double),
+        ("sweep_matvecs", ctypes.c_int64), ("start_used", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -225,6 +225,7 @@ flz_status flz_params_default(flz_params* p) {
   p->recurrence = FLZ_REC_FORWARD;
   p->transition = 0.0;
   p->ortho = FLZ_ORTHO_AUTO;
+  p->start_mode = FLZ_START_KRYLOV;
   return FLZ_OK;
 }
 
@@ -557,7 +558,8 @@ flz_status flz_solver_create(flz_matrix* A, const flz_params* params, flz_solver
   if (p.degree < 0 || p.max_degree < 1 || p.check_every < 1 || !(p.tol > 0.0) || !(p.degree_eps > 0.0) ||
       p.bounds_steps < 1 || p.max_basis < 0 || p.guard < 0 || p.damping < 0 || p.damping > 2 || !(p.transition >= 0.0) ||
       (p.recurrence != FLZ_REC_FORWARD && p.recurrence != FLZ_REC_CLENSHAW) || p.ortho < FLZ_ORTHO_AUTO ||
-      p.ortho > FLZ_ORTHO_TENSOR || p.refine < 0 || p.refine > 1)
+      p.ortho > FLZ_ORTHO_TENSOR || p.refine < 0 || p.refine > 1 ||
+      (p.start_mode != FLZ_START_KRYLOV && p.start_mode != FLZ_START_SUBSPACE))
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.ortho == FLZ_ORTHO_TENSOR && (!flz::TcBasis::supported(p.block_size) || p.precision == FLZ_PREC_DF64))
     fail(FLZ_ERR_INVALID_ARG, "tensor-core reorthogonalization needs an FP64 basis (not the double-FP32 precision)");

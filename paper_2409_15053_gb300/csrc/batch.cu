@@ -43,6 +43,8 @@ struct flz_batch {
   std::vector<std::vector<double>> evals, resid;
   std::vector<std::unique_ptr<flz::DevBuf<double>>> evecs;  // n_i x count_i column-major
   std::vector<flz_stats> stats;
+  int32_t max_row_nnz = 0;  // longest row of any problem
+  flz::FxBatch fxb;         // the fixed-point filter's layout and tables
 };
 
 namespace flz {
@@ -590,6 +592,19 @@ struct BatchEngine {
     FLZ_CUDA(cudaMemcpyAsync(mdeg.p, m.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st));
     FLZ_CUDA(cudaMemcpyAsync(cc.p, c.data(), sizeof(double) * count, cudaMemcpyHostToDevice, st));
     FLZ_CUDA(cudaMemcpyAsync(ee.p, e.data(), sizeof(double) * count, cudaMemcpyHostToDevice, st));
+    if (precision == FLZ_PREC_FX64) {
+      // the fixed-point filter where its format holds every problem, else FP64
+      if (fx_batch_prepare(B->fxb, N, B->nnz, B->rowptr.p, B->col.p, B->val.p, B->diag_pos.p, B->max_row_nnz,
+                           B->d_off.p, count, cc.p, ee.p, r, st) &&
+          fx_batch_coefficients(B->fxb, coeffs, st))
+        return;
+      precision = FLZ_PREC_FP64;
+      const size_t nr = (size_t)N * r;
+      v64.reserve(nr);
+      ya64.reserve(nr);
+      yb64.reserve(nr);
+      sval64.reserve((size_t)B->nnz);
+    }
     const size_t sm = sizeof(int) * (count + 1);
     if (precision == FLZ_PREC_FP64)
       seg_scale_kernel<double><<<gsb(N), 256, sm, st>>>(N, B->rowptr.p, B->diag_pos.p, B->val.p, B->d_off.p, count, cc.p, ee.p, sval64.p);
@@ -661,7 +676,9 @@ struct BatchEngine {
   template <int R>
   void apply_filter() {
     const long long nr = N * R;
-    if (precision == FLZ_PREC_FP64) {
+    if (precision == FLZ_PREC_FX64) {
+      fx_batch_filter(B->fxb, R, Q.p, jdev.p, B->d_off.p, mdeg.p, active.p, W.p, pdl, st);
+    } else if (precision == FLZ_PREC_FP64) {
       // V = Q_j in a fixed buffer (the graph is replayed with a moving j); the sum is W
       load_block_kernel<double><<<gsb(nr), 256, 0, st>>>(Q.p, jdev.p, nr, v64.p);
       FLZ_LAUNCH_CHECK();
@@ -957,6 +974,7 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
   E.setup(B, R, nbmax, p.precision, st);
   E.set_active(act);
   E.set_filter(cvec, evec, coeffs);
+  for (int i = 0; i < count; ++i) B->stats[i].filter_precision = E.precision;
   E.start_block<R>(p.seed);
 
   const int guard = p.guard > 0 ? p.guard : std::max(R, 3);
@@ -997,6 +1015,7 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
     const auto tc = std::chrono::steady_clock::now();
     int hfail = 0;
     FLZ_CUDA(cudaMemcpy(&hfail, E.fail.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (E.precision == FLZ_PREC_FX64) fx_batch_check_flag(B->fxb, st);
     std::vector<double> Dh((size_t)count * nbmax * R * R), Sh(Dh.size());
     FLZ_CUDA(cudaMemcpy(Dh.data(), E.Dh.p, sizeof(double) * Dh.size(), cudaMemcpyDeviceToHost));
     FLZ_CUDA(cudaMemcpy(Sh.data(), E.Sh.p, sizeof(double) * Sh.size(), cudaMemcpyDeviceToHost));
@@ -1015,7 +1034,8 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
       for (int q = 0; q < K; ++q) w.order[q] = K - 1 - q;
       const int m = B->stats[i].degree;
       const double anorm = std::max(std::fabs(B->stats[i].lmin), std::fabs(B->stats[i].lmax));
-      const double p_gate = std::min(p.precision == FLZ_PREC_FP64 ? 1e-2 : 1e-1,
+      const bool fp64_class = E.precision == FLZ_PREC_FP64 || E.precision == FLZ_PREC_FX64;
+      const double p_gate = std::min(fp64_class ? 1e-2 : 1e-1,
                                      10.0 * 1.1 * (double)m * m * p.tol * anorm / B->stats[i].e);
       const int g_cnt = std::min(gate_len[i], K);
       const double* S = &Sh[((size_t)i * nbmax + k - 1) * R * R];
@@ -1119,13 +1139,9 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
               std::swap(grown.p, buf.p);
               std::swap(grown.count, buf.count);
             }
-            rows_to_columns(X.p + (size_t)B->off[i] * 16 + t, n_i, 1, 16, buf.p + (size_t)found[i] * n_i, n_i, st);
-            std::vector<double> sc(1, 1.0 / std::sqrt(xx));
-            DevBuf<double> scd;
-            scd.reserve(1);
-            FLZ_CUDA(cudaMemcpyAsync(scd.p, sc.data(), sizeof(double), cudaMemcpyHostToDevice, st));
-            basis_update(buf.p + (size_t)found[i] * n_i, 1, n_i, 1, scd.p, 1, 1.0, 0.0, buf.p + (size_t)found[i] * n_i, 1, st);
-            FLZ_CUDA(cudaStreamSynchronize(st));
+            // the unit eigenvector, in one launch with no host round trip
+            rows_to_columns(X.p + (size_t)B->off[i] * 16 + t, n_i, 1, 16, buf.p + (size_t)found[i] * n_i, n_i, st,
+                            1.0 / std::sqrt(xx));
             found_vals[i].push_back(l);
             found_res[i].push_back(res);
             ++found[i];
@@ -1311,8 +1327,8 @@ flz_status flz_batch_create(int32_t count, flz_matrix* const* mats, const double
       p.damping < 0 || p.damping > 2 || !(p.transition >= 0.0))
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.recurrence != FLZ_REC_FORWARD) fail(FLZ_ERR_INVALID_ARG, "batches use the forward recurrence only");
-  if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_DF64)
-    fail(FLZ_ERR_INVALID_ARG, "batches support the FP64, FP32 and BF16 filters");
+  if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_FX64)
+    fail(FLZ_ERR_INVALID_ARG, "batches support the FP64, FP32, BF16, double-FP32 and fixed-point filters");
   std::unique_ptr<flz_batch> B(new flz_batch());
   B->count = count;
   B->p = p;
@@ -1327,6 +1343,7 @@ flz_status flz_batch_create(int32_t count, flz_matrix* const* mats, const double
     if ((int64_t)B->off[i] + mats[i]->n > 2147483647LL) fail(FLZ_ERR_INVALID_ARG, "total rows exceed int32");
     B->off[i + 1] = B->off[i] + (int)mats[i]->n;
     nnz += mats[i]->nnz;
+    B->max_row_nnz = std::max(B->max_row_nnz, mats[i]->max_row_nnz);
   }
   if (nnz > 2147483647LL) fail(FLZ_ERR_INVALID_ARG, "total nnz exceeds int32");
   B->N = B->off[count];

@@ -291,12 +291,26 @@ __global__ void random_normal_kernel(T* __restrict__ X, long long count, uint64_
 }
 
 __global__ void rows_to_columns_kernel(const double* __restrict__ X, long long n, int s, int ld,
-                                       double* __restrict__ out, long long ldo) {
+                                       double* __restrict__ out, long long ldo, double scale) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n * s;
        e += (long long)gridDim.x * blockDim.x) {
     const long long i = e / s;
     const int t = (int)(e - i * s);
-    out[(size_t)t * ldo + i] = X[(size_t)i * ld + t];
+    out[(size_t)t * ldo + i] = scale * X[(size_t)i * ld + t];
+  }
+}
+
+__global__ void columns_to_blocks_kernel(const double* __restrict__ X, long long n, long long ldx, int cols,
+                                         double* __restrict__ Out) {
+  // one thread per (row, column) pair, consecutive threads along a row of a block
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n * cols;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(e / (n * 16));
+    const long long rem = e - (long long)b * n * 16;
+    const int width = cols - 16 * b < 16 ? cols - 16 * b : 16;
+    const long long i = rem / width;
+    const int t = (int)(rem - i * width);
+    Out[(size_t)b * n * 16 + (size_t)i * 16 + t] = X[(size_t)(16 * b + t) * ldx + i];
   }
 }
 
@@ -597,8 +611,15 @@ void random_normal(dfloat* X, int64_t count, uint64_t seed, uint64_t offset, cud
   FLZ_LAUNCH_CHECK();
 }
 
-void rows_to_columns(const double* X, int64_t n, int s, int ld, double* out, int64_t ldo, cudaStream_t st) {
-  rows_to_columns_kernel<<<gs_blocks(n * s), 256, 0, st>>>(X, n, s, ld, out, ldo);
+void rows_to_columns(const double* X, int64_t n, int s, int ld, double* out, int64_t ldo, cudaStream_t st,
+                     double scale) {
+  rows_to_columns_kernel<<<gs_blocks(n * s), 256, 0, st>>>(X, n, s, ld, out, ldo, scale);
+  FLZ_LAUNCH_CHECK();
+}
+
+void columns_to_blocks(const double* X, int64_t n, int64_t ldx, int cols, double* Out, cudaStream_t st) {
+  if (cols <= 0 || n <= 0) return;
+  columns_to_blocks_kernel<<<gs_blocks(n * cols), 256, 0, st>>>(X, n, ldx, cols, Out);
   FLZ_LAUNCH_CHECK();
 }
 

@@ -730,4 +730,357 @@ void fx_check_flag(flz_matrix* A) {
   }
 }
 
+
+// ---- batches ------------------------------------------------------------------
+// The same degree step over the block-diagonal concatenation of a batch's
+// problems: each row takes its problem's coefficients, sum scaling, degree
+// and active flag; a CTA whose rows all belong to finished problems returns
+// before staging anything.
+
+namespace {
+
+struct FxSegArgs {
+  int n, nsl, emax, vec_bulk, count;
+  const int* off;         // SELL slice offsets of the concatenation
+  const int* scol;
+  const uint64_t* sval;   // 2 Ahat_i, offset-binary, units 2^-61
+  const int* d_off;       // count + 1 problem row offsets
+  const uint64_t* bfix;   // coefficient table: b_k of problem i at k * count + i
+  const int* sexp;        // per-problem sum exponent s_i
+  const int* zexp;        // 16 zero column exponents (unit columns)
+  const int* mdeg;        // per-problem degree m_i
+  const int* active;
+  uint64_t* acc;          // running sums (aliases W)
+  double* W;
+  int vec_bits;
+  uint64_t limit;
+  unsigned* flag;
+  uint64_t wait_ns;
+};
+
+__device__ __forceinline__ int seg_problem(const int* __restrict__ d_off, int count, int row) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(d_off + mid) <= row) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int R, int U, bool FIRST>
+__global__ void __launch_bounds__(kThreads, R <= 4 ? 4 : (R <= 8 ? 2 : 1)) fx_seg_sell_kernel(FxSegArgs a, int k, const uint64_t* __restrict__ ycur,
+                                                               const uint64_t* yprev, uint64_t* ynext) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);         // [0] matrix range, [1] vector rows
+  int* s_live = reinterpret_cast<int*>(smem + 16);
+  uint64_t* s_own = reinterpret_cast<uint64_t*>(smem + 32);  // V (first step) or Y_{k-1} rows
+  uint64_t* s_sum = s_own + kThreads * R;                    // running-sum rows
+  uint64_t* s_val = s_sum + kThreads * R;
+  int* s_col = reinterpret_cast<int*>(s_val + a.emax);
+  const int row0 = blockIdx.x * kThreads, rows = min(kThreads, a.n - row0);
+  if (threadIdx.x == 0) {
+    int live = 0;
+    const int p0 = seg_problem(a.d_off, a.count, row0), p1 = seg_problem(a.d_off, a.count, row0 + rows - 1);
+    for (int i = p0; i <= p1 && !live; ++i) live = __ldg(a.active + i) && k + 1 <= __ldg(a.mdeg + i);
+    *s_live = live;
+  }
+  __syncthreads();
+  if (!*s_live) return;  // reads nothing the previous degree writes
+  const int sl0 = blockIdx.x * 8, sl1 = min(a.nsl, sl0 + 8);
+  const int e0 = __ldg(a.off + sl0), e1 = __ldg(a.off + sl1);
+  const bool vb = a.vec_bulk && ((rows * R) % 2 == 0);  // uniform over the CTA
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
+    tc::fence_mbar_init();
+    tc::mbar_expect_tx(&bar[0], (uint32_t)(e1 - e0) * 12u);
+    tc::bulk_g2s(s_val, a.sval + e0, (uint32_t)(e1 - e0) * 8u, &bar[0]);
+    tc::bulk_g2s(s_col, a.scol + e0, (uint32_t)(e1 - e0) * 4u, &bar[0]);
+  }
+  __syncthreads();
+  allow_dependents();
+  grid_dependency_wait();  // the vectors below are the previous degree's output
+  if (threadIdx.x == 0 && vb) {
+    const uint32_t bytes = (uint32_t)rows * R * 8u;
+    const size_t at = (size_t)row0 * R;
+    if (FIRST) {
+      tc::mbar_expect_tx(&bar[1], bytes);
+      tc::bulk_g2s(s_own, ycur + at, bytes, &bar[1]);
+    } else {
+      tc::mbar_expect_tx(&bar[1], 2 * bytes);
+      tc::bulk_g2s(s_own, yprev + at, bytes, &bar[1]);
+      tc::bulk_g2s(s_sum, a.acc + at, bytes, &bar[1]);
+    }
+  }
+  const int t = threadIdx.x, row = row0 + t;
+  int pi = 0, md = 0;
+  bool active = row < a.n;
+  if (active) {
+    pi = seg_problem(a.d_off, a.count, row);
+    md = __ldg(a.mdeg + pi);
+    active = __ldg(a.active + pi) && k + 1 <= md;
+  }
+  Acc S[R];
+#pragma unroll
+  for (int c = 0; c < R; ++c) acc_init(S[c], FIRST ? kValBits + 1 : kValBits);
+  uint64_t sa = 0;
+  const bool ok0 = stage_wait(&bar[0], a.flag, a.wait_ns);
+  if (active && ok0) {
+    const int sl = row >> 5;
+    const int so = __ldg(a.off + sl);
+    const int w = (__ldg(a.off + sl + 1) - so) >> 5;
+    const int loc = so - e0 + (row & 31);
+    int j = 0;
+    for (; j + U <= w; j += U) {
+      int cj[U];
+      uint64_t av[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        cj[u] = s_col[loc + 32 * (j + u)];
+        av[u] = s_val[loc + 32 * (j + u)];
+      }
+      uint64_t y[U][R];
+#pragma unroll
+      for (int u = 0; u < U; ++u) load_u64_row<R>(ycur + (size_t)cj[u] * R, y[u]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        sa += av[u];
+#pragma unroll
+        for (int c = 0; c < R; ++c) mac(S[c], av[u], y[u][c]);
+      }
+    }
+    for (; j < w; ++j) {
+      const int cj = s_col[loc + 32 * j];
+      const uint64_t av = s_val[loc + 32 * j];
+      uint64_t y[R];
+      load_u64_row<R>(ycur + (size_t)cj * R, y);
+      sa += av;
+#pragma unroll
+      for (int c = 0; c < R; ++c) mac(S[c], av, y[c]);
+    }
+  }
+  const bool ok1 = vb ? stage_wait(&bar[1], a.flag, a.wait_ns) : true;
+  if (active && ok0 && ok1) {
+    const size_t idx = (size_t)row * R;
+    FxStep ks{FIRST ? __ldg(a.bfix + pi) : 0ull, __ldg(a.bfix + (size_t)(k + 1) * a.count + pi), a.zexp,
+              __ldg(a.sexp + pi), a.vec_bits, a.limit, a.flag, a.wait_ns};
+    uint64_t own[R], sum[R];
+    if (vb) {
+#pragma unroll
+      for (int c = 0; c < R; ++c) {
+        own[c] = s_own[t * R + c];
+        sum[c] = FIRST ? 0ull : s_sum[t * R + c];
+      }
+    } else {
+      load_u64_row<R>((FIRST ? ycur : yprev) + idx, own);
+      if (FIRST) {
+#pragma unroll
+        for (int c = 0; c < R; ++c) sum[c] = 0ull;
+      } else {
+        load_u64_row<R>(a.acc + idx, sum);
+      }
+    }
+    if (k + 1 == md) finish_row<R, FIRST, true>(idx, S, sa, own, sum, ynext, a.acc, a.W, ks);
+    else finish_row<R, FIRST, false>(idx, S, sa, own, sum, ynext, a.acc, a.W, ks);
+  }
+  // nothing may still be copying into this CTA's shared memory when it exits
+  if (!ok0) tc::mbar_wait_drain(&bar[0], 0);
+  if (!ok1) tc::mbar_wait_drain(&bar[1], 0);
+}
+
+// Y_0 = round(Q_j 2^F), offset-binary (unit columns: column exponent 0)
+__global__ void fx_seg_load_kernel(const double* __restrict__ Q, const int* __restrict__ jdev, int64_t nr, int vec_bits,
+                                   uint64_t* __restrict__ y0) {
+  const double* src = Q + (size_t)(*jdev) * nr;
+  const double sc = pow2(vec_bits);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nr; i += (int64_t)gridDim.x * blockDim.x)
+    y0[i] = (uint64_t)__double2ll_rn(src[i] * sc) + kOff;
+}
+
+// 2 Ahat_i in the SELL-32 layout of the concatenation, each row in its
+// problem's map; records the largest absolute row sum.
+__global__ void fx_seg_values_kernel(int64_t n, const int* __restrict__ rowptr, const int* __restrict__ diag_pos,
+                                     const double* __restrict__ val, const int* __restrict__ off,
+                                     const int* __restrict__ d_off, int count, const double* __restrict__ cc,
+                                     const double* __restrict__ ee, uint64_t* __restrict__ out,
+                                     unsigned long long* __restrict__ rowsum_bits) {
+  double big = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int pi = seg_problem(d_off, count, (int)i);
+    const double s = 2.0 / ee[pi], shift = cc[pi];
+    const int j0 = rowptr[i], len = rowptr[i + 1] - j0, d = diag_pos[i];
+    const int64_t sl = i >> 5;
+    const int base = off[sl] + (int)(i & 31);
+    const int w = (off[sl + 1] - off[sl]) >> 5;
+    double rs = 0.0;
+    for (int j = 0; j < w; ++j) {
+      double v = 0.0;
+      if (j < len) v = s * (val[j0 + j] - (j0 + j == d ? shift : 0.0));
+      rs += fabs(v);
+      out[base + 32 * j] = (uint64_t)__double2ll_rn(v * 0x1p61) + kOff;
+    }
+    big = fmax(big, rs);
+  }
+  for (int d = 16; d > 0; d >>= 1) big = fmax(big, __shfl_xor_sync(0xffffffffu, big, d));
+  if ((threadIdx.x & 31) == 0 && big > 0.0) atomicMax(rowsum_bits, (unsigned long long)__double_as_longlong(big));
+}
+
+size_t seg_stage_bytes(int R, int64_t emax) { return 32 + 2 * (size_t)kThreads * R * 8 + (size_t)emax * 12; }
+
+template <int R, int U, bool FIRST>
+void seg_stage_limit(size_t bytes) {
+  static size_t done = 0;
+  if (bytes > done) {
+    FLZ_CUDA(cudaFuncSetAttribute(fx_seg_sell_kernel<R, U, FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)bytes));
+    done = bytes;
+  }
+}
+
+template <int R, int U>
+void run_fx_seg(FxBatch& F, const FxSegArgs& a, bool pdl, cudaStream_t st) {
+  const unsigned grid = (unsigned)((F.n + kThreads - 1) / kThreads);
+  const size_t smem = seg_stage_bytes(R, F.emax);
+  seg_stage_limit<R, U, true>(smem);
+  seg_stage_limit<R, U, false>(smem);
+  fx_seg_sell_kernel<R, U, true><<<grid, kThreads, smem, st>>>(a, 0, F.y0.p, nullptr, F.ya.p);
+  FLZ_LAUNCH_CHECK();
+  const uint64_t* prev = F.y0.p;
+  const uint64_t* cur = F.ya.p;
+  for (int k = 1; k < F.mmax; ++k) {
+    uint64_t* next = (k == 1) ? F.yb.p : const_cast<uint64_t*>(prev);
+    if (pdl)
+      launch_dependent(fx_seg_sell_kernel<R, U, false>, grid, kThreads, smem, st, a, k, cur, prev, next);
+    else
+      fx_seg_sell_kernel<R, U, false><<<grid, kThreads, smem, st>>>(a, k, cur, prev, next);
+    FLZ_LAUNCH_CHECK();
+    prev = cur;
+    cur = next;
+  }
+}
+
+}  // namespace
+
+bool fx_batch_prepare(FxBatch& F, int64_t N, int64_t nnz, const int* rowptr, const int* col, const double* val,
+                      const int* diag_pos, int32_t max_row_nnz, const int* d_off, int count, const double* cc,
+                      const double* ee, int r, cudaStream_t st) {
+  if (!fx_supported(r) || max_row_nnz > kLongRow) return false;
+  if (!F.layout_built) {
+    F.layout_built = true;
+    F.layout_ok = false;
+    flz_matrix tmp;  // borrows the concatenation's structure to build its SELL-32 layout
+    tmp.n = N;
+    tmp.nnz = nnz;
+    tmp.rowptr.p = const_cast<int*>(rowptr);
+    tmp.col.p = const_cast<int*>(col);
+    build_sell(&tmp);
+    tmp.rowptr.p = nullptr;
+    tmp.col.p = nullptr;
+    if (tmp.sell) {
+      std::swap(F.sell_off.p, tmp.sell_off.p);
+      std::swap(F.sell_off.count, tmp.sell_off.count);
+      std::swap(F.sell_col.p, tmp.sell_col.p);
+      std::swap(F.sell_col.count, tmp.sell_col.count);
+      F.n = N;
+      F.nsl = (N + 31) / 32;
+      F.emax = tmp.sell_cta_entries;
+      F.sval.reserve((size_t)std::max<int64_t>(tmp.sell_len, 1));
+      F.zexp.reserve(16);
+      FLZ_CUDA(cudaMemset(F.zexp.p, 0, sizeof(int) * 16));
+      F.flag.reserve(2);
+      FLZ_CUDA(cudaMemset(F.flag.p, 0, sizeof(unsigned) * 2));
+      FLZ_CUDA(cudaMallocHost(reinterpret_cast<void**>(&F.flag_host), sizeof(unsigned)));
+      *F.flag_host = 0;
+      F.layout_ok = true;
+    }
+  }
+  if (!F.layout_ok || seg_stage_bytes(r, F.emax) > kMaxStage) return false;
+  F.count = count;
+  unsigned long long* bits_dev = reinterpret_cast<unsigned long long*>(F.flag.p);  // the flag words, reused
+  FLZ_CUDA(cudaMemsetAsync(bits_dev, 0, sizeof(unsigned long long), st));
+  fx_seg_values_kernel<<<blocks_for(N), 256, 0, st>>>(N, rowptr, diag_pos, val, F.sell_off.p, d_off, count, cc, ee,
+                                                      F.sval.p, bits_dev);
+  FLZ_LAUNCH_CHECK();
+  unsigned long long bits = 0;
+  FLZ_CUDA(cudaMemcpyAsync(&bits, bits_dev, sizeof(bits), cudaMemcpyDeviceToHost, st));
+  FLZ_CUDA(cudaStreamSynchronize(st));
+  FLZ_CUDA(cudaMemsetAsync(bits_dev, 0, sizeof(unsigned long long), st));
+  std::memcpy(&F.rowsum, &bits, sizeof(double));
+  if (!(F.rowsum <= kRowSumLimit)) return false;
+  F.vec_bits = F.rowsum <= kRowSumFine ? 61 : 60;
+  const size_t nr2 = ((size_t)N * r + 1) & ~size_t(1);
+  F.y0.reserve(nr2);
+  F.ya.reserve(nr2);
+  F.yb.reserve(nr2);
+  return true;
+}
+
+bool fx_batch_coefficients(FxBatch& F, const std::vector<std::vector<double>>& coeffs, cudaStream_t st) {
+  const int count = (int)coeffs.size();
+  int mmax = 0;
+  for (const auto& v : coeffs) {
+    if (v.size() < 2) return false;  // degree 0: no recurrence step
+    mmax = std::max(mmax, (int)v.size() - 1);
+  }
+  std::vector<uint64_t> table((size_t)(mmax + 1) * count, kOff);
+  std::vector<int> sexp(count);
+  for (int i = 0; i < count; ++i) {
+    // the same scaling as a single application: the running sum below
+    // 0.9375 2^(63-F) and every scaled |b_k| below 3.9
+    double partial = 0.0, big = 0.0, bmax = 0.0;
+    for (double b : coeffs[i]) {
+      partial += std::fabs(b);
+      big = std::max(big, partial);
+      bmax = std::max(bmax, std::fabs(b));
+    }
+    int sc = 0;
+    while (big * 1.25 * std::ldexp(1.0, -sc) >= 0.9375 * std::ldexp(1.0, 63 - F.vec_bits) ||
+           bmax * std::ldexp(1.0, -sc) >= 3.9)
+      ++sc;
+    if (sc > 60) return false;
+    sexp[i] = sc;
+    for (size_t q = 0; q < coeffs[i].size(); ++q)
+      table[q * count + i] = (uint64_t)std::llrint(std::ldexp(coeffs[i][q], kValBits - sc)) + kOff;
+  }
+  F.mmax = mmax;
+  F.bfix.reserve(table.size());
+  F.sexp.reserve(count);
+  FLZ_CUDA(cudaMemcpyAsync(F.bfix.p, table.data(), sizeof(uint64_t) * table.size(), cudaMemcpyHostToDevice, st));
+  FLZ_CUDA(cudaMemcpyAsync(F.sexp.p, sexp.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st));
+  FLZ_CUDA(cudaStreamSynchronize(st));  // the host tables go out of scope
+  return true;
+}
+
+void fx_batch_filter(FxBatch& F, int r, const double* Q, const int* jdev, const int* d_off, const int* mdeg,
+                     const int* active, double* W, bool pdl, cudaStream_t st) {
+  const int64_t nr = F.n * (int64_t)r;
+  fx_seg_load_kernel<<<blocks_for(nr), 256, 0, st>>>(Q, jdev, nr, F.vec_bits, F.y0.p);
+  FLZ_LAUNCH_CHECK();
+  FxSegArgs a{(int)F.n, (int)F.nsl, (int)F.emax, reinterpret_cast<uintptr_t>(W) % 16 == 0 ? 1 : 0, F.count,
+              F.sell_off.p, F.sell_col.p, F.sval.p, d_off, F.bfix.p, F.sexp.p, F.zexp.p, mdeg, active,
+              reinterpret_cast<uint64_t*>(W), W, F.vec_bits, 5ull << (F.vec_bits - 2), F.flag.p, wait_limit_ns()};
+  switch (r) {
+    case 1: run_fx_seg<1, 8>(F, a, pdl, st); break;
+    case 2: run_fx_seg<2, 8>(F, a, pdl, st); break;
+    case 4: run_fx_seg<4, 4>(F, a, pdl, st); break;
+    case 8: run_fx_seg<8, 2>(F, a, pdl, st); break;
+    case 16: run_fx_seg<16, 1>(F, a, pdl, st); break;
+    default: fail(FLZ_ERR_INVALID_ARG, "batch block width %d", r);
+  }
+}
+
+void fx_batch_check_flag(FxBatch& F, cudaStream_t st) {
+  if (!F.flag_host) return;
+  FLZ_CUDA(cudaMemcpyAsync(F.flag_host, F.flag.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  FLZ_CUDA(cudaStreamSynchronize(st));
+  const unsigned f = *F.flag_host;
+  if (!f) return;
+  *F.flag_host = 0;
+  FLZ_CUDA(cudaMemsetAsync(F.flag.p, 0, sizeof(unsigned), st));
+  if (f & 2u) fail(FLZ_ERR_TIMEOUT, "batch fixed-point filter: a shared-memory stage wait expired");
+  fail(FLZ_ERR_INVALID_ARG, "batch fixed-point filter: a recurrence value left [-1.25, 1.25] (a spectrum of some "
+                            "(A_i - c_i I)/e_i is not inside [-1, 1])");
+}
+
 }  // namespace flz

@@ -176,6 +176,28 @@ struct FxValues {
     if (flag_host) cudaFreeHost(flag_host);
   }
 };
+
+// The fixed-point filter of a batch (the block-diagonal concatenation of its
+// problems): SELL-32 layout of the concatenation, its values 2 Ahat_i in each
+// problem's own map, per-problem coefficient tables and the recurrence
+// vectors.
+struct FxBatch {
+  bool layout_built = false, layout_ok = false;
+  int64_t n = 0, nsl = 0, emax = 0;
+  DevBuf<int32_t> sell_off, sell_col;
+  DevBuf<uint64_t> sval, y0, ya, yb, bfix;
+  DevBuf<int> sexp, zexp;
+  DevBuf<unsigned> flag;
+  unsigned* flag_host = nullptr;
+  int vec_bits = 61, mmax = 0, count = 0;
+  double rowsum = 0.0;
+  FxBatch() = default;
+  FxBatch(const FxBatch&) = delete;
+  FxBatch& operator=(const FxBatch&) = delete;
+  ~FxBatch() {
+    if (flag_host) cudaFreeHost(flag_host);
+  }
+};
 }  // namespace flz
 
 // Matrix handle: a device copy of a symmetric CSR matrix (Section 3.2.1).
@@ -278,6 +300,26 @@ bool fx_filter_apply(flz_matrix* A, double c, double e, const double* coeffs, in
                      double* W, cudaStream_t st);
 bool fx_supported(int r);
 void fx_check_flag(flz_matrix* A);
+// Batches. fx_batch_prepare builds the SELL-32 layout of the concatenation
+// (once) and the fixed-point values of every problem's 2 Ahat_i = (2/e_i)(A_i -
+// c_i I) (cc, ee: device arrays of c_i, e_i; d_off: the count + 1 row offsets);
+// false where the fixed-point filter does not apply (padding above 30 %, rows
+// longer than 256 entries, a shared-memory stage above its limit at width r,
+// or a row of some 2 Ahat_i with absolute sum above 3.9): the batch then uses
+// FP64. fx_batch_coefficients loads the per-problem coefficient tables
+// (offset-binary, each problem's own sum scaling); false if a table does not
+// fit the format. fx_batch_filter runs W = p_i(Ahat_i) Q_j for the active
+// problems (j read from jdev on the device: graph-capturable); the columns of
+// every problem's Q_j must have norm at most 1 (within 2^-20).
+bool fx_batch_prepare(FxBatch& F, int64_t N, int64_t nnz, const int* rowptr, const int* col, const double* val,
+                      const int* diag_pos, int32_t max_row_nnz, const int* d_off, int count, const double* cc,
+                      const double* ee, int r, cudaStream_t st);
+bool fx_batch_coefficients(FxBatch& F, const std::vector<std::vector<double>>& coeffs, cudaStream_t st);
+void fx_batch_filter(FxBatch& F, int r, const double* Q, const int* jdev, const int* d_off, const int* mdeg,
+                     const int* active, double* W, bool pdl, cudaStream_t st);
+// Reads and clears the batch filter's flag: FLZ_ERR_TIMEOUT (a stage wait
+// expired) or FLZ_ERR_INVALID_ARG (a value left the format's range) raised.
+void fx_batch_check_flag(FxBatch& F, cudaStream_t st);
 // ---- refine.cu ---------------------------------------------------------------------
 // Filtered subspace iteration in FP64-class arithmetic with Rayleigh-Ritz on A,
 // polishing the pairs of a reduced-precision solve (see refine.cu).
@@ -287,6 +329,15 @@ struct RefineArgs {
   std::vector<double> filter;       // the solve's filter coefficients (interior windows)
   std::vector<double> filter_half;  // the same filter at half the degree (first sweep)
   int wanted;                       // pairs the reduced-precision solve found in the window
+  // first sweep: the half-degree solve filter on the columns past `wanted`
+  // only (the start vectors pass unchanged), whatever the window
+  bool flat_first = false;
+  // give up when a sweep does not halve the worst residual, or when the
+  // products of A with a vector, extrapolated at the last sweep's rate to tol,
+  // would pass matvec_budget (0: no budget)
+  bool stop_on_stall = false;
+  int64_t matvec_budget = 0;
+  double range_scale = 1e-2;        // the damping polynomial's ratio across the window <= range_scale / residual
 };
 struct RefineResult {
   int sweeps = 0, kp = 0, filter_precision = 0;
@@ -294,6 +345,8 @@ struct RefineResult {
   std::vector<int> index;          // columns of X holding the wanted pairs
   std::vector<double> vals, res;   // their Rayleigh quotients and residuals / ||A||
   std::vector<int> degrees;        // filter degree of each sweep
+  int64_t matvecs = 0;             // products of A with a vector in the filters (columns x degree)
+  int outside = 0;                 // Ritz values of the final block outside [alpha, beta]
   double ms = 0.0;
 };
 // X: n x kp (kp a multiple of 16) as blocks of 16 columns, row-major; refined in place.
@@ -347,7 +400,12 @@ void random_normal(dev::dfloat* X, int64_t count, uint64_t seed, uint64_t offset
 void combine_columns(const double* X, int64_t n, int64_t ld, int cols, const double* G, int r, double scale,
                      double* Out, cudaStream_t st);
 // Column j of a row-major n x s block (stride ld) into column-major out (stride ldo).
-void rows_to_columns(const double* X, int64_t n, int s, int ld, double* out, int64_t ldo, cudaStream_t st);
+// out[t * ldo + i] = scale * X[i * ld + t] (row-major block to columns)
+void rows_to_columns(const double* X, int64_t n, int s, int ld, double* out, int64_t ldo, cudaStream_t st,
+                     double scale = 1.0);
+// The inverse: column j of the column-major X (leading dimension ldx) into column
+// j % 16 of the row-major 16-column block j / 16 of Out (blocks n * 16 apart).
+void columns_to_blocks(const double* X, int64_t n, int64_t ldx, int cols, double* Out, cudaStream_t st);
 // Gershgorin interval and max row length on the device.
 void gershgorin(const flz_matrix* A, double* glo, double* ghi, int32_t* max_row_nnz);
 // Structural/symmetry validation on the device; returns status (BAD_CSR, NOT_SYMMETRIC, OK).

@@ -115,6 +115,7 @@ RefineResult refine(flz_matrix* A, const RefineArgs& g, double* X, int kp, cudaS
   const bool lower = g.alpha <= g.lmin, upper = g.beta >= g.lmax;
   std::vector<double> mu, res;
   rayleigh(A, X, AY.p, n, kp, dev, part, mu, res, st);
+  double prev_worst = 1e300;
   for (int sweep = 0; sweep < g.max_sweeps; ++sweep) {
     // ---- the filter of this sweep ----
     // worst: the largest residual among the `wanted` best pairs in the window
@@ -130,14 +131,40 @@ RefineResult refine(flz_matrix* A, const RefineArgs& g, double* X, int kp, cudaS
     std::sort(inres.begin(), inres.end());
     const double worst =
         inres.empty() ? 1.0 : inres[std::min<size_t>(inres.size(), (size_t)std::max(g.wanted, 1)) - 1];
+    // A start block that converges too slowly (judged from the second sweep
+    // on) is given up: a sweep must halve the worst residual, and the
+    // products still needed must fit the budget. At an end of the spectrum
+    // the estimate is optimistic: the damping polynomial's asymptotic rate at
+    // the window's edge, acosh|a z_w + b| per degree, with the damping
+    // starting at the block's outermost Ritz value; for interior windows the
+    // last sweep's rate is extrapolated.
+    if (g.stop_on_stall && sweep >= 2) {
+      const double rho = worst / prev_worst;
+      if (!(rho <= 0.5)) break;
+      if (g.matvec_budget > 0 && worst > g.tol) {
+        double more_degrees;
+        if (lower != upper) {
+          const double edge = lower ? hi_blk : lo_blk;
+          const double zc = std::min(lower ? (edge - c) / e : -(edge - c) / e, 1.0 - 1e-12);
+          const double zw = lower ? (g.beta - c) / e : -(g.alpha - c) / e;
+          const double u = std::fabs((2.0 * zw - (1.0 + zc)) / (1.0 - zc));
+          more_degrees = u > 1.0 ? std::log(worst / g.tol) / std::acosh(u) : 1e300;
+        } else {
+          more_degrees = std::log(worst / g.tol) / std::log(1.0 / rho) * out.degrees.back();
+        }
+        if ((double)out.matvecs + more_degrees * kp > (double)g.matvec_budget) break;
+      }
+    }
+    prev_worst = worst;
     std::vector<double> coeffs;
     // A polynomial with a large ratio between its values at the window's two
     // ends amplifies the errors of the pairs at the far end (about `worst` in
     // size) relative to those pairs themselves: keep that ratio below
     // 0.01 / worst, and use the flat solve filter where that leaves less than
     // a factor 20 of damping beyond the block.
-    const double range_max = std::min(1e6, std::max(10.0, 1e-2 / std::max(worst, 1e-300)));
-    if ((lower && !upper && hi_blk > g.beta) || (upper && !lower && lo_blk < g.alpha)) {
+    const double range_max = std::min(1e6, std::max(10.0, g.range_scale / std::max(worst, 1e-300)));
+    const bool damp_ok = !(g.flat_first && sweep == 0);  // random extra columns: the window filter first
+    if (damp_ok && ((lower && !upper && hi_blk > g.beta) || (upper && !lower && lo_blk < g.alpha))) {
       const double edge = lower ? hi_blk : lo_blk;
       const double zc = std::min(lower ? (edge - c) / e : -(edge - c) / e, 1.0 - 1e-12);  // damping interval [zc, 1]
       const double zw = lower ? (g.beta - c) / e : -(g.alpha - c) / e;   // the wanted end nearest it
@@ -165,9 +192,18 @@ RefineResult refine(flz_matrix* A, const RefineArgs& g, double* X, int kp, cudaS
     if (coeffs.empty()) coeffs = (sweep == 0 && g.filter_half.size() > 1) ? g.filter_half : g.filter;
     out.degrees.push_back((int)coeffs.size() - 1);
     const int m = (int)coeffs.size() - 1;
+    out.matvecs += (int64_t)kp * m;
     // the filter runs on 4-column slices of the 16-column blocks (its fastest width)
+    const bool extras_only = g.flat_first && sweep == 0;
+    if (extras_only) out.matvecs -= (int64_t)(g.wanted / 4 * 4) * m;
     for (int b = 0; b < kp / 16; ++b)
       for (int q = 0; q < 4; ++q) {
+        if (extras_only && 16 * b + 4 * q + 4 <= g.wanted) {  // a slice of start vectors: Y = X
+          FLZ_CUDA(cudaMemcpy2DAsync(Y.p + (size_t)b * n * 16 + 4 * q, 16 * sizeof(double),
+                                     X + (size_t)b * n * 16 + 4 * q, 16 * sizeof(double), 4 * sizeof(double),
+                                     (size_t)n, cudaMemcpyDeviceToDevice, st));
+          continue;
+        }
         FLZ_CUDA(cudaMemcpy2DAsync(S4.p, 4 * sizeof(double), X + (size_t)b * n * 16 + 4 * q, 16 * sizeof(double),
                                    4 * sizeof(double), (size_t)n, cudaMemcpyDeviceToDevice, st));
         filter_apply(A, c, e, coeffs.data(), m, 4, S4.p, T4.p, FLZ_PREC_FX64, FLZ_REC_FORWARD, st);
@@ -281,6 +317,8 @@ RefineResult refine(flz_matrix* A, const RefineArgs& g, double* X, int kp, cudaS
       out.index.push_back(j);
       out.vals.push_back(mu[j]);
       out.res.push_back(res[j] / anorm);
+    } else {
+      ++out.outside;
     }
   out.ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
   return out;

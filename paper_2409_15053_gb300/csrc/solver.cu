@@ -312,6 +312,66 @@ void apply_filter(flz_matrix* A, double c, double e, const std::vector<double>& 
   filter_apply(A, c, e, coeffs.data(), m, r, X, Y, p.recurrence, st);
 }
 
+// The in-window pairs of a subspace sweep's block (rr over Xr, blocks of 16
+// rows-major columns) become the solver's eigenvectors, as unit columns.
+void store_refined(flz_solver* s, const RefineResult& rr, const double* Xr, cudaStream_t st) {
+  const int64_t n = s->A->n;
+  const int64_t found = (int64_t)rr.vals.size();
+  s->evecs.reserve((size_t)std::max<int64_t>(found, 1) * n);
+  for (int64_t i = 0; i < found; ++i) {
+    const int col = rr.index[i];
+    rows_to_columns(Xr + (size_t)(col / 16) * n * 16 + (col % 16), n, 1, 16, s->evecs.p + (size_t)i * n, n, st);
+  }
+  DevBuf<double> dv, prt;
+  dv.reserve(2);
+  prt.reserve(column_sums_scratch(n, 1) + 64);
+  for (int64_t i = 0; i < found; ++i) {
+    double* x = s->evecs.p + (size_t)i * n;
+    column_sums(x, x, nullptr, n, 1, 1, 0, dv.p, prt.p, st);
+    double xx = 0.0;
+    FLZ_CUDA(cudaMemcpyAsync(&xx, dv.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    FLZ_CUDA(cudaStreamSynchronize(st));
+    const double sc = 1.0 / std::sqrt(std::max(xx, 1e-300));
+    FLZ_CUDA(cudaMemcpyAsync(dv.p + 1, &sc, sizeof(double), cudaMemcpyHostToDevice, st));
+    basis_update(x, 1, n, 1, dv.p + 1, 1, 1.0, 0.0, x, 1, st);
+  }
+  FLZ_CUDA(cudaStreamSynchronize(st));
+}
+
+// Sorts the found pairs ascending (eigenvectors with them) into the solver's results.
+void finish_results(flz_solver* s, const std::vector<double>& found_vals, const std::vector<double>& found_res,
+                    cudaStream_t st) {
+  const int64_t n = s->A->n;
+  const int found = (int)found_vals.size();
+  std::vector<int> perm(found);
+  for (int i = 0; i < found; ++i) perm[i] = i;
+  std::sort(perm.begin(), perm.end(), [&](int a, int b) { return found_vals[a] < found_vals[b]; });
+  bool sorted = true;
+  for (int i = 0; i < found; ++i) sorted &= perm[i] == i;
+  if (!sorted && found > 0) {
+    DevBuf<double> tmp;
+    tmp.reserve((size_t)found * n);
+    for (int i = 0; i < found; ++i)
+      FLZ_CUDA(cudaMemcpyAsync(tmp.p + (size_t)i * n, s->evecs.p + (size_t)perm[i] * n, sizeof(double) * n,
+                               cudaMemcpyDeviceToDevice, st));
+    FLZ_CUDA(cudaStreamSynchronize(st));
+    std::swap(tmp.p, s->evecs.p);
+    std::swap(tmp.count, s->evecs.count);
+  }
+  s->evals.resize(found);
+  s->resid.resize(found);
+  double maxres = 0.0;
+  for (int i = 0; i < found; ++i) {
+    s->evals[i] = found_vals[perm[i]];
+    s->resid[i] = found_res[perm[i]];
+    maxres = std::max(maxres, s->resid[i]);
+  }
+  s->count = found;
+  s->solved = true;
+  s->stats.count = found;
+  s->stats.max_residual = maxres;
+}
+
 template <class BT>
 flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   const auto t_start = Clock::now();
@@ -380,6 +440,60 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
     filter_coeffs_for(p, am, bm, m, coeffs.data());
   }
   const double anorm = std::max(std::fabs(lmin), std::fabs(lmax));
+  const int guard = p.guard > 0 ? p.guard : std::max(r, 3);
+
+  // 3b. subspace start (params.start_mode SUBSPACE): filtered subspace
+  // iteration on [start vectors, guard and extra columns]; on success the
+  // solve ends here, without a Krylov basis.
+  if constexpr (std::is_same<BT, double>::value)
+    if (s->start_cols > 0 && p.start_mode == FLZ_START_SUBSPACE && !whole) {
+      int kp = s->start_cols + guard + std::max(16, s->start_cols / 3);
+      kp = (kp + 15) / 16 * 16;
+      if ((int64_t)kp * 4 <= n) {
+        DevBuf<double> Xr;
+        Xr.reserve((size_t)n * kp);
+        random_normal(Xr.p, n * kp, p.seed ^ 0x5eed5ull, 0, st);
+        columns_to_blocks(s->start.p, n, n, s->start_cols, Xr.p, st);
+        std::vector<double> half;
+        if (m >= 8) {
+          half.resize(m / 2 + 1);
+          filter_coeffs_for(p, am, bm, m / 2, half.data());
+        }
+        RefineArgs ra{s->alpha, s->beta, lmin, lmax, p.tol, 12, std::max(m, 64), coeffs, half, s->start_cols};
+        ra.flat_first = true;
+        ra.stop_on_stall = true;
+        // After Rayleigh-Ritz a Ritz vector's error lies outside the block's
+        // span, so a steep damping polynomial (up to the 1e6 cap across the
+        // window) cannot let the favoured pairs swamp the others.
+        ra.range_scale = 1e30;
+        // about what filtered Lanczos would take: three block vectors per
+        // wanted or guard pair, each at the solve's degree
+        ra.matvec_budget = 3 * (int64_t)(s->start_cols + guard) * m;
+        RefineResult rr;
+        bool ok = false;
+        try {
+          rr = refine(A, ra, Xr.p, kp, st);
+          ok = rr.converged && rr.outside >= guard;
+        } catch (const Failure& f) {
+          if (f.status != FLZ_ERR_NOT_CONVERGED) throw;  // a lost rank falls back; device errors do not
+          clear_last_error();
+        }
+        stats.refine_sweeps = rr.sweeps;
+        stats.refine_degree = rr.degrees.empty() ? 0 : *std::max_element(rr.degrees.begin(), rr.degrees.end());
+        stats.ms_refine = rr.ms;
+        stats.sweep_matvecs = rr.matvecs;
+        if (ok) {
+          store_refined(s, rr, Xr.p, st);
+          finish_results(s, rr.vals, rr.res, st);
+          stats.start_used = 2;
+          stats.converged = 1;
+          stats.ms_total = ms_since(t_start);
+          stats.kernel_launches = g_kernel_launches - launches0;
+          stats.filter_precision = A->last_filter_precision;
+          return FLZ_OK;
+        }
+      }
+    }
 
   // 4. basis capacity
   int64_t kcap = p.max_basis > 0 ? p.max_basis : 2000;
@@ -431,12 +545,12 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
     if (s->start_cols > 0) {
       warm_start(E, s->start.p, s->start_cols, p.seed);
       warm = true;
+      stats.start_used = 1;
     }
   if (!warm) orthonormal_start(E, p.seed);
 
   Projected P;
   P.r = r;
-  const int guard = p.guard > 0 ? p.guard : std::max(r, 3);
   auto filt = [&](const BT* X, BT* Y) { apply_filter(A, c, e, coeffs, m, r, p, X, Y, st); };
   double ms_check = 0.0;
   int64_t prev_count = -1;
@@ -563,11 +677,7 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
             std::swap(grown.p, s->evecs.p);
             std::swap(grown.count, s->evecs.count);
           }
-          rows_to_columns(s->X.p + t, n, 1, 16, s->evecs.p + (size_t)found * n, n, st);
-          std::vector<double> sc(1, 1.0 / std::sqrt(xx));
-          FLZ_CUDA(cudaMemcpyAsync(dev + 64, sc.data(), sizeof(double), cudaMemcpyHostToDevice, st));
-          basis_update(s->evecs.p + (size_t)found * n, 1, n, 1, dev + 64, 1, 1.0, 0.0,
-                       s->evecs.p + (size_t)found * n, 1, st);
+          rows_to_columns(s->X.p + t, n, 1, 16, s->evecs.p + (size_t)found * n, n, st, 1.0 / std::sqrt(xx));
           found_vals.push_back(lam);
           found_res.push_back(res);
           ++found;
@@ -645,60 +755,15 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
         found = (int64_t)rr.vals.size();
         found_vals = rr.vals;
         found_res = rr.res;
-        s->evecs.reserve((size_t)std::max<int64_t>(found, 1) * n);
-        for (int64_t i = 0; i < found; ++i) {
-          const int col = rr.index[i];
-          rows_to_columns(Xr.p + (size_t)(col / 16) * n * 16 + (col % 16), n, 1, 16, s->evecs.p + (size_t)i * n, n, st);
-        }
-        // unit columns
-        DevBuf<double> dv, prt;
-        dv.reserve(2);
-        prt.reserve(column_sums_scratch(n, 1) + 64);
-        for (int64_t i = 0; i < found; ++i) {
-          double* x = s->evecs.p + (size_t)i * n;
-          column_sums(x, x, nullptr, n, 1, 1, 0, dv.p, prt.p, st);
-          double xx = 0.0;
-          FLZ_CUDA(cudaMemcpyAsync(&xx, dv.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-          FLZ_CUDA(cudaStreamSynchronize(st));
-          const double sc = 1.0 / std::sqrt(std::max(xx, 1e-300));
-          FLZ_CUDA(cudaMemcpyAsync(dv.p + 1, &sc, sizeof(double), cudaMemcpyHostToDevice, st));
-          basis_update(x, 1, n, 1, dv.p + 1, 1, 1.0, 0.0, x, 1, st);
-        }
-        FLZ_CUDA(cudaStreamSynchronize(st));
+        stats.sweep_matvecs = rr.matvecs;
+        store_refined(s, rr, Xr.p, st);
       }
     }
 
-  // sort ascending
-  std::vector<int> perm(found);
-  for (int i = 0; i < found; ++i) perm[i] = i;
-  std::sort(perm.begin(), perm.end(), [&](int a, int b) { return found_vals[a] < found_vals[b]; });
-  bool sorted = true;
-  for (int i = 0; i < found; ++i) sorted &= perm[i] == i;
-  if (!sorted && found > 0) {
-    DevBuf<double> tmp;
-    tmp.reserve((size_t)found * n);
-    for (int i = 0; i < found; ++i)
-      FLZ_CUDA(cudaMemcpyAsync(tmp.p + (size_t)i * n, s->evecs.p + (size_t)perm[i] * n, sizeof(double) * n,
-                               cudaMemcpyDeviceToDevice, st));
-    FLZ_CUDA(cudaStreamSynchronize(st));
-    std::swap(tmp.p, s->evecs.p);
-    std::swap(tmp.count, s->evecs.count);
-  }
-  s->evals.resize(found);
-  s->resid.resize(found);
-  double maxres = 0.0;
-  for (int i = 0; i < found; ++i) {
-    s->evals[i] = found_vals[perm[i]];
-    s->resid[i] = found_res[perm[i]];
-    maxres = std::max(maxres, s->resid[i]);
-  }
-  s->count = found;
-  s->solved = true;
+  finish_results(s, found_vals, found_res, st);
   stats.iters = k;
   stats.matvecs = (int64_t)r * m * k;
-  stats.count = found;
   stats.converged = converged ? 1 : 0;
-  stats.max_residual = maxres;
   stats.ms_filter = E.ms_op;
   stats.ms_orth = E.ms_orth;
   stats.ms_check = ms_check;

@@ -83,6 +83,44 @@ def test_batch_fp64_matches_dense(r):
     check(csrs, intervals, out, 1e-10)
 
 
+@pytest.mark.parametrize("r", [4, 8, 16])
+def test_batch_fixed_point_filter_matches_dense(r):
+    # the 64-bit fixed-point filter over the concatenation: per-problem maps,
+    # coefficient tables and sum scalings in one kernel per degree
+    csrs, intervals = small_batch(3, 6)
+    st, out = run_batch(csrs, intervals, block_size=r, degree=40, check_every=5, precision=flz.FLZ_PREC_FX64)
+    assert st == flz.FLZ_OK
+    assert all(o["stats"]["filter_precision"] == flz.FLZ_PREC_FX64 for o in out)
+    check(csrs, intervals, out, 1e-10)
+
+
+def test_batch_fixed_point_filter_with_per_problem_degrees():
+    # automatic degrees differ between problems: each problem's rows stop at
+    # its own last degree (the running sum becomes W there) while the others go on
+    csrs, intervals = small_batch(5, 4)
+    st, out = run_batch(csrs, intervals, block_size=4, degree=0, check_every=5, precision=flz.FLZ_PREC_FX64)
+    assert st == flz.FLZ_OK
+    assert len({o["stats"]["degree"] for o in out}) > 1
+    assert all(o["stats"]["filter_precision"] == flz.FLZ_PREC_FX64 for o in out)
+    check(csrs, intervals, out, 1e-10)
+
+
+def test_batch_fixed_point_request_falls_back_to_fp64_for_irregular_rows():
+    # power-law graphs: the SELL-32 padding exceeds 30 %, the fixed-point
+    # layout is not built and the batch filters in FP64
+    from synth import powerlaw_graph_laplacian
+    csrs, intervals = [], []
+    for seed in (7, 8):
+        c = powerlaw_graph_laplacian(1500, seed=seed)
+        w = np.linalg.eigvalsh(c.to_dense())
+        csrs.append(c)
+        intervals.append(gap_interval(w, 30, 12))
+    st, out = run_batch(csrs, intervals, block_size=4, degree=60, check_every=5, precision=flz.FLZ_PREC_FX64)
+    assert st == flz.FLZ_OK
+    assert all(o["stats"]["filter_precision"] == flz.FLZ_PREC_FP64 for o in out)
+    check(csrs, intervals, out, 1e-10)
+
+
 def test_batch_double_fp32_filter_matches_dense():
     # the double-FP32 filter (FP32 pipes, FP64-class accuracy) with the batch's FP64 basis
     csrs, intervals = small_batch(11, 5)
@@ -121,8 +159,8 @@ def test_batch_rejects_bad_arguments():
     flz.flz_matrix_destroy(h)
 
 
-@pytest.mark.parametrize("precision,tol", [(flz.FLZ_PREC_FP32, 1e-6), (flz.FLZ_PREC_FP64, 1e-10)],
-                         ids=["fp32", "fp64"])
+@pytest.mark.parametrize("precision,tol", [(flz.FLZ_PREC_FP32, 1e-6), (flz.FLZ_PREC_FP64, 1e-10),
+                                           (flz.FLZ_PREC_FX64, 1e-10)], ids=["fp32", "fp64", "fx64"])
 def test_full_size_batch64_matches_oracle_reference(precision, tol):
     # 64 problems, n log-uniform in [1e4, 2e5] (sum ~4.7e6), autotuned r,
     # degree 60: the batched launch shape the benchmark times, against the

@@ -526,6 +526,94 @@ def test_warm_started_sequence_of_perturbed_potentials():
     assert steps_warm < steps_cold, (steps_warm, steps_cold)
 
 
+def test_subspace_started_sequence_of_perturbed_potentials():
+    # The same kind of sequence at 20^3 with params.start_mode SUBSPACE: each
+    # solve after the first is filtered subspace iteration on the previous
+    # eigenvectors. Counts and eigenvalues against dense eigensolves,
+    # residuals recomputed here, orthonormal eigenvectors; no block Lanczos
+    # steps, and fewer products of A with a vector than the random start.
+    g = 20
+    rng = np.random.Generator(np.random.PCG64(2025))
+    v0 = 0.5 * rng.random(g ** 3)
+    dv = rng.random(g ** 3) - 0.5
+    prev = None
+    for t in range(4):
+        csr = laplacian_3d_7pt(g, g, g, v0 + 0.02 * t * dv)
+        w = np.linalg.eigvalsh(csr.to_dense())
+        win = np.arange(55, 70)
+        k = int(win[np.argmax(w[win + 1] - w[win])])
+        beta = 0.5 * (w[k] + w[k + 1])
+        want = w[w <= beta]
+        h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+        try:
+            outs = {}
+            for mode in ("cold", "subspace"):
+                if mode == "subspace" and prev is None:
+                    continue
+                p = flz.flz_params_default()
+                p.block_size = 4
+                p.degree = 60
+                p.check_every = 5
+                p.precision = flz.FLZ_PREC_FX64
+                p.start_mode = flz.FLZ_START_SUBSPACE
+                s = flz.flz_solver_create(h, p)
+                try:
+                    flz.flz_solver_set_interval(s, 0.0, beta)
+                    if mode == "subspace":
+                        flz.flz_solver_set_start_vectors(s, prev)
+                    assert flz.flz_solve(s) == flz.FLZ_OK
+                    outs[mode] = (flz.flz_get_eigenvalues(s), flz.flz_get_stats(s), flz.get_eigenvectors_host(s, csr.n))
+                finally:
+                    flz.flz_solver_destroy(s)
+        finally:
+            flz.flz_matrix_destroy(h)
+        for mode, (vals, st, X) in outs.items():
+            assert vals.shape == want.shape, (mode, vals.shape, want.shape)
+            assert np.max(np.abs(vals - want)) < 1e-10 * 12.5
+            R = csr.to_scipy() @ X - X * vals
+            assert np.max(np.linalg.norm(R, axis=0)) / max(abs(st["lmin"]), abs(st["lmax"])) <= 1e-10
+            assert np.max(np.abs(X.T @ X - np.eye(X.shape[1]))) < 1e-10
+        if t > 0:
+            cold, sub = outs["cold"][1], outs["subspace"][1]
+            assert sub["start_used"] == 2 and sub["iters"] == 0 and sub["refine_sweeps"] >= 1, \
+                (t, sub["start_used"], sub["refine_sweeps"], sub["sweep_matvecs"], cold["matvecs"])
+            assert sub["sweep_matvecs"] < cold["matvecs"], (sub["sweep_matvecs"], cold["matvecs"])
+        prev = outs["subspace" if t > 0 else "cold"][2]
+
+
+def test_subspace_start_falls_back_to_lanczos_when_the_block_is_too_small():
+    # five start vectors for a window of about 40 eigenvalues: the subspace
+    # block (32 columns) cannot hold the window and its guard pairs, so the
+    # solve continues as filtered Lanczos from those vectors and stays correct
+    g = 16
+    rng = np.random.Generator(np.random.PCG64(8))
+    csr = laplacian_3d_7pt(g, g, g, 0.5 * rng.random(g ** 3))
+    w = np.linalg.eigvalsh(csr.to_dense())
+    beta = 0.5 * (w[39] + w[40])
+    h = flz.flz_matrix_create_csr(csr.n, csr.nnz, csr.rowptr, csr.col, csr.val)
+    try:
+        p = flz.flz_params_default()
+        p.block_size = 4
+        p.degree = 60
+        p.check_every = 5
+        p.precision = flz.FLZ_PREC_FX64
+        p.start_mode = flz.FLZ_START_SUBSPACE
+        s = flz.flz_solver_create(h, p)
+        try:
+            flz.flz_solver_set_interval(s, 0.0, beta)
+            _, V = np.linalg.eigh(csr.to_dense())
+            flz.flz_solver_set_start_vectors(s, np.asfortranarray(V[:, :5]))
+            assert flz.flz_solve(s) == flz.FLZ_OK
+            st = flz.flz_get_stats(s)
+            assert st["start_used"] == 1 and st["iters"] > 0
+            vals = flz.flz_get_eigenvalues(s)
+            assert vals.shape == (40,) and np.max(np.abs(vals - w[:40])) < 1e-10 * 12.5
+        finally:
+            flz.flz_solver_destroy(s)
+    finally:
+        flz.flz_matrix_destroy(h)
+
+
 def test_start_vectors_are_validated_and_cleared():
     A = laplacian_3d_7pt(8, 8, 8)
     h = flz.flz_matrix_create_csr(A.n, A.nnz, A.rowptr, A.col, A.val)
