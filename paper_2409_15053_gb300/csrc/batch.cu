@@ -706,6 +706,71 @@ struct BatchEngine {
 
   DevBuf<double> v64;
 
+  // Tensor-core reorthogonalization: each problem keeps its own digit copy of
+  // its basis (grown as the basis grows) and the projections and updates run
+  // per problem, host-driven between the two captured halves of a step.
+  // The problems' kernels are small; they run on kSide side streams (problem
+  // i on stream i % kSide), forked from and joined back into the main stream.
+  static constexpr int kSide = 8;
+  bool tc = false;
+  std::vector<std::unique_ptr<TcBasis>> tcb;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
+
+  void setup_tc(int64_t kcap0) {
+    tcb.clear();
+    for (int i = 0; i < count; ++i) {
+      tcb.emplace_back(new TcBasis());
+      tcb[i]->reserve(B->off[i + 1] - B->off[i], std::min<int64_t>(kcap0, (int64_t)nbmax * r));
+    }
+    FLZ_CUDA(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+    for (int q = 0; q < kSide; ++q) {
+      FLZ_CUDA(cudaStreamCreateWithFlags(&side[q], cudaStreamNonBlocking));
+      FLZ_CUDA(cudaEventCreateWithFlags(&join_ev[q], cudaEventDisableTiming));
+    }
+    tc = true;
+  }
+  ~BatchEngine() {
+    for (int q = 0; q < kSide; ++q) {
+      if (side[q]) cudaStreamSynchronize(side[q]), cudaStreamDestroy(side[q]);
+      if (join_ev[q]) cudaEventDestroy(join_ev[q]);
+    }
+    if (fork_ev) cudaEventDestroy(fork_ev);
+  }
+  // runs f(i, stream) for the active problems on the side streams, ordered
+  // after everything on the main stream and before anything issued to it later
+  template <class F>
+  void on_side_streams(const std::vector<int>& act, F f) {
+    FLZ_CUDA(cudaEventRecord(fork_ev, st));
+    for (int q = 0; q < kSide; ++q) FLZ_CUDA(cudaStreamWaitEvent(side[q], fork_ev, 0));
+    for (int i = 0; i < count; ++i)
+      if (act[i]) f(i, side[i % kSide]);
+    for (int q = 0; q < kSide; ++q) {
+      FLZ_CUDA(cudaEventRecord(join_ev[q], side[q]));
+      FLZ_CUDA(cudaStreamWaitEvent(st, join_ev[q], 0));
+    }
+  }
+  // CGS2 of every active problem's W against its K basis columns, writing the
+  // two projections where the history kernels read them.
+  void tc_orth(int K, const std::vector<int>& act) {
+    const size_t cs = (size_t)nbmax * r * r;
+    on_side_streams(act, [&](int i, cudaStream_t s) {
+      tcb[i]->cgs2(K, W.p + (size_t)B->off[i] * r, r, C1.p + i * cs, C2.p + i * cs, s);
+    });
+  }
+  // Digits of the newest block (index col0 / r, just stored) of every active problem.
+  void tc_append(int col0, const std::vector<int>& act) {
+    const double* blk = Q.p + (size_t)(col0 / r) * N * r;
+    on_side_streams(act, [&](int i, cudaStream_t s) {
+      tcb[i]->grow(col0 + r, s);
+      tcb[i]->append(const_cast<double*>(blk) + (size_t)B->off[i] * r, r, col0, s);
+    });
+  }
+  // raises FLZ_ERR_TIMEOUT if a tensor-core wait expired (after a stream sync)
+  void tc_check() {
+    for (auto& t : tcb) t->check_status();
+  }
+
   // One block Lanczos step for every active problem (graph-capturable).
   template <int R>
   void step() {
@@ -715,6 +780,13 @@ struct BatchEngine {
     update<R>(Q.p, 0, R, C1.p, (long long)nbmax * R * R, -1.0, 1.0, W.p, R, active.p);
     dot<R>(Q.p, 0, W.p, C2.p);
     update<R>(Q.p, 0, R, C2.p, (long long)nbmax * R * R, -1.0, 1.0, W.p, R, active.p);
+    step_tail<R>();
+  }
+
+  // The part of a step after the reorthogonalization: projection history,
+  // block QR, S history, the new basis block, the step index.
+  template <int R>
+  void step_tail() {
     d_history_kernel<<<gsb((long long)count * R * R), 256, 0, st>>>(count, R, nbmax, jdev.p, active.p, C1.p, C2.p, Dh.p);
     FLZ_LAUNCH_CHECK();
     qr<R>();
@@ -835,13 +907,13 @@ void run_lockstep(BatchEngine& E, int steps) {
 // Captures one block step of E into an executable graph. Nothing in a step
 // allocates or synchronizes; if anything fails the capture is ended before
 // the error propagates, so the stream is usable again.
-template <int R>
-cudaGraphExec_t capture_step_once(BatchEngine& E) {
+template <class F>
+cudaGraphExec_t capture_once(BatchEngine& E, F part) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ge = nullptr;
   FLZ_CUDA(cudaStreamBeginCapture(E.st, cudaStreamCaptureModeThreadLocal));
   try {
-    E.step<R>();
+    part();
   } catch (...) {
     cudaGraph_t partial = nullptr;
     cudaStreamEndCapture(E.st, &partial);
@@ -856,17 +928,17 @@ cudaGraphExec_t capture_step_once(BatchEngine& E) {
   return ge;
 }
 
-// Captures one block step; if the programmatic dependent launches cannot be
-// captured, captures again with plain launches.
-template <int R>
-cudaGraphExec_t capture_step(BatchEngine& E) {
+// Captures part of a block step; if the programmatic dependent launches
+// cannot be captured, captures again with plain launches.
+template <class F>
+cudaGraphExec_t capture_part(BatchEngine& E, F part) {
   try {
-    return capture_step_once<R>(E);
+    return capture_once(E, part);
   } catch (const Failure&) {
     if (!E.pdl) throw;
     cudaGetLastError();
     E.pdl = false;
-    return capture_step_once<R>(E);
+    return capture_once(E, part);
   }
 }
 
@@ -969,13 +1041,27 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
   FLZ_CUDA(cudaMemGetInfo(&free_b, &total_b));
   kcap = std::min<int64_t>(kcap, (int64_t)(0.5 * (double)free_b / (8.0 * (double)B->N)));
   kcap = std::min<int64_t>(kcap, nmax_rows);
+  // Tensor-core reorthogonalization unless the CUDA cores are asked for: the
+  // digit copies (16 bytes per value, grown with the basis) and the FP64
+  // basis share 60 % of the free memory; AUTO keeps the CUDA cores where
+  // that would shrink the basis below 200 vectors per problem.
+  const int64_t kcap_tc = (int64_t)(0.6 * (double)free_b / (24.0 * (double)B->N));
+  const bool use_tc = p.ortho == FLZ_ORTHO_TENSOR || (p.ortho == FLZ_ORTHO_AUTO && std::min(kcap, kcap_tc) >= 200);
+  if (use_tc) kcap = std::max<int64_t>(2 * R, std::min(kcap, kcap_tc));
   const int nbmax = (int)std::max<int64_t>(2, kcap / R);
   BatchEngine E;
   E.setup(B, R, nbmax, p.precision, st);
   E.set_active(act);
   E.set_filter(cvec, evec, coeffs);
-  for (int i = 0; i < count; ++i) B->stats[i].filter_precision = E.precision;
+  for (int i = 0; i < count; ++i) {
+    B->stats[i].filter_precision = E.precision;
+    B->stats[i].ortho = use_tc ? FLZ_ORTHO_TENSOR : FLZ_ORTHO_CUDA_CORES;
+  }
   E.start_block<R>(p.seed);
+  if (use_tc) {
+    E.setup_tc(16 * R);
+    E.tc_append(0, act);
+  }
 
   const int guard = p.guard > 0 ? p.guard : std::max(R, 3);
   std::vector<int64_t> prev_count(count, -1);
@@ -994,22 +1080,38 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
 
   int k = 0;
   double ms_steps = 0.0, ms_check = 0.0;
-  // graph of one step, replayed between checks
+  // graph of one step (CUDA-core reorthogonalization), or of its two halves
+  // around the per-problem tensor-core CGS2, replayed between checks
   const int64_t before_capture = g_kernel_launches;
-  cudaGraphExec_t gexec = capture_step<R>(E);
   struct GraphGuard {
-    cudaGraphExec_t g;
-    ~GraphGuard() { cudaGraphExecDestroy(g); }
-  } guard_graph{gexec};
+    cudaGraphExec_t g = nullptr;
+    ~GraphGuard() {
+      if (g) cudaGraphExecDestroy(g);
+    }
+  } graph_a, graph_b;
+  if (use_tc) {
+    graph_a.g = capture_part(E, [&] { E.apply_filter<R>(); });
+    graph_b.g = capture_part(E, [&] { E.step_tail<R>(); });
+  } else {
+    graph_a.g = capture_part(E, [&] { E.step<R>(); });
+  }
   const int64_t launches_per_step = g_kernel_launches - before_capture;
   g_kernel_launches = before_capture;  // captured, not launched
   while (k < nbmax) {
     const auto ts = std::chrono::steady_clock::now();
     const int todo = std::min(p.check_every - (k % p.check_every), nbmax - k);
-    for (int s = 0; s < todo; ++s) FLZ_CUDA(cudaGraphLaunch(gexec, st));
+    for (int s = 0; s < todo; ++s) {
+      FLZ_CUDA(cudaGraphLaunch(graph_a.g, st));
+      if (use_tc) {
+        E.tc_orth((k + s + 1) * R, act);  // the basis holds Q_0 .. Q_j, j = k + s
+        FLZ_CUDA(cudaGraphLaunch(graph_b.g, st));
+        E.tc_append((k + s + 1) * R, act);
+      }
+    }
     g_kernel_launches += (int64_t)todo * launches_per_step;
     k += todo;
     FLZ_CUDA(cudaStreamSynchronize(st));
+    if (use_tc) E.tc_check();
     ms_steps += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts).count();
     const bool last = k >= nbmax;
     const auto tc = std::chrono::steady_clock::now();
@@ -1083,7 +1185,13 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
       Ytab.reserve(tab.size());
       FLZ_CUDA(cudaMemcpyAsync(Ytab.p, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st));
       FLZ_CUDA(cudaMemcpyAsync(walking.p, walk_flag.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st));
-      E.update<16>(E.Q.p, k, R, Ytab.p, (long long)K * 16, 1.0, 0.0, X.p, 16, walking.p);
+      if (use_tc) {
+        E.on_side_streams(walk_flag, [&](int i, cudaStream_t s) {
+          E.tcb[i]->multiply(K, Ytab.p + (size_t)i * K * 16, 16, 16, X.p + (size_t)B->off[i] * 16, 16, s);
+        });
+      } else {
+        E.update<16>(E.Q.p, k, R, Ytab.p, (long long)K * 16, 1.0, 0.0, X.p, 16, walking.p);
+      }
       seg_spmm_kernel<<<(unsigned)(((B->N + 1) / 2 * 32 + 255) / 256), 256, 0, st>>>(B->N, 16, 16, B->rowptr.p, B->col.p,
                                                                               B->val.p, X.p, AX.p);
       FLZ_LAUNCH_CHECK();

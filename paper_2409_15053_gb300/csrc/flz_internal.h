@@ -134,6 +134,8 @@ struct TcBasis {
   static size_t bytes_for(int64_t n, int64_t kcap);   // digit storage for kcap columns
   void release();
   void reserve(int64_t n, int64_t kcap);
+  // room for kcap columns, keeping the digits written so far (at least doubles the capacity)
+  void grow(int64_t kcap, cudaStream_t st);
   // rounds X (n x r, row-major) to the 2^-62 grid in place; its digits become columns col0..col0+r-1
   void append(double* X, int r, int col0, cudaStream_t st);
   // out[j] = largest |W[i, j]| (as the upper word of the FP64 bits), j < r

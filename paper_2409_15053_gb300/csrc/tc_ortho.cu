@@ -832,6 +832,26 @@ void TcBasis::reserve(int64_t n_, int64_t kcap) {
   *status_host = 0;
 }
 
+void TcBasis::grow(int64_t kcap, cudaStream_t st) {
+  const int groups = (int)((kcap + 15) / 16);
+  if (groups <= groups_cap) return;
+  const int ng = std::max(groups, 2 * groups_cap);
+  // groups are contiguous, group-major: the written ones are a prefix
+  const size_t old_bytes = (size_t)groups_cap * 16 * (size_t)n_pad * 16;
+  const size_t bytes = (size_t)ng * 16 * (size_t)n_pad * 16;
+  DevBuf<uint8_t> nq;
+  nq.reserve(bytes);
+  FLZ_CUDA(cudaMemcpyAsync(nq.p, q.p, old_bytes, cudaMemcpyDeviceToDevice, st));
+  FLZ_CUDA(cudaMemsetAsync(nq.p + old_bytes, 0, bytes - old_bytes, st));
+  FLZ_CUDA(cudaStreamSynchronize(st));  // the old copy is freed on return
+  std::swap(q.p, nq.p);
+  std::swap(q.count, nq.count);
+  hs.reserve((size_t)ng * 64 * 16 + 64);
+  acc.reserve((size_t)ng * 128 * 128);  // zero between projections
+  FLZ_CUDA(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long) * acc.count, st));
+  groups_cap = ng;
+}
+
 void TcBasis::append(double* X, int r, int col0, cudaStream_t st) {
   if (col0 + r > groups_cap * 16) fail(FLZ_ERR_CAPACITY, "digit basis holds %d columns", groups_cap * 16);
   const int64_t work = n_oct * r;

@@ -75,11 +75,25 @@ def small_batch(seed, count):
     return csrs, intervals
 
 
+@pytest.mark.parametrize("ortho", [flz.FLZ_ORTHO_TENSOR, flz.FLZ_ORTHO_CUDA_CORES], ids=["tensor", "cuda-cores"])
 @pytest.mark.parametrize("r", [4, 8])
-def test_batch_fp64_matches_dense(r):
+def test_batch_fp64_matches_dense(r, ortho):
+    # reorthogonalization per problem on the tensor cores (exact digit
+    # products), or segmented over the concatenation on the CUDA cores
     csrs, intervals = small_batch(3, 6)
-    st, out = run_batch(csrs, intervals, block_size=r, degree=40, check_every=5)
+    st, out = run_batch(csrs, intervals, block_size=r, degree=40, check_every=5, ortho=ortho)
     assert st == flz.FLZ_OK
+    assert all(o["stats"]["ortho"] == ortho for o in out)
+    check(csrs, intervals, out, 1e-10)
+
+
+def test_batch_tensor_core_basis_grows_past_its_first_capacity():
+    # r = 16 and degree 8: the digit copies start at 256 columns and must
+    # grow (keeping their digits) before these problems converge
+    csrs, intervals = small_batch(13, 3)
+    st, out = run_batch(csrs, intervals, block_size=16, degree=8, check_every=5, ortho=flz.FLZ_ORTHO_TENSOR)
+    assert st == flz.FLZ_OK
+    assert max(o["stats"]["basis_vectors"] for o in out) > 256
     check(csrs, intervals, out, 1e-10)
 
 
