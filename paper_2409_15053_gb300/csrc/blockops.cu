@@ -617,6 +617,181 @@ void rows_to_columns(const double* X, int64_t n, int s, int ld, double* out, int
   FLZ_LAUNCH_CHECK();
 }
 
+// ---- device CholeskyQR (single solver) ----------------------------------------
+// Passes X -> X R_1^{-1} -> ... of an n x R block, every small step on the
+// device. A pass: the Gram matrix's upper triangle as per-CTA partial sums
+// (R(R+1)/2 products per row, not R^2), its factorization, and the
+// triangular update (R(R+1)/2 products per row). The third pass runs only if
+// the first needed the shift (shifted CholeskyQR3; otherwise CholeskyQR2):
+// its kernels read the skip word the first factorization wrote.
+constexpr int kQrParts = 152 * 2;
+
+template <int R>
+__global__ void __launch_bounds__(kThreads) qr_gram_kernel(const double* __restrict__ X, long long n,
+                                                           double* __restrict__ part, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  constexpr int NT = R * (R + 1) / 2;
+  double g[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) g[t] = 0.0;
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+    double x[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) x[a] = X[i * R + a];
+    int t = 0;
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = a; b < R; ++b) {
+        g[t] = fma(x[a], x[b], g[t]);
+        ++t;
+      }
+  }
+  __shared__ double red[kThreads / 32][NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    double v = g[t];
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][t] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NT; t += kThreads) {
+    double v = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) v += red[w][t];
+    part[(size_t)blockIdx.x * NT + t] = v;
+  }
+}
+
+// Sums the partial Gram triangles (fixed order), then on one thread: R with
+// R^T R = G; on pass 0 a failed factorization is retried with G + shift I,
+// shift = 11 (n r + r (r + 1)) u max_i G_ii r, and skip[0] records whether the
+// third pass can be skipped; a factorization that still fails keeps
+// R = diag(sqrt(G_ii)). Rinv = R^{-1}, S = R S (S = R on pass 0).
+__global__ void qr_factor_kernel(const double* __restrict__ part, int nparts, int r, double nrows, int pass,
+                                 double* __restrict__ Rinv, double* __restrict__ S, int* __restrict__ skip) {
+  if (pass == 2 && *skip) return;
+  const int NT = r * (r + 1) / 2;
+  __shared__ double gs[16 * 17 / 2];
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+    double v = 0.0;
+    for (int q = 0; q < nparts; ++q) v += part[(size_t)q * NT + t];
+    gs[t] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double G[16 * 16], R[16 * 16], Ri[16 * 16];
+  for (int a = 0, t = 0; a < r; ++a)
+    for (int b = a; b < r; ++b, ++t) G[a * r + b] = G[b * r + a] = gs[t];
+  auto factor = [&](double shift) {
+    for (int a = 0; a < r * r; ++a) R[a] = 0.0;
+    for (int a = 0; a < r; ++a) {
+      double d = G[a * r + a] + shift;
+      for (int q = 0; q < a; ++q) d -= R[q * r + a] * R[q * r + a];
+      if (!(d > 0.0)) return false;
+      const double rd = sqrt(d);
+      R[a * r + a] = rd;
+      for (int b = a + 1; b < r; ++b) {
+        double v = G[a * r + b];
+        for (int q = 0; q < a; ++q) v -= R[q * r + a] * R[q * r + b];
+        R[a * r + b] = v / rd;
+      }
+    }
+    return true;
+  };
+  bool ok = factor(0.0);
+  if (pass == 0) *skip = ok ? 1 : 0;
+  if (!ok && pass == 0) {
+    double gmax = 0.0;
+    for (int d = 0; d < r; ++d) gmax = fmax(gmax, G[d * r + d]);
+    ok = factor(11.0 * (nrows * r + (double)r * (r + 1)) * 1.1102230246251565e-16 * fmax(gmax * r, 1e-300));
+  }
+  if (!ok) {
+    for (int a = 0; a < r * r; ++a) R[a] = 0.0;
+    for (int a = 0; a < r; ++a) R[a * r + a] = sqrt(fmax(G[a * r + a], 1e-300));
+  }
+  for (int a = 0; a < r * r; ++a) Ri[a] = 0.0;
+  for (int b = 0; b < r; ++b) {
+    Ri[b * r + b] = 1.0 / R[b * r + b];
+    for (int a = b - 1; a >= 0; --a) {
+      double v = 0.0;
+      for (int q = a + 1; q <= b; ++q) v += R[a * r + q] * Ri[q * r + b];
+      Ri[a * r + b] = -v / R[a * r + a];
+    }
+  }
+  for (int a = 0; a < r * r; ++a) Rinv[a] = Ri[a];
+  if (pass == 0) {
+    for (int a = 0; a < r * r; ++a) S[a] = R[a];
+  } else {
+    double T[16 * 16];
+    for (int a = 0; a < r; ++a)
+      for (int b = 0; b < r; ++b) {
+        double v = 0.0;
+        for (int q = 0; q < r; ++q) v += R[a * r + q] * S[q * r + b];
+        T[a * r + b] = v;
+      }
+    for (int a = 0; a < r * r; ++a) S[a] = T[a];
+  }
+}
+
+// Out = X Rinv with Rinv upper triangular (in place allowed: a row is read whole first)
+template <int R>
+__global__ void __launch_bounds__(kThreads) qr_update_kernel(const double* X, const double* __restrict__ Rinv,
+                                                             double* Out, long long n, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double ri[R * R];
+  for (int t = threadIdx.x; t < R * R; t += kThreads) ri[t] = Rinv[t];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+    double x[R], y[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) x[a] = X[i * R + a];
+#pragma unroll
+    for (int b = 0; b < R; ++b) {
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a <= b; ++a) v = fma(x[a], ri[a * R + b], v);
+      y[b] = v;
+    }
+#pragma unroll
+    for (int b = 0; b < R; ++b) Out[i * R + b] = y[b];
+  }
+}
+
+template <int R>
+void qr_device_r(const double* X, double* Out, int64_t n, double* scratch, cudaStream_t st) {
+  double* Rinv = scratch;
+  double* S = scratch + 256;
+  int* skip = reinterpret_cast<int*>(scratch + 512);
+  double* part = scratch + 520;
+  const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(kQrParts, (n + kThreads - 1) / kThreads));
+  const double* src = X;
+  for (int pass = 0; pass < 3; ++pass) {
+    const int* sk = pass == 2 ? skip : nullptr;
+    qr_gram_kernel<R><<<grid, kThreads, 0, st>>>(src, n, part, sk);
+    FLZ_LAUNCH_CHECK();
+    qr_factor_kernel<<<1, 64, 0, st>>>(part, (int)grid, R, (double)n, pass, Rinv, S, skip);
+    FLZ_LAUNCH_CHECK();
+    qr_update_kernel<R><<<gs_blocks(n), kThreads, 0, st>>>(src, Rinv, Out, n, sk);
+    FLZ_LAUNCH_CHECK();
+    src = Out;
+  }
+}
+
+size_t qr_device_scratch() { return 520 + (size_t)kQrParts * 136; }
+
+void qr_device(const double* X, double* Out, int64_t n, int r, double* scratch, cudaStream_t st) {
+  switch (r) {
+#define FLZ_QR(R_) \
+  case R_:         \
+    qr_device_r<R_>(X, Out, n, scratch, st); \
+    break;
+    FLZ_QR(1) FLZ_QR(2) FLZ_QR(3) FLZ_QR(4) FLZ_QR(5) FLZ_QR(6) FLZ_QR(7) FLZ_QR(8)
+    FLZ_QR(9) FLZ_QR(10) FLZ_QR(11) FLZ_QR(12) FLZ_QR(13) FLZ_QR(14) FLZ_QR(15) FLZ_QR(16)
+#undef FLZ_QR
+    default: fail(FLZ_ERR_INVALID_ARG, "block width %d", r);
+  }
+}
+
 void columns_to_blocks(const double* X, int64_t n, int64_t ldx, int cols, double* Out, cudaStream_t st) {
   if (cols <= 0 || n <= 0) return;
   columns_to_blocks_kernel<<<gs_blocks(n * cols), 256, 0, st>>>(X, n, ldx, cols, Out);

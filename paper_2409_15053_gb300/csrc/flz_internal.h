@@ -266,6 +266,13 @@ struct flz_solver {
   // start vectors of the next solve (flz_solver_set_start_vectors): n x start_cols, column-major
   flz::DevBuf<double> start;
   int32_t start_cols = 0;
+  double* pinned = nullptr;  // page-locked host words for the per-step D_j and S_j
+  flz_solver() = default;
+  flz_solver(const flz_solver&) = delete;
+  flz_solver& operator=(const flz_solver&) = delete;
+  ~flz_solver() {
+    if (pinned) cudaFreeHost(pinned);
+  }
 };
 
 namespace flz {
@@ -405,6 +412,13 @@ void combine_columns(const double* X, int64_t n, int64_t ld, int cols, const dou
 // out[t * ldo + i] = scale * X[i * ld + t] (row-major block to columns)
 void rows_to_columns(const double* X, int64_t n, int s, int ld, double* out, int64_t ldo, cudaStream_t st,
                      double scale = 1.0);
+// Block QR of the n x r block X (row-major) into Out (in place allowed) with
+// no host round trip: CholeskyQR2, or shifted CholeskyQR3 when the first
+// Cholesky factorization fails. scratch: qr_device_scratch() device doubles;
+// on return S (the product of the factors, r x r upper triangular, X = Out S)
+// is at scratch + 256.
+size_t qr_device_scratch();
+void qr_device(const double* X, double* Out, int64_t n, int r, double* scratch, cudaStream_t st);
 // The inverse: column j of the column-major X (leading dimension ldx) into column
 // j % 16 of the row-major 16-column block j / 16 of Out (blocks n * 16 apart).
 void columns_to_blocks(const double* X, int64_t n, int64_t ldx, int cols, double* Out, cudaStream_t st);

@@ -78,6 +78,11 @@ struct Engine {
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   TcBasis* tcb = nullptr;  // digit copy of an FP64 basis: reorthogonalization on the tensor cores
   bool fx = false;         // the filter runs in fixed point: check its overflow flag after each step
+  // FP64 basis: the block QR runs on the device (scratch qrs) and a step's
+  // D_j and S_j reach the host through `pinned` (3 r x r words) at its one
+  // synchronization
+  double* pinned = nullptr;
+  double* qrs = nullptr;
 
   T* block(int b) const { return Q + (size_t)b * n * r; }
 
@@ -144,6 +149,9 @@ struct Engine {
     return S;
   }
 
+  // Block QR of X into Out on the device (qr_device); S is left at qrs + 256.
+  void block_qr_device(const double* X, double* Out) { qr_device(X, Out, n, r, qrs, st); }
+
   // Classical Gram-Schmidt twice of X against blocks 0..nb-1; returns the
   // total projection coefficients of the last block (r x r, row-major) in Dlast.
   void cgs2(T* X, int nb, std::vector<double>* Dlast) {
@@ -178,21 +186,48 @@ struct Engine {
     FLZ_CUDA(cudaEventRecord(ev[0], st));
     op(block(j), W);
     FLZ_CUDA(cudaEventRecord(ev[1], st));
-    std::vector<double> D;
-    cgs2(W, j + 1, &D);
-    P.D.push_back(D);
     T* next = (j + 1 < nb_cap) ? block(j + 1) : nullptr;
     T* dst = next ? next : W;
-    std::vector<double> S = block_qr(W, dst);
+    std::vector<double> D, S;
+    bool device_qr = false;
+    if constexpr (std::is_same<T, double>::value)
+      if (pinned) {
+        // one synchronization per step: CGS2, the device QR, the new block's
+        // digits, then D_j and S_j to the host
+        device_qr = true;
+        cgs2(W, j + 1, nullptr);
+        block_qr_device(W, dst);
+        if (next) seal(j + 1);
+        const size_t rr = (size_t)r * r, off = (size_t)j * rr;
+        FLZ_CUDA(cudaMemcpyAsync(pinned, C + off, sizeof(double) * rr, cudaMemcpyDeviceToHost, st));
+        FLZ_CUDA(cudaMemcpyAsync(pinned + rr, C2 + off, sizeof(double) * rr, cudaMemcpyDeviceToHost, st));
+        FLZ_CUDA(cudaMemcpyAsync(pinned + 2 * rr, qrs + 256, sizeof(double) * rr, cudaMemcpyDeviceToHost, st));
+        FLZ_CUDA(cudaEventRecord(ev[2], st));
+        FLZ_CUDA(cudaEventSynchronize(ev[2]));
+        D.resize(rr);
+        S.assign(pinned + 2 * rr, pinned + 3 * rr);
+        for (size_t i = 0; i < rr; ++i) D[i] = pinned[i] + pinned[rr + i];
+      }
+    if (!device_qr) {
+      cgs2(W, j + 1, &D);
+      S = block_qr(W, dst);
+    }
+    P.D.push_back(D);
     // breakdown: the new block is (nearly) dependent on the basis; its
     // directions are rounding noise and must be made orthogonal to the basis.
     double smin = 1e300;
     for (int i = 0; i < r; ++i) smin = std::min(smin, std::fabs(S[i * r + i]));
-    if (next && smin < 1e-12 * std::max(op_norm, 1e-300)) {
+    const bool breakdown = next && smin < 1e-12 * std::max(op_norm, 1e-300);
+    if (breakdown) {
       cgs2(next, j + 1, nullptr);
-      block_qr(next, next);
+      if constexpr (std::is_same<T, double>::value) {
+        if (device_qr) block_qr_device(next, next);
+        else block_qr(next, next);
+      } else {
+        block_qr(next, next);
+      }
     }
-    if (next) seal(j + 1);
+    if (next && (!device_qr || breakdown)) seal(j + 1);
     P.S.push_back(S);
     FLZ_CUDA(cudaEventRecord(ev[2], st));
     FLZ_CUDA(cudaEventSynchronize(ev[2]));
@@ -527,7 +562,7 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   s->C.reserve((size_t)nb_cap * r * r);
   s->C2.reserve((size_t)nb_cap * r * r);
   s->part.reserve(std::max(basis_dot_scratch(n, nb_cap, r, r), (size_t)1));
-  s->small.reserve(16 * 16 + 64);
+  s->small.reserve(16 * 16 + 64 + qr_device_scratch());  // host-path R^{-1}; the device QR's scratch after it
   s->X.reserve((size_t)n * 16);
   s->AX.reserve((size_t)n * 16);
   FLZ_CUDA(cudaMemsetAsync(s->X.p, 0, sizeof(double) * n * 16, st));  // columns a short chunk leaves unwritten
@@ -535,6 +570,11 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   static_assert(sizeof(BT) == sizeof(double), "basis storage reuses the FP64 buffers");
   BT* Qt = reinterpret_cast<BT*>(s->Q.p);
   Engine<BT> E{A, n, r, st, Qt, nb_cap, reinterpret_cast<BT*>(s->W.p), s->C.p, s->C2.p, s->part.p, s->small.p};
+  if constexpr (std::is_same<BT, double>::value) {
+    if (!s->pinned) FLZ_CUDA(cudaMallocHost(reinterpret_cast<void**>(&s->pinned), sizeof(double) * 3 * 16 * 16));
+    E.pinned = s->pinned;
+    E.qrs = s->small.p + 16 * 16 + 64;
+  }
   if (use_tc) {
     s->tcb.reserve(n, (int64_t)nb_cap * r);
     E.tcb = &s->tcb;
