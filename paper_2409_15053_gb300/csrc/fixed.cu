@@ -112,6 +112,9 @@ __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((lon
 struct FxStep {
   uint64_t b_cur;    // b_0 (first step only), offset-binary, units 2^-61 scaled by 2^-s
   uint64_t b_next;   // b_{k+1}
+  uint64_t b_m1;     // b_k     (batches: the terms added three at a time)
+  uint64_t b_m2;     // b_{k-1}
+  int t;             // k + 1: the index of the value this step forms
   const int* cexp;   // column scale exponents E_t
   int sum_exp;       // s: the running sum is held in units of 2^(s - F)
   int vec_bits;      // F
@@ -190,6 +193,55 @@ __device__ __forceinline__ void finish_row_global(size_t idx, const Acc (&S)[R],
   load_u64_row<R>((FIRST ? ycur : yprev) + idx, own);
   if (!FIRST) load_u64_row<R>(acc + idx, sum);
   finish_row<R, FIRST, LAST>(idx, S, sa, own, sum, ynext, acc, W, k);
+}
+
+// Batches read and write the running sum sum_k b_k Y_k every third degree
+// only: the step forming Y_t (t = k + 1) also holds Y_{k-1} (its recurrence
+// operand) and reads its own row of Y_k, so it adds the terms of indices
+// t-2, t-1, t when t = 1 (mod 3), and the pending one or two at the last
+// step. Each term is rounded once and the sums are exact integers, so the
+// result is the same as adding every term at its own step. (The single
+// problem's staged kernel is faster with a term per step: there the saved
+// bytes do not pay for the registers the extra terms take.)
+__device__ __forceinline__ int flush_terms(int t, bool last) {
+  const int p = (t - 1) % 3;
+  return p == 0 ? 3 : (last ? p : 0);
+}
+
+// finish_row with the terms added three at a time; sum is read only when
+// terms are added, ycur (Y_k) only when two or more are.
+template <int R, bool FIRST, bool LAST>
+__device__ __forceinline__ void finish_row_flush3(size_t idx, const Acc (&S)[R], uint64_t sa,
+                                                  const uint64_t (&own)[R], uint64_t (&sum)[R],
+                                                  const uint64_t* ycur, uint64_t* ynext, uint64_t* acc, double* W,
+                                                  const FxStep& k) {
+  const int nt = FIRST ? 2 : flush_terms(k.t, LAST);
+  uint64_t yk[R];
+  if (!FIRST && nt >= 2) load_u64_row<R>(ycur + idx, yk);
+  uint64_t yn[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    if (FIRST) {
+      yn[t] = acc_result(S[t], sa, kValBits + 1) + kOff;  // Y_1 = (1/2)(2 Ahat) V
+      sum[t] = coeff_times(k.b_cur, own[t]) + coeff_times(k.b_next, yn[t]);
+    } else {
+      yn[t] = acc_result(S[t], sa, kValBits) - own[t];  // Y_{k+1} = 2 Ahat Y_k - Y_{k-1}
+      if (nt >= 1) sum[t] += coeff_times(k.b_next, yn[t]);
+      if (nt >= 2) sum[t] += coeff_times(k.b_m1, yk[t]);
+      if (nt >= 3) sum[t] += coeff_times(k.b_m2, own[t]);
+    }
+    check_range(yn[t], k.limit, k.flag);
+  }
+  if (!LAST) {
+    store_u64_row<R>(ynext + idx, yn);
+    if (nt > 0) store_u64_row<R>(acc + idx, sum);
+  } else {
+    double w[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t)
+      w[t] = __ll2double_rn((long long)sum[t]) * pow2(k.cexp[t] + k.sum_exp - k.vec_bits);
+    store_u64_row<R>(W + idx, w);
+  }
 }
 
 // Bounded wait for phase 0 of a CTA barrier: false after wait_ns (2 s unless
@@ -687,7 +739,7 @@ bool fx_filter_apply(flz_matrix* A, double c, double e, const double* coeffs, in
   FLZ_LAUNCH_CHECK();
   fx_to_fixed_kernel<<<blocks_for(nr), 256, 0, st>>>(V, nr, r, cexp, Fb, y0);
   FLZ_LAUNCH_CHECK();
-  FxStep base{0, 0, cexp, s, Fb, 5ull << (Fb - 2), flag, wait_limit_ns()};
+  FxStep base{0, 0, kOff, kOff, 1, cexp, s, Fb, 5ull << (Fb - 2), flag, wait_limit_ns()};
   uint64_t* acc = reinterpret_cast<uint64_t*>(W);
   const uint64_t* vs = F.sell.p;
   const uint64_t* vc = F.csr.p;
@@ -790,6 +842,9 @@ __global__ void __launch_bounds__(kThreads, R <= 4 ? 4 : (R <= 8 ? 2 : 1)) fx_se
   const int sl0 = blockIdx.x * 8, sl1 = min(a.nsl, sl0 + 8);
   const int e0 = __ldg(a.off + sl0), e1 = __ldg(a.off + sl1);
   const bool vb = a.vec_bulk && ((rows * R) % 2 == 0);  // uniform over the CTA
+  // the running sums are staged on the regular flush steps; a problem whose
+  // last degree falls between them reads its rows' sums directly
+  const bool regular = !FIRST && flush_terms(k + 1, false) > 0;
   if (threadIdx.x == 0) {
     tc::mbar_init(&bar[0], 1);
     tc::mbar_init(&bar[1], 1);
@@ -808,9 +863,9 @@ __global__ void __launch_bounds__(kThreads, R <= 4 ? 4 : (R <= 8 ? 2 : 1)) fx_se
       tc::mbar_expect_tx(&bar[1], bytes);
       tc::bulk_g2s(s_own, ycur + at, bytes, &bar[1]);
     } else {
-      tc::mbar_expect_tx(&bar[1], 2 * bytes);
+      tc::mbar_expect_tx(&bar[1], regular ? 2 * bytes : bytes);
       tc::bulk_g2s(s_own, yprev + at, bytes, &bar[1]);
-      tc::bulk_g2s(s_sum, a.acc + at, bytes, &bar[1]);
+      if (regular) tc::bulk_g2s(s_sum, a.acc + at, bytes, &bar[1]);
     }
   }
   const int t = threadIdx.x, row = row0 + t;
@@ -863,26 +918,30 @@ __global__ void __launch_bounds__(kThreads, R <= 4 ? 4 : (R <= 8 ? 2 : 1)) fx_se
   const bool ok1 = vb ? stage_wait(&bar[1], a.flag, a.wait_ns) : true;
   if (active && ok0 && ok1) {
     const size_t idx = (size_t)row * R;
-    FxStep ks{FIRST ? __ldg(a.bfix + pi) : 0ull, __ldg(a.bfix + (size_t)(k + 1) * a.count + pi), a.zexp,
-              __ldg(a.sexp + pi), a.vec_bits, a.limit, a.flag, a.wait_ns};
+    const bool last = k + 1 == md;
+    FxStep ks{FIRST ? __ldg(a.bfix + pi) : kOff, __ldg(a.bfix + (size_t)(k + 1) * a.count + pi),
+              FIRST ? kOff : __ldg(a.bfix + (size_t)k * a.count + pi),
+              k >= 1 ? __ldg(a.bfix + (size_t)(k - 1) * a.count + pi) : kOff, k + 1, a.zexp, __ldg(a.sexp + pi),
+              a.vec_bits, a.limit, a.flag, a.wait_ns};
+    const bool need_sum = !FIRST && flush_terms(k + 1, last) > 0;
     uint64_t own[R], sum[R];
+#pragma unroll
+    for (int c = 0; c < R; ++c) sum[c] = 0ull;
     if (vb) {
 #pragma unroll
-      for (int c = 0; c < R; ++c) {
-        own[c] = s_own[t * R + c];
-        sum[c] = FIRST ? 0ull : s_sum[t * R + c];
+      for (int c = 0; c < R; ++c) own[c] = s_own[t * R + c];
+      if (need_sum && regular) {
+#pragma unroll
+        for (int c = 0; c < R; ++c) sum[c] = s_sum[t * R + c];
+      } else if (need_sum) {
+        load_u64_row<R>(a.acc + idx, sum);
       }
     } else {
       load_u64_row<R>((FIRST ? ycur : yprev) + idx, own);
-      if (FIRST) {
-#pragma unroll
-        for (int c = 0; c < R; ++c) sum[c] = 0ull;
-      } else {
-        load_u64_row<R>(a.acc + idx, sum);
-      }
+      if (need_sum) load_u64_row<R>(a.acc + idx, sum);
     }
-    if (k + 1 == md) finish_row<R, FIRST, true>(idx, S, sa, own, sum, ynext, a.acc, a.W, ks);
-    else finish_row<R, FIRST, false>(idx, S, sa, own, sum, ynext, a.acc, a.W, ks);
+    if (last) finish_row_flush3<R, FIRST, true>(idx, S, sa, own, sum, ycur, ynext, a.acc, a.W, ks);
+    else finish_row_flush3<R, FIRST, false>(idx, S, sa, own, sum, ycur, ynext, a.acc, a.W, ks);
   }
   // nothing may still be copying into this CTA's shared memory when it exits
   if (!ok0) tc::mbar_wait_drain(&bar[0], 0);

@@ -97,12 +97,13 @@ def test_batch_tensor_core_basis_grows_past_its_first_capacity():
     check(csrs, intervals, out, 1e-10)
 
 
-@pytest.mark.parametrize("r", [4, 8, 16])
-def test_batch_fixed_point_filter_matches_dense(r):
+@pytest.mark.parametrize("r,m", [(4, 40), (4, 41), (4, 42), (8, 40), (16, 40)])
+def test_batch_fixed_point_filter_matches_dense(r, m):
     # the 64-bit fixed-point filter over the concatenation: per-problem maps,
-    # coefficient tables and sum scalings in one kernel per degree
+    # coefficient tables and sum scalings in one kernel per degree; degrees
+    # 40, 41, 42 end with 3, 1 and 2 running-sum terms added at the last step
     csrs, intervals = small_batch(3, 6)
-    st, out = run_batch(csrs, intervals, block_size=r, degree=40, check_every=5, precision=flz.FLZ_PREC_FX64)
+    st, out = run_batch(csrs, intervals, block_size=r, degree=m, check_every=5, precision=flz.FLZ_PREC_FX64)
     assert st == flz.FLZ_OK
     assert all(o["stats"]["filter_precision"] == flz.FLZ_PREC_FX64 for o in out)
     check(csrs, intervals, out, 1e-10)

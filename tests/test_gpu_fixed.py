@@ -110,9 +110,11 @@ def test_fixed_point_filter_matches_oracle(name, make, r):
     assert err <= fp64_bound(csr, c, e, m, V)
 
 
-@pytest.mark.parametrize("m", [0, 1, 2, 3, 4, 50, 200])
+@pytest.mark.parametrize("m", [0, 1, 2, 3, 4, 5, 6, 7, 50, 101, 200])
 @pytest.mark.parametrize("r", [3, 4])
 def test_fixed_point_filter_degrees(m, r):
+    # degrees of every residue mod 3: the running sum takes its terms three
+    # at a time, and the last degree adds the one or two still pending
     csr = laplacian_3d_7pt(12, 12, 12, 0.5 * np.linspace(0, 1, 1728))
     M = Mat(csr)
     coeffs = chebyshev.filter_coefficients(-1.0, -0.9, m)
@@ -134,6 +136,22 @@ def test_single_term_is_cosine_on_a_diagonal_matrix(k):
     got = run_filter(M, 0.0, 1.0, b, V)
     want = np.cos(k * np.arccos(d))[:, None] * V
     assert np.max(np.abs(got - want)) <= 64 * (k + 1) ** 2 * U64 * np.max(np.abs(V))
+
+
+@pytest.mark.parametrize("k", range(11))
+def test_single_term_inside_the_series_is_counted_once(k):
+    # degree 10 with only b_k nonzero, for every k: each term enters the
+    # running sum exactly once, whichever degree step adds it
+    n = 5000
+    d = np.cos(np.linspace(0.0, np.pi, n))
+    from synth import diagonal_csr
+    M = Mat(diagonal_csr(d))
+    b = np.zeros(11)
+    b[k] = 1.0
+    V = random_normal_block(n, 4, 2)
+    got = run_filter(M, 0.0, 1.0, b, V)
+    want = np.cos(k * np.arccos(d))[:, None] * V
+    assert np.max(np.abs(got - want)) <= 64 * 11 ** 2 * U64 * np.max(np.abs(V))
 
 
 @pytest.mark.parametrize("name,make,r", [("lap3d_pot_13x9x11", CASES[1][1], 2), ("fd4_wells_8",
