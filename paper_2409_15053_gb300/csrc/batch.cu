@@ -595,7 +595,7 @@ struct BatchEngine {
     if (precision == FLZ_PREC_FX64) {
       // the fixed-point filter where its format holds every problem, else FP64
       if (fx_batch_prepare(B->fxb, N, B->nnz, B->rowptr.p, B->col.p, B->val.p, B->diag_pos.p, B->max_row_nnz,
-                           B->d_off.p, count, cc.p, ee.p, r, st) &&
+                           B->d_off.p, B->off, count, cc.p, ee.p, r, st) &&
           fx_batch_coefficients(B->fxb, coeffs, st))
         return;
       precision = FLZ_PREC_FP64;

@@ -672,10 +672,14 @@ __global__ void qr_factor_kernel(const double* __restrict__ part, int nparts, in
   if (pass == 2 && *skip) return;
   const int NT = r * (r + 1) / 2;
   __shared__ double gs[16 * 17 / 2];
-  for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+  // entry t of the triangle summed by one warp (lanes over the partial
+  // sums, then a fixed shuffle tree: the same order on every run)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int t = warp; t < NT; t += nw) {
     double v = 0.0;
-    for (int q = 0; q < nparts; ++q) v += part[(size_t)q * NT + t];
-    gs[t] = v;
+    for (int q = lane; q < nparts; q += 32) v += part[(size_t)q * NT + t];
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    if (lane == 0) gs[t] = v;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
@@ -769,7 +773,7 @@ void qr_device_r(const double* X, double* Out, int64_t n, double* scratch, cudaS
     const int* sk = pass == 2 ? skip : nullptr;
     qr_gram_kernel<R><<<grid, kThreads, 0, st>>>(src, n, part, sk);
     FLZ_LAUNCH_CHECK();
-    qr_factor_kernel<<<1, 64, 0, st>>>(part, (int)grid, R, (double)n, pass, Rinv, S, skip);
+    qr_factor_kernel<<<1, 256, 0, st>>>(part, (int)grid, R, (double)n, pass, Rinv, S, skip);
     FLZ_LAUNCH_CHECK();
     qr_update_kernel<R><<<gs_blocks(n), kThreads, 0, st>>>(src, Rinv, Out, n, sk);
     FLZ_LAUNCH_CHECK();

@@ -797,6 +797,7 @@ struct FxSegArgs {
   const int* scol;
   const uint64_t* sval;   // 2 Ahat_i, offset-binary, units 2^-61
   const int* d_off;       // count + 1 problem row offsets
+  const int* cta_p0;      // problem of each CTA's first row
   const uint64_t* bfix;   // coefficient table: b_k of problem i at k * count + i
   const int* sexp;        // per-problem sum exponent s_i
   const int* zexp;        // 16 zero column exponents (unit columns)
@@ -825,20 +826,23 @@ __global__ void __launch_bounds__(kThreads, R <= 4 ? 4 : (R <= 8 ? 2 : 1)) fx_se
                                                                const uint64_t* yprev, uint64_t* ynext) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);         // [0] matrix range, [1] vector rows
-  int* s_live = reinterpret_cast<int*>(smem + 16);
   uint64_t* s_own = reinterpret_cast<uint64_t*>(smem + 32);  // V (first step) or Y_{k-1} rows
   uint64_t* s_sum = s_own + kThreads * R;                    // running-sum rows
   uint64_t* s_val = s_sum + kThreads * R;
   int* s_col = reinterpret_cast<int*>(s_val + a.emax);
   const int row0 = blockIdx.x * kThreads, rows = min(kThreads, a.n - row0);
-  if (threadIdx.x == 0) {
-    int live = 0;
-    const int p0 = seg_problem(a.d_off, a.count, row0), p1 = seg_problem(a.d_off, a.count, row0 + rows - 1);
-    for (int i = p0; i <= p1 && !live; ++i) live = __ldg(a.active + i) && k + 1 <= __ldg(a.mdeg + i);
-    *s_live = live;
+  // the row's problem: forward from the CTA's first row's (rows of a CTA
+  // span one or a few problems)
+  const int t = threadIdx.x, row = row0 + t;
+  int pi = 0, md = 0;
+  bool active = row < a.n;
+  if (active) {
+    pi = __ldg(a.cta_p0 + blockIdx.x);
+    while (pi + 1 < a.count && __ldg(a.d_off + pi + 1) <= row) ++pi;
+    md = __ldg(a.mdeg + pi);
+    active = __ldg(a.active + pi) && k + 1 <= md;
   }
-  __syncthreads();
-  if (!*s_live) return;  // reads nothing the previous degree writes
+  if (!__syncthreads_or(active)) return;  // reads nothing the previous degree writes
   const int sl0 = blockIdx.x * 8, sl1 = min(a.nsl, sl0 + 8);
   const int e0 = __ldg(a.off + sl0), e1 = __ldg(a.off + sl1);
   const bool vb = a.vec_bulk && ((rows * R) % 2 == 0);  // uniform over the CTA
@@ -867,14 +871,6 @@ __global__ void __launch_bounds__(kThreads, R <= 4 ? 4 : (R <= 8 ? 2 : 1)) fx_se
       tc::bulk_g2s(s_own, yprev + at, bytes, &bar[1]);
       if (regular) tc::bulk_g2s(s_sum, a.acc + at, bytes, &bar[1]);
     }
-  }
-  const int t = threadIdx.x, row = row0 + t;
-  int pi = 0, md = 0;
-  bool active = row < a.n;
-  if (active) {
-    pi = seg_problem(a.d_off, a.count, row);
-    md = __ldg(a.mdeg + pi);
-    active = __ldg(a.active + pi) && k + 1 <= md;
   }
   Acc S[R];
 #pragma unroll
@@ -1022,10 +1018,20 @@ void run_fx_seg(FxBatch& F, const FxSegArgs& a, bool pdl, cudaStream_t st) {
 }  // namespace
 
 bool fx_batch_prepare(FxBatch& F, int64_t N, int64_t nnz, const int* rowptr, const int* col, const double* val,
-                      const int* diag_pos, int32_t max_row_nnz, const int* d_off, int count, const double* cc,
-                      const double* ee, int r, cudaStream_t st) {
+                      const int* diag_pos, int32_t max_row_nnz, const int* d_off, const std::vector<int>& off_host,
+                      int count, const double* cc, const double* ee, int r, cudaStream_t st) {
   if (!fx_supported(r) || max_row_nnz > kLongRow) return false;
   if (!F.layout_built) {
+    // the problem of every CTA's first row
+    const int64_t ctas = (N + kThreads - 1) / kThreads;
+    std::vector<int> p0(ctas);
+    int p = 0;
+    for (int64_t b = 0; b < ctas; ++b) {
+      while (p + 1 < count && (int64_t)off_host[p + 1] <= b * kThreads) ++p;
+      p0[b] = p;
+    }
+    F.cta_p0.reserve((size_t)ctas);
+    FLZ_CUDA(cudaMemcpy(F.cta_p0.p, p0.data(), sizeof(int) * ctas, cudaMemcpyHostToDevice));
     F.layout_built = true;
     F.layout_ok = false;
     flz_matrix tmp;  // borrows the concatenation's structure to build its SELL-32 layout
@@ -1117,7 +1123,7 @@ void fx_batch_filter(FxBatch& F, int r, const double* Q, const int* jdev, const 
   fx_seg_load_kernel<<<blocks_for(nr), 256, 0, st>>>(Q, jdev, nr, F.vec_bits, F.y0.p);
   FLZ_LAUNCH_CHECK();
   FxSegArgs a{(int)F.n, (int)F.nsl, (int)F.emax, reinterpret_cast<uintptr_t>(W) % 16 == 0 ? 1 : 0, F.count,
-              F.sell_off.p, F.sell_col.p, F.sval.p, d_off, F.bfix.p, F.sexp.p, F.zexp.p, mdeg, active,
+              F.sell_off.p, F.sell_col.p, F.sval.p, d_off, F.cta_p0.p, F.bfix.p, F.sexp.p, F.zexp.p, mdeg, active,
               reinterpret_cast<uint64_t*>(W), W, F.vec_bits, 5ull << (F.vec_bits - 2), F.flag.p, wait_limit_ns()};
   switch (r) {
     case 1: run_fx_seg<1, 8>(F, a, pdl, st); break;

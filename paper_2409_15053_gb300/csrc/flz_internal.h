@@ -188,7 +188,7 @@ struct FxBatch {
   int64_t n = 0, nsl = 0, emax = 0;
   DevBuf<int32_t> sell_off, sell_col;
   DevBuf<uint64_t> sval, y0, ya, yb, bfix;
-  DevBuf<int> sexp, zexp;
+  DevBuf<int> sexp, zexp, cta_p0;
   DevBuf<unsigned> flag;
   unsigned* flag_host = nullptr;
   int vec_bits = 61, mmax = 0, count = 0;
@@ -321,8 +321,8 @@ void fx_check_flag(flz_matrix* A);
 // problems (j read from jdev on the device: graph-capturable); the columns of
 // every problem's Q_j must have norm at most 1 (within 2^-20).
 bool fx_batch_prepare(FxBatch& F, int64_t N, int64_t nnz, const int* rowptr, const int* col, const double* val,
-                      const int* diag_pos, int32_t max_row_nnz, const int* d_off, int count, const double* cc,
-                      const double* ee, int r, cudaStream_t st);
+                      const int* diag_pos, int32_t max_row_nnz, const int* d_off, const std::vector<int>& off_host,
+                      int count, const double* cc, const double* ee, int r, cudaStream_t st);
 bool fx_batch_coefficients(FxBatch& F, const std::vector<std::vector<double>>& coeffs, cudaStream_t st);
 void fx_batch_filter(FxBatch& F, int r, const double* Q, const int* jdev, const int* d_off, const int* mdeg,
                      const int* active, double* W, bool pdl, cudaStream_t st);
