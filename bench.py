@@ -360,7 +360,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32/BF16-filter solves reported under 'variants'")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch-of-64 leg")
-    ap.add_argument("--batch-legs", default="fp32,fp64,df64,fx64,sequential",
+    ap.add_argument("--batch-legs", default="fp32,fp64,df64,fx64,fx64_persistent,sequential",
                     help="--mode batch: the legs to run (a single leg with --batch-once runs one solve, no warm-up)")
     ap.add_argument("--batch-once", action="store_true", help="--mode batch: one solve per leg, no warm-up (profiling)")
     ap.add_argument("--batch-block-size", type=int, default=0,
@@ -597,7 +597,8 @@ def variant_leg(flz, torch, h, p, alpha, beta, stream, flush, ref_vals, args):
     return out
 
 
-def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "sequential"), once=False, block_size=0):
+def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "fx64_persistent", "sequential"), once=False,
+              block_size=0):
     """The batched form against one-at-a-time FP64 solves on the same GPU.
 
     Workload: 64 independent 2D/3D Laplacians with U(0,1) potentials, n
@@ -637,7 +638,8 @@ def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "sequent
 
     out = {"problems": len(items), "sum_n": int(sum(c.n for c, _, _ in items)), "eigenpairs": total}
     for name, prec, tol in (("batch_fp32", flz.FLZ_PREC_FP32, 1e-6), ("batch_fp64", flz.FLZ_PREC_FP64, 1e-10),
-                            ("batch_df64", flz.FLZ_PREC_DF64, 1e-10), ("batch_fx64", flz.FLZ_PREC_FX64, 1e-10)):
+                            ("batch_df64", flz.FLZ_PREC_DF64, 1e-10), ("batch_fx64", flz.FLZ_PREC_FX64, 1e-10),
+                            ("batch_fx64_persistent", flz.FLZ_PREC_FX64, 1e-10)):
         if name[6:] not in legs:
             continue
         p = flz.flz_params_default()
@@ -646,6 +648,7 @@ def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "sequent
         p.precision = prec
         p.tol = tol
         p.check_every = 5
+        p.persistent = 1 if name.endswith("persistent") else 0
         bt = flz.flz_batch_create(hs, alphas, betas, p)
         if not once:
             flz.flz_batch_solve(bt, stream)

@@ -169,6 +169,11 @@ typedef struct flz_params {
                            FX64 filter (FP64 where it does not apply) and Rayleigh-Ritz on A in FP64: the
                            mixed-precision form (not in the paper). See flz_stats.refine_sweeps. */
   int32_t start_mode;   /* flz_start_mode, used when start vectors are set; default FLZ_START_KRYLOV */
+  int32_t persistent;   /* batches with the fixed-point filter only. 0 (default): one launch per degree
+                           step, the steps of a block step replayed as a CUDA graph. 1: every degree of a
+                           filter application in one cooperative launch whose CTAs meet at a grid barrier
+                           between degrees (bounded: a wait beyond the limit of flz_set_wait_limit ends
+                           the solve with FLZ_ERR_TIMEOUT). Other solves ignore it. */
 } flz_params;
 
 /* One convergence check of a solve (Section 3.2.2's periodic Rayleigh-Ritz

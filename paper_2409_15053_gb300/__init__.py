@@ -63,6 +63,7 @@ class flz_params(ctypes.Structure):
         ("recurrence", ctypes.c_int32), ("transition", ctypes.c_double), ("ortho", ctypes.c_int32),
         ("refine", ctypes.c_int32),
         ("start_mode", ctypes.c_int32),
+        ("persistent", ctypes.c_int32),
     ]
 
 

@@ -559,7 +559,8 @@ flz_status flz_solver_create(flz_matrix* A, const flz_params* params, flz_solver
       p.bounds_steps < 1 || p.max_basis < 0 || p.guard < 0 || p.damping < 0 || p.damping > 2 || !(p.transition >= 0.0) ||
       (p.recurrence != FLZ_REC_FORWARD && p.recurrence != FLZ_REC_CLENSHAW) || p.ortho < FLZ_ORTHO_AUTO ||
       p.ortho > FLZ_ORTHO_TENSOR || p.refine < 0 || p.refine > 1 ||
-      (p.start_mode != FLZ_START_KRYLOV && p.start_mode != FLZ_START_SUBSPACE))
+      (p.start_mode != FLZ_START_KRYLOV && p.start_mode != FLZ_START_SUBSPACE) || p.persistent < 0 ||
+      p.persistent > 1)
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.ortho == FLZ_ORTHO_TENSOR && (!flz::TcBasis::supported(p.block_size) || p.precision == FLZ_PREC_DF64))
     fail(FLZ_ERR_INVALID_ARG, "tensor-core reorthogonalization needs an FP64 basis (not the double-FP32 precision)");

@@ -523,6 +523,7 @@ struct BatchEngine {
   DevBuf<int> jdev, active, mdeg, fail;
   int mmax = 0;
   bool pdl = true;  // degree steps as programmatic dependent launches
+  bool persistent = false;  // fixed-point filter: every degree in one cooperative launch
   int n_chunks = 0;
 
   void setup(flz_batch* b, int r_, int nbmax_, int prec, cudaStream_t s) {
@@ -677,7 +678,7 @@ struct BatchEngine {
   void apply_filter() {
     const long long nr = N * R;
     if (precision == FLZ_PREC_FX64) {
-      fx_batch_filter(B->fxb, R, Q.p, jdev.p, B->d_off.p, mdeg.p, active.p, W.p, pdl, st);
+      fx_batch_filter(B->fxb, R, Q.p, jdev.p, B->d_off.p, mdeg.p, active.p, W.p, pdl, persistent, st);
     } else if (precision == FLZ_PREC_FP64) {
       // V = Q_j in a fixed buffer (the graph is replayed with a moving j); the sum is W
       load_block_kernel<double><<<gsb(nr), 256, 0, st>>>(Q.p, jdev.p, nr, v64.p);
@@ -775,6 +776,12 @@ struct BatchEngine {
   template <int R>
   void step() {
     apply_filter<R>();
+    step_after_filter<R>();
+  }
+
+  // CUDA-core CGS2 and the rest of the step after the filter
+  template <int R>
+  void step_after_filter() {
     // CGS2 against Q_0..Q_j (nb from the device step index)
     dot<R>(Q.p, 0, W.p, C1.p);
     update<R>(Q.p, 0, R, C1.p, (long long)nbmax * R * R, -1.0, 1.0, W.p, R, active.p);
@@ -1089,9 +1096,13 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
       if (g) cudaGraphExecDestroy(g);
     }
   } graph_a, graph_b;
+  // the persistent filter is launched directly (one cooperative launch per step)
+  E.persistent = p.persistent == 1 && E.precision == FLZ_PREC_FX64;
   if (use_tc) {
-    graph_a.g = capture_part(E, [&] { E.apply_filter<R>(); });
+    if (!E.persistent) graph_a.g = capture_part(E, [&] { E.apply_filter<R>(); });
     graph_b.g = capture_part(E, [&] { E.step_tail<R>(); });
+  } else if (E.persistent) {
+    graph_b.g = capture_part(E, [&] { E.step_after_filter<R>(); });
   } else {
     graph_a.g = capture_part(E, [&] { E.step<R>(); });
   }
@@ -1101,11 +1112,14 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
     const auto ts = std::chrono::steady_clock::now();
     const int todo = std::min(p.check_every - (k % p.check_every), nbmax - k);
     for (int s = 0; s < todo; ++s) {
-      FLZ_CUDA(cudaGraphLaunch(graph_a.g, st));
+      if (E.persistent) E.apply_filter<R>();
+      else FLZ_CUDA(cudaGraphLaunch(graph_a.g, st));
       if (use_tc) {
         E.tc_orth((k + s + 1) * R, act);  // the basis holds Q_0 .. Q_j, j = k + s
         FLZ_CUDA(cudaGraphLaunch(graph_b.g, st));
         E.tc_append((k + s + 1) * R, act);
+      } else if (E.persistent) {
+        FLZ_CUDA(cudaGraphLaunch(graph_b.g, st));
       }
     }
     g_kernel_launches += (int64_t)todo * launches_per_step;
@@ -1432,7 +1446,7 @@ flz_status flz_batch_create(int32_t count, flz_matrix* const* mats, const double
         p.block_size == 16))
     fail(FLZ_ERR_INVALID_ARG, "batch block_size must be 0 (autotune) or one of 1, 2, 4, 8, 16");
   if (p.degree < 0 || p.max_degree < 1 || p.check_every < 1 || !(p.tol > 0.0) || p.bounds_steps < 1 ||
-      p.damping < 0 || p.damping > 2 || !(p.transition >= 0.0))
+      p.damping < 0 || p.damping > 2 || !(p.transition >= 0.0) || p.persistent < 0 || p.persistent > 1)
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.recurrence != FLZ_REC_FORWARD) fail(FLZ_ERR_INVALID_ARG, "batches use the forward recurrence only");
   if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_FX64)

@@ -137,6 +137,23 @@ __device__ __forceinline__ void load_u64_row(const uint64_t* p, uint64_t (&v)[R]
     for (int i = 0; i < R; ++i) v[i] = p[i];
   }
 }
+// The same through L2 only (__ldcg): values another CTA of the same launch
+// wrote (the persistent batch kernel), never a stale L1 line.
+template <int R>
+__device__ __forceinline__ void load_u64_row_cg(const uint64_t* p, uint64_t (&v)[R]) {
+  if constexpr ((R & 1) == 0) {
+#pragma unroll
+    for (int i = 0; i < R; i += 2) {
+      const ulonglong2 t = __ldcg(reinterpret_cast<const ulonglong2*>(p + i));
+      v[i] = t.x;
+      v[i + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = __ldcg(reinterpret_cast<const unsigned long long*>(p + i));
+  }
+}
+
 template <int R, class T>
 __device__ __forceinline__ void store_u64_row(T* p, const T (&v)[R]) {
   if constexpr ((R & 1) == 0) {
@@ -210,14 +227,17 @@ __device__ __forceinline__ int flush_terms(int t, bool last) {
 
 // finish_row with the terms added three at a time; sum is read only when
 // terms are added, ycur (Y_k) only when two or more are.
-template <int R, bool FIRST, bool LAST>
+template <int R, bool FIRST, bool LAST, bool CG = false>
 __device__ __forceinline__ void finish_row_flush3(size_t idx, const Acc (&S)[R], uint64_t sa,
                                                   const uint64_t (&own)[R], uint64_t (&sum)[R],
                                                   const uint64_t* ycur, uint64_t* ynext, uint64_t* acc, double* W,
                                                   const FxStep& k) {
   const int nt = FIRST ? 2 : flush_terms(k.t, LAST);
   uint64_t yk[R];
-  if (!FIRST && nt >= 2) load_u64_row<R>(ycur + idx, yk);
+  if (!FIRST && nt >= 2) {
+    if (CG) load_u64_row_cg<R>(ycur + idx, yk);
+    else load_u64_row<R>(ycur + idx, yk);
+  }
   uint64_t yn[R];
 #pragma unroll
   for (int t = 0; t < R; ++t) {
@@ -981,6 +1001,153 @@ __global__ void fx_seg_values_kernel(int64_t n, const int* __restrict__ rowptr, 
   if ((threadIdx.x & 31) == 0 && big > 0.0) atomicMax(rowsum_bits, (unsigned long long)__double_as_longlong(big));
 }
 
+// ---- the persistent variant: every degree in one cooperative launch ----
+// The grid (all CTAs resident: a cooperative launch) walks the 256-row tiles
+// of the concatenation for degree 0, meets at a grid barrier, walks them for
+// degree 1, and so on. No shared-memory staging: the vectors another CTA
+// wrote in the previous degree are read through L2 (__ldcg), the constant
+// matrix through the read-only path. The barrier is bounded: a CTA that waits
+// longer than wait_ns sets bit 2 of the flag (a timeout) and leaves, and the
+// others then time out at their next barrier; nothing spins without limit.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, uint64_t wait_ns,
+                                             unsigned* flag) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = *reinterpret_cast<volatile unsigned*>(gen);
+    __threadfence();  // this CTA's writes of the degree before its arrival
+    if (atomicAdd(count, 1u) == nblocks - 1) {
+      *reinterpret_cast<volatile unsigned*>(count) = 0u;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const uint64_t t0 = tc::globaltimer();
+      while (*reinterpret_cast<volatile unsigned*>(gen) == g) {
+        if (wait_ns == 0 || tc::globaltimer() - t0 > wait_ns) {
+          atomicOr(flag, 2u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int R, int U>
+__device__ __forceinline__ void seg_tile_plain(const FxSegArgs& a, int k, int tile, const uint64_t* ycur,
+                                               const uint64_t* yprev, uint64_t* ynext) {
+  const bool first = k == 0;
+  const int row = tile * kThreads + (int)threadIdx.x;
+  if (row >= a.n) return;
+  int pi = __ldg(a.cta_p0 + tile);
+  while (pi + 1 < a.count && __ldg(a.d_off + pi + 1) <= row) ++pi;
+  const int md = __ldg(a.mdeg + pi);
+  if (!__ldg(a.active + pi) || k + 1 > md) return;
+  const int sl = row >> 5;
+  const int so = __ldg(a.off + sl);
+  const int w = (__ldg(a.off + sl + 1) - so) >> 5;
+  const int base = so + (row & 31);
+  Acc S[R];
+#pragma unroll
+  for (int c = 0; c < R; ++c) acc_init(S[c], first ? kValBits + 1 : kValBits);
+  uint64_t sa = 0;
+  int j = 0;
+  for (; j + U <= w; j += U) {
+    int cj[U];
+    uint64_t av[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      cj[u] = __ldg(a.scol + base + 32 * (j + u));
+      av[u] = __ldg(a.sval + base + 32 * (j + u));
+    }
+    uint64_t y[U][R];
+#pragma unroll
+    for (int u = 0; u < U; ++u) load_u64_row_cg<R>(ycur + (size_t)cj[u] * R, y[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      sa += av[u];
+#pragma unroll
+      for (int c = 0; c < R; ++c) mac(S[c], av[u], y[u][c]);
+    }
+  }
+  for (; j < w; ++j) {
+    const int cj = __ldg(a.scol + base + 32 * j);
+    const uint64_t av = __ldg(a.sval + base + 32 * j);
+    uint64_t y[R];
+    load_u64_row_cg<R>(ycur + (size_t)cj * R, y);
+    sa += av;
+#pragma unroll
+    for (int c = 0; c < R; ++c) mac(S[c], av, y[c]);
+  }
+  const size_t idx = (size_t)row * R;
+  const bool last = k + 1 == md;
+  FxStep ks{first ? __ldg(a.bfix + pi) : kOff, __ldg(a.bfix + (size_t)(k + 1) * a.count + pi),
+            first ? kOff : __ldg(a.bfix + (size_t)k * a.count + pi),
+            k >= 1 ? __ldg(a.bfix + (size_t)(k - 1) * a.count + pi) : kOff, k + 1, a.zexp, __ldg(a.sexp + pi),
+            a.vec_bits, a.limit, a.flag, a.wait_ns};
+  uint64_t own[R], sum[R];
+#pragma unroll
+  for (int c = 0; c < R; ++c) sum[c] = 0ull;
+  load_u64_row_cg<R>((first ? ycur : yprev) + idx, own);
+  if (!first && flush_terms(k + 1, last) > 0) load_u64_row_cg<R>(a.acc + idx, sum);
+  if (first) {
+    if (last) finish_row_flush3<R, true, true, true>(idx, S, sa, own, sum, ycur, ynext, a.acc, a.W, ks);
+    else finish_row_flush3<R, true, false, true>(idx, S, sa, own, sum, ycur, ynext, a.acc, a.W, ks);
+  } else {
+    if (last) finish_row_flush3<R, false, true, true>(idx, S, sa, own, sum, ycur, ynext, a.acc, a.W, ks);
+    else finish_row_flush3<R, false, false, true>(idx, S, sa, own, sum, ycur, ynext, a.acc, a.W, ks);
+  }
+}
+
+template <int R, int U>
+__global__ void __launch_bounds__(kThreads, R <= 4 ? 4 : (R <= 8 ? 2 : 1))
+    fx_seg_persistent_kernel(FxSegArgs a, int mmax, const uint64_t* y0, uint64_t* ya, uint64_t* yb, unsigned* gbar) {
+  const int ntiles = (a.n + kThreads - 1) / kThreads;
+  const uint64_t* prev = nullptr;
+  const uint64_t* cur = y0;
+  uint64_t* next = ya;
+  for (int k = 0; k < mmax; ++k) {
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) seg_tile_plain<R, U>(a, k, tile, cur, prev, next);
+    if (k + 1 < mmax && !grid_barrier(gbar, gbar + 1, gridDim.x, a.wait_ns, a.flag)) return;
+    uint64_t* nn = (k == 0) ? yb : const_cast<uint64_t*>(prev);
+    prev = cur;
+    cur = next;
+    next = nn;
+  }
+}
+
+template <int R, int U>
+void run_fx_seg_persistent(FxBatch& F, const FxSegArgs& a, cudaStream_t st) {
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    FLZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fx_seg_persistent_kernel<R, U>, kThreads, 0));
+    if (per_sm < 1) fail(FLZ_ERR_CUDA, "persistent batch kernel: no resident CTA");
+  }
+  int dev = 0, sms = 0;
+  FLZ_CUDA(cudaGetDevice(&dev));
+  FLZ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int ntiles = (int)((F.n + kThreads - 1) / kThreads);
+  const int grid = std::max(1, std::min(ntiles, per_sm * sms));
+  FxSegArgs args = a;
+  int mmax = F.mmax;
+  const uint64_t* y0 = F.y0.p;
+  uint64_t* ya = F.ya.p;
+  uint64_t* yb = F.yb.p;
+  unsigned* gbar = F.gbar.p;
+  void* params[] = {&args, &mmax, &y0, &ya, &yb, &gbar};
+  // a barrier an earlier launch left early (a timeout) must not count its arrivals here
+  FLZ_CUDA(cudaMemsetAsync(gbar, 0, sizeof(unsigned), st));
+  FLZ_CUDA(cudaLaunchCooperativeKernel((const void*)fx_seg_persistent_kernel<R, U>, dim3(grid), dim3(kThreads),
+                                       params, 0, st));
+  FLZ_LAUNCH_CHECK();
+}
+
 size_t seg_stage_bytes(int R, int64_t emax) { return 32 + 2 * (size_t)kThreads * R * 8 + (size_t)emax * 12; }
 
 template <int R, int U, bool FIRST>
@@ -1055,6 +1222,8 @@ bool fx_batch_prepare(FxBatch& F, int64_t N, int64_t nnz, const int* rowptr, con
       FLZ_CUDA(cudaMemset(F.zexp.p, 0, sizeof(int) * 16));
       F.flag.reserve(2);
       FLZ_CUDA(cudaMemset(F.flag.p, 0, sizeof(unsigned) * 2));
+      F.gbar.reserve(2);  // grid-barrier arrival count and generation
+      FLZ_CUDA(cudaMemset(F.gbar.p, 0, sizeof(unsigned) * 2));
       FLZ_CUDA(cudaMallocHost(reinterpret_cast<void**>(&F.flag_host), sizeof(unsigned)));
       *F.flag_host = 0;
       F.layout_ok = true;
@@ -1118,13 +1287,24 @@ bool fx_batch_coefficients(FxBatch& F, const std::vector<std::vector<double>>& c
 }
 
 void fx_batch_filter(FxBatch& F, int r, const double* Q, const int* jdev, const int* d_off, const int* mdeg,
-                     const int* active, double* W, bool pdl, cudaStream_t st) {
+                     const int* active, double* W, bool pdl, bool persistent, cudaStream_t st) {
   const int64_t nr = F.n * (int64_t)r;
   fx_seg_load_kernel<<<blocks_for(nr), 256, 0, st>>>(Q, jdev, nr, F.vec_bits, F.y0.p);
   FLZ_LAUNCH_CHECK();
   FxSegArgs a{(int)F.n, (int)F.nsl, (int)F.emax, reinterpret_cast<uintptr_t>(W) % 16 == 0 ? 1 : 0, F.count,
               F.sell_off.p, F.sell_col.p, F.sval.p, d_off, F.cta_p0.p, F.bfix.p, F.sexp.p, F.zexp.p, mdeg, active,
               reinterpret_cast<uint64_t*>(W), W, F.vec_bits, 5ull << (F.vec_bits - 2), F.flag.p, wait_limit_ns()};
+  if (persistent) {
+    switch (r) {
+      case 1: run_fx_seg_persistent<1, 8>(F, a, st); break;
+      case 2: run_fx_seg_persistent<2, 8>(F, a, st); break;
+      case 4: run_fx_seg_persistent<4, 4>(F, a, st); break;
+      case 8: run_fx_seg_persistent<8, 2>(F, a, st); break;
+      case 16: run_fx_seg_persistent<16, 1>(F, a, st); break;
+      default: fail(FLZ_ERR_INVALID_ARG, "batch block width %d", r);
+    }
+    return;
+  }
   switch (r) {
     case 1: run_fx_seg<1, 8>(F, a, pdl, st); break;
     case 2: run_fx_seg<2, 8>(F, a, pdl, st); break;

@@ -189,7 +189,7 @@ struct FxBatch {
   DevBuf<int32_t> sell_off, sell_col;
   DevBuf<uint64_t> sval, y0, ya, yb, bfix;
   DevBuf<int> sexp, zexp, cta_p0;
-  DevBuf<unsigned> flag;
+  DevBuf<unsigned> flag, gbar;
   unsigned* flag_host = nullptr;
   int vec_bits = 61, mmax = 0, count = 0;
   double rowsum = 0.0;
@@ -324,8 +324,10 @@ bool fx_batch_prepare(FxBatch& F, int64_t N, int64_t nnz, const int* rowptr, con
                       const int* diag_pos, int32_t max_row_nnz, const int* d_off, const std::vector<int>& off_host,
                       int count, const double* cc, const double* ee, int r, cudaStream_t st);
 bool fx_batch_coefficients(FxBatch& F, const std::vector<std::vector<double>>& coeffs, cudaStream_t st);
+// persistent: every degree in one cooperative launch with a bounded grid
+// barrier between degrees, instead of one launch per degree.
 void fx_batch_filter(FxBatch& F, int r, const double* Q, const int* jdev, const int* d_off, const int* mdeg,
-                     const int* active, double* W, bool pdl, cudaStream_t st);
+                     const int* active, double* W, bool pdl, bool persistent, cudaStream_t st);
 // Reads and clears the batch filter's flag: FLZ_ERR_TIMEOUT (a stage wait
 // expired) or FLZ_ERR_INVALID_ARG (a value left the format's range) raised.
 void fx_batch_check_flag(FxBatch& F, cudaStream_t st);

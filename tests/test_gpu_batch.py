@@ -109,6 +109,26 @@ def test_batch_fixed_point_filter_matches_dense(r, m):
     check(csrs, intervals, out, 1e-10)
 
 
+@pytest.mark.parametrize("r,m", [(4, 40), (4, 41), (16, 42)])
+def test_batch_persistent_degree_loop_matches_dense(r, m):
+    # every degree of a filter application in one cooperative launch, the
+    # CTAs meeting at a bounded grid barrier between degrees
+    csrs, intervals = small_batch(3, 6)
+    st, out = run_batch(csrs, intervals, block_size=r, degree=m, check_every=5, precision=flz.FLZ_PREC_FX64,
+                        persistent=1)
+    assert st == flz.FLZ_OK
+    assert all(o["stats"]["filter_precision"] == flz.FLZ_PREC_FX64 for o in out)
+    check(csrs, intervals, out, 1e-10)
+
+
+def test_batch_persistent_loop_with_cuda_core_reorthogonalization_and_auto_degrees():
+    csrs, intervals = small_batch(5, 4)
+    st, out = run_batch(csrs, intervals, block_size=4, degree=0, check_every=5, precision=flz.FLZ_PREC_FX64,
+                        persistent=1, ortho=flz.FLZ_ORTHO_CUDA_CORES)
+    assert st == flz.FLZ_OK
+    check(csrs, intervals, out, 1e-10)
+
+
 def test_batch_fixed_point_filter_with_per_problem_degrees():
     # automatic degrees differ between problems: each problem's rows stop at
     # its own last degree (the running sum becomes W there) while the others go on

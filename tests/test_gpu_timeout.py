@@ -113,3 +113,37 @@ def test_solve_times_out_then_succeeds_in_the_same_process():
             flz.flz_solver_destroy(s)
     finally:
         flz.flz_matrix_destroy(h)
+
+
+def test_persistent_batch_grid_barrier_times_out_then_succeeds():
+    # the persistent batch filter's grid barrier with a zero wait limit: the
+    # CTAs that arrive before the last one give up at once, the solve ends
+    # with FLZ_ERR_TIMEOUT, and the same batch then solves normally
+    A = [laplacian_3d_7pt(14, 14, 14), laplacian_3d_7pt(12, 13, 15)]
+    hs = [flz.flz_matrix_create_csr(c.n, c.nnz, c.rowptr, c.col, c.val) for c in A]
+    try:
+        p = flz.flz_params_default()
+        p.block_size = 4
+        p.degree = 40
+        p.check_every = 5
+        p.precision = flz.FLZ_PREC_FX64
+        p.persistent = 1
+        p.ortho = flz.FLZ_ORTHO_CUDA_CORES
+        b = flz.flz_batch_create(hs, [0.0, 0.0], [0.5, 0.5], p)
+        try:
+            with ZeroWaitLimit():
+                with pytest.raises(flz.FlzError) as e:
+                    flz.flz_batch_solve(b)
+                assert e.value.status == flz.FLZ_ERR_TIMEOUT
+            assert flz.flz_batch_solve(b) == flz.FLZ_OK
+            for i, c in enumerate(A):
+                w = np.linalg.eigvalsh(c.to_dense())
+                want = w[w <= 0.5]
+                got = flz.flz_batch_get_eigenvalues(b, i)
+                assert got.shape == want.shape and np.max(np.abs(got - want)) < 1e-10 * 12.0
+        finally:
+            flz.flz_batch_destroy(b)
+    finally:
+        for h in hs:
+            flz.flz_matrix_destroy(h)
+
