@@ -363,6 +363,8 @@ def main():
     ap.add_argument("--batch-legs", default="fp32,fp64,df64,fx64,fx64_persistent,sequential",
                     help="--mode batch: the legs to run (a single leg with --batch-once runs one solve, no warm-up)")
     ap.add_argument("--batch-once", action="store_true", help="--mode batch: one solve per leg, no warm-up (profiling)")
+    ap.add_argument("--batch-tile-rows", type=int, default=0,
+                    help="--mode batch: rows per CTA of the fixed-point batch kernel (0: autotuned; 128 or 256)")
     ap.add_argument("--batch-block-size", type=int, default=0,
                     help="--mode batch: block width of the batch legs (0: autotuned, which timings under a profiler distort)")
     ap.add_argument("--ortho-n", type=int, default=1_000_000, help="rows of the --mode ortho basis")
@@ -401,7 +403,8 @@ def main():
     if args.mode == "batch":
         print(json.dumps({"mode": "batch", **batch_leg(flz, torch, torch.cuda.current_stream(),
                                                         legs=args.batch_legs.split(","), once=args.batch_once,
-                                                        block_size=args.batch_block_size)}))
+                                                        block_size=args.batch_block_size,
+                                                        tile_rows=args.batch_tile_rows)}))
         return
     if args.mode == "table2":
         return table2_mode(flz, torch, prec, args)
@@ -598,7 +601,7 @@ def variant_leg(flz, torch, h, p, alpha, beta, stream, flush, ref_vals, args):
 
 
 def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "fx64_persistent", "sequential"), once=False,
-              block_size=0):
+              block_size=0, tile_rows=0):
     """The batched form against one-at-a-time FP64 solves on the same GPU.
 
     Workload: 64 independent 2D/3D Laplacians with U(0,1) potentials, n
@@ -649,6 +652,7 @@ def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "fx64_pe
         p.tol = tol
         p.check_every = 5
         p.persistent = 1 if name.endswith("persistent") else 0
+        p.tile_rows = tile_rows
         bt = flz.flz_batch_create(hs, alphas, betas, p)
         if not once:
             flz.flz_batch_solve(bt, stream)
@@ -662,6 +666,7 @@ def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "fx64_pe
                      "tol": tol, "counts_match_oracle": ok, "max_rel_eig_err_vs_oracle": err,
                      "block_size": stats[0]["block_size"], "max_iters": max(x["iters"] for x in stats),
                      "filter_precision": PRECISION_NAMES.get(stats[0]["filter_precision"]),
+                     "tile_rows": stats[0]["tile_rows"],
                      "ms_bounds": stats[0]["ms_bounds"], "ms_steps": stats[0]["ms_filter"],
                      "ms_check": stats[0]["ms_check"], "max_checks": max(x["checks"] for x in stats),
                      # rows and stored entries times block steps, summed over the problems (filter traffic)

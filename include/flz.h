@@ -174,6 +174,9 @@ typedef struct flz_params {
                            filter application in one cooperative launch whose CTAs meet at a grid barrier
                            between degrees (bounded: a wait beyond the limit of flz_set_wait_limit ends
                            the solve with FLZ_ERR_TIMEOUT). Other solves ignore it. */
+  int32_t tile_rows;    /* batches with the fixed-point filter: rows per CTA of the degree step, 128 or
+                           256; 0 (default) times both at the batch handle's first flz_batch_solve and
+                           keeps the faster. Other solves ignore it. */
 } flz_params;
 
 /* One convergence check of a solve (Section 3.2.2's periodic Rayleigh-Ritz
@@ -220,6 +223,8 @@ typedef struct flz_stats {
   int64_t sweep_matvecs;    /* products of A with a vector in the subspace sweeps (columns x degree) */
   int32_t start_used;       /* 0: random start block; 1: Krylov start from the start vectors;
                                2: the subspace start converged (no block Lanczos steps) */
+  int32_t tile_rows;        /* batches with the fixed-point filter: rows per CTA of its degree step
+                               (128 or 256); 0 otherwise */
 } flz_stats;
 
 /* ---- status and parameters ------------------------------------------------ */
@@ -487,13 +492,18 @@ flz_status flz_get_checks(const flz_solver* s, flz_check* out, int64_t cap, int6
  * matrix per call): problem i is all eigenpairs of mats[i] in
  * [alphas[i], betas[i]] (A's units). Every matrix must outlive the batch.
  * params (NULL = defaults) apply to all problems; block_size = 0 picks r in
- * {4, 8, 16} by timing the filter kernel at each width (autotuning). The
+ * {4, 8, 16} by timing the filter kernel at each width, and tile_rows = 0
+ * picks the fixed-point filter's rows per CTA (autotuning; done at the
+ * handle's first flz_batch_solve and reused by its later solves). The
  * problems are concatenated into one block-diagonal device matrix and run in
  * lockstep: each kernel of a block Lanczos step serves every problem at once,
  * with per-problem bounds, filter degree and coefficients, and per-problem
- * (segmented) reorthogonalization, block QR and convergence. One whole block
- * step is captured once as a CUDA graph and replayed. Problems stop when they
- * converge. Host arrays alphas/betas have `count` entries. */
+ * (segmented) block QR and convergence; the reorthogonalization runs per
+ * problem on the tensor cores (params.ortho AUTO or TENSOR) or segmented on
+ * the CUDA cores. The kernels of a block step are captured as CUDA graphs and
+ * replayed (params.persistent: the fixed-point filter as one cooperative
+ * launch instead). Problems stop when they converge. Host arrays
+ * alphas/betas have `count` entries. */
 flz_status flz_batch_create(int32_t count, flz_matrix* const* mats, const double* alphas, const double* betas,
                             const flz_params* params, flz_batch** out);
 flz_status flz_batch_destroy(flz_batch* b);

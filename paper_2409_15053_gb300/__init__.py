@@ -64,6 +64,7 @@ class flz_params(ctypes.Structure):
         ("refine", ctypes.c_int32),
         ("start_mode", ctypes.c_int32),
         ("persistent", ctypes.c_int32),
+        ("tile_rows", ctypes.c_int32),
     ]
 
 
@@ -78,7 +79,7 @@ class flz_stats(ctypes.Structure):
         ("ms_total", ctypes.c_double), ("basis_vectors", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64), ("ortho", ctypes.c_int32), ("filter_precision", ctypes.c_int32),
         ("refine_sweeps", ctypes.c_int32), ("refine_degree", ctypes.c_int32), ("ms_refine", ctypes.c_double),
-        ("sweep_matvecs", ctypes.c_int64), ("start_used", ctypes.c_int32),
+        ("sweep_matvecs", ctypes.c_int64), ("start_used", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -560,7 +560,7 @@ flz_status flz_solver_create(flz_matrix* A, const flz_params* params, flz_solver
       (p.recurrence != FLZ_REC_FORWARD && p.recurrence != FLZ_REC_CLENSHAW) || p.ortho < FLZ_ORTHO_AUTO ||
       p.ortho > FLZ_ORTHO_TENSOR || p.refine < 0 || p.refine > 1 ||
       (p.start_mode != FLZ_START_KRYLOV && p.start_mode != FLZ_START_SUBSPACE) || p.persistent < 0 ||
-      p.persistent > 1)
+      p.persistent > 1 || (p.tile_rows != 0 && p.tile_rows != 128 && p.tile_rows != 256))
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.ortho == FLZ_ORTHO_TENSOR && (!flz::TcBasis::supported(p.block_size) || p.precision == FLZ_PREC_DF64))
     fail(FLZ_ERR_INVALID_ARG, "tensor-core reorthogonalization needs an FP64 basis (not the double-FP32 precision)");

@@ -45,6 +45,7 @@ struct flz_batch {
   std::vector<flz_stats> stats;
   int32_t max_row_nnz = 0;  // longest row of any problem
   flz::FxBatch fxb;         // the fixed-point filter's layout and tables
+  int tuned_r = 0, tuned_rows = 0;  // the autotuner's choices, kept for the handle's later solves
 };
 
 namespace flz {
@@ -1344,6 +1345,7 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
     B->stats[i].ms_check = ms_check;
     B->stats[i].ms_total = total;
     B->stats[i].kernel_launches = g_kernel_launches - launches0;
+    B->stats[i].tile_rows = E.precision == FLZ_PREC_FX64 ? B->fxb.rows : 0;
   }
   B->solved = true;
 }
@@ -1351,6 +1353,7 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
 }  // namespace
 
 int batch_autotune(flz_batch* B, cudaStream_t st);
+void tune_rows(flz_batch* B, int r, double t256, cudaStream_t st);
 
 flz_status batch_solve(flz_batch* B, cudaStream_t user) {
   // Work runs on a private non-blocking stream (graphs cannot be captured on
@@ -1370,8 +1373,15 @@ flz_status batch_solve(flz_batch* B, cudaStream_t user) {
   guard.e = ev;
   FLZ_CUDA(cudaEventRecord(ev, user));
   FLZ_CUDA(cudaStreamWaitEvent(st, ev, 0));
+  // tuned on the handle's first solve; later solves reuse the choice
   int r = B->p.block_size;
-  if (r == 0) r = batch_autotune(B, st);
+  if (B->tuned_rows == 0 || (r == 0 && B->tuned_r == 0)) {
+    if (r == 0) B->tuned_r = batch_autotune(B, st);
+    else tune_rows(B, r, 0.0, st);
+    B->tuned_rows = B->fxb.rows;
+  }
+  if (r == 0) r = B->tuned_r;
+  B->fxb.rows = B->tuned_rows;
   B->r = r;
   FLZ_DISPATCH_R(r, batch_solve_r, B, st);
   FLZ_CUDA(cudaStreamSynchronize(st));
@@ -1380,48 +1390,88 @@ flz_status batch_solve(flz_batch* B, cudaStream_t user) {
   return FLZ_OK;
 }
 
-// Picks r in {4, 8, 16}: times one filter degree of the concatenated matrix at
-// each width; a wider block is taken only if it is at least 25 % cheaper per
-// vector than the current choice (a wider block reaches a lower Krylov degree
-// within the same basis capacity, and near-equal timings must not flip the
-// choice from run to run).
-int batch_autotune(flz_batch* B, cudaStream_t st) {
-  double best = 1e300;
-  int best_r = 4;
+// Filter timings of the concatenated matrix at block width r and, for the
+// fixed-point filter, `rows` rows per CTA: the time of a degree-16
+// application minus that of a degree-8 one (each the best of three after a
+// warm-up), i.e. of 8 middle degree steps, the steps that dominate a solve.
+// Returns ms per vector and degree step.
+double time_filter_degree(flz_batch* B, int r, int rows, int degree, cudaStream_t st);
+double time_filter(flz_batch* B, int r, int rows, cudaStream_t st) {
+  const double t16 = time_filter_degree(B, r, rows, 16, st);
+  const double t8 = time_filter_degree(B, r, rows, 8, st);
+  return std::max(t16 - t8, 1e-9) / 8.0;
+}
+double time_filter_degree(flz_batch* B, int r, int rows, int degree, cudaStream_t st) {
   cudaEvent_t e0, e1;
   FLZ_CUDA(cudaEventCreate(&e0));
   FLZ_CUDA(cudaEventCreate(&e1));
-  for (int r : {4, 8, 16}) {
-    BatchEngine E;
-    E.setup(B, r, 2, B->p.precision, st);
-    std::vector<int> act(B->count, 1);
-    E.set_active(act);
-    E.set_filter(std::vector<double>(B->count, 0.0), std::vector<double>(B->count, 1e6),
-                 std::vector<std::vector<double>>(B->count, std::vector<double>{0.0, 0.0, 0.0, 1.0}));
-    FLZ_CUDA(cudaMemsetAsync(E.Q.p, 0, sizeof(double) * B->N * r, st));
-    FLZ_CUDA(cudaMemsetAsync(E.jdev.p, 0, sizeof(int), st));
-    auto run = [&] {
-      switch (r) {
-        case 4: E.apply_filter<4>(); break;
-        case 8: E.apply_filter<8>(); break;
-        default: E.apply_filter<16>(); break;
-      }
-    };
-    run();
+  BatchEngine E;
+  E.setup(B, r, 2, B->p.precision, st);
+  std::vector<int> act(B->count, 1);
+  E.set_active(act);
+  std::vector<double> probe(degree + 1, 0.0);
+  probe[degree] = 1.0;
+  E.set_filter(std::vector<double>(B->count, 0.0), std::vector<double>(B->count, 1e6),
+               std::vector<std::vector<double>>(B->count, probe));
+  B->fxb.rows = rows;
+  FLZ_CUDA(cudaMemsetAsync(E.Q.p, 0, sizeof(double) * B->N * r, st));
+  FLZ_CUDA(cudaMemsetAsync(E.jdev.p, 0, sizeof(int), st));
+  auto run = [&] {
+    switch (r) {
+      case 4: E.apply_filter<4>(); break;
+      case 8: E.apply_filter<8>(); break;
+      default: E.apply_filter<16>(); break;
+    }
+  };
+  run();
+  float best = 1e30f;
+  for (int q = 0; q < 3; ++q) {
     FLZ_CUDA(cudaEventRecord(e0, st));
-    for (int q = 0; q < 3; ++q) run();
+    run();
     FLZ_CUDA(cudaEventRecord(e1, st));
     FLZ_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
     FLZ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    const double per_vec = ms / r;
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best / r;
+}
+
+// The fixed-point filter's tile shape at width r (t256: its time_filter at
+// 256 rows per CTA, if already measured): 128 rows per CTA only if that is at least 5 %
+// faster (near-equal timings must not flip the choice from run to run), else
+// 256. A tile shape the caller fixed is kept.
+void tune_rows(flz_batch* B, int r, double t256, cudaStream_t st) {
+  if (B->p.tile_rows != 0) {
+    B->fxb.rows = B->p.tile_rows;
+    return;
+  }
+  B->fxb.rows = 256;
+  if (B->p.precision != FLZ_PREC_FX64) return;
+  if (t256 <= 0.0) t256 = time_filter(B, r, 256, st);
+  const double t128 = time_filter(B, r, 128, st);
+  B->fxb.rows = t128 < 0.95 * t256 ? 128 : 256;
+}
+
+// Picks r in {4, 8, 16} (at 256 rows per CTA, or the caller's tile shape),
+// then the fixed-point filter's rows per CTA at that r: a wider block is
+// taken only if it is at least 25 % cheaper per vector than the current
+// choice (a wider block reaches a lower Krylov degree within the same basis
+// capacity, and near-equal timings must not flip the choice from run to run).
+int batch_autotune(flz_batch* B, cudaStream_t st) {
+  double best = 1e300;
+  int best_r = 4;
+  const int rows0 = B->p.tile_rows != 0 ? B->p.tile_rows : 256;
+  for (int r : {4, 8, 16}) {
+    const double per_vec = time_filter(B, r, rows0, st);
     if (per_vec < 0.75 * best) {
       best = per_vec;
       best_r = r;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  tune_rows(B, best_r, best, st);
   return best_r;
 }
 
@@ -1446,7 +1496,8 @@ flz_status flz_batch_create(int32_t count, flz_matrix* const* mats, const double
         p.block_size == 16))
     fail(FLZ_ERR_INVALID_ARG, "batch block_size must be 0 (autotune) or one of 1, 2, 4, 8, 16");
   if (p.degree < 0 || p.max_degree < 1 || p.check_every < 1 || !(p.tol > 0.0) || p.bounds_steps < 1 ||
-      p.damping < 0 || p.damping > 2 || !(p.transition >= 0.0) || p.persistent < 0 || p.persistent > 1)
+      p.damping < 0 || p.damping > 2 || !(p.transition >= 0.0) || p.persistent < 0 || p.persistent > 1 ||
+      (p.tile_rows != 0 && p.tile_rows != 128 && p.tile_rows != 256))
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.recurrence != FLZ_REC_FORWARD) fail(FLZ_ERR_INVALID_ARG, "batches use the forward recurrence only");
   if (p.precision < FLZ_PREC_FP64 || p.precision > FLZ_PREC_FX64)

@@ -811,13 +811,15 @@ void fx_check_flag(flz_matrix* A) {
 
 namespace {
 
+constexpr int kTileP0 = 128;  // rows per entry of the starting-problem table
+
 struct FxSegArgs {
   int n, nsl, emax, vec_bulk, count;
   const int* off;         // SELL slice offsets of the concatenation
   const int* scol;
   const uint64_t* sval;   // 2 Ahat_i, offset-binary, units 2^-61
   const int* d_off;       // count + 1 problem row offsets
-  const int* cta_p0;      // problem of each CTA's first row
+  const int* cta_p0;      // problem of the first row of every kTileP0 rows
   const uint64_t* bfix;   // coefficient table: b_k of problem i at k * count + i
   const int* sexp;        // per-problem sum exponent s_i
   const int* zexp;        // 16 zero column exponents (unit columns)
@@ -841,29 +843,31 @@ __device__ __forceinline__ int seg_problem(const int* __restrict__ d_off, int co
   return lo;
 }
 
-template <int R, int U, bool FIRST>
-__global__ void __launch_bounds__(kThreads, R <= 4 ? 4 : (R <= 8 ? 2 : 1)) fx_seg_sell_kernel(FxSegArgs a, int k, const uint64_t* __restrict__ ycur,
-                                                               const uint64_t* yprev, uint64_t* ynext) {
+// ROWS rows (ROWS / 32 SELL slices) per CTA, 128 or 256: a tile shape the
+// batch autotuner times.
+template <int R, int U, bool FIRST, int ROWS>
+__global__ void __launch_bounds__(ROWS, (R <= 4 ? 4 : (R <= 8 ? 2 : 1)) * (256 / ROWS))
+    fx_seg_sell_kernel(FxSegArgs a, int k, const uint64_t* __restrict__ ycur, const uint64_t* yprev, uint64_t* ynext) {
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);         // [0] matrix range, [1] vector rows
   uint64_t* s_own = reinterpret_cast<uint64_t*>(smem + 32);  // V (first step) or Y_{k-1} rows
-  uint64_t* s_sum = s_own + kThreads * R;                    // running-sum rows
-  uint64_t* s_val = s_sum + kThreads * R;
+  uint64_t* s_sum = s_own + ROWS * R;                        // running-sum rows
+  uint64_t* s_val = s_sum + ROWS * R;
   int* s_col = reinterpret_cast<int*>(s_val + a.emax);
-  const int row0 = blockIdx.x * kThreads, rows = min(kThreads, a.n - row0);
+  const int row0 = blockIdx.x * ROWS, rows = min(ROWS, a.n - row0);
   // the row's problem: forward from the CTA's first row's (rows of a CTA
   // span one or a few problems)
   const int t = threadIdx.x, row = row0 + t;
   int pi = 0, md = 0;
   bool active = row < a.n;
   if (active) {
-    pi = __ldg(a.cta_p0 + blockIdx.x);
+    pi = __ldg(a.cta_p0 + blockIdx.x * (ROWS / kTileP0));
     while (pi + 1 < a.count && __ldg(a.d_off + pi + 1) <= row) ++pi;
     md = __ldg(a.mdeg + pi);
     active = __ldg(a.active + pi) && k + 1 <= md;
   }
   if (!__syncthreads_or(active)) return;  // reads nothing the previous degree writes
-  const int sl0 = blockIdx.x * 8, sl1 = min(a.nsl, sl0 + 8);
+  const int sl0 = blockIdx.x * (ROWS / 32), sl1 = min(a.nsl, sl0 + ROWS / 32);
   const int e0 = __ldg(a.off + sl0), e1 = __ldg(a.off + sl1);
   const bool vb = a.vec_bulk && ((rows * R) % 2 == 0);  // uniform over the CTA
   // the running sums are staged on the regular flush steps; a problem whose
@@ -1045,7 +1049,7 @@ __device__ __forceinline__ void seg_tile_plain(const FxSegArgs& a, int k, int ti
   const bool first = k == 0;
   const int row = tile * kThreads + (int)threadIdx.x;
   if (row >= a.n) return;
-  int pi = __ldg(a.cta_p0 + tile);
+  int pi = __ldg(a.cta_p0 + tile * (kThreads / kTileP0));
   while (pi + 1 < a.count && __ldg(a.d_off + pi + 1) <= row) ++pi;
   const int md = __ldg(a.mdeg + pi);
   if (!__ldg(a.active + pi) || k + 1 > md) return;
@@ -1148,38 +1152,46 @@ void run_fx_seg_persistent(FxBatch& F, const FxSegArgs& a, cudaStream_t st) {
   FLZ_LAUNCH_CHECK();
 }
 
-size_t seg_stage_bytes(int R, int64_t emax) { return 32 + 2 * (size_t)kThreads * R * 8 + (size_t)emax * 12; }
+// emax: the most entries of any 8 consecutive slices (256 rows), which bounds
+// those of 4 slices too
+size_t seg_stage_bytes(int R, int64_t emax, int rows = 256) { return 32 + 2 * (size_t)rows * R * 8 + (size_t)emax * 12; }
 
-template <int R, int U, bool FIRST>
+template <int R, int U, bool FIRST, int ROWS>
 void seg_stage_limit(size_t bytes) {
   static size_t done = 0;
   if (bytes > done) {
-    FLZ_CUDA(cudaFuncSetAttribute(fx_seg_sell_kernel<R, U, FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    FLZ_CUDA(cudaFuncSetAttribute(fx_seg_sell_kernel<R, U, FIRST, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)bytes));
     done = bytes;
   }
 }
 
-template <int R, int U>
-void run_fx_seg(FxBatch& F, const FxSegArgs& a, bool pdl, cudaStream_t st) {
-  const unsigned grid = (unsigned)((F.n + kThreads - 1) / kThreads);
-  const size_t smem = seg_stage_bytes(R, F.emax);
-  seg_stage_limit<R, U, true>(smem);
-  seg_stage_limit<R, U, false>(smem);
-  fx_seg_sell_kernel<R, U, true><<<grid, kThreads, smem, st>>>(a, 0, F.y0.p, nullptr, F.ya.p);
+template <int R, int U, int ROWS>
+void run_fx_seg_rows(FxBatch& F, const FxSegArgs& a, bool pdl, cudaStream_t st) {
+  const unsigned grid = (unsigned)((F.n + ROWS - 1) / ROWS);
+  const size_t smem = seg_stage_bytes(R, F.emax, ROWS);
+  seg_stage_limit<R, U, true, ROWS>(smem);
+  seg_stage_limit<R, U, false, ROWS>(smem);
+  fx_seg_sell_kernel<R, U, true, ROWS><<<grid, ROWS, smem, st>>>(a, 0, F.y0.p, nullptr, F.ya.p);
   FLZ_LAUNCH_CHECK();
   const uint64_t* prev = F.y0.p;
   const uint64_t* cur = F.ya.p;
   for (int k = 1; k < F.mmax; ++k) {
     uint64_t* next = (k == 1) ? F.yb.p : const_cast<uint64_t*>(prev);
     if (pdl)
-      launch_dependent(fx_seg_sell_kernel<R, U, false>, grid, kThreads, smem, st, a, k, cur, prev, next);
+      launch_dependent(fx_seg_sell_kernel<R, U, false, ROWS>, grid, ROWS, smem, st, a, k, cur, prev, next);
     else
-      fx_seg_sell_kernel<R, U, false><<<grid, kThreads, smem, st>>>(a, k, cur, prev, next);
+      fx_seg_sell_kernel<R, U, false, ROWS><<<grid, ROWS, smem, st>>>(a, k, cur, prev, next);
     FLZ_LAUNCH_CHECK();
     prev = cur;
     cur = next;
   }
+}
+
+template <int R, int U>
+void run_fx_seg(FxBatch& F, const FxSegArgs& a, bool pdl, cudaStream_t st) {
+  if (F.rows == 128) run_fx_seg_rows<R, U, 128>(F, a, pdl, st);
+  else run_fx_seg_rows<R, U, 256>(F, a, pdl, st);
 }
 
 }  // namespace
@@ -1190,11 +1202,11 @@ bool fx_batch_prepare(FxBatch& F, int64_t N, int64_t nnz, const int* rowptr, con
   if (!fx_supported(r) || max_row_nnz > kLongRow) return false;
   if (!F.layout_built) {
     // the problem of every CTA's first row
-    const int64_t ctas = (N + kThreads - 1) / kThreads;
+    const int64_t ctas = (N + kTileP0 - 1) / kTileP0;
     std::vector<int> p0(ctas);
     int p = 0;
     for (int64_t b = 0; b < ctas; ++b) {
-      while (p + 1 < count && (int64_t)off_host[p + 1] <= b * kThreads) ++p;
+      while (p + 1 < count && (int64_t)off_host[p + 1] <= b * kTileP0) ++p;
       p0[b] = p;
     }
     F.cta_p0.reserve((size_t)ctas);

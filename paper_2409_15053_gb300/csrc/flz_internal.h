@@ -192,6 +192,7 @@ struct FxBatch {
   DevBuf<unsigned> flag, gbar;
   unsigned* flag_host = nullptr;
   int vec_bits = 61, mmax = 0, count = 0;
+  int rows = 256;  // rows per CTA of the degree-step kernel (128 or 256; the batch autotuner's choice)
   double rowsum = 0.0;
   FxBatch() = default;
   FxBatch(const FxBatch&) = delete;

@@ -97,15 +97,19 @@ def test_batch_tensor_core_basis_grows_past_its_first_capacity():
     check(csrs, intervals, out, 1e-10)
 
 
-@pytest.mark.parametrize("r,m", [(4, 40), (4, 41), (4, 42), (8, 40), (16, 40)])
-def test_batch_fixed_point_filter_matches_dense(r, m):
+@pytest.mark.parametrize("r,m,rows", [(4, 40, 256), (4, 41, 128), (4, 42, 256), (8, 40, 128), (16, 40, 256),
+                                      (16, 41, 128)])
+def test_batch_fixed_point_filter_matches_dense(r, m, rows):
     # the 64-bit fixed-point filter over the concatenation: per-problem maps,
     # coefficient tables and sum scalings in one kernel per degree; degrees
-    # 40, 41, 42 end with 3, 1 and 2 running-sum terms added at the last step
+    # 40, 41, 42 end with 3, 1 and 2 running-sum terms added at the last
+    # step; both tile shapes (128 and 256 rows per CTA)
     csrs, intervals = small_batch(3, 6)
-    st, out = run_batch(csrs, intervals, block_size=r, degree=m, check_every=5, precision=flz.FLZ_PREC_FX64)
+    st, out = run_batch(csrs, intervals, block_size=r, degree=m, check_every=5, precision=flz.FLZ_PREC_FX64,
+                        tile_rows=rows)
     assert st == flz.FLZ_OK
     assert all(o["stats"]["filter_precision"] == flz.FLZ_PREC_FX64 for o in out)
+    assert all(o["stats"]["tile_rows"] == rows for o in out)
     check(csrs, intervals, out, 1e-10)
 
 
@@ -164,12 +168,27 @@ def test_batch_double_fp32_filter_matches_dense():
     check(csrs, intervals, out, 1e-10)
 
 
-def test_batch_autotuned_block_width_and_auto_degree():
+@pytest.mark.parametrize("precision", [flz.FLZ_PREC_FP64, flz.FLZ_PREC_FX64], ids=["fp64", "fx64"])
+def test_batch_autotuned_block_width_and_auto_degree(precision):
+    # the autotuner picks r (and, for the fixed-point filter, 128 or 256 rows per CTA)
     csrs, intervals = small_batch(5, 4)
-    st, out = run_batch(csrs, intervals, block_size=0, degree=0, check_every=5)
+    st, out = run_batch(csrs, intervals, block_size=0, degree=0, check_every=5, precision=precision)
     assert st == flz.FLZ_OK
     assert all(o["stats"]["block_size"] in (4, 8, 16) for o in out)
+    want_rows = (128, 256) if precision == flz.FLZ_PREC_FX64 else (0,)
+    assert all(o["stats"]["tile_rows"] in want_rows for o in out)
     check(csrs, intervals, out, 1e-10)
+
+
+def test_batch_rejects_a_tile_shape_it_has_no_kernel_for():
+    c = laplacian_2d(10, 10)
+    h = flz.flz_matrix_create_csr(c.n, c.nnz, c.rowptr, c.col, c.val)
+    p = flz.flz_params_default()
+    p.tile_rows = 192
+    with pytest.raises(flz.FlzError) as e:
+        flz.flz_batch_create([h], [0.0], [1.0], p)
+    assert e.value.status == flz.FLZ_ERR_INVALID_ARG
+    flz.flz_matrix_destroy(h)
 
 
 def test_batch_of_one_matches_single_solver():
