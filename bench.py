@@ -360,7 +360,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32/BF16-filter solves reported under 'variants'")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch-of-64 leg")
-    ap.add_argument("--batch-legs", default="fp32,fp64,df64,fx64,fx64_persistent,sequential",
+    ap.add_argument("--batch-legs", default="fp32,fp64,df64,fx64,fx64_persistent,fp32_refined,sequential",
                     help="--mode batch: the legs to run (a single leg with --batch-once runs one solve, no warm-up)")
     ap.add_argument("--batch-once", action="store_true", help="--mode batch: one solve per leg, no warm-up (profiling)")
     ap.add_argument("--batch-tile-rows", type=int, default=0,
@@ -600,7 +600,8 @@ def variant_leg(flz, torch, h, p, alpha, beta, stream, flush, ref_vals, args):
     return out
 
 
-def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "fx64_persistent", "sequential"), once=False,
+def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "fx64_persistent", "fp32_refined", "sequential"),
+              once=False,
               block_size=0, tile_rows=0):
     """The batched form against one-at-a-time FP64 solves on the same GPU.
 
@@ -642,7 +643,8 @@ def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "fx64_pe
     out = {"problems": len(items), "sum_n": int(sum(c.n for c, _, _ in items)), "eigenpairs": total}
     for name, prec, tol in (("batch_fp32", flz.FLZ_PREC_FP32, 1e-6), ("batch_fp64", flz.FLZ_PREC_FP64, 1e-10),
                             ("batch_df64", flz.FLZ_PREC_DF64, 1e-10), ("batch_fx64", flz.FLZ_PREC_FX64, 1e-10),
-                            ("batch_fx64_persistent", flz.FLZ_PREC_FX64, 1e-10)):
+                            ("batch_fx64_persistent", flz.FLZ_PREC_FX64, 1e-10),
+                            ("batch_fp32_refined", flz.FLZ_PREC_FP32, 1e-8)):
         if name[6:] not in legs:
             continue
         p = flz.flz_params_default()
@@ -652,6 +654,7 @@ def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "fx64_pe
         p.tol = tol
         p.check_every = 5
         p.persistent = 1 if name.endswith("persistent") else 0
+        p.refine = 1 if name.endswith("refined") else 0
         p.tile_rows = tile_rows
         bt = flz.flz_batch_create(hs, alphas, betas, p)
         if not once:
@@ -666,6 +669,7 @@ def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "fx64_pe
                      "tol": tol, "counts_match_oracle": ok, "max_rel_eig_err_vs_oracle": err,
                      "block_size": stats[0]["block_size"], "max_iters": max(x["iters"] for x in stats),
                      "filter_precision": PRECISION_NAMES.get(stats[0]["filter_precision"]),
+                     "refine_ms_sum": sum(x["ms_refine"] for x in stats),
                      "tile_rows": stats[0]["tile_rows"],
                      "ms_bounds": stats[0]["ms_bounds"], "ms_steps": stats[0]["ms_filter"],
                      "ms_check": stats[0]["ms_check"], "max_checks": max(x["checks"] for x in stats),

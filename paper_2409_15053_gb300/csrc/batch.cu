@@ -950,6 +950,76 @@ cudaGraphExec_t capture_part(BatchEngine& E, F part) {
   }
 }
 
+// The mixed-precision batch: each converged problem's pairs (FP32 / BF16
+// filter quality) are refined to params.tol by filtered subspace iteration
+// with the fixed-point filter on its own matrix and Rayleigh-Ritz on A (the
+// single solve's refinement), one problem after another. The block is the
+// found eigenvectors plus guard and extra random columns (the extras are
+// filtered with the problem's filter at half degree in the first sweep).
+void refine_problems(flz_batch* B, const std::vector<std::vector<double>>& coeffs, const std::vector<int>& converged,
+                     int guard, cudaStream_t st) {
+  const flz_params& p = B->p;
+  for (int i = 0; i < B->count; ++i) {
+    flz_stats& s = B->stats[i];
+    const int64_t f = s.count;
+    const int64_t n_i = B->off[i + 1] - B->off[i];
+    if (!converged[i] || f == 0) continue;
+    int kp = (int)(f + guard + std::max<int64_t>(16, f / 3));
+    kp = (kp + 15) / 16 * 16;
+    if ((int64_t)kp * 4 > n_i) continue;  // too small a problem for a subspace block: its phase result stands
+    DevBuf<double> Xr;
+    Xr.reserve((size_t)n_i * kp);
+    random_normal(Xr.p, n_i * kp, p.seed ^ (0x51ull + (uint64_t)i), 0, st);
+    columns_to_blocks(B->evecs[i]->p, n_i, n_i, (int)f, Xr.p, st);
+    const int m = s.degree;
+    std::vector<double> half;
+    if (m >= 8) {
+      half.resize(m / 2 + 1);
+      filter_coeffs_for(p, s.alpha_mapped, s.beta_mapped, m / 2, half.data());
+    }
+    RefineArgs ra{B->alpha[i], B->beta[i], s.lmin, s.lmax, p.tol, p.precision == FLZ_PREC_FP32 ? 16 : 24,
+                  std::max(m, 64), coeffs[i], half, (int)f};
+    ra.flat_first = true;
+    const RefineResult rr = refine(B->mats[i], ra, Xr.p, kp, st);
+    s.refine_sweeps = rr.sweeps;
+    s.refine_degree = rr.degrees.empty() ? 0 : *std::max_element(rr.degrees.begin(), rr.degrees.end());
+    s.ms_refine = rr.ms;
+    s.sweep_matvecs = rr.matvecs;
+    // the refined pairs, ascending, as unit columns
+    const int64_t g = (int64_t)rr.vals.size();
+    std::vector<int> perm(g);
+    for (int q = 0; q < g; ++q) perm[q] = q;
+    std::sort(perm.begin(), perm.end(), [&](int a, int b) { return rr.vals[a] < rr.vals[b]; });
+    std::vector<double> nrm2(kp, 1.0);
+    DevBuf<double> dv, prt;
+    dv.reserve(16);
+    prt.reserve(column_sums_scratch(n_i, 16) + 64);
+    for (int b = 0; b < kp / 16; ++b) {
+      const double* Xb = Xr.p + (size_t)b * n_i * 16;
+      column_sums(Xb, Xb, nullptr, n_i, 16, 16, 0, dv.p, prt.p, st);
+      FLZ_CUDA(cudaMemcpyAsync(nrm2.data() + 16 * b, dv.p, sizeof(double) * 16, cudaMemcpyDeviceToHost, st));
+    }
+    FLZ_CUDA(cudaStreamSynchronize(st));
+    auto& buf = *B->evecs[i];
+    if (buf.count < (size_t)std::max<int64_t>(g, 1) * n_i) buf.reserve((size_t)std::max<int64_t>(g, 1) * n_i);
+    B->evals[i].resize(g);
+    B->resid[i].resize(g);
+    double maxres = 0.0;
+    for (int64_t q = 0; q < g; ++q) {
+      const int col = rr.index[perm[q]];
+      rows_to_columns(Xr.p + (size_t)(col / 16) * n_i * 16 + (col % 16), n_i, 1, 16, buf.p + (size_t)q * n_i, n_i, st,
+                      1.0 / std::sqrt(std::max(nrm2[col], 1e-300)));
+      B->evals[i][q] = rr.vals[perm[q]];
+      B->resid[i][q] = rr.res[perm[q]];
+      maxres = std::max(maxres, rr.res[perm[q]]);
+    }
+    FLZ_CUDA(cudaStreamSynchronize(st));
+    s.count = g;
+    s.max_residual = maxres;
+    s.converged = rr.converged ? 1 : 0;
+  }
+}
+
 template <int R>
 void batch_solve_r(flz_batch* B, cudaStream_t st) {
   const int count = B->count;
@@ -1072,6 +1142,10 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
   }
 
   const int guard = p.guard > 0 ? p.guard : std::max(R, 3);
+  // With refinement (reduced-precision filter) the lockstep phase stops at the
+  // filter's floor and each problem's pairs are then refined to p.tol.
+  const bool refining = p.refine == 1 && (E.precision == FLZ_PREC_FP32 || E.precision == FLZ_PREC_BF16);
+  const double tol = refining ? std::max(p.tol, E.precision == FLZ_PREC_FP32 ? 1e-5 : 1e-2) : p.tol;
   std::vector<int64_t> prev_count(count, -1);
   std::vector<int> gate_len(count, 16), iters(count, 0), checks(count, 0);
   std::vector<int> converged(count, 0);
@@ -1153,7 +1227,7 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
       const double anorm = std::max(std::fabs(B->stats[i].lmin), std::fabs(B->stats[i].lmax));
       const bool fp64_class = E.precision == FLZ_PREC_FP64 || E.precision == FLZ_PREC_FX64;
       const double p_gate = std::min(fp64_class ? 1e-2 : 1e-1,
-                                     10.0 * 1.1 * (double)m * m * p.tol * anorm / B->stats[i].e);
+                                     10.0 * 1.1 * (double)m * m * tol * anorm / B->stats[i].e);
       const int g_cnt = std::min(gate_len[i], K);
       const double* S = &Sh[((size_t)i * nbmax + k - 1) * R * R];
       for (int g0 = 0; g0 < g_cnt && w.all_small; g0 += 8) {
@@ -1245,7 +1319,7 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
           const double xx = hs[(size_t)i * 16 + t];
           const double l = hl[(size_t)i * 16 + t];
           const double res = std::sqrt(std::max(hr[(size_t)i * 16 + t], 0.0) / std::max(xx, 1e-300)) / anorm;
-          if (!(res <= p.tol)) {
+          if (!(res <= tol)) {
             w.all_small = false;
             w.done = true;
             break;
@@ -1339,6 +1413,7 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
     }
   }
   FLZ_CUDA(cudaStreamSynchronize(st));
+  if (refining) refine_problems(B, coeffs, converged, guard, st);
   const double total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   for (int i = 0; i < count; ++i) {
     B->stats[i].ms_filter = ms_steps;  // the lockstep steps (filter + orthogonalization) of the whole batch
@@ -1496,7 +1571,7 @@ flz_status flz_batch_create(int32_t count, flz_matrix* const* mats, const double
         p.block_size == 16))
     fail(FLZ_ERR_INVALID_ARG, "batch block_size must be 0 (autotune) or one of 1, 2, 4, 8, 16");
   if (p.degree < 0 || p.max_degree < 1 || p.check_every < 1 || !(p.tol > 0.0) || p.bounds_steps < 1 ||
-      p.damping < 0 || p.damping > 2 || !(p.transition >= 0.0) || p.persistent < 0 || p.persistent > 1 ||
+      p.damping < 0 || p.damping > 2 || !(p.transition >= 0.0) || p.persistent < 0 || p.persistent > 1 || p.refine < 0 || p.refine > 1 ||
       (p.tile_rows != 0 && p.tile_rows != 128 && p.tile_rows != 256))
     fail(FLZ_ERR_INVALID_ARG, "invalid parameter");
   if (p.recurrence != FLZ_REC_FORWARD) fail(FLZ_ERR_INVALID_ARG, "batches use the forward recurrence only");

@@ -160,6 +160,43 @@ def test_batch_fixed_point_request_falls_back_to_fp64_for_irregular_rows():
     check(csrs, intervals, out, 1e-10)
 
 
+def low_end_batch(seed, count):
+    # windows [w_0 - 1, gap midpoint] at the bottom of each spectrum, as in the
+    # batch benchmark's workload
+    rng = np.random.Generator(np.random.PCG64(seed))
+    csrs, intervals = [], []
+    for i in range(count):
+        s = int(rng.integers(11, 15)) if i % 2 == 0 else int(rng.integers(30, 45))
+        c = laplacian_3d_7pt(s, s, s, rng.random(s ** 3)) if i % 2 == 0 else laplacian_2d(s, s, rng.random(s * s))
+        w = np.linalg.eigvalsh(c.to_dense())
+        csrs.append(c)
+        intervals.append(gap_interval(w, 0, int(rng.integers(10, 25))))
+    return csrs, intervals
+
+
+@pytest.mark.parametrize("precision", [flz.FLZ_PREC_FP32, flz.FLZ_PREC_BF16], ids=["fp32", "bf16"])
+def test_batch_reduced_precision_filter_refined_to_1e8(precision):
+    # the lockstep phase with an FP32 / BF16 filter stops at its floor, then
+    # every problem's pairs are refined to 1e-8 by filtered subspace iteration
+    # with the fixed-point filter and Rayleigh-Ritz on its own matrix
+    csrs, intervals = low_end_batch(3, 6)
+    st, out = run_batch(csrs, intervals, block_size=4, degree=40, check_every=5, precision=precision, refine=1,
+                        tol=1e-8)
+    assert st == flz.FLZ_OK
+    assert all(o["stats"]["refine_sweeps"] >= 1 for o in out)
+    check(csrs, intervals, out, 1e-8)
+
+
+def test_batch_fp32_filter_refined_on_interior_windows():
+    # interior windows: the refinement sweeps with each problem's own (flat) filter
+    csrs, intervals = small_batch(3, 6)
+    st, out = run_batch(csrs, intervals, block_size=4, degree=80, check_every=5, precision=flz.FLZ_PREC_FP32,
+                        refine=1, tol=1e-8)
+    assert st == flz.FLZ_OK
+    assert all(o["stats"]["refine_sweeps"] >= 1 for o in out)
+    check(csrs, intervals, out, 1e-8)
+
+
 def test_batch_double_fp32_filter_matches_dense():
     # the double-FP32 filter (FP32 pipes, FP64-class accuracy) with the batch's FP64 basis
     csrs, intervals = small_batch(11, 5)
@@ -213,9 +250,10 @@ def test_batch_rejects_bad_arguments():
     flz.flz_matrix_destroy(h)
 
 
-@pytest.mark.parametrize("precision,tol", [(flz.FLZ_PREC_FP32, 1e-6), (flz.FLZ_PREC_FP64, 1e-10),
-                                           (flz.FLZ_PREC_FX64, 1e-10)], ids=["fp32", "fp64", "fx64"])
-def test_full_size_batch64_matches_oracle_reference(precision, tol):
+@pytest.mark.parametrize("precision,tol,refine", [(flz.FLZ_PREC_FP32, 1e-6, 0), (flz.FLZ_PREC_FP64, 1e-10, 0),
+                                                  (flz.FLZ_PREC_FX64, 1e-10, 0), (flz.FLZ_PREC_FP32, 1e-8, 1)],
+                         ids=["fp32", "fp64", "fx64", "fp32-refined"])
+def test_full_size_batch64_matches_oracle_reference(precision, tol, refine):
     # 64 problems, n log-uniform in [1e4, 2e5] (sum ~4.7e6), autotuned r,
     # degree 60: the batched launch shape the benchmark times, against the
     # eigenvalues the CPU oracle computed for every problem (tests/golden).
@@ -231,7 +269,8 @@ def test_full_size_batch64_matches_oracle_reference(precision, tol):
     csrs = [c for c, _, _ in items]
     assert [csr_checksum(c) for c in csrs] == [p["matrix_checksum"] for p in ref]
     intervals = [(p["alpha"], p["beta"]) for p in ref]
-    st, out = run_batch(csrs, intervals, block_size=0, degree=60, check_every=5, precision=precision, tol=tol)
+    st, out = run_batch(csrs, intervals, block_size=0, degree=60, check_every=5, precision=precision, tol=tol,
+                        refine=refine)
     assert st == flz.FLZ_OK
     for c, p, o in zip(csrs, ref, out):
         want = np.array(p["eigenvalues"])
