@@ -19,6 +19,8 @@
 #include <cstring>
 #include <memory>
 #include <thread>
+#include <atomic>
+#include <string>
 
 #include "device_common.cuh"
 #include "flz_internal.h"
@@ -953,71 +955,149 @@ cudaGraphExec_t capture_part(BatchEngine& E, F part) {
 // The mixed-precision batch: each converged problem's pairs (FP32 / BF16
 // filter quality) are refined to params.tol by filtered subspace iteration
 // with the fixed-point filter on its own matrix and Rayleigh-Ritz on A (the
-// single solve's refinement), one problem after another. The block is the
-// found eigenvectors plus guard and extra random columns (the extras are
-// filtered with the problem's filter at half degree in the first sweep).
-void refine_problems(flz_batch* B, const std::vector<std::vector<double>>& coeffs, const std::vector<int>& converged,
-                     int guard, cudaStream_t st) {
+// single solve's refinement). The block is the found eigenvectors plus guard
+// and extra random columns (the extras are filtered with the problem's
+// filter at half degree in the first sweep). The problems are small and a
+// refinement is a few hundred small launches with host synchronizations, so
+// up to eight host threads run them, each on its own stream with its own
+// workspace sized for the largest problem beforehand (nothing is allocated
+// or freed per problem: cudaFree would synchronize the whole device).
+struct RefineSlot {
+  cudaStream_t st = nullptr;
+  RefineWorkspace ws;
+  DevBuf<double> X, dv, prt;
+  std::vector<double> nrm2;
+  ~RefineSlot() {
+    if (st) cudaStreamSynchronize(st), cudaStreamDestroy(st);
+  }
+};
+
+int refine_block_width(int64_t f, int guard) {
+  const int kp = (int)(f + guard + std::max<int64_t>(16, f / 3));
+  return (kp + 15) / 16 * 16;
+}
+
+void refine_one(flz_batch* B, int i, const std::vector<double>& coeffs, int guard, RefineSlot& slot) {
   const flz_params& p = B->p;
+  cudaStream_t st = slot.st;
+  flz_stats& s = B->stats[i];
+  const int64_t f = s.count;
+  const int64_t n_i = B->off[i + 1] - B->off[i];
+  const int kp = refine_block_width(f, guard);
+  double* Xr = slot.X.p;
+  random_normal(Xr, n_i * kp, p.seed ^ (0x51ull + (uint64_t)i), 0, st);
+  columns_to_blocks(B->evecs[i]->p, n_i, n_i, (int)f, Xr, st);
+  const int m = s.degree;
+  std::vector<double> half;
+  if (m >= 8) {
+    half.resize(m / 2 + 1);
+    filter_coeffs_for(p, s.alpha_mapped, s.beta_mapped, m / 2, half.data());
+  }
+  RefineArgs ra{B->alpha[i], B->beta[i], s.lmin, s.lmax, p.tol, p.precision == FLZ_PREC_FP32 ? 16 : 24,
+                std::max(m, 64), coeffs, half, (int)f};
+  ra.flat_first = true;
+  const RefineResult rr = refine(B->mats[i], ra, Xr, kp, st, &slot.ws);
+  s.refine_sweeps = rr.sweeps;
+  s.refine_degree = rr.degrees.empty() ? 0 : *std::max_element(rr.degrees.begin(), rr.degrees.end());
+  s.ms_refine = rr.ms;
+  s.sweep_matvecs = rr.matvecs;
+  // the refined pairs, ascending, as unit columns
+  const int64_t g = (int64_t)rr.vals.size();
+  std::vector<int> perm(g);
+  for (int q = 0; q < g; ++q) perm[q] = q;
+  std::sort(perm.begin(), perm.end(), [&](int a, int b) { return rr.vals[a] < rr.vals[b]; });
+  slot.nrm2.assign(kp, 1.0);
+  for (int b = 0; b < kp / 16; ++b) {
+    const double* Xb = Xr + (size_t)b * n_i * 16;
+    column_sums(Xb, Xb, nullptr, n_i, 16, 16, 0, slot.dv.p, slot.prt.p, st);
+    FLZ_CUDA(cudaMemcpyAsync(slot.nrm2.data() + 16 * b, slot.dv.p, sizeof(double) * 16, cudaMemcpyDeviceToHost, st));
+  }
+  FLZ_CUDA(cudaStreamSynchronize(st));
+  auto& buf = *B->evecs[i];
+  if (buf.count < (size_t)std::max<int64_t>(g, 1) * n_i) buf.reserve((size_t)std::max<int64_t>(g, 1) * n_i);
+  B->evals[i].resize(g);
+  B->resid[i].resize(g);
+  double maxres = 0.0;
+  for (int64_t q = 0; q < g; ++q) {
+    const int col = rr.index[perm[q]];
+    rows_to_columns(Xr + (size_t)(col / 16) * n_i * 16 + (col % 16), n_i, 1, 16, buf.p + (size_t)q * n_i, n_i, st,
+                    1.0 / std::sqrt(std::max(slot.nrm2[col], 1e-300)));
+    B->evals[i][q] = rr.vals[perm[q]];
+    B->resid[i][q] = rr.res[perm[q]];
+    maxres = std::max(maxres, rr.res[perm[q]]);
+  }
+  FLZ_CUDA(cudaStreamSynchronize(st));
+  s.count = g;
+  s.max_residual = maxres;
+  s.converged = rr.converged ? 1 : 0;
+}
+
+void refine_problems(flz_batch* B, const std::vector<std::vector<double>>& coeffs, const std::vector<int>& converged,
+                     int guard) {
+  // the problems to refine, largest first (each thread's first is its largest)
+  std::vector<int> todo;
+  int64_t n_max = 0;
+  int kp_max = 16;
   for (int i = 0; i < B->count; ++i) {
-    flz_stats& s = B->stats[i];
-    const int64_t f = s.count;
+    const int64_t f = B->stats[i].count;
     const int64_t n_i = B->off[i + 1] - B->off[i];
     if (!converged[i] || f == 0) continue;
-    int kp = (int)(f + guard + std::max<int64_t>(16, f / 3));
-    kp = (kp + 15) / 16 * 16;
+    const int kp = refine_block_width(f, guard);
     if ((int64_t)kp * 4 > n_i) continue;  // too small a problem for a subspace block: its phase result stands
-    DevBuf<double> Xr;
-    Xr.reserve((size_t)n_i * kp);
-    random_normal(Xr.p, n_i * kp, p.seed ^ (0x51ull + (uint64_t)i), 0, st);
-    columns_to_blocks(B->evecs[i]->p, n_i, n_i, (int)f, Xr.p, st);
-    const int m = s.degree;
-    std::vector<double> half;
-    if (m >= 8) {
-      half.resize(m / 2 + 1);
-      filter_coeffs_for(p, s.alpha_mapped, s.beta_mapped, m / 2, half.data());
-    }
-    RefineArgs ra{B->alpha[i], B->beta[i], s.lmin, s.lmax, p.tol, p.precision == FLZ_PREC_FP32 ? 16 : 24,
-                  std::max(m, 64), coeffs[i], half, (int)f};
-    ra.flat_first = true;
-    const RefineResult rr = refine(B->mats[i], ra, Xr.p, kp, st);
-    s.refine_sweeps = rr.sweeps;
-    s.refine_degree = rr.degrees.empty() ? 0 : *std::max_element(rr.degrees.begin(), rr.degrees.end());
-    s.ms_refine = rr.ms;
-    s.sweep_matvecs = rr.matvecs;
-    // the refined pairs, ascending, as unit columns
-    const int64_t g = (int64_t)rr.vals.size();
-    std::vector<int> perm(g);
-    for (int q = 0; q < g; ++q) perm[q] = q;
-    std::sort(perm.begin(), perm.end(), [&](int a, int b) { return rr.vals[a] < rr.vals[b]; });
-    std::vector<double> nrm2(kp, 1.0);
-    DevBuf<double> dv, prt;
-    dv.reserve(16);
-    prt.reserve(column_sums_scratch(n_i, 16) + 64);
-    for (int b = 0; b < kp / 16; ++b) {
-      const double* Xb = Xr.p + (size_t)b * n_i * 16;
-      column_sums(Xb, Xb, nullptr, n_i, 16, 16, 0, dv.p, prt.p, st);
-      FLZ_CUDA(cudaMemcpyAsync(nrm2.data() + 16 * b, dv.p, sizeof(double) * 16, cudaMemcpyDeviceToHost, st));
-    }
-    FLZ_CUDA(cudaStreamSynchronize(st));
-    auto& buf = *B->evecs[i];
-    if (buf.count < (size_t)std::max<int64_t>(g, 1) * n_i) buf.reserve((size_t)std::max<int64_t>(g, 1) * n_i);
-    B->evals[i].resize(g);
-    B->resid[i].resize(g);
-    double maxres = 0.0;
-    for (int64_t q = 0; q < g; ++q) {
-      const int col = rr.index[perm[q]];
-      rows_to_columns(Xr.p + (size_t)(col / 16) * n_i * 16 + (col % 16), n_i, 1, 16, buf.p + (size_t)q * n_i, n_i, st,
-                      1.0 / std::sqrt(std::max(nrm2[col], 1e-300)));
-      B->evals[i][q] = rr.vals[perm[q]];
-      B->resid[i][q] = rr.res[perm[q]];
-      maxres = std::max(maxres, rr.res[perm[q]]);
-    }
-    FLZ_CUDA(cudaStreamSynchronize(st));
-    s.count = g;
-    s.max_residual = maxres;
-    s.converged = rr.converged ? 1 : 0;
+    todo.push_back(i);
+    n_max = std::max(n_max, n_i);
+    kp_max = std::max(kp_max, kp);
   }
+  if (todo.empty()) return;
+  std::sort(todo.begin(), todo.end(), [&](int a, int b) { return B->off[a + 1] - B->off[a] > B->off[b + 1] - B->off[b]; });
+  const int threads = (int)std::min<size_t>(8, todo.size());
+  std::vector<std::unique_ptr<RefineSlot>> slots;
+  for (int t = 0; t < threads; ++t) {
+    slots.emplace_back(new RefineSlot());
+    RefineSlot& sl = *slots.back();
+    FLZ_CUDA(cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking));
+    sl.X.reserve((size_t)n_max * kp_max);
+    sl.dv.reserve(16);
+    sl.prt.reserve(column_sums_scratch(n_max, 16) + 64);
+    RefineWorkspace& w = sl.ws;
+    w.Y.reserve((size_t)n_max * kp_max);
+    w.AY.reserve((size_t)n_max * kp_max);
+    w.S4.reserve((size_t)n_max * 4);
+    w.T4.reserve((size_t)n_max * 4);
+    w.dev.reserve(64);
+    w.part.reserve(column_sums_scratch(n_max, 16) + 64);
+    w.Vd.reserve((size_t)kp_max * kp_max);
+    w.Md.reserve((size_t)kp_max * kp_max);
+    w.Hd.reserve((size_t)kp_max * kp_max);
+    w.tb.reserve(n_max, kp_max);
+    w.tb.wd.reserve((size_t)w.tb.n_pad * 128 * 2);  // W's digits at the widest projection
+  }
+  // the first (largest) problem on this thread: every kernel's one-time
+  // attribute set-up happens before the threads start
+  refine_one(B, todo[0], coeffs[todo[0]], guard, *slots[0]);
+  std::atomic<size_t> next{1};
+  std::vector<flz_status> status(threads, FLZ_OK);
+  std::vector<std::string> message(threads);
+  std::vector<int64_t> launches(threads, 0);
+  std::vector<std::thread> pool;
+  for (int t = 0; t < threads; ++t)
+    pool.emplace_back([&, t] {
+      const int64_t l0 = g_kernel_launches;
+      try {
+        for (size_t q = next++; q < todo.size(); q = next++) refine_one(B, todo[q], coeffs[todo[q]], guard, *slots[t]);
+      } catch (const Failure& f) {
+        status[t] = f.status;
+        message[t] = flz_last_error();
+      } catch (...) {
+        status[t] = FLZ_ERR_CUDA;
+        message[t] = "refinement thread failed";
+      }
+      launches[t] = g_kernel_launches - l0;
+    });
+  for (auto& th : pool) th.join();
+  for (int t = 0; t < threads; ++t) g_kernel_launches += launches[t];
+  for (int t = 0; t < threads; ++t)
+    if (status[t] != FLZ_OK) fail(status[t], "%s", message[t].c_str());
 }
 
 template <int R>
@@ -1413,7 +1493,7 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
     }
   }
   FLZ_CUDA(cudaStreamSynchronize(st));
-  if (refining) refine_problems(B, coeffs, converged, guard, st);
+  if (refining) refine_problems(B, coeffs, converged, guard);
   const double total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   for (int i = 0; i < count; ++i) {
     B->stats[i].ms_filter = ms_steps;  // the lockstep steps (filter + orthogonalization) of the whole batch

@@ -136,6 +136,9 @@ struct TcBasis {
   void reserve(int64_t n, int64_t kcap);
   // room for kcap columns, keeping the digits written so far (at least doubles the capacity)
   void grow(int64_t kcap, cudaStream_t st);
+  // an empty digit basis of n rows and kcap columns in the allocation already
+  // held when it is large enough (zeroed on st), else a new one
+  void reshape(int64_t n, int64_t kcap, cudaStream_t st);
   // rounds X (n x r, row-major) to the 2^-62 grid in place; its digits become columns col0..col0+r-1
   void append(double* X, int r, int col0, cudaStream_t st);
   // out[j] = largest |W[i, j]| (as the upper word of the FP64 bits), j < r
@@ -361,8 +364,16 @@ struct RefineResult {
   int outside = 0;                 // Ritz values of the final block outside [alpha, beta]
   double ms = 0.0;
 };
+// Device buffers of a refinement, kept across calls so that a caller refining
+// many problems (one per host thread and stream) allocates and frees nothing
+// per problem (cudaFree synchronizes the whole device).
+struct RefineWorkspace {
+  DevBuf<double> Y, AY, Vd, dev, part, S4, T4, Md, Hd;
+  TcBasis tb;
+};
 // X: n x kp (kp a multiple of 16) as blocks of 16 columns, row-major; refined in place.
-RefineResult refine(flz_matrix* A, const RefineArgs& g, double* X, int kp, cudaStream_t st);
+RefineResult refine(flz_matrix* A, const RefineArgs& g, double* X, int kp, cudaStream_t st,
+                    RefineWorkspace* ws = nullptr);
 // Chebyshev coefficients of T_d(a z + b) / T_d(-a + b), [zc, 1] mapped onto [-1, 1] by z -> a z + b.
 void damping_coefficients(double zc, int d, double* out);
 // ---- probe.cu ----------------------------------------------------------------------

@@ -99,11 +99,13 @@ inline double outside_by(double mu, double alpha, double beta) {
 
 }  // namespace
 
-RefineResult refine(flz_matrix* A, const RefineArgs& g, double* X, int kp, cudaStream_t st) {
+RefineResult refine(flz_matrix* A, const RefineArgs& g, double* X, int kp, cudaStream_t st, RefineWorkspace* ws) {
   const auto t0 = Clock::now();
   const int64_t n = A->n;
   RefineResult out;
-  DevBuf<double> Y, AY, Vd, dev, part, S4, T4;
+  RefineWorkspace local;
+  RefineWorkspace& w = ws ? *ws : local;
+  DevBuf<double>&Y = w.Y, &AY = w.AY, &Vd = w.Vd, &dev = w.dev, &part = w.part, &S4 = w.S4, &T4 = w.T4;
   S4.reserve((size_t)n * 4);
   T4.reserve((size_t)n * 4);
   Y.reserve((size_t)n * kp);
@@ -212,11 +214,11 @@ RefineResult refine(flz_matrix* A, const RefineArgs& g, double* X, int kp, cudaS
       }
     out.filter_precision = A->last_filter_precision;
     // ---- Rayleigh-Ritz on A in the span of Y ----
-    TcBasis tb;
-    tb.reserve(n, kp);
+    TcBasis& tb = w.tb;
+    tb.reshape(n, kp, st);
     for (int b = 0; b < kp / 16; ++b) tb.append(Y.p + (size_t)b * n * 16, 16, 16 * b, st);  // rounds Y to the grid
     Vd.reserve((size_t)kp * kp);
-    DevBuf<double> Md, Hd;
+    DevBuf<double>&Md = w.Md, &Hd = w.Hd;
     Md.reserve((size_t)kp * kp);
     Hd.reserve((size_t)kp * kp);
     for (int b = 0; b < kp / 16; ++b) {

@@ -852,6 +852,23 @@ void TcBasis::grow(int64_t kcap, cudaStream_t st) {
   groups_cap = ng;
 }
 
+void TcBasis::reshape(int64_t n_, int64_t kcap, cudaStream_t st) {
+  const int64_t n_pad_ = (n_ + kRange - 1) / kRange * kRange;
+  const int groups = (int)((kcap + 15) / 16);
+  const size_t bytes = (size_t)groups * 16 * (size_t)n_pad_ * 16;
+  if (!q.p || q.count < bytes || acc.count < (size_t)groups * 128 * 128 ||
+      hs.count < (size_t)groups * 64 * 16 + 64 || !status.p) {
+    release();
+    reserve(n_, kcap);
+    return;
+  }
+  n = n_;
+  n_pad = n_pad_;
+  n_oct = n_pad / 8;
+  groups_cap = groups;
+  FLZ_CUDA(cudaMemsetAsync(q.p, 0, bytes, st));  // digits outside the written columns and rows must be zero
+}
+
 void TcBasis::append(double* X, int r, int col0, cudaStream_t st) {
   if (col0 + r > groups_cap * 16) fail(FLZ_ERR_CAPACITY, "digit basis holds %d columns", groups_cap * 16);
   const int64_t work = n_oct * r;
