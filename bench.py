@@ -466,6 +466,7 @@ def main():
         res = flz.flz_get_residuals(s)
         found.append(int(np.sum(res <= 1e-8)))
         stats_list.append(flz.flz_get_stats(s))
+        check_history = flz.flz_get_checks(s)
         assert st == flz.FLZ_OK, flz.flz_status_string(st)
     clocks = sampler.stop()
     total_time, total_pairs = aggregate_ranks(float(np.sum(times)), int(sum(found)), dist, "cuda")
@@ -530,6 +531,9 @@ def main():
                                           "max_residual", "ms_bounds", "ms_filter", "ms_orth", "ms_check",
                                           "ms_total", "basis_vectors", "kernel_launches", "ortho")},
             "ortho": ortho_summary(st, csr.n, args.block_size, hbm),
+            # the timed solve's convergence checks: [block steps, pairs inside, walked, outside, all passed, ended]
+            "check_history": [[c["block_steps"], c["inside"], c["walked"], c["outside"], c["all_small"], c["converged"]]
+                              for c in check_history],
             "found_per_step": found,
         }
         print(json.dumps(line))
