@@ -1251,29 +1251,46 @@ void batch_solve_r(flz_batch* B, cudaStream_t st) {
       if (g) cudaGraphExecDestroy(g);
     }
   } graph_a, graph_b;
-  // the persistent filter is launched directly (one cooperative launch per step)
+  // the persistent filter (one cooperative launch per step) is captured too
+  // where stream capture takes a cooperative launch; otherwise it is launched
+  // directly each step
   E.persistent = p.persistent == 1 && E.precision == FLZ_PREC_FX64;
-  if (use_tc) {
-    if (!E.persistent) graph_a.g = capture_part(E, [&] { E.apply_filter<R>(); });
+  bool direct_filter = false;
+  if (E.persistent) {
+    const int64_t before_a = g_kernel_launches;
+    try {
+      graph_a.g = capture_part(E, [&] { E.apply_filter<R>(); });
+    } catch (const Failure&) {
+      cudaGetLastError();
+      clear_last_error();
+      g_kernel_launches = before_a;  // launches of the abandoned capture
+      graph_a.g = nullptr;
+      direct_filter = true;
+    }
+    graph_b.g = capture_part(E, [&] {
+      if (use_tc) E.step_tail<R>();
+      else E.step_after_filter<R>();
+    });
+  } else if (use_tc) {
+    graph_a.g = capture_part(E, [&] { E.apply_filter<R>(); });
     graph_b.g = capture_part(E, [&] { E.step_tail<R>(); });
-  } else if (E.persistent) {
-    graph_b.g = capture_part(E, [&] { E.step_after_filter<R>(); });
   } else {
     graph_a.g = capture_part(E, [&] { E.step<R>(); });
   }
+  const bool split = use_tc || E.persistent;  // filter and the rest in separate graphs
   const int64_t launches_per_step = g_kernel_launches - before_capture;
   g_kernel_launches = before_capture;  // captured, not launched
   while (k < nbmax) {
     const auto ts = std::chrono::steady_clock::now();
     const int todo = std::min(p.check_every - (k % p.check_every), nbmax - k);
     for (int s = 0; s < todo; ++s) {
-      if (E.persistent) E.apply_filter<R>();
+      if (direct_filter) E.apply_filter<R>();
       else FLZ_CUDA(cudaGraphLaunch(graph_a.g, st));
       if (use_tc) {
         E.tc_orth((k + s + 1) * R, act);  // the basis holds Q_0 .. Q_j, j = k + s
         FLZ_CUDA(cudaGraphLaunch(graph_b.g, st));
         E.tc_append((k + s + 1) * R, act);
-      } else if (E.persistent) {
+      } else if (split) {
         FLZ_CUDA(cudaGraphLaunch(graph_b.g, st));
       }
     }
