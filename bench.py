@@ -363,6 +363,8 @@ def main():
     ap.add_argument("--batch-legs", default="fp32,fp64,df64,fx64,fx64_persistent,fp32_refined,sequential",
                     help="--mode batch: the legs to run (a single leg with --batch-once runs one solve, no warm-up)")
     ap.add_argument("--batch-once", action="store_true", help="--mode batch: one solve per leg, no warm-up (profiling)")
+    ap.add_argument("--batch-check-every", type=int, default=5,
+                    help="--mode batch: block steps between convergence checks of the batch legs")
     ap.add_argument("--batch-tile-rows", type=int, default=0,
                     help="--mode batch: rows per CTA of the fixed-point batch kernel (0: autotuned; 128 or 256)")
     ap.add_argument("--batch-block-size", type=int, default=0,
@@ -404,7 +406,8 @@ def main():
         print(json.dumps({"mode": "batch", **batch_leg(flz, torch, torch.cuda.current_stream(),
                                                         legs=args.batch_legs.split(","), once=args.batch_once,
                                                         block_size=args.batch_block_size,
-                                                        tile_rows=args.batch_tile_rows)}))
+                                                        tile_rows=args.batch_tile_rows,
+                                                        check_every=args.batch_check_every)}))
         return
     if args.mode == "table2":
         return table2_mode(flz, torch, prec, args)
@@ -606,7 +609,7 @@ def variant_leg(flz, torch, h, p, alpha, beta, stream, flush, ref_vals, args):
 
 def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "fx64_persistent", "fp32_refined", "sequential"),
               once=False,
-              block_size=0, tile_rows=0):
+              block_size=0, tile_rows=0, check_every=5):
     """The batched form against one-at-a-time FP64 solves on the same GPU.
 
     Workload: 64 independent 2D/3D Laplacians with U(0,1) potentials, n
@@ -656,7 +659,7 @@ def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "fx64_pe
         p.degree = BATCH_DEGREE
         p.precision = prec
         p.tol = tol
-        p.check_every = 5
+        p.check_every = check_every
         p.persistent = 1 if name.endswith("persistent") else 0
         p.refine = 1 if name.endswith("refined") else 0
         p.tile_rows = tile_rows
@@ -685,7 +688,7 @@ def batch_leg(flz, torch, stream, legs=("fp32", "fp64", "df64", "fx64", "fx64_pe
         p = flz.flz_params_default()
         p.block_size = 4
         p.degree = BATCH_DEGREE
-        p.check_every = 5
+        p.check_every = check_every
         solvers = []
         for h, a, z in zip(hs, alphas, betas):
             sv = flz.flz_solver_create(h, p)
