@@ -180,7 +180,76 @@ struct Engine {
 
   // One block Lanczos step j: W = op(Q_j), reorthogonalize, QR into Q_{j+1}.
   // Returns false if the new block could not be formed (no slot).
+  // With the device QR a step splits in two halves: step_issue queues all of
+  // its GPU work (no host wait); step_finish waits for it, takes D_j and S_j
+  // and handles a breakdown. The solver issues the next step before a
+  // convergence check's host work, so the two overlap.
+  bool issued = false;
+  bool can_split() const {
+    if constexpr (std::is_same<T, double>::value) return pinned != nullptr;
+    return false;
+  }
+  void step_issue(int j, const std::function<void(const T*, T*)>& op) {
+    if (!ev[0])
+      for (auto& x : ev) FLZ_CUDA(cudaEventCreate(&x));
+    FLZ_CUDA(cudaEventRecord(ev[0], st));
+    op(block(j), W);
+    FLZ_CUDA(cudaEventRecord(ev[1], st));
+    if constexpr (std::is_same<T, double>::value) {
+      T* next = (j + 1 < nb_cap) ? block(j + 1) : nullptr;
+      cgs2(W, j + 1, nullptr);
+      block_qr_device(W, next ? next : W);
+      if (next) seal(j + 1);
+      const size_t rr = (size_t)r * r, off = (size_t)j * rr;
+      FLZ_CUDA(cudaMemcpyAsync(pinned, C + off, sizeof(double) * rr, cudaMemcpyDeviceToHost, st));
+      FLZ_CUDA(cudaMemcpyAsync(pinned + rr, C2 + off, sizeof(double) * rr, cudaMemcpyDeviceToHost, st));
+      FLZ_CUDA(cudaMemcpyAsync(pinned + 2 * rr, qrs + 256, sizeof(double) * rr, cudaMemcpyDeviceToHost, st));
+    }
+    FLZ_CUDA(cudaEventRecord(ev[2], st));
+    issued = true;
+  }
+  // keep = false: the step's results are not wanted (the solve stopped at the
+  // check it overlapped); it is only waited for and timed
+  void step_finish(int j, Projected& P, double op_norm, bool keep = true) {
+    FLZ_CUDA(cudaEventSynchronize(ev[2]));
+    issued = false;
+    if constexpr (std::is_same<T, double>::value) {
+      if (keep) {
+        T* next = (j + 1 < nb_cap) ? block(j + 1) : nullptr;
+        const size_t rr = (size_t)r * r;
+        std::vector<double> D(rr), S(pinned + 2 * rr, pinned + 3 * rr);
+        for (size_t i = 0; i < rr; ++i) D[i] = pinned[i] + pinned[rr + i];
+        P.D.push_back(D);
+        // breakdown: the new block is (nearly) dependent on the basis; its
+        // directions are rounding noise and must be made orthogonal to the basis.
+        double smin = 1e300;
+        for (int i = 0; i < r; ++i) smin = std::min(smin, std::fabs(S[i * r + i]));
+        if (next && smin < 1e-12 * std::max(op_norm, 1e-300)) {
+          cgs2(next, j + 1, nullptr);
+          block_qr_device(next, next);
+          seal(j + 1);
+          FLZ_CUDA(cudaEventRecord(ev[2], st));
+          FLZ_CUDA(cudaEventSynchronize(ev[2]));
+        }
+        P.S.push_back(S);
+      }
+    }
+    if (tcb) tcb->check_status();
+    if (fx) fx_check_flag(A);
+    float a = 0.f, b = 0.f;
+    FLZ_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
+    FLZ_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
+    ms_op += a;
+    ms_orth += b;
+  }
+
+  // One block Lanczos step j: W = op(Q_j), reorthogonalize, QR into Q_{j+1}.
   void step(int j, const std::function<void(const T*, T*)>& op, Projected& P, double op_norm) {
+    if (can_split()) {
+      step_issue(j, op);
+      step_finish(j, P, op_norm);
+      return;
+    }
     if (!ev[0])
       for (auto& x : ev) FLZ_CUDA(cudaEventCreate(&x));
     FLZ_CUDA(cudaEventRecord(ev[0], st));
@@ -188,46 +257,18 @@ struct Engine {
     FLZ_CUDA(cudaEventRecord(ev[1], st));
     T* next = (j + 1 < nb_cap) ? block(j + 1) : nullptr;
     T* dst = next ? next : W;
-    std::vector<double> D, S;
-    bool device_qr = false;
-    if constexpr (std::is_same<T, double>::value)
-      if (pinned) {
-        // one synchronization per step: CGS2, the device QR, the new block's
-        // digits, then D_j and S_j to the host
-        device_qr = true;
-        cgs2(W, j + 1, nullptr);
-        block_qr_device(W, dst);
-        if (next) seal(j + 1);
-        const size_t rr = (size_t)r * r, off = (size_t)j * rr;
-        FLZ_CUDA(cudaMemcpyAsync(pinned, C + off, sizeof(double) * rr, cudaMemcpyDeviceToHost, st));
-        FLZ_CUDA(cudaMemcpyAsync(pinned + rr, C2 + off, sizeof(double) * rr, cudaMemcpyDeviceToHost, st));
-        FLZ_CUDA(cudaMemcpyAsync(pinned + 2 * rr, qrs + 256, sizeof(double) * rr, cudaMemcpyDeviceToHost, st));
-        FLZ_CUDA(cudaEventRecord(ev[2], st));
-        FLZ_CUDA(cudaEventSynchronize(ev[2]));
-        D.resize(rr);
-        S.assign(pinned + 2 * rr, pinned + 3 * rr);
-        for (size_t i = 0; i < rr; ++i) D[i] = pinned[i] + pinned[rr + i];
-      }
-    if (!device_qr) {
-      cgs2(W, j + 1, &D);
-      S = block_qr(W, dst);
-    }
+    std::vector<double> D;
+    cgs2(W, j + 1, &D);
+    std::vector<double> S = block_qr(W, dst);
     P.D.push_back(D);
-    // breakdown: the new block is (nearly) dependent on the basis; its
-    // directions are rounding noise and must be made orthogonal to the basis.
+    // breakdown (as in step_finish)
     double smin = 1e300;
     for (int i = 0; i < r; ++i) smin = std::min(smin, std::fabs(S[i * r + i]));
-    const bool breakdown = next && smin < 1e-12 * std::max(op_norm, 1e-300);
-    if (breakdown) {
+    if (next && smin < 1e-12 * std::max(op_norm, 1e-300)) {
       cgs2(next, j + 1, nullptr);
-      if constexpr (std::is_same<T, double>::value) {
-        if (device_qr) block_qr_device(next, next);
-        else block_qr(next, next);
-      } else {
-        block_qr(next, next);
-      }
+      block_qr(next, next);
     }
-    if (next && (!device_qr || breakdown)) seal(j + 1);
+    if (next) seal(j + 1);
     P.S.push_back(S);
     FLZ_CUDA(cudaEventRecord(ev[2], st));
     FLZ_CUDA(cudaEventSynchronize(ev[2]));
@@ -611,10 +652,15 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
   std::vector<double> lastT, lastTheta;  // the last check's T_k and its eigenvalues (refinement)
   int64_t found = 0;
   for (int j = 0; j < nb_cap; ++j) {
-    E.step(j, filt, P, 1.0);
+    if (E.issued) E.step_finish(j, P, 1.0);  // issued before the previous check's host work
+    else E.step(j, filt, P, 1.0);
     k = j + 1;
     const bool last = (k == nb_cap) || ((int64_t)(k + 1) * r > n);
     if (k % p.check_every != 0 && !last) continue;
+    // the next block step runs on the GPU while the host works on this check
+    // (its results are dropped if the check ends the solve); the check's GPU
+    // work queues behind it and reads only the first k blocks
+    if (E.can_split() && !last) E.step_issue(j + 1, filt);
 
     // ---- convergence check ----
     const auto tc = Clock::now();
@@ -746,7 +792,10 @@ flz_status solve_impl(flz_solver* s, cudaStream_t st) {
       lastT.swap(T);
       lastTheta.swap(theta);
     }
-    if (converged || last) break;
+    if (converged || last) {
+      if (E.issued) E.step_finish(k, P, 1.0, false);
+      break;
+    }
   }
   FLZ_CUDA(cudaStreamSynchronize(st));
   if (E.tcb) {  // the last check's Ritz vectors ran after the last step's status read
