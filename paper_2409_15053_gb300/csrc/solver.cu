@@ -209,7 +209,9 @@ struct Engine {
     issued = true;
   }
   // keep = false: the step's results are not wanted (the solve stopped at the
-  // check it overlapped); it is only waited for and timed
+  // check it overlapped); it is only waited for, and its time counts in the
+  // solve's total but not in the filter and orthogonalization phases (which
+  // stay the time of the `iters` steps the results come from)
   void step_finish(int j, Projected& P, double op_norm, bool keep = true) {
     FLZ_CUDA(cudaEventSynchronize(ev[2]));
     issued = false;
@@ -236,6 +238,7 @@ struct Engine {
     }
     if (tcb) tcb->check_status();
     if (fx) fx_check_flag(A);
+    if (!keep) return;
     float a = 0.f, b = 0.f;
     FLZ_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
     FLZ_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]));
