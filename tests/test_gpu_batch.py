@@ -250,10 +250,12 @@ def test_batch_rejects_bad_arguments():
     flz.flz_matrix_destroy(h)
 
 
-@pytest.mark.parametrize("precision,tol,refine", [(flz.FLZ_PREC_FP32, 1e-6, 0), (flz.FLZ_PREC_FP64, 1e-10, 0),
-                                                  (flz.FLZ_PREC_FX64, 1e-10, 0), (flz.FLZ_PREC_FP32, 1e-8, 1)],
-                         ids=["fp32", "fp64", "fx64", "fp32-refined"])
-def test_full_size_batch64_matches_oracle_reference(precision, tol, refine):
+@pytest.mark.parametrize("precision,tol,refine,extra", [
+    (flz.FLZ_PREC_FP32, 1e-6, 0, {}), (flz.FLZ_PREC_FP64, 1e-10, 0, {}), (flz.FLZ_PREC_FX64, 1e-10, 0, {}),
+    (flz.FLZ_PREC_FP32, 1e-8, 1, {}), (flz.FLZ_PREC_FX64, 1e-10, 0, {"persistent": 1}),
+    (flz.FLZ_PREC_FX64, 1e-10, 0, {"tile_rows": 128})],
+    ids=["fp32", "fp64", "fx64", "fp32-refined", "fx64-persistent", "fx64-128-rows"])
+def test_full_size_batch64_matches_oracle_reference(precision, tol, refine, extra):
     # 64 problems, n log-uniform in [1e4, 2e5] (sum ~4.7e6), autotuned r,
     # degree 60: the batched launch shape the benchmark times, against the
     # eigenvalues the CPU oracle computed for every problem (tests/golden).
@@ -270,7 +272,7 @@ def test_full_size_batch64_matches_oracle_reference(precision, tol, refine):
     assert [csr_checksum(c) for c in csrs] == [p["matrix_checksum"] for p in ref]
     intervals = [(p["alpha"], p["beta"]) for p in ref]
     st, out = run_batch(csrs, intervals, block_size=0, degree=60, check_every=5, precision=precision, tol=tol,
-                        refine=refine)
+                        refine=refine, **extra)
     assert st == flz.FLZ_OK
     for c, p, o in zip(csrs, ref, out):
         want = np.array(p["eigenvalues"])
