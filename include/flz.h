@@ -167,7 +167,10 @@ typedef struct flz_params {
                            max(tol, 1e-5) (FP32) or max(tol, 1e-2) (BF16), then its wanted, guard and
                            extra Ritz pairs are refined to tol by filtered subspace iteration with the
                            FX64 filter (FP64 where it does not apply) and Rayleigh-Ritz on A in FP64: the
-                           mixed-precision form (not in the paper). See flz_stats.refine_sweeps. */
+                           mixed-precision form (not in the paper). See flz_stats.refine_sweeps. In a
+                           batch the lockstep phase stops at the same floor and every converged problem
+                           is refined on its own matrix from its found eigenvectors (plus guard and
+                           random extra columns), up to eight problems at a time on host threads. */
   int32_t start_mode;   /* flz_start_mode, used when start vectors are set; default FLZ_START_KRYLOV */
   int32_t persistent;   /* batches with the fixed-point filter only. 0 (default): one launch per degree
                            step, the steps of a block step replayed as a CUDA graph. 1: every degree of a
