@@ -72,11 +72,6 @@ __device__ __forceinline__ int problem_of(const int* soff, int count, int row) {
   return lo;
 }
 
-__device__ __forceinline__ void load_offsets(int* soff, const int* off, int count) {
-  for (int i = threadIdx.x; i <= count; i += blockDim.x) soff[i] = off[i];
-  __syncthreads();
-}
-
 // Fused degree step over all problems (same arithmetic as the single-problem
 // kernel) with per-problem coefficients coef[k * count + i] and degrees.
 template <int R, class MS, class VS, class AccS, bool FIRST>
