@@ -164,7 +164,7 @@ KERNEL_NAMES = {
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
 # is now, on this workload (profiles/); absent where no capture of the current
 # kernel exists.
-TRAFFIC = {("fx64", "forward"): 179.70e6 + 33.97e6}  # profiles/fx_sell_kernel_fx64_laplacian3d_100cubed_r4.md
+TRAFFIC = {("fx64", "forward"): 179.72e6 + 33.35e6}  # profiles/fx_sell_kernel_fx64_laplacian3d_100cubed_r4.md
 
 
 def alu_fraction(flz, fprec, csr, r, ms_per_launch):
