@@ -147,7 +147,7 @@ struct TcBasis {
   void project(int K, const double* W, int r, int ldw, const uint32_t* wmax, double* C, int ldc, cudaStream_t st);
   // W -= Q[:, :K] C; records the new column maxima of W in wmax_out if not null
   void subtract(int K, const double* C, int ldc, double* W, int r, int ldw, uint32_t* wmax_out, cudaStream_t st);
-  // X[:, :s] = Q[:, :K] C (C K x s with row stride ldc, X row stride ldx), four columns per pass
+  // X[:, :s] = Q[:, :K] C (C K x s with row stride ldc, X row stride ldx), eight columns per pass
   void multiply(int K, const double* C, int ldc, int s, double* X, int ldx, cudaStream_t st);
   // classical Gram-Schmidt twice of W (n x r) against columns 0..K-1; C, C2 the two projections
   void cgs2(int K, double* W, int r, double* C, double* C2, cudaStream_t st);
